@@ -1,0 +1,743 @@
+/*
+ * slm_oracle.c -- plain, slow, single-threaded CPU oracle of the Synchronised
+ * Louvain Method (Chiem, Havelange, Van Dooren, "A parallel implementation of
+ * the Synchronised Louvain Method", arXiv:1702.04645).
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this file.  The library's product path
+ * never calls it, links it or shares code with it.
+ *
+ * Every function follows one passage of the paper, cited beside it.  Where the
+ * paper is silent or ambiguous the reading taken is stated at the function.
+ * Graphs are symmetric CSR with int32 row pointers, sorted unique columns and
+ * positive int32 weights; a self-loop W_ii is stored once.  With W symmetric,
+ * the weighted modularity Q_w of Section 2.4 becomes
+ *     Q = (1/m_w^2) * sum_C ( m_w * W_in(C) - Sigma_C^2 ),
+ * with s_i = sum_j W_ij, m_w = sum_i s_i, Sigma_C = sum_{i in C} s_i and
+ * W_in(C) = sum_{i,j in C} W_ij.  Every gain below is that numerator's change
+ * divided by two, an exact int64 whenever m_w < 2^31.
+ *
+ * Random acceptance (Section 3.4, Algorithm MAXIMAL): the paper leaves the
+ * probability p to Browet's thesis.  Reading: a parameter P in [0, 2^32];
+ * node i at level t, sweep k is accepted iff
+ *     (mix64(seed ^ mix64((t<<48) | (k<<32) | i)) >> 32) < P,
+ * where mix64 is the splitmix64 output function (Steele, Lea, Flood 2014).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef int32_t i32;
+typedef int64_t i64;
+typedef uint64_t u64;
+
+#define ORC_FLAG_NO_POSITIVE 1u
+
+/* ------------------------------------------------------------------------- */
+/* splitmix64 output function, written from its published definition.        */
+/* ------------------------------------------------------------------------- */
+u64 orc_mix64(u64 z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* The 32-bit uniform draw p(i) of Algorithm MAXIMAL (reading above). */
+uint32_t orc_draw(u64 seed, i32 level, i32 sweep, i32 i) {
+    u64 ctr = ((u64)(uint32_t)level << 48) | ((u64)(uint32_t)sweep << 32) | (u64)(uint32_t)i;
+    return (uint32_t)(orc_mix64(seed ^ orc_mix64(ctr)) >> 32);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Strengths s_i and total weight m_w (Section 2.4, definition of m_w).      */
+/* ------------------------------------------------------------------------- */
+i64 orc_strengths(i32 n, const i32 *rp, const i32 *col, const i32 *w, i64 *s) {
+    i64 m = 0;
+    for (i32 i = 0; i < n; i++) {
+        i64 acc = 0;
+        for (i32 p = rp[i]; p < rp[i + 1]; p++) acc += w[p];
+        s[i] = acc;
+        m += acc;
+    }
+    (void)col;
+    return m;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Modularity (Section 2.4, Q_w) of a labelling, as the exact numerator      */
+/* sum_C (m_w W_in(C) - Sigma_C^2) and the quotient by m_w^2.                */
+/* labels take values in [0, n).                                             */
+/* ------------------------------------------------------------------------- */
+i64 orc_modularity_num(i32 n, const i32 *rp, const i32 *col, const i32 *w, const i32 *labels) {
+    i64 *s = (i64 *)calloc((size_t)n + 1, sizeof(i64));
+    i64 *win = (i64 *)calloc((size_t)n + 1, sizeof(i64));
+    i64 *sig = (i64 *)calloc((size_t)n + 1, sizeof(i64));
+    i64 m = orc_strengths(n, rp, col, w, s);
+    for (i32 u = 0; u < n; u++) {
+        sig[labels[u]] += s[u];
+        for (i32 p = rp[u]; p < rp[u + 1]; p++)
+            if (labels[col[p]] == labels[u]) win[labels[u]] += w[p];
+    }
+    __int128 num = 0;
+    for (i32 c = 0; c < n; c++)
+        num += (__int128)m * win[c] - (__int128)sig[c] * sig[c];
+    free(s); free(win); free(sig);
+    return (i64)num; /* |num| <= m_w^2 < 2^62 */
+}
+
+double orc_modularity(i32 n, const i32 *rp, const i32 *col, const i32 *w, const i32 *labels) {
+    i64 m = 0;
+    for (i32 p = 0; p < rp[n]; p++) m += w[p];
+    if (m == 0) return 0.0;
+    i64 num = orc_modularity_num(n, rp, col, w, labels);
+    return (double)num / ((double)m * (double)m);
+}
+
+/* ------------------------------------------------------------------------- */
+/* ASSIGN (Section 3.1, Algorithm ASSIGN): each node points at its best      */
+/* neighbour.  From the all-singleton state, moving i into {j} changes the   */
+/* numerator by 2 (m_w W_ij - s_i s_j).  Reading: self-assign when no        */
+/* neighbour gives a strictly positive gain; ties go to the smallest j.      */
+/* ------------------------------------------------------------------------- */
+void orc_assign(i32 n, const i32 *rp, const i32 *col, const i32 *w, const i64 *s, i64 m,
+                i32 *a) {
+    for (i32 i = 0; i < n; i++) {
+        i32 bestj = -1;
+        i64 bests = 0;
+        for (i32 p = rp[i]; p < rp[i + 1]; p++) {
+            i32 j = col[p];
+            if (j == i) continue;
+            i64 sc = m * (i64)w[p] - s[i] * s[j];
+            if (bestj < 0 || sc > bests || (sc == bests && j < bestj)) {
+                bestj = j;
+                bests = sc;
+            }
+        }
+        a[i] = (bestj >= 0 && bests > 0) ? bestj : i;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* COMPONENTS (Section 3.2, Algorithm ASSIGN's WCC): communities are the     */
+/* weakly connected components of the assignment graph, each holding one     */
+/* directed cycle.  Reading: a community is named by the smallest node id    */
+/* on its cycle.  Linear-time walk with three colours.                      */
+/* ------------------------------------------------------------------------- */
+void orc_rootlabel(i32 n, const i32 *a, i32 *root) {
+    unsigned char *state = (unsigned char *)calloc((size_t)n + 1, 1);
+    i32 *stack = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    for (i32 v = 0; v < n; v++) {
+        if (state[v] == 2) continue;
+        i32 top = 0, x = v;
+        while (state[x] == 0) {
+            state[x] = 1;
+            stack[top++] = x;
+            x = a[x];
+        }
+        i32 r;
+        if (state[x] == 1) {
+            /* x lies on a cycle found in this walk: its name is the cycle minimum */
+            r = x;
+            for (i32 y = a[x]; y != x; y = a[y])
+                if (y < r) r = y;
+            root[x] = r;
+            state[x] = 2;
+            for (i32 y = a[x]; y != x; y = a[y]) { root[y] = r; state[y] = 2; }
+        } else {
+            r = root[x];
+        }
+        for (i32 k = 0; k < top; k++) {
+            if (state[stack[k]] != 2) { root[stack[k]] = r; state[stack[k]] = 2; }
+        }
+    }
+    free(state);
+    free(stack);
+}
+
+/* Sigma_C = sum of s over the community named C (Section 2.4). */
+void orc_sigma(i32 n, const i32 *root, const i64 *s, i64 *sigma) {
+    for (i32 v = 0; v < n; v++) sigma[v] = 0;
+    for (i32 v = 0; v < n; v++) sigma[root[v]] += s[v];
+}
+
+/* ------------------------------------------------------------------------- */
+/* The per-node half of MAXIMAL (Section 3.4; Algorithm MAXIMAL's first      */
+/* loop): best community c_i^* among the communities of i's neighbours, and  */
+/* the local gain g(i) of Algorithm POSITIVE.  With k_{i,C} the weight from  */
+/* i to C (self-loop excluded), score(C) = m_w k_{i,C} - s_i (Sigma_C -      */
+/* [C = c_i] s_i); moving i from c_i to C changes the numerator by           */
+/* 2 (score(C) - score(c_i)).  Reading: c_i^* differs from c_i only when its */
+/* gain is strictly positive; ties go to the smallest community name.        */
+/* ------------------------------------------------------------------------- */
+void orc_scan(i32 n, const i32 *rp, const i32 *col, const i32 *w, const i64 *s, i64 m,
+              const i32 *root, const i64 *sigma, i32 *best, i64 *gain, i64 *g) {
+    i64 *acc = (i64 *)calloc((size_t)n + 1, sizeof(i64));
+    i32 *touched = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    for (i32 i = 0; i < n; i++) {
+        i32 nt = 0, ci = root[i];
+        for (i32 p = rp[i]; p < rp[i + 1]; p++) {
+            i32 j = col[p];
+            if (j == i) continue;
+            i32 c = root[j];
+            if (acc[c] == 0) touched[nt++] = c;
+            acc[c] += w[p];
+        }
+        i64 own = m * acc[ci] - s[i] * (sigma[ci] - s[i]);
+        i32 bc = -1;
+        i64 bs = 0;
+        for (i32 k = 0; k < nt; k++) {
+            i32 c = touched[k];
+            if (c == ci) continue;
+            i64 sc = m * acc[c] - s[i] * sigma[c];
+            if (bc < 0 || sc > bs || (sc == bs && c < bc)) { bc = c; bs = sc; }
+        }
+        for (i32 k = 0; k < nt; k++) acc[touched[k]] = 0;
+        g[i] = own;
+        if (bc >= 0 && bs - own > 0) { best[i] = bc; gain[i] = bs - own; }
+        else { best[i] = ci; gain[i] = 0; }
+    }
+    free(acc);
+    free(touched);
+}
+
+/* Children lists of the assignment graph (reverse of a, self-loops dropped). */
+static void build_children(i32 n, const i32 *a, i32 *cp, i32 *ch) {
+    for (i32 v = 0; v <= n; v++) cp[v] = 0;
+    for (i32 v = 0; v < n; v++) if (a[v] != v) cp[a[v] + 1]++;
+    for (i32 v = 0; v < n; v++) cp[v + 1] += cp[v];
+    i32 *fill = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    memcpy(fill, cp, ((size_t)n + 1) * sizeof(i32));
+    for (i32 v = 0; v < n; v++) if (a[v] != v) ch[fill[a[v]]++] = v;
+    free(fill);
+}
+
+/* Tail of i (Section 3.4): every node with a directed path to i in the      */
+/* assignment graph, plus i.  Reverse breadth-first search; returns size.    */
+static i32 tail_of(i32 i, const i32 *cp, const i32 *ch, i32 *out, unsigned char *mark) {
+    i32 head = 0, tl = 0;
+    out[tl++] = i;
+    mark[i] = 1;
+    while (head < tl) {
+        i32 x = out[head++];
+        for (i32 k = cp[x]; k < cp[x + 1]; k++) {
+            i32 y = ch[k];
+            if (y >= 0 && !mark[y]) { mark[y] = 1; out[tl++] = y; }
+        }
+    }
+    return tl;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Branch gain Delta H(c_i -> b(i) -> c_i^*) (Algorithm MAXIMAL): moving the */
+/* tail S of i from A = c_i to B changes the numerator by twice              */
+/*   m_w (W(S,B) - W(S, A\S)) - Sigma_S (Sigma_B - Sigma_A + Sigma_S).       */
+/* ------------------------------------------------------------------------- */
+static i64 branch_gain_impl(i32 i, i32 B, const i32 *rp, const i32 *col, const i32 *w,
+                            const i64 *s, i64 m, const i32 *root, const i64 *sigma,
+                            const i32 *cp, const i32 *ch, i32 *buf, unsigned char *mark) {
+    i32 A = root[i];
+    i32 k = tail_of(i, cp, ch, buf, mark);
+    i64 sS = 0, wB = 0, wA = 0;
+    for (i32 t = 0; t < k; t++) {
+        i32 u = buf[t];
+        sS += s[u];
+        for (i32 p = rp[u]; p < rp[u + 1]; p++) {
+            i32 v = col[p];
+            if (root[v] == B) wB += w[p];
+            else if (root[v] == A && !mark[v]) wA += w[p];
+        }
+    }
+    for (i32 t = 0; t < k; t++) mark[buf[t]] = 0;
+    return m * (wB - wA) - sS * (sigma[B] - sigma[A] + sS);
+}
+
+i64 orc_branch_gain(i32 n, const i32 *rp, const i32 *col, const i32 *w, const i64 *s, i64 m,
+                    const i32 *a, const i32 *root, const i64 *sigma, i32 i, i32 B) {
+    i32 *cp = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    i32 *ch = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    i32 *buf = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    unsigned char *mark = (unsigned char *)calloc((size_t)n + 1, 1);
+    build_children(n, a, cp, ch);
+    i64 r = branch_gain_impl(i, B, rp, col, w, s, m, root, sigma, cp, ch, buf, mark);
+    free(cp); free(ch); free(buf); free(mark);
+    return r;
+}
+
+/* Target node (Algorithm MAXIMAL, update of a(i)): the neighbour j of i in  */
+/* community B maximising m_w W_ij - s_i s_j.  Reading: ties go to the       */
+/* smallest j; the maximum is taken even when negative.                      */
+i32 orc_target(const i32 *rp, const i32 *col, const i32 *w, const i64 *s, i64 m,
+               const i32 *root, i32 i, i32 B) {
+    i32 bj = -1;
+    i64 bs = 0;
+    for (i32 p = rp[i]; p < rp[i + 1]; p++) {
+        i32 j = col[p];
+        if (j == i || root[j] != B) continue;
+        i64 sc = m * (i64)w[p] - s[i] * s[j];
+        if (bj < 0 || sc > bs || (sc == bs && j < bj)) { bj = j; bs = sc; }
+    }
+    return bj;
+}
+
+/* ------------------------------------------------------------------------- */
+/* POSITIVE (Section 3.3, Algorithm POSITIVE).  The local gain of i is       */
+/* g(i) = m_w k_{i,c_i} - s_i (Sigma_{c_i} - s_i).  A community holding a    */
+/* node with g < 0 is bisected optimally, and the parts are examined again,  */
+/* until no node has a negative local gain.  Candidate bisections:           */
+/*   branch cut at a non-cycle node u: a(u) <- u, parts tail(u) and rest;    */
+/*   cycle cut at two distinct cycle nodes u, v: a(u) <- u, a(v) <- v, each  */
+/*   part being the nodes whose path reaches u (resp. v) first.              */
+/* Splitting A into S and R changes the numerator by twice                   */
+/*   Sigma_S Sigma_R - m_w W(S,R).                                           */
+/* Readings: the best split is applied even when that value is not positive; */
+/* ties prefer the larger value, then a branch cut over a cycle cut, then    */
+/* the smaller u, then the smaller v.  Communities are independent (Section  */
+/* 4.2), so the order in which they are examined does not matter.            */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    i32 n;
+    const i32 *rp, *col, *w;
+    const i64 *s;
+    i64 m;
+    i32 *a, *root;
+    /* scratch */
+    i32 *cp, *ch, *buf, *entry, *cyc, *cidx, *stk;
+    unsigned char *mark, *inpart, *oncyc, *state;
+} pos_ctx;
+
+/* Re-name the members of one community after its assignments changed. */
+static void relabel_members(pos_ctx *c, const i32 *mem, i32 cnt) {
+    /* the forward path of a member never leaves the member set */
+    for (i32 k = 0; k < cnt; k++) c->state[mem[k]] = 0;
+    for (i32 k = 0; k < cnt; k++) {
+        i32 v = mem[k];
+        if (c->state[v] == 2) continue;
+        i32 top = 0, x = v;
+        while (c->state[x] == 0) { c->state[x] = 1; c->stk[top++] = x; x = c->a[x]; }
+        i32 r;
+        if (c->state[x] == 1) {
+            r = x;
+            for (i32 y = c->a[x]; y != x; y = c->a[y]) if (y < r) r = y;
+            c->root[x] = r; c->state[x] = 2;
+            for (i32 y = c->a[x]; y != x; y = c->a[y]) { c->root[y] = r; c->state[y] = 2; }
+        } else r = c->root[x];
+        for (i32 t = 0; t < top; t++)
+            if (c->state[c->stk[t]] != 2) { c->root[c->stk[t]] = r; c->state[c->stk[t]] = 2; }
+    }
+}
+
+/* W(S, A\S) where S is marked in c->inpart and A is the community named A. */
+static i64 cut_weight(pos_ctx *c, const i32 *S, i32 k, i32 A) {
+    i64 tot = 0;
+    for (i32 t = 0; t < k; t++) {
+        i32 u = S[t];
+        for (i32 p = c->rp[u]; p < c->rp[u + 1]; p++) {
+            i32 v = c->col[p];
+            if (c->root[v] == A && !c->inpart[v]) tot += c->w[p];
+        }
+    }
+    return tot;
+}
+
+/* Remove x from the children list of its old parent (children lists are    */
+/* kept consistent with a across splits).                                    */
+static void drop_child(pos_ctx *c, i32 parent, i32 x) {
+    for (i32 k = c->cp[parent]; k < c->cp[parent + 1]; k++)
+        if (c->ch[k] == x) { c->ch[k] = -1; return; }
+}
+
+/* Examine one community (members mem[0..cnt)); split it if a member has a   */
+/* negative local gain.  Returns 1 when split (mem reordered so that the     */
+/* first *k1 members form one part), 0 otherwise.                            */
+static int positive_one(pos_ctx *c, i32 *mem, i32 cnt, i32 *k1) {
+    if (cnt < 2) return 0;
+    i32 A = c->root[mem[0]];
+    i64 sigA = 0;
+    for (i32 t = 0; t < cnt; t++) sigA += c->s[mem[t]];
+    int neg = 0;
+    for (i32 t = 0; t < cnt && !neg; t++) {
+        i32 i = mem[t];
+        i64 kown = 0;
+        for (i32 p = c->rp[i]; p < c->rp[i + 1]; p++) {
+            i32 j = c->col[p];
+            if (j != i && c->root[j] == A) kown += c->w[p];
+        }
+        i64 g = c->m * kown - c->s[i] * (sigA - c->s[i]);
+        if (g < 0) neg = 1;
+    }
+    if (!neg) return 0;
+
+    /* the cycle of the community, listed from its smallest node */
+    i32 L = 0;
+    {
+        i32 x = mem[0];
+        for (i32 t = 0; t < cnt; t++) c->mark[mem[t]] = 0;
+        while (!c->mark[x]) { c->mark[x] = 1; x = c->a[x]; }
+        i32 r = x;
+        for (i32 y = c->a[x]; y != x; y = c->a[y]) if (y < r) r = y;
+        i32 y = r;
+        do { c->cyc[L] = y; c->cidx[y] = L; L++; y = c->a[y]; } while (y != r);
+        for (i32 t = 0; t < cnt; t++) c->mark[mem[t]] = 0;
+        for (i32 t = 0; t < cnt; t++) c->oncyc[mem[t]] = 0;
+        for (i32 t = 0; t < L; t++) c->oncyc[c->cyc[t]] = 1;
+    }
+
+    int have = 0, btype = 0;
+    i64 bscore = 0;
+    i32 bu = -1, bv = -1;
+#define ORC_BETTER(sc, ty, uu, vv) \
+    (!have || (sc) > bscore || ((sc) == bscore && ((ty) < btype || ((ty) == btype && \
+      ((uu) < bu || ((uu) == bu && (vv) < bv))))))
+
+    /* branch cuts */
+    for (i32 t = 0; t < cnt; t++) {
+        i32 u = mem[t];
+        if (c->oncyc[u]) continue;
+        i32 k = tail_of(u, c->cp, c->ch, c->buf, c->inpart);
+        i64 sS = 0;
+        for (i32 q = 0; q < k; q++) sS += c->s[c->buf[q]];
+        i64 cw = cut_weight(c, c->buf, k, A);
+        for (i32 q = 0; q < k; q++) c->inpart[c->buf[q]] = 0;
+        i64 sc = sS * (sigA - sS) - c->m * cw;
+        if (ORC_BETTER(sc, 0, u, -1)) { have = 1; bscore = sc; btype = 0; bu = u; bv = -1; }
+    }
+    /* cycle cuts */
+    if (L >= 2) {
+        /* entry[v] = index of the first cycle node on v's path */
+        for (i32 t = 0; t < cnt; t++) {
+            i32 x = mem[t];
+            while (!c->oncyc[x]) x = c->a[x];
+            c->entry[mem[t]] = c->cidx[x];
+        }
+        for (i32 p = 0; p < L; p++) {
+            for (i32 q = p + 1; q < L; q++) {
+                /* part V: entries in (p, q] */
+                i32 k = 0;
+                i64 sV = 0;
+                for (i32 t = 0; t < cnt; t++) {
+                    i32 x = mem[t];
+                    if (c->entry[x] > p && c->entry[x] <= q) {
+                        c->buf[k++] = x; c->inpart[x] = 1; sV += c->s[x];
+                    }
+                }
+                i64 cw = cut_weight(c, c->buf, k, A);
+                for (i32 t = 0; t < k; t++) c->inpart[c->buf[t]] = 0;
+                i64 sc = sV * (sigA - sV) - c->m * cw;
+                i32 u = c->cyc[p] < c->cyc[q] ? c->cyc[p] : c->cyc[q];
+                i32 v = c->cyc[p] < c->cyc[q] ? c->cyc[q] : c->cyc[p];
+                if (ORC_BETTER(sc, 1, u, v)) { have = 1; bscore = sc; btype = 1; bu = u; bv = v; }
+            }
+        }
+    }
+#undef ORC_BETTER
+    /* apply: the removed assignments become self-assignments */
+    drop_child(c, c->a[bu], bu);
+    c->a[bu] = bu;
+    if (btype == 1) { drop_child(c, c->a[bv], bv); c->a[bv] = bv; }
+    relabel_members(c, mem, cnt);
+    /* reorder members: part of bu first */
+    i32 r1 = c->root[bu];
+    i32 lo = 0, hi = cnt - 1;
+    while (lo <= hi) {
+        if (c->root[mem[lo]] == r1) lo++;
+        else { i32 tmp = mem[lo]; mem[lo] = mem[hi]; mem[hi] = tmp; hi--; }
+    }
+    *k1 = lo;
+    return 1;
+}
+
+i32 orc_positive(i32 n, const i32 *rp, const i32 *col, const i32 *w, const i64 *s, i64 m,
+                 i32 *a, i32 *root) {
+    pos_ctx c;
+    c.n = n; c.rp = rp; c.col = col; c.w = w; c.s = s; c.m = m; c.a = a; c.root = root;
+    size_t N = (size_t)n + 1;
+    c.cp = (i32 *)malloc(N * sizeof(i32));
+    c.ch = (i32 *)malloc(N * sizeof(i32));
+    c.buf = (i32 *)malloc(N * sizeof(i32));
+    c.entry = (i32 *)malloc(N * sizeof(i32));
+    c.cyc = (i32 *)malloc(N * sizeof(i32));
+    c.cidx = (i32 *)malloc(N * sizeof(i32));
+    c.stk = (i32 *)malloc(N * sizeof(i32));
+    c.mark = (unsigned char *)calloc(N, 1);
+    c.inpart = (unsigned char *)calloc(N, 1);
+    c.oncyc = (unsigned char *)calloc(N, 1);
+    c.state = (unsigned char *)calloc(N, 1);
+    build_children(n, a, c.cp, c.ch); /* entries set to -1 are removed children */
+    /* members grouped by community name */
+    i32 *mem = (i32 *)malloc(N * sizeof(i32));
+    i32 *cnt = (i32 *)calloc(N, sizeof(i32));
+    i32 *off = (i32 *)calloc(N + 1, sizeof(i32));
+    for (i32 v = 0; v < n; v++) cnt[root[v]]++;
+    for (i32 v = 0; v < n; v++) off[v + 1] = off[v] + cnt[v];
+    for (i32 v = 0; v < n; v++) cnt[v] = 0;
+    for (i32 v = 0; v < n; v++) mem[off[root[v]] + cnt[root[v]]++] = v;
+    /* work list of member ranges */
+    i32 *wl_off = (i32 *)malloc(2 * N * sizeof(i32));
+    i32 *wl_len = (i32 *)malloc(2 * N * sizeof(i32));
+    i32 nw = 0;
+    for (i32 v = n - 1; v >= 0; v--)
+        if (cnt[v] > 0) { wl_off[nw] = off[v]; wl_len[nw] = cnt[v]; nw++; }
+    i32 splits = 0;
+    while (nw > 0) {
+        nw--;
+        i32 o = wl_off[nw], l = wl_len[nw], k1 = 0;
+        if (positive_one(&c, mem + o, l, &k1)) {
+            splits++;
+            wl_off[nw] = o; wl_len[nw] = k1; nw++;
+            wl_off[nw] = o + k1; wl_len[nw] = l - k1; nw++;
+        }
+    }
+    free(mem); free(cnt); free(off); free(wl_off); free(wl_len);
+    free(c.cp); free(c.ch); free(c.buf); free(c.entry); free(c.cyc); free(c.cidx); free(c.stk);
+    free(c.mark); free(c.inpart); free(c.oncyc); free(c.state);
+    return splits;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Compaction of community names into ids 0..K-1, ordered by name (the       */
+/* relabelling that AGGREGATE of Section 3.5 implies).                       */
+/* ------------------------------------------------------------------------- */
+i32 orc_compact(i32 n, const i32 *root, i32 *id) {
+    i32 *rank = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    i32 K = 0;
+    for (i32 v = 0; v < n; v++) rank[v] = (root[v] == v) ? K++ : -1;
+    for (i32 v = 0; v < n; v++) id[v] = rank[root[v]];
+    free(rank);
+    return K;
+}
+
+/* ------------------------------------------------------------------------- */
+/* AGGREGATE (Section 3.5): each community becomes a super node; the weight  */
+/* between super nodes A and B is the sum of W_uv over u in A, v in B, the   */
+/* diagonal included, so strengths and m_w are preserved.  Output CSR with  */
+/* sorted unique columns; returns nnz of the result.                          */
+/* ------------------------------------------------------------------------- */
+i32 orc_aggregate(i32 n, const i32 *rp, const i32 *col, const i32 *w, const i32 *id, i32 K,
+                  i32 *rp_out, i32 *col_out, i32 *w_out) {
+    i64 *acc = (i64 *)calloc((size_t)K + 1, sizeof(i64));
+    i32 *touched = (i32 *)malloc(((size_t)K + 1) * sizeof(i32));
+    /* members of each super node */
+    i32 *cnt = (i32 *)calloc((size_t)K + 1, sizeof(i32));
+    i32 *off = (i32 *)calloc((size_t)K + 2, sizeof(i32));
+    i32 *mem = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    for (i32 v = 0; v < n; v++) cnt[id[v]]++;
+    for (i32 A = 0; A < K; A++) off[A + 1] = off[A] + cnt[A];
+    for (i32 A = 0; A < K; A++) cnt[A] = 0;
+    for (i32 v = 0; v < n; v++) mem[off[id[v]] + cnt[id[v]]++] = v;
+    i32 nnz = 0;
+    rp_out[0] = 0;
+    for (i32 A = 0; A < K; A++) {
+        i32 nt = 0;
+        for (i32 t = off[A]; t < off[A + 1]; t++) {
+            i32 u = mem[t];
+            for (i32 p = rp[u]; p < rp[u + 1]; p++) {
+                i32 B = id[col[p]];
+                if (acc[B] == 0) touched[nt++] = B;
+                acc[B] += w[p];
+            }
+        }
+        /* sorted columns: insertion sort of the touched list */
+        for (i32 x = 1; x < nt; x++) {
+            i32 key = touched[x], y = x - 1;
+            while (y >= 0 && touched[y] > key) { touched[y + 1] = touched[y]; y--; }
+            touched[y + 1] = key;
+        }
+        for (i32 x = 0; x < nt; x++) {
+            col_out[nnz] = touched[x];
+            w_out[nnz] = (i32)acc[touched[x]];
+            nnz++;
+            acc[touched[x]] = 0;
+        }
+        rp_out[A + 1] = nnz;
+    }
+    free(acc); free(touched); free(cnt); free(off); free(mem);
+    return nnz;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The whole method (Section 3, Algorithm 1).                                */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    i32 n0;
+    i32 levels;
+    i32 cap;
+    i32 *level_n, *level_K;
+    i32 **level_labels;
+    i32 *final_labels;
+    /* per level statistics */
+    i32 *sweeps, *status; /* status: 0 converged, 1 stalled, 2 sweep limit */
+    i64 *moves, *splits, *cands, *edges_scanned;
+    /* per sweep trace: level, sweep, candidates, positive, accepted, splits */
+    i64 *trace;
+    i64 ntrace, trace_cap;
+    int level_limit_hit;
+    int top_status; /* sweep status of the last, unrecorded level */
+    i32 top_sweeps;
+} orc_run;
+
+static void run_grow(orc_run *r) {
+    if (r->levels < r->cap) return;
+    r->cap = r->cap ? 2 * r->cap : 8;
+    r->level_n = (i32 *)realloc(r->level_n, (size_t)r->cap * sizeof(i32));
+    r->level_K = (i32 *)realloc(r->level_K, (size_t)r->cap * sizeof(i32));
+    r->level_labels = (i32 **)realloc(r->level_labels, (size_t)r->cap * sizeof(i32 *));
+    r->sweeps = (i32 *)realloc(r->sweeps, (size_t)r->cap * sizeof(i32));
+    r->status = (i32 *)realloc(r->status, (size_t)r->cap * sizeof(i32));
+    r->moves = (i64 *)realloc(r->moves, (size_t)r->cap * sizeof(i64));
+    r->splits = (i64 *)realloc(r->splits, (size_t)r->cap * sizeof(i64));
+    r->cands = (i64 *)realloc(r->cands, (size_t)r->cap * sizeof(i64));
+    r->edges_scanned = (i64 *)realloc(r->edges_scanned, (size_t)r->cap * sizeof(i64));
+}
+
+static void trace_push(orc_run *r, i64 lv, i64 sw, i64 cand, i64 pos, i64 acc, i64 spl) {
+    if (r->ntrace == r->trace_cap) {
+        r->trace_cap = r->trace_cap ? 2 * r->trace_cap : 256;
+        r->trace = (i64 *)realloc(r->trace, (size_t)r->trace_cap * 6 * sizeof(i64));
+    }
+    i64 *t = r->trace + 6 * r->ntrace++;
+    t[0] = lv; t[1] = sw; t[2] = cand; t[3] = pos; t[4] = acc; t[5] = spl;
+}
+
+orc_run *orc_slm(i32 n0, const i32 *rp0, const i32 *col0, const i32 *w0, u64 seed, u64 P,
+                 i32 max_sweeps, i32 max_levels, uint32_t flags) {
+    orc_run *r = (orc_run *)calloc(1, sizeof(orc_run));
+    r->n0 = n0;
+    r->final_labels = (i32 *)malloc(((size_t)n0 + 1) * sizeof(i32));
+    for (i32 v = 0; v < n0; v++) r->final_labels[v] = v;
+    /* current level graph (owned copies) */
+    i32 n = n0;
+    i32 nnz = rp0[n0];
+    i32 *rp = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    i32 *col = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+    i32 *w = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+    memcpy(rp, rp0, ((size_t)n + 1) * sizeof(i32));
+    memcpy(col, col0, (size_t)nnz * sizeof(i32));
+    memcpy(w, w0, (size_t)nnz * sizeof(i32));
+    i32 t = 0;
+    for (;;) {
+        size_t N = (size_t)n + 1;
+        i64 *s = (i64 *)malloc(N * sizeof(i64));
+        i64 *sigma = (i64 *)malloc(N * sizeof(i64));
+        i64 *gain = (i64 *)malloc(N * sizeof(i64));
+        i64 *g = (i64 *)malloc(N * sizeof(i64));
+        i64 *bg = (i64 *)malloc(N * sizeof(i64));
+        i32 *a = (i32 *)malloc(N * sizeof(i32));
+        i32 *root = (i32 *)malloc(N * sizeof(i32));
+        i32 *best = (i32 *)malloc(N * sizeof(i32));
+        i32 *tgt = (i32 *)malloc(N * sizeof(i32));
+        i32 *cp = (i32 *)malloc(N * sizeof(i32));
+        i32 *ch = (i32 *)malloc(N * sizeof(i32));
+        i32 *buf = (i32 *)malloc(N * sizeof(i32));
+        unsigned char *mark = (unsigned char *)calloc(N, 1);
+        unsigned char *acc = (unsigned char *)calloc(N, 1);
+        i64 m = orc_strengths(n, rp, col, w, s);
+
+        /* ASSIGN, COMPONENTS, POSITIVE (Algorithm 1, first two lines of the loop) */
+        orc_assign(n, rp, col, w, s, m, a);
+        orc_rootlabel(n, a, root);
+        i64 lv_splits = 0, lv_moves = 0, lv_cands = 0, lv_edges = 0;
+        if (!(flags & ORC_FLAG_NO_POSITIVE)) lv_splits += orc_positive(n, rp, col, w, s, m, a, root);
+
+        /* alternate MAXIMAL and POSITIVE while a positive move exists; on exit
+           `sweep` counts the scans performed */
+        i32 sweep = 0;
+        int status = 2;
+        for (; sweep < max_sweeps; sweep++) {
+            orc_sigma(n, root, s, sigma);
+            orc_scan(n, rp, col, w, s, m, root, sigma, best, gain, g);
+            lv_edges += nnz;
+            i64 ncand = 0, npos = 0, nacc = 0, nspl = 0;
+            for (i32 i = 0; i < n; i++) if (gain[i] > 0) ncand++;
+            lv_cands += ncand;
+            if (ncand == 0) { status = 0; trace_push(r, t, sweep, 0, 0, 0, 0); sweep++; break; }
+            build_children(n, a, cp, ch);
+            for (i32 i = 0; i < n; i++) {
+                acc[i] = 0;
+                if (gain[i] <= 0) continue;
+                bg[i] = branch_gain_impl(i, best[i], rp, col, w, s, m, root, sigma, cp, ch, buf, mark);
+                if (bg[i] > 0) {
+                    npos++;
+                    if ((u64)orc_draw(seed, t, sweep, i) < P) acc[i] = 1;
+                }
+            }
+            if (npos == 0) { status = 1; trace_push(r, t, sweep, ncand, 0, 0, 0); sweep++; break; }
+            /* targets on the snapshot, then one synchronous write */
+            for (i32 i = 0; i < n; i++)
+                if (acc[i]) { tgt[i] = orc_target(rp, col, w, s, m, root, i, best[i]); nacc++; }
+            for (i32 i = 0; i < n; i++) if (acc[i]) a[i] = tgt[i];
+            lv_moves += nacc;
+            if (nacc > 0) {
+                orc_rootlabel(n, a, root);
+                if (!(flags & ORC_FLAG_NO_POSITIVE)) nspl = orc_positive(n, rp, col, w, s, m, a, root);
+                lv_splits += nspl;
+            }
+            trace_push(r, t, sweep, ncand, npos, nacc, nspl);
+        }
+        i32 *id = (i32 *)malloc(N * sizeof(i32));
+        i32 K = orc_compact(n, root, id);
+        free(s); free(sigma); free(gain); free(g); free(bg); free(a); free(root); free(best);
+        free(tgt); free(cp); free(ch); free(buf); free(mark); free(acc);
+        if (K == n) {
+            /* no community structure left: stop without recording the level */
+            r->top_status = status;
+            r->top_sweeps = sweep;
+            free(id);
+            break;
+        }
+        run_grow(r);
+        r->level_n[r->levels] = n;
+        r->level_K[r->levels] = K;
+        r->level_labels[r->levels] = id;
+        r->sweeps[r->levels] = sweep;
+        r->status[r->levels] = status;
+        r->moves[r->levels] = lv_moves;
+        r->splits[r->levels] = lv_splits;
+        r->cands[r->levels] = lv_cands;
+        r->edges_scanned[r->levels] = lv_edges;
+        r->levels++;
+        for (i32 v = 0; v < n0; v++) r->final_labels[v] = id[r->final_labels[v]];
+        /* AGGREGATE */
+        i32 *rp2 = (i32 *)malloc(((size_t)K + 1) * sizeof(i32));
+        i32 *col2 = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+        i32 *w2 = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+        i32 nnz2 = orc_aggregate(n, rp, col, w, id, K, rp2, col2, w2);
+        free(rp); free(col); free(w);
+        rp = rp2; col = col2; w = w2; n = K; nnz = nnz2;
+        t++;
+        if (t >= max_levels) { r->level_limit_hit = 1; break; }
+    }
+    free(rp); free(col); free(w);
+    return r;
+}
+
+/* accessors for the test harness */
+i32 orc_run_levels(const orc_run *r) { return r->levels; }
+i32 orc_run_level_n(const orc_run *r, i32 l) { return r->level_n[l]; }
+i32 orc_run_level_K(const orc_run *r, i32 l) { return r->level_K[l]; }
+void orc_run_level_labels(const orc_run *r, i32 l, i32 *out) {
+    memcpy(out, r->level_labels[l], (size_t)r->level_n[l] * sizeof(i32));
+}
+void orc_run_final_labels(const orc_run *r, i32 *out) {
+    memcpy(out, r->final_labels, (size_t)r->n0 * sizeof(i32));
+}
+/* stats: sweeps, status, moves, splits, candidates, edges scanned */
+void orc_run_level_stats(const orc_run *r, i32 l, i64 *out6) {
+    out6[0] = r->sweeps[l]; out6[1] = r->status[l]; out6[2] = r->moves[l];
+    out6[3] = r->splits[l]; out6[4] = r->cands[l]; out6[5] = r->edges_scanned[l];
+}
+i64 orc_run_trace_len(const orc_run *r) { return r->ntrace; }
+void orc_run_trace(const orc_run *r, i64 *out) {
+    memcpy(out, r->trace, (size_t)r->ntrace * 6 * sizeof(i64));
+}
+void orc_run_top(const orc_run *r, i32 *out3) {
+    out3[0] = r->top_status; out3[1] = r->top_sweeps; out3[2] = r->level_limit_hit;
+}
+void orc_run_free(orc_run *r) {
+    if (!r) return;
+    for (i32 l = 0; l < r->levels; l++) free(r->level_labels[l]);
+    free(r->level_labels); free(r->level_n); free(r->level_K); free(r->final_labels);
+    free(r->sweeps); free(r->status); free(r->moves); free(r->splits); free(r->cands);
+    free(r->edges_scanned); free(r->trace);
+    free(r);
+}
