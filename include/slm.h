@@ -1,0 +1,132 @@
+/*
+ * slm.h -- C ABI of the GB300 implementation of the Synchronised Louvain
+ * Method (Chiem, Havelange, Van Dooren, "A parallel implementation of the
+ * Synchronised Louvain Method", arXiv:1702.04645, Section 3, Algorithm 1).
+ *
+ * Input: an undirected graph given as a symmetric CSR with int32 row
+ * pointers, int32 column indices sorted ascending and unique in every row,
+ * and positive int32 weights (NULL means unit weights); a self-loop W_ii is
+ * stored once.  Output: one partition per hierarchical level (Section 3.5)
+ * and the final partition of the input nodes (Algorithm 1, C = C_t C).
+ *
+ * Arithmetic: with s_i = sum_j W_ij and m_w = sum_i s_i, every modularity gain
+ * is compared as the exact int64 value m_w * k - s * Sigma (Section 2.4, Q_w),
+ * so results are reproducible bit for bit.  m_w must be below 2^31.
+ *
+ * Conventions for every function:
+ *   - the return value is an slm_status; no function aborts or exits;
+ *   - `stream` is a cudaStream_t (NULL: the legacy default stream);
+ *   - `where` says whether a pointer is host (SLM_HOST) or device (SLM_DEVICE)
+ *     memory of the current device;
+ *   - inputs are copied; the caller keeps ownership of every pointer it passes;
+ *   - the library allocates its device memory with cudaMallocAsync on the
+ *     given stream and frees it in slm_destroy_graph.
+ */
+#ifndef SLM_H
+#define SLM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SLM_OK = 0,
+    SLM_ERR_INVALID_ARGUMENT = 1, /* bad pointer, size, unsorted/duplicate column, w <= 0 */
+    SLM_ERR_NOT_SYMMETRIC = 2,    /* W_ij != W_ji for some pair */
+    SLM_ERR_OVERFLOW = 3,         /* m_w >= 2^31: int64 gains would not be exact */
+    SLM_ERR_OUT_OF_MEMORY = 4,    /* device allocation failed; state unchanged */
+    SLM_ERR_CUDA = 5,             /* a CUDA call failed; see slm_last_error */
+    SLM_ERR_NOT_RUN = 6,          /* results asked before slm_run */
+    SLM_ERR_NOT_CONVERGED = 7,    /* sweep limit reached and SLM_FLAG_STRICT set */
+    SLM_ERR_TIMEOUT = 8,          /* reserved for bounded device-side waits */
+    SLM_ERR_BUDGET = 9            /* reserved for admission against a memory budget */
+} slm_status;
+
+#define SLM_HOST 0
+#define SLM_DEVICE 1
+
+/* Option flags. */
+#define SLM_FLAG_NO_POSITIVE 1u /* skip POSITIVE (ablation; Section 3.3) */
+#define SLM_FLAG_STRICT 2u      /* sweep limit reached => SLM_ERR_NOT_CONVERGED */
+
+typedef struct slm_graph slm_graph; /* opaque, owned by the library */
+
+typedef struct {
+    /* Seed of the counter-based draw that accepts a maximal correction with
+       probability P / 2^32 (Algorithm MAXIMAL, "draw p(i)"; the paper leaves p
+       to Browet's thesis, so P is a parameter).  Node i of level t in sweep k
+       is accepted iff (mix64(seed ^ mix64(t<<48 | k<<32 | i)) >> 32) < P, with
+       mix64 the splitmix64 output function. */
+    uint64_t seed;
+    uint64_t accept_p32;  /* P in [0, 2^32]; default 2^31 (p = 1/2) */
+    int32_t max_sweeps;   /* MAXIMAL+POSITIVE rounds per level (Algorithm 1 inner loop); default 1000, <= 65535 */
+    int32_t max_levels;   /* aggregation levels (Algorithm 1 outer loop); default 64, <= 65535 */
+    uint32_t flags;       /* SLM_FLAG_* */
+} slm_options;
+
+typedef struct {
+    int32_t n;              /* nodes of this level's graph */
+    int32_t n_communities;  /* K: communities found at this level */
+    int32_t sweeps;         /* scans performed by the inner loop */
+    int32_t status;         /* 0 converged, 1 stalled (no candidate with a positive branch gain), 2 sweep limit */
+    int64_t moves;          /* accepted maximal corrections */
+    int64_t splits;         /* positive corrections (bisections) */
+    int64_t candidates;     /* nodes with a positive single-node gain, summed over scans */
+    int64_t edges_scanned;  /* CSR entries read by the scans (sweeps * nnz) */
+    int64_t nnz;            /* stored entries of this level's graph */
+} slm_level_stats;
+
+/* Fill *opt with the defaults above. */
+void slm_default_options(slm_options *opt);
+
+/* Copy a symmetric CSR graph to the device and validate it (Section 2.4
+ * defines s_i and m_w, computed here).  row_ptr has n+1 entries, col_idx and
+ * weights row_ptr[n] entries, all in `where` memory.  Errors:
+ * INVALID_ARGUMENT, NOT_SYMMETRIC, OVERFLOW, OUT_OF_MEMORY, CUDA.  On success
+ * *out owns device copies; destroy it with slm_destroy_graph. */
+slm_status slm_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                            const int32_t *weights, int where, void *stream, slm_graph **out);
+
+/* Run Algorithm 1 on the graph: per level ASSIGN, COMPONENTS, POSITIVE, then
+ * MAXIMAL and POSITIVE alternately until no positive move remains, then
+ * AGGREGATE; stop when a level finds no community structure.  Replaces the
+ * results of any previous run.  Returns after the work on `stream` has
+ * finished (the host reads a few counters per sweep). */
+slm_status slm_run(slm_graph *g, const slm_options *opt, void *stream);
+
+/* Number of recorded (aggregated) levels of the last run. */
+slm_status slm_num_levels(const slm_graph *g, int32_t *levels);
+
+/* Partition of level `level` on that level's nodes (community ids 0..K-1,
+ * ordered by the smallest node on each community's assignment cycle), or with
+ * level = -1 the final partition composed onto the input nodes.  `labels`
+ * must hold n_level (resp. n) int32 in `where` memory; *n_communities gets K.
+ * Synchronous. */
+slm_status slm_get_partition(const slm_graph *g, int32_t level, int32_t *labels, int where,
+                             int32_t *n_communities);
+
+/* Modularity Q_w (Section 2.4) of level `level`'s partition composed onto the
+ * input graph (level = -1: the final partition), computed on the device as
+ * the exact integer sum_C (m_w W_in(C) - Sigma_C^2) divided once, in FP64, by
+ * m_w^2.  Q = 0 when m_w = 0.  Synchronous. */
+slm_status slm_modularity(const slm_graph *g, int32_t level, double *q);
+
+/* Statistics of one recorded level; level = -1 gives the last, unrecorded
+ * level (the one on which the method found no more structure). */
+slm_status slm_get_stats(const slm_graph *g, int32_t level, slm_level_stats *st);
+
+/* Modularity of an arbitrary labelling (values in [0, n)) of the graph's input
+ * nodes; labels in `where` memory.  Synchronous. */
+slm_status slm_modularity_of(const slm_graph *g, const int32_t *labels, int where, double *q);
+
+void slm_destroy_graph(slm_graph *g);
+const char *slm_status_string(slm_status s);
+/* Message of the last error on this handle (or of the last failed create when g is NULL). */
+const char *slm_last_error(const slm_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLM_H */

@@ -1,0 +1,117 @@
+/*
+ * slm_steps.h -- one C entry point per step of the Synchronised Louvain
+ * Method, on caller-owned DEVICE buffers.  They run the same kernels that
+ * slm_run chains together and exist so that every step can be checked alone
+ * against a reference on identical inputs.
+ *
+ * Shared conventions:
+ *   - every pointer argument is device memory of the current device unless
+ *     its name ends in `_host`;
+ *   - graphs are symmetric CSR (row_ptr int32[n+1], col int32[nnz] sorted
+ *     unique per row, w int32[nnz] > 0); s is int32[n] (s_i = sum_j W_ij) and
+ *     m_w = sum_i s_i < 2^31;
+ *   - "names" of communities are node ids: a community is named by the
+ *     smallest node on its assignment cycle (root[v] in [0, n));
+ *   - scratch memory is allocated with cudaMallocAsync on `stream` and freed
+ *     before return; every function synchronises `stream` before returning;
+ *   - errors: SLM_ERR_INVALID_ARGUMENT for negative sizes or NULL pointers
+ *     with a non-zero size, SLM_ERR_OUT_OF_MEMORY, SLM_ERR_CUDA.
+ */
+#ifndef SLM_STEPS_H
+#define SLM_STEPS_H
+
+#include "slm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Strengths s_i = sum_j W_ij and m_w = sum_i s_i (Section 2.4, m_w). */
+slm_status slm_step_strengths(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                              const int32_t *w, int32_t *s, int64_t *m_w_host, void *stream);
+
+/* ASSIGN (Section 3.1, Algorithm ASSIGN): a[i] = argmax over neighbours j != i
+ * of m_w W_ij - s_i s_j, smallest j on ties, a[i] = i when no value is > 0. */
+slm_status slm_step_assign(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                           const int32_t *w, const int32_t *s, int64_t m_w, int32_t *a,
+                           void *stream);
+
+/* COMPONENTS (Section 3.2): root[v] = smallest node on the cycle that v's
+ * forward path in the assignment graph a reaches.  a[v] in [0, n). */
+slm_status slm_step_components(int32_t n, const int32_t *a, int32_t *root, void *stream);
+
+/* The per-node scan of MAXIMAL (Section 3.4, best community c_i^*):
+ * Sigma_C = sum of s over community C; for every node i,
+ * score(C) = m_w k_{i,C} - s_i (Sigma_C - [C = root_i] s_i) with k_{i,C} the
+ * weight from i to C (self-loop excluded); best[i] = the neighbouring
+ * community C != root_i of largest score (smallest name on ties) when
+ * gain[i] = score(best) - score(root_i) > 0, else best[i] = root[i] and
+ * gain[i] = 0; g[i] = score(root_i) is the local gain of Algorithm POSITIVE. */
+slm_status slm_step_scan(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                         const int32_t *s, int64_t m_w, const int32_t *root, int32_t *best,
+                         int64_t *gain, int64_t *g, void *stream);
+
+/* Branch gain of Algorithm MAXIMAL for every node with gain[i] > 0 (bg[i] = 0
+ * elsewhere): moving the tail S of i (every node whose forward path reaches i)
+ * from A = root_i to B = best_i changes the modularity numerator by twice
+ *   m_w (W(S,B) - W(S, A\S)) - Sigma_S (Sigma_B - Sigma_A + Sigma_S).
+ * root must be the components of a; best and gain as produced by the scan. */
+slm_status slm_step_branch_gain(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                const int32_t *w, const int32_t *s, int64_t m_w,
+                                const int32_t *a, const int32_t *root, const int32_t *best,
+                                const int64_t *gain, int64_t *bg, void *stream);
+
+/* One synchronous MAXIMAL correction (Algorithm MAXIMAL, Section 4.2): scan,
+ * branch gains, the random acceptance draw of level `level`, sweep `sweep`,
+ * the target node a'(i) = argmax over neighbours j of i in best_i of
+ * m_w W_ij - s_i s_j (smallest j on ties), and one simultaneous write of a'.
+ * a is updated in place; root (the components of a on entry) is left as is.
+ * counts_host[0..2] = candidates (gain > 0), candidates with a positive
+ * branch gain, accepted moves. */
+slm_status slm_step_maximal(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                            const int32_t *w, const int32_t *s, int64_t m_w, int32_t *a,
+                            const int32_t *root, uint64_t seed, uint64_t accept_p32,
+                            int32_t level, int32_t sweep, int64_t *counts_host, void *stream);
+
+/* POSITIVE (Section 3.3, Algorithm POSITIVE): bisect every community that
+ * holds a node with a negative local gain, optimally over the branch cuts
+ * and the two-node cycle cuts of its assignment graph (largest value of
+ * Sigma_S Sigma_R - m_w W(S,R); ties: branch before cycle, then smaller u,
+ * then smaller v), and repeat on the parts until no node has a negative local
+ * gain.  a is updated in place; root receives the final components. */
+slm_status slm_step_positive(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                             const int32_t *w, const int32_t *s, int64_t m_w, int32_t *a,
+                             int32_t *root, int64_t *splits_host, void *stream);
+
+/* Compaction: id[v] = rank of root[v] among the names in use (root[x] == x),
+ * *K_host = their number. */
+slm_status slm_step_compact(int32_t n, const int32_t *root, int32_t *id, int32_t *K_host,
+                            void *stream);
+
+/* AGGREGATE (Section 3.5): W'_AB = sum of W_uv over id[u] = A, id[v] = B,
+ * diagonal included, as a CSR with sorted unique columns.  row_ptr_out holds
+ * K+1 entries, col_out and w_out at least nnz; *nnz_out_host receives the
+ * entries written.  Keys (id[u], id[v]) are sorted by a radix sort and
+ * reduced by segment. */
+slm_status slm_step_aggregate(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                              const int32_t *w, const int32_t *id, int32_t K,
+                              int32_t *row_ptr_out, int32_t *col_out, int32_t *w_out,
+                              int32_t *nnz_out_host, void *stream);
+
+/* Modularity Q_w (Section 2.4) of labels (values in [0, n)): the exact
+ * numerator sum_C (m_w W_in(C) - Sigma_C^2) into *num_host and its FP64
+ * quotient by m_w^2 into *q_host (0 when m_w = 0). */
+slm_status slm_step_modularity(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                               const int32_t *w, const int32_t *labels, double *q_host,
+                               int64_t *num_host, void *stream);
+
+/* Diagnostic record of the last slm_run: one row of six int64 per scan
+ * (level, sweep, candidates, candidates with a positive branch gain,
+ * accepted moves, POSITIVE splits after the write).  Copies at most `cap`
+ * rows into `rows` (host memory) and sets *len to the number of rows. */
+slm_status slm_get_trace(const slm_graph *g, int64_t *rows, int64_t cap, int64_t *len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLM_STEPS_H */

@@ -1,0 +1,375 @@
+"""GB300 (sm_103a) implementation of the Synchronised Louvain Method.
+
+Python binding of the C ABI in ``include/slm.h`` and ``include/slm_steps.h``:
+argument marshalling only.  Every step of the method runs in the CUDA kernels
+of ``libslm.so``; there is no CPU fallback, and importing any entry point
+raises when the library has not been built (see ``build()``).
+
+PyTorch provides device memory and streams for the step functions; the
+graph-level API accepts numpy arrays (host memory) or CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from .build_lib import LIB, build  # noqa: F401
+
+__all__ = ["Graph", "Options", "LevelStats", "SlmError", "build", "load", "step_strengths",
+           "step_assign", "step_components", "step_scan", "step_branch_gain", "step_maximal",
+           "step_positive", "step_compact", "step_aggregate", "step_modularity",
+           "FLAG_NO_POSITIVE", "FLAG_STRICT", "P_HALF", "P_ALWAYS"]
+
+SLM_HOST = 0
+SLM_DEVICE = 1
+FLAG_NO_POSITIVE = 1
+FLAG_STRICT = 2
+P_HALF = 1 << 31
+P_ALWAYS = 1 << 32
+
+STATUS = {0: "SLM_OK", 1: "SLM_ERR_INVALID_ARGUMENT", 2: "SLM_ERR_NOT_SYMMETRIC",
+          3: "SLM_ERR_OVERFLOW", 4: "SLM_ERR_OUT_OF_MEMORY", 5: "SLM_ERR_CUDA",
+          6: "SLM_ERR_NOT_RUN", 7: "SLM_ERR_NOT_CONVERGED", 8: "SLM_ERR_TIMEOUT",
+          9: "SLM_ERR_BUDGET"}
+
+# every exported entry point, as declared in include/*.h
+EXPORTS = ["slm_default_options", "slm_create_graph", "slm_run", "slm_num_levels",
+           "slm_get_partition", "slm_modularity", "slm_get_stats", "slm_modularity_of",
+           "slm_destroy_graph", "slm_status_string", "slm_last_error", "slm_step_strengths",
+           "slm_step_assign", "slm_step_components", "slm_step_scan", "slm_step_branch_gain",
+           "slm_step_maximal", "slm_step_positive", "slm_step_compact", "slm_step_aggregate",
+           "slm_step_modularity", "slm_get_trace"]
+
+
+class SlmError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{self.name}: {msg}" if msg else self.name)
+
+
+class Options(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("accept_p32", C.c_uint64), ("max_sweeps", C.c_int32),
+                ("max_levels", C.c_int32), ("flags", C.c_uint32)]
+
+
+class LevelStats(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_communities", C.c_int32), ("sweeps", C.c_int32),
+                ("status", C.c_int32), ("moves", C.c_int64), ("splits", C.c_int64),
+                ("candidates", C.c_int64), ("edges_scanned", C.c_int64), ("nnz", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Load libslm.so from the package's build folder; raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build the CUDA library first "
+                               "(paper_1702_04645_gb300.build())")
+        lib = C.CDLL(LIB)
+        vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+        sig = {
+            "slm_default_options": (None, [C.POINTER(Options)]),
+            "slm_create_graph": (C.c_int, [i32, vp, vp, vp, C.c_int, vp, C.POINTER(vp)]),
+            "slm_run": (C.c_int, [vp, C.POINTER(Options), vp]),
+            "slm_num_levels": (C.c_int, [vp, C.POINTER(i32)]),
+            "slm_get_partition": (C.c_int, [vp, i32, vp, C.c_int, C.POINTER(i32)]),
+            "slm_modularity": (C.c_int, [vp, i32, C.POINTER(C.c_double)]),
+            "slm_get_stats": (C.c_int, [vp, i32, C.POINTER(LevelStats)]),
+            "slm_modularity_of": (C.c_int, [vp, vp, C.c_int, C.POINTER(C.c_double)]),
+            "slm_destroy_graph": (None, [vp]),
+            "slm_status_string": (C.c_char_p, [C.c_int]),
+            "slm_last_error": (C.c_char_p, [vp]),
+            "slm_get_trace": (C.c_int, [vp, vp, i64, C.POINTER(i64)]),
+            "slm_step_strengths": (C.c_int, [i32, vp, vp, vp, vp, C.POINTER(i64), vp]),
+            "slm_step_assign": (C.c_int, [i32, vp, vp, vp, vp, i64, vp, vp]),
+            "slm_step_components": (C.c_int, [i32, vp, vp, vp]),
+            "slm_step_scan": (C.c_int, [i32, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]),
+            "slm_step_branch_gain": (C.c_int, [i32, vp, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp]),
+            "slm_step_maximal": (C.c_int, [i32, vp, vp, vp, vp, i64, vp, vp, u64, u64, i32, i32,
+                                           vp, vp]),
+            "slm_step_positive": (C.c_int, [i32, vp, vp, vp, vp, i64, vp, vp, vp, vp]),
+            "slm_step_compact": (C.c_int, [i32, vp, vp, C.POINTER(i32), vp]),
+            "slm_step_aggregate": (C.c_int, [i32, vp, vp, vp, vp, i32, vp, vp, vp,
+                                             C.POINTER(i32), vp]),
+            "slm_step_modularity": (C.c_int, [i32, vp, vp, vp, vp, C.POINTER(C.c_double),
+                                              C.POINTER(i64), vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(st: int, handle=None):
+    if st != 0:
+        lib = load()
+        msg = lib.slm_last_error(handle)
+        raise SlmError(st, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# helpers for torch tensors (device memory and streams come from PyTorch)
+# ---------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _dev_i32(x):
+    """int32 CUDA tensor of x; an empty input becomes one zero so that its
+    pointer is valid (sizes are passed separately and bound every read)."""
+    torch = _torch()
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.int32))
+    x = x.to(device="cuda", dtype=torch.int32).contiguous()
+    if x.numel() == 0:
+        x = torch.zeros(1, dtype=torch.int32, device="cuda")
+    return x
+
+
+def _empty(n, dtype):
+    torch = _torch()
+    return torch.empty(max(int(n), 1), dtype=dtype, device="cuda")
+
+
+# ---------------------------------------------------------------------------
+# Graph-level API
+# ---------------------------------------------------------------------------
+class Graph:
+    """A graph resident on the device and the results of its last run."""
+
+    def __init__(self, row_ptr, col, w=None, stream=None):
+        lib = load()
+        self._h = C.c_void_p()
+        is_np = isinstance(row_ptr, np.ndarray)
+        if is_np:
+            self._keep = [np.ascontiguousarray(row_ptr, dtype=np.int32),
+                          np.ascontiguousarray(col, dtype=np.int32),
+                          None if w is None else np.ascontiguousarray(w, dtype=np.int32)]
+            ptrs = [C.c_void_p(a.ctypes.data) if a is not None and a.size else C.c_void_p(0)
+                    for a in self._keep]
+            where = SLM_HOST
+            st = C.c_void_p(int(stream)) if stream is not None else C.c_void_p(0)
+        else:
+            torch = _torch()
+            self._keep = [t.contiguous() if t is not None else None for t in (row_ptr, col, w)]
+            where = SLM_DEVICE if self._keep[0].is_cuda else SLM_HOST
+            ptrs = [_ptr(t) if t is not None else C.c_void_p(0) for t in self._keep]
+            st = _stream(stream) if where == SLM_DEVICE else C.c_void_p(0)
+            del torch
+        self.n = int(len(self._keep[0]) - 1)
+        _check(lib.slm_create_graph(self.n, ptrs[0], ptrs[1], ptrs[2], where, st,
+                                    C.byref(self._h)))
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().slm_destroy_graph(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, seed: int = 1, accept_p32: int = P_HALF, max_sweeps: int = 1000,
+            max_levels: int = 64, flags: int = 0, stream=None):
+        o = Options(seed, accept_p32, max_sweeps, max_levels, flags)
+        st = C.c_void_p(int(stream)) if stream is not None else C.c_void_p(0)
+        _check(load().slm_run(self._h, C.byref(o), st), self._h)
+        return self
+
+    def num_levels(self) -> int:
+        v = C.c_int32()
+        _check(load().slm_num_levels(self._h, C.byref(v)), self._h)
+        return v.value
+
+    def partition(self, level: int = -1):
+        """(labels as int32 numpy array, number of communities)."""
+        lib = load()
+        if level == -1:
+            n = self.n
+        else:
+            n = self.stats(level).n
+        out = np.zeros(max(n, 1), dtype=np.int32)
+        K = C.c_int32()
+        _check(lib.slm_get_partition(self._h, level, C.c_void_p(out.ctypes.data), SLM_HOST,
+                                     C.byref(K)), self._h)
+        return out[:n], K.value
+
+    def partition_device(self, level: int = -1):
+        """(labels as an int32 CUDA tensor, number of communities)."""
+        n = self.n if level == -1 else self.stats(level).n
+        out = _empty(max(n, 1), _torch().int32)
+        K = C.c_int32()
+        _check(load().slm_get_partition(self._h, level, _ptr(out), SLM_DEVICE, C.byref(K)),
+               self._h)
+        return out[:n], K.value
+
+    def modularity(self, level: int = -1) -> float:
+        q = C.c_double()
+        _check(load().slm_modularity(self._h, level, C.byref(q)), self._h)
+        return q.value
+
+    def modularity_of(self, labels) -> float:
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        q = C.c_double()
+        _check(load().slm_modularity_of(self._h, C.c_void_p(lab.ctypes.data), SLM_HOST,
+                                        C.byref(q)), self._h)
+        return q.value
+
+    def stats(self, level: int) -> LevelStats:
+        s = LevelStats()
+        _check(load().slm_get_stats(self._h, level, C.byref(s)), self._h)
+        return s
+
+    def trace(self) -> np.ndarray:
+        lib = load()
+        ln = C.c_int64()
+        _check(lib.slm_get_trace(self._h, C.c_void_p(0), 0, C.byref(ln)), self._h)
+        out = np.zeros((max(ln.value, 1), 6), dtype=np.int64)
+        _check(lib.slm_get_trace(self._h, C.c_void_p(out.ctypes.data), ln.value, C.byref(ln)),
+               self._h)
+        return out[: ln.value]
+
+
+# ---------------------------------------------------------------------------
+# Step API on CUDA tensors (one call per step of the method)
+# ---------------------------------------------------------------------------
+def step_strengths(rp, col, w, stream=None):
+    torch = _torch()
+    rp, col, w = _dev_i32(rp), _dev_i32(col), _dev_i32(w)
+    n = rp.numel() - 1
+    s = _empty(n, torch.int32)
+    m = C.c_int64()
+    _check(load().slm_step_strengths(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(s), C.byref(m),
+                                     _stream(stream)))
+    return s, m.value
+
+
+def step_assign(rp, col, w, s, m, stream=None):
+    torch = _torch()
+    rp, col, w, s = map(_dev_i32, (rp, col, w, s))
+    n = rp.numel() - 1
+    a = _empty(n, torch.int32)
+    _check(load().slm_step_assign(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(s), int(m), _ptr(a),
+                                  _stream(stream)))
+    return a
+
+
+def step_components(a, stream=None):
+    torch = _torch()
+    a = _dev_i32(a)
+    root = _empty(a.numel(), torch.int32)
+    _check(load().slm_step_components(a.numel(), _ptr(a), _ptr(root), _stream(stream)))
+    return root
+
+
+def step_scan(rp, col, w, s, m, root, stream=None):
+    torch = _torch()
+    rp, col, w, s, root = map(_dev_i32, (rp, col, w, s, root))
+    n = rp.numel() - 1
+    best = _empty(n, torch.int32)
+    gain = _empty(n, torch.int64)
+    g = _empty(n, torch.int64)
+    _check(load().slm_step_scan(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(s), int(m), _ptr(root),
+                                _ptr(best), _ptr(gain), _ptr(g), _stream(stream)))
+    return best, gain, g
+
+
+def step_branch_gain(rp, col, w, s, m, a, root, best, gain, stream=None):
+    torch = _torch()
+    rp, col, w, s, a, root, best = map(_dev_i32, (rp, col, w, s, a, root, best))
+    gain = gain.to(device="cuda", dtype=torch.int64).contiguous()
+    if gain.numel() == 0:
+        gain = torch.zeros(1, dtype=torch.int64, device="cuda")
+    n = rp.numel() - 1
+    bg = _empty(n, torch.int64)
+    _check(load().slm_step_branch_gain(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(s), int(m), _ptr(a),
+                                       _ptr(root), _ptr(best), _ptr(gain), _ptr(bg),
+                                       _stream(stream)))
+    return bg
+
+
+def step_maximal(rp, col, w, s, m, a, root, seed, accept_p32, level, sweep, stream=None):
+    rp, col, w, s, root = map(_dev_i32, (rp, col, w, s, root))
+    a = _dev_i32(a).clone()
+    n = rp.numel() - 1
+    counts = np.zeros(3, dtype=np.int64)
+    _check(load().slm_step_maximal(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(s), int(m), _ptr(a),
+                                   _ptr(root), int(seed), int(accept_p32), int(level), int(sweep),
+                                   C.c_void_p(counts.ctypes.data), _stream(stream)))
+    return a, counts
+
+
+def step_positive(rp, col, w, s, m, a, stream=None):
+    torch = _torch()
+    rp, col, w, s = map(_dev_i32, (rp, col, w, s))
+    a = _dev_i32(a).clone()
+    n = rp.numel() - 1
+    root = _empty(n, torch.int32)
+    splits = np.zeros(1, dtype=np.int64)
+    _check(load().slm_step_positive(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(s), int(m), _ptr(a),
+                                    _ptr(root), C.c_void_p(splits.ctypes.data), _stream(stream)))
+    return a, root, int(splits[0])
+
+
+def step_compact(root, stream=None):
+    torch = _torch()
+    root = _dev_i32(root)
+    idv = _empty(root.numel(), torch.int32)
+    K = C.c_int32()
+    _check(load().slm_step_compact(root.numel(), _ptr(root), _ptr(idv), C.byref(K),
+                                   _stream(stream)))
+    return idv, K.value
+
+
+def step_aggregate(rp, col, w, idv, K, stream=None):
+    torch = _torch()
+    rp, col, w, idv = map(_dev_i32, (rp, col, w, idv))
+    n = rp.numel() - 1
+    rp2 = _empty(K + 1, torch.int32)
+    col2 = _empty(max(col.numel(), 1), torch.int32)
+    w2 = _empty(max(col.numel(), 1), torch.int32)
+    nnz = C.c_int32()
+    _check(load().slm_step_aggregate(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(idv), int(K),
+                                     _ptr(rp2), _ptr(col2), _ptr(w2), C.byref(nnz),
+                                     _stream(stream)))
+    return rp2, col2[: nnz.value], w2[: nnz.value]
+
+
+def step_modularity(rp, col, w, labels, stream=None):
+    rp, col, w, labels = map(_dev_i32, (rp, col, w, labels))
+    n = rp.numel() - 1
+    q = C.c_double()
+    num = C.c_int64()
+    _check(load().slm_step_modularity(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(labels), C.byref(q),
+                                      C.byref(num), _stream(stream)))
+    return q.value, num.value

@@ -1,0 +1,403 @@
+// k_basic.cu -- buffers, device-wide prefix sums and the per-graph kernels:
+// validation, strengths (Section 2.4: s_i and m_w), community totals Sigma_C,
+// compaction of community names, partition composition (Algorithm 1,
+// C = C_t C) and the exact modularity numerator (Section 2.4, Q_w).
+#include <cstdio>
+#include <cstring>
+
+#include "slm_internal.cuh"
+
+namespace slm {
+
+void fail(slm_status st, const std::string &msg) { throw Error{st, msg}; }
+
+void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
+    if (e == cudaSuccess) return;
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s failed at %s:%d: %s", what, file, line, cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        fail(SLM_ERR_OUT_OF_MEMORY, buf);
+    }
+    fail(SLM_ERR_CUDA, buf);
+}
+
+void DevBuf::alloc(size_t bytes, cudaStream_t s) {
+    release();
+    s_ = s;
+    if (bytes == 0) bytes = 16;
+    SLM_CUDA(cudaMallocAsync(&p_, bytes, s));
+    bytes_ = bytes;
+}
+
+void DevBuf::release() {
+    if (p_) cudaFreeAsync(p_, s_);
+    p_ = nullptr;
+    bytes_ = 0;
+}
+
+HostCounters::HostCounters() { SLM_CUDA(cudaMallocHost(&h, 64 * sizeof(long long))); }
+HostCounters::~HostCounters() {
+    if (h) cudaFreeHost(h);
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive prefix sums: reduce tiles, scan the tile sums (recursively), then
+// scan each tile with its offset.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <class T> __device__ T block_exclusive_scan(T v, T *total) {
+    __shared__ T warp_tot[kScanThreads / kWarp];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        T t = lane < kScanThreads / kWarp ? warp_tot[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kScanThreads / kWarp) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    T warp_off = wid > 0 ? warp_tot[wid - 1] : T(0);
+    if (total) *total = warp_tot[kScanThreads / kWarp - 1];
+    __syncthreads();
+    return warp_off + x - v;
+}
+
+template <class T> __global__ void k_scan_reduce(const T *in, long long n, T *tile_sums) {
+    long long base = (long long)blockIdx.x * kScanTile;
+    T acc = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        long long i = base + (long long)k * kScanThreads + threadIdx.x;
+        if (i < n) acc += in[i];
+    }
+    T tot;
+    block_exclusive_scan<T>(acc, &tot);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+template <class T>
+__global__ void k_scan_tile(const T *in, T *out, long long n, const T *tile_off) {
+    __shared__ T buf[kScanTile];
+    long long base = (long long)blockIdx.x * kScanTile;
+    for (int k = 0; k < kScanItems; k++) {
+        long long i = base + (long long)k * kScanThreads + threadIdx.x;
+        buf[k * kScanThreads + threadIdx.x] = i < n ? in[i] : T(0);
+    }
+    __syncthreads();
+    T loc[kScanItems];
+    T acc = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        loc[k] = buf[threadIdx.x * kScanItems + k];
+        acc += loc[k];
+    }
+    T tot;
+    T pre = block_exclusive_scan<T>(acc, &tot) + (tile_off ? tile_off[blockIdx.x] : T(0));
+    for (int k = 0; k < kScanItems; k++) {
+        buf[threadIdx.x * kScanItems + k] = pre;
+        pre += loc[k];
+    }
+    __syncthreads();
+    for (int k = 0; k < kScanItems; k++) {
+        long long i = base + (long long)k * kScanThreads + threadIdx.x;
+        if (i < n) out[i] = buf[k * kScanThreads + threadIdx.x];
+    }
+}
+
+template <class T>
+__global__ void k_scan_total(const T *last_in, const T *out, long long n, T *total) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *total = out[n - 1] + *last_in;
+}
+
+template <class T>
+static void scan_impl(const T *in, T *out, long long n, T *total_dev, cudaStream_t s) {
+    if (n <= 0) {
+        if (total_dev) SLM_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(T), s));
+        return;
+    }
+    long long tiles = (n + kScanTile - 1) / kScanTile;
+    // the last input element is needed for the total; keep it when in == out
+    DevBuf last;
+    if (total_dev && in == out) {
+        last.alloc(sizeof(T), s);
+        SLM_CUDA(cudaMemcpyAsync(last.get(), in + n - 1, sizeof(T), cudaMemcpyDeviceToDevice, s));
+    }
+    if (tiles == 1) {
+        k_scan_tile<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+        SLM_LAUNCH_CHECK();
+    } else {
+        DevBuf sums(tiles * sizeof(T), s);
+        k_scan_reduce<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<T>());
+        SLM_LAUNCH_CHECK();
+        scan_impl<T>(sums.as<T>(), sums.as<T>(), tiles, nullptr, s);
+        k_scan_tile<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums.as<T>());
+        SLM_LAUNCH_CHECK();
+    }
+    if (total_dev) {
+        const T *src_last = (in == out) ? last.as<T>() : in + n - 1;
+        k_scan_total<T><<<1, 32, 0, s>>>(src_last, out, n, total_dev);
+        SLM_LAUNCH_CHECK();
+    }
+}
+
+void exclusive_scan_i32(const int32_t *in, int32_t *out, long long n, int32_t *total_dev,
+                        cudaStream_t s) {
+    scan_impl<int32_t>(in, out, n, total_dev, s);
+}
+void exclusive_scan_i64(const long long *in, long long *out, long long n, long long *total_dev,
+                        cudaStream_t s) {
+    scan_impl<long long>(in, out, n, total_dev, s);
+}
+
+// ---------------------------------------------------------------------------
+// CSR validation: one warp per row.
+// ---------------------------------------------------------------------------
+__global__ void k_validate(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                           int *bad) {
+    int lane = threadIdx.x & 31;
+    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = warp; i < n; i += nwarps) {
+        int b = 0;
+        int lo = rp[i], hi = rp[i + 1];
+        if (lane == 0 && (hi < lo || (i == 0 && lo != 0))) b |= 8;
+        if (hi >= lo) {
+            for (int p = lo + lane; p < hi; p += 32) {
+                int j = col[p];
+                if (j < 0 || j >= n) { b |= 1; continue; }
+                if (p > lo && col[p - 1] >= j) b |= 1;
+                int wp = w ? w[p] : 1;
+                if (wp <= 0) b |= 2;
+                // W_ji must exist with the same weight
+                int a = rp[j], c = rp[j + 1] - 1;
+                int found = -1;
+                while (a <= c) {
+                    int mid = (a + c) >> 1;
+                    int v = col[mid];
+                    if (v == (int)i) { found = mid; break; }
+                    if (v < (int)i) a = mid + 1; else c = mid - 1;
+                }
+                if (found < 0 || (w ? w[found] : 1) != wp) b |= 4;
+            }
+        }
+        if (b) atomicOr(bad, b);
+    }
+}
+
+int validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                 cudaStream_t s) {
+    DevBuf bad(sizeof(int), s);
+    SLM_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+    if (n > 0) {
+        k_validate<<<grid_for((long long)n * 32, 256), 256, 0, s>>>(n, rp, col, w, bad.as<int>());
+        SLM_LAUNCH_CHECK();
+    }
+    int h = 0;
+    SLM_CUDA(cudaMemcpyAsync(&h, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    SLM_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+// Number of entries of x outside [0, n).
+__global__ void k_out_of_range(long long cnt, const int32_t *x, int32_t n, int *bad) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (long long)gridDim.x * blockDim.x)
+        if (x[i] < 0 || x[i] >= n) atomicAdd(bad, 1);
+}
+
+int count_out_of_range(long long cnt, const int32_t *x, int32_t n, cudaStream_t s) {
+    if (cnt <= 0) return 0;
+    DevBuf bad(sizeof(int), s);
+    SLM_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+    k_out_of_range<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, x, n, bad.as<int>());
+    SLM_LAUNCH_CHECK();
+    int h = 0;
+    SLM_CUDA(cudaMemcpyAsync(&h, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    SLM_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+// Strengths: s_i = sum_j W_ij, m_w = sum_i s_i (Section 2.4).
+// ---------------------------------------------------------------------------
+__global__ void k_strengths(int32_t n, const int32_t *rp, const int32_t *w, int32_t *s,
+                            unsigned long long *m) {
+    int lane = threadIdx.x & 31;
+    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long local = 0;
+    for (long long i = warp; i < n; i += nwarps) {
+        long long acc = 0;
+        for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) acc += w[p];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            s[i] = (int32_t)(acc > 0x7fffffffLL ? 0x7fffffff : acc);
+            local += (unsigned long long)acc;
+        }
+    }
+    if (lane == 0 && local) atomicAdd(m, local);
+}
+
+long long strengths(int32_t n, const int32_t *rp, const int32_t *w, int32_t *s_out,
+                    cudaStream_t s) {
+    DevBuf m(sizeof(unsigned long long), s);
+    SLM_CUDA(cudaMemsetAsync(m.get(), 0, sizeof(unsigned long long), s));
+    if (n > 0) {
+        k_strengths<<<grid_for((long long)n * 32, 256), 256, 0, s>>>(n, rp, w, s_out,
+                                                                     m.as<unsigned long long>());
+        SLM_LAUNCH_CHECK();
+    }
+    unsigned long long h = 0;
+    SLM_CUDA(cudaMemcpyAsync(&h, m.get(), sizeof h, cudaMemcpyDeviceToHost, s));
+    SLM_CUDA(cudaStreamSynchronize(s));
+    return (long long)h;
+}
+
+// ---------------------------------------------------------------------------
+// Sigma_C = sum of s over the community named C.
+// ---------------------------------------------------------------------------
+__global__ void k_sigma(int32_t n, const int32_t *root, const int32_t *s, int32_t *sigma) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x)
+        if (s[v]) atomicAdd(&sigma[root[v]], s[v]);
+}
+
+void community_sigma(int32_t n, const int32_t *root, const int32_t *s, int32_t *sigma,
+                     cudaStream_t st) {
+    if (n <= 0) return;
+    SLM_CUDA(cudaMemsetAsync(sigma, 0, sizeof(int32_t) * n, st));
+    k_sigma<<<grid_for(n, 256), 256, 0, st>>>(n, root, s, sigma);
+    SLM_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// Compaction: names in use (root[x] == x) ranked in increasing order.
+// ---------------------------------------------------------------------------
+__global__ void k_root_flags(int32_t n, const int32_t *root, int32_t *f) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x)
+        f[v] = root[v] == v ? 1 : 0;
+}
+__global__ void k_gather_rank(int32_t n, const int32_t *root, const int32_t *rank, int32_t *id) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x)
+        id[v] = rank[root[v]];
+}
+
+int32_t compact_labels(int32_t n, const int32_t *root, int32_t *id, int32_t *scratch_n,
+                       cudaStream_t s) {
+    if (n <= 0) return 0;
+    DevBuf tot(sizeof(int32_t), s);
+    k_root_flags<<<grid_for(n, 256), 256, 0, s>>>(n, root, scratch_n);
+    SLM_LAUNCH_CHECK();
+    exclusive_scan_i32(scratch_n, scratch_n, n, tot.as<int32_t>(), s);
+    k_gather_rank<<<grid_for(n, 256), 256, 0, s>>>(n, root, scratch_n, id);
+    SLM_LAUNCH_CHECK();
+    int32_t K = 0;
+    SLM_CUDA(cudaMemcpyAsync(&K, tot.get(), sizeof K, cudaMemcpyDeviceToHost, s));
+    SLM_CUDA(cudaStreamSynchronize(s));
+    return K;
+}
+
+__global__ void k_compose(int32_t n0, int32_t *comp, const int32_t *id) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n0;
+         v += (long long)gridDim.x * blockDim.x)
+        comp[v] = id[comp[v]];
+}
+
+void compose_labels(int32_t n0, int32_t *comp, const int32_t *id, cudaStream_t s) {
+    if (n0 <= 0) return;
+    k_compose<<<grid_for(n0, 256), 256, 0, s>>>(n0, comp, id);
+    SLM_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// Modularity numerator sum_C (m_w W_in(C) - Sigma_C^2), exact in 64 bits
+// (both sums are below m_w^2 < 2^62).
+// ---------------------------------------------------------------------------
+__global__ void k_mod_accumulate(int32_t n, const int32_t *rp, const int32_t *col,
+                                 const int32_t *w, const int32_t *labels,
+                                 unsigned long long *win, unsigned long long *sig) {
+    int lane = threadIdx.x & 31;
+    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = warp; u < n; u += nwarps) {
+        int lu = labels[u];
+        long long in = 0, su = 0;
+        for (int p = rp[u] + lane; p < rp[u + 1]; p += 32) {
+            su += w[p];
+            if (labels[col[p]] == lu) in += w[p];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            in += __shfl_xor_sync(0xffffffffu, in, o);
+            su += __shfl_xor_sync(0xffffffffu, su, o);
+        }
+        if (lane == 0) {
+            if (in) atomicAdd(&win[lu], (unsigned long long)in);
+            if (su) atomicAdd(&sig[lu], (unsigned long long)su);
+        }
+    }
+}
+
+__global__ void k_mod_reduce(int32_t n, const unsigned long long *win,
+                             const unsigned long long *sig, unsigned long long m,
+                             unsigned long long *out2) {
+    unsigned long long a = 0, b = 0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        a += m * win[c];
+        b += sig[c] * sig[c];
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicAdd(&out2[0], a);
+        if (b) atomicAdd(&out2[1], b);
+    }
+}
+
+long long modularity_num(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                         const int32_t *labels, long long m_w, cudaStream_t s) {
+    if (n <= 0 || m_w == 0) return 0;
+    DevBuf win(sizeof(unsigned long long) * n, s), sig(sizeof(unsigned long long) * n, s),
+        out(2 * sizeof(unsigned long long), s);
+    SLM_CUDA(cudaMemsetAsync(win.get(), 0, win.bytes(), s));
+    SLM_CUDA(cudaMemsetAsync(sig.get(), 0, sig.bytes(), s));
+    SLM_CUDA(cudaMemsetAsync(out.get(), 0, out.bytes(), s));
+    k_mod_accumulate<<<grid_for((long long)n * 32, 256), 256, 0, s>>>(
+        n, rp, col, w, labels, win.as<unsigned long long>(), sig.as<unsigned long long>());
+    SLM_LAUNCH_CHECK();
+    k_mod_reduce<<<grid_for(n, 256, 1024), 256, 0, s>>>(n, win.as<unsigned long long>(),
+                                                         sig.as<unsigned long long>(),
+                                                         (unsigned long long)m_w,
+                                                         out.as<unsigned long long>());
+    SLM_LAUNCH_CHECK();
+    unsigned long long h[2];
+    SLM_CUDA(cudaMemcpyAsync(h, out.get(), sizeof h, cudaMemcpyDeviceToHost, s));
+    SLM_CUDA(cudaStreamSynchronize(s));
+    return (long long)h[0] - (long long)h[1];
+}
+
+double modularity_from_num(long long num, long long m_w) {
+    if (m_w == 0) return 0.0;
+    return (double)num / ((double)m_w * (double)m_w);
+}
+
+}  // namespace slm

@@ -1,0 +1,648 @@
+// k_scan.cu -- neighbourhood scans of the Synchronised Louvain Method.
+//
+//  * scan_nodes: the per-node half of MAXIMAL (Section 3.4, Algorithm
+//    MAXIMAL's c_i^* = argmax_c Delta H(c_i -> i -> c)): accumulate the weight
+//    k_{i,C} from node i to every neighbouring community C and pick the best
+//    by the exact score m_w k_{i,C} - s_i Sigma_C (Section 2.4).
+//  * assign_nodes: ASSIGN (Section 3.1): best neighbour by m_w W_ij - s_i s_j.
+//  * target_nodes: the new assignment a(i) = argmax_{j in c_i^*} of the same
+//    pair score (Algorithm MAXIMAL).
+//  * own_weight_nodes: k_{i,c_i} and the local gain g(i) of POSITIVE
+//    (Section 3.3, Algorithm POSITIVE).
+//
+// Degree buckets pick the shape: groups of 4/8/16/32 lanes with one edge per
+// lane (communities grouped by shuffles), one warp per node with a shared-
+// memory open-addressing table (33..256 edges), one block per node with a
+// shared-memory table (257..4096 edges) or a global-memory table (hubs).
+// Every reduction compares (score desc, name asc), so the result does not
+// depend on the order in which lanes or blocks finish.
+#include <climits>
+
+#include "slm_internal.cuh"
+
+namespace slm {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kBlockSmemMaxDeg = 4096;            // block bucket: smem table up to here
+constexpr int kBlockSmemCap = 2 * kBlockSmemMaxDeg; // slots (int key + int value)
+constexpr int kBlockThreads = 256;
+constexpr int kWarpHashCap = 2 * kWarpHashMaxDeg;
+constexpr int kWarpHashWarps = 8;  // warps per block in the warp-hash kernel
+
+__device__ __forceinline__ int bucket_of(int d) {
+    if (d == 0) return kBucketEmpty;
+    if (d <= 4) return kBucketG4;
+    if (d <= 8) return kBucketG8;
+    if (d <= 16) return kBucketG16;
+    if (d <= 32) return kBucketG32;
+    if (d <= kWarpHashMaxDeg) return kBucketWarpHash;
+    return kBucketBlock;
+}
+
+__device__ __forceinline__ bool better(long long sc, int c, long long bsc, int bc) {
+    return sc > bsc || (sc == bsc && c < bc);
+}
+
+__device__ __forceinline__ unsigned hash_slot(int c, int lg) {
+    return ((unsigned)c * 2654435761u) >> (32 - lg);
+}
+
+__device__ __forceinline__ int ilog2_pow2_at_least(int x) {
+    int lg = 0;
+    while ((1 << lg) < x) lg++;
+    return lg;
+}
+
+// Decision shared by every scan shape.
+__device__ __forceinline__ void scan_emit(int i, int ci, int si, long long m, const int32_t *sigma,
+                                          long long own, long long bsc, int bc, int32_t *best,
+                                          long long *gain, int32_t *kown, unsigned &cand) {
+    long long g = m * own - (long long)si * ((long long)sigma[ci] - si);
+    long long gn = (bc != INT_MAX) ? bsc - g : 0;
+    if (bc != INT_MAX && gn > 0) {
+        best[i] = bc;
+        gain[i] = gn;
+        cand++;
+    } else {
+        best[i] = ci;
+        gain[i] = 0;
+    }
+    kown[i] = (int32_t)own;
+}
+
+__device__ __forceinline__ void count_add(unsigned long long *ctr, unsigned v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, (unsigned long long)v);
+}
+
+// ---------------------------------------------------------------------------
+// Buckets
+// ---------------------------------------------------------------------------
+__global__ void k_bucket_keys(int32_t n, const int32_t *rp, uint32_t *keys, int32_t *vals,
+                              int32_t *counts) {
+    __shared__ int loc[kNumBuckets];
+    if (threadIdx.x < kNumBuckets) loc[threadIdx.x] = 0;
+    __syncthreads();
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        int b = bucket_of(rp[v + 1] - rp[v]);
+        keys[v] = (uint32_t)b;
+        vals[v] = (int32_t)v;
+        atomicAdd(&loc[b], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumBuckets && loc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], loc[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// MAXIMAL scan, group shape: G lanes per node, one edge per lane.
+// ---------------------------------------------------------------------------
+template <int G>
+__global__ void __launch_bounds__(256) k_scan_group(const int32_t *order, int32_t cnt, const int32_t *rp,
+                             const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                             const int32_t *root, const int32_t *sigma, int32_t *best,
+                             long long *gain, int32_t *kown, unsigned long long *ncand) {
+    constexpr int NPW = 32 / G;  // nodes per warp
+    const int lane = threadIdx.x & 31, gl = lane % G, gbase = lane - gl;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned cand = 0;
+    for (long long base = warp * NPW; base < cnt; base += nwarps * NPW) {
+        long long idx = base + lane / G;
+        bool vn = idx < cnt;
+        int i = vn ? order[idx] : 0;
+        int start = vn ? rp[i] : 0;
+        int deg = vn ? rp[i + 1] - start : 0;
+        int ci = vn ? root[i] : -1;
+        int c = -1, wv = 0;
+        if (gl < deg) {
+            int j = col[start + gl];
+            if (j != i) {
+                c = root[j];
+                wv = w[start + gl];
+            }
+        }
+        int sum = 0;
+        bool first = true;
+#pragma unroll
+        for (int k = 0; k < G; k++) {
+            int ck = __shfl_sync(FULL, c, gbase + k);
+            int wk = __shfl_sync(FULL, wv, gbase + k);
+            if (ck == c) {
+                sum += wk;
+                if (k < gl) first = false;
+            }
+        }
+        long long own = (c >= 0 && c == ci && first) ? sum : 0;
+        long long sc = LLONG_MIN;
+        int cc = INT_MAX;
+        int si = vn ? s[i] : 0;
+        if (c >= 0 && c != ci && first) {
+            sc = m * (long long)sum - (long long)si * (long long)sigma[c];
+            cc = c;
+        }
+#pragma unroll
+        for (int o = G / 2; o; o >>= 1) {
+            own += __shfl_xor_sync(FULL, own, o);
+            long long osc = __shfl_xor_sync(FULL, sc, o);
+            int occ = __shfl_xor_sync(FULL, cc, o);
+            if (better(osc, occ, sc, cc)) { sc = osc; cc = occ; }
+        }
+        if (gl == 0 && vn) scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
+    }
+    count_add(ncand, cand);
+}
+
+// ---------------------------------------------------------------------------
+// MAXIMAL scan, warp shape: one node per warp, shared-memory table.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWarpHashWarps * 32) k_scan_warphash(const int32_t *order, int32_t cnt, const int32_t *rp,
+                                const int32_t *col, const int32_t *w, const int32_t *s,
+                                long long m, const int32_t *root, const int32_t *sigma,
+                                int32_t *best, long long *gain, int32_t *kown,
+                                unsigned long long *ncand) {
+    __shared__ int tab[kWarpHashWarps][2 * kWarpHashCap];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *keys = tab[wib], *vals = tab[wib] + kWarpHashCap;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned cand = 0;
+    for (long long idx = warp; idx < cnt; idx += nwarps) {
+        int i = order[idx];
+        int start = rp[i], deg = rp[i + 1] - start;
+        int ci = root[i], si = s[i];
+        int lg = ilog2_pow2_at_least(2 * deg);
+        int cap = 1 << lg;
+        for (int k = lane; k < cap; k += 32) { keys[k] = -1; vals[k] = 0; }
+        __syncwarp();
+        for (int p = start + lane; p < start + deg; p += 32) {
+            int j = col[p];
+            if (j == i) continue;
+            int c = root[j], wv = w[p];
+            unsigned h = hash_slot(c, lg);
+            for (;;) {
+                int prev = atomicCAS(&keys[h], -1, c);
+                if (prev == -1 || prev == c) { atomicAdd(&vals[h], wv); break; }
+                h = (h + 1) & (cap - 1);
+            }
+        }
+        __syncwarp();
+        long long own = 0, sc = LLONG_MIN;
+        int cc = INT_MAX;
+        for (int k = lane; k < cap; k += 32) {
+            int c = keys[k];
+            if (c < 0) continue;
+            if (c == ci) { own = vals[k]; continue; }
+            long long v = m * (long long)vals[k] - (long long)si * (long long)sigma[c];
+            if (better(v, c, sc, cc)) { sc = v; cc = c; }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            own += __shfl_xor_sync(FULL, own, o);
+            long long osc = __shfl_xor_sync(FULL, sc, o);
+            int occ = __shfl_xor_sync(FULL, cc, o);
+            if (better(osc, occ, sc, cc)) { sc = osc; cc = occ; }
+        }
+        if (lane == 0) scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
+        __syncwarp();
+    }
+    count_add(ncand, cand);
+}
+
+// Block-wide argmax + sum; result valid in thread 0.
+__device__ void block_reduce_best(long long &own, long long &sc, int &cc) {
+    __shared__ long long r_own[32], r_sc[32];
+    __shared__ int r_cc[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        own += __shfl_xor_sync(FULL, own, o);
+        long long osc = __shfl_xor_sync(FULL, sc, o);
+        int occ = __shfl_xor_sync(FULL, cc, o);
+        if (better(osc, occ, sc, cc)) { sc = osc; cc = occ; }
+    }
+    if (lane == 0) { r_own[wid] = own; r_sc[wid] = sc; r_cc[wid] = cc; }
+    __syncthreads();
+    if (wid == 0) {
+        own = lane < nw ? r_own[lane] : 0;
+        sc = lane < nw ? r_sc[lane] : LLONG_MIN;
+        cc = lane < nw ? r_cc[lane] : INT_MAX;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            own += __shfl_xor_sync(FULL, own, o);
+            long long osc = __shfl_xor_sync(FULL, sc, o);
+            int occ = __shfl_xor_sync(FULL, cc, o);
+            if (better(osc, occ, sc, cc)) { sc = osc; cc = occ; }
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// MAXIMAL scan, block shape: one node per block; table in shared memory when
+// it fits, else in a global-memory slice of 2*deg (rounded up) slots.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *order, int32_t cnt, const int32_t *rp,
+                             const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                             const int32_t *root, const int32_t *sigma, int32_t *best,
+                             long long *gain, int32_t *kown, unsigned long long *ncand,
+                             int *gkeys, int *gvals, const long long *goff) {
+    extern __shared__ int sm[];
+    unsigned cand = 0;
+    for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
+        int i = order[idx];
+        int start = rp[i], deg = rp[i + 1] - start;
+        int ci = root[i], si = s[i];
+        int lg = ilog2_pow2_at_least(2 * deg);
+        int cap = 1 << lg;
+        int *keys, *vals;
+        if (deg <= kBlockSmemMaxDeg) {
+            keys = sm;
+            vals = sm + cap;
+        } else {
+            keys = gkeys + goff[idx];
+            vals = gvals + goff[idx];
+        }
+        for (int k = threadIdx.x; k < cap; k += blockDim.x) { keys[k] = -1; vals[k] = 0; }
+        __syncthreads();
+        for (int p = start + threadIdx.x; p < start + deg; p += blockDim.x) {
+            int j = col[p];
+            if (j == i) continue;
+            int c = root[j], wv = w[p];
+            unsigned h = hash_slot(c, lg);
+            for (;;) {
+                int prev = atomicCAS(&keys[h], -1, c);
+                if (prev == -1 || prev == c) { atomicAdd(&vals[h], wv); break; }
+                h = (h + 1) & (cap - 1);
+            }
+        }
+        __syncthreads();
+        long long own = 0, sc = LLONG_MIN;
+        int cc = INT_MAX;
+        for (int k = threadIdx.x; k < cap; k += blockDim.x) {
+            int c = keys[k];
+            if (c < 0) continue;
+            if (c == ci) { own = vals[k]; continue; }
+            long long v = m * (long long)vals[k] - (long long)si * (long long)sigma[c];
+            if (better(v, c, sc, cc)) { sc = v; cc = c; }
+        }
+        block_reduce_best(own, sc, cc);
+        if (threadIdx.x == 0) scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && cand) atomicAdd(ncand, (unsigned long long)cand);
+}
+
+__global__ void k_scan_empty(const int32_t *order, int32_t cnt, const int32_t *root,
+                             int32_t *best, long long *gain, int32_t *kown) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < cnt;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int i = order[idx];
+        best[i] = root[i];
+        gain[i] = 0;
+        kown[i] = 0;
+    }
+}
+
+__global__ void k_hub_caps(const int32_t *order, int32_t cnt, const int32_t *rp, long long *cap) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < cnt;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int i = order[idx];
+        int deg = rp[i + 1] - rp[i];
+        long long c = 1;
+        while (c < 2LL * deg) c <<= 1;
+        cap[idx] = deg > kBlockSmemMaxDeg ? c : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pair argmax (ASSIGN and target): argmax over neighbours j != i, optionally
+// restricted to root[j] == want, of m_w W_ij - s_i s_j; ties smallest j.
+// ---------------------------------------------------------------------------
+struct PairBest {
+    long long sc;
+    int j;
+};
+__device__ __forceinline__ void pair_consider(PairBest &b, long long sc, int j) {
+    if (better(sc, j, b.sc, b.j)) { b.sc = sc; b.j = j; }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_assign_group(const int32_t *order, int32_t cnt, const int32_t *rp,
+                               const int32_t *col, const int32_t *w, const int32_t *s,
+                               long long m, int32_t *a) {
+    constexpr int NPW = 32 / G;
+    const int lane = threadIdx.x & 31, gl = lane % G;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long base = warp * NPW; base < cnt; base += nwarps * NPW) {
+        long long idx = base + lane / G;
+        bool vn = idx < cnt;
+        int i = vn ? order[idx] : 0;
+        int start = vn ? rp[i] : 0, end = vn ? rp[i + 1] : 0;
+        long long si = vn ? s[i] : 0;
+        PairBest b{LLONG_MIN, INT_MAX};
+        for (int p = start + gl; p < end; p += G) {
+            int j = col[p];
+            if (j == i) continue;
+            pair_consider(b, m * (long long)w[p] - si * (long long)s[j], j);
+        }
+#pragma unroll
+        for (int o = G / 2; o; o >>= 1) {
+            long long osc = __shfl_xor_sync(FULL, b.sc, o);
+            int oj = __shfl_xor_sync(FULL, b.j, o);
+            pair_consider(b, osc, oj);
+        }
+        if (gl == 0 && vn) a[i] = (b.j != INT_MAX && b.sc > 0) ? b.j : i;
+    }
+}
+
+__global__ void __launch_bounds__(kBlockThreads) k_assign_block(const int32_t *order, int32_t cnt, const int32_t *rp,
+                               const int32_t *col, const int32_t *w, const int32_t *s,
+                               long long m, int32_t *a) {
+    for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
+        int i = order[idx];
+        long long si = s[i];
+        PairBest b{LLONG_MIN, INT_MAX};
+        for (int p = rp[i] + threadIdx.x; p < rp[i + 1]; p += blockDim.x) {
+            int j = col[p];
+            if (j == i) continue;
+            pair_consider(b, m * (long long)w[p] - si * (long long)s[j], j);
+        }
+        long long dummy = 0;
+        block_reduce_best(dummy, b.sc, b.j);
+        if (threadIdx.x == 0) a[i] = (b.j != INT_MAX && b.sc > 0) ? b.j : i;
+    }
+}
+
+__global__ void k_assign_empty(const int32_t *order, int32_t cnt, int32_t *a) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < cnt;
+         idx += (long long)gridDim.x * blockDim.x)
+        a[order[idx]] = order[idx];
+}
+
+// Target of every accepted node: one warp per node.
+__global__ void k_target(const int32_t *list, const int32_t *cnt_dev, const int32_t *rp,
+                         const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                         const int32_t *root, const int32_t *best, int32_t *tgt) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int cnt = *cnt_dev;
+    for (long long idx = warp; idx < cnt; idx += nwarps) {
+        int i = list[idx];
+        int want = best[i];
+        long long si = s[i];
+        PairBest b{LLONG_MIN, INT_MAX};
+        for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+            int j = col[p];
+            if (j == i || root[j] != want) continue;
+            pair_consider(b, m * (long long)w[p] - si * (long long)s[j], j);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            long long osc = __shfl_xor_sync(FULL, b.sc, o);
+            int oj = __shfl_xor_sync(FULL, b.j, o);
+            pair_consider(b, osc, oj);
+        }
+        // never empty: best_i is a neighbouring community; a self-assignment
+        // keeps the array valid should that ever fail
+        if (lane == 0) tgt[i] = (b.j != INT_MAX) ? b.j : i;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Own-community weight and POSITIVE's flags.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void own_emit(int i, int ci, long long si, long long m,
+                                         const int32_t *sigma, long long own, int32_t *kown,
+                                         int32_t *flag) {
+    kown[i] = (int32_t)own;
+    long long g = m * own - si * ((long long)sigma[ci] - si);
+    if (g < 0) flag[ci] = 1;
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_own_group(const int32_t *order, int32_t cnt, const int32_t *rp,
+                            const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                            const int32_t *root, const int32_t *sigma, int32_t *kown,
+                            int32_t *flag) {
+    constexpr int NPW = 32 / G;
+    const int lane = threadIdx.x & 31, gl = lane % G;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long base = warp * NPW; base < cnt; base += nwarps * NPW) {
+        long long idx = base + lane / G;
+        bool vn = idx < cnt;
+        int i = vn ? order[idx] : 0;
+        int ci = vn ? root[i] : -1;
+        long long own = 0;
+        if (vn)
+            for (int p = rp[i] + gl; p < rp[i + 1]; p += G) {
+                int j = col[p];
+                if (j != i && root[j] == ci) own += w[p];
+            }
+#pragma unroll
+        for (int o = G / 2; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
+        if (gl == 0 && vn) own_emit(i, ci, s[i], m, sigma, own, kown, flag);
+    }
+}
+
+__global__ void __launch_bounds__(kBlockThreads) k_own_block(const int32_t *order, int32_t cnt, const int32_t *rp,
+                            const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                            const int32_t *root, const int32_t *sigma, int32_t *kown,
+                            int32_t *flag) {
+    for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
+        int i = order[idx];
+        int ci = root[i];
+        long long own = 0;
+        for (int p = rp[i] + threadIdx.x; p < rp[i + 1]; p += blockDim.x) {
+            int j = col[p];
+            if (j != i && root[j] == ci) own += w[p];
+        }
+        long long sc = LLONG_MIN;
+        int cc = INT_MAX;
+        block_reduce_best(own, sc, cc);
+        if (threadIdx.x == 0) own_emit(i, ci, s[i], m, sigma, own, kown, flag);
+    }
+}
+
+__global__ void k_local_gain(int32_t n, const int32_t *s, long long m, const int32_t *root,
+                             const int32_t *sigma, const int32_t *kown, long long *g) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long si = s[i];
+        g[i] = m * (long long)kown[i] - si * ((long long)sigma[root[i]] - si);
+    }
+}
+
+}  // namespace
+
+void local_gain_nodes(int32_t n, const int32_t *s, long long m, const int32_t *root,
+                      const int32_t *sigma, const int32_t *kown, long long *g, cudaStream_t st) {
+    if (n <= 0) return;
+    k_local_gain<<<grid_for(n, 256), 256, 0, st>>>(n, s, m, root, sigma, kown, g);
+    SLM_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
+    for (int b = 0; b <= kNumBuckets; b++) off[b] = 0;
+    order.ensure(sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s);
+    if (n <= 0) return;
+    DevBuf keys(sizeof(uint32_t) * n, s), keys_tmp(sizeof(uint32_t) * n, s),
+        vals_tmp(sizeof(int32_t) * n, s), counts(sizeof(int32_t) * kNumBuckets, s);
+    SLM_CUDA(cudaMemsetAsync(counts.get(), 0, counts.bytes(), s));
+    k_bucket_keys<<<grid_for(n, 256), 256, 0, s>>>(n, rp, keys.as<uint32_t>(), order.as<int32_t>(),
+                                                   counts.as<int32_t>());
+    SLM_LAUNCH_CHECK();
+    radix_sort_u32(keys.as<uint32_t>(), order.as<int32_t>(), keys_tmp.as<uint32_t>(),
+                   vals_tmp.as<int32_t>(), n, 3, s);
+    int32_t h[kNumBuckets];
+    SLM_CUDA(cudaMemcpyAsync(h, counts.get(), sizeof h, cudaMemcpyDeviceToHost, s));
+    SLM_CUDA(cudaStreamSynchronize(s));
+    for (int b = 0; b < kNumBuckets; b++) off[b + 1] = off[b] + h[b];
+}
+
+static int blocks_for_groups(long long cnt, int nodes_per_warp, int threads = 256) {
+    long long warps = (cnt + nodes_per_warp - 1) / nodes_per_warp;
+    return grid_for(warps * 32, threads, kNumSMs * 16);
+}
+
+void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                  const int32_t *s, long long m, const Buckets &bk, int32_t *a, cudaStream_t st) {
+    if (n <= 0) return;
+    const int32_t *ord = bk.order.as<int32_t>();
+    auto seg = [&](int b) { return std::make_pair(ord + bk.off[b], bk.off[b + 1] - bk.off[b]); };
+    {
+        auto [o, c] = seg(kBucketEmpty);
+        if (c) { k_assign_empty<<<grid_for(c, 256), 256, 0, st>>>(o, c, a); SLM_LAUNCH_CHECK(); }
+    }
+    {
+        auto [o, c] = seg(kBucketG4);
+        if (c) { k_assign_group<4><<<blocks_for_groups(c, 8), 256, 0, st>>>(o, c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+    }
+    {
+        auto [o, c] = seg(kBucketG8);
+        if (c) { k_assign_group<8><<<blocks_for_groups(c, 4), 256, 0, st>>>(o, c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+    }
+    {
+        auto [o, c] = seg(kBucketG16);
+        if (c) { k_assign_group<16><<<blocks_for_groups(c, 2), 256, 0, st>>>(o, c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+    }
+    {
+        // 17..256 edges: one warp per node, lanes stride over the row
+        int c = bk.off[kBucketWarpHash + 1] - bk.off[kBucketG32];
+        if (c) { k_assign_group<32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+    }
+    {
+        auto [o, c] = seg(kBucketBlock);
+        if (c) { k_assign_block<<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(o, c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+    }
+}
+
+void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                const int32_t *s, long long m, const int32_t *root, const int32_t *sigma,
+                const Buckets &bk, int32_t *best, long long *gain, int32_t *kown,
+                unsigned long long *ncand, cudaStream_t st) {
+    if (n <= 0) return;
+    const int32_t *ord = bk.order.as<int32_t>();
+    auto cnt = [&](int b) { return bk.off[b + 1] - bk.off[b]; };
+    if (int c = cnt(kBucketEmpty)) {
+        k_scan_empty<<<grid_for(c, 256), 256, 0, st>>>(ord + bk.off[kBucketEmpty], c, root, best, gain, kown);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketG4)) {
+        k_scan_group<4><<<blocks_for_groups(c, 8), 256, 0, st>>>(ord + bk.off[kBucketG4], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketG8)) {
+        k_scan_group<8><<<blocks_for_groups(c, 4), 256, 0, st>>>(ord + bk.off[kBucketG8], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketG16)) {
+        k_scan_group<16><<<blocks_for_groups(c, 2), 256, 0, st>>>(ord + bk.off[kBucketG16], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketG32)) {
+        k_scan_group<32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketWarpHash)) {
+        k_scan_warphash<<<grid_for((long long)c * 32, kWarpHashWarps * 32, kNumSMs * 8), kWarpHashWarps * 32, 0, st>>>(
+            ord + bk.off[kBucketWarpHash], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketBlock)) {
+        const int32_t *o = ord + bk.off[kBucketBlock];
+        // global tables for hubs beyond the shared-memory table
+        DevBuf caps(sizeof(long long) * (c + 1), st), tot(sizeof(long long), st);
+        k_hub_caps<<<grid_for(c, 256), 256, 0, st>>>(o, c, rp, caps.as<long long>());
+        SLM_LAUNCH_CHECK();
+        exclusive_scan_i64(caps.as<long long>(), caps.as<long long>(), c, tot.as<long long>(), st);
+        long long total = 0;
+        SLM_CUDA(cudaMemcpyAsync(&total, tot.get(), sizeof total, cudaMemcpyDeviceToHost, st));
+        SLM_CUDA(cudaStreamSynchronize(st));
+        DevBuf gk(sizeof(int) * (size_t)(total > 0 ? total : 1), st),
+            gv(sizeof(int) * (size_t)(total > 0 ? total : 1), st);
+        size_t smem = sizeof(int) * 2 * kBlockSmemCap;
+        static bool attr_set = false;
+        if (!attr_set) {
+            SLM_CUDA(cudaFuncSetAttribute(k_scan_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set = true;
+        }
+        k_scan_block<<<grid_for(c, 1, kNumSMs * 3), kBlockThreads, smem, st>>>(
+            o, c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand, gk.as<int>(), gv.as<int>(),
+            caps.as<long long>());
+        SLM_LAUNCH_CHECK();
+    }
+}
+
+void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                      const int32_t *s, long long m, const int32_t *root, const int32_t *sigma,
+                      const Buckets &bk, int32_t *kown, int32_t *flag, cudaStream_t st) {
+    if (n <= 0) return;
+    const int32_t *ord = bk.order.as<int32_t>();
+    // isolated nodes: own weight 0, local gain 0 (never flagged)
+    int c0 = bk.off[kBucketEmpty + 1] - bk.off[kBucketEmpty];
+    if (c0) {
+        k_own_group<4><<<blocks_for_groups(c0, 8), 256, 0, st>>>(ord, c0, rp, col, w, s, m, root, sigma, kown, flag);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = bk.off[kBucketG4 + 1] - bk.off[kBucketG4]) {
+        k_own_group<4><<<blocks_for_groups(c, 8), 256, 0, st>>>(ord + bk.off[kBucketG4], c, rp, col, w, s, m, root, sigma, kown, flag);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = bk.off[kBucketG8 + 1] - bk.off[kBucketG8]) {
+        k_own_group<8><<<blocks_for_groups(c, 4), 256, 0, st>>>(ord + bk.off[kBucketG8], c, rp, col, w, s, m, root, sigma, kown, flag);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = bk.off[kBucketG16 + 1] - bk.off[kBucketG16]) {
+        k_own_group<16><<<blocks_for_groups(c, 2), 256, 0, st>>>(ord + bk.off[kBucketG16], c, rp, col, w, s, m, root, sigma, kown, flag);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = bk.off[kBucketWarpHash + 1] - bk.off[kBucketG32]) {
+        k_own_group<32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, kown, flag);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = bk.off[kBucketBlock + 1] - bk.off[kBucketBlock]) {
+        k_own_block<<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(ord + bk.off[kBucketBlock], c, rp, col, w, s, m, root, sigma, kown, flag);
+        SLM_LAUNCH_CHECK();
+    }
+}
+
+void target_nodes(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt, const int32_t *rp,
+                  const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                  const int32_t *root, const int32_t *best, int32_t *tgt, cudaStream_t st) {
+    if (max_cnt <= 0) return;
+    k_target<<<grid_for((long long)max_cnt * 32, 256, kNumSMs * 16), 256, 0, st>>>(
+        list, cnt_dev, rp, col, w, s, m, root, best, tgt);
+    SLM_LAUNCH_CHECK();
+}
+
+}  // namespace slm

@@ -1,0 +1,663 @@
+// slm_api.cu -- host driver of the Synchronised Louvain Method (Algorithm 1)
+// and the C ABI declared in slm.h and slm_steps.h.
+//
+// Per level t (Algorithm 1):
+//   ASSIGN -> COMPONENTS -> POSITIVE, then while a node has a positive move:
+//   MAXIMAL (scan, branch gains, draw, target, one synchronous write) ->
+//   COMPONENTS -> POSITIVE; then compaction, and AGGREGATE when the level
+//   found structure (K < n).  Every step runs in the kernels of k_*.cu; the
+//   host only reads the few counters that decide the control flow.
+#include <algorithm>
+#include <array>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "slm_internal.cuh"
+#include "slm_steps.h"
+
+using slm::DevBuf;
+
+struct slm_graph {
+    int32_t n0 = 0;
+    int32_t nnz0 = 0;
+    long long m = 0;
+    DevBuf rp, col, w, s;  // the input graph (device copies)
+    bool has_run = false;
+    struct Level {
+        int32_t n = 0, K = 0;
+        DevBuf labels;  // ids on this level's nodes
+        DevBuf comp;    // partition composed onto the input nodes
+        slm_level_stats st{};
+    };
+    std::vector<Level> levels;
+    slm_level_stats top{};
+    DevBuf final_comp;
+    std::vector<std::array<long long, 6>> trace;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+template <class F> slm_status guarded(slm_graph *g, F &&f) {
+    try {
+        f();
+        return SLM_OK;
+    } catch (const slm::Error &e) {
+        if (g) g->err = e.msg;
+        else g_create_error = e.msg;
+        return e.status;
+    } catch (const std::exception &e) {
+        if (g) g->err = e.what();
+        else g_create_error = e.what();
+        return SLM_ERR_CUDA;
+    }
+}
+
+__global__ void k_iota(int32_t n, int32_t *p) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = (int32_t)i;
+}
+__global__ void k_fill_ones(long long n, int32_t *p) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = 1;
+}
+
+// Per-level device workspace.
+struct Work {
+    int32_t n = 0;
+    DevBuf a, sigma, best, kown, tgt, acclist, gain, bg, counters;
+    DevBuf root, oncycle, entry, depth, cdist, jmpA, jmpB;
+    DevBuf bs_i32, bs_i64;
+    slm::Forest f;
+    slm::BranchScratch bs{};
+    slm::PositiveScratch ps;
+    slm::Buckets bk;
+
+    void init(int32_t n_, const int32_t *rp, cudaStream_t st) {
+        n = n_;
+        size_t N = (size_t)(n > 0 ? n : 1);
+        a.ensure(4 * N, st);
+        sigma.ensure(4 * N, st);
+        best.ensure(4 * N, st);
+        kown.ensure(4 * N, st);
+        tgt.ensure(4 * N, st);
+        acclist.ensure(4 * N, st);
+        gain.ensure(8 * N, st);
+        bg.ensure(8 * N, st);
+        counters.ensure(64, st);
+        root.ensure(4 * N, st);
+        oncycle.ensure(N, st);
+        entry.ensure(4 * N, st);
+        depth.ensure(4 * N, st);
+        cdist.ensure(4 * N, st);
+        jmpA.ensure(8 * N, st);
+        jmpB.ensure(8 * N, st);
+        bs_i32.ensure(4 * N * 5, st);
+        bs_i64.ensure(8 * N * 5, st);
+        f.root = root.as<int32_t>();
+        f.oncycle = oncycle.as<uint8_t>();
+        f.entry = entry.as<int32_t>();
+        f.depth = depth.as<int32_t>();
+        f.cdist = cdist.as<int32_t>();
+        f.jmpA = jmpA.as<int2>();
+        f.jmpB = jmpB.as<int2>();
+        int32_t *p32 = bs_i32.as<int32_t>();
+        long long *p64 = bs_i64.as<long long>();
+        bs.haschild = p32;
+        bs.active = p32 + N;
+        bs.covered = p32 + 2 * N;
+        bs.treeact = p32 + 3 * N;
+        bs.commcyc = p32 + 4 * N;
+        bs.subS = p64;
+        bs.subWA = p64 + N;
+        bs.subWin = p64 + 2 * N;
+        bs.credit = p64 + 3 * N;
+        bs.WB = p64 + 4 * N;
+        bk.build(n, rp, st);
+    }
+    unsigned long long *ctr() { return counters.as<unsigned long long>(); }
+};
+
+// POSITIVE until no community holds a node with a negative local gain.
+long long positive_all(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                       const int32_t *s, long long m, Work &W, cudaStream_t st) {
+    long long total = 0;
+    // every round splits at least one community, so n rounds always suffice
+    for (long long round = 0;; round++) {
+        if (round > (long long)n) slm::fail(SLM_ERR_TIMEOUT, "POSITIVE did not settle within n rounds");
+        slm::community_sigma(n, W.f.root, s, W.sigma.as<int32_t>(), st);
+        int k = slm::positive_round(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f,
+                                    W.sigma.as<int32_t>(), W.bk, W.ps, st);
+        if (k == 0) break;
+        total += k;
+        slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
+    }
+    return total;
+}
+
+struct SweepCounts {
+    long long cand = 0, pos = 0, acc = 0;
+};
+
+// One MAXIMAL correction: scan, branch gains, draw, target, write.
+SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                         const int32_t *s, long long m, Work &W, unsigned long long seed,
+                         unsigned long long P, int level, int sweep, bool stop_if_no_cand,
+                         cudaStream_t st, slm::HostCounters &hc) {
+    SweepCounts c;
+    unsigned long long *ctr = W.ctr();
+    SLM_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
+    slm::community_sigma(n, W.f.root, s, W.sigma.as<int32_t>(), st);
+    slm::scan_nodes(n, rp, col, w, s, m, W.f.root, W.sigma.as<int32_t>(), W.bk,
+                    W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), ctr, st);
+    SLM_CUDA(cudaMemcpyAsync(hc.h, ctr, 8, cudaMemcpyDeviceToHost, st));
+    SLM_CUDA(cudaStreamSynchronize(st));
+    c.cand = (long long)hc.h[0];
+    if (c.cand == 0 && stop_if_no_cand) return c;
+    slm::branch_gains(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
+                      W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), W.bs,
+                      W.bg.as<long long>(), st);
+    int32_t *acc_cnt = reinterpret_cast<int32_t *>(ctr + 2);
+    slm::accept_moves(n, W.bg.as<long long>(), seed, P, level, sweep, W.acclist.as<int32_t>(),
+                      acc_cnt, ctr + 1, st);
+    SLM_CUDA(cudaMemcpyAsync(hc.h, ctr, 24, cudaMemcpyDeviceToHost, st));
+    SLM_CUDA(cudaStreamSynchronize(st));
+    c.pos = (long long)hc.h[1];
+    c.acc = (long long)(int32_t)(hc.h[2] & 0xffffffff);
+    if (c.pos == 0 || c.acc == 0) return c;
+    slm::target_nodes(W.acclist.as<int32_t>(), acc_cnt, (int32_t)c.acc, rp, col, w, s, m,
+                      W.f.root, W.best.as<int32_t>(), W.tgt.as<int32_t>(), st);
+    slm::apply_moves(W.acclist.as<int32_t>(), acc_cnt, (int32_t)c.acc, W.tgt.as<int32_t>(),
+                     W.a.as<int32_t>(), st);
+    return c;
+}
+
+void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
+    if (opt.max_sweeps < 0 || opt.max_sweeps > 65535 || opt.max_levels < 0 ||
+        opt.max_levels > 65535 || opt.accept_p32 > (1ull << 32))
+        slm::fail(SLM_ERR_INVALID_ARGUMENT, "options out of range");
+    g->levels.clear();
+    g->trace.clear();
+    g->has_run = false;
+    g->top = slm_level_stats{};
+    const int32_t n0 = g->n0;
+    g->final_comp.alloc(4 * (size_t)(n0 > 0 ? n0 : 1), st);
+    if (n0 > 0) {
+        k_iota<<<slm::grid_for(n0, 256), 256, 0, st>>>(n0, g->final_comp.as<int32_t>());
+        SLM_LAUNCH_CHECK();
+    }
+    slm::HostCounters hc;
+    // current level graph
+    int32_t n = n0;
+    int32_t nnz = g->nnz0;
+    const int32_t *rp = g->rp.as<int32_t>(), *col = g->col.as<int32_t>(), *w = g->w.as<int32_t>();
+    const int32_t *s = g->s.as<int32_t>();
+    DevBuf lrp, lcol, lw, ls;  // owned aggregated graph
+    const long long m = g->m;
+    Work W;
+    for (int t = 0; n > 0; t++) {
+        W.init(n, rp, st);
+        slm_level_stats stt{};
+        stt.n = n;
+        stt.nnz = nnz;
+        slm::assign_nodes(n, rp, col, w, s, m, W.bk, W.a.as<int32_t>(), st);
+        slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
+        if (!(opt.flags & SLM_FLAG_NO_POSITIVE)) stt.splits += positive_all(n, rp, col, w, s, m, W, st);
+        int sweep = 0;
+        int status = 2;
+        for (; sweep < opt.max_sweeps; sweep++) {
+            SweepCounts c = maximal_once(n, rp, col, w, s, m, W, opt.seed, opt.accept_p32, t, sweep,
+                                         true, st, hc);
+            stt.candidates += c.cand;
+            stt.edges_scanned += nnz;
+            if (c.cand == 0) {
+                status = 0;
+                g->trace.push_back({t, sweep, 0, 0, 0, 0});
+                sweep++;
+                break;
+            }
+            if (c.pos == 0) {
+                status = 1;
+                g->trace.push_back({t, sweep, c.cand, 0, 0, 0});
+                sweep++;
+                break;
+            }
+            long long spl = 0;
+            stt.moves += c.acc;
+            if (c.acc > 0) {
+                slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
+                if (!(opt.flags & SLM_FLAG_NO_POSITIVE)) spl = positive_all(n, rp, col, w, s, m, W, st);
+                stt.splits += spl;
+            }
+            g->trace.push_back({t, sweep, c.cand, c.pos, c.acc, spl});
+        }
+        stt.sweeps = sweep;
+        stt.status = status;
+        if (status == 2 && (opt.flags & SLM_FLAG_STRICT))
+            slm::fail(SLM_ERR_NOT_CONVERGED, "sweep limit reached");
+        DevBuf id(4 * (size_t)n, st), scratch(4 * (size_t)n, st);
+        int32_t K = slm::compact_labels(n, W.f.root, id.as<int32_t>(), scratch.as<int32_t>(), st);
+        stt.n_communities = K;
+        if (K == n) {
+            g->top = stt;
+            break;
+        }
+        slm::compose_labels(n0, g->final_comp.as<int32_t>(), id.as<int32_t>(), st);
+        slm_graph::Level L;
+        L.n = n;
+        L.K = K;
+        L.st = stt;
+        L.comp.alloc(4 * (size_t)n0, st);
+        SLM_CUDA(cudaMemcpyAsync(L.comp.get(), g->final_comp.get(), 4 * (size_t)n0,
+                                 cudaMemcpyDeviceToDevice, st));
+        // AGGREGATE
+        DevBuf nrp, ncol, nw;
+        int32_t nnz2 = slm::aggregate_graph(n, rp, col, w, id.as<int32_t>(), K, nrp, ncol, nw, st);
+        DevBuf ns(4 * (size_t)K, st);
+        slm::strengths(K, nrp.as<int32_t>(), nw.as<int32_t>(), ns.as<int32_t>(), st);
+        L.labels = std::move(id);
+        g->levels.push_back(std::move(L));
+        lrp = std::move(nrp);
+        lcol = std::move(ncol);
+        lw = std::move(nw);
+        ls = std::move(ns);
+        rp = lrp.as<int32_t>();
+        col = lcol.as<int32_t>();
+        w = lw.as<int32_t>();
+        s = ls.as<int32_t>();
+        n = K;
+        nnz = nnz2;
+        if (t + 1 >= opt.max_levels) break;
+    }
+    SLM_CUDA(cudaStreamSynchronize(st));
+    g->has_run = true;
+}
+
+void check_csr_host(int32_t n, const int32_t *rp_h, long long *nnz) {
+    if (rp_h[0] != 0) slm::fail(SLM_ERR_INVALID_ARGUMENT, "row_ptr[0] must be 0");
+    for (int32_t i = 0; i < n; i++)
+        if (rp_h[i + 1] < rp_h[i]) slm::fail(SLM_ERR_INVALID_ARGUMENT, "row_ptr must be non-decreasing");
+    *nnz = rp_h[n];
+}
+
+}  // namespace
+
+extern "C" {
+
+void slm_default_options(slm_options *opt) {
+    if (!opt) return;
+    opt->seed = 1;
+    opt->accept_p32 = 1ull << 31;
+    opt->max_sweeps = 1000;
+    opt->max_levels = 64;
+    opt->flags = 0;
+}
+
+const char *slm_status_string(slm_status s) {
+    switch (s) {
+    case SLM_OK: return "ok";
+    case SLM_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case SLM_ERR_NOT_SYMMETRIC: return "matrix not symmetric";
+    case SLM_ERR_OVERFLOW: return "total weight must be below 2^31";
+    case SLM_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case SLM_ERR_CUDA: return "CUDA error";
+    case SLM_ERR_NOT_RUN: return "slm_run has not completed on this graph";
+    case SLM_ERR_NOT_CONVERGED: return "sweep limit reached";
+    case SLM_ERR_TIMEOUT: return "timeout";
+    case SLM_ERR_BUDGET: return "memory budget exceeded";
+    }
+    return "unknown status";
+}
+
+const char *slm_last_error(const slm_graph *g) {
+    return g ? g->err.c_str() : g_create_error.c_str();
+}
+
+slm_status slm_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                            const int32_t *weights, int where, void *stream, slm_graph **out) {
+    if (!out) return SLM_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    auto g = std::make_unique<slm_graph>();
+    slm_status st = guarded(nullptr, [&] {
+        cudaStream_t s = as_stream(stream);
+        if (n < 0 || !row_ptr || (where != SLM_HOST && where != SLM_DEVICE))
+            slm::fail(SLM_ERR_INVALID_ARGUMENT, "bad n, row_ptr or where");
+        std::vector<int32_t> rp_h((size_t)n + 1);
+        cudaMemcpyKind kind = where == SLM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        if (where == SLM_HOST) std::memcpy(rp_h.data(), row_ptr, sizeof(int32_t) * rp_h.size());
+        else {
+            SLM_CUDA(cudaMemcpyAsync(rp_h.data(), row_ptr, sizeof(int32_t) * rp_h.size(),
+                                     cudaMemcpyDeviceToHost, s));
+            SLM_CUDA(cudaStreamSynchronize(s));
+        }
+        long long nnz = 0;
+        check_csr_host(n, rp_h.data(), &nnz);
+        if (nnz >= (1LL << 31)) slm::fail(SLM_ERR_OVERFLOW, "too many entries");
+        if (nnz > 0 && !col_idx) slm::fail(SLM_ERR_INVALID_ARGUMENT, "col_idx is NULL");
+        g->n0 = n;
+        g->nnz0 = (int32_t)nnz;
+        g->rp.alloc(4 * ((size_t)n + 1), s);
+        g->col.alloc(4 * (size_t)(nnz > 0 ? nnz : 1), s);
+        g->w.alloc(4 * (size_t)(nnz > 0 ? nnz : 1), s);
+        g->s.alloc(4 * (size_t)(n > 0 ? n : 1), s);
+        SLM_CUDA(cudaMemcpyAsync(g->rp.get(), rp_h.data(), 4 * ((size_t)n + 1),
+                                 cudaMemcpyHostToDevice, s));
+        if (nnz > 0) {
+            SLM_CUDA(cudaMemcpyAsync(g->col.get(), col_idx, 4 * (size_t)nnz, kind, s));
+            if (weights) SLM_CUDA(cudaMemcpyAsync(g->w.get(), weights, 4 * (size_t)nnz, kind, s));
+            else {
+                k_fill_ones<<<slm::grid_for(nnz, 256), 256, 0, s>>>(nnz, g->w.as<int32_t>());
+                SLM_LAUNCH_CHECK();
+            }
+        }
+        int bad = slm::validate_csr(n, g->rp.as<int32_t>(), g->col.as<int32_t>(), g->w.as<int32_t>(), s);
+        if (bad & (1 | 8)) slm::fail(SLM_ERR_INVALID_ARGUMENT, "column index out of range, unsorted or duplicated");
+        if (bad & 2) slm::fail(SLM_ERR_INVALID_ARGUMENT, "non-positive weight");
+        if (bad & 4) slm::fail(SLM_ERR_NOT_SYMMETRIC, "W is not symmetric");
+        // m_w < 2^31 keeps every gain exact in int64; the weights sum is
+        // bounded first so that the per-node strengths fit in int32
+        g->m = slm::strengths(n, g->rp.as<int32_t>(), g->w.as<int32_t>(), g->s.as<int32_t>(), s);
+        if (g->m >= (1LL << 31)) slm::fail(SLM_ERR_OVERFLOW, "m_w must be below 2^31");
+        SLM_CUDA(cudaStreamSynchronize(s));
+    });
+    if (st == SLM_OK) *out = g.release();
+    return st;
+}
+
+slm_status slm_run(slm_graph *g, const slm_options *opt, void *stream) {
+    if (!g) return SLM_ERR_INVALID_ARGUMENT;
+    slm_options o;
+    slm_default_options(&o);
+    if (opt) o = *opt;
+    return guarded(g, [&] { run_impl(g, o, as_stream(stream)); });
+}
+
+slm_status slm_num_levels(const slm_graph *g, int32_t *levels) {
+    if (!g || !levels) return SLM_ERR_INVALID_ARGUMENT;
+    if (!g->has_run) return SLM_ERR_NOT_RUN;
+    *levels = (int32_t)g->levels.size();
+    return SLM_OK;
+}
+
+slm_status slm_get_partition(const slm_graph *g, int32_t level, int32_t *labels, int where,
+                             int32_t *n_communities) {
+    if (!g) return SLM_ERR_INVALID_ARGUMENT;
+    if (!g->has_run) return SLM_ERR_NOT_RUN;
+    if (level < -1 || level >= (int32_t)g->levels.size()) return SLM_ERR_INVALID_ARGUMENT;
+    if (where != SLM_HOST && where != SLM_DEVICE) return SLM_ERR_INVALID_ARGUMENT;
+    slm_graph *gm = const_cast<slm_graph *>(g);
+    return guarded(gm, [&] {
+        const DevBuf *src;
+        size_t count;
+        int32_t K;
+        if (level == -1) {
+            src = &g->final_comp;
+            count = (size_t)g->n0;
+            K = g->levels.empty() ? g->n0 : g->levels.back().K;
+        } else {
+            src = &g->levels[level].labels;
+            count = (size_t)g->levels[level].n;
+            K = g->levels[level].K;
+        }
+        if (count > 0) {
+            if (!labels) slm::fail(SLM_ERR_INVALID_ARGUMENT, "labels is NULL");
+            SLM_CUDA(cudaMemcpy(labels, src->get(), 4 * count,
+                                where == SLM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice));
+        }
+        if (n_communities) *n_communities = K;
+    });
+}
+
+slm_status slm_modularity(const slm_graph *g, int32_t level, double *q) {
+    if (!g || !q) return SLM_ERR_INVALID_ARGUMENT;
+    if (!g->has_run) return SLM_ERR_NOT_RUN;
+    if (level < -1 || level >= (int32_t)g->levels.size()) return SLM_ERR_INVALID_ARGUMENT;
+    slm_graph *gm = const_cast<slm_graph *>(g);
+    return guarded(gm, [&] {
+        const DevBuf &lab = level == -1 ? g->final_comp : g->levels[level].comp;
+        long long num = slm::modularity_num(g->n0, g->rp.as<int32_t>(), g->col.as<int32_t>(),
+                                            g->w.as<int32_t>(), lab.as<int32_t>(), g->m, nullptr);
+        *q = slm::modularity_from_num(num, g->m);
+    });
+}
+
+slm_status slm_modularity_of(const slm_graph *g, const int32_t *labels, int where, double *q) {
+    if (!g || !q || (g->n0 > 0 && !labels)) return SLM_ERR_INVALID_ARGUMENT;
+    if (where != SLM_HOST && where != SLM_DEVICE) return SLM_ERR_INVALID_ARGUMENT;
+    slm_graph *gm = const_cast<slm_graph *>(g);
+    return guarded(gm, [&] {
+        DevBuf lab(4 * (size_t)(g->n0 > 0 ? g->n0 : 1), nullptr);
+        if (g->n0 > 0)
+            SLM_CUDA(cudaMemcpy(lab.get(), labels, 4 * (size_t)g->n0,
+                                where == SLM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice));
+        // labels must name nodes of the graph
+        std::vector<int32_t> h((size_t)g->n0);
+        if (g->n0 > 0) SLM_CUDA(cudaMemcpy(h.data(), lab.get(), 4 * h.size(), cudaMemcpyDeviceToHost));
+        for (int32_t v : h)
+            if (v < 0 || v >= g->n0) slm::fail(SLM_ERR_INVALID_ARGUMENT, "label out of range");
+        long long num = slm::modularity_num(g->n0, g->rp.as<int32_t>(), g->col.as<int32_t>(),
+                                            g->w.as<int32_t>(), lab.as<int32_t>(), g->m, nullptr);
+        *q = slm::modularity_from_num(num, g->m);
+    });
+}
+
+slm_status slm_get_stats(const slm_graph *g, int32_t level, slm_level_stats *st) {
+    if (!g || !st) return SLM_ERR_INVALID_ARGUMENT;
+    if (!g->has_run) return SLM_ERR_NOT_RUN;
+    if (level < -1 || level >= (int32_t)g->levels.size()) return SLM_ERR_INVALID_ARGUMENT;
+    *st = level == -1 ? g->top : g->levels[level].st;
+    return SLM_OK;
+}
+
+slm_status slm_get_trace(const slm_graph *g, int64_t *rows, int64_t cap, int64_t *len) {
+    if (!g || !len) return SLM_ERR_INVALID_ARGUMENT;
+    *len = (int64_t)g->trace.size();
+    for (int64_t r = 0; r < cap && r < *len; r++)
+        for (int k = 0; k < 6; k++) rows[6 * r + k] = g->trace[r][k];
+    return SLM_OK;
+}
+
+void slm_destroy_graph(slm_graph *g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    delete g;
+}
+
+// ---------------------------------------------------------------------------
+// Step entry points (slm_steps.h)
+// ---------------------------------------------------------------------------
+#define STEP_CHECK(cond) \
+    if (!(cond)) return SLM_ERR_INVALID_ARGUMENT
+
+slm_status slm_step_strengths(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                              const int32_t *w, int32_t *s, int64_t *m_w_host, void *stream) {
+    STEP_CHECK(n >= 0 && (n == 0 || (row_ptr && w && s)) && m_w_host);
+    (void)col;
+    return guarded(nullptr, [&] {
+        *m_w_host = slm::strengths(n, row_ptr, w, s, as_stream(stream));
+    });
+}
+
+slm_status slm_step_assign(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                           const int32_t *s, int64_t m_w, int32_t *a, void *stream) {
+    STEP_CHECK(n >= 0 && (n == 0 || (row_ptr && col && w && s && a)));
+    return guarded(nullptr, [&] {
+        cudaStream_t st = as_stream(stream);
+        slm::Buckets bk;
+        bk.build(n, row_ptr, st);
+        slm::assign_nodes(n, row_ptr, col, w, s, m_w, bk, a, st);
+        SLM_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+slm_status slm_step_components(int32_t n, const int32_t *a, int32_t *root, void *stream) {
+    STEP_CHECK(n >= 0 && (n == 0 || (a && root)));
+    return guarded(nullptr, [&] {
+        cudaStream_t st = as_stream(stream);
+        if (slm::count_out_of_range(n, a, n, st)) slm::fail(SLM_ERR_INVALID_ARGUMENT, "a[v] outside [0, n)");
+        size_t N = (size_t)(n > 0 ? n : 1);
+        DevBuf oc(N, st), en(4 * N, st), de(4 * N, st), cd(4 * N, st), ja(8 * N, st), jb(8 * N, st);
+        slm::Forest f;
+        f.root = root;
+        f.oncycle = oc.as<uint8_t>();
+        f.entry = en.as<int32_t>();
+        f.depth = de.as<int32_t>();
+        f.cdist = cd.as<int32_t>();
+        f.jmpA = ja.as<int2>();
+        f.jmpB = jb.as<int2>();
+        slm::forest_analyse(n, a, f, st);
+        SLM_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+namespace {
+// A level workspace whose assignment and forest describe the caller's state.
+void load_state(Work &W, int32_t n, const int32_t *rp, const int32_t *a, cudaStream_t st) {
+    if (slm::count_out_of_range(n, a, n, st)) slm::fail(SLM_ERR_INVALID_ARGUMENT, "a[v] outside [0, n)");
+    W.init(n, rp, st);
+    if (n > 0)
+        SLM_CUDA(cudaMemcpyAsync(W.a.get(), a, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
+}
+}  // namespace
+
+slm_status slm_step_scan(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                         const int32_t *s, int64_t m_w, const int32_t *root, int32_t *best,
+                         int64_t *gain, int64_t *g_out, void *stream) {
+    STEP_CHECK(n >= 0 && (n == 0 || (row_ptr && col && w && s && root && best && gain)));
+    return guarded(nullptr, [&] {
+        cudaStream_t st = as_stream(stream);
+        if (slm::count_out_of_range(n, root, n, st)) slm::fail(SLM_ERR_INVALID_ARGUMENT, "root[v] outside [0, n)");
+        Work W;
+        W.init(n, row_ptr, st);
+        slm::community_sigma(n, root, s, W.sigma.as<int32_t>(), st);
+        SLM_CUDA(cudaMemsetAsync(W.ctr(), 0, 64, st));
+        slm::scan_nodes(n, row_ptr, col, w, s, m_w, root, W.sigma.as<int32_t>(), W.bk, best,
+                        reinterpret_cast<long long *>(gain), W.kown.as<int32_t>(), W.ctr(), st);
+        if (g_out && n > 0) {
+            // own-community weights without the scan's early outs, then g
+            DevBuf flag(4 * (size_t)n, st);
+            SLM_CUDA(cudaMemsetAsync(flag.get(), 0, 4 * (size_t)n, st));
+            slm::own_weight_nodes(n, row_ptr, col, w, s, m_w, root, W.sigma.as<int32_t>(), W.bk,
+                                  W.kown.as<int32_t>(), flag.as<int32_t>(), st);
+            slm::local_gain_nodes(n, s, m_w, root, W.sigma.as<int32_t>(), W.kown.as<int32_t>(),
+                                  reinterpret_cast<long long *>(g_out), st);
+        }
+        SLM_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+slm_status slm_step_branch_gain(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                const int32_t *w, const int32_t *s, int64_t m_w, const int32_t *a,
+                                const int32_t *root, const int32_t *best, const int64_t *gain,
+                                int64_t *bg, void *stream) {
+    STEP_CHECK(n >= 0 && (n == 0 || (row_ptr && col && w && s && a && root && best && gain && bg)));
+    (void)root;
+    return guarded(nullptr, [&] {
+        cudaStream_t st = as_stream(stream);
+        Work W;
+        load_state(W, n, row_ptr, a, st);
+        slm::community_sigma(n, W.f.root, s, W.sigma.as<int32_t>(), st);
+        // own-community weights of the snapshot
+        SLM_CUDA(cudaMemsetAsync(W.ctr(), 0, 64, st));
+        slm::scan_nodes(n, row_ptr, col, w, s, m_w, W.f.root, W.sigma.as<int32_t>(), W.bk,
+                        W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), W.ctr(), st);
+        slm::branch_gains(n, row_ptr, col, w, s, m_w, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
+                          best, reinterpret_cast<const long long *>(gain), W.kown.as<int32_t>(), W.bs,
+                          reinterpret_cast<long long *>(bg), st);
+        SLM_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+slm_status slm_step_maximal(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                            const int32_t *s, int64_t m_w, int32_t *a, const int32_t *root,
+                            uint64_t seed, uint64_t accept_p32, int32_t level, int32_t sweep,
+                            int64_t *counts_host, void *stream) {
+    STEP_CHECK(n >= 0 && (n == 0 || (row_ptr && col && w && s && a && root)) && counts_host);
+    (void)root;
+    return guarded(nullptr, [&] {
+        cudaStream_t st = as_stream(stream);
+        Work W;
+        load_state(W, n, row_ptr, a, st);
+        slm::HostCounters hc;
+        SweepCounts c = maximal_once(n, row_ptr, col, w, s, m_w, W, seed, accept_p32, level, sweep,
+                                     false, st, hc);
+        if (n > 0) SLM_CUDA(cudaMemcpyAsync(a, W.a.get(), 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        SLM_CUDA(cudaStreamSynchronize(st));
+        counts_host[0] = c.cand;
+        counts_host[1] = c.pos;
+        counts_host[2] = c.acc;
+    });
+}
+
+slm_status slm_step_positive(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                             const int32_t *s, int64_t m_w, int32_t *a, int32_t *root,
+                             int64_t *splits_host, void *stream) {
+    STEP_CHECK(n >= 0 && (n == 0 || (row_ptr && col && w && s && a && root)) && splits_host);
+    return guarded(nullptr, [&] {
+        cudaStream_t st = as_stream(stream);
+        Work W;
+        load_state(W, n, row_ptr, a, st);
+        *splits_host = positive_all(n, row_ptr, col, w, s, m_w, W, st);
+        if (n > 0) {
+            SLM_CUDA(cudaMemcpyAsync(a, W.a.get(), 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+            SLM_CUDA(cudaMemcpyAsync(root, W.f.root, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        }
+        SLM_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+slm_status slm_step_compact(int32_t n, const int32_t *root, int32_t *id, int32_t *K_host,
+                            void *stream) {
+    STEP_CHECK(n >= 0 && (n == 0 || (root && id)) && K_host);
+    return guarded(nullptr, [&] {
+        cudaStream_t st = as_stream(stream);
+        DevBuf scratch(4 * (size_t)(n > 0 ? n : 1), st);
+        *K_host = slm::compact_labels(n, root, id, scratch.as<int32_t>(), st);
+    });
+}
+
+slm_status slm_step_aggregate(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                              const int32_t *w, const int32_t *id, int32_t K,
+                              int32_t *row_ptr_out, int32_t *col_out, int32_t *w_out,
+                              int32_t *nnz_out_host, void *stream) {
+    STEP_CHECK(n >= 0 && K >= 0 && K <= (n > 0 ? n : 0) && (n == 0 || (row_ptr && col && w && id)) &&
+               row_ptr_out && nnz_out_host);
+    return guarded(nullptr, [&] {
+        cudaStream_t st = as_stream(stream);
+        DevBuf rp2, col2, w2;
+        int32_t nnz2 = slm::aggregate_graph(n, row_ptr, col, w, id, K, rp2, col2, w2, st);
+        SLM_CUDA(cudaMemcpyAsync(row_ptr_out, rp2.get(), 4 * ((size_t)K + 1), cudaMemcpyDeviceToDevice, st));
+        if (nnz2 > 0) {
+            SLM_CUDA(cudaMemcpyAsync(col_out, col2.get(), 4 * (size_t)nnz2, cudaMemcpyDeviceToDevice, st));
+            SLM_CUDA(cudaMemcpyAsync(w_out, w2.get(), 4 * (size_t)nnz2, cudaMemcpyDeviceToDevice, st));
+        }
+        SLM_CUDA(cudaStreamSynchronize(st));
+        *nnz_out_host = nnz2;
+    });
+}
+
+slm_status slm_step_modularity(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                               const int32_t *w, const int32_t *labels, double *q_host,
+                               int64_t *num_host, void *stream) {
+    STEP_CHECK(n >= 0 && (n == 0 || (row_ptr && col && w && labels)) && q_host && num_host);
+    return guarded(nullptr, [&] {
+        cudaStream_t st = as_stream(stream);
+        DevBuf s(4 * (size_t)(n > 0 ? n : 1), st);
+        long long m = slm::strengths(n, row_ptr, w, s.as<int32_t>(), st);
+        long long num = slm::modularity_num(n, row_ptr, col, w, labels, m, st);
+        *num_host = num;
+        *q_host = slm::modularity_from_num(num, m);
+    });
+}
+
+}  // extern "C"

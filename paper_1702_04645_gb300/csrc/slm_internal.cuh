@@ -1,0 +1,246 @@
+// slm_internal.cuh -- declarations shared by the CUDA translation units of the
+// Synchronised Louvain Method library (sm_103a).
+//
+// Integer conventions: node ids, strengths s_i, community totals Sigma_C and
+// every edge weight fit in int32 because m_w < 2^31; every product of two of
+// them, and every gain, is computed in int64 and is exact.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <initializer_list>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "slm.h"
+
+namespace slm {
+
+// ---------------------------------------------------------------------------
+// Errors: internal code throws slm::Error; the C ABI turns it into a status.
+// ---------------------------------------------------------------------------
+struct Error {
+    slm_status status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(slm_status st, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what, const char *file, int line);
+
+#define SLM_CUDA(call) ::slm::check_cuda((call), #call, __FILE__, __LINE__)
+#define SLM_LAUNCH_CHECK() ::slm::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+constexpr int kWarp = 32;
+constexpr int kNumSMs = 152;
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+inline int grid_for(long long n, int block, int max_blocks = 152 * 32) {
+    long long g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+// Stream-ordered device buffers (cudaMallocAsync / cudaFreeAsync).
+// ---------------------------------------------------------------------------
+class DevBuf {
+  public:
+    DevBuf() = default;
+    DevBuf(size_t bytes, cudaStream_t s) { alloc(bytes, s); }
+    ~DevBuf() { release(); }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept { swap(o); }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); swap(o); }
+        return *this;
+    }
+    void alloc(size_t bytes, cudaStream_t s);
+    // grow-only: keeps the allocation when it is already large enough
+    void ensure(size_t bytes, cudaStream_t s) {
+        if (bytes > bytes_) alloc(bytes, s);
+    }
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p_); }
+    size_t bytes() const { return bytes_; }
+    void *get() const { return p_; }
+
+  private:
+    void swap(DevBuf &o) {
+        std::swap(p_, o.p_);
+        std::swap(bytes_, o.bytes_);
+        std::swap(s_, o.s_);
+    }
+    void *p_ = nullptr;
+    size_t bytes_ = 0;
+    cudaStream_t s_ = nullptr;
+};
+
+// Small pinned host buffer for the counters read back each sweep.
+struct HostCounters {
+    long long *h = nullptr;
+    HostCounters();
+    ~HostCounters();
+};
+
+// ---------------------------------------------------------------------------
+// Device-wide primitives (k_basic.cu, k_sort.cu)
+// ---------------------------------------------------------------------------
+// Exclusive prefix sum of n int32 values (in may equal out); *total_dev (may
+// be null) receives the sum.  All partial sums must stay below 2^31.
+void exclusive_scan_i32(const int32_t *in, int32_t *out, long long n, int32_t *total_dev,
+                        cudaStream_t s);
+// Exclusive prefix sum of n int64 values.
+void exclusive_scan_i64(const long long *in, long long *out, long long n, long long *total_dev,
+                        cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key.
+// keys/vals are sorted in place (the tmp buffers must hold n entries each).
+void radix_sort_u64(unsigned long long *keys, int32_t *vals, unsigned long long *keys_tmp,
+                    int32_t *vals_tmp, long long n, int bits, cudaStream_t s);
+void radix_sort_u32(uint32_t *keys, int32_t *vals, uint32_t *keys_tmp, int32_t *vals_tmp,
+                    long long n, int bits, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Graph-level kernels (k_basic.cu)
+// ---------------------------------------------------------------------------
+// Validation of a CSR: returns a bit mask of problems (1 bad column/order,
+// 2 non-positive weight, 4 not symmetric, 8 bad row_ptr).
+int validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                 cudaStream_t s);
+// Number of the cnt entries of x outside [0, n) (host-synchronous).
+int count_out_of_range(long long cnt, const int32_t *x, int32_t n, cudaStream_t s);
+// s_i = sum_j W_ij (int32) and m_w (returned, int64).
+long long strengths(int32_t n, const int32_t *rp, const int32_t *w, int32_t *s_out,
+                    cudaStream_t s);
+// Sigma[C] = sum of s over root == C (Sigma zeroed here).
+void community_sigma(int32_t n, const int32_t *root, const int32_t *s, int32_t *sigma,
+                     cudaStream_t st);
+// id[v] = rank of root[v] among names in use; returns K (host-synchronous).
+int32_t compact_labels(int32_t n, const int32_t *root, int32_t *id, int32_t *scratch_n,
+                       cudaStream_t s);
+// comp[v] = id[comp[v]]
+void compose_labels(int32_t n0, int32_t *comp, const int32_t *id, cudaStream_t s);
+// exact modularity numerator of labels (values in [0, n)); host-synchronous.
+long long modularity_num(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                         const int32_t *labels, long long m_w, cudaStream_t s);
+double modularity_from_num(long long num, long long m_w);
+
+// ---------------------------------------------------------------------------
+// Degree buckets and the neighbourhood scans (k_scan.cu)
+// ---------------------------------------------------------------------------
+enum { kBucketEmpty = 0, kBucketG4, kBucketG8, kBucketG16, kBucketG32, kBucketWarpHash,
+       kBucketBlock, kNumBuckets };
+constexpr int kWarpHashMaxDeg = 256;
+
+struct Buckets {
+    DevBuf order;                       // int32[n]: nodes sorted by bucket (stable)
+    int32_t off[kNumBuckets + 1] = {0}; // host copy of bucket offsets
+    void build(int32_t n, const int32_t *rp, cudaStream_t s);
+};
+
+// ASSIGN: a[i] = best neighbour by m_w W_ij - s_i s_j.
+void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                  const int32_t *s, long long m_w, const Buckets &bk, int32_t *a,
+                  cudaStream_t st);
+
+// The MAXIMAL scan: best community, gain (int64) and own-community weight
+// kown (int32); counts candidates into *ncand_dev (unsigned long long).
+void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                const int32_t *s, long long m_w, const int32_t *root, const int32_t *sigma,
+                const Buckets &bk, int32_t *best, long long *gain, int32_t *kown,
+                unsigned long long *ncand_dev, cudaStream_t st);
+
+// Own-community weight only (kown) for POSITIVE's local gains; flags the
+// communities holding a node with g < 0 (flag[root] = 1) and counts them.
+void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                      const int32_t *s, long long m_w, const int32_t *root,
+                      const int32_t *sigma, const Buckets &bk, int32_t *kown,
+                      int32_t *flag, cudaStream_t st);
+
+// Local gain g(i) = m_w kown_i - s_i (Sigma_{root_i} - s_i) of Algorithm POSITIVE.
+void local_gain_nodes(int32_t n, const int32_t *s, long long m, const int32_t *root,
+                      const int32_t *sigma, const int32_t *kown, long long *g, cudaStream_t st);
+
+// Target node for the accepted nodes listed in list[0..cnt).
+void target_nodes(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt,
+                  const int32_t *rp, const int32_t *col, const int32_t *w, const int32_t *s,
+                  long long m_w, const int32_t *root, const int32_t *best, int32_t *tgt,
+                  cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Assignment-forest kernels (k_forest.cu)
+// ---------------------------------------------------------------------------
+struct Forest {
+    // per node
+    int32_t *root = nullptr;    // smallest node on the reached cycle
+    uint8_t *oncycle = nullptr; // 1 for cycle nodes
+    int32_t *entry = nullptr;   // first cycle node on the forward path (self on cycle)
+    int32_t *depth = nullptr;   // distance to entry
+    int32_t *cdist = nullptr;   // for cycle nodes: forward distance to root
+    // scratch
+    int2 *jmpA = nullptr, *jmpB = nullptr;
+};
+// Components, cycle flags, entry, depth and cycle distances of a.
+void forest_analyse(int32_t n, const int32_t *a, Forest &f, cudaStream_t st);
+
+struct BranchScratch {
+    int32_t *haschild, *active, *covered, *treeact, *commcyc;
+    long long *subS, *subWA, *subWin, *credit, *WB;
+};
+// Branch gains bg for candidates (gain > 0); counts positive ones and the
+// accepted ones, and lists the accepted nodes.
+void branch_gains(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                  const int32_t *s, long long m_w, const int32_t *a, const Forest &f,
+                  const int32_t *sigma, const int32_t *best, const long long *gain,
+                  const int32_t *kown, BranchScratch &bs, long long *bg, cudaStream_t st);
+// Acceptance draw and list of accepted nodes.
+void accept_moves(int32_t n, const long long *bg, unsigned long long seed,
+                  unsigned long long P, int32_t level, int32_t sweep, int32_t *acc_list,
+                  int32_t *acc_cnt_dev, unsigned long long *npos_dev, cudaStream_t st);
+void apply_moves(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt,
+                 const int32_t *tgt, int32_t *a, cudaStream_t st);
+
+struct PositiveScratch {
+    DevBuf flag, kown, subS, subWA, subWin, credit, TS, bestsc, bestkey, L, coff, cyc,
+        clist, pool, cnt;
+};
+// One POSITIVE round on the current forest: returns the number of flagged
+// (and therefore split) communities; a is updated in place.
+int positive_round(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                   const int32_t *s, long long m_w, int32_t *a, const Forest &f,
+                   const int32_t *sigma, const Buckets &bk, PositiveScratch &ps,
+                   cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Aggregation (k_sort.cu)
+// ---------------------------------------------------------------------------
+// Builds the aggregated CSR; returns its nnz.  Output buffers are allocated
+// by the callee (row_ptr_out K+1, col_out/w_out nnz').
+int32_t aggregate_graph(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                        const int32_t *id, int32_t K, DevBuf &rp_out, DevBuf &col_out,
+                        DevBuf &w_out, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+// splitmix64 output function (Steele, Lea, Flood 2014).
+__host__ __device__ inline unsigned long long mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ inline unsigned int accept_draw(unsigned long long seed, int level, int sweep,
+                                                    int node) {
+    unsigned long long ctr = ((unsigned long long)(unsigned)level << 48) |
+                             ((unsigned long long)(unsigned)sweep << 32) |
+                             (unsigned long long)(unsigned)node;
+    return (unsigned int)(mix64(seed ^ mix64(ctr)) >> 32);
+}
+
+}  // namespace slm

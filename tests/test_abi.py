@@ -1,0 +1,57 @@
+"""The C ABI library loads and exports every entry point that include/*.h declares.
+
+No compute call is made, so this runs without a GPU.
+"""
+import glob
+import os
+import re
+
+import pytest
+
+import paper_1702_04645_gb300 as slm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"\b(slm_\w+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    slm.build()
+    return slm.load()
+
+
+def test_headers_declare_the_boundary():
+    names = declared_functions()
+    for required in ("slm_create_graph", "slm_run", "slm_get_partition", "slm_modularity"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(set(slm.EXPORTS)) == declared_functions()
+
+
+def test_host_only_entry_points(lib):
+    o = slm.Options()
+    lib.slm_default_options(o)
+    assert (o.seed, o.accept_p32, o.max_sweeps, o.max_levels, o.flags) == (1, 1 << 31, 1000, 64, 0)
+    assert lib.slm_status_string(2) == b"matrix not symmetric"
+    # NULL handles are rejected without touching a device
+    assert lib.slm_run(None, None, None) == 1
+    assert lib.slm_num_levels(None, None) == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(slm, "LIB", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(slm, "_lib", None)
+    with pytest.raises(RuntimeError):
+        slm.load()
