@@ -1,0 +1,304 @@
+#!/usr/bin/env python3
+"""Benchmark of the Synchronised Louvain Method on GB300.
+
+Workload: the R-MAT graph of scale 20 (1,048,576 nodes, 16 * 2^20 draws with
+a=0.57 b=0.19 c=0.19 d=0.05, integer weights uniform in [1, 8], self-loops and
+duplicates merged, symmetric CSR, seed 2).  One step is one complete run of
+the method on that graph (every level: ASSIGN, COMPONENTS, POSITIVE,
+MAXIMAL/POSITIVE sweeps, compaction, AGGREGATE, composition), with the input
+already resident in HBM.
+
+Metric: local-move GTEPS = CSR entries read by the local-moving scans of the
+run (sum over all levels of sweeps * nnz) / step time.
+
+The JSON line also carries the roofline of the scan kernel (algorithmic bytes
+per scan / scan time, both measured inside the timed region with CUDA events
+on the run's stream), an end-to-end figure through the C ABI with host
+buffers, and the CPU oracle timed on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+WORKLOAD = "rmat_s20"
+WORKLOAD_DESC = ("R-MAT scale 20, 16*2^20 draws (a,b,c)=(0.57,0.19,0.19), w~U[1,8], "
+                 "merged symmetric CSR, seed 2")
+METRIC = "local-move GTEPS"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+
+
+def scan_bytes(n: int, nnz: int) -> int:
+    """Algorithmic bytes of one scan (accumulate + argmax) over a level graph:
+    col + w (8 per entry) and per node row_ptr, own name, strength, the
+    community total, best, gain (8) and own weight (4 + 4 + 4 + 4 + 4 + 8 + 4)."""
+    return 8 * nnz + 32 * n
+
+
+def load_graph():
+    return gg.cached("rmat_s20_seed2", gg.rmat, scale=20, seed=2)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+SAMPLE_SCALE = 18
+
+
+def oracle_sample():
+    """The CPU oracle as it stands on a bounded sample of the workload: one
+    complete run (every level) on the R-MAT graph of the same generator and
+    parameters at scale 18 (262,144 nodes, 1/4 of the benchmark graph).
+    Returns (GTEPS, seconds, entries scanned, description)."""
+    import oracle as O
+    g = gg.cached(f"rmat_s{SAMPLE_SCALE}_seed2", gg.rmat, scale=SAMPLE_SCALE, seed=2)
+    t0 = time.perf_counter()
+    r = O.slm(g, seed=1, P=O.P_HALF)
+    dt = time.perf_counter() - t0
+    scanned = sum(st[5] for st in r.stats)
+    desc = (f"complete oracle run (all levels) on R-MAT scale {SAMPLE_SCALE} with the same "
+            f"generator parameters (n={g.n}, nnz={g.nnz}): {scanned} entries scanned in "
+            f"{dt:.1f} s, single thread")
+    return scanned / dt / 1e9, dt, scanned, desc
+
+
+def peaks():
+    try:
+        d = json.load(open(PEAKS))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    g = load_graph()
+    for _ in range(args.warmup):
+        oracle_sample()
+    secs, scanned = 0.0, 0
+    for _ in range(args.steps):
+        v, dt, sc, sample = oracle_sample()
+        secs += dt
+        scanned += sc
+    value = scanned / secs / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "n": g.n, "nnz": g.nnz},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1702_04645_gb300 as slm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    g = load_graph()
+    G = slm.Graph(g.row_ptr, g.col, g.w)
+    run_kw = dict(seed=args.seed, accept_p32=slm.P_HALF, stream=stream.cuda_stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        G.run(**run_kw)
+    torch.cuda.synchronize(dev)
+
+    # units per step: entries read by the local-moving scans, all levels
+    levels = G.num_levels()
+    per_level = [G.stats(l) for l in range(levels)] + [G.stats(-1)]
+    units = sum(st.edges_scanned for st in per_level)
+    bytes_per_step = sum(st.sweeps * scan_bytes(st.n, st.nnz) for st in per_level)
+
+    launches0 = slm.launch_count()
+    phase_tot = {}
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            G.run(flags=slm.FLAG_TIMING, **run_kw)
+            for k, (ms, cnt) in G.timing().items():
+                a, b = phase_tot.get(k, (0.0, 0))
+                phase_tot[k] = (a + ms, b + cnt)
+        ev1.record(stream)
+        barrier()
+    launches = slm.launch_count() - launches0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = units * args.steps * world / (elapsed_ms / 1e3) / 1e9
+
+    # roofline of the scan kernel (accumulate + argmax), timed on the run's stream
+    hbm, peak_kind = peaks()
+    scan_ms, scan_cnt = phase_tot.get("scan", (0.0, 0))
+    achieved = (bytes_per_step * args.steps / 1e9) / (scan_ms / 1e3) if scan_ms > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                "kernel": "scan (accumulate + argmax), all degree buckets of one sweep",
+                "peak_source": peak_kind,
+                "launches_timed": scan_cnt,
+                "avg_launch_ms": scan_ms / scan_cnt if scan_cnt else None,
+                "bytes_per_step": bytes_per_step}
+    prof = os.path.join(ROOT, "profiles", "scan_traffic_rmat_s20.json")
+    if os.path.exists(prof):
+        try:
+            roofline["traffic"] = json.load(open(prof)).get("traffic_per_sweep_level0")
+        except Exception:
+            pass
+
+    # end to end through the C ABI with host buffers: copy in, run, read the partition
+    e2e = None
+    if not args.no_e2e:
+        e2e_ms = []
+        for _ in range(2):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            G2 = slm.Graph(g.row_ptr, g.col, g.w)
+            G2.run(**run_kw)
+            lab, _ = G2.partition(-1)
+            G2.close()
+            torch.cuda.synchronize(dev)
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        e2e_t = min(e2e_ms)
+        e2e = {"value": units / (e2e_t / 1e3) / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": int(4 * (g.n + 1) + 8 * g.nnz),
+               "d2h_bytes_per_step": int(4 * g.n), "ms_per_step": e2e_t}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, sc, desc = oracle_sample()
+        cpu = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "n": g.n, "nnz": g.nnz,
+                           "levels": levels, "scans_per_step": sum(st.sweeps for st in per_level),
+                           "units_per_step": units, "accept_p32": slm.P_HALF, "seed": args.seed,
+                           "l2": "inputs larger than L2 (CSR %.0f MB > 129 MB)" % ((8 * g.nnz + 4 * g.n) / 1e6),
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clocks,
+                "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in phase_tot.items()}}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

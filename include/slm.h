@@ -50,6 +50,7 @@ typedef enum {
 /* Option flags. */
 #define SLM_FLAG_NO_POSITIVE 1u /* skip POSITIVE (ablation; Section 3.3) */
 #define SLM_FLAG_STRICT 2u      /* sweep limit reached => SLM_ERR_NOT_CONVERGED */
+#define SLM_FLAG_TIMING 4u      /* time the phases of slm_run with CUDA events (see slm_get_timing) */
 
 typedef struct slm_graph slm_graph; /* opaque, owned by the library */
 

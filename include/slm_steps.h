@@ -111,6 +111,16 @@ slm_status slm_step_modularity(int32_t n, const int32_t *row_ptr, const int32_t 
  * rows into `rows` (host memory) and sets *len to the number of rows. */
 slm_status slm_get_trace(const slm_graph *g, int64_t *rows, int64_t cap, int64_t *len);
 
+/* Device time of the phases of the last slm_run made with SLM_FLAG_TIMING,
+ * measured with CUDA events on the run's stream: ms8[k] milliseconds over
+ * count8[k] intervals for k = 0 assign, 1 components, 2 positive rounds,
+ * 3 scan (accumulate + argmax), 4 branch gains + draw + target + write,
+ * 5 level set-up, compaction and aggregation, 6 community totals, 7 unused. */
+slm_status slm_get_timing(const slm_graph *g, double *ms8, int64_t *count8);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t slm_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,8 @@ SLM_HOST = 0
 SLM_DEVICE = 1
 FLAG_NO_POSITIVE = 1
 FLAG_STRICT = 2
+FLAG_TIMING = 4
+PHASES = ["assign", "components", "positive", "scan", "move", "level", "sigma", "unused"]
 P_HALF = 1 << 31
 P_ALWAYS = 1 << 32
 
@@ -41,7 +43,12 @@ EXPORTS = ["slm_default_options", "slm_create_graph", "slm_run", "slm_num_levels
            "slm_destroy_graph", "slm_status_string", "slm_last_error", "slm_step_strengths",
            "slm_step_assign", "slm_step_components", "slm_step_scan", "slm_step_branch_gain",
            "slm_step_maximal", "slm_step_positive", "slm_step_compact", "slm_step_aggregate",
-           "slm_step_modularity", "slm_get_trace"]
+           "slm_step_modularity", "slm_get_trace", "slm_get_timing", "slm_launch_count"]
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load().slm_launch_count())
 
 
 class SlmError(RuntimeError):
@@ -93,6 +100,8 @@ def load():
             "slm_status_string": (C.c_char_p, [C.c_int]),
             "slm_last_error": (C.c_char_p, [vp]),
             "slm_get_trace": (C.c_int, [vp, vp, i64, C.POINTER(i64)]),
+            "slm_get_timing": (C.c_int, [vp, vp, vp]),
+            "slm_launch_count": (u64, []),
             "slm_step_strengths": (C.c_int, [i32, vp, vp, vp, vp, C.POINTER(i64), vp]),
             "slm_step_assign": (C.c_int, [i32, vp, vp, vp, vp, i64, vp, vp]),
             "slm_step_components": (C.c_int, [i32, vp, vp, vp]),
@@ -249,6 +258,14 @@ class Graph:
         s = LevelStats()
         _check(load().slm_get_stats(self._h, level, C.byref(s)), self._h)
         return s
+
+    def timing(self):
+        """{phase: (milliseconds, intervals)} of the last run made with FLAG_TIMING."""
+        ms = np.zeros(8, dtype=np.float64)
+        cnt = np.zeros(8, dtype=np.int64)
+        _check(load().slm_get_timing(self._h, C.c_void_p(ms.ctypes.data),
+                                     C.c_void_p(cnt.ctypes.data)), self._h)
+        return {PHASES[k]: (float(ms[k]), int(cnt[k])) for k in range(7)}
 
     def trace(self) -> np.ndarray:
         lib = load()

@@ -2,6 +2,7 @@
 // validation, strengths (Section 2.4: s_i and m_w), community totals Sigma_C,
 // compaction of community names, partition composition (Algorithm 1,
 // C = C_t C) and the exact modularity numerator (Section 2.4, Q_w).
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 
@@ -10,6 +11,10 @@
 namespace slm {
 
 void fail(slm_status st, const std::string &msg) { throw Error{st, msg}; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(); }
 
 void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
     if (e == cudaSuccess) return;

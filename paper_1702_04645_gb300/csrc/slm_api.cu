@@ -37,11 +37,46 @@ struct slm_graph {
     DevBuf final_comp;
     std::vector<std::array<long long, 6>> trace;
     std::string err;
+    // per-phase device time of the last run (SLM_FLAG_TIMING)
+    double phase_ms[8] = {0};
+    long long phase_cnt[8] = {0};
 };
 
 namespace {
 
 thread_local std::string g_create_error;
+
+// Phases timed with CUDA events on the run's stream when SLM_FLAG_TIMING is set.
+enum Phase { kPhAssign = 0, kPhComponents, kPhPositive, kPhScan, kPhMove, kPhLevel, kPhSigma, kNumPhases };
+
+struct PhaseTimer {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    double *ms = nullptr;
+    long long *cnt = nullptr;
+    PhaseTimer(bool enable, cudaStream_t s, double *ms_, long long *cnt_) : on(enable), st(s), ms(ms_), cnt(cnt_) {
+        if (!on) return;
+        SLM_CUDA(cudaEventCreate(&a));
+        SLM_CUDA(cudaEventCreate(&b));
+    }
+    ~PhaseTimer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    void start() {
+        if (on) SLM_CUDA(cudaEventRecord(a, st));
+    }
+    void stop(int phase) {
+        if (!on) return;
+        SLM_CUDA(cudaEventRecord(b, st));
+        SLM_CUDA(cudaEventSynchronize(b));
+        float t = 0;
+        SLM_CUDA(cudaEventElapsedTime(&t, a, b));
+        ms[phase] += t;
+        cnt[phase] += 1;
+    }
+};
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -129,17 +164,22 @@ struct Work {
 
 // POSITIVE until no community holds a node with a negative local gain.
 long long positive_all(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                       const int32_t *s, long long m, Work &W, cudaStream_t st) {
+                       const int32_t *s, long long m, Work &W, cudaStream_t st,
+                       PhaseTimer *tm = nullptr) {
     long long total = 0;
     // every round splits at least one community, so n rounds always suffice
     for (long long round = 0;; round++) {
         if (round > (long long)n) slm::fail(SLM_ERR_TIMEOUT, "POSITIVE did not settle within n rounds");
+        if (tm) tm->start();
         slm::community_sigma(n, W.f.root, s, W.sigma.as<int32_t>(), st);
         int k = slm::positive_round(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f,
                                     W.sigma.as<int32_t>(), W.bk, W.ps, st);
+        if (tm) tm->stop(kPhPositive);
         if (k == 0) break;
         total += k;
+        if (tm) tm->start();
         slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
+        if (tm) tm->stop(kPhComponents);
     }
     return total;
 }
@@ -152,17 +192,25 @@ struct SweepCounts {
 SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                          const int32_t *s, long long m, Work &W, unsigned long long seed,
                          unsigned long long P, int level, int sweep, bool stop_if_no_cand,
-                         cudaStream_t st, slm::HostCounters &hc) {
+                         cudaStream_t st, slm::HostCounters &hc, PhaseTimer *tm = nullptr) {
     SweepCounts c;
     unsigned long long *ctr = W.ctr();
+    if (tm) tm->start();
     SLM_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
     slm::community_sigma(n, W.f.root, s, W.sigma.as<int32_t>(), st);
+    if (tm) tm->stop(kPhSigma);
+    if (tm) tm->start();
     slm::scan_nodes(n, rp, col, w, s, m, W.f.root, W.sigma.as<int32_t>(), W.bk,
                     W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), ctr, st);
+    if (tm) tm->stop(kPhScan);
+    if (tm) tm->start();
     SLM_CUDA(cudaMemcpyAsync(hc.h, ctr, 8, cudaMemcpyDeviceToHost, st));
     SLM_CUDA(cudaStreamSynchronize(st));
     c.cand = (long long)hc.h[0];
-    if (c.cand == 0 && stop_if_no_cand) return c;
+    if (c.cand == 0 && stop_if_no_cand) {
+        if (tm) tm->stop(kPhMove);
+        return c;
+    }
     slm::branch_gains(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
                       W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), W.bs,
                       W.bg.as<long long>(), st);
@@ -173,11 +221,15 @@ SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const
     SLM_CUDA(cudaStreamSynchronize(st));
     c.pos = (long long)hc.h[1];
     c.acc = (long long)(int32_t)(hc.h[2] & 0xffffffff);
-    if (c.pos == 0 || c.acc == 0) return c;
+    if (c.pos == 0 || c.acc == 0) {
+        if (tm) tm->stop(kPhMove);
+        return c;
+    }
     slm::target_nodes(W.acclist.as<int32_t>(), acc_cnt, (int32_t)c.acc, rp, col, w, s, m,
                       W.f.root, W.best.as<int32_t>(), W.tgt.as<int32_t>(), st);
     slm::apply_moves(W.acclist.as<int32_t>(), acc_cnt, (int32_t)c.acc, W.tgt.as<int32_t>(),
                      W.a.as<int32_t>(), st);
+    if (tm) tm->stop(kPhMove);
     return c;
 }
 
@@ -196,6 +248,9 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         SLM_LAUNCH_CHECK();
     }
     slm::HostCounters hc;
+    for (int k = 0; k < 8; k++) { g->phase_ms[k] = 0; g->phase_cnt[k] = 0; }
+    PhaseTimer tmr((opt.flags & SLM_FLAG_TIMING) != 0, st, g->phase_ms, g->phase_cnt);
+    PhaseTimer *tm = tmr.on ? &tmr : nullptr;
     // current level graph
     int32_t n = n0;
     int32_t nnz = g->nnz0;
@@ -205,18 +260,24 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
     const long long m = g->m;
     Work W;
     for (int t = 0; n > 0; t++) {
+        if (tm) tm->start();
         W.init(n, rp, st);
+        if (tm) tm->stop(kPhLevel);
         slm_level_stats stt{};
         stt.n = n;
         stt.nnz = nnz;
+        if (tm) tm->start();
         slm::assign_nodes(n, rp, col, w, s, m, W.bk, W.a.as<int32_t>(), st);
+        if (tm) tm->stop(kPhAssign);
+        if (tm) tm->start();
         slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
-        if (!(opt.flags & SLM_FLAG_NO_POSITIVE)) stt.splits += positive_all(n, rp, col, w, s, m, W, st);
+        if (tm) tm->stop(kPhComponents);
+        if (!(opt.flags & SLM_FLAG_NO_POSITIVE)) stt.splits += positive_all(n, rp, col, w, s, m, W, st, tm);
         int sweep = 0;
         int status = 2;
         for (; sweep < opt.max_sweeps; sweep++) {
             SweepCounts c = maximal_once(n, rp, col, w, s, m, W, opt.seed, opt.accept_p32, t, sweep,
-                                         true, st, hc);
+                                         true, st, hc, tm);
             stt.candidates += c.cand;
             stt.edges_scanned += nnz;
             if (c.cand == 0) {
@@ -234,8 +295,10 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
             long long spl = 0;
             stt.moves += c.acc;
             if (c.acc > 0) {
+                if (tm) tm->start();
                 slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
-                if (!(opt.flags & SLM_FLAG_NO_POSITIVE)) spl = positive_all(n, rp, col, w, s, m, W, st);
+                if (tm) tm->stop(kPhComponents);
+                if (!(opt.flags & SLM_FLAG_NO_POSITIVE)) spl = positive_all(n, rp, col, w, s, m, W, st, tm);
                 stt.splits += spl;
             }
             g->trace.push_back({t, sweep, c.cand, c.pos, c.acc, spl});
@@ -244,10 +307,12 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         stt.status = status;
         if (status == 2 && (opt.flags & SLM_FLAG_STRICT))
             slm::fail(SLM_ERR_NOT_CONVERGED, "sweep limit reached");
+        if (tm) tm->start();
         DevBuf id(4 * (size_t)n, st), scratch(4 * (size_t)n, st);
         int32_t K = slm::compact_labels(n, W.f.root, id.as<int32_t>(), scratch.as<int32_t>(), st);
         stt.n_communities = K;
         if (K == n) {
+            if (tm) tm->stop(kPhLevel);
             g->top = stt;
             break;
         }
@@ -276,6 +341,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         s = ls.as<int32_t>();
         n = K;
         nnz = nnz2;
+        if (tm) tm->stop(kPhLevel);
         if (t + 1 >= opt.max_levels) break;
     }
     SLM_CUDA(cudaStreamSynchronize(st));
@@ -465,6 +531,17 @@ slm_status slm_get_trace(const slm_graph *g, int64_t *rows, int64_t cap, int64_t
         for (int k = 0; k < 6; k++) rows[6 * r + k] = g->trace[r][k];
     return SLM_OK;
 }
+
+slm_status slm_get_timing(const slm_graph *g, double *ms8, int64_t *count8) {
+    if (!g || !ms8 || !count8) return SLM_ERR_INVALID_ARGUMENT;
+    for (int k = 0; k < 8; k++) {
+        ms8[k] = g->phase_ms[k];
+        count8[k] = g->phase_cnt[k];
+    }
+    return SLM_OK;
+}
+
+uint64_t slm_launch_count(void) { return slm::launch_count(); }
 
 void slm_destroy_graph(slm_graph *g) {
     if (!g) return;

@@ -27,10 +27,18 @@ struct Error {
 };
 
 [[noreturn]] void fail(slm_status st, const std::string &msg);
+unsigned long long launch_count();
 void check_cuda(cudaError_t e, const char *what, const char *file, int line);
 
+// Every kernel launch of the library is followed by SLM_LAUNCH_CHECK(), which
+// also counts it (the count is reported by slm_launch_count()).
+void note_launch();
 #define SLM_CUDA(call) ::slm::check_cuda((call), #call, __FILE__, __LINE__)
-#define SLM_LAUNCH_CHECK() ::slm::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+#define SLM_LAUNCH_CHECK()   \
+    do {                     \
+        ::slm::note_launch(); \
+        ::slm::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__); \
+    } while (0)
 
 constexpr int kWarp = 32;
 constexpr int kNumSMs = 152;
