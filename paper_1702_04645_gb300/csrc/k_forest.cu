@@ -12,26 +12,16 @@
 //    inner tree nodes aggregate their subtree by ancestor walks, with the
 //    weight inside the subtree credited at the lowest common ancestor of each
 //    edge's endpoints.
-//  * positive_round: one round of Algorithm POSITIVE over every community
-//    holding a node with a negative local gain: score every branch cut and
-//    every cut of two cycle assignments, keep the best per community, apply.
 #include <climits>
 
-#include "slm_internal.cuh"
+#include "forest_dev.cuh"
 
 namespace slm {
 
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-
-__device__ __forceinline__ void add64(long long *p, long long v) {
-    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
-}
-
-#define GRID_STRIDE(v, n)                                                          \
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < (n); \
-         v += (long long)gridDim.x * blockDim.x)
+#define GRID_STRIDE SLM_GRID_STRIDE
 
 // ---------------------------------------------------------------------------
 // Components
@@ -77,16 +67,6 @@ __global__ void k_dist_final(int32_t n, const int2 *D, const uint8_t *oncycle, i
         if (oncycle[v]) { entry[v] = (int)v; depth[v] = 0; cdist[v] = d.y; }
         else { entry[v] = d.x; depth[v] = d.y; cdist[v] = 0; }
     }
-}
-
-// Lowest common ancestor of two nodes with the same entry: walk up by depth.
-// Every loop is bounded by the depths, so it ends even on inconsistent input.
-__device__ __forceinline__ int lca_walk(int x, int y, const int32_t *a, const int32_t *depth) {
-    int dx = depth[x], dy = depth[y];
-    while (dx > dy) { x = a[x]; dx--; }
-    while (dy > dx) { y = a[y]; dy--; }
-    while (dx > 0 && x != y) { x = a[x]; y = a[y]; dx--; }
-    return x;
 }
 
 // ---------------------------------------------------------------------------
@@ -287,165 +267,6 @@ __global__ void k_apply(const int32_t *list, const int32_t *cnt, const int32_t *
     }
 }
 
-// ---------------------------------------------------------------------------
-// POSITIVE
-// ---------------------------------------------------------------------------
-__global__ void k_count_flags(int32_t n, const int32_t *root, const int32_t *flag, int32_t *cnt) {
-    unsigned loc = 0;
-    GRID_STRIDE(v, n) if (root[v] == v && flag[v]) loc++;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) loc += __shfl_xor_sync(FULL, loc, o);
-    if ((threadIdx.x & 31) == 0 && loc) atomicAdd(cnt, (int)loc);
-}
-
-__global__ void k_pos_walk(int32_t n, const int32_t *a, const int32_t *depth,
-                           const int32_t *root, const int32_t *flag, const int32_t *s,
-                           const int32_t *kown, long long *subS, long long *subWA,
-                           long long *TS) {
-    GRID_STRIDE(x, n) {
-        if (!flag[root[x]]) continue;
-        long long sx = s[x], kx = kown[x];
-        int y = (int)x;
-        for (int d = depth[x]; d > 0; d--) {
-            add64(&subS[y], sx);
-            add64(&subWA[y], kx);
-            y = a[y];
-        }
-        add64(&TS[y], sx);  // total of the entry's hanging tree, entry included
-    }
-}
-
-// cycle length of flagged names (0 elsewhere), and sizes of the pools
-__global__ void k_pos_cycles(int32_t n, const int32_t *a, const int32_t *root,
-                             const int32_t *flag, const int32_t *cdist, int32_t *L,
-                             long long *msize, int32_t *csize) {
-    GRID_STRIDE(r, n) {
-        int l = 0;
-        if (root[r] == r && flag[r]) l = (a[r] == r) ? 1 : cdist[a[r]] + 1;
-        L[r] = l;
-        msize[r] = l >= 2 ? (long long)l * l : 0;
-        csize[r] = l >= 2 ? l : 0;
-    }
-}
-
-__device__ __forceinline__ int cyc_index(int v, int r, int l, const int32_t *cdist) {
-    return v == r ? 0 : l - cdist[v];
-}
-
-__global__ void k_pos_cyclist(int32_t n, const uint8_t *oncycle, const int32_t *root,
-                              const int32_t *L, const int32_t *cdist, const int32_t *coff,
-                              int32_t *cyc, int32_t *clist, int32_t *ccnt) {
-    GRID_STRIDE(v, n) {
-        if (!oncycle[v]) continue;
-        int r = root[v];
-        int l = L[r];
-        if (l < 2) continue;
-        int k = cyc_index((int)v, r, l, cdist);
-        if (k >= 0 && k < l) cyc[coff[r] + k] = (int)v;
-        if (v == r) clist[atomicAdd(ccnt, 1)] = r;
-    }
-}
-
-__global__ void k_pos_edges(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                            const int32_t *a, const uint8_t *oncycle, const int32_t *entry,
-                            const int32_t *depth, const int32_t *root, const int32_t *flag,
-                            const int32_t *L, const int32_t *cdist, const long long *moff,
-                            long long *M, long long *credit) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long xx = warp; xx < n; xx += nwarps) {
-        const int x = (int)xx;
-        const int r = root[x];
-        if (!flag[r]) continue;
-        const int ex = entry[x];
-        for (int p = rp[x] + lane; p < rp[x + 1]; p += 32) {
-            int j = col[p];
-            if (j == x || root[j] != r) continue;
-            int ej = entry[j], wv = w[p];
-            if (ej == ex) {
-                int l = lca_walk(x, j, a, depth);
-                if (!oncycle[l]) add64(&credit[l], wv);
-            } else {
-                int l = L[r];
-                int kx = cyc_index(ex, r, l, cdist), kj = cyc_index(ej, r, l, cdist);
-                if (l >= 2 && kx >= 0 && kx < l && kj >= 0 && kj < l)
-                    add64(&M[moff[r] + (long long)kx * l + kj], wv);
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ unsigned long long split_key(int type, int u, int v) {
-    return ((unsigned long long)type << 62) | ((unsigned long long)(unsigned)u << 31) |
-           (unsigned long long)(unsigned)v;
-}
-
-__global__ void k_pos_branch(int32_t n, const uint8_t *oncycle, const int32_t *root,
-                             const int32_t *flag, const int32_t *sigma, long long m,
-                             const long long *subS, const long long *subWA,
-                             const long long *subWin, long long *bestsc,
-                             unsigned long long *bestkey, int pass) {
-    GRID_STRIDE(u, n) {
-        if (oncycle[u]) continue;
-        int r = root[u];
-        if (!flag[r]) continue;
-        long long sS = subS[u], sA = sigma[r];
-        long long sc = sS * (sA - sS) - m * (subWA[u] - subWin[u]);
-        if (pass == 0) atomicMax(&bestsc[r], sc);
-        else if (sc == bestsc[r]) atomicMin(&bestkey[r], split_key(0, (int)u, 0));
-    }
-}
-
-// one block per flagged community with a cycle of length >= 2; thread per p
-__global__ void k_pos_cycle(const int32_t *clist, const int32_t *ccnt, const int32_t *L,
-                            const int32_t *coff, const int32_t *cyc, const long long *moff,
-                            const long long *M, const long long *TS, const int32_t *sigma,
-                            long long m, long long *bestsc, unsigned long long *bestkey,
-                            int pass) {
-    for (int b = blockIdx.x; b < *ccnt; b += gridDim.x) {
-        const int r = clist[b];
-        const int l = L[r];
-        const int32_t *cy = cyc + coff[r];
-        const long long *Mr = M + moff[r];
-        const long long sA = sigma[r];
-        for (int p = threadIdx.x; p < l; p += blockDim.x) {
-            long long cut = 0, sV = 0;
-            for (int q = p + 1; q < l; q++) {
-                long long rowq = 0, inV = 0;
-                for (int t = 0; t < l; t++) rowq += Mr[(long long)q * l + t];
-                for (int k = p + 1; k < q; k++) inV += Mr[(long long)k * l + q];
-                cut += rowq - 2 * inV;
-                sV += TS[cy[q]];
-                long long sc = sV * (sA - sV) - m * cut;
-                int cp = cy[p], cq = cy[q];
-                int u = min(cp, cq), v = max(cp, cq);
-                if (pass == 0) atomicMax(&bestsc[r], sc);
-                else if (sc == bestsc[r]) atomicMin(&bestkey[r], split_key(1, u, v));
-            }
-        }
-    }
-}
-
-__global__ void k_pos_apply(int32_t n, const int32_t *root, const int32_t *flag,
-                            const unsigned long long *bestkey, int32_t *a) {
-    GRID_STRIDE(r, n) {
-        if (root[r] != r || !flag[r]) continue;
-        unsigned long long key = bestkey[r];
-        if (key == ~0ull) continue;  // no option recorded (cannot happen for size >= 2)
-        int type = (int)(key >> 62);
-        int u = (int)((key >> 31) & 0x7fffffffu);
-        int v = (int)(key & 0x7fffffffu);
-        if (u < n) a[u] = u;
-        if (type == 1 && v < n) a[v] = v;
-    }
-}
-
-__global__ void k_fill_i64(long long *p, long long n, long long v) { GRID_STRIDE(i, n) p[i] = v; }
-__global__ void k_fill_u64(unsigned long long *p, long long n, unsigned long long v) {
-    GRID_STRIDE(i, n) p[i] = v;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -530,91 +351,6 @@ void apply_moves(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt, c
     if (max_cnt <= 0) return;
     k_apply<<<grid_for(max_cnt, 256), 256, 0, st>>>(list, cnt_dev, tgt, a);
     SLM_LAUNCH_CHECK();
-}
-
-int positive_round(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                   const int32_t *s, long long m, int32_t *a, const Forest &f,
-                   const int32_t *sigma, const Buckets &bk, PositiveScratch &ps,
-                   cudaStream_t st) {
-    if (n <= 0) return 0;
-    const size_t N = (size_t)n;
-    const int g = grid_for(n, 256);
-    const int gw = grid_for((long long)n * 32, 256, kNumSMs * 16);
-    ps.flag.ensure(4 * N, st);
-    ps.kown.ensure(4 * N, st);
-    ps.cnt.ensure(64, st);
-    SLM_CUDA(cudaMemsetAsync(ps.flag.get(), 0, 4 * N, st));
-    SLM_CUDA(cudaMemsetAsync(ps.cnt.get(), 0, 64, st));
-    int32_t *flag = ps.flag.as<int32_t>(), *kown = ps.kown.as<int32_t>();
-    int32_t *cnt = ps.cnt.as<int32_t>();
-    own_weight_nodes(n, rp, col, w, s, m, f.root, sigma, bk, kown, flag, st);
-    k_count_flags<<<g, 256, 0, st>>>(n, f.root, flag, cnt);
-    SLM_LAUNCH_CHECK();
-    int32_t nflag = 0;
-    SLM_CUDA(cudaMemcpyAsync(&nflag, cnt, sizeof nflag, cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
-    if (nflag == 0) return 0;
-
-    for (DevBuf *b : {&ps.subS, &ps.subWA, &ps.subWin, &ps.credit, &ps.TS, &ps.bestsc, &ps.bestkey}) {
-        b->ensure(8 * N, st);
-    }
-    for (DevBuf *b : {&ps.subS, &ps.subWA, &ps.subWin, &ps.credit, &ps.TS})
-        SLM_CUDA(cudaMemsetAsync(b->get(), 0, 8 * N, st));
-    k_fill_i64<<<g, 256, 0, st>>>(ps.bestsc.as<long long>(), n, LLONG_MIN);
-    SLM_LAUNCH_CHECK();
-    k_fill_u64<<<g, 256, 0, st>>>(ps.bestkey.as<unsigned long long>(), n, ~0ull);
-    SLM_LAUNCH_CHECK();
-    long long *subS = ps.subS.as<long long>(), *subWA = ps.subWA.as<long long>(),
-              *subWin = ps.subWin.as<long long>(), *credit = ps.credit.as<long long>(),
-              *TS = ps.TS.as<long long>(), *bestsc = ps.bestsc.as<long long>();
-    unsigned long long *bestkey = ps.bestkey.as<unsigned long long>();
-
-    k_pos_walk<<<g, 256, 0, st>>>(n, a, f.depth, f.root, flag, s, kown, subS, subWA, TS);
-    SLM_LAUNCH_CHECK();
-
-    // cycles of the flagged communities: lengths, pools, ordered lists
-    ps.L.ensure(4 * N, st);
-    ps.coff.ensure(4 * (N + 1), st);
-    DevBuf moff(8 * (N + 1), st), tot(16, st);
-    int32_t *L = ps.L.as<int32_t>(), *coff = ps.coff.as<int32_t>();
-    k_pos_cycles<<<g, 256, 0, st>>>(n, a, f.root, flag, f.cdist, L, moff.as<long long>(), coff);
-    SLM_LAUNCH_CHECK();
-    exclusive_scan_i64(moff.as<long long>(), moff.as<long long>(), n, tot.as<long long>(), st);
-    exclusive_scan_i32(coff, coff, n, reinterpret_cast<int32_t *>(tot.as<long long>() + 1), st);
-    long long htot[2] = {0, 0};
-    SLM_CUDA(cudaMemcpyAsync(htot, tot.get(), 16, cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
-    const long long mtot = htot[0];
-    const int32_t ctot = (int32_t)(htot[1] & 0xffffffff);
-    ps.pool.ensure(8 * (size_t)(mtot > 0 ? mtot : 1), st);
-    ps.cyc.ensure(4 * (size_t)(ctot > 0 ? ctot : 1), st);
-    ps.clist.ensure(4 * (size_t)(ctot > 0 ? ctot : 1), st);
-    long long *M = ps.pool.as<long long>();
-    if (mtot > 0) SLM_CUDA(cudaMemsetAsync(M, 0, 8 * (size_t)mtot, st));
-    k_pos_cyclist<<<g, 256, 0, st>>>(n, f.oncycle, f.root, L, f.cdist, coff, ps.cyc.as<int32_t>(),
-                                     ps.clist.as<int32_t>(), cnt + 1);
-    SLM_LAUNCH_CHECK();
-
-    k_pos_edges<<<gw, 256, 0, st>>>(n, rp, col, w, a, f.oncycle, f.entry, f.depth, f.root, flag, L,
-                                    f.cdist, moff.as<long long>(), M, credit);
-    SLM_LAUNCH_CHECK();
-    k_walk_credit<<<g, 256, 0, st>>>(n, a, f.depth, nullptr, credit, subWin);
-    SLM_LAUNCH_CHECK();
-    const int gc = ctot > 0 ? grid_for(ctot, 1, kNumSMs * 8) : 1;
-    for (int pass = 0; pass < 2; pass++) {
-        k_pos_branch<<<g, 256, 0, st>>>(n, f.oncycle, f.root, flag, sigma, m, subS, subWA, subWin,
-                                        bestsc, bestkey, pass);
-        SLM_LAUNCH_CHECK();
-        if (ctot > 0) {
-            k_pos_cycle<<<gc, 128, 0, st>>>(ps.clist.as<int32_t>(), cnt + 1, L, coff,
-                                            ps.cyc.as<int32_t>(), moff.as<long long>(), M, TS,
-                                            sigma, m, bestsc, bestkey, pass);
-            SLM_LAUNCH_CHECK();
-        }
-    }
-    k_pos_apply<<<g, 256, 0, st>>>(n, f.root, flag, bestkey, a);
-    SLM_LAUNCH_CHECK();
-    return nflag;
 }
 
 }  // namespace slm

@@ -1,0 +1,468 @@
+// k_positive.cu -- Algorithm POSITIVE (Section 3.3) on the GPU.
+//
+// The local gain of node i is g(i) = m_w k_{i,c_i} - s_i (Sigma_{c_i} - s_i)
+// (Section 2.4 specialised to a symmetric W).  Every community holding a node
+// with g < 0 is bisected optimally and its parts are examined again, until no
+// node has a negative local gain.  The candidate bisections of a community A
+// are
+//   * a branch cut at a non-cycle node u: a(u) <- u, parts tail(u) and A\tail(u);
+//   * a cycle cut at two distinct cycle nodes u, v: a(u) <- u, a(v) <- v, each
+//     part being the nodes whose forward path reaches u (resp. v) first;
+// and splitting A into S and R changes the modularity numerator by twice
+// Sigma_S Sigma_R - m_w W(S,R).  The best value wins even when it is not
+// positive; ties prefer a branch cut, then the smaller u, then the smaller v.
+//
+// Communities are independent (Section 4.2), so every flagged community is
+// split in the same round.  A round touches only the members of the flagged
+// communities: their subtree sums (ancestor walks, with the weight inside a
+// subtree credited at the lowest common ancestor of each edge), the L x L
+// weights between the trees hanging from a cycle of length L >= 2, the best
+// split, and afterwards the members' components, totals and local gains.
+#include <climits>
+
+#include "forest_dev.cuh"
+
+namespace slm {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+#define GRID_STRIDE SLM_GRID_STRIDE
+
+__device__ __forceinline__ unsigned long long split_key(int type, int u, int v) {
+    return ((unsigned long long)type << 62) | ((unsigned long long)(unsigned)u << 31) |
+           (unsigned long long)(unsigned)v;
+}
+
+__device__ __forceinline__ int cyc_index(int v, int r, int l, const int32_t *cdist) {
+    return v == r ? 0 : l - cdist[v];
+}
+
+// ---------------------------------------------------------------------------
+// member lists
+// ---------------------------------------------------------------------------
+// mark[k] = 1 when the k-th node (list[k], or k itself when list is null) lies
+// in a flagged community
+__global__ void k_mark(long long cnt, const int32_t *list, const int32_t *root,
+                       const int32_t *flag, int32_t *mark) {
+    GRID_STRIDE(k, cnt) {
+        int v = list ? list[k] : (int)k;
+        mark[k] = flag[root[v]] ? 1 : 0;
+    }
+}
+__global__ void k_compact(long long cnt, const int32_t *list, const int32_t *root,
+                          const int32_t *flag, const int32_t *pos, int32_t *out) {
+    GRID_STRIDE(k, cnt) {
+        int v = list ? list[k] : (int)k;
+        if (flag[root[v]]) out[pos[k]] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one round
+// ---------------------------------------------------------------------------
+__global__ void k_round_init(int cnt, const int32_t *M, const int32_t *root, long long *subS,
+                             long long *subWA, long long *subWin, long long *credit,
+                             long long *TS, int32_t *rlist, int32_t *rcnt, int32_t *posr) {
+    GRID_STRIDE(k, cnt) {
+        int v = M[k];
+        subS[v] = 0;
+        subWA[v] = 0;
+        subWin[v] = 0;
+        credit[v] = 0;
+        TS[v] = 0;
+        if (root[v] == v) {
+            int q = atomicAdd(rcnt, 1);
+            rlist[q] = v;
+            posr[v] = q;
+        }
+    }
+}
+
+__global__ void k_root_init(int R, const int32_t *rlist, const int32_t *a, const int32_t *cdist,
+                            int32_t *L, long long *msz, int32_t *csz, long long *bestsc,
+                            unsigned long long *bestkey) {
+    GRID_STRIDE(q, R) {
+        int r = rlist[q];
+        int l = (a[r] == r) ? 1 : cdist[a[r]] + 1;
+        L[q] = l;
+        msz[q] = l >= 2 ? (long long)l * l : 0;
+        csz[q] = l >= 2 ? l : 0;
+        bestsc[q] = LLONG_MIN;
+        bestkey[q] = ~0ull;
+    }
+}
+
+// every member adds itself to its non-cycle ancestors (itself included) and to
+// the total of the tree hanging from its entry
+__global__ void k_walk(int cnt, const int32_t *M, const int32_t *a, const int32_t *depth,
+                       const int32_t *s, const int32_t *kown, long long *subS, long long *subWA,
+                       long long *TS) {
+    GRID_STRIDE(k, cnt) {
+        int x = M[k];
+        long long sx = s[x], kx = kown[x];
+        int y = x;
+        for (int d = depth[x]; d > 0; d--) {
+            add64(&subS[y], sx);
+            add64(&subWA[y], kx);
+            y = a[y];
+        }
+        add64(&TS[y], sx);
+    }
+}
+
+__global__ void k_cycle_order(int cnt, const int32_t *M, const uint8_t *oncycle,
+                              const int32_t *root, const int32_t *posr, const int32_t *L,
+                              const int32_t *cdist, const int32_t *coff, int32_t *cyc) {
+    GRID_STRIDE(k, cnt) {
+        int v = M[k];
+        if (!oncycle[v]) continue;
+        int r = root[v];
+        int q = posr[r];
+        int l = L[q];
+        if (l < 2) continue;
+        int c = cyc_index(v, r, l, cdist);
+        if (c >= 0 && c < l) cyc[coff[q] + c] = v;
+    }
+}
+
+// one warp per member: LCA credits inside a tree, tree-to-tree weights of the cycle
+__global__ void k_edges(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
+                        const int32_t *w, const int32_t *a, const uint8_t *oncycle,
+                        const int32_t *entry, const int32_t *depth, const int32_t *root,
+                        const int32_t *posr, const int32_t *L, const int32_t *cdist,
+                        const long long *moff, long long *Mw, long long *credit) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = warp; k < cnt; k += nwarps) {
+        const int x = M[k];
+        const int r = root[x];
+        const int ex = entry[x];
+        const int q = posr[r];
+        for (int p = rp[x] + lane; p < rp[x + 1]; p += 32) {
+            int j = col[p];
+            if (j == x || root[j] != r) continue;
+            int ej = entry[j], wv = w[p];
+            if (ej == ex) {
+                int l = lca_walk(x, j, a, depth);
+                if (!oncycle[l]) add64(&credit[l], wv);
+            } else {
+                int l = L[q];
+                int kx = cyc_index(ex, r, l, cdist), kj = cyc_index(ej, r, l, cdist);
+                if (l >= 2 && kx >= 0 && kx < l && kj >= 0 && kj < l)
+                    add64(&Mw[moff[q] + (long long)kx * l + kj], wv);
+            }
+        }
+    }
+}
+
+__global__ void k_credit(int cnt, const int32_t *M, const int32_t *a, const int32_t *depth,
+                         const long long *credit, long long *subWin) {
+    GRID_STRIDE(k, cnt) {
+        int x = M[k];
+        long long c = credit[x];
+        if (c == 0) continue;
+        int y = x;
+        for (int d = depth[x]; d > 0; d--) {
+            add64(&subWin[y], c);
+            y = a[y];
+        }
+    }
+}
+
+__global__ void k_branch(int cnt, const int32_t *M, const uint8_t *oncycle, const int32_t *root,
+                         const int32_t *posr, const int32_t *sigma, long long m,
+                         const long long *subS, const long long *subWA, const long long *subWin,
+                         long long *bestsc, unsigned long long *bestkey, int pass) {
+    GRID_STRIDE(k, cnt) {
+        int u = M[k];
+        if (oncycle[u]) continue;
+        int r = root[u];
+        int q = posr[r];
+        long long sS = subS[u], sA = sigma[r];
+        long long sc = sS * (sA - sS) - m * (subWA[u] - subWin[u]);
+        if (pass == 0) atomicMax(&bestsc[q], sc);
+        else if (sc == bestsc[q]) atomicMin(&bestkey[q], split_key(0, u, 0));
+    }
+}
+
+// one block per community with a cycle of length >= 2; one thread per p, the
+// part V = trees (p, q] grows with q: W(V+q, U-q) = W(V,U) + row(q) - 2 W(V,q)
+__global__ void k_cycle(int R, const int32_t *rlist, const int32_t *L, const int32_t *coff,
+                        const int32_t *cyc, const long long *moff, const long long *Mw,
+                        const long long *TS, const int32_t *sigma, long long m, int32_t n,
+                        long long *bestsc, unsigned long long *bestkey, int pass) {
+    for (int q0 = blockIdx.x; q0 < R; q0 += gridDim.x) {
+        const int l = L[q0];
+        if (l < 2) continue;
+        const int r = rlist[q0];
+        const int32_t *cy = cyc + coff[q0];
+        const long long *Mr = Mw + moff[q0];
+        const long long sA = sigma[r];
+        for (int p = threadIdx.x; p < l; p += blockDim.x) {
+            long long cut = 0, sV = 0;
+            for (int q = p + 1; q < l; q++) {
+                long long rowq = 0, inV = 0;
+                for (int t = 0; t < l; t++) rowq += Mr[(long long)q * l + t];
+                for (int k = p + 1; k < q; k++) inV += Mr[(long long)k * l + q];
+                int cp = cy[p], cq = cy[q];
+                if (cp < 0 || cp >= n || cq < 0 || cq >= n) return;  // unfilled slot: skip the community
+                cut += rowq - 2 * inV;
+                sV += TS[cq];
+                long long sc = sV * (sA - sV) - m * cut;
+                int u = min(cp, cq), v = max(cp, cq);
+                if (pass == 0) atomicMax(&bestsc[q0], sc);
+                else if (sc == bestsc[q0]) atomicMin(&bestkey[q0], split_key(1, u, v));
+            }
+        }
+    }
+}
+
+__global__ void k_apply_split(int R, const int32_t *rlist, const unsigned long long *bestkey,
+                              int32_t n, int32_t *a) {
+    GRID_STRIDE(q, R) {
+        unsigned long long key = bestkey[q];
+        if (key == ~0ull) continue;  // no option recorded (cannot happen for size >= 2)
+        int type = (int)(key >> 62);
+        int u = (int)((key >> 31) & 0x7fffffffu);
+        int v = (int)(key & 0x7fffffffu);
+        if (u < n) a[u] = u;
+        if (type == 1 && v < n) a[v] = v;
+    }
+}
+
+// components of the members again: their forward paths stay inside the
+// member set, so pointer jumping over the members alone is exact
+__global__ void k_jinit(int cnt, const int32_t *M, const int32_t *a, int2 *J, uint8_t *oncycle) {
+    GRID_STRIDE(k, cnt) {
+        int v = M[k];
+        J[v] = make_int2(a[v], v);
+        oncycle[v] = 0;
+    }
+}
+__global__ void k_jround(int cnt, const int32_t *M, const int2 *in, int2 *out) {
+    GRID_STRIDE(k, cnt) {
+        int v = M[k];
+        int2 x = in[v];
+        int2 y = in[x.x];
+        out[v] = make_int2(y.x, min(x.y, y.y));
+    }
+}
+__global__ void k_jfinal(int cnt, const int32_t *M, const int2 *J, int32_t *root, uint8_t *oncycle) {
+    GRID_STRIDE(k, cnt) {
+        int v = M[k];
+        int c = J[v].x;
+        root[v] = J[c].y;
+        oncycle[c] = 1;
+    }
+}
+__global__ void k_dinit(int cnt, const int32_t *M, const int32_t *a, const int32_t *root,
+                        const uint8_t *oncycle, int2 *D) {
+    GRID_STRIDE(k, cnt) {
+        int v = M[k];
+        if (oncycle[v] && root[v] == v) D[v] = make_int2(v, 0);
+        else D[v] = make_int2(a[v], 1);
+    }
+}
+__global__ void k_dround(int cnt, const int32_t *M, const int2 *in, int2 *out,
+                         const uint8_t *oncycle) {
+    GRID_STRIDE(k, cnt) {
+        int v = M[k];
+        int2 x = in[v];
+        if (!oncycle[v] && oncycle[x.x]) { out[v] = x; continue; }
+        int2 y = in[x.x];
+        out[v] = make_int2(y.x, x.y + y.y);
+    }
+}
+__global__ void k_dfinal(int cnt, const int32_t *M, const int2 *D, const uint8_t *oncycle,
+                         int32_t *entry, int32_t *depth, int32_t *cdist, int32_t *sigma,
+                         int32_t *flag) {
+    GRID_STRIDE(k, cnt) {
+        int v = M[k];
+        int2 d = D[v];
+        if (oncycle[v]) { entry[v] = v; depth[v] = 0; cdist[v] = d.y; }
+        else { entry[v] = d.x; depth[v] = d.y; cdist[v] = 0; }
+        sigma[v] = 0;  // the names in use inside the member set are members
+        flag[v] = 0;
+    }
+}
+__global__ void k_sigma_members(int cnt, const int32_t *M, const int32_t *root, const int32_t *s,
+                                int32_t *sigma) {
+    GRID_STRIDE(k, cnt) {
+        int v = M[k];
+        if (s[v]) atomicAdd(&sigma[root[v]], s[v]);
+    }
+}
+// one warp per member: own-community weight and local gain
+__global__ void k_own_members(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
+                              const int32_t *w, const int32_t *s, long long m,
+                              const int32_t *root, const int32_t *sigma, int32_t *kown,
+                              int32_t *flag) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = warp; k < cnt; k += nwarps) {
+        int i = M[k];
+        int ci = root[i];
+        long long own = 0;
+        for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+            int j = col[p];
+            if (j != i && root[j] == ci) own += w[p];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
+        if (lane == 0) {
+            kown[i] = (int32_t)own;
+            long long si = s[i];
+            if (m * own - si * ((long long)sigma[ci] - si) < 0) flag[ci] = 1;
+        }
+    }
+}
+
+}  // namespace
+
+// Member list of the flagged communities: from all nodes (list == nullptr) or
+// from a previous list; returns its length (host-synchronous).
+static int32_t compact_members(long long cnt, const int32_t *list, const int32_t *root,
+                               const int32_t *flag, int32_t *out, DevBuf &mark, DevBuf &tot,
+                               cudaStream_t st) {
+    if (cnt <= 0) return 0;
+    mark.ensure(4 * (size_t)cnt, st);
+    const int g = grid_for(cnt, 256);
+    k_mark<<<g, 256, 0, st>>>(cnt, list, root, flag, mark.as<int32_t>());
+    SLM_LAUNCH_CHECK();
+    exclusive_scan_i32(mark.as<int32_t>(), mark.as<int32_t>(), cnt, tot.as<int32_t>(), st);
+    k_compact<<<g, 256, 0, st>>>(cnt, list, root, flag, mark.as<int32_t>(), out);
+    SLM_LAUNCH_CHECK();
+    int32_t h = 0;
+    SLM_CUDA(cudaMemcpyAsync(&h, tot.get(), sizeof h, cudaMemcpyDeviceToHost, st));
+    SLM_CUDA(cudaStreamSynchronize(st));
+    return h;
+}
+
+long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                           const int32_t *s, long long m, int32_t *a, Forest &f, int32_t *sigma,
+                           const Buckets &bk, PositiveScratch &ps, cudaStream_t st,
+                           long long *rounds_out) {
+    if (rounds_out) *rounds_out = 0;
+    if (n <= 0) return 0;
+    const size_t N = (size_t)n;
+    for (DevBuf *b : {&ps.flag, &ps.kown, &ps.listA, &ps.listB, &ps.rlist, &ps.posr, &ps.L, &ps.coff})
+        b->ensure(4 * (N + 1), st);
+    for (DevBuf *b : {&ps.subS, &ps.subWA, &ps.subWin, &ps.credit, &ps.TS, &ps.msz, &ps.bestsc,
+                      &ps.bestkey})
+        b->ensure(8 * (N + 1), st);
+    ps.cnt.ensure(64, st);
+    int32_t *flag = ps.flag.as<int32_t>(), *kown = ps.kown.as<int32_t>();
+    int32_t *rcnt = ps.cnt.as<int32_t>();
+
+    // local gains of every node for the current forest
+    community_sigma(n, f.root, s, sigma, st);
+    SLM_CUDA(cudaMemsetAsync(flag, 0, 4 * N, st));
+    own_weight_nodes(n, rp, col, w, s, m, f.root, sigma, bk, kown, flag, st);
+    int32_t *M = ps.listA.as<int32_t>(), *M2 = ps.listB.as<int32_t>();
+    int32_t cnt = compact_members(n, nullptr, f.root, flag, M, ps.mark, ps.tot, st);
+
+    long long splits = 0, rounds = 0;
+    long long *subS = ps.subS.as<long long>(), *subWA = ps.subWA.as<long long>(),
+              *subWin = ps.subWin.as<long long>(), *credit = ps.credit.as<long long>(),
+              *TS = ps.TS.as<long long>(), *msz = ps.msz.as<long long>(),
+              *bestsc = ps.bestsc.as<long long>();
+    unsigned long long *bestkey = ps.bestkey.as<unsigned long long>();
+    int32_t *rlist = ps.rlist.as<int32_t>(), *posr = ps.posr.as<int32_t>(), *L = ps.L.as<int32_t>(),
+            *coff = ps.coff.as<int32_t>();
+    while (cnt > 0) {
+        // every round splits at least one community, so n rounds always suffice
+        if (++rounds > (long long)n) fail(SLM_ERR_TIMEOUT, "POSITIVE did not settle within n rounds");
+        const int gm = grid_for(cnt, 256);
+        const int gmw = grid_for((long long)cnt * 32, 256, kNumSMs * 16);
+        SLM_CUDA(cudaMemsetAsync(rcnt, 0, 64, st));
+        k_round_init<<<gm, 256, 0, st>>>(cnt, M, f.root, subS, subWA, subWin, credit, TS, rlist,
+                                         rcnt, posr);
+        SLM_LAUNCH_CHECK();
+        int32_t R = 0;
+        SLM_CUDA(cudaMemcpyAsync(&R, rcnt, sizeof R, cudaMemcpyDeviceToHost, st));
+        SLM_CUDA(cudaStreamSynchronize(st));
+        const int gr = grid_for(R, 256);
+        k_root_init<<<gr, 256, 0, st>>>(R, rlist, a, f.cdist, L, msz, coff, bestsc, bestkey);
+        SLM_LAUNCH_CHECK();
+        // pools for the cycle orders and the L x L tree weights
+        DevBuf tot2(16, st);
+        SLM_CUDA(cudaMemsetAsync(tot2.get(), 0, 16, st));
+        exclusive_scan_i64(msz, msz, R, tot2.as<long long>(), st);
+        exclusive_scan_i32(coff, coff, R, reinterpret_cast<int32_t *>(tot2.as<long long>() + 1), st);
+        long long ht[2] = {0, 0};
+        SLM_CUDA(cudaMemcpyAsync(ht, tot2.get(), 16, cudaMemcpyDeviceToHost, st));
+        SLM_CUDA(cudaStreamSynchronize(st));
+        const long long mtot = ht[0];
+        const long long ctot = ht[1] & 0xffffffffLL;
+        ps.pool.ensure(8 * (size_t)(mtot > 0 ? mtot : 1), st);
+        ps.cyc.ensure(4 * (size_t)(ctot > 0 ? ctot : 1), st);
+        long long *Mw = ps.pool.as<long long>();
+        if (mtot > 0) SLM_CUDA(cudaMemsetAsync(Mw, 0, 8 * (size_t)mtot, st));
+        if (ctot > 0) SLM_CUDA(cudaMemsetAsync(ps.cyc.get(), 0xff, 4 * (size_t)ctot, st));
+
+        k_walk<<<gm, 256, 0, st>>>(cnt, M, a, f.depth, s, kown, subS, subWA, TS);
+        SLM_LAUNCH_CHECK();
+        if (ctot > 0) {
+            k_cycle_order<<<gm, 256, 0, st>>>(cnt, M, f.oncycle, f.root, posr, L, f.cdist, coff,
+                                              ps.cyc.as<int32_t>());
+            SLM_LAUNCH_CHECK();
+        }
+        k_edges<<<gmw, 256, 0, st>>>(cnt, M, rp, col, w, a, f.oncycle, f.entry, f.depth, f.root,
+                                     posr, L, f.cdist, msz, Mw, credit);
+        SLM_LAUNCH_CHECK();
+        k_credit<<<gm, 256, 0, st>>>(cnt, M, a, f.depth, credit, subWin);
+        SLM_LAUNCH_CHECK();
+        for (int pass = 0; pass < 2; pass++) {
+            k_branch<<<gm, 256, 0, st>>>(cnt, M, f.oncycle, f.root, posr, sigma, m, subS, subWA,
+                                         subWin, bestsc, bestkey, pass);
+            SLM_LAUNCH_CHECK();
+            if (ctot > 0) {
+                k_cycle<<<grid_for(R, 1, kNumSMs * 8), 128, 0, st>>>(
+                    R, rlist, L, coff, ps.cyc.as<int32_t>(), msz, Mw, TS, sigma, m, n, bestsc,
+                    bestkey, pass);
+                SLM_LAUNCH_CHECK();
+            }
+        }
+        k_apply_split<<<gr, 256, 0, st>>>(R, rlist, bestkey, n, a);
+        SLM_LAUNCH_CHECK();
+        splits += R;
+
+        // components, totals and local gains of the members after the splits
+        int K = 0;
+        while ((1LL << K) < (long long)cnt) K++;
+        k_jinit<<<gm, 256, 0, st>>>(cnt, M, a, f.jmpA, f.oncycle);
+        SLM_LAUNCH_CHECK();
+        int2 *cur = f.jmpA, *nxt = f.jmpB;
+        for (int k = 0; k < K; k++) {
+            k_jround<<<gm, 256, 0, st>>>(cnt, M, cur, nxt);
+            SLM_LAUNCH_CHECK();
+            std::swap(cur, nxt);
+        }
+        k_jfinal<<<gm, 256, 0, st>>>(cnt, M, cur, f.root, f.oncycle);
+        SLM_LAUNCH_CHECK();
+        k_dinit<<<gm, 256, 0, st>>>(cnt, M, a, f.root, f.oncycle, f.jmpA);
+        SLM_LAUNCH_CHECK();
+        cur = f.jmpA;
+        nxt = f.jmpB;
+        for (int k = 0; k < K; k++) {
+            k_dround<<<gm, 256, 0, st>>>(cnt, M, cur, nxt, f.oncycle);
+            SLM_LAUNCH_CHECK();
+            std::swap(cur, nxt);
+        }
+        k_dfinal<<<gm, 256, 0, st>>>(cnt, M, cur, f.oncycle, f.entry, f.depth, f.cdist, sigma, flag);
+        SLM_LAUNCH_CHECK();
+        k_sigma_members<<<gm, 256, 0, st>>>(cnt, M, f.root, s, sigma);
+        SLM_LAUNCH_CHECK();
+        k_own_members<<<gmw, 256, 0, st>>>(cnt, M, rp, col, w, s, m, f.root, sigma, kown, flag);
+        SLM_LAUNCH_CHECK();
+        cnt = compact_members(cnt, M, f.root, flag, M2, ps.mark, ps.tot, st);
+        std::swap(M, M2);
+    }
+    if (rounds_out) *rounds_out = rounds;
+    return splits;
+}
+
+}  // namespace slm

@@ -166,22 +166,12 @@ struct Work {
 long long positive_all(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                        const int32_t *s, long long m, Work &W, cudaStream_t st,
                        PhaseTimer *tm = nullptr) {
-    long long total = 0;
-    // every round splits at least one community, so n rounds always suffice
-    for (long long round = 0;; round++) {
-        if (round > (long long)n) slm::fail(SLM_ERR_TIMEOUT, "POSITIVE did not settle within n rounds");
-        if (tm) tm->start();
-        slm::community_sigma(n, W.f.root, s, W.sigma.as<int32_t>(), st);
-        int k = slm::positive_round(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f,
-                                    W.sigma.as<int32_t>(), W.bk, W.ps, st);
-        if (tm) tm->stop(kPhPositive);
-        if (k == 0) break;
-        total += k;
-        if (tm) tm->start();
-        slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
-        if (tm) tm->stop(kPhComponents);
-    }
-    return total;
+    if (tm) tm->start();
+    long long rounds = 0;
+    long long splits = slm::positive_correct(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f,
+                                             W.sigma.as<int32_t>(), W.bk, W.ps, st, &rounds);
+    if (tm) tm->stop(kPhPositive);
+    return splits;
 }
 
 struct SweepCounts {

@@ -213,15 +213,17 @@ void apply_moves(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt,
                  const int32_t *tgt, int32_t *a, cudaStream_t st);
 
 struct PositiveScratch {
-    DevBuf flag, kown, subS, subWA, subWin, credit, TS, bestsc, bestkey, L, coff, cyc,
-        clist, pool, cnt;
+    DevBuf flag, kown, listA, listB, rlist, posr, L, coff, subS, subWA, subWin, credit, TS, msz,
+        bestsc, bestkey, pool, cyc, cnt, mark, tot;
 };
-// One POSITIVE round on the current forest: returns the number of flagged
-// (and therefore split) communities; a is updated in place.
-int positive_round(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                   const int32_t *s, long long m_w, int32_t *a, const Forest &f,
-                   const int32_t *sigma, const Buckets &bk, PositiveScratch &ps,
-                   cudaStream_t st);
+// Algorithm POSITIVE until no node has a negative local gain.  a and the
+// forest f are updated in place (only the members of split communities are
+// recomputed); sigma is used as scratch.  Returns the number of splits and,
+// in *rounds_out, the number of rounds.
+long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                           const int32_t *s, long long m, int32_t *a, Forest &f, int32_t *sigma,
+                           const Buckets &bk, PositiveScratch &ps, cudaStream_t st,
+                           long long *rounds_out);
 
 // ---------------------------------------------------------------------------
 // Aggregation (k_sort.cu)
