@@ -354,6 +354,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
                       &ps.bestkey})
         b->ensure(8 * (N + 1), st);
     ps.cnt.ensure(64, st);
+    ps.tot.ensure(16, st);
     int32_t *flag = ps.flag.as<int32_t>(), *kown = ps.kown.as<int32_t>();
     int32_t *rcnt = ps.cnt.as<int32_t>();
 
