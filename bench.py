@@ -293,7 +293,11 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks,
-                "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in phase_tot.items()}}
+                "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in phase_tot.items()
+                                       if k != "positive_rounds"},
+                "positive_per_step": {
+                    "rounds": phase_tot.get("positive_rounds", (0, 0))[1] / args.steps,
+                    "member_visits": phase_tot.get("positive_rounds", (0, 0))[0] / args.steps}}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -113,9 +113,11 @@ slm_status slm_get_trace(const slm_graph *g, int64_t *rows, int64_t cap, int64_t
 
 /* Device time of the phases of the last slm_run made with SLM_FLAG_TIMING,
  * measured with CUDA events on the run's stream: ms8[k] milliseconds over
- * count8[k] intervals for k = 0 assign, 1 components, 2 positive rounds,
- * 3 scan (accumulate + argmax), 4 branch gains + draw + target + write,
- * 5 level set-up, compaction and aggregation, 6 community totals, 7 unused. */
+ * count8[k] intervals for k = 0 assign, 1 components, 2 POSITIVE, 3 scan
+ * (accumulate + argmax), 4 branch gains + draw + target + write, 5 level
+ * set-up, compaction and aggregation, 6 community totals.  Slot 7 is not a
+ * time: count8[7] is the number of POSITIVE rounds and ms8[7] the member
+ * visits summed over those rounds. */
 slm_status slm_get_timing(const slm_graph *g, double *ms8, int64_t *count8);
 
 /* Number of kernels this library has launched in the process so far. */

@@ -28,7 +28,8 @@ SLM_DEVICE = 1
 FLAG_NO_POSITIVE = 1
 FLAG_STRICT = 2
 FLAG_TIMING = 4
-PHASES = ["assign", "components", "positive", "scan", "move", "level", "sigma", "unused"]
+PHASES = ["assign", "components", "positive", "scan", "move", "level", "sigma",
+          "positive_rounds"]
 P_HALF = 1 << 31
 P_ALWAYS = 1 << 32
 
@@ -265,7 +266,7 @@ class Graph:
         cnt = np.zeros(8, dtype=np.int64)
         _check(load().slm_get_timing(self._h, C.c_void_p(ms.ctypes.data),
                                      C.c_void_p(cnt.ctypes.data)), self._h)
-        return {PHASES[k]: (float(ms[k]), int(cnt[k])) for k in range(7)}
+        return {PHASES[k]: (float(ms[k]), int(cnt[k])) for k in range(8)}
 
     def trace(self) -> np.ndarray:
         lib = load()

@@ -344,8 +344,9 @@ static int32_t compact_members(long long cnt, const int32_t *list, const int32_t
 long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                            const int32_t *s, long long m, int32_t *a, Forest &f, int32_t *sigma,
                            const Buckets &bk, PositiveScratch &ps, cudaStream_t st,
-                           long long *rounds_out) {
+                           long long *rounds_out, long long *visits_out) {
     if (rounds_out) *rounds_out = 0;
+    if (visits_out) *visits_out = 0;
     if (n <= 0) return 0;
     const size_t N = (size_t)n;
     for (DevBuf *b : {&ps.flag, &ps.kown, &ps.listA, &ps.listB, &ps.rlist, &ps.posr, &ps.L, &ps.coff})
@@ -365,7 +366,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     int32_t *M = ps.listA.as<int32_t>(), *M2 = ps.listB.as<int32_t>();
     int32_t cnt = compact_members(n, nullptr, f.root, flag, M, ps.mark, ps.tot, st);
 
-    long long splits = 0, rounds = 0;
+    long long splits = 0, rounds = 0, visits = 0;
     long long *subS = ps.subS.as<long long>(), *subWA = ps.subWA.as<long long>(),
               *subWin = ps.subWin.as<long long>(), *credit = ps.credit.as<long long>(),
               *TS = ps.TS.as<long long>(), *msz = ps.msz.as<long long>(),
@@ -376,6 +377,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     while (cnt > 0) {
         // every round splits at least one community, so n rounds always suffice
         if (++rounds > (long long)n) fail(SLM_ERR_TIMEOUT, "POSITIVE did not settle within n rounds");
+        visits += cnt;
         const int gm = grid_for(cnt, 256);
         const int gmw = grid_for((long long)cnt * 32, 256, kNumSMs * 16);
         SLM_CUDA(cudaMemsetAsync(rcnt, 0, 64, st));
@@ -463,6 +465,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
         std::swap(M, M2);
     }
     if (rounds_out) *rounds_out = rounds;
+    if (visits_out) *visits_out = visits;
     return splits;
 }
 

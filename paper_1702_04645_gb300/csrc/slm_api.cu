@@ -47,7 +47,8 @@ namespace {
 thread_local std::string g_create_error;
 
 // Phases timed with CUDA events on the run's stream when SLM_FLAG_TIMING is set.
-enum Phase { kPhAssign = 0, kPhComponents, kPhPositive, kPhScan, kPhMove, kPhLevel, kPhSigma, kNumPhases };
+enum Phase { kPhAssign = 0, kPhComponents, kPhPositive, kPhScan, kPhMove, kPhLevel, kPhSigma,
+             kPhPosRounds, kNumPhases };
 
 struct PhaseTimer {
     bool on = false;
@@ -167,10 +168,15 @@ long long positive_all(int32_t n, const int32_t *rp, const int32_t *col, const i
                        const int32_t *s, long long m, Work &W, cudaStream_t st,
                        PhaseTimer *tm = nullptr) {
     if (tm) tm->start();
-    long long rounds = 0;
+    long long rounds = 0, visits = 0;
     long long splits = slm::positive_correct(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f,
-                                             W.sigma.as<int32_t>(), W.bk, W.ps, st, &rounds);
-    if (tm) tm->stop(kPhPositive);
+                                             W.sigma.as<int32_t>(), W.bk, W.ps, st, &rounds,
+                                             &visits);
+    if (tm) {
+        tm->stop(kPhPositive);
+        tm->ms[kPhPosRounds] += (double)visits;
+        tm->cnt[kPhPosRounds] += rounds;
+    }
     return splits;
 }
 

@@ -218,12 +218,13 @@ struct PositiveScratch {
 };
 // Algorithm POSITIVE until no node has a negative local gain.  a and the
 // forest f are updated in place (only the members of split communities are
-// recomputed); sigma is used as scratch.  Returns the number of splits and,
-// in *rounds_out, the number of rounds.
+// recomputed); sigma is used as scratch.  Returns the number of splits;
+// *rounds_out gets the number of rounds and *visits_out the member visits
+// summed over the rounds.
 long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                            const int32_t *s, long long m, int32_t *a, Forest &f, int32_t *sigma,
                            const Buckets &bk, PositiveScratch &ps, cudaStream_t st,
-                           long long *rounds_out);
+                           long long *rounds_out, long long *visits_out);
 
 // ---------------------------------------------------------------------------
 // Aggregation (k_sort.cu)
