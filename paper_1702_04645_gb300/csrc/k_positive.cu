@@ -26,7 +26,6 @@ namespace slm {
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
 #define GRID_STRIDE SLM_GRID_STRIDE
 
 __device__ __forceinline__ unsigned long long split_key(int type, int u, int v) {
@@ -61,11 +60,14 @@ __global__ void k_compact(long long cnt, const int32_t *list, const int32_t *roo
 // ---------------------------------------------------------------------------
 // one round
 // ---------------------------------------------------------------------------
-__global__ void k_round_init(int cnt, const int32_t *M, const int32_t *root, long long *subS,
-                             long long *subWA, long long *subWin, long long *credit,
-                             long long *TS, int32_t *rlist, int32_t *rcnt, int32_t *posr) {
+__global__ void k_round_init(int cnt, const int32_t *M, const int32_t *rp, const int32_t *root,
+                             long long *subS, long long *subWA, long long *subWin,
+                             long long *credit, long long *TS, int32_t *rlist, int32_t *rcnt,
+                             int32_t *posr, int32_t *degm, long long *kacc) {
     GRID_STRIDE(k, cnt) {
         int v = M[k];
+        degm[k] = rp[v + 1] - rp[v];
+        kacc[k] = 0;
         subS[v] = 0;
         subWA[v] = 0;
         subWin[v] = 0;
@@ -79,10 +81,16 @@ __global__ void k_round_init(int cnt, const int32_t *M, const int32_t *root, lon
     }
 }
 
-__global__ void k_root_init(int R, const int32_t *rlist, const int32_t *a, const int32_t *cdist,
-                            int32_t *L, long long *msz, int32_t *csz, long long *bestsc,
-                            unsigned long long *bestkey) {
-    GRID_STRIDE(q, R) {
+__global__ void k_root_init(int cnt, const int32_t *Rdev, const int32_t *rlist, const int32_t *a,
+                            const int32_t *cdist, int32_t *L, long long *msz, int32_t *csz,
+                            long long *bestsc, unsigned long long *bestkey) {
+    const int R = *Rdev;
+    GRID_STRIDE(q, cnt) {
+        if (q >= R) {  // padding so that the offsets can be scanned over cnt entries
+            msz[q] = 0;
+            csz[q] = 0;
+            continue;
+        }
         int r = rlist[q];
         int l = (a[r] == r) ? 1 : cdist[a[r]] + 1;
         L[q] = l;
@@ -126,33 +134,43 @@ __global__ void k_cycle_order(int cnt, const int32_t *M, const uint8_t *oncycle,
     }
 }
 
-// one warp per member: LCA credits inside a tree, tree-to-tree weights of the cycle
-__global__ void k_edges(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
-                        const int32_t *w, const int32_t *a, const uint8_t *oncycle,
-                        const int32_t *entry, const int32_t *depth, const int32_t *root,
-                        const int32_t *posr, const int32_t *L, const int32_t *cdist,
-                        const long long *moff, long long *Mw, long long *credit) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long k = warp; k < cnt; k += nwarps) {
+// member owning edge slot e of the members' concatenated rows
+__device__ __forceinline__ int owner_of(long long e, const int32_t *epref, int cnt) {
+    int lo = 0, hi = cnt - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if ((long long)epref[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// one thread per edge of a member: LCA credits inside a tree, tree-to-tree
+// weights of the cycle
+__global__ void k_edges(int cnt, const int32_t *M, const int32_t *epref, const int32_t *Edev,
+                        const int32_t *rp, const int32_t *col, const int32_t *w, const int32_t *a,
+                        const uint8_t *oncycle, const int32_t *entry, const int32_t *depth,
+                        const int32_t *root, const int32_t *posr, const int32_t *L,
+                        const int32_t *cdist, const long long *moff, long long *Mw,
+                        long long *credit) {
+    const long long E = *Edev;
+    GRID_STRIDE(e, E) {
+        int k = owner_of(e, epref, cnt);
         const int x = M[k];
+        const int p = rp[x] + (int)(e - epref[k]);
+        const int j = col[p];
         const int r = root[x];
-        const int ex = entry[x];
-        const int q = posr[r];
-        for (int p = rp[x] + lane; p < rp[x + 1]; p += 32) {
-            int j = col[p];
-            if (j == x || root[j] != r) continue;
-            int ej = entry[j], wv = w[p];
-            if (ej == ex) {
-                int l = lca_walk(x, j, a, depth);
-                if (!oncycle[l]) add64(&credit[l], wv);
-            } else {
-                int l = L[q];
-                int kx = cyc_index(ex, r, l, cdist), kj = cyc_index(ej, r, l, cdist);
-                if (l >= 2 && kx >= 0 && kx < l && kj >= 0 && kj < l)
-                    add64(&Mw[moff[q] + (long long)kx * l + kj], wv);
-            }
+        if (j == x || root[j] != r) continue;
+        const int ex = entry[x], ej = entry[j], wv = w[p];
+        if (ej == ex) {
+            int l = lca_walk(x, j, a, depth);
+            if (!oncycle[l]) add64(&credit[l], wv);
+        } else {
+            const int q = posr[r];
+            int l = L[q];
+            int kx = cyc_index(ex, r, l, cdist), kj = cyc_index(ej, r, l, cdist);
+            if (l >= 2 && kx >= 0 && kx < l && kj >= 0 && kj < l)
+                add64(&Mw[moff[q] + (long long)kx * l + kj], wv);
         }
     }
 }
@@ -189,10 +207,11 @@ __global__ void k_branch(int cnt, const int32_t *M, const uint8_t *oncycle, cons
 
 // one block per community with a cycle of length >= 2; one thread per p, the
 // part V = trees (p, q] grows with q: W(V+q, U-q) = W(V,U) + row(q) - 2 W(V,q)
-__global__ void k_cycle(int R, const int32_t *rlist, const int32_t *L, const int32_t *coff,
+__global__ void k_cycle(const int32_t *Rdev, const int32_t *rlist, const int32_t *L, const int32_t *coff,
                         const int32_t *cyc, const long long *moff, const long long *Mw,
                         const long long *TS, const int32_t *sigma, long long m, int32_t n,
                         long long *bestsc, unsigned long long *bestkey, int pass) {
+    const int R = *Rdev;
     for (int q0 = blockIdx.x; q0 < R; q0 += gridDim.x) {
         const int l = L[q0];
         if (l < 2) continue;
@@ -219,8 +238,9 @@ __global__ void k_cycle(int R, const int32_t *rlist, const int32_t *L, const int
     }
 }
 
-__global__ void k_apply_split(int R, const int32_t *rlist, const unsigned long long *bestkey,
-                              int32_t n, int32_t *a) {
+__global__ void k_apply_split(const int32_t *Rdev, const int32_t *rlist,
+                              const unsigned long long *bestkey, int32_t n, int32_t *a) {
+    const int R = *Rdev;
     GRID_STRIDE(q, R) {
         unsigned long long key = bestkey[q];
         if (key == ~0ull) continue;  // no option recorded (cannot happen for size >= 2)
@@ -294,29 +314,29 @@ __global__ void k_sigma_members(int cnt, const int32_t *M, const int32_t *root, 
         if (s[v]) atomicAdd(&sigma[root[v]], s[v]);
     }
 }
-// one warp per member: own-community weight and local gain
-__global__ void k_own_members(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
-                              const int32_t *w, const int32_t *s, long long m,
-                              const int32_t *root, const int32_t *sigma, int32_t *kown,
-                              int32_t *flag) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long k = warp; k < cnt; k += nwarps) {
+// own-community weight of every member, one thread per member edge
+__global__ void k_own_edges(int cnt, const int32_t *M, const int32_t *epref, const int32_t *Edev,
+                            const int32_t *rp, const int32_t *col, const int32_t *w,
+                            const int32_t *root, long long *kacc) {
+    const long long E = *Edev;
+    GRID_STRIDE(e, E) {
+        int k = owner_of(e, epref, cnt);
+        const int x = M[k];
+        const int p = rp[x] + (int)(e - epref[k]);
+        const int j = col[p];
+        if (j != x && root[j] == root[x]) add64(&kacc[k], w[p]);
+    }
+}
+__global__ void k_own_finish(int cnt, const int32_t *M, const int32_t *s, long long m,
+                             const int32_t *root, const int32_t *sigma, const long long *kacc,
+                             int32_t *kown, int32_t *flag) {
+    GRID_STRIDE(k, cnt) {
         int i = M[k];
         int ci = root[i];
-        long long own = 0;
-        for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
-            int j = col[p];
-            if (j != i && root[j] == ci) own += w[p];
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
-        if (lane == 0) {
-            kown[i] = (int32_t)own;
-            long long si = s[i];
-            if (m * own - si * ((long long)sigma[ci] - si) < 0) flag[ci] = 1;
-        }
+        long long own = kacc[k];
+        kown[i] = (int32_t)own;
+        long long si = s[i];
+        if (m * own - si * ((long long)sigma[ci] - si) < 0) flag[ci] = 1;
     }
 }
 
@@ -374,32 +394,41 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     unsigned long long *bestkey = ps.bestkey.as<unsigned long long>();
     int32_t *rlist = ps.rlist.as<int32_t>(), *posr = ps.posr.as<int32_t>(), *L = ps.L.as<int32_t>(),
             *coff = ps.coff.as<int32_t>();
+    // per round header on the device: R (roots), E (member edges), and the
+    // sizes of the cycle pools; read back once per round
+    struct Hdr {
+        long long mtot;
+        int32_t ctot, pad0;
+        int32_t R, E;
+    };
+    ps.hdr.ensure(sizeof(Hdr), st);
+    ps.epref.ensure(4 * (N + 1), st);
+    ps.kacc.ensure(8 * (N + 1), st);
+    Hdr *hdr = ps.hdr.as<Hdr>();
+    int32_t *epref = ps.epref.as<int32_t>();
+    long long *kacc = ps.kacc.as<long long>();
+    const int ge = kNumSMs * 16;  // grid of the edge-parallel kernels (grid-stride)
     while (cnt > 0) {
         // every round splits at least one community, so n rounds always suffice
         if (++rounds > (long long)n) fail(SLM_ERR_TIMEOUT, "POSITIVE did not settle within n rounds");
         visits += cnt;
         const int gm = grid_for(cnt, 256);
-        const int gmw = grid_for((long long)cnt * 32, 256, kNumSMs * 16);
-        SLM_CUDA(cudaMemsetAsync(rcnt, 0, 64, st));
-        k_round_init<<<gm, 256, 0, st>>>(cnt, M, f.root, subS, subWA, subWin, credit, TS, rlist,
-                                         rcnt, posr);
+        SLM_CUDA(cudaMemsetAsync(hdr, 0, sizeof(Hdr), st));
+        k_round_init<<<gm, 256, 0, st>>>(cnt, M, rp, f.root, subS, subWA, subWin, credit, TS, rlist,
+                                         &hdr->R, posr, epref, kacc);
         SLM_LAUNCH_CHECK();
-        int32_t R = 0;
-        SLM_CUDA(cudaMemcpyAsync(&R, rcnt, sizeof R, cudaMemcpyDeviceToHost, st));
+        k_root_init<<<gm, 256, 0, st>>>(cnt, &hdr->R, rlist, a, f.cdist, L, msz, coff, bestsc, bestkey);
+        SLM_LAUNCH_CHECK();
+        exclusive_scan_i64(msz, msz, cnt, &hdr->mtot, st);
+        exclusive_scan_i32(coff, coff, cnt, &hdr->ctot, st);
+        exclusive_scan_i32(epref, epref, cnt, &hdr->E, st);
+        Hdr h;
+        SLM_CUDA(cudaMemcpyAsync(&h, hdr, sizeof h, cudaMemcpyDeviceToHost, st));
         SLM_CUDA(cudaStreamSynchronize(st));
-        const int gr = grid_for(R, 256);
-        k_root_init<<<gr, 256, 0, st>>>(R, rlist, a, f.cdist, L, msz, coff, bestsc, bestkey);
-        SLM_LAUNCH_CHECK();
+        const long long mtot = h.mtot;
+        const long long ctot = h.ctot;
+        const int R = h.R;
         // pools for the cycle orders and the L x L tree weights
-        DevBuf tot2(16, st);
-        SLM_CUDA(cudaMemsetAsync(tot2.get(), 0, 16, st));
-        exclusive_scan_i64(msz, msz, R, tot2.as<long long>(), st);
-        exclusive_scan_i32(coff, coff, R, reinterpret_cast<int32_t *>(tot2.as<long long>() + 1), st);
-        long long ht[2] = {0, 0};
-        SLM_CUDA(cudaMemcpyAsync(ht, tot2.get(), 16, cudaMemcpyDeviceToHost, st));
-        SLM_CUDA(cudaStreamSynchronize(st));
-        const long long mtot = ht[0];
-        const long long ctot = ht[1] & 0xffffffffLL;
         ps.pool.ensure(8 * (size_t)(mtot > 0 ? mtot : 1), st);
         ps.cyc.ensure(4 * (size_t)(ctot > 0 ? ctot : 1), st);
         long long *Mw = ps.pool.as<long long>();
@@ -413,8 +442,8 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
                                               ps.cyc.as<int32_t>());
             SLM_LAUNCH_CHECK();
         }
-        k_edges<<<gmw, 256, 0, st>>>(cnt, M, rp, col, w, a, f.oncycle, f.entry, f.depth, f.root,
-                                     posr, L, f.cdist, msz, Mw, credit);
+        k_edges<<<ge, 256, 0, st>>>(cnt, M, epref, &hdr->E, rp, col, w, a, f.oncycle, f.entry,
+                                    f.depth, f.root, posr, L, f.cdist, msz, Mw, credit);
         SLM_LAUNCH_CHECK();
         k_credit<<<gm, 256, 0, st>>>(cnt, M, a, f.depth, credit, subWin);
         SLM_LAUNCH_CHECK();
@@ -424,12 +453,12 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
             SLM_LAUNCH_CHECK();
             if (ctot > 0) {
                 k_cycle<<<grid_for(R, 1, kNumSMs * 8), 128, 0, st>>>(
-                    R, rlist, L, coff, ps.cyc.as<int32_t>(), msz, Mw, TS, sigma, m, n, bestsc,
+                    &hdr->R, rlist, L, coff, ps.cyc.as<int32_t>(), msz, Mw, TS, sigma, m, n, bestsc,
                     bestkey, pass);
                 SLM_LAUNCH_CHECK();
             }
         }
-        k_apply_split<<<gr, 256, 0, st>>>(R, rlist, bestkey, n, a);
+        k_apply_split<<<grid_for(R, 256), 256, 0, st>>>(&hdr->R, rlist, bestkey, n, a);
         SLM_LAUNCH_CHECK();
         splits += R;
 
@@ -459,7 +488,9 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
         SLM_LAUNCH_CHECK();
         k_sigma_members<<<gm, 256, 0, st>>>(cnt, M, f.root, s, sigma);
         SLM_LAUNCH_CHECK();
-        k_own_members<<<gmw, 256, 0, st>>>(cnt, M, rp, col, w, s, m, f.root, sigma, kown, flag);
+        k_own_edges<<<ge, 256, 0, st>>>(cnt, M, epref, &hdr->E, rp, col, w, f.root, kacc);
+        SLM_LAUNCH_CHECK();
+        k_own_finish<<<gm, 256, 0, st>>>(cnt, M, s, m, f.root, sigma, kacc, kown, flag);
         SLM_LAUNCH_CHECK();
         cnt = compact_members(cnt, M, f.root, flag, M2, ps.mark, ps.tot, st);
         std::swap(M, M2);
