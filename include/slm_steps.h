@@ -105,6 +105,32 @@ slm_status slm_step_modularity(int32_t n, const int32_t *row_ptr, const int32_t 
                                const int32_t *w, const int32_t *labels, double *q_host,
                                int64_t *num_host, void *stream);
 
+/* Modularity of labels without any device allocation, for callers that
+ * cannot let a library call cudaMalloc (for instance a framework that has
+ * handed all device memory to its own caching allocator or arena and forbids
+ * further allocations in the middle of its work).  The paper has no
+ * counterpart: this is the computation of slm_step_modularity with its
+ * scratch moved into one fixed, file-scope device array of 2^21 + 4 words
+ * (16 MiB), which every GPU that loads this library holds until the process
+ * exits.
+ *   - n must not exceed 1048576 (else SLM_ERR_INVALID_ARGUMENT and a message
+ *     for slm_last_error(NULL)); labels and columns must lie in [0, n) (else
+ *     SLM_ERR_INVALID_ARGUMENT, detected on the device, nothing written
+ *     out of bounds);
+ *   - *num_out (int64) and *q_out (double) are DEVICE pointers receiving the
+ *     exact numerator sum_C (m_w W_in(C) - Sigma_C^2) and its FP64 quotient by
+ *     m_w^2 (0 when m_w = 0), the same values slm_step_modularity returns;
+ *   - the first call on a device looks up the array's device address (a
+ *     cudaGetSymbolAddress with that device current), so make that first call
+ *     before any stream capture;
+ *   - every call shares the one array and clears what it uses; calls that
+ *     overlap on the GPU (two streams, or two threads) race and must not be
+ *     issued concurrently;
+ *   - the call synchronises `stream` before returning. */
+slm_status slm_step_modularity_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                       const int32_t *w, const int32_t *labels, int64_t *num_out,
+                                       double *q_out, void *stream);
+
 /* Diagnostic record of the last slm_run: one row of six int64 per scan
  * (level, sweep, candidates, candidates with a positive branch gain,
  * accepted moves, POSITIVE splits after the write).  Copies at most `cap`

@@ -44,7 +44,8 @@ EXPORTS = ["slm_default_options", "slm_create_graph", "slm_run", "slm_num_levels
            "slm_destroy_graph", "slm_status_string", "slm_last_error", "slm_step_strengths",
            "slm_step_assign", "slm_step_components", "slm_step_scan", "slm_step_branch_gain",
            "slm_step_maximal", "slm_step_positive", "slm_step_compact", "slm_step_aggregate",
-           "slm_step_modularity", "slm_get_trace", "slm_get_timing", "slm_launch_count"]
+           "slm_step_modularity", "slm_get_trace", "slm_get_timing", "slm_launch_count",
+           "slm_step_modularity_noalloc"]
 
 
 def launch_count() -> int:
@@ -116,6 +117,7 @@ def load():
                                              C.POINTER(i32), vp]),
             "slm_step_modularity": (C.c_int, [i32, vp, vp, vp, vp, C.POINTER(C.c_double),
                                               C.POINTER(i64), vp]),
+            "slm_step_modularity_noalloc": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -381,6 +383,19 @@ def step_aggregate(rp, col, w, idv, K, stream=None):
                                      _ptr(rp2), _ptr(col2), _ptr(w2), C.byref(nnz),
                                      _stream(stream)))
     return rp2, col2[: nnz.value], w2[: nnz.value]
+
+
+def step_modularity_noalloc(rp, col, w, labels, stream=None):
+    """Modularity through the entry point that allocates no device memory;
+    returns (q, num) read back from the device outputs."""
+    torch = _torch()
+    rp, col, w, labels = map(_dev_i32, (rp, col, w, labels))
+    n = rp.numel() - 1
+    num = torch.zeros(1, dtype=torch.int64, device="cuda")
+    q = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _check(load().slm_step_modularity_noalloc(n, _ptr(rp), _ptr(col), _ptr(w), _ptr(labels),
+                                              _ptr(num), _ptr(q), _stream(stream)))
+    return float(q.item()), int(num.item())
 
 
 def step_modularity(rp, col, w, labels, stream=None):

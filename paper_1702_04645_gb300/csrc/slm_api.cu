@@ -81,6 +81,14 @@ struct PhaseTimer {
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+}  // namespace
+
+namespace slm {
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace slm
+
+namespace {
+
 template <class F> slm_status guarded(slm_graph *g, F &&f) {
     try {
         f();

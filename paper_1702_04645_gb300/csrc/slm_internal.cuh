@@ -28,6 +28,8 @@ struct Error {
 
 [[noreturn]] void fail(slm_status st, const std::string &msg);
 unsigned long long launch_count();
+// message returned by slm_last_error(NULL) on this thread
+void set_global_error(const std::string &msg);
 void check_cuda(cudaError_t e, const char *what, const char *file, int line);
 
 // Every kernel launch of the library is followed by SLM_LAUNCH_CHECK(), which
