@@ -238,82 +238,113 @@ __global__ void k_cycle(const int32_t *Rdev, const int32_t *rlist, const int32_t
     }
 }
 
-__global__ void k_apply_split(const int32_t *Rdev, const int32_t *rlist,
-                              const unsigned long long *bestkey, int32_t n, int32_t *a) {
+// per split community: record the cut, set the totals of the two parts from
+// the subtree sums, and remove the cut assignments (a(u) <- u, a(v) <- v)
+__global__ void k_cut_info(const int32_t *Rdev, const int32_t *rlist,
+                           const unsigned long long *bestkey, int32_t n, const int32_t *L,
+                           const int32_t *coff, const int32_t *cyc, const long long *TS,
+                           const int32_t *depth, const int32_t *cdist, const long long *subS,
+                           int32_t *sigma, int4 *cut, int32_t *a) {
     const int R = *Rdev;
     GRID_STRIDE(q, R) {
-        unsigned long long key = bestkey[q];
-        if (key == ~0ull) continue;  // no option recorded (cannot happen for size >= 2)
-        int type = (int)(key >> 62);
-        int u = (int)((key >> 31) & 0x7fffffffu);
-        int v = (int)(key & 0x7fffffffu);
-        if (u < n) a[u] = u;
-        if (type == 1 && v < n) a[v] = v;
+        const int r = rlist[q];
+        const unsigned long long key = bestkey[q];
+        if (key == ~0ull) {  // no option recorded (cannot happen for size >= 2)
+            cut[q] = make_int4(-1, 0, 0, 0);
+            continue;
+        }
+        const int type = (int)(key >> 62);
+        const int u = (int)((key >> 31) & 0x7fffffffu);
+        const int v = (int)(key & 0x7fffffffu);
+        if (u >= n || (type == 1 && v >= n)) {
+            cut[q] = make_int4(-1, 0, 0, 0);
+            continue;
+        }
+        if (type == 0) {
+            const long long sS = subS[u];
+            cut[q] = make_int4(0, u, depth[u], 0);
+            sigma[r] = (int32_t)((long long)sigma[r] - sS);
+            sigma[u] = (int32_t)sS;
+            a[u] = u;
+        } else {
+            const int l = L[q];
+            const int iu = cyc_index(u, r, l, cdist), iv = cyc_index(v, r, l, cdist);
+            const int p = min(iu, iv), pq = max(iu, iv);
+            const int32_t *cy = cyc + coff[q];
+            long long sV = 0;
+            for (int k = p + 1; k <= pq; k++) sV += TS[cy[k]];
+            const long long sA = sigma[r];
+            const int cp = cy[p], cq = cy[pq];
+            cut[q] = make_int4(1, p, pq, l);
+            sigma[cq] = (int32_t)sV;
+            sigma[cp] = (int32_t)(sA - sV);
+            a[cp] = cp;
+            a[cq] = cq;
+        }
     }
 }
 
-// components of the members again: their forward paths stay inside the
-// member set, so pointer jumping over the members alone is exact
-__global__ void k_jinit(int cnt, const int32_t *M, const int32_t *a, int2 *J, uint8_t *oncycle) {
+// components of the members after the cuts, in closed form from the old
+// forest: a branch cut at u roots tail(u) at u (depths shift by depth(u)); a
+// cycle cut at positions p < q of the cycle roots the trees of (p, q] at
+// c_q and the others at c_p, each tree's depth growing by its distance along
+// the cycle.  Read-only phase: the new values go to per-member scratch.
+__global__ void k_forest_new(int cnt, const int32_t *M, const int32_t *a, const int32_t *root,
+                             const int32_t *entry, const int32_t *depth, const int32_t *cdist,
+                             const uint8_t *oncycle, const int32_t *posr, const int4 *cut,
+                             const int32_t *coff, const int32_t *cyc, int4 *nf, uint8_t *noc) {
     GRID_STRIDE(k, cnt) {
-        int v = M[k];
-        J[v] = make_int2(a[v], v);
-        oncycle[v] = 0;
+        const int x = M[k];
+        const int r = root[x];
+        const int4 ct = cut[posr[r]];
+        int4 v = make_int4(r, entry[x], depth[x], cdist[x]);
+        uint8_t oc = oncycle[x];
+        if (ct.x == 0) {
+            const int u = ct.y, du = ct.z;
+            int dx = depth[x];
+            if (dx >= du) {
+                int y = x;
+                for (int t = dx - du; t > 0; t--) y = a[y];
+                if (y == u) {
+                    v = make_int4(u, u, dx - du, 0);
+                    oc = (x == u);
+                }
+            }
+        } else if (ct.x == 1) {
+            const int p = ct.y, pq = ct.z, l = ct.w;
+            const int e = entry[x];
+            const int ie = cyc_index(e, r, l, cdist);
+            const int32_t *cy = cyc + coff[posr[r]];
+            if (ie > p && ie <= pq) {
+                const int cq = cy[pq];
+                v = make_int4(cq, cq, depth[x] + (pq - ie), 0);
+                oc = (x == cq);
+            } else {
+                const int cp = cy[p];
+                v = make_int4(cp, cp, depth[x] + ((p - ie + l) % l), 0);
+                oc = (x == cp);
+            }
+        }
+        nf[k] = v;
+        noc[k] = oc;
     }
 }
-__global__ void k_jround(int cnt, const int32_t *M, const int2 *in, int2 *out) {
+
+__global__ void k_forest_write(int cnt, const int32_t *M, const int4 *nf, const uint8_t *noc,
+                               int32_t *root, int32_t *entry, int32_t *depth, int32_t *cdist,
+                               uint8_t *oncycle, int32_t *flag) {
     GRID_STRIDE(k, cnt) {
-        int v = M[k];
-        int2 x = in[v];
-        int2 y = in[x.x];
-        out[v] = make_int2(y.x, min(x.y, y.y));
+        const int x = M[k];
+        const int4 v = nf[k];
+        root[x] = v.x;
+        entry[x] = v.y;
+        depth[x] = v.z;
+        cdist[x] = v.w;
+        oncycle[x] = noc[k];
+        flag[x] = 0;  // the names in use inside the member set are members
     }
 }
-__global__ void k_jfinal(int cnt, const int32_t *M, const int2 *J, int32_t *root, uint8_t *oncycle) {
-    GRID_STRIDE(k, cnt) {
-        int v = M[k];
-        int c = J[v].x;
-        root[v] = J[c].y;
-        oncycle[c] = 1;
-    }
-}
-__global__ void k_dinit(int cnt, const int32_t *M, const int32_t *a, const int32_t *root,
-                        const uint8_t *oncycle, int2 *D) {
-    GRID_STRIDE(k, cnt) {
-        int v = M[k];
-        if (oncycle[v] && root[v] == v) D[v] = make_int2(v, 0);
-        else D[v] = make_int2(a[v], 1);
-    }
-}
-__global__ void k_dround(int cnt, const int32_t *M, const int2 *in, int2 *out,
-                         const uint8_t *oncycle) {
-    GRID_STRIDE(k, cnt) {
-        int v = M[k];
-        int2 x = in[v];
-        if (!oncycle[v] && oncycle[x.x]) { out[v] = x; continue; }
-        int2 y = in[x.x];
-        out[v] = make_int2(y.x, x.y + y.y);
-    }
-}
-__global__ void k_dfinal(int cnt, const int32_t *M, const int2 *D, const uint8_t *oncycle,
-                         int32_t *entry, int32_t *depth, int32_t *cdist, int32_t *sigma,
-                         int32_t *flag) {
-    GRID_STRIDE(k, cnt) {
-        int v = M[k];
-        int2 d = D[v];
-        if (oncycle[v]) { entry[v] = v; depth[v] = 0; cdist[v] = d.y; }
-        else { entry[v] = d.x; depth[v] = d.y; cdist[v] = 0; }
-        sigma[v] = 0;  // the names in use inside the member set are members
-        flag[v] = 0;
-    }
-}
-__global__ void k_sigma_members(int cnt, const int32_t *M, const int32_t *root, const int32_t *s,
-                                int32_t *sigma) {
-    GRID_STRIDE(k, cnt) {
-        int v = M[k];
-        if (s[v]) atomicAdd(&sigma[root[v]], s[v]);
-    }
-}
+
 // own-community weight of every member, one thread per member edge
 __global__ void k_own_edges(int cnt, const int32_t *M, const int32_t *epref, const int32_t *Edev,
                             const int32_t *rp, const int32_t *col, const int32_t *w,
@@ -404,6 +435,9 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     ps.hdr.ensure(sizeof(Hdr), st);
     ps.epref.ensure(4 * (N + 1), st);
     ps.kacc.ensure(8 * (N + 1), st);
+    ps.cut.ensure(16 * (N + 1), st);
+    ps.nf.ensure(16 * (N + 1), st);
+    ps.noc.ensure(N + 1, st);
     Hdr *hdr = ps.hdr.as<Hdr>();
     int32_t *epref = ps.epref.as<int32_t>();
     long long *kacc = ps.kacc.as<long long>();
@@ -458,35 +492,17 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
                 SLM_LAUNCH_CHECK();
             }
         }
-        k_apply_split<<<grid_for(R, 256), 256, 0, st>>>(&hdr->R, rlist, bestkey, n, a);
+        k_cut_info<<<grid_for(R, 256), 256, 0, st>>>(&hdr->R, rlist, bestkey, n, L, coff,
+                                                      ps.cyc.as<int32_t>(), TS, f.depth, f.cdist,
+                                                      subS, sigma, ps.cut.as<int4>(), a);
         SLM_LAUNCH_CHECK();
         splits += R;
-
-        // components, totals and local gains of the members after the splits
-        int K = 0;
-        while ((1LL << K) < (long long)cnt) K++;
-        k_jinit<<<gm, 256, 0, st>>>(cnt, M, a, f.jmpA, f.oncycle);
+        k_forest_new<<<gm, 256, 0, st>>>(cnt, M, a, f.root, f.entry, f.depth, f.cdist, f.oncycle,
+                                         posr, ps.cut.as<int4>(), coff, ps.cyc.as<int32_t>(),
+                                         ps.nf.as<int4>(), ps.noc.as<uint8_t>());
         SLM_LAUNCH_CHECK();
-        int2 *cur = f.jmpA, *nxt = f.jmpB;
-        for (int k = 0; k < K; k++) {
-            k_jround<<<gm, 256, 0, st>>>(cnt, M, cur, nxt);
-            SLM_LAUNCH_CHECK();
-            std::swap(cur, nxt);
-        }
-        k_jfinal<<<gm, 256, 0, st>>>(cnt, M, cur, f.root, f.oncycle);
-        SLM_LAUNCH_CHECK();
-        k_dinit<<<gm, 256, 0, st>>>(cnt, M, a, f.root, f.oncycle, f.jmpA);
-        SLM_LAUNCH_CHECK();
-        cur = f.jmpA;
-        nxt = f.jmpB;
-        for (int k = 0; k < K; k++) {
-            k_dround<<<gm, 256, 0, st>>>(cnt, M, cur, nxt, f.oncycle);
-            SLM_LAUNCH_CHECK();
-            std::swap(cur, nxt);
-        }
-        k_dfinal<<<gm, 256, 0, st>>>(cnt, M, cur, f.oncycle, f.entry, f.depth, f.cdist, sigma, flag);
-        SLM_LAUNCH_CHECK();
-        k_sigma_members<<<gm, 256, 0, st>>>(cnt, M, f.root, s, sigma);
+        k_forest_write<<<gm, 256, 0, st>>>(cnt, M, ps.nf.as<int4>(), ps.noc.as<uint8_t>(), f.root,
+                                           f.entry, f.depth, f.cdist, f.oncycle, flag);
         SLM_LAUNCH_CHECK();
         k_own_edges<<<ge, 256, 0, st>>>(cnt, M, epref, &hdr->E, rp, col, w, f.root, kacc);
         SLM_LAUNCH_CHECK();

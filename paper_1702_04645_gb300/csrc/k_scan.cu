@@ -16,6 +16,7 @@
 // shared-memory table (257..4096 edges) or a global-memory table (hubs).
 // Every reduction compares (score desc, name asc), so the result does not
 // depend on the order in which lanes or blocks finish.
+#include <algorithm>
 #include <climits>
 
 #include "slm_internal.cuh"
@@ -25,8 +26,7 @@ namespace slm {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kBlockSmemMaxDeg = 4096;            // block bucket: smem table up to here
-constexpr int kBlockSmemCap = 2 * kBlockSmemMaxDeg; // slots (int key + int value)
+constexpr int kBlockSmemCap = 2 * kBlockSmemMaxDeg; // slots of the block table (int key + int value)
 constexpr int kBlockThreads = 256;
 constexpr int kWarpHashCap = 2 * kWarpHashMaxDeg;
 constexpr int kWarpHashWarps = 8;  // warps per block in the warp-hash kernel
@@ -38,7 +38,8 @@ __device__ __forceinline__ int bucket_of(int d) {
     if (d <= 16) return kBucketG16;
     if (d <= 32) return kBucketG32;
     if (d <= kWarpHashMaxDeg) return kBucketWarpHash;
-    return kBucketBlock;
+    if (d <= kBlockSmemMaxDeg) return kBucketBlock;
+    return kBucketHub;
 }
 
 __device__ __forceinline__ bool better(long long sc, int c, long long bsc, int bc) {
@@ -242,14 +243,12 @@ __device__ void block_reduce_best(long long &own, long long &sc, int &cc) {
 }
 
 // ---------------------------------------------------------------------------
-// MAXIMAL scan, block shape: one node per block; table in shared memory when
-// it fits, else in a global-memory slice of 2*deg (rounded up) slots.
+// MAXIMAL scan, block shape: one node per block, table in shared memory.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *order, int32_t cnt, const int32_t *rp,
                              const int32_t *col, const int32_t *w, const int32_t *s, long long m,
                              const int32_t *root, const int32_t *sigma, int32_t *best,
-                             long long *gain, int32_t *kown, unsigned long long *ncand,
-                             int *gkeys, int *gvals, const long long *goff) {
+                             long long *gain, int32_t *kown, unsigned long long *ncand) {
     extern __shared__ int sm[];
     unsigned cand = 0;
     for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
@@ -258,14 +257,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *ord
         int ci = root[i], si = s[i];
         int lg = ilog2_pow2_at_least(2 * deg);
         int cap = 1 << lg;
-        int *keys, *vals;
-        if (deg <= kBlockSmemMaxDeg) {
-            keys = sm;
-            vals = sm + cap;
-        } else {
-            keys = gkeys + goff[idx];
-            vals = gvals + goff[idx];
-        }
+        int *keys = sm, *vals = sm + cap;
         for (int k = threadIdx.x; k < cap; k += blockDim.x) { keys[k] = -1; vals[k] = 0; }
         __syncthreads();
         for (int p = start + threadIdx.x; p < start + deg; p += blockDim.x) {
@@ -307,15 +299,108 @@ __global__ void k_scan_empty(const int32_t *order, int32_t cnt, const int32_t *r
     }
 }
 
-__global__ void k_hub_caps(const int32_t *order, int32_t cnt, const int32_t *rp, long long *cap) {
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < cnt;
-         idx += (long long)gridDim.x * blockDim.x) {
-        int i = order[idx];
-        int deg = rp[i + 1] - rp[i];
-        long long c = 1;
-        while (c < 2LL * deg) c <<= 1;
-        cap[idx] = deg > kBlockSmemMaxDeg ? c : 0;
+// ---------------------------------------------------------------------------
+// MAXIMAL scan, hub shape: a hub's row is split into chunks of kHubChunk
+// edges, one block each, all inserting into the hub's global table; a second
+// kernel, one block per hub, reads the table, resets it for the next sweep,
+// and picks the best community.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks, int nchunk, const int32_t *hubs,
+                             const long long *hoff, const int32_t *hlg, const int32_t *col,
+                             const int32_t *w, const int32_t *root, int *tkeys, int *tvals) {
+    for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+        int4 ch = chunks[c];  // (hub index, first edge, end edge, unused)
+        const int i = hubs[ch.x];
+        const int lg = hlg[ch.x];
+        const int cap = 1 << lg;
+        int *keys = tkeys + hoff[ch.x], *vals = tvals + hoff[ch.x];
+        for (int p = ch.y + threadIdx.x; p < ch.z; p += blockDim.x) {
+            int j = col[p];
+            if (j == i) continue;
+            int cc = root[j], wv = w[p];
+            unsigned h = hash_slot(cc, lg);
+            for (;;) {
+                int prev = atomicCAS(&keys[h], -1, cc);
+                if (prev == -1 || prev == cc) { atomicAdd(&vals[h], wv); break; }
+                h = (h + 1) & (cap - 1);
+            }
+        }
     }
+}
+
+__global__ void __launch_bounds__(kBlockThreads) k_hub_argmax(int nhub, const int32_t *hubs, const long long *hoff,
+                             const int32_t *hlg, const int32_t *s, long long m,
+                             const int32_t *root, const int32_t *sigma, int *tkeys, int *tvals,
+                             int32_t *best, long long *gain, int32_t *kown,
+                             unsigned long long *ncand) {
+    unsigned cand = 0;
+    for (int h = blockIdx.x; h < nhub; h += gridDim.x) {
+        const int i = hubs[h];
+        const int ci = root[i], si = s[i];
+        const int cap = 1 << hlg[h];
+        int *keys = tkeys + hoff[h], *vals = tvals + hoff[h];
+        long long own = 0, sc = LLONG_MIN;
+        int cc = INT_MAX;
+        for (int k = threadIdx.x; k < cap; k += blockDim.x) {
+            int c = keys[k];
+            if (c < 0) continue;
+            int v = vals[k];
+            keys[k] = -1;  // leave the table empty for the next sweep
+            vals[k] = 0;
+            if (c == ci) { own = v; continue; }
+            long long x = m * (long long)v - (long long)si * (long long)sigma[c];
+            if (better(x, c, sc, cc)) { sc = x; cc = c; }
+        }
+        block_reduce_best(own, sc, cc);
+        if (threadIdx.x == 0) scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && cand) atomicAdd(ncand, (unsigned long long)cand);
+}
+
+// own-community weight of hubs: chunk partial sums, then the local gain
+__global__ void __launch_bounds__(kBlockThreads) k_own_hub_chunk(const int4 *chunks, int nchunk, const int32_t *hubs,
+                                const int32_t *col, const int32_t *w, const int32_t *root,
+                                unsigned long long *acc) {
+    __shared__ unsigned long long red[kBlockThreads / 32];
+    for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+        int4 ch = chunks[c];
+        const int i = hubs[ch.x];
+        const int ci = root[i];
+        unsigned long long own = 0;
+        for (int p = ch.y + threadIdx.x; p < ch.z; p += blockDim.x) {
+            int j = col[p];
+            if (j != i && root[j] == ci) own += (unsigned long long)w[p];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = own;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int k = 0; k < kBlockThreads / 32; k++) t += red[k];
+            if (t) atomicAdd(&acc[ch.x], t);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_own_hub_finish(int nhub, const int32_t *hubs, const int32_t *s, long long m,
+                                 const int32_t *root, const int32_t *sigma,
+                                 const unsigned long long *acc, int32_t *kown, int32_t *flag) {
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < nhub; h += gridDim.x * blockDim.x) {
+        int i = hubs[h];
+        int ci = root[i];
+        long long own = (long long)acc[h];
+        kown[i] = (int32_t)own;
+        long long si = s[i];
+        if (m * own - si * ((long long)sigma[ci] - si) < 0) flag[ci] = 1;
+    }
+}
+
+__global__ void k_hub_rows(int nhub, const int32_t *hubs, const int32_t *rp, int2 *rows) {
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < nhub; h += gridDim.x * blockDim.x)
+        rows[h] = make_int2(rp[hubs[h]], rp[hubs[h] + 1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -507,6 +592,46 @@ void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
     SLM_CUDA(cudaMemcpyAsync(h, counts.get(), sizeof h, cudaMemcpyDeviceToHost, s));
     SLM_CUDA(cudaStreamSynchronize(s));
     for (int b = 0; b < kNumBuckets; b++) off[b + 1] = off[b] + h[b];
+    // hubs: table offsets and chunk list, built on the host (hubs are few)
+    nhub = off[kBucketHub + 1] - off[kBucketHub];
+    nchunk = 0;
+    if (nhub > 0) {
+        DevBuf rows(sizeof(int2) * nhub, s);
+        const int32_t *hubs = order.as<int32_t>() + off[kBucketHub];
+        k_hub_rows<<<grid_for(nhub, 256), 256, 0, s>>>(nhub, hubs, rp, rows.as<int2>());
+        SLM_LAUNCH_CHECK();
+        std::vector<int2> hr(nhub);
+        SLM_CUDA(cudaMemcpyAsync(hr.data(), rows.get(), sizeof(int2) * nhub, cudaMemcpyDeviceToHost, s));
+        SLM_CUDA(cudaStreamSynchronize(s));
+        std::vector<long long> hoff(nhub);
+        std::vector<int32_t> hlg(nhub);
+        std::vector<int4> ch;
+        long long tot = 0;
+        for (int k = 0; k < nhub; k++) {
+            int deg = hr[k].y - hr[k].x;
+            int lg = 0;
+            while ((1LL << lg) < 2LL * deg) lg++;
+            hoff[k] = tot;
+            hlg[k] = lg;
+            tot += 1LL << lg;
+            for (int p0 = hr[k].x; p0 < hr[k].y; p0 += kHubChunk)
+                ch.push_back(make_int4(k, p0, std::min(p0 + kHubChunk, hr[k].y), 0));
+        }
+        nchunk = (int32_t)ch.size();
+        hub_off.alloc(sizeof(long long) * nhub, s);
+        hub_lg.alloc(sizeof(int32_t) * nhub, s);
+        chunks.alloc(sizeof(int4) * ch.size(), s);
+        hub_acc.alloc(sizeof(unsigned long long) * nhub, s);
+        tkeys.alloc(sizeof(int) * tot, s);
+        tvals.alloc(sizeof(int) * tot, s);
+        SLM_CUDA(cudaMemcpyAsync(hub_off.get(), hoff.data(), sizeof(long long) * nhub, cudaMemcpyHostToDevice, s));
+        SLM_CUDA(cudaMemcpyAsync(hub_lg.get(), hlg.data(), sizeof(int32_t) * nhub, cudaMemcpyHostToDevice, s));
+        SLM_CUDA(cudaMemcpyAsync(chunks.get(), ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
+        // the tables start empty and every scan leaves them empty
+        SLM_CUDA(cudaMemsetAsync(tkeys.get(), 0xff, sizeof(int) * tot, s));
+        SLM_CUDA(cudaMemsetAsync(tvals.get(), 0, sizeof(int) * tot, s));
+        SLM_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+    }
 }
 
 static int blocks_for_groups(long long cnt, int nodes_per_warp, int threads = 256) {
@@ -541,8 +666,8 @@ void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_
         if (c) { k_assign_group<32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
     }
     {
-        auto [o, c] = seg(kBucketBlock);
-        if (c) { k_assign_block<<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(o, c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+        int c = bk.off[kBucketHub + 1] - bk.off[kBucketBlock];
+        if (c) { k_assign_block<<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(ord + bk.off[kBucketBlock], c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
     }
 }
 
@@ -579,17 +704,6 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
         SLM_LAUNCH_CHECK();
     }
     if (int c = cnt(kBucketBlock)) {
-        const int32_t *o = ord + bk.off[kBucketBlock];
-        // global tables for hubs beyond the shared-memory table
-        DevBuf caps(sizeof(long long) * (c + 1), st), tot(sizeof(long long), st);
-        k_hub_caps<<<grid_for(c, 256), 256, 0, st>>>(o, c, rp, caps.as<long long>());
-        SLM_LAUNCH_CHECK();
-        exclusive_scan_i64(caps.as<long long>(), caps.as<long long>(), c, tot.as<long long>(), st);
-        long long total = 0;
-        SLM_CUDA(cudaMemcpyAsync(&total, tot.get(), sizeof total, cudaMemcpyDeviceToHost, st));
-        SLM_CUDA(cudaStreamSynchronize(st));
-        DevBuf gk(sizeof(int) * (size_t)(total > 0 ? total : 1), st),
-            gv(sizeof(int) * (size_t)(total > 0 ? total : 1), st);
         size_t smem = sizeof(int) * 2 * kBlockSmemCap;
         static bool attr_set = false;
         if (!attr_set) {
@@ -597,8 +711,18 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
             attr_set = true;
         }
         k_scan_block<<<grid_for(c, 1, kNumSMs * 3), kBlockThreads, smem, st>>>(
-            o, c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand, gk.as<int>(), gv.as<int>(),
-            caps.as<long long>());
+            ord + bk.off[kBucketBlock], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (bk.nhub > 0) {
+        const int32_t *hubs = ord + bk.off[kBucketHub];
+        k_hub_insert<<<grid_for(bk.nchunk, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(
+            bk.chunks.as<int4>(), bk.nchunk, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(),
+            col, w, root, bk.tkeys.as<int>(), bk.tvals.as<int>());
+        SLM_LAUNCH_CHECK();
+        k_hub_argmax<<<grid_for(bk.nhub, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(
+            bk.nhub, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(), s, m, root, sigma,
+            bk.tkeys.as<int>(), bk.tvals.as<int>(), best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
     }
 }
@@ -632,6 +756,16 @@ void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const in
     }
     if (int c = bk.off[kBucketBlock + 1] - bk.off[kBucketBlock]) {
         k_own_block<<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(ord + bk.off[kBucketBlock], c, rp, col, w, s, m, root, sigma, kown, flag);
+        SLM_LAUNCH_CHECK();
+    }
+    if (bk.nhub > 0) {
+        const int32_t *hubs = ord + bk.off[kBucketHub];
+        SLM_CUDA(cudaMemsetAsync(bk.hub_acc.get(), 0, sizeof(unsigned long long) * bk.nhub, st));
+        k_own_hub_chunk<<<grid_for(bk.nchunk, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(
+            bk.chunks.as<int4>(), bk.nchunk, hubs, col, w, root, bk.hub_acc.as<unsigned long long>());
+        SLM_LAUNCH_CHECK();
+        k_own_hub_finish<<<grid_for(bk.nhub, 256), 256, 0, st>>>(bk.nhub, hubs, s, m, root, sigma,
+                                                               bk.hub_acc.as<unsigned long long>(), kown, flag);
         SLM_LAUNCH_CHECK();
     }
 }

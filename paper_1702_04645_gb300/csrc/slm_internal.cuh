@@ -143,12 +143,18 @@ double modularity_from_num(long long num, long long m_w);
 // Degree buckets and the neighbourhood scans (k_scan.cu)
 // ---------------------------------------------------------------------------
 enum { kBucketEmpty = 0, kBucketG4, kBucketG8, kBucketG16, kBucketG32, kBucketWarpHash,
-       kBucketBlock, kNumBuckets };
+       kBucketBlock, kBucketHub, kNumBuckets };
 constexpr int kWarpHashMaxDeg = 256;
+constexpr int kBlockSmemMaxDeg = 4096;  // above this a node is a hub
+constexpr int kHubChunk = 2048;         // edges of a hub handled by one block
 
 struct Buckets {
     DevBuf order;                       // int32[n]: nodes sorted by bucket (stable)
     int32_t off[kNumBuckets + 1] = {0}; // host copy of bucket offsets
+    // hubs: per hub its global table (offset, log2 capacity), and the chunks
+    // (hub index, first edge, end edge) that split its row across blocks
+    int32_t nhub = 0, nchunk = 0;
+    DevBuf hub_off, hub_lg, chunks, tkeys, tvals, hub_acc;
     void build(int32_t n, const int32_t *rp, cudaStream_t s);
 };
 
@@ -216,7 +222,7 @@ void apply_moves(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt,
 
 struct PositiveScratch {
     DevBuf flag, kown, listA, listB, rlist, posr, L, coff, subS, subWA, subWin, credit, TS, msz,
-        bestsc, bestkey, pool, cyc, cnt, mark, tot, hdr, epref, kacc;
+        bestsc, bestkey, pool, cyc, cnt, mark, tot, hdr, epref, kacc, cut, nf, noc;
 };
 // Algorithm POSITIVE until no node has a negative local gain.  a and the
 // forest f are updated in place (only the members of split communities are
