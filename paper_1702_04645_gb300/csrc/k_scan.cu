@@ -26,7 +26,7 @@ namespace slm {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kBlockSmemCap = 2 * kBlockSmemMaxDeg; // slots of the block table (int key + int value)
+constexpr int kHubSlice = 4096;  // hub table slots read by one block
 constexpr int kBlockThreads = 256;
 constexpr int kWarpHashCap = 2 * kWarpHashMaxDeg;
 constexpr int kWarpHashWarps = 8;  // warps per block in the warp-hash kernel
@@ -38,7 +38,8 @@ __device__ __forceinline__ int bucket_of(int d) {
     if (d <= 16) return kBucketG16;
     if (d <= 32) return kBucketG32;
     if (d <= kWarpHashMaxDeg) return kBucketWarpHash;
-    if (d <= kBlockSmemMaxDeg) return kBucketBlock;
+    if (d <= kBlockSmallMaxDeg) return kBucketBlockS;
+    if (d <= kBlockSmemMaxDeg) return kBucketBlockL;
     return kBucketHub;
 }
 
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(256) k_scan_group(const int32_t *order, int32_
 // ---------------------------------------------------------------------------
 // MAXIMAL scan, warp shape: one node per warp, shared-memory table.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWarpHashWarps * 32) k_scan_warphash(const int32_t *order, int32_t cnt, const int32_t *rp,
+__global__ void __launch_bounds__(kWarpHashWarps * 32, 4) k_scan_warphash(const int32_t *order, int32_t cnt, const int32_t *rp,
                                 const int32_t *col, const int32_t *w, const int32_t *s,
                                 long long m, const int32_t *root, const int32_t *sigma,
                                 int32_t *best, long long *gain, int32_t *kown,
@@ -178,27 +179,48 @@ __global__ void __launch_bounds__(kWarpHashWarps * 32) k_scan_warphash(const int
         int lg = ilog2_pow2_at_least(2 * deg);
         int cap = 1 << lg;
         for (int k = lane; k < cap; k += 32) { keys[k] = -1; vals[k] = 0; }
+        // every lane fetches its (at most 8) edges and their communities before
+        // inserting, so the loads overlap instead of waiting one by one
+        int cv[kWarpHashMaxDeg / 32], wv[kWarpHashMaxDeg / 32];
+#pragma unroll
+        for (int t = 0; t < kWarpHashMaxDeg / 32; t++) {
+            int p = start + lane + 32 * t;
+            bool ok = p < start + deg;
+            cv[t] = ok ? col[p] : -1;
+            wv[t] = ok ? w[p] : 0;
+        }
+#pragma unroll
+        for (int t = 0; t < kWarpHashMaxDeg / 32; t++) cv[t] = (cv[t] >= 0 && cv[t] != i) ? root[cv[t]] : -1;
         __syncwarp();
-        for (int p = start + lane; p < start + deg; p += 32) {
-            int j = col[p];
-            if (j == i) continue;
-            int c = root[j], wv = w[p];
-            unsigned h = hash_slot(c, lg);
+#pragma unroll
+        for (int t = 0; t < kWarpHashMaxDeg / 32; t++) {
+            if (cv[t] < 0) continue;
+            unsigned h = hash_slot(cv[t], lg);
             for (;;) {
-                int prev = atomicCAS(&keys[h], -1, c);
-                if (prev == -1 || prev == c) { atomicAdd(&vals[h], wv); break; }
+                int prev = atomicCAS(&keys[h], -1, cv[t]);
+                if (prev == -1 || prev == cv[t]) { atomicAdd(&vals[h], wv[t]); break; }
                 h = (h + 1) & (cap - 1);
             }
         }
         __syncwarp();
         long long own = 0, sc = LLONG_MIN;
         int cc = INT_MAX;
-        for (int k = lane; k < cap; k += 32) {
-            int c = keys[k];
+        int kk[kWarpHashCap / 32], sg[kWarpHashCap / 32];
+#pragma unroll
+        for (int t = 0; t < kWarpHashCap / 32; t++) {
+            int k = lane + 32 * t;
+            kk[t] = k < cap ? keys[k] : -1;
+        }
+#pragma unroll
+        for (int t = 0; t < kWarpHashCap / 32; t++) sg[t] = (kk[t] >= 0 && kk[t] != ci) ? sigma[kk[t]] : 0;
+#pragma unroll
+        for (int t = 0; t < kWarpHashCap / 32; t++) {
+            int c = kk[t];
             if (c < 0) continue;
-            if (c == ci) { own = vals[k]; continue; }
-            long long v = m * (long long)vals[k] - (long long)si * (long long)sigma[c];
-            if (better(v, c, sc, cc)) { sc = v; cc = c; }
+            int v = vals[lane + 32 * t];
+            if (c == ci) { own = v; continue; }
+            long long x = m * (long long)v - (long long)si * (long long)sg[t];
+            if (better(x, c, sc, cc)) { sc = x; cc = c; }
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
@@ -243,43 +265,70 @@ __device__ void block_reduce_best(long long &own, long long &sc, int &cc) {
 }
 
 // ---------------------------------------------------------------------------
-// MAXIMAL scan, block shape: one node per block, table in shared memory.
+// MAXIMAL scan, block shape: one node per block, table of CAP slots in
+// shared memory; every thread fetches its edges in batches of 8.
 // ---------------------------------------------------------------------------
+template <int CAP>
 __global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *order, int32_t cnt, const int32_t *rp,
                              const int32_t *col, const int32_t *w, const int32_t *s, long long m,
                              const int32_t *root, const int32_t *sigma, int32_t *best,
                              long long *gain, int32_t *kown, unsigned long long *ncand) {
     extern __shared__ int sm[];
+    constexpr int B = 8;
     unsigned cand = 0;
     for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
         int i = order[idx];
-        int start = rp[i], deg = rp[i + 1] - start;
+        int start = rp[i], end = rp[i + 1];
+        int deg = end - start;
         int ci = root[i], si = s[i];
         int lg = ilog2_pow2_at_least(2 * deg);
-        int cap = 1 << lg;
+        int cap = 1 << lg;  // <= CAP because deg <= CAP / 2
         int *keys = sm, *vals = sm + cap;
         for (int k = threadIdx.x; k < cap; k += blockDim.x) { keys[k] = -1; vals[k] = 0; }
         __syncthreads();
-        for (int p = start + threadIdx.x; p < start + deg; p += blockDim.x) {
-            int j = col[p];
-            if (j == i) continue;
-            int c = root[j], wv = w[p];
-            unsigned h = hash_slot(c, lg);
-            for (;;) {
-                int prev = atomicCAS(&keys[h], -1, c);
-                if (prev == -1 || prev == c) { atomicAdd(&vals[h], wv); break; }
-                h = (h + 1) & (cap - 1);
+        for (int p0 = start + threadIdx.x; p0 < end; p0 += B * blockDim.x) {
+            int cv[B], wv[B];
+#pragma unroll
+            for (int t = 0; t < B; t++) {
+                int p = p0 + t * blockDim.x;
+                bool ok = p < end;
+                cv[t] = ok ? col[p] : -1;
+                wv[t] = ok ? w[p] : 0;
+            }
+#pragma unroll
+            for (int t = 0; t < B; t++) cv[t] = (cv[t] >= 0 && cv[t] != i) ? root[cv[t]] : -1;
+#pragma unroll
+            for (int t = 0; t < B; t++) {
+                if (cv[t] < 0) continue;
+                unsigned h = hash_slot(cv[t], lg);
+                for (;;) {
+                    int prev = atomicCAS(&keys[h], -1, cv[t]);
+                    if (prev == -1 || prev == cv[t]) { atomicAdd(&vals[h], wv[t]); break; }
+                    h = (h + 1) & (cap - 1);
+                }
             }
         }
         __syncthreads();
         long long own = 0, sc = LLONG_MIN;
         int cc = INT_MAX;
-        for (int k = threadIdx.x; k < cap; k += blockDim.x) {
-            int c = keys[k];
-            if (c < 0) continue;
-            if (c == ci) { own = vals[k]; continue; }
-            long long v = m * (long long)vals[k] - (long long)si * (long long)sigma[c];
-            if (better(v, c, sc, cc)) { sc = v; cc = c; }
+        for (int k0 = threadIdx.x; k0 < cap; k0 += B * blockDim.x) {
+            int kk[B], sg[B];
+#pragma unroll
+            for (int t = 0; t < B; t++) {
+                int k = k0 + t * blockDim.x;
+                kk[t] = k < cap ? keys[k] : -1;
+            }
+#pragma unroll
+            for (int t = 0; t < B; t++) sg[t] = (kk[t] >= 0 && kk[t] != ci) ? sigma[kk[t]] : 0;
+#pragma unroll
+            for (int t = 0; t < B; t++) {
+                int c = kk[t];
+                if (c < 0) continue;
+                int v = vals[k0 + t * blockDim.x];
+                if (c == ci) { own = v; continue; }
+                long long x = m * (long long)v - (long long)si * (long long)sg[t];
+                if (better(x, c, sc, cc)) { sc = x; cc = c; }
+            }
         }
         block_reduce_best(own, sc, cc);
         if (threadIdx.x == 0) scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
@@ -328,34 +377,82 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks
     }
 }
 
-__global__ void __launch_bounds__(kBlockThreads) k_hub_argmax(int nhub, const int32_t *hubs, const long long *hoff,
-                             const int32_t *hlg, const int32_t *s, long long m,
-                             const int32_t *root, const int32_t *sigma, int *tkeys, int *tvals,
-                             int32_t *best, long long *gain, int32_t *kown,
-                             unsigned long long *ncand) {
-    unsigned cand = 0;
-    for (int h = blockIdx.x; h < nhub; h += gridDim.x) {
-        const int i = hubs[h];
+// one block per slice of kHubSlice slots of a hub table: partial (own
+// weight, best score, best community), and the slots are reset
+__global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunks, int ntchunk, const int32_t *hubs,
+                             const long long *hoff, const int32_t *hlg, const int32_t *s,
+                             long long m, const int32_t *root, const int32_t *sigma, int *tkeys,
+                             int *tvals, long long *part_own, long long *part_sc,
+                             int32_t *part_cc) {
+    constexpr int B = kHubSlice / kBlockThreads;
+    for (int tc = blockIdx.x; tc < ntchunk; tc += gridDim.x) {
+        const int2 d = tchunks[tc];  // (hub index, first slot)
+        const int i = hubs[d.x];
         const int ci = root[i], si = s[i];
-        const int cap = 1 << hlg[h];
-        int *keys = tkeys + hoff[h], *vals = tvals + hoff[h];
+        const int cap = 1 << hlg[d.x];
+        int *keys = tkeys + hoff[d.x], *vals = tvals + hoff[d.x];
+        int kk[B], vv[B], sg[B];
+#pragma unroll
+        for (int t = 0; t < B; t++) {
+            int k = d.y + threadIdx.x + t * kBlockThreads;
+            kk[t] = k < cap ? keys[k] : -1;
+        }
+#pragma unroll
+        for (int t = 0; t < B; t++) {
+            int k = d.y + threadIdx.x + t * kBlockThreads;
+            vv[t] = kk[t] >= 0 ? vals[k] : 0;
+            sg[t] = (kk[t] >= 0 && kk[t] != ci) ? sigma[kk[t]] : 0;
+        }
         long long own = 0, sc = LLONG_MIN;
         int cc = INT_MAX;
-        for (int k = threadIdx.x; k < cap; k += blockDim.x) {
-            int c = keys[k];
+#pragma unroll
+        for (int t = 0; t < B; t++) {
+            int c = kk[t];
             if (c < 0) continue;
-            int v = vals[k];
+            int k = d.y + threadIdx.x + t * kBlockThreads;
             keys[k] = -1;  // leave the table empty for the next sweep
             vals[k] = 0;
-            if (c == ci) { own = v; continue; }
-            long long x = m * (long long)v - (long long)si * (long long)sigma[c];
+            if (c == ci) { own = vv[t]; continue; }
+            long long x = m * (long long)vv[t] - (long long)si * (long long)sg[t];
             if (better(x, c, sc, cc)) { sc = x; cc = c; }
         }
         block_reduce_best(own, sc, cc);
-        if (threadIdx.x == 0) scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
-        __syncthreads();
+        if (threadIdx.x == 0) {
+            part_own[tc] = own;
+            part_sc[tc] = sc;
+            part_cc[tc] = cc;
+        }
     }
-    if (threadIdx.x == 0 && cand) atomicAdd(ncand, (unsigned long long)cand);
+}
+
+// one warp per hub: reduce the slices' partials and decide
+__global__ void k_hub_finish(int nhub, const int32_t *hubs, const int32_t *tc_off, const int32_t *s,
+                             long long m, const int32_t *root, const int32_t *sigma,
+                             const long long *part_own, const long long *part_sc,
+                             const int32_t *part_cc, int32_t *best, long long *gain,
+                             int32_t *kown, unsigned long long *ncand) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned cand = 0;
+    for (long long h = warp; h < nhub; h += nwarps) {
+        const int i = hubs[h];
+        long long own = 0, sc = LLONG_MIN;
+        int cc = INT_MAX;
+        for (int t = tc_off[h] + lane; t < tc_off[h + 1]; t += 32) {
+            own += part_own[t];
+            if (better(part_sc[t], part_cc[t], sc, cc)) { sc = part_sc[t]; cc = part_cc[t]; }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            own += __shfl_xor_sync(FULL, own, o);
+            long long osc = __shfl_xor_sync(FULL, sc, o);
+            int occ = __shfl_xor_sync(FULL, cc, o);
+            if (better(osc, occ, sc, cc)) { sc = osc; cc = occ; }
+        }
+        if (lane == 0) scan_emit(i, root[i], s[i], m, sigma, own, sc, cc, best, gain, kown, cand);
+    }
+    count_add(ncand, cand);
 }
 
 // own-community weight of hubs: chunk partial sums, then the local gain
@@ -587,7 +684,7 @@ void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
                                                    counts.as<int32_t>());
     SLM_LAUNCH_CHECK();
     radix_sort_u32(keys.as<uint32_t>(), order.as<int32_t>(), keys_tmp.as<uint32_t>(),
-                   vals_tmp.as<int32_t>(), n, 3, s);
+                   vals_tmp.as<int32_t>(), n, 4, s);
     int32_t h[kNumBuckets];
     SLM_CUDA(cudaMemcpyAsync(h, counts.get(), sizeof h, cudaMemcpyDeviceToHost, s));
     SLM_CUDA(cudaStreamSynchronize(s));
@@ -604,8 +701,9 @@ void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
         SLM_CUDA(cudaMemcpyAsync(hr.data(), rows.get(), sizeof(int2) * nhub, cudaMemcpyDeviceToHost, s));
         SLM_CUDA(cudaStreamSynchronize(s));
         std::vector<long long> hoff(nhub);
-        std::vector<int32_t> hlg(nhub);
+        std::vector<int32_t> hlg(nhub), tcoff(nhub + 1);
         std::vector<int4> ch;
+        std::vector<int2> tch;
         long long tot = 0;
         for (int k = 0; k < nhub; k++) {
             int deg = hr[k].y - hr[k].x;
@@ -616,7 +714,18 @@ void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
             tot += 1LL << lg;
             for (int p0 = hr[k].x; p0 < hr[k].y; p0 += kHubChunk)
                 ch.push_back(make_int4(k, p0, std::min(p0 + kHubChunk, hr[k].y), 0));
+            tcoff[k] = (int32_t)tch.size();
+            for (long long s0 = 0; s0 < (1LL << lg); s0 += kHubSlice) tch.push_back(make_int2(k, (int)s0));
         }
+        tcoff[nhub] = (int32_t)tch.size();
+        ntchunk = (int32_t)tch.size();
+        tchunks.alloc(sizeof(int2) * tch.size(), s);
+        tc_off.alloc(sizeof(int32_t) * (nhub + 1), s);
+        part_own.alloc(sizeof(long long) * tch.size(), s);
+        part_sc.alloc(sizeof(long long) * tch.size(), s);
+        part_cc.alloc(sizeof(int32_t) * tch.size(), s);
+        SLM_CUDA(cudaMemcpyAsync(tchunks.get(), tch.data(), sizeof(int2) * tch.size(), cudaMemcpyHostToDevice, s));
+        SLM_CUDA(cudaMemcpyAsync(tc_off.get(), tcoff.data(), sizeof(int32_t) * (nhub + 1), cudaMemcpyHostToDevice, s));
         nchunk = (int32_t)ch.size();
         hub_off.alloc(sizeof(long long) * nhub, s);
         hub_lg.alloc(sizeof(int32_t) * nhub, s);
@@ -666,8 +775,8 @@ void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_
         if (c) { k_assign_group<32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
     }
     {
-        int c = bk.off[kBucketHub + 1] - bk.off[kBucketBlock];
-        if (c) { k_assign_block<<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(ord + bk.off[kBucketBlock], c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+        int c = bk.off[kBucketHub + 1] - bk.off[kBucketBlockS];
+        if (c) { k_assign_block<<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
     }
 }
 
@@ -703,15 +812,22 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
             ord + bk.off[kBucketWarpHash], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
     }
-    if (int c = cnt(kBucketBlock)) {
-        size_t smem = sizeof(int) * 2 * kBlockSmemCap;
+    if (int c = cnt(kBucketBlockS)) {
+        constexpr int CAP = 2 * kBlockSmallMaxDeg;
+        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, sizeof(int) * 2 * CAP, st>>>(
+            ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketBlockL)) {
+        constexpr int CAP = 2 * kBlockSmemMaxDeg;
+        const size_t smem = sizeof(int) * 2 * CAP;
         static bool attr_set = false;
         if (!attr_set) {
-            SLM_CUDA(cudaFuncSetAttribute(k_scan_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            SLM_CUDA(cudaFuncSetAttribute(k_scan_block<CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr_set = true;
         }
-        k_scan_block<<<grid_for(c, 1, kNumSMs * 3), kBlockThreads, smem, st>>>(
-            ord + bk.off[kBucketBlock], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 3), kBlockThreads, smem, st>>>(
+            ord + bk.off[kBucketBlockL], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
     }
     if (bk.nhub > 0) {
@@ -720,9 +836,14 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
             bk.chunks.as<int4>(), bk.nchunk, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(),
             col, w, root, bk.tkeys.as<int>(), bk.tvals.as<int>());
         SLM_LAUNCH_CHECK();
-        k_hub_argmax<<<grid_for(bk.nhub, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(
-            bk.nhub, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(), s, m, root, sigma,
-            bk.tkeys.as<int>(), bk.tvals.as<int>(), best, gain, kown, ncand);
+        k_hub_slices<<<grid_for(bk.ntchunk, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(
+            bk.tchunks.as<int2>(), bk.ntchunk, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(),
+            s, m, root, sigma, bk.tkeys.as<int>(), bk.tvals.as<int>(), bk.part_own.as<long long>(),
+            bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>());
+        SLM_LAUNCH_CHECK();
+        k_hub_finish<<<grid_for((long long)bk.nhub * 32, 256), 256, 0, st>>>(
+            bk.nhub, hubs, bk.tc_off.as<int32_t>(), s, m, root, sigma, bk.part_own.as<long long>(),
+            bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>(), best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
     }
 }
@@ -754,8 +875,8 @@ void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const in
         k_own_group<32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
-    if (int c = bk.off[kBucketBlock + 1] - bk.off[kBucketBlock]) {
-        k_own_block<<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(ord + bk.off[kBucketBlock], c, rp, col, w, s, m, root, sigma, kown, flag);
+    if (int c = bk.off[kBucketBlockL + 1] - bk.off[kBucketBlockS]) {
+        k_own_block<<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (bk.nhub > 0) {

@@ -143,9 +143,10 @@ double modularity_from_num(long long num, long long m_w);
 // Degree buckets and the neighbourhood scans (k_scan.cu)
 // ---------------------------------------------------------------------------
 enum { kBucketEmpty = 0, kBucketG4, kBucketG8, kBucketG16, kBucketG32, kBucketWarpHash,
-       kBucketBlock, kBucketHub, kNumBuckets };
+       kBucketBlockS, kBucketBlockL, kBucketHub, kNumBuckets };
 constexpr int kWarpHashMaxDeg = 256;
-constexpr int kBlockSmemMaxDeg = 4096;  // above this a node is a hub
+constexpr int kBlockSmallMaxDeg = 1024; // block shape with a 16 KB table up to here
+constexpr int kBlockSmemMaxDeg = 4096;  // block shape with a 64 KB table up to here; above: hub
 constexpr int kHubChunk = 2048;         // edges of a hub handled by one block
 
 struct Buckets {
@@ -153,8 +154,10 @@ struct Buckets {
     int32_t off[kNumBuckets + 1] = {0}; // host copy of bucket offsets
     // hubs: per hub its global table (offset, log2 capacity), and the chunks
     // (hub index, first edge, end edge) that split its row across blocks
-    int32_t nhub = 0, nchunk = 0;
+    int32_t nhub = 0, nchunk = 0, ntchunk = 0;
     DevBuf hub_off, hub_lg, chunks, tkeys, tvals, hub_acc;
+    // slices of the hub tables read by one block each, and their partial results
+    DevBuf tchunks, tc_off, part_own, part_sc, part_cc;
     void build(int32_t n, const int32_t *rp, cudaStream_t s);
 };
 
