@@ -159,7 +159,9 @@ __global__ void __launch_bounds__(256) k_scan_group(const int32_t *order, int32_
 }
 
 // ---------------------------------------------------------------------------
-// MAXIMAL scan, warp shape: one node per warp, shared-memory table.
+// MAXIMAL scan, warp shape: one node per warp, shared-memory table.  The
+// slots a node occupies are listed as they are claimed, so the decision pass
+// and the reset touch only the distinct communities, not the whole table.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kWarpHashWarps * 32, 4) k_scan_warphash(const int32_t *order, int32_t cnt, const int32_t *rp,
                                 const int32_t *col, const int32_t *w, const int32_t *s,
@@ -167,10 +169,16 @@ __global__ void __launch_bounds__(kWarpHashWarps * 32, 4) k_scan_warphash(const 
                                 int32_t *best, long long *gain, int32_t *kown,
                                 unsigned long long *ncand) {
     __shared__ int tab[kWarpHashWarps][2 * kWarpHashCap];
+    __shared__ unsigned short used[kWarpHashWarps][kWarpHashMaxDeg];
+    __shared__ int nused[kWarpHashWarps];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *keys = tab[wib], *vals = tab[wib] + kWarpHashCap;
+    unsigned short *ul = used[wib];
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (int k = lane; k < kWarpHashCap; k += 32) { keys[k] = -1; vals[k] = 0; }
+    if (lane == 0) nused[wib] = 0;
+    __syncwarp();
     unsigned cand = 0;
     for (long long idx = warp; idx < cnt; idx += nwarps) {
         int i = order[idx];
@@ -178,7 +186,6 @@ __global__ void __launch_bounds__(kWarpHashWarps * 32, 4) k_scan_warphash(const 
         int ci = root[i], si = s[i];
         int lg = ilog2_pow2_at_least(2 * deg);
         int cap = 1 << lg;
-        for (int k = lane; k < cap; k += 32) { keys[k] = -1; vals[k] = 0; }
         // every lane fetches its (at most 8) edges and their communities before
         // inserting, so the loads overlap instead of waiting one by one
         int cv[kWarpHashMaxDeg / 32], wv[kWarpHashMaxDeg / 32];
@@ -191,35 +198,28 @@ __global__ void __launch_bounds__(kWarpHashWarps * 32, 4) k_scan_warphash(const 
         }
 #pragma unroll
         for (int t = 0; t < kWarpHashMaxDeg / 32; t++) cv[t] = (cv[t] >= 0 && cv[t] != i) ? root[cv[t]] : -1;
-        __syncwarp();
 #pragma unroll
         for (int t = 0; t < kWarpHashMaxDeg / 32; t++) {
             if (cv[t] < 0) continue;
             unsigned h = hash_slot(cv[t], lg);
             for (;;) {
                 int prev = atomicCAS(&keys[h], -1, cv[t]);
+                if (prev == -1) ul[atomicAdd(&nused[wib], 1)] = (unsigned short)h;
                 if (prev == -1 || prev == cv[t]) { atomicAdd(&vals[h], wv[t]); break; }
                 h = (h + 1) & (cap - 1);
             }
         }
         __syncwarp();
+        const int nu = nused[wib];
         long long own = 0, sc = LLONG_MIN;
         int cc = INT_MAX;
-        int kk[kWarpHashCap / 32], sg[kWarpHashCap / 32];
-#pragma unroll
-        for (int t = 0; t < kWarpHashCap / 32; t++) {
-            int k = lane + 32 * t;
-            kk[t] = k < cap ? keys[k] : -1;
-        }
-#pragma unroll
-        for (int t = 0; t < kWarpHashCap / 32; t++) sg[t] = (kk[t] >= 0 && kk[t] != ci) ? sigma[kk[t]] : 0;
-#pragma unroll
-        for (int t = 0; t < kWarpHashCap / 32; t++) {
-            int c = kk[t];
-            if (c < 0) continue;
-            int v = vals[lane + 32 * t];
+        for (int k = lane; k < nu; k += 32) {
+            int h = ul[k];
+            int c = keys[h], v = vals[h];
+            keys[h] = -1;  // leave the table empty for the next node
+            vals[h] = 0;
             if (c == ci) { own = v; continue; }
-            long long x = m * (long long)v - (long long)si * (long long)sg[t];
+            long long x = m * (long long)v - (long long)si * (long long)sigma[c];
             if (better(x, c, sc, cc)) { sc = x; cc = c; }
         }
 #pragma unroll
@@ -229,7 +229,10 @@ __global__ void __launch_bounds__(kWarpHashWarps * 32, 4) k_scan_warphash(const 
             int occ = __shfl_xor_sync(FULL, cc, o);
             if (better(osc, occ, sc, cc)) { sc = osc; cc = occ; }
         }
-        if (lane == 0) scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
+        if (lane == 0) {
+            scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
+            nused[wib] = 0;
+        }
         __syncwarp();
     }
     count_add(ncand, cand);
@@ -266,15 +269,27 @@ __device__ void block_reduce_best(long long &own, long long &sc, int &cc) {
 
 // ---------------------------------------------------------------------------
 // MAXIMAL scan, block shape: one node per block, table of CAP slots in
-// shared memory; every thread fetches its edges in batches of 8.
+// shared memory followed by the list of occupied slots; every thread fetches
+// its edges in batches of 8.
 // ---------------------------------------------------------------------------
+template <int CAP>
+constexpr size_t block_smem_bytes() {
+    return sizeof(int) * 2 * CAP + sizeof(unsigned short) * (CAP / 2) + 16;
+}
+
 template <int CAP>
 __global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *order, int32_t cnt, const int32_t *rp,
                              const int32_t *col, const int32_t *w, const int32_t *s, long long m,
                              const int32_t *root, const int32_t *sigma, int32_t *best,
                              long long *gain, int32_t *kown, unsigned long long *ncand) {
     extern __shared__ int sm[];
+    int *keys = sm, *vals = sm + CAP;
+    unsigned short *ul = reinterpret_cast<unsigned short *>(sm + 2 * CAP);
+    int *nused = reinterpret_cast<int *>(ul + CAP / 2);
     constexpr int B = 8;
+    for (int k = threadIdx.x; k < CAP; k += blockDim.x) { keys[k] = -1; vals[k] = 0; }
+    if (threadIdx.x == 0) *nused = 0;
+    __syncthreads();
     unsigned cand = 0;
     for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
         int i = order[idx];
@@ -283,9 +298,6 @@ __global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *ord
         int ci = root[i], si = s[i];
         int lg = ilog2_pow2_at_least(2 * deg);
         int cap = 1 << lg;  // <= CAP because deg <= CAP / 2
-        int *keys = sm, *vals = sm + cap;
-        for (int k = threadIdx.x; k < cap; k += blockDim.x) { keys[k] = -1; vals[k] = 0; }
-        __syncthreads();
         for (int p0 = start + threadIdx.x; p0 < end; p0 += B * blockDim.x) {
             int cv[B], wv[B];
 #pragma unroll
@@ -303,35 +315,30 @@ __global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *ord
                 unsigned h = hash_slot(cv[t], lg);
                 for (;;) {
                     int prev = atomicCAS(&keys[h], -1, cv[t]);
+                    if (prev == -1) ul[atomicAdd(nused, 1)] = (unsigned short)h;
                     if (prev == -1 || prev == cv[t]) { atomicAdd(&vals[h], wv[t]); break; }
                     h = (h + 1) & (cap - 1);
                 }
             }
         }
         __syncthreads();
+        const int nu = *nused;
         long long own = 0, sc = LLONG_MIN;
         int cc = INT_MAX;
-        for (int k0 = threadIdx.x; k0 < cap; k0 += B * blockDim.x) {
-            int kk[B], sg[B];
-#pragma unroll
-            for (int t = 0; t < B; t++) {
-                int k = k0 + t * blockDim.x;
-                kk[t] = k < cap ? keys[k] : -1;
-            }
-#pragma unroll
-            for (int t = 0; t < B; t++) sg[t] = (kk[t] >= 0 && kk[t] != ci) ? sigma[kk[t]] : 0;
-#pragma unroll
-            for (int t = 0; t < B; t++) {
-                int c = kk[t];
-                if (c < 0) continue;
-                int v = vals[k0 + t * blockDim.x];
-                if (c == ci) { own = v; continue; }
-                long long x = m * (long long)v - (long long)si * (long long)sg[t];
-                if (better(x, c, sc, cc)) { sc = x; cc = c; }
-            }
+        for (int k = threadIdx.x; k < nu; k += blockDim.x) {
+            int h = ul[k];
+            int c = keys[h], v = vals[h];
+            keys[h] = -1;  // leave the table empty for the next node
+            vals[h] = 0;
+            if (c == ci) { own = v; continue; }
+            long long x = m * (long long)v - (long long)si * (long long)sigma[c];
+            if (better(x, c, sc, cc)) { sc = x; cc = c; }
         }
         block_reduce_best(own, sc, cc);
-        if (threadIdx.x == 0) scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
+        if (threadIdx.x == 0) {
+            scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
+            *nused = 0;
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0 && cand) atomicAdd(ncand, (unsigned long long)cand);
@@ -814,13 +821,13 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
     }
     if (int c = cnt(kBucketBlockS)) {
         constexpr int CAP = 2 * kBlockSmallMaxDeg;
-        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, sizeof(int) * 2 * CAP, st>>>(
+        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, block_smem_bytes<CAP>(), st>>>(
             ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
     }
     if (int c = cnt(kBucketBlockL)) {
         constexpr int CAP = 2 * kBlockSmemMaxDeg;
-        const size_t smem = sizeof(int) * 2 * CAP;
+        const size_t smem = block_smem_bytes<CAP>();
         static bool attr_set = false;
         if (!attr_set) {
             SLM_CUDA(cudaFuncSetAttribute(k_scan_block<CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
