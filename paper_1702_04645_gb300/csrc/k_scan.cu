@@ -17,6 +17,7 @@
 // Every reduction compares (score desc, name asc), so the result does not
 // depend on the order in which lanes or blocks finish.
 #include <algorithm>
+#include <mutex>
 #include <climits>
 
 #include "slm_internal.cuh"
@@ -668,6 +669,33 @@ __global__ void k_local_gain(int32_t n, const int32_t *s, long long m, const int
     }
 }
 
+// Side streams on which the independent bucket kernels of one scan overlap
+// (created once per device; the scan forks to them and joins back with events).
+struct SideStreams {
+    static constexpr int kN = 3;
+    cudaStream_t s[kN] = {};
+    cudaEvent_t fork = nullptr, join[kN] = {};
+};
+
+SideStreams &side_streams() {
+    static std::mutex mu;
+    static SideStreams per_dev[64];
+    static bool made[64] = {false};
+    int dev = 0;
+    SLM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    SideStreams &ss = per_dev[dev & 63];
+    if (!made[dev & 63]) {
+        for (int k = 0; k < SideStreams::kN; k++) {
+            SLM_CUDA(cudaStreamCreateWithFlags(&ss.s[k], cudaStreamNonBlocking));
+            SLM_CUDA(cudaEventCreateWithFlags(&ss.join[k], cudaEventDisableTiming));
+        }
+        SLM_CUDA(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+        made[dev & 63] = true;
+    }
+    return ss;
+}
+
 }  // namespace
 
 void local_gain_nodes(int32_t n, const int32_t *s, long long m, const int32_t *root,
@@ -794,37 +822,11 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
     if (n <= 0) return;
     const int32_t *ord = bk.order.as<int32_t>();
     auto cnt = [&](int b) { return bk.off[b + 1] - bk.off[b]; };
-    if (int c = cnt(kBucketEmpty)) {
-        k_scan_empty<<<grid_for(c, 256), 256, 0, st>>>(ord + bk.off[kBucketEmpty], c, root, best, gain, kown);
-        SLM_LAUNCH_CHECK();
-    }
-    if (int c = cnt(kBucketG4)) {
-        k_scan_group<4><<<blocks_for_groups(c, 8), 256, 0, st>>>(ord + bk.off[kBucketG4], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-    }
-    if (int c = cnt(kBucketG8)) {
-        k_scan_group<8><<<blocks_for_groups(c, 4), 256, 0, st>>>(ord + bk.off[kBucketG8], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-    }
-    if (int c = cnt(kBucketG16)) {
-        k_scan_group<16><<<blocks_for_groups(c, 2), 256, 0, st>>>(ord + bk.off[kBucketG16], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-    }
-    if (int c = cnt(kBucketG32)) {
-        k_scan_group<32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-    }
-    if (int c = cnt(kBucketWarpHash)) {
-        k_scan_warphash<<<grid_for((long long)c * 32, kWarpHashWarps * 32, kNumSMs * 8), kWarpHashWarps * 32, 0, st>>>(
-            ord + bk.off[kBucketWarpHash], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-    }
-    if (int c = cnt(kBucketBlockS)) {
-        constexpr int CAP = 2 * kBlockSmallMaxDeg;
-        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, block_smem_bytes<CAP>(), st>>>(
-            ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-    }
+    // the buckets write disjoint nodes: run them side by side
+    SideStreams &ss = side_streams();
+    SLM_CUDA(cudaEventRecord(ss.fork, st));
+    for (int k = 0; k < SideStreams::kN; k++) SLM_CUDA(cudaStreamWaitEvent(ss.s[k], ss.fork, 0));
+    cudaStream_t s0 = st, s1 = ss.s[0], s2 = ss.s[1], s3 = ss.s[2];
     if (int c = cnt(kBucketBlockL)) {
         constexpr int CAP = 2 * kBlockSmemMaxDeg;
         const size_t smem = block_smem_bytes<CAP>();
@@ -833,25 +835,60 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
             SLM_CUDA(cudaFuncSetAttribute(k_scan_block<CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr_set = true;
         }
-        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 3), kBlockThreads, smem, st>>>(
+        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 3), kBlockThreads, smem, s0>>>(
             ord + bk.off[kBucketBlockL], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketWarpHash)) {
+        k_scan_warphash<<<grid_for((long long)c * 32, kWarpHashWarps * 32, kNumSMs * 8), kWarpHashWarps * 32, 0, s1>>>(
+            ord + bk.off[kBucketWarpHash], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
     }
     if (bk.nhub > 0) {
         const int32_t *hubs = ord + bk.off[kBucketHub];
-        k_hub_insert<<<grid_for(bk.nchunk, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(
+        k_hub_insert<<<grid_for(bk.nchunk, 1, kNumSMs * 8), kBlockThreads, 0, s3>>>(
             bk.chunks.as<int4>(), bk.nchunk, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(),
             col, w, root, bk.tkeys.as<int>(), bk.tvals.as<int>());
         SLM_LAUNCH_CHECK();
-        k_hub_slices<<<grid_for(bk.ntchunk, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(
+        k_hub_slices<<<grid_for(bk.ntchunk, 1, kNumSMs * 8), kBlockThreads, 0, s3>>>(
             bk.tchunks.as<int2>(), bk.ntchunk, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(),
             s, m, root, sigma, bk.tkeys.as<int>(), bk.tvals.as<int>(), bk.part_own.as<long long>(),
             bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>());
         SLM_LAUNCH_CHECK();
-        k_hub_finish<<<grid_for((long long)bk.nhub * 32, 256), 256, 0, st>>>(
+        k_hub_finish<<<grid_for((long long)bk.nhub * 32, 256), 256, 0, s3>>>(
             bk.nhub, hubs, bk.tc_off.as<int32_t>(), s, m, root, sigma, bk.part_own.as<long long>(),
             bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>(), best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketBlockS)) {
+        constexpr int CAP = 2 * kBlockSmallMaxDeg;
+        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, block_smem_bytes<CAP>(), s2>>>(
+            ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketG16)) {
+        k_scan_group<16><<<blocks_for_groups(c, 2), 256, 0, s2>>>(ord + bk.off[kBucketG16], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketG32)) {
+        k_scan_group<32><<<blocks_for_groups(c, 1), 256, 0, s2>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketG4)) {
+        k_scan_group<4><<<blocks_for_groups(c, 8), 256, 0, s3>>>(ord + bk.off[kBucketG4], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketG8)) {
+        k_scan_group<8><<<blocks_for_groups(c, 4), 256, 0, s3>>>(ord + bk.off[kBucketG8], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketEmpty)) {
+        k_scan_empty<<<grid_for(c, 256), 256, 0, s1>>>(ord + bk.off[kBucketEmpty], c, root, best, gain, kown);
+        SLM_LAUNCH_CHECK();
+    }
+    for (int k = 0; k < SideStreams::kN; k++) {
+        SLM_CUDA(cudaEventRecord(ss.join[k], ss.s[k]));
+        SLM_CUDA(cudaStreamWaitEvent(st, ss.join[k], 0));
     }
 }
 
