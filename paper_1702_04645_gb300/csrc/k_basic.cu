@@ -81,7 +81,7 @@ template <class T> __device__ T block_exclusive_scan(T v, T *total) {
     return warp_off + x - v;
 }
 
-template <class T> __global__ void k_scan_reduce(const T *in, long long n, T *tile_sums) {
+template <class T> __global__ void k_psum_reduce(const T *in, long long n, T *tile_sums) {
     long long base = (long long)blockIdx.x * kScanTile;
     T acc = 0;
     for (int k = 0; k < kScanItems; k++) {
@@ -94,7 +94,7 @@ template <class T> __global__ void k_scan_reduce(const T *in, long long n, T *ti
 }
 
 template <class T>
-__global__ void k_scan_tile(const T *in, T *out, long long n, const T *tile_off) {
+__global__ void k_psum_tile(const T *in, T *out, long long n, const T *tile_off) {
     __shared__ T buf[kScanTile];
     long long base = (long long)blockIdx.x * kScanTile;
     for (int k = 0; k < kScanItems; k++) {
@@ -122,7 +122,7 @@ __global__ void k_scan_tile(const T *in, T *out, long long n, const T *tile_off)
 }
 
 template <class T>
-__global__ void k_scan_total(const T *last_in, const T *out, long long n, T *total) {
+__global__ void k_psum_total(const T *last_in, const T *out, long long n, T *total) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *total = out[n - 1] + *last_in;
 }
 
@@ -140,19 +140,19 @@ static void scan_impl(const T *in, T *out, long long n, T *total_dev, cudaStream
         SLM_CUDA(cudaMemcpyAsync(last.get(), in + n - 1, sizeof(T), cudaMemcpyDeviceToDevice, s));
     }
     if (tiles == 1) {
-        k_scan_tile<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+        k_psum_tile<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
         SLM_LAUNCH_CHECK();
     } else {
         DevBuf sums(tiles * sizeof(T), s);
-        k_scan_reduce<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<T>());
+        k_psum_reduce<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<T>());
         SLM_LAUNCH_CHECK();
         scan_impl<T>(sums.as<T>(), sums.as<T>(), tiles, nullptr, s);
-        k_scan_tile<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums.as<T>());
+        k_psum_tile<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums.as<T>());
         SLM_LAUNCH_CHECK();
     }
     if (total_dev) {
         const T *src_last = (in == out) ? last.as<T>() : in + n - 1;
-        k_scan_total<T><<<1, 32, 0, s>>>(src_last, out, n, total_dev);
+        k_psum_total<T><<<1, 32, 0, s>>>(src_last, out, n, total_dev);
         SLM_LAUNCH_CHECK();
     }
 }
