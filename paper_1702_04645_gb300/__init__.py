@@ -18,7 +18,7 @@ import numpy as np
 
 from .build_lib import LIB, build  # noqa: F401
 
-__all__ = ["Graph", "Options", "LevelStats", "SlmError", "build", "load", "step_strengths",
+__all__ = ["Graph", "Batch", "pack_forest", "Options", "LevelStats", "SlmError", "build", "load", "step_strengths",
            "step_assign", "step_components", "step_scan", "step_branch_gain", "step_maximal",
            "step_positive", "step_compact", "step_aggregate", "step_modularity",
            "FLAG_NO_POSITIVE", "FLAG_STRICT", "P_HALF", "P_ALWAYS"]
@@ -45,7 +45,10 @@ EXPORTS = ["slm_default_options", "slm_create_graph", "slm_run", "slm_num_levels
            "slm_step_assign", "slm_step_components", "slm_step_scan", "slm_step_branch_gain",
            "slm_step_maximal", "slm_step_positive", "slm_step_compact", "slm_step_aggregate",
            "slm_step_modularity", "slm_get_trace", "slm_get_timing", "slm_launch_count",
-           "slm_step_modularity_noalloc"]
+           "slm_step_modularity_noalloc", "slm_batch_create", "slm_batch_run",
+           "slm_batch_num_graphs", "slm_batch_num_levels", "slm_batch_get_partition",
+           "slm_batch_modularity", "slm_batch_get_stats", "slm_batch_run_info",
+           "slm_batch_destroy", "slm_batch_last_error"]
 
 
 def launch_count() -> int:
@@ -118,6 +121,16 @@ def load():
             "slm_step_modularity": (C.c_int, [i32, vp, vp, vp, vp, C.POINTER(C.c_double),
                                               C.POINTER(i64), vp]),
             "slm_step_modularity_noalloc": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, vp]),
+            "slm_batch_create": (C.c_int, [i32, vp, vp, vp, vp, vp, C.c_int, vp, C.POINTER(vp)]),
+            "slm_batch_run": (C.c_int, [vp, C.POINTER(Options), vp]),
+            "slm_batch_num_graphs": (C.c_int, [vp, C.POINTER(i32)]),
+            "slm_batch_num_levels": (C.c_int, [vp, i32, C.POINTER(i32)]),
+            "slm_batch_get_partition": (C.c_int, [vp, i32, i32, vp, C.POINTER(i32)]),
+            "slm_batch_modularity": (C.c_int, [vp, i32, C.POINTER(C.c_double)]),
+            "slm_batch_get_stats": (C.c_int, [vp, i32, i32, C.POINTER(LevelStats)]),
+            "slm_batch_run_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i64)]),
+            "slm_batch_destroy": (None, [vp]),
+            "slm_batch_last_error": (C.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -278,6 +291,109 @@ class Graph:
         _check(lib.slm_get_trace(self._h, C.c_void_p(out.ctypes.data), ln.value, C.byref(ln)),
                self._h)
         return out[: ln.value]
+
+
+# ---------------------------------------------------------------------------
+# Batched API: a forest of independent graphs in one run
+# ---------------------------------------------------------------------------
+def pack_forest(graphs):
+    """Concatenate CSR graphs (objects with n, row_ptr, col, w) into one
+    block-diagonal CSR; returns (graph_off, row_ptr, col, w) numpy arrays."""
+    goff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for k, g in enumerate(graphs):
+        goff[k + 1] = goff[k] + g.n
+    nnz = sum(int(g.row_ptr[-1]) for g in graphs)
+    rp = np.zeros(int(goff[-1]) + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    w = np.zeros(nnz, dtype=np.int32)
+    e = 0
+    for k, g in enumerate(graphs):
+        gr = np.asarray(g.row_ptr, dtype=np.int64)
+        rp[goff[k] + 1: goff[k + 1] + 1] = gr[1:] + e
+        m = int(gr[-1])
+        col[e:e + m] = np.asarray(g.col, dtype=np.int64) + goff[k]
+        w[e:e + m] = g.w
+        e += m
+    if e >= 2**31 or goff[-1] >= 2**31:
+        raise ValueError("forest too large for int32 CSR")
+    return goff.astype(np.int32), rp.astype(np.int32), col, w
+
+
+class Batch:
+    """Many graphs run together (include/slm_batch.h)."""
+
+    def __init__(self, graphs=None, *, graph_off=None, row_ptr=None, col=None, w=None,
+                 seeds=None, stream=None):
+        lib = load()
+        if graphs is not None:
+            graph_off, row_ptr, col, w = pack_forest(graphs)
+        goff = np.ascontiguousarray(graph_off, dtype=np.int32)
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        ww = None if w is None else np.ascontiguousarray(w, dtype=np.int32)
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+        self.G = len(goff) - 1
+        self.goff = goff
+        self._h = C.c_void_p()
+        st = C.c_void_p(int(stream)) if stream is not None else C.c_void_p(0)
+        ptr = lambda a: C.c_void_p(a.ctypes.data) if a is not None and a.size else C.c_void_p(0)  # noqa: E731
+        rc = lib.slm_batch_create(self.G, ptr(goff), ptr(rp), ptr(cl), ptr(ww), ptr(sd), SLM_HOST,
+                                  st, C.byref(self._h))
+        if rc != 0:
+            msg = lib.slm_batch_last_error(None)
+            raise SlmError(rc, msg.decode() if msg else "")
+
+    def _check(self, rc):
+        if rc != 0:
+            msg = load().slm_batch_last_error(self._h)
+            raise SlmError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().slm_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, seed: int = 1, accept_p32: int = P_HALF, max_sweeps: int = 1000,
+            max_levels: int = 64, flags: int = 0, stream=None):
+        o = Options(seed, accept_p32, max_sweeps, max_levels, flags)
+        st = C.c_void_p(int(stream)) if stream is not None else C.c_void_p(0)
+        self._check(load().slm_batch_run(self._h, C.byref(o), st))
+        return self
+
+    def num_levels(self, g: int) -> int:
+        v = C.c_int32()
+        self._check(load().slm_batch_num_levels(self._h, g, C.byref(v)))
+        return v.value
+
+    def stats(self, g: int, level: int) -> LevelStats:
+        s = LevelStats()
+        self._check(load().slm_batch_get_stats(self._h, g, level, C.byref(s)))
+        return s
+
+    def partition(self, g: int, level: int = -1):
+        n = int(self.goff[g + 1] - self.goff[g]) if level == -1 else self.stats(g, level).n
+        out = np.zeros(max(n, 1), dtype=np.int32)
+        K = C.c_int32()
+        self._check(load().slm_batch_get_partition(self._h, g, level, C.c_void_p(out.ctypes.data),
+                                                   C.byref(K)))
+        return out[:n], K.value
+
+    def modularity(self, g: int) -> float:
+        q = C.c_double()
+        self._check(load().slm_batch_modularity(self._h, g, C.byref(q)))
+        return q.value
+
+    def run_info(self):
+        lv = C.c_int32()
+        sw = C.c_int64()
+        self._check(load().slm_batch_run_info(self._h, C.byref(lv), C.byref(sw)))
+        return lv.value, sw.value
 
 
 # ---------------------------------------------------------------------------

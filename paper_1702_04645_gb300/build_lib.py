@@ -60,7 +60,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             list(ex.map(run, jobs))
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+        # -z defs: every symbol the library uses must be defined in it or in a
+        # linked library, so a declaration without a definition fails here
+        run([nvcc, *ARCH, "-shared", "-Xlinker", "-z,defs", "-o", tmp, *objs])
         os.replace(tmp, LIB)
     return LIB
 

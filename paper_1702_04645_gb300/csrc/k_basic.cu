@@ -405,4 +405,142 @@ double modularity_from_num(long long num, long long m_w) {
     return (double)num / ((double)m_w * (double)m_w);
 }
 
+// ---------------------------------------------------------------------------
+// Forests of graphs: one block-diagonal CSR, node ranges per graph.
+// ---------------------------------------------------------------------------
+__global__ void k_gid(int32_t n, const int32_t *goff, int32_t G, int32_t *gid) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = G - 1;  // last g with goff[g] <= v
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (goff[mid] <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        gid[v] = lo;
+    }
+}
+
+void graph_of_nodes(int32_t n, const int32_t *goff, int32_t G, int32_t *gid, cudaStream_t st) {
+    if (n <= 0 || G <= 0) return;
+    k_gid<<<grid_for(n, 256), 256, 0, st>>>(n, goff, G, gid);
+    SLM_LAUNCH_CHECK();
+}
+
+__global__ void k_forest_check(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *s,
+                               const int32_t *gid, unsigned long long *mg,
+                               unsigned long long *cross) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = warp; u < n; u += nwarps) {
+        const int g = gid[u];
+        unsigned c = 0;
+        for (int p = rp[u] + lane; p < rp[u + 1]; p += 32) c += gid[col[p]] != g;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) {
+            if (c) atomicAdd(cross, (unsigned long long)c);
+            if (s[u]) atomicAdd(&mg[g], (unsigned long long)s[u]);
+        }
+    }
+}
+
+long long forest_check_and_weights(int32_t n, const int32_t *rp, const int32_t *col,
+                                   const int32_t *s, const int32_t *gid, int32_t G,
+                                   long long *mg, cudaStream_t st) {
+    DevBuf cross(8, st);
+    SLM_CUDA(cudaMemsetAsync(cross.get(), 0, 8, st));
+    SLM_CUDA(cudaMemsetAsync(mg, 0, 8 * (size_t)G, st));
+    if (n > 0) {
+        k_forest_check<<<grid_for((long long)n * 32, 256), 256, 0, st>>>(
+            n, rp, col, s, gid, reinterpret_cast<unsigned long long *>(mg), cross.as<unsigned long long>());
+        SLM_LAUNCH_CHECK();
+    }
+    unsigned long long h = 0;
+    SLM_CUDA(cudaMemcpyAsync(&h, cross.get(), 8, cudaMemcpyDeviceToHost, st));
+    SLM_CUDA(cudaStreamSynchronize(st));
+    return (long long)h;
+}
+
+__global__ void k_roots_per_graph(int32_t n, const int32_t *root, const int32_t *gid, int32_t *Kg) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x)
+        if (root[v] == v) atomicAdd(&Kg[gid[v]], 1);
+}
+
+void roots_per_graph(int32_t n, const int32_t *root, const int32_t *gid, int32_t *Kg,
+                     cudaStream_t st) {
+    if (n <= 0) return;
+    k_roots_per_graph<<<grid_for(n, 256), 256, 0, st>>>(n, root, gid, Kg);
+    SLM_LAUNCH_CHECK();
+}
+
+__global__ void k_cands_per_graph(int32_t n, const int32_t *gid, const int32_t *active,
+                                  long long *gain, int32_t *cand_g) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        if (gain[v] <= 0) continue;
+        const int g = gid[v];
+        if (!active[g]) gain[v] = 0;  // a graph that stopped keeps its partition
+        else atomicAdd(&cand_g[g], 1);
+    }
+}
+
+void candidates_per_graph(int32_t n, const int32_t *gid, const int32_t *active, long long *gain,
+                          int32_t *cand_g, cudaStream_t st) {
+    if (n <= 0) return;
+    k_cands_per_graph<<<grid_for(n, 256), 256, 0, st>>>(n, gid, active, gain, cand_g);
+    SLM_LAUNCH_CHECK();
+}
+
+__global__ void k_modf_reduce(int32_t nlab, const unsigned long long *win,
+                              const unsigned long long *sig, const int32_t *loff, int32_t G,
+                              const long long *mg, unsigned long long *a, unsigned long long *b) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nlab;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (!win[c] && !sig[c]) continue;
+        int lo = 0, hi = G - 1;  // graph owning label c
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (loff[mid] <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        if (win[c]) atomicAdd(&a[lo], (unsigned long long)mg[lo] * win[c]);
+        if (sig[c]) atomicAdd(&b[lo], sig[c] * sig[c]);
+    }
+}
+
+__global__ void k_modf_finish(int32_t G, const unsigned long long *a, const unsigned long long *b,
+                              long long *nums) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+        nums[g] = (long long)a[g] - (long long)b[g];
+}
+
+void modularity_forest(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                       const int32_t *labels, int32_t nlab, const int32_t *gid,
+                       const int32_t *loff, int32_t G, const long long *mg, long long *nums,
+                       cudaStream_t st) {
+    (void)gid;
+    if (G <= 0) return;
+    const size_t L = (size_t)(nlab > 0 ? nlab : 1);
+    DevBuf win(8 * L, st), sig(8 * L, st), a(8 * (size_t)G, st), b(8 * (size_t)G, st);
+    SLM_CUDA(cudaMemsetAsync(win.get(), 0, 8 * L, st));
+    SLM_CUDA(cudaMemsetAsync(sig.get(), 0, 8 * L, st));
+    SLM_CUDA(cudaMemsetAsync(a.get(), 0, 8 * (size_t)G, st));
+    SLM_CUDA(cudaMemsetAsync(b.get(), 0, 8 * (size_t)G, st));
+    if (n > 0) {
+        k_mod_accumulate<<<grid_for((long long)n * 32, 256), 256, 0, st>>>(
+            n, rp, col, w, labels, win.as<unsigned long long>(), sig.as<unsigned long long>());
+        SLM_LAUNCH_CHECK();
+        k_modf_reduce<<<grid_for(nlab, 256), 256, 0, st>>>(
+            nlab, win.as<unsigned long long>(), sig.as<unsigned long long>(), loff, G, mg,
+            a.as<unsigned long long>(), b.as<unsigned long long>());
+        SLM_LAUNCH_CHECK();
+    }
+    k_modf_finish<<<grid_for(G, 256), 256, 0, st>>>(G, a.as<unsigned long long>(),
+                                                    b.as<unsigned long long>(), nums);
+    SLM_LAUNCH_CHECK();
+}
+
 }  // namespace slm

@@ -228,10 +228,11 @@ __global__ void k_edges_cycle(int32_t n, const int32_t *rp, const int32_t *col, 
 
 __global__ void k_bg_final(int32_t n, const int32_t *a, const uint8_t *oncycle,
                            const int32_t *root, const int32_t *haschild, const int32_t *sigma,
-                           const int32_t *best, const long long *gain, long long m,
+                           const int32_t *best, const long long *gain, MParam mp,
                            const long long *subS, const long long *subWA, const long long *subWin,
                            const long long *WB, long long *bg) {
     GRID_STRIDE(i, n) {
+        const long long m = mp.of((int)i);
         int k = cand_kind((int)i, a, oncycle, haschild, gain);
         long long r = 0;
         long long sA = sigma[root[i]], sB = sigma[best[i]];
@@ -246,14 +247,21 @@ __global__ void k_bg_final(int32_t n, const int32_t *a, const uint8_t *oncycle,
     }
 }
 
-__global__ void k_accept(int32_t n, const long long *bg, unsigned long long seed,
-                         unsigned long long P, int level, int sweep, int32_t *list, int32_t *cnt,
-                         unsigned long long *npos) {
+__global__ void k_accept(int32_t n, const long long *bg, RngParam rng, unsigned long long P,
+                         int level, int sweep, int32_t *list, int32_t *cnt,
+                         unsigned long long *npos, const int32_t *active, int32_t *per_graph) {
     unsigned loc = 0;
     GRID_STRIDE(i, n) {
         if (bg[i] <= 0) continue;
+        const int g = rng.gid ? rng.gid[i] : 0;
+        if (active && !active[g]) continue;
         loc++;
-        if ((unsigned long long)accept_draw(seed, level, sweep, (int)i) < P) list[atomicAdd(cnt, 1)] = (int)i;
+        bool acc = (unsigned long long)accept_draw(rng.seed_of((int)i), level, sweep, rng.local((int)i)) < P;
+        if (per_graph) {
+            atomicAdd(&per_graph[2 * g], 1);
+            if (acc) atomicAdd(&per_graph[2 * g + 1], 1);
+        }
+        if (acc) list[atomicAdd(cnt, 1)] = (int)i;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) loc += __shfl_xor_sync(FULL, loc, o);
@@ -307,7 +315,7 @@ void forest_analyse(int32_t n, const int32_t *a, Forest &f, cudaStream_t st) {
 }
 
 void branch_gains(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                  const int32_t *s, long long m, const int32_t *a, const Forest &f,
+                  const int32_t *s, MParam m, const int32_t *a, const Forest &f,
                   const int32_t *sigma, const int32_t *best, const long long *gain,
                   const int32_t *kown, BranchScratch &bs, long long *bg, cudaStream_t st) {
     if (n <= 0) return;
@@ -337,12 +345,13 @@ void branch_gains(int32_t n, const int32_t *rp, const int32_t *col, const int32_
     SLM_LAUNCH_CHECK();
 }
 
-void accept_moves(int32_t n, const long long *bg, unsigned long long seed, unsigned long long P,
+void accept_moves(int32_t n, const long long *bg, RngParam rng, unsigned long long P,
                   int32_t level, int32_t sweep, int32_t *acc_list, int32_t *acc_cnt_dev,
-                  unsigned long long *npos_dev, cudaStream_t st) {
+                  unsigned long long *npos_dev, cudaStream_t st, const int32_t *active,
+                  int32_t *per_graph) {
     if (n <= 0) return;
-    k_accept<<<grid_for(n, 256), 256, 0, st>>>(n, bg, seed, P, level, sweep, acc_list, acc_cnt_dev,
-                                               npos_dev);
+    k_accept<<<grid_for(n, 256), 256, 0, st>>>(n, bg, rng, P, level, sweep, acc_list, acc_cnt_dev,
+                                               npos_dev, active, per_graph);
     SLM_LAUNCH_CHECK();
 }
 

@@ -190,11 +190,12 @@ __global__ void k_credit(int cnt, const int32_t *M, const int32_t *a, const int3
 }
 
 __global__ void k_branch(int cnt, const int32_t *M, const uint8_t *oncycle, const int32_t *root,
-                         const int32_t *posr, const int32_t *sigma, long long m,
+                         const int32_t *posr, const int32_t *sigma, MParam mp,
                          const long long *subS, const long long *subWA, const long long *subWin,
                          long long *bestsc, unsigned long long *bestkey, int pass) {
     GRID_STRIDE(k, cnt) {
         int u = M[k];
+        const long long m = mp.of(u);
         if (oncycle[u]) continue;
         int r = root[u];
         int q = posr[r];
@@ -209,13 +210,14 @@ __global__ void k_branch(int cnt, const int32_t *M, const uint8_t *oncycle, cons
 // part V = trees (p, q] grows with q: W(V+q, U-q) = W(V,U) + row(q) - 2 W(V,q)
 __global__ void k_cycle(const int32_t *Rdev, const int32_t *rlist, const int32_t *L, const int32_t *coff,
                         const int32_t *cyc, const long long *moff, const long long *Mw,
-                        const long long *TS, const int32_t *sigma, long long m, int32_t n,
+                        const long long *TS, const int32_t *sigma, MParam mp, int32_t n,
                         long long *bestsc, unsigned long long *bestkey, int pass) {
     const int R = *Rdev;
     for (int q0 = blockIdx.x; q0 < R; q0 += gridDim.x) {
         const int l = L[q0];
         if (l < 2) continue;
         const int r = rlist[q0];
+        const long long m = mp.of(r);
         const int32_t *cy = cyc + coff[q0];
         const long long *Mr = Mw + moff[q0];
         const long long sA = sigma[r];
@@ -244,10 +246,12 @@ __global__ void k_cut_info(const int32_t *Rdev, const int32_t *rlist,
                            const unsigned long long *bestkey, int32_t n, const int32_t *L,
                            const int32_t *coff, const int32_t *cyc, const long long *TS,
                            const int32_t *depth, const int32_t *cdist, const long long *subS,
-                           int32_t *sigma, int4 *cut, int32_t *a) {
+                           int32_t *sigma, int4 *cut, int32_t *a, const int32_t *gid,
+                           int32_t *splits_per_graph) {
     const int R = *Rdev;
     GRID_STRIDE(q, R) {
         const int r = rlist[q];
+        if (splits_per_graph) atomicAdd(&splits_per_graph[gid ? gid[r] : 0], 1);
         const unsigned long long key = bestkey[q];
         if (key == ~0ull) {  // no option recorded (cannot happen for size >= 2)
             cut[q] = make_int4(-1, 0, 0, 0);
@@ -358,11 +362,12 @@ __global__ void k_own_edges(int cnt, const int32_t *M, const int32_t *epref, con
         if (j != x && root[j] == root[x]) add64(&kacc[k], w[p]);
     }
 }
-__global__ void k_own_finish(int cnt, const int32_t *M, const int32_t *s, long long m,
+__global__ void k_own_finish(int cnt, const int32_t *M, const int32_t *s, MParam mp,
                              const int32_t *root, const int32_t *sigma, const long long *kacc,
                              int32_t *kown, int32_t *flag) {
     GRID_STRIDE(k, cnt) {
         int i = M[k];
+        const long long m = mp.of(i);
         int ci = root[i];
         long long own = kacc[k];
         kown[i] = (int32_t)own;
@@ -393,9 +398,10 @@ static int32_t compact_members(long long cnt, const int32_t *list, const int32_t
 }
 
 long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                           const int32_t *s, long long m, int32_t *a, Forest &f, int32_t *sigma,
+                           const int32_t *s, MParam m, int32_t *a, Forest &f, int32_t *sigma,
                            const Buckets &bk, PositiveScratch &ps, cudaStream_t st,
-                           long long *rounds_out, long long *visits_out) {
+                           long long *rounds_out, long long *visits_out,
+                           int32_t *splits_per_graph) {
     if (rounds_out) *rounds_out = 0;
     if (visits_out) *visits_out = 0;
     if (n <= 0) return 0;
@@ -494,7 +500,8 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
         }
         k_cut_info<<<grid_for(R, 256), 256, 0, st>>>(&hdr->R, rlist, bestkey, n, L, coff,
                                                       ps.cyc.as<int32_t>(), TS, f.depth, f.cdist,
-                                                      subS, sigma, ps.cut.as<int4>(), a);
+                                                      subS, sigma, ps.cut.as<int4>(), a, m.gid,
+                                                      splits_per_graph);
         SLM_LAUNCH_CHECK();
         splits += R;
         k_forest_new<<<gm, 256, 0, st>>>(cnt, M, a, f.root, f.entry, f.depth, f.cdist, f.oncycle,

@@ -105,7 +105,7 @@ __global__ void k_bucket_keys(int32_t n, const int32_t *rp, uint32_t *keys, int3
 // ---------------------------------------------------------------------------
 template <int G>
 __global__ void __launch_bounds__(256) k_scan_group(const int32_t *order, int32_t cnt, const int32_t *rp,
-                             const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                             const int32_t *col, const int32_t *w, const int32_t *s, MParam mp,
                              const int32_t *root, const int32_t *sigma, int32_t *best,
                              long long *gain, int32_t *kown, unsigned long long *ncand) {
     constexpr int NPW = 32 / G;  // nodes per warp
@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(256) k_scan_group(const int32_t *order, int32_
         long long idx = base + lane / G;
         bool vn = idx < cnt;
         int i = vn ? order[idx] : 0;
+        const long long m = mp.of(i);
         int start = vn ? rp[i] : 0;
         int deg = vn ? rp[i + 1] - start : 0;
         int ci = vn ? root[i] : -1;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(256) k_scan_group(const int32_t *order, int32_
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kWarpHashWarps * 32, 4) k_scan_warphash(const int32_t *order, int32_t cnt, const int32_t *rp,
                                 const int32_t *col, const int32_t *w, const int32_t *s,
-                                long long m, const int32_t *root, const int32_t *sigma,
+                                MParam mp, const int32_t *root, const int32_t *sigma,
                                 int32_t *best, long long *gain, int32_t *kown,
                                 unsigned long long *ncand) {
     __shared__ int tab[kWarpHashWarps][2 * kWarpHashCap];
@@ -183,6 +184,7 @@ __global__ void __launch_bounds__(kWarpHashWarps * 32, 4) k_scan_warphash(const 
     unsigned cand = 0;
     for (long long idx = warp; idx < cnt; idx += nwarps) {
         int i = order[idx];
+        const long long m = mp.of(i);
         int start = rp[i], deg = rp[i + 1] - start;
         int ci = root[i], si = s[i];
         int lg = ilog2_pow2_at_least(2 * deg);
@@ -280,7 +282,7 @@ constexpr size_t block_smem_bytes() {
 
 template <int CAP>
 __global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *order, int32_t cnt, const int32_t *rp,
-                             const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                             const int32_t *col, const int32_t *w, const int32_t *s, MParam mp,
                              const int32_t *root, const int32_t *sigma, int32_t *best,
                              long long *gain, int32_t *kown, unsigned long long *ncand) {
     extern __shared__ int sm[];
@@ -294,6 +296,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *ord
     unsigned cand = 0;
     for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
         int i = order[idx];
+        const long long m = mp.of(i);
         int start = rp[i], end = rp[i + 1];
         int deg = end - start;
         int ci = root[i], si = s[i];
@@ -389,13 +392,14 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks
 // weight, best score, best community), and the slots are reset
 __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunks, int ntchunk, const int32_t *hubs,
                              const long long *hoff, const int32_t *hlg, const int32_t *s,
-                             long long m, const int32_t *root, const int32_t *sigma, int *tkeys,
+                             MParam mp, const int32_t *root, const int32_t *sigma, int *tkeys,
                              int *tvals, long long *part_own, long long *part_sc,
                              int32_t *part_cc) {
     constexpr int B = kHubSlice / kBlockThreads;
     for (int tc = blockIdx.x; tc < ntchunk; tc += gridDim.x) {
         const int2 d = tchunks[tc];  // (hub index, first slot)
         const int i = hubs[d.x];
+        const long long m = mp.of(i);
         const int ci = root[i], si = s[i];
         const int cap = 1 << hlg[d.x];
         int *keys = tkeys + hoff[d.x], *vals = tvals + hoff[d.x];
@@ -435,7 +439,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunk
 
 // one warp per hub: reduce the slices' partials and decide
 __global__ void k_hub_finish(int nhub, const int32_t *hubs, const int32_t *tc_off, const int32_t *s,
-                             long long m, const int32_t *root, const int32_t *sigma,
+                             MParam mp, const int32_t *root, const int32_t *sigma,
                              const long long *part_own, const long long *part_sc,
                              const int32_t *part_cc, int32_t *best, long long *gain,
                              int32_t *kown, unsigned long long *ncand) {
@@ -445,6 +449,7 @@ __global__ void k_hub_finish(int nhub, const int32_t *hubs, const int32_t *tc_of
     unsigned cand = 0;
     for (long long h = warp; h < nhub; h += nwarps) {
         const int i = hubs[h];
+        const long long m = mp.of(i);
         long long own = 0, sc = LLONG_MIN;
         int cc = INT_MAX;
         for (int t = tc_off[h] + lane; t < tc_off[h + 1]; t += 32) {
@@ -490,11 +495,12 @@ __global__ void __launch_bounds__(kBlockThreads) k_own_hub_chunk(const int4 *chu
     }
 }
 
-__global__ void k_own_hub_finish(int nhub, const int32_t *hubs, const int32_t *s, long long m,
+__global__ void k_own_hub_finish(int nhub, const int32_t *hubs, const int32_t *s, MParam mp,
                                  const int32_t *root, const int32_t *sigma,
                                  const unsigned long long *acc, int32_t *kown, int32_t *flag) {
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < nhub; h += gridDim.x * blockDim.x) {
         int i = hubs[h];
+        const long long m = mp.of(i);
         int ci = root[i];
         long long own = (long long)acc[h];
         kown[i] = (int32_t)own;
@@ -523,7 +529,7 @@ __device__ __forceinline__ void pair_consider(PairBest &b, long long sc, int j) 
 template <int G>
 __global__ void __launch_bounds__(256) k_assign_group(const int32_t *order, int32_t cnt, const int32_t *rp,
                                const int32_t *col, const int32_t *w, const int32_t *s,
-                               long long m, int32_t *a) {
+                               MParam mp, int32_t *a) {
     constexpr int NPW = 32 / G;
     const int lane = threadIdx.x & 31, gl = lane % G;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -532,6 +538,7 @@ __global__ void __launch_bounds__(256) k_assign_group(const int32_t *order, int3
         long long idx = base + lane / G;
         bool vn = idx < cnt;
         int i = vn ? order[idx] : 0;
+        const long long m = mp.of(i);
         int start = vn ? rp[i] : 0, end = vn ? rp[i + 1] : 0;
         long long si = vn ? s[i] : 0;
         PairBest b{LLONG_MIN, INT_MAX};
@@ -552,9 +559,10 @@ __global__ void __launch_bounds__(256) k_assign_group(const int32_t *order, int3
 
 __global__ void __launch_bounds__(kBlockThreads) k_assign_block(const int32_t *order, int32_t cnt, const int32_t *rp,
                                const int32_t *col, const int32_t *w, const int32_t *s,
-                               long long m, int32_t *a) {
+                               MParam mp, int32_t *a) {
     for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
         int i = order[idx];
+        const long long m = mp.of(i);
         long long si = s[i];
         PairBest b{LLONG_MIN, INT_MAX};
         for (int p = rp[i] + threadIdx.x; p < rp[i + 1]; p += blockDim.x) {
@@ -576,7 +584,7 @@ __global__ void k_assign_empty(const int32_t *order, int32_t cnt, int32_t *a) {
 
 // Target of every accepted node: one warp per node.
 __global__ void k_target(const int32_t *list, const int32_t *cnt_dev, const int32_t *rp,
-                         const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                         const int32_t *col, const int32_t *w, const int32_t *s, MParam mp,
                          const int32_t *root, const int32_t *best, int32_t *tgt) {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -584,6 +592,7 @@ __global__ void k_target(const int32_t *list, const int32_t *cnt_dev, const int3
     const int cnt = *cnt_dev;
     for (long long idx = warp; idx < cnt; idx += nwarps) {
         int i = list[idx];
+        const long long m = mp.of(i);
         int want = best[i];
         long long si = s[i];
         PairBest b{LLONG_MIN, INT_MAX};
@@ -617,7 +626,7 @@ __device__ __forceinline__ void own_emit(int i, int ci, long long si, long long 
 
 template <int G>
 __global__ void __launch_bounds__(256) k_own_group(const int32_t *order, int32_t cnt, const int32_t *rp,
-                            const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                            const int32_t *col, const int32_t *w, const int32_t *s, MParam mp,
                             const int32_t *root, const int32_t *sigma, int32_t *kown,
                             int32_t *flag) {
     constexpr int NPW = 32 / G;
@@ -628,6 +637,7 @@ __global__ void __launch_bounds__(256) k_own_group(const int32_t *order, int32_t
         long long idx = base + lane / G;
         bool vn = idx < cnt;
         int i = vn ? order[idx] : 0;
+        const long long m = mp.of(i);
         int ci = vn ? root[i] : -1;
         long long own = 0;
         if (vn)
@@ -642,11 +652,12 @@ __global__ void __launch_bounds__(256) k_own_group(const int32_t *order, int32_t
 }
 
 __global__ void __launch_bounds__(kBlockThreads) k_own_block(const int32_t *order, int32_t cnt, const int32_t *rp,
-                            const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                            const int32_t *col, const int32_t *w, const int32_t *s, MParam mp,
                             const int32_t *root, const int32_t *sigma, int32_t *kown,
                             int32_t *flag) {
     for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
         int i = order[idx];
+        const long long m = mp.of(i);
         int ci = root[i];
         long long own = 0;
         for (int p = rp[i] + threadIdx.x; p < rp[i + 1]; p += blockDim.x) {
@@ -660,45 +671,19 @@ __global__ void __launch_bounds__(kBlockThreads) k_own_block(const int32_t *orde
     }
 }
 
-__global__ void k_local_gain(int32_t n, const int32_t *s, long long m, const int32_t *root,
+__global__ void k_local_gain(int32_t n, const int32_t *s, MParam mp, const int32_t *root,
                              const int32_t *sigma, const int32_t *kown, long long *g) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
+        const long long m = mp.of((int)i);
         long long si = s[i];
         g[i] = m * (long long)kown[i] - si * ((long long)sigma[root[i]] - si);
     }
 }
 
-// Side streams on which the independent bucket kernels of one scan overlap
-// (created once per device; the scan forks to them and joins back with events).
-struct SideStreams {
-    static constexpr int kN = 3;
-    cudaStream_t s[kN] = {};
-    cudaEvent_t fork = nullptr, join[kN] = {};
-};
-
-SideStreams &side_streams() {
-    static std::mutex mu;
-    static SideStreams per_dev[64];
-    static bool made[64] = {false};
-    int dev = 0;
-    SLM_CUDA(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lk(mu);
-    SideStreams &ss = per_dev[dev & 63];
-    if (!made[dev & 63]) {
-        for (int k = 0; k < SideStreams::kN; k++) {
-            SLM_CUDA(cudaStreamCreateWithFlags(&ss.s[k], cudaStreamNonBlocking));
-            SLM_CUDA(cudaEventCreateWithFlags(&ss.join[k], cudaEventDisableTiming));
-        }
-        SLM_CUDA(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
-        made[dev & 63] = true;
-    }
-    return ss;
-}
-
 }  // namespace
 
-void local_gain_nodes(int32_t n, const int32_t *s, long long m, const int32_t *root,
+void local_gain_nodes(int32_t n, const int32_t *s, MParam m, const int32_t *root,
                       const int32_t *sigma, const int32_t *kown, long long *g, cudaStream_t st) {
     if (n <= 0) return;
     k_local_gain<<<grid_for(n, 256), 256, 0, st>>>(n, s, m, root, sigma, kown, g);
@@ -708,7 +693,22 @@ void local_gain_nodes(int32_t n, const int32_t *s, long long m, const int32_t *r
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+Buckets::~Buckets() {
+    for (int k = 0; k < kSide; k++) {
+        if (side[k]) cudaStreamDestroy(side[k]);
+        if (join[k]) cudaEventDestroy(join[k]);
+    }
+    if (fork) cudaEventDestroy(fork);
+}
+
 void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
+    if (!fork) {
+        for (int k = 0; k < kSide; k++) {
+            SLM_CUDA(cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking));
+            SLM_CUDA(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
+        }
+        SLM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    }
     for (int b = 0; b <= kNumBuckets; b++) off[b] = 0;
     order.ensure(sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s);
     if (n <= 0) return;
@@ -784,7 +784,7 @@ static int blocks_for_groups(long long cnt, int nodes_per_warp, int threads = 25
 }
 
 void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                  const int32_t *s, long long m, const Buckets &bk, int32_t *a, cudaStream_t st) {
+                  const int32_t *s, MParam m, const Buckets &bk, int32_t *a, cudaStream_t st) {
     if (n <= 0) return;
     const int32_t *ord = bk.order.as<int32_t>();
     auto seg = [&](int b) { return std::make_pair(ord + bk.off[b], bk.off[b + 1] - bk.off[b]); };
@@ -816,17 +816,16 @@ void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_
 }
 
 void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                const int32_t *s, long long m, const int32_t *root, const int32_t *sigma,
+                const int32_t *s, MParam m, const int32_t *root, const int32_t *sigma,
                 const Buckets &bk, int32_t *best, long long *gain, int32_t *kown,
                 unsigned long long *ncand, cudaStream_t st) {
     if (n <= 0) return;
     const int32_t *ord = bk.order.as<int32_t>();
     auto cnt = [&](int b) { return bk.off[b + 1] - bk.off[b]; };
     // the buckets write disjoint nodes: run them side by side
-    SideStreams &ss = side_streams();
-    SLM_CUDA(cudaEventRecord(ss.fork, st));
-    for (int k = 0; k < SideStreams::kN; k++) SLM_CUDA(cudaStreamWaitEvent(ss.s[k], ss.fork, 0));
-    cudaStream_t s0 = st, s1 = ss.s[0], s2 = ss.s[1], s3 = ss.s[2];
+    SLM_CUDA(cudaEventRecord(bk.fork, st));
+    for (int k = 0; k < Buckets::kSide; k++) SLM_CUDA(cudaStreamWaitEvent(bk.side[k], bk.fork, 0));
+    cudaStream_t s0 = st, s1 = bk.side[0], s2 = bk.side[1], s3 = bk.side[2];
     if (int c = cnt(kBucketBlockL)) {
         constexpr int CAP = 2 * kBlockSmemMaxDeg;
         const size_t smem = block_smem_bytes<CAP>();
@@ -886,14 +885,14 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
         k_scan_empty<<<grid_for(c, 256), 256, 0, s1>>>(ord + bk.off[kBucketEmpty], c, root, best, gain, kown);
         SLM_LAUNCH_CHECK();
     }
-    for (int k = 0; k < SideStreams::kN; k++) {
-        SLM_CUDA(cudaEventRecord(ss.join[k], ss.s[k]));
-        SLM_CUDA(cudaStreamWaitEvent(st, ss.join[k], 0));
+    for (int k = 0; k < Buckets::kSide; k++) {
+        SLM_CUDA(cudaEventRecord(bk.join[k], bk.side[k]));
+        SLM_CUDA(cudaStreamWaitEvent(st, bk.join[k], 0));
     }
 }
 
 void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                      const int32_t *s, long long m, const int32_t *root, const int32_t *sigma,
+                      const int32_t *s, MParam m, const int32_t *root, const int32_t *sigma,
                       const Buckets &bk, int32_t *kown, int32_t *flag, cudaStream_t st) {
     if (n <= 0) return;
     const int32_t *ord = bk.order.as<int32_t>();
@@ -936,7 +935,7 @@ void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const in
 }
 
 void target_nodes(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt, const int32_t *rp,
-                  const int32_t *col, const int32_t *w, const int32_t *s, long long m,
+                  const int32_t *col, const int32_t *w, const int32_t *s, MParam m,
                   const int32_t *root, const int32_t *best, int32_t *tgt, cudaStream_t st) {
     if (max_cnt <= 0) return;
     k_target<<<grid_for((long long)max_cnt * 32, 256, kNumSMs * 16), 256, 0, st>>>(

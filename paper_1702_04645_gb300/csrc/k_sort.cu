@@ -101,16 +101,20 @@ void radix_sort_impl(K *keys, int32_t *vals, K *ktmp, int32_t *vtmp, long long n
 // ---------------------------------------------------------------------------
 // Aggregation
 // ---------------------------------------------------------------------------
+// rows of nodes whose graph is marked in drop_graph (a forest) get the key
+// K*K, one past every real key, so that they sort last and are cut off
 __global__ void k_agg_keys(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                            const int32_t *id, long long K, unsigned long long *keys,
-                           int32_t *vals) {
+                           int32_t *vals, const int32_t *gid, const int32_t *drop_graph) {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long u = warp; u < n; u += nwarps) {
+        const bool drop = drop_graph && drop_graph[gid[u]];
         unsigned long long hi = (unsigned long long)id[u] * (unsigned long long)K;
         for (int p = rp[u] + lane; p < rp[u + 1]; p += 32) {
-            keys[p] = hi + (unsigned long long)id[col[p]];
+            keys[p] = drop ? (unsigned long long)K * (unsigned long long)K
+                           : hi + (unsigned long long)id[col[p]];
             vals[p] = w[p];
         }
     }
@@ -166,10 +170,12 @@ void radix_sort_u32(uint32_t *keys, int32_t *vals, uint32_t *keys_tmp, int32_t *
 
 int32_t aggregate_graph(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                         const int32_t *id, int32_t K, DevBuf &rp_out, DevBuf &col_out,
-                        DevBuf &w_out, cudaStream_t st) {
-    int32_t nnz = 0;
-    SLM_CUDA(cudaMemcpyAsync(&nnz, rp + n, sizeof nnz, cudaMemcpyDeviceToHost, st));
+                        DevBuf &w_out, cudaStream_t st, const int32_t *gid,
+                        const int32_t *drop_graph, long long dropped) {
+    int32_t nnz_all = 0;
+    SLM_CUDA(cudaMemcpyAsync(&nnz_all, rp + n, sizeof nnz_all, cudaMemcpyDeviceToHost, st));
     SLM_CUDA(cudaStreamSynchronize(st));
+    const int32_t nnz = nnz_all - (int32_t)dropped;  // entries kept after the sort
     rp_out.alloc(sizeof(int32_t) * ((size_t)K + 1), st);
     SLM_CUDA(cudaMemsetAsync(rp_out.get(), 0, sizeof(int32_t) * ((size_t)K + 1), st));
     if (nnz == 0 || K == 0) {
@@ -177,16 +183,16 @@ int32_t aggregate_graph(int32_t n, const int32_t *rp, const int32_t *col, const 
         w_out.alloc(16, st);
         return 0;
     }
-    DevBuf keys(8 * (size_t)nnz, st), ktmp(8 * (size_t)nnz, st), vals(4 * (size_t)nnz, st),
-        vtmp(4 * (size_t)nnz, st), seg(4 * (size_t)nnz, st), tot(8, st);
+    DevBuf keys(8 * (size_t)nnz_all, st), ktmp(8 * (size_t)nnz_all, st), vals(4 * (size_t)nnz_all, st),
+        vtmp(4 * (size_t)nnz_all, st), seg(4 * (size_t)nnz, st), tot(8, st);
     k_agg_keys<<<grid_for((long long)n * 32, 256, kNumSMs * 16), 256, 0, st>>>(
-        n, rp, col, w, id, K, keys.as<unsigned long long>(), vals.as<int32_t>());
+        n, rp, col, w, id, K, keys.as<unsigned long long>(), vals.as<int32_t>(), gid, drop_graph);
     SLM_LAUNCH_CHECK();
-    unsigned long long maxkey = (unsigned long long)K * (unsigned long long)K;
+    unsigned long long maxkey = (unsigned long long)K * (unsigned long long)K + (dropped > 0 ? 1 : 0);
     int bits = 0;
     while (bits < 64 && (1ull << bits) < maxkey) bits++;
     radix_sort_u64(keys.as<unsigned long long>(), vals.as<int32_t>(), ktmp.as<unsigned long long>(),
-                   vtmp.as<int32_t>(), nnz, bits, st);
+                   vtmp.as<int32_t>(), nnz_all, bits, st);
     k_agg_heads<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, keys.as<unsigned long long>(), seg.as<int32_t>());
     SLM_LAUNCH_CHECK();
     exclusive_scan_i32(seg.as<int32_t>(), seg.as<int32_t>(), nnz, tot.as<int32_t>(), st);

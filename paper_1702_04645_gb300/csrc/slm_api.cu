@@ -15,10 +15,12 @@
 #include <string>
 #include <vector>
 
+#include "driver.cuh"
 #include "slm_internal.cuh"
 #include "slm_steps.h"
 
 using slm::DevBuf;
+using slm::Work;
 
 struct slm_graph {
     int32_t n0 = 0;
@@ -114,62 +116,6 @@ __global__ void k_fill_ones(long long n, int32_t *p) {
          i += (long long)gridDim.x * blockDim.x)
         p[i] = 1;
 }
-
-// Per-level device workspace.
-struct Work {
-    int32_t n = 0;
-    DevBuf a, sigma, best, kown, tgt, acclist, gain, bg, counters;
-    DevBuf root, oncycle, entry, depth, cdist, jmpA, jmpB;
-    DevBuf bs_i32, bs_i64;
-    slm::Forest f;
-    slm::BranchScratch bs{};
-    slm::PositiveScratch ps;
-    slm::Buckets bk;
-
-    void init(int32_t n_, const int32_t *rp, cudaStream_t st) {
-        n = n_;
-        size_t N = (size_t)(n > 0 ? n : 1);
-        a.ensure(4 * N, st);
-        sigma.ensure(4 * N, st);
-        best.ensure(4 * N, st);
-        kown.ensure(4 * N, st);
-        tgt.ensure(4 * N, st);
-        acclist.ensure(4 * N, st);
-        gain.ensure(8 * N, st);
-        bg.ensure(8 * N, st);
-        counters.ensure(64, st);
-        root.ensure(4 * N, st);
-        oncycle.ensure(N, st);
-        entry.ensure(4 * N, st);
-        depth.ensure(4 * N, st);
-        cdist.ensure(4 * N, st);
-        jmpA.ensure(8 * N, st);
-        jmpB.ensure(8 * N, st);
-        bs_i32.ensure(4 * N * 5, st);
-        bs_i64.ensure(8 * N * 5, st);
-        f.root = root.as<int32_t>();
-        f.oncycle = oncycle.as<uint8_t>();
-        f.entry = entry.as<int32_t>();
-        f.depth = depth.as<int32_t>();
-        f.cdist = cdist.as<int32_t>();
-        f.jmpA = jmpA.as<int2>();
-        f.jmpB = jmpB.as<int2>();
-        int32_t *p32 = bs_i32.as<int32_t>();
-        long long *p64 = bs_i64.as<long long>();
-        bs.haschild = p32;
-        bs.active = p32 + N;
-        bs.covered = p32 + 2 * N;
-        bs.treeact = p32 + 3 * N;
-        bs.commcyc = p32 + 4 * N;
-        bs.subS = p64;
-        bs.subWA = p64 + N;
-        bs.subWin = p64 + 2 * N;
-        bs.credit = p64 + 3 * N;
-        bs.WB = p64 + 4 * N;
-        bk.build(n, rp, st);
-    }
-    unsigned long long *ctr() { return counters.as<unsigned long long>(); }
-};
 
 // POSITIVE until no community holds a node with a negative local gain.
 long long positive_all(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,

@@ -45,6 +45,29 @@ void note_launch();
 constexpr int kWarp = 32;
 constexpr int kNumSMs = 152;
 
+// m_w of the graph a node belongs to: one value for a single graph, or per
+// graph through the node -> graph map of a forest of graphs.
+struct MParam {
+    long long m = 0;
+    const int32_t *gid = nullptr;
+    const long long *mg = nullptr;
+    __host__ __device__ MParam(long long v = 0) : m(v) {}
+    __host__ __device__ MParam(const int32_t *g, const long long *per_graph) : gid(g), mg(per_graph) {}
+    __device__ __forceinline__ long long of(int i) const { return gid ? mg[gid[i]] : m; }
+};
+
+// Key of the random acceptance draw: the seed and node id of a single graph,
+// or per graph (seed of the node's graph, id local to that graph).
+struct RngParam {
+    unsigned long long seed = 0;
+    const int32_t *gid = nullptr;
+    const unsigned long long *seeds = nullptr;
+    const int32_t *goff = nullptr;
+    __host__ __device__ RngParam(unsigned long long s = 0) : seed(s) {}
+    __device__ __forceinline__ unsigned long long seed_of(int i) const { return gid ? seeds[gid[i]] : seed; }
+    __device__ __forceinline__ int local(int i) const { return gid ? i - goff[gid[i]] : i; }
+};
+
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 inline int grid_for(long long n, int block, int max_blocks = 152 * 32) {
     long long g = (n + block - 1) / block;
@@ -158,36 +181,45 @@ struct Buckets {
     DevBuf hub_off, hub_lg, chunks, tkeys, tvals, hub_acc;
     // slices of the hub tables read by one block each, and their partial results
     DevBuf tchunks, tc_off, part_own, part_sc, part_cc;
+    // side streams on which the independent bucket kernels of a scan overlap
+    // (owned here so that concurrent runs never share fork/join events)
+    static constexpr int kSide = 3;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, join[kSide] = {};
     void build(int32_t n, const int32_t *rp, cudaStream_t s);
+    Buckets() = default;
+    Buckets(const Buckets &) = delete;
+    Buckets &operator=(const Buckets &) = delete;
+    ~Buckets();
 };
 
 // ASSIGN: a[i] = best neighbour by m_w W_ij - s_i s_j.
 void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                  const int32_t *s, long long m_w, const Buckets &bk, int32_t *a,
+                  const int32_t *s, MParam m_w, const Buckets &bk, int32_t *a,
                   cudaStream_t st);
 
 // The MAXIMAL scan: best community, gain (int64) and own-community weight
 // kown (int32); counts candidates into *ncand_dev (unsigned long long).
 void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                const int32_t *s, long long m_w, const int32_t *root, const int32_t *sigma,
+                const int32_t *s, MParam m_w, const int32_t *root, const int32_t *sigma,
                 const Buckets &bk, int32_t *best, long long *gain, int32_t *kown,
                 unsigned long long *ncand_dev, cudaStream_t st);
 
 // Own-community weight only (kown) for POSITIVE's local gains; flags the
 // communities holding a node with g < 0 (flag[root] = 1) and counts them.
 void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                      const int32_t *s, long long m_w, const int32_t *root,
+                      const int32_t *s, MParam m_w, const int32_t *root,
                       const int32_t *sigma, const Buckets &bk, int32_t *kown,
                       int32_t *flag, cudaStream_t st);
 
 // Local gain g(i) = m_w kown_i - s_i (Sigma_{root_i} - s_i) of Algorithm POSITIVE.
-void local_gain_nodes(int32_t n, const int32_t *s, long long m, const int32_t *root,
+void local_gain_nodes(int32_t n, const int32_t *s, MParam m, const int32_t *root,
                       const int32_t *sigma, const int32_t *kown, long long *g, cudaStream_t st);
 
 // Target node for the accepted nodes listed in list[0..cnt).
 void target_nodes(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt,
                   const int32_t *rp, const int32_t *col, const int32_t *w, const int32_t *s,
-                  long long m_w, const int32_t *root, const int32_t *best, int32_t *tgt,
+                  MParam m_w, const int32_t *root, const int32_t *best, int32_t *tgt,
                   cudaStream_t st);
 
 // ---------------------------------------------------------------------------
@@ -213,13 +245,17 @@ struct BranchScratch {
 // Branch gains bg for candidates (gain > 0); counts positive ones and the
 // accepted ones, and lists the accepted nodes.
 void branch_gains(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                  const int32_t *s, long long m_w, const int32_t *a, const Forest &f,
+                  const int32_t *s, MParam m_w, const int32_t *a, const Forest &f,
                   const int32_t *sigma, const int32_t *best, const long long *gain,
                   const int32_t *kown, BranchScratch &bs, long long *bg, cudaStream_t st);
 // Acceptance draw and list of accepted nodes.
-void accept_moves(int32_t n, const long long *bg, unsigned long long seed,
-                  unsigned long long P, int32_t level, int32_t sweep, int32_t *acc_list,
-                  int32_t *acc_cnt_dev, unsigned long long *npos_dev, cudaStream_t st);
+// With a forest (rng.gid set), per_graph gets, for every graph, the counts
+// of positive branch gains [0] and accepted moves [1] (int32 pairs), and
+// nodes of graphs whose active[g] is 0 are skipped.
+void accept_moves(int32_t n, const long long *bg, RngParam rng, unsigned long long P,
+                  int32_t level, int32_t sweep, int32_t *acc_list, int32_t *acc_cnt_dev,
+                  unsigned long long *npos_dev, cudaStream_t st,
+                  const int32_t *active = nullptr, int32_t *per_graph = nullptr);
 void apply_moves(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt,
                  const int32_t *tgt, int32_t *a, cudaStream_t st);
 
@@ -232,19 +268,47 @@ struct PositiveScratch {
 // recomputed); sigma is used as scratch.  Returns the number of splits;
 // *rounds_out gets the number of rounds and *visits_out the member visits
 // summed over the rounds.
+// With a forest, splits_per_graph (int32[G], may be null) counts each graph's splits.
 long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                           const int32_t *s, long long m, int32_t *a, Forest &f, int32_t *sigma,
+                           const int32_t *s, MParam m, int32_t *a, Forest &f, int32_t *sigma,
                            const Buckets &bk, PositiveScratch &ps, cudaStream_t st,
-                           long long *rounds_out, long long *visits_out);
+                           long long *rounds_out, long long *visits_out,
+                           int32_t *splits_per_graph = nullptr);
 
 // ---------------------------------------------------------------------------
 // Aggregation (k_sort.cu)
 // ---------------------------------------------------------------------------
 // Builds the aggregated CSR; returns its nnz.  Output buffers are allocated
 // by the callee (row_ptr_out K+1, col_out/w_out nnz').
+// With a forest, rows of the graphs marked in drop_graph (gid: node -> graph)
+// are left out; `dropped` is their number of entries.
 int32_t aggregate_graph(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                         const int32_t *id, int32_t K, DevBuf &rp_out, DevBuf &col_out,
-                        DevBuf &w_out, cudaStream_t st);
+                        DevBuf &w_out, cudaStream_t st, const int32_t *gid = nullptr,
+                        const int32_t *drop_graph = nullptr, long long dropped = 0);
+
+// ---------------------------------------------------------------------------
+// Forests of graphs (k_basic.cu)
+// ---------------------------------------------------------------------------
+// gid[v] = the graph whose node range [goff[g], goff[g+1]) holds v.
+void graph_of_nodes(int32_t n, const int32_t *goff, int32_t G, int32_t *gid, cudaStream_t st);
+// per graph: m_w (int64) from the strengths; returns the number of entries
+// whose endpoints lie in different graphs (host-synchronous).
+long long forest_check_and_weights(int32_t n, const int32_t *rp, const int32_t *col,
+                                   const int32_t *s, const int32_t *gid, int32_t G,
+                                   long long *mg, cudaStream_t st);
+// per graph: number of names in use (root[v] == v)
+void roots_per_graph(int32_t n, const int32_t *root, const int32_t *gid, int32_t *Kg,
+                     cudaStream_t st);
+// per graph: candidates (gain > 0) of active graphs; gains of inactive graphs zeroed
+void candidates_per_graph(int32_t n, const int32_t *gid, const int32_t *active, long long *gain,
+                          int32_t *cand_g, cudaStream_t st);
+// per graph exact modularity numerator of labels (global ids in [0, nlab)),
+// labels of graph g lying in [loff[g], loff[g+1]); nums[g] = m_g sum W_in - sum Sigma^2
+void modularity_forest(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                       const int32_t *labels, int32_t nlab, const int32_t *gid,
+                       const int32_t *loff, int32_t G, const long long *mg, long long *nums,
+                       cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Device helpers
