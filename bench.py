@@ -133,6 +133,112 @@ def oracle_sample():
     return scanned / dt / 1e9, dt, scanned, desc
 
 
+FOREST_DESC = ("4096 planted-partition graphs, n log-uniform in [100, 50000], 4-64 blocks, "
+               "intra/inter expected degree 12/3, w~U[1,4], seeds 1000+g, one block-diagonal CSR")
+
+
+def load_forest():
+    cache = os.path.join(ROOT, ".graph_cache", "forest_sbm_4096.npz")
+    if os.path.exists(cache):
+        z = np.load(cache)
+        return z["goff"], z["rp"], z["col"], z["w"], z["seeds"]
+    params = gg.forest_sbm_params()
+    goff, rp, col, w, sds = gg.forest_sbm(params)
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    np.savez(cache + ".tmp.npz", goff=goff, rp=rp, col=col, w=w, seeds=sds)
+    os.replace(cache + ".tmp.npz", cache)
+    return goff, rp, col, w, sds
+
+
+def _oracle_forest_job(args):
+    """One graph of the forest through the oracle (run in a spawned worker)."""
+    import oracle as O
+    n, b, sd = args
+    g = gg.forest_sbm_graph(n, b, sd)
+    t0 = time.perf_counter()
+    O.slm(g, seed=sd, P=O.P_HALF)
+    return time.perf_counter() - t0
+
+
+def run_forest(args):
+    """Batched form: graphs/s of one slm_batch_run over the whole forest,
+    beside a per-graph loop of slm_run on every 16th graph (same partitions)."""
+    import torch
+    import paper_1702_04645_gb300 as slm
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    goff, rp, col, w, sds = load_forest()
+    G = len(goff) - 1
+    B = slm.Batch(graph_off=goff, row_ptr=rp, col=col, w=w, seeds=sds)
+    for _ in range(args.warmup):
+        B.run(accept_p32=slm.P_HALF, stream=stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    launches0 = slm.launch_count()
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            B.run(accept_p32=slm.P_HALF, stream=stream.cuda_stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    launches = slm.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    levels, sweeps = B.run_info()
+    # per-graph loop of the single-graph path on a sample, partitions compared
+    sample = list(range(0, G, 16))
+    t_loop = 0.0
+    identical = True
+    for k in sample:
+        lo, hi = int(goff[k]), int(goff[k + 1])
+        e0, e1 = int(rp[lo]), int(rp[hi])
+        g_rp = (rp[lo:hi + 1] - rp[lo]).astype(np.int32)
+        g_col = (col[e0:e1] - lo).astype(np.int32)
+        g_w = w[e0:e1]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        Gk = slm.Graph(g_rp, g_col, g_w)
+        Gk.run(seed=int(sds[k]), accept_p32=slm.P_HALF, stream=stream.cuda_stream)
+        lab, _ = Gk.partition(-1)
+        torch.cuda.synchronize(dev)
+        t_loop += time.perf_counter() - t0
+        Gk.close()
+        identical &= bool((lab == B.partition(k, -1)[0]).all())
+    loop_gps = len(sample) / t_loop
+    cpu = None
+    if not args.no_cpu_baseline:
+        import multiprocessing as mp
+        params = gg.forest_sbm_params()
+        csample = [params[k] for k in range(0, G, 64)]
+        cores = os.cpu_count() or 1
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        with ctx.Pool(cores) as pool:
+            per = pool.map(_oracle_forest_job, csample)
+        wall = time.perf_counter() - t0
+        cpu = {"value": len(csample) / wall, "unit": "graphs/s", "cores": cores, "kind": "oracle",
+               "sample": (f"oracle on every 64th graph of the forest ({len(csample)} graphs) in "
+                          f"{cores} spawned processes: {wall:.1f} s wall, {sum(per):.1f} s of CPU")}
+    line = {"metric": "graphs/s (batched)", "value": G / (ms / 1e3), "unit": "graphs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": "forest_sbm_4096", "desc": FOREST_DESC, "graphs": G,
+                       "nodes": int(goff[-1]), "nnz": int(rp[-1]), "batch_levels": levels,
+                       "batch_sweeps": sweeps,
+                       "l2": "inputs larger than L2 (CSR %.0f MB)" % ((8 * rp[-1] + 4 * goff[-1]) / 1e6)},
+            "per_graph_loop": {"value": loop_gps, "unit": "graphs/s",
+                               "sample": f"slm_run on every 16th graph ({len(sample)} graphs), "
+                                         "host CSR in, labels out",
+                               "identical_partitions": identical},
+            "speedup_vs_loop": (G / (ms / 1e3)) / loop_gps,
+            "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def peaks():
     try:
         d = json.load(open(PEAKS))
@@ -176,11 +282,14 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["rmat", "forest"], default="rmat")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "forest":
+        return run_forest(args)
 
     import torch
     import paper_1702_04645_gb300 as slm

@@ -64,21 +64,26 @@ def mix64(z: np.ndarray) -> np.ndarray:
     return z ^ (z >> np.uint64(31))
 
 
-def _draw_u64(seed: int, stream: int, idx) -> np.ndarray:
+def _draw_u64(seed, stream: int, idx) -> np.ndarray:
+    """64 random bits for (seed, stream, counter); seed may be an array of the
+    same shape as idx (one seed per draw)."""
     idx = np.asarray(idx, dtype=np.uint64)
-    key = np.uint64(seed & 0xFFFFFFFFFFFFFFFF)
+    if np.ndim(seed) == 0:
+        key = np.uint64(int(seed) & 0xFFFFFFFFFFFFFFFF)
+    else:
+        key = np.asarray(seed, dtype=np.uint64)
     with np.errstate(over="ignore"):
         s = mix64(np.uint64(stream & 0xFFFFFFFFFFFFFFFF) ^ key)
         return mix64(idx ^ s)
 
 
-def uniform01(seed: int, stream: int, idx) -> np.ndarray:
+def uniform01(seed, stream: int, idx) -> np.ndarray:
     """Uniform doubles in [0, 1) with 53 random bits."""
     u = _draw_u64(seed, stream, idx) >> np.uint64(11)
     return u.astype(np.float64) * (1.0 / 9007199254740992.0)
 
 
-def uniform_int(seed: int, stream: int, idx, lo: int, hi: int) -> np.ndarray:
+def uniform_int(seed, stream: int, idx, lo: int, hi: int) -> np.ndarray:
     """Integers uniform in [lo, hi] (inclusive) by a multiply-shift on 32 bits."""
     span = np.uint64(hi - lo + 1)
     u = _draw_u64(seed, stream, idx) >> np.uint64(32)
@@ -344,6 +349,87 @@ def forest_sbm_graph(n: int, blocks: int, seed: int, deg_in: float = 12.0,
     w = uniform_int(seed, 14, np.arange(u.shape[0], dtype=np.int64), wmin, wmax)
     keep = u != v
     return from_edges(n, u[keep], v[keep], w[keep])
+
+
+def forest_sbm(params, deg_in: float = 12.0, deg_out: float = 3.0, wmin: int = 1, wmax: int = 4,
+               chunk: int = 256):
+    """All graphs of forest_sbm_params packed as one block-diagonal CSR:
+    returns (graph_off, row_ptr, col, w, seeds).  Graph g is exactly
+    forest_sbm_graph(n_g, blocks_g, seed_g) shifted by graph_off[g].  Graphs
+    are drawn `chunk` at a time with vectorised draws."""
+    parts = [_forest_sbm_chunk(params[k:k + chunk], deg_in, deg_out, wmin, wmax)
+             for k in range(0, len(params), chunk)]
+    G = len(params)
+    goff = np.zeros(G + 1, dtype=np.int64)
+    rps, cols, ws = [], [], []
+    nbase, ebase, g0 = 0, 0, 0
+    for (pg, prp, pcol, pw, _) in parts:
+        k = pg.shape[0] - 1
+        goff[g0 + 1: g0 + k + 1] = pg[1:].astype(np.int64) + nbase
+        rps.append(prp[1:].astype(np.int64) + ebase)
+        cols.append(pcol.astype(np.int64) + nbase)
+        ws.append(pw)
+        nbase += int(pg[-1])
+        ebase += int(prp[-1])
+        g0 += k
+    if ebase >= 2**31:
+        raise ValueError("forest too large for int32 CSR")
+    rp = np.concatenate([np.zeros(1, np.int64)] + rps).astype(np.int32)
+    col = np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32)
+    w = np.concatenate(ws).astype(np.int32) if ws else np.zeros(0, np.int32)
+    sds = np.array([p[2] for p in params], dtype=np.uint64)
+    return goff.astype(np.int32), rp, col, w, sds
+
+
+def _forest_sbm_chunk(params, deg_in, deg_out, wmin, wmax):
+    G = len(params)
+    ns = np.array([p[0] for p in params], dtype=np.int64)
+    bs = np.array([p[1] for p in params], dtype=np.int64)
+    sds = np.array([p[2] for p in params], dtype=np.uint64)
+    goff = np.zeros(G + 1, dtype=np.int64)
+    np.cumsum(ns, out=goff[1:])
+    m_in = np.rint(ns * deg_in / 2).astype(np.int64)
+    m_out = np.where(bs > 1, np.rint(ns * deg_out / 2), 0).astype(np.int64)
+
+    def per_draw(counts):
+        gidx = np.repeat(np.arange(G, dtype=np.int64), counts)
+        start = np.zeros(G + 1, dtype=np.int64)
+        np.cumsum(counts, out=start[1:])
+        local = np.arange(gidx.shape[0], dtype=np.int64) - start[gidx]
+        return gidx, local
+
+    def blocks_of(gidx, node):  # contiguous near-equal blocks: b(v) = floor(v * B / n) with a fix-up
+        n_ = ns[gidx]
+        B_ = bs[gidx]
+        b = (node * B_) // n_
+        # block_start(b) = floor(b * n / B); move to the block whose range holds node
+        b = np.where((b + 1) * n_ // B_ <= node, b + 1, b)
+        b = np.where(b * n_ // B_ > node, b - 1, b)
+        return b, (b * n_) // B_, ((b + 1) * n_) // B_
+    g1, i1 = per_draw(m_in)
+    sd1 = sds[g1]
+    u1 = (uniform01(sd1, 10, i1) * ns[g1]).astype(np.int64)
+    b1, lo1, hi1 = blocks_of(g1, u1)
+    v1 = lo1 + (uniform01(sd1, 11, i1) * (hi1 - lo1)).astype(np.int64)
+    g2, i2 = per_draw(m_out)
+    sd2 = sds[g2]
+    u2 = (uniform01(sd2, 12, i2) * ns[g2]).astype(np.int64)
+    b2, lo2, hi2 = blocks_of(g2, u2)
+    bl2 = hi2 - lo2
+    r = (uniform01(sd2, 13, i2) * (ns[g2] - bl2)).astype(np.int64)
+    v2 = np.where(r >= lo2, r + bl2, r)
+    # weights are drawn over each graph's concatenated (intra, inter) draw list
+    wi1 = i1
+    wi2 = m_in[g2] + i2
+    w1 = uniform_int(sd1, 14, wi1, wmin, wmax)
+    w2 = uniform_int(sd2, 14, wi2, wmin, wmax)
+    gg_ = np.concatenate([g1, g2])
+    u = np.concatenate([u1, u2]) + goff[gg_]
+    v = np.concatenate([v1, v2]) + goff[gg_]
+    w = np.concatenate([w1, w2])
+    keep = u != v
+    csr = from_edges(int(goff[-1]), u[keep], v[keep], w[keep])
+    return goff.astype(np.int32), csr.row_ptr, csr.col, csr.w, sds
 
 
 # ---------------------------------------------------------------------------
