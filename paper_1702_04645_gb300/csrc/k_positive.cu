@@ -18,9 +18,14 @@
 // subtree credited at the lowest common ancestor of each edge), the L x L
 // weights between the trees hanging from a cycle of length L >= 2, the best
 // split, and afterwards the members' components, totals and local gains.
+#include <algorithm>
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "forest_dev.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace slm {
 
@@ -57,10 +62,22 @@ __global__ void k_compact(long long cnt, const int32_t *list, const int32_t *roo
     }
 }
 
+__device__ __forceinline__ void d_mark(int cnt, const int32_t *list, const int32_t *root,
+                                       const int32_t *flag, int32_t *mark) {
+    GRID_STRIDE(k, cnt) mark[k] = flag[root[list[k]]] ? 1 : 0;
+}
+__device__ __forceinline__ void d_compact(int cnt, const int32_t *list, const int32_t *root,
+                                          const int32_t *flag, const int32_t *pos, int32_t *out) {
+    GRID_STRIDE(k, cnt) {
+        int v = list[k];
+        if (flag[root[v]]) out[pos[k]] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
-// one round
+// one round (phases of the persistent kernel below)
 // ---------------------------------------------------------------------------
-__global__ void k_round_init(int cnt, const int32_t *M, const int32_t *rp, const int32_t *root,
+__device__ __forceinline__ void k_round_init(int cnt, const int32_t *M, const int32_t *rp, const int32_t *root,
                              long long *subS, long long *subWA, long long *subWin,
                              long long *credit, long long *TS, int32_t *rlist, int32_t *rcnt,
                              int32_t *posr, int32_t *degm, long long *kacc) {
@@ -81,7 +98,7 @@ __global__ void k_round_init(int cnt, const int32_t *M, const int32_t *rp, const
     }
 }
 
-__global__ void k_root_init(int cnt, const int32_t *Rdev, const int32_t *rlist, const int32_t *a,
+__device__ __forceinline__ void k_root_init(int cnt, const int32_t *Rdev, const int32_t *rlist, const int32_t *a,
                             const int32_t *cdist, int32_t *L, long long *msz, int32_t *csz,
                             long long *bestsc, unsigned long long *bestkey) {
     const int R = *Rdev;
@@ -103,7 +120,7 @@ __global__ void k_root_init(int cnt, const int32_t *Rdev, const int32_t *rlist, 
 
 // every member adds itself to its non-cycle ancestors (itself included) and to
 // the total of the tree hanging from its entry
-__global__ void k_walk(int cnt, const int32_t *M, const int32_t *a, const int32_t *depth,
+__device__ __forceinline__ void k_walk(int cnt, const int32_t *M, const int32_t *a, const int32_t *depth,
                        const int32_t *s, const int32_t *kown, long long *subS, long long *subWA,
                        long long *TS) {
     GRID_STRIDE(k, cnt) {
@@ -119,7 +136,7 @@ __global__ void k_walk(int cnt, const int32_t *M, const int32_t *a, const int32_
     }
 }
 
-__global__ void k_cycle_order(int cnt, const int32_t *M, const uint8_t *oncycle,
+__device__ __forceinline__ void k_cycle_order(int cnt, const int32_t *M, const uint8_t *oncycle,
                               const int32_t *root, const int32_t *posr, const int32_t *L,
                               const int32_t *cdist, const int32_t *coff, int32_t *cyc) {
     GRID_STRIDE(k, cnt) {
@@ -147,7 +164,7 @@ __device__ __forceinline__ int owner_of(long long e, const int32_t *epref, int c
 
 // one thread per edge of a member: LCA credits inside a tree, tree-to-tree
 // weights of the cycle
-__global__ void k_edges(int cnt, const int32_t *M, const int32_t *epref, const int32_t *Edev,
+__device__ __forceinline__ void k_edges(int cnt, const int32_t *M, const int32_t *epref, const int32_t *Edev,
                         const int32_t *rp, const int32_t *col, const int32_t *w, const int32_t *a,
                         const uint8_t *oncycle, const int32_t *entry, const int32_t *depth,
                         const int32_t *root, const int32_t *posr, const int32_t *L,
@@ -175,7 +192,7 @@ __global__ void k_edges(int cnt, const int32_t *M, const int32_t *epref, const i
     }
 }
 
-__global__ void k_credit(int cnt, const int32_t *M, const int32_t *a, const int32_t *depth,
+__device__ __forceinline__ void k_credit(int cnt, const int32_t *M, const int32_t *a, const int32_t *depth,
                          const long long *credit, long long *subWin) {
     GRID_STRIDE(k, cnt) {
         int x = M[k];
@@ -189,7 +206,7 @@ __global__ void k_credit(int cnt, const int32_t *M, const int32_t *a, const int3
     }
 }
 
-__global__ void k_branch(int cnt, const int32_t *M, const uint8_t *oncycle, const int32_t *root,
+__device__ __forceinline__ void k_branch(int cnt, const int32_t *M, const uint8_t *oncycle, const int32_t *root,
                          const int32_t *posr, const int32_t *sigma, MParam mp,
                          const long long *subS, const long long *subWA, const long long *subWin,
                          long long *bestsc, unsigned long long *bestkey, int pass) {
@@ -208,7 +225,7 @@ __global__ void k_branch(int cnt, const int32_t *M, const uint8_t *oncycle, cons
 
 // one block per community with a cycle of length >= 2; one thread per p, the
 // part V = trees (p, q] grows with q: W(V+q, U-q) = W(V,U) + row(q) - 2 W(V,q)
-__global__ void k_cycle(const int32_t *Rdev, const int32_t *rlist, const int32_t *L, const int32_t *coff,
+__device__ __forceinline__ void k_cycle(const int32_t *Rdev, const int32_t *rlist, const int32_t *L, const int32_t *coff,
                         const int32_t *cyc, const long long *moff, const long long *Mw,
                         const long long *TS, const int32_t *sigma, MParam mp, int32_t n,
                         long long *bestsc, unsigned long long *bestkey, int pass) {
@@ -242,7 +259,7 @@ __global__ void k_cycle(const int32_t *Rdev, const int32_t *rlist, const int32_t
 
 // per split community: record the cut, set the totals of the two parts from
 // the subtree sums, and remove the cut assignments (a(u) <- u, a(v) <- v)
-__global__ void k_cut_info(const int32_t *Rdev, const int32_t *rlist,
+__device__ __forceinline__ void k_cut_info(const int32_t *Rdev, const int32_t *rlist,
                            const unsigned long long *bestkey, int32_t n, const int32_t *L,
                            const int32_t *coff, const int32_t *cyc, const long long *TS,
                            const int32_t *depth, const int32_t *cdist, const long long *subS,
@@ -293,7 +310,7 @@ __global__ void k_cut_info(const int32_t *Rdev, const int32_t *rlist,
 // cycle cut at positions p < q of the cycle roots the trees of (p, q] at
 // c_q and the others at c_p, each tree's depth growing by its distance along
 // the cycle.  Read-only phase: the new values go to per-member scratch.
-__global__ void k_forest_new(int cnt, const int32_t *M, const int32_t *a, const int32_t *root,
+__device__ __forceinline__ void k_forest_new(int cnt, const int32_t *M, const int32_t *a, const int32_t *root,
                              const int32_t *entry, const int32_t *depth, const int32_t *cdist,
                              const uint8_t *oncycle, const int32_t *posr, const int4 *cut,
                              const int32_t *coff, const int32_t *cyc, int4 *nf, uint8_t *noc) {
@@ -334,7 +351,7 @@ __global__ void k_forest_new(int cnt, const int32_t *M, const int32_t *a, const 
     }
 }
 
-__global__ void k_forest_write(int cnt, const int32_t *M, const int4 *nf, const uint8_t *noc,
+__device__ __forceinline__ void k_forest_write(int cnt, const int32_t *M, const int4 *nf, const uint8_t *noc,
                                int32_t *root, int32_t *entry, int32_t *depth, int32_t *cdist,
                                uint8_t *oncycle, int32_t *flag) {
     GRID_STRIDE(k, cnt) {
@@ -350,7 +367,7 @@ __global__ void k_forest_write(int cnt, const int32_t *M, const int4 *nf, const 
 }
 
 // own-community weight of every member, one thread per member edge
-__global__ void k_own_edges(int cnt, const int32_t *M, const int32_t *epref, const int32_t *Edev,
+__device__ __forceinline__ void k_own_edges(int cnt, const int32_t *M, const int32_t *epref, const int32_t *Edev,
                             const int32_t *rp, const int32_t *col, const int32_t *w,
                             const int32_t *root, long long *kacc) {
     const long long E = *Edev;
@@ -362,7 +379,7 @@ __global__ void k_own_edges(int cnt, const int32_t *M, const int32_t *epref, con
         if (j != x && root[j] == root[x]) add64(&kacc[k], w[p]);
     }
 }
-__global__ void k_own_finish(int cnt, const int32_t *M, const int32_t *s, MParam mp,
+__device__ __forceinline__ void k_own_finish(int cnt, const int32_t *M, const int32_t *s, MParam mp,
                              const int32_t *root, const int32_t *sigma, const long long *kacc,
                              int32_t *kown, int32_t *flag) {
     GRID_STRIDE(k, cnt) {
@@ -373,6 +390,262 @@ __global__ void k_own_finish(int cnt, const int32_t *M, const int32_t *s, MParam
         kown[i] = (int32_t)own;
         long long si = s[i];
         if (m * own - si * ((long long)sigma[ci] - si) < 0) flag[ci] = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Grid-wide exclusive prefix sums inside the persistent kernel: block t owns a
+// contiguous chunk; block sums are scanned by block 0.  Up to three arrays of
+// the same length are scanned together.  Ends after a grid barrier.
+// ---------------------------------------------------------------------------
+constexpr int kPosThreads = 256;
+
+template <class T> __device__ T block_sum(T v, T *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    T t = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kPosThreads / 32; k++) t += red[k];
+    __syncthreads();
+    if (threadIdx.x == 0) red[0] = t;
+    __syncthreads();
+    t = red[0];
+    __syncthreads();
+    return t;
+}
+
+// exclusive scan of one tile (one value per thread); returns the tile total
+template <class T> __device__ T tile_scan(T v, T &excl, T *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) red[wid] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T acc = 0;
+        for (int k = 0; k < kPosThreads / 32; k++) {
+            T c = red[k];
+            red[k] = acc;
+            acc += c;
+        }
+        red[kPosThreads / 32] = acc;
+    }
+    __syncthreads();
+    excl = red[wid] + x - v;
+    T tot = red[kPosThreads / 32];
+    __syncthreads();
+    return tot;
+}
+
+struct ScanSlots {
+    long long *a;
+    int32_t *b, *c;  // arrays (c may be null)
+    long long *tot_a;
+    int32_t *tot_b, *tot_c;
+    long long *bs_a;  // block sums, gridDim.x entries each
+    int32_t *bs_b, *bs_c;
+};
+
+__device__ void grid_scan(const ScanSlots &S, int n, cg::grid_group &grid) {
+    __shared__ long long red64[kPosThreads / 32 + 1];
+    __shared__ int32_t red32[kPosThreads / 32 + 1];
+    const int nb = gridDim.x;
+    const int chunk = (n + nb - 1) / nb;
+    const int lo = min(n, (int)blockIdx.x * chunk), hi = min(n, lo + chunk);
+    long long sa = 0;
+    int32_t sb = 0, sc = 0;
+    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        if (S.a) sa += S.a[k];
+        sb += S.b[k];
+        if (S.c) sc += S.c[k];
+    }
+    if (S.a) sa = block_sum<long long>(sa, red64);
+    sb = block_sum<int32_t>(sb, red32);
+    if (S.c) sc = block_sum<int32_t>(sc, red32);
+    if (threadIdx.x == 0) {
+        if (S.a) S.bs_a[blockIdx.x] = sa;
+        S.bs_b[blockIdx.x] = sb;
+        if (S.c) S.bs_c[blockIdx.x] = sc;
+    }
+    grid.sync();
+    if (blockIdx.x == 0) {
+        long long ca = 0;
+        int32_t cb = 0, cc = 0;
+        for (int t0 = 0; t0 < nb; t0 += blockDim.x) {
+            const int t = t0 + threadIdx.x;
+            long long va = (S.a && t < nb) ? S.bs_a[t] : 0, ea = 0;
+            int32_t vb = t < nb ? S.bs_b[t] : 0, eb = 0;
+            int32_t vc = (S.c && t < nb) ? S.bs_c[t] : 0, ec = 0;
+            long long ta = S.a ? tile_scan<long long>(va, ea, red64) : 0;
+            int32_t tb = tile_scan<int32_t>(vb, eb, red32);
+            int32_t tc = S.c ? tile_scan<int32_t>(vc, ec, red32) : 0;
+            if (t < nb) {
+                if (S.a) S.bs_a[t] = ca + ea;
+                S.bs_b[t] = cb + eb;
+                if (S.c) S.bs_c[t] = cc + ec;
+            }
+            ca += ta;
+            cb += tb;
+            cc += tc;
+        }
+        if (threadIdx.x == 0) {
+            if (S.a) *S.tot_a = ca;
+            *S.tot_b = cb;
+            if (S.c) *S.tot_c = cc;
+        }
+    }
+    grid.sync();
+    long long ca = S.a ? S.bs_a[blockIdx.x] : 0;
+    int32_t cb = S.bs_b[blockIdx.x], cc = S.c ? S.bs_c[blockIdx.x] : 0;
+    for (int k0 = lo; k0 < hi; k0 += blockDim.x) {
+        const int k = k0 + threadIdx.x;
+        long long va = (S.a && k < hi) ? S.a[k] : 0, ea = 0;
+        int32_t vb = k < hi ? S.b[k] : 0, eb = 0;
+        int32_t vc = (S.c && k < hi) ? S.c[k] : 0, ec = 0;
+        long long ta = S.a ? tile_scan<long long>(va, ea, red64) : 0;
+        int32_t tb = tile_scan<int32_t>(vb, eb, red32);
+        int32_t tc = S.c ? tile_scan<int32_t>(vc, ec, red32) : 0;
+        if (k < hi) {
+            if (S.a) S.a[k] = ca + ea;
+            S.b[k] = cb + eb;
+            if (S.c) S.c[k] = cc + ec;
+        }
+        ca += ta;
+        cb += tb;
+        cc += tc;
+    }
+    grid.sync();
+}
+
+// Control block shared by the host and the persistent kernel.
+struct PosCtrl {
+    int32_t cnt;     // members of the current round
+    int32_t R;       // roots of the current round
+    int32_t E;       // member edges of the current round
+    int32_t ctot;    // cycle-order pool entries in use
+    long long mtot;  // tree-weight pool entries in use
+    int32_t next;    // members kept for the next round
+    int32_t error;   // 1: round limit, 2: pool too small
+    long long rounds, visits, splits;
+};
+
+struct PosArgs {
+    int32_t n;
+    const int32_t *rp, *col, *w, *s;
+    MParam m;
+    int32_t *a, *root, *entry, *depth, *cdist;
+    uint8_t *oncycle;
+    int32_t *sigma, *flag, *kown, *listA, *listB, *rlist, *posr, *L, *coff, *epref, *mark, *cyc;
+    long long *msz, *subS, *subWA, *subWin, *credit, *TS, *bestsc, *kacc, *Mw;
+    unsigned long long *bestkey;
+    int4 *cut, *nf;
+    uint8_t *noc;
+    int32_t *splits_per_graph;
+    long long *bs64;
+    int32_t *bs32a, *bs32b;
+    long long pool_cap, cyc_cap, max_rounds;
+    PosCtrl *ctrl;
+};
+
+// All rounds of POSITIVE in one cooperative launch: the phases of a round are
+// separated by grid barriers and the loop ends on the device when no member
+// is left.
+__global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
+    cg::grid_group grid = cg::this_grid();
+    PosCtrl *C = A.ctrl;
+    int32_t *M = A.listA, *M2 = A.listB;
+    const int32_t n = A.n;
+    for (;;) {
+        const int cnt = C->cnt;
+        if (cnt == 0) break;
+        if (C->rounds >= A.max_rounds) {
+            if (grid.thread_rank() == 0) C->error = 1;
+            break;
+        }
+        k_round_init(cnt, M, A.rp, A.root, A.subS, A.subWA, A.subWin, A.credit, A.TS, A.rlist, &C->R,
+                     A.posr, A.epref, A.kacc);
+        grid.sync();
+        k_root_init(cnt, &C->R, A.rlist, A.a, A.cdist, A.L, A.msz, A.coff, A.bestsc, A.bestkey);
+        grid.sync();
+        {
+            ScanSlots S{A.msz, A.coff, A.epref, &C->mtot, &C->ctot, &C->E, A.bs64, A.bs32a, A.bs32b};
+            grid_scan(S, cnt, grid);
+        }
+        if (C->mtot > A.pool_cap || C->ctot > A.cyc_cap) {
+            if (grid.thread_rank() == 0) C->error = 2;
+            break;
+        }
+        const long long mtot = C->mtot, ctot = C->ctot;
+        GRID_STRIDE(k, mtot) A.Mw[k] = 0;
+        GRID_STRIDE(k, ctot) A.cyc[k] = -1;
+        grid.sync();
+        k_walk(cnt, M, A.a, A.depth, A.s, A.kown, A.subS, A.subWA, A.TS);
+        if (ctot > 0) k_cycle_order(cnt, M, A.oncycle, A.root, A.posr, A.L, A.cdist, A.coff, A.cyc);
+        k_edges(cnt, M, A.epref, &C->E, A.rp, A.col, A.w, A.a, A.oncycle, A.entry, A.depth, A.root,
+                A.posr, A.L, A.cdist, A.msz, A.Mw, A.credit);
+        grid.sync();
+        k_credit(cnt, M, A.a, A.depth, A.credit, A.subWin);
+        grid.sync();
+        for (int pass = 0; pass < 2; pass++) {
+            k_branch(cnt, M, A.oncycle, A.root, A.posr, A.sigma, A.m, A.subS, A.subWA, A.subWin,
+                     A.bestsc, A.bestkey, pass);
+            if (ctot > 0)
+                k_cycle(&C->R, A.rlist, A.L, A.coff, A.cyc, A.msz, A.Mw, A.TS, A.sigma, A.m, n,
+                        A.bestsc, A.bestkey, pass);
+            grid.sync();
+        }
+        k_cut_info(&C->R, A.rlist, A.bestkey, n, A.L, A.coff, A.cyc, A.TS, A.depth, A.cdist, A.subS,
+                   A.sigma, A.cut, A.a, A.m.gid, A.splits_per_graph);
+        grid.sync();
+        k_forest_new(cnt, M, A.a, A.root, A.entry, A.depth, A.cdist, A.oncycle, A.posr, A.cut, A.coff,
+                     A.cyc, A.nf, A.noc);
+        grid.sync();
+        k_forest_write(cnt, M, A.nf, A.noc, A.root, A.entry, A.depth, A.cdist, A.oncycle, A.flag);
+        grid.sync();
+        k_own_edges(cnt, M, A.epref, &C->E, A.rp, A.col, A.w, A.root, A.kacc);
+        grid.sync();
+        k_own_finish(cnt, M, A.s, A.m, A.root, A.sigma, A.kacc, A.kown, A.flag);
+        grid.sync();
+        d_mark(cnt, M, A.root, A.flag, A.mark);
+        grid.sync();
+        {
+            ScanSlots S{nullptr, A.mark, nullptr, nullptr, &C->next, nullptr, nullptr, A.bs32a, nullptr};
+            grid_scan(S, cnt, grid);
+        }
+        d_compact(cnt, M, A.root, A.flag, A.mark, M2);
+        if (grid.thread_rank() == 0) {
+            C->rounds += 1;
+            C->visits += cnt;
+            C->splits += C->R;
+            C->cnt = C->next;
+            C->R = 0;
+        }
+        grid.sync();
+        int32_t *tmp = M;
+        M = M2;
+        M2 = tmp;
+    }
+}
+
+// bound of the pools: cycle lengths never grow during POSITIVE
+__global__ void k_pool_bound(int cnt, const int32_t *M, const int32_t *root, const int32_t *a,
+                             const int32_t *cdist, unsigned long long *msum,
+                             unsigned long long *csum) {
+    GRID_STRIDE(k, cnt) {
+        int r = M[k];
+        if (root[r] != r) continue;
+        long long l = (a[r] == r) ? 1 : cdist[a[r]] + 1;
+        if (l >= 2) {
+            atomicAdd(msum, (unsigned long long)(l * l));
+            atomicAdd(csum, (unsigned long long)l);
+        }
     }
 }
 
@@ -423,101 +696,96 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     int32_t *M = ps.listA.as<int32_t>(), *M2 = ps.listB.as<int32_t>();
     int32_t cnt = compact_members(n, nullptr, f.root, flag, M, ps.mark, ps.tot, st);
 
-    long long splits = 0, rounds = 0, visits = 0;
+    if (cnt == 0) return 0;
     long long *subS = ps.subS.as<long long>(), *subWA = ps.subWA.as<long long>(),
               *subWin = ps.subWin.as<long long>(), *credit = ps.credit.as<long long>(),
               *TS = ps.TS.as<long long>(), *msz = ps.msz.as<long long>(),
               *bestsc = ps.bestsc.as<long long>();
     unsigned long long *bestkey = ps.bestkey.as<unsigned long long>();
-    int32_t *rlist = ps.rlist.as<int32_t>(), *posr = ps.posr.as<int32_t>(), *L = ps.L.as<int32_t>(),
-            *coff = ps.coff.as<int32_t>();
-    // per round header on the device: R (roots), E (member edges), and the
-    // sizes of the cycle pools; read back once per round
-    struct Hdr {
-        long long mtot;
-        int32_t ctot, pad0;
-        int32_t R, E;
-    };
-    ps.hdr.ensure(sizeof(Hdr), st);
     ps.epref.ensure(4 * (N + 1), st);
     ps.kacc.ensure(8 * (N + 1), st);
     ps.cut.ensure(16 * (N + 1), st);
     ps.nf.ensure(16 * (N + 1), st);
     ps.noc.ensure(N + 1, st);
-    Hdr *hdr = ps.hdr.as<Hdr>();
-    int32_t *epref = ps.epref.as<int32_t>();
-    long long *kacc = ps.kacc.as<long long>();
-    const int ge = kNumSMs * 16;  // grid of the edge-parallel kernels (grid-stride)
-    while (cnt > 0) {
-        // every round splits at least one community, so n rounds always suffice
-        if (++rounds > (long long)n) fail(SLM_ERR_TIMEOUT, "POSITIVE did not settle within n rounds");
-        visits += cnt;
-        const int gm = grid_for(cnt, 256);
-        SLM_CUDA(cudaMemsetAsync(hdr, 0, sizeof(Hdr), st));
-        k_round_init<<<gm, 256, 0, st>>>(cnt, M, rp, f.root, subS, subWA, subWin, credit, TS, rlist,
-                                         &hdr->R, posr, epref, kacc);
-        SLM_LAUNCH_CHECK();
-        k_root_init<<<gm, 256, 0, st>>>(cnt, &hdr->R, rlist, a, f.cdist, L, msz, coff, bestsc, bestkey);
-        SLM_LAUNCH_CHECK();
-        exclusive_scan_i64(msz, msz, cnt, &hdr->mtot, st);
-        exclusive_scan_i32(coff, coff, cnt, &hdr->ctot, st);
-        exclusive_scan_i32(epref, epref, cnt, &hdr->E, st);
-        Hdr h;
-        SLM_CUDA(cudaMemcpyAsync(&h, hdr, sizeof h, cudaMemcpyDeviceToHost, st));
-        SLM_CUDA(cudaStreamSynchronize(st));
-        const long long mtot = h.mtot;
-        const long long ctot = h.ctot;
-        const int R = h.R;
-        // pools for the cycle orders and the L x L tree weights
-        ps.pool.ensure(8 * (size_t)(mtot > 0 ? mtot : 1), st);
-        ps.cyc.ensure(4 * (size_t)(ctot > 0 ? ctot : 1), st);
-        long long *Mw = ps.pool.as<long long>();
-        if (mtot > 0) SLM_CUDA(cudaMemsetAsync(Mw, 0, 8 * (size_t)mtot, st));
-        if (ctot > 0) SLM_CUDA(cudaMemsetAsync(ps.cyc.get(), 0xff, 4 * (size_t)ctot, st));
-
-        k_walk<<<gm, 256, 0, st>>>(cnt, M, a, f.depth, s, kown, subS, subWA, TS);
-        SLM_LAUNCH_CHECK();
-        if (ctot > 0) {
-            k_cycle_order<<<gm, 256, 0, st>>>(cnt, M, f.oncycle, f.root, posr, L, f.cdist, coff,
-                                              ps.cyc.as<int32_t>());
-            SLM_LAUNCH_CHECK();
-        }
-        k_edges<<<ge, 256, 0, st>>>(cnt, M, epref, &hdr->E, rp, col, w, a, f.oncycle, f.entry,
-                                    f.depth, f.root, posr, L, f.cdist, msz, Mw, credit);
-        SLM_LAUNCH_CHECK();
-        k_credit<<<gm, 256, 0, st>>>(cnt, M, a, f.depth, credit, subWin);
-        SLM_LAUNCH_CHECK();
-        for (int pass = 0; pass < 2; pass++) {
-            k_branch<<<gm, 256, 0, st>>>(cnt, M, f.oncycle, f.root, posr, sigma, m, subS, subWA,
-                                         subWin, bestsc, bestkey, pass);
-            SLM_LAUNCH_CHECK();
-            if (ctot > 0) {
-                k_cycle<<<grid_for(R, 1, kNumSMs * 8), 128, 0, st>>>(
-                    &hdr->R, rlist, L, coff, ps.cyc.as<int32_t>(), msz, Mw, TS, sigma, m, n, bestsc,
-                    bestkey, pass);
-                SLM_LAUNCH_CHECK();
-            }
-        }
-        k_cut_info<<<grid_for(R, 256), 256, 0, st>>>(&hdr->R, rlist, bestkey, n, L, coff,
-                                                      ps.cyc.as<int32_t>(), TS, f.depth, f.cdist,
-                                                      subS, sigma, ps.cut.as<int4>(), a, m.gid,
-                                                      splits_per_graph);
-        SLM_LAUNCH_CHECK();
-        splits += R;
-        k_forest_new<<<gm, 256, 0, st>>>(cnt, M, a, f.root, f.entry, f.depth, f.cdist, f.oncycle,
-                                         posr, ps.cut.as<int4>(), coff, ps.cyc.as<int32_t>(),
-                                         ps.nf.as<int4>(), ps.noc.as<uint8_t>());
-        SLM_LAUNCH_CHECK();
-        k_forest_write<<<gm, 256, 0, st>>>(cnt, M, ps.nf.as<int4>(), ps.noc.as<uint8_t>(), f.root,
-                                           f.entry, f.depth, f.cdist, f.oncycle, flag);
-        SLM_LAUNCH_CHECK();
-        k_own_edges<<<ge, 256, 0, st>>>(cnt, M, epref, &hdr->E, rp, col, w, f.root, kacc);
-        SLM_LAUNCH_CHECK();
-        k_own_finish<<<gm, 256, 0, st>>>(cnt, M, s, m, f.root, sigma, kacc, kown, flag);
-        SLM_LAUNCH_CHECK();
-        cnt = compact_members(cnt, M, f.root, flag, M2, ps.mark, ps.tot, st);
-        std::swap(M, M2);
-    }
+    ps.mark.ensure(4 * (N + 1), st);
+    // pools sized once: the first round holds the longest cycles
+    ps.hdr.ensure(64, st);
+    SLM_CUDA(cudaMemsetAsync(ps.hdr.get(), 0, 64, st));
+    unsigned long long *bnd = ps.hdr.as<unsigned long long>();
+    k_pool_bound<<<grid_for(cnt, 256), 256, 0, st>>>(cnt, M, f.root, a, f.cdist, bnd, bnd + 1);
+    SLM_LAUNCH_CHECK();
+    unsigned long long hb[2] = {0, 0};
+    SLM_CUDA(cudaMemcpyAsync(hb, bnd, 16, cudaMemcpyDeviceToHost, st));
+    SLM_CUDA(cudaStreamSynchronize(st));
+    ps.pool.ensure(8 * (size_t)(hb[0] > 0 ? hb[0] : 1), st);
+    ps.cyc.ensure(4 * (size_t)(hb[1] > 0 ? hb[1] : 1), st);
+    // one cooperative launch runs every round
+    int dev = 0, sms = 0, per_sm = 0;
+    SLM_CUDA(cudaGetDevice(&dev));
+    SLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_positive_rounds, kPosThreads, 0));
+    if (per_sm < 1) fail(SLM_ERR_CUDA, "POSITIVE kernel cannot be resident");
+    const int nblocks = sms * std::min(per_sm, 4);
+    ps.bs.ensure(8 * (size_t)nblocks * 3, st);
+    ps.ctrl.ensure(sizeof(PosCtrl), st);
+    PosCtrl hc{};
+    hc.cnt = cnt;
+    SLM_CUDA(cudaMemcpyAsync(ps.ctrl.get(), &hc, sizeof hc, cudaMemcpyHostToDevice, st));
+    PosArgs A;
+    A.n = n;
+    A.rp = rp;
+    A.col = col;
+    A.w = w;
+    A.s = s;
+    A.m = m;
+    A.a = a;
+    A.root = f.root;
+    A.entry = f.entry;
+    A.depth = f.depth;
+    A.cdist = f.cdist;
+    A.oncycle = f.oncycle;
+    A.sigma = sigma;
+    A.flag = flag;
+    A.kown = kown;
+    A.listA = M;
+    A.listB = M2;
+    A.rlist = ps.rlist.as<int32_t>();
+    A.posr = ps.posr.as<int32_t>();
+    A.L = ps.L.as<int32_t>();
+    A.coff = ps.coff.as<int32_t>();
+    A.epref = ps.epref.as<int32_t>();
+    A.mark = ps.mark.as<int32_t>();
+    A.cyc = ps.cyc.as<int32_t>();
+    A.msz = msz;
+    A.subS = subS;
+    A.subWA = subWA;
+    A.subWin = subWin;
+    A.credit = credit;
+    A.TS = TS;
+    A.bestsc = bestsc;
+    A.kacc = ps.kacc.as<long long>();
+    A.Mw = ps.pool.as<long long>();
+    A.bestkey = bestkey;
+    A.cut = ps.cut.as<int4>();
+    A.nf = ps.nf.as<int4>();
+    A.noc = ps.noc.as<uint8_t>();
+    A.splits_per_graph = splits_per_graph;
+    A.bs64 = ps.bs.as<long long>();
+    A.bs32a = reinterpret_cast<int32_t *>(ps.bs.as<long long>() + nblocks);
+    A.bs32b = reinterpret_cast<int32_t *>(ps.bs.as<long long>() + 2 * nblocks);
+    A.pool_cap = (long long)(hb[0] > 0 ? hb[0] : 1);
+    A.cyc_cap = (long long)(hb[1] > 0 ? hb[1] : 1);
+    A.max_rounds = (long long)n;  // every round splits at least one community
+    A.ctrl = ps.ctrl.as<PosCtrl>();
+    void *kargs[] = {&A};
+    SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_positive_rounds, dim3(nblocks),
+                                         dim3(kPosThreads), kargs, 0, st));
+    SLM_LAUNCH_CHECK();
+    SLM_CUDA(cudaMemcpyAsync(&hc, ps.ctrl.get(), sizeof hc, cudaMemcpyDeviceToHost, st));
+    SLM_CUDA(cudaStreamSynchronize(st));
+    if (hc.error == 1) fail(SLM_ERR_TIMEOUT, "POSITIVE did not settle within n rounds");
+    if (hc.error == 2) fail(SLM_ERR_CUDA, "POSITIVE cycle pools smaller than their bound");
+    const long long splits = hc.splits, rounds = hc.rounds, visits = hc.visits;
     if (rounds_out) *rounds_out = rounds;
     if (visits_out) *visits_out = visits;
     return splits;

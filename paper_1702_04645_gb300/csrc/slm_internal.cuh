@@ -261,7 +261,7 @@ void apply_moves(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt,
 
 struct PositiveScratch {
     DevBuf flag, kown, listA, listB, rlist, posr, L, coff, subS, subWA, subWin, credit, TS, msz,
-        bestsc, bestkey, pool, cyc, cnt, mark, tot, hdr, epref, kacc, cut, nf, noc;
+        bestsc, bestkey, pool, cyc, cnt, mark, tot, hdr, epref, kacc, cut, nf, noc, bs, ctrl;
 };
 // Algorithm POSITIVE until no node has a negative local gain.  a and the
 // forest f are updated in place (only the members of split communities are
