@@ -40,6 +40,10 @@ WORKLOAD_DESC = ("R-MAT scale 20, 16*2^20 draws (a,b,c)=(0.57,0.19,0.19), w~U[1,
 METRIC = "local-move GTEPS"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
+# DRAM bytes (read + write) of one level-0 scan of the benchmark graph, from the
+# ncu capture summarised in profiles/scan_rmat_s20_level0.md; None once the
+# scan kernels change after that capture
+SCAN_TRAFFIC_L0 = 585.2e6
 
 
 def scan_bytes(n: int, nnz: int) -> int:
@@ -239,6 +243,161 @@ def run_forest(args):
     return 0
 
 
+def run_scan(args):
+    """The MAXIMAL scan alone on the level-0 state of the benchmark graph
+    (after ASSIGN, COMPONENTS and POSITIVE), repeated: the small, single-kernel
+    case used for profiling the scan.  Each repetition goes through
+    slm_step_scan (buckets, community totals, scan); the line reports the
+    entry point's time per call."""
+    import torch
+    import paper_1702_04645_gb300 as slm
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    g = load_graph()
+    rp, col, w = (torch.from_numpy(x).to(dev) for x in (g.row_ptr, g.col, g.w))
+    s, m = slm.step_strengths(rp, col, w)
+    a = slm.step_assign(rp, col, w, s, m)
+    a, root, _ = slm.step_positive(rp, col, w, s, m, a)
+    for _ in range(args.warmup):
+        slm.step_scan(rp, col, w, s, m, root)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        slm.step_scan(rp, col, w, s, m, root)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    hbm, kind = peaks()
+    gbs = scan_bytes(g.n, g.nnz) / (ms / 1e3) / 1e9
+    if rank == 0:
+        print(json.dumps({"metric": "level-0 scan call GB/s", "value": gbs, "unit": "GB/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "higher_is_better": True, "dtype": "int64",
+                          "data": "synthetic",
+                          "config": {"workload": WORKLOAD + "_scan_level0", "n": g.n, "nnz": g.nnz},
+                          "frac_of_peak": gbs / hbm, "peak_source": kind}), flush=True)
+    return 0
+
+
+SERVED_DESC = ("Poisson arrivals (mean {rate:g} req/s for {dur:g} s, seed 4) of R-MAT requests "
+               "(a,b,c)=(0.57,0.19,0.19), n log-uniform in [1e3, 1e6], 8n draws, w~U[1,8]; "
+               "request k runs graph k mod {pool} of a pool of {pool} distinct graphs drawn from "
+               "the stream's own sizes, with its own acceptance seed")
+
+
+def _served_graph_job(args):
+    n, sd = args
+    g = gg.served_graph(n, sd)
+    return g.row_ptr, g.col, g.w
+
+
+def served_pool(reqs, pool):
+    """Graphs of the first `pool` requests, generated in spawned workers."""
+    import multiprocessing as mp
+    jobs = [(n, sd) for _, n, sd in reqs[:pool]]
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as p:
+        return p.map(_served_graph_job, jobs)
+
+
+def run_served(args):
+    """Served form: requests arrive on a Poisson clock and are submitted to
+    the request server as they arrive; latency is submission to partition in
+    host memory.  Beside it, a per-graph loop of slm_run over a sample of the
+    same requests (same partitions required)."""
+    import threading
+    import torch
+    import paper_1702_04645_gb300 as slm
+    rank, world, local = dist_env()
+    reqs = gg.served_stream(rate=args.rate, duration=args.duration)
+    pool = served_pool(reqs, args.pool)  # before any GPU call (spawned workers)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    budget = 60 << 30
+    sv = slm.Server(budget_bytes=budget, slots=args.slots)
+    # warm-up: one request of every pool graph through the server
+    warm = [sv.submit(*pool[k], seed=1) for k in range(min(args.warmup, len(pool)))]
+    for t in warm:
+        sv.wait(t)
+        sv.result(t)
+    launches0 = slm.launch_count()
+    tickets = []
+    late = []
+
+    def producer():
+        t0 = time.perf_counter()
+        for k, (ta, n, sd) in enumerate(reqs):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            late.append(time.perf_counter() - t0 - ta)
+            rp, col, w = pool[k % len(pool)]
+            tickets.append(sv.submit(rp, col, w, seed=1000 + k, accept_p32=slm.P_HALF))
+
+    with ClockSampler(local) as clk:
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        for t in tickets:
+            sv.wait(t)
+    launches = slm.launch_count() - launches0
+    infos = [sv.info(t) for t in tickets]
+    stats = sv.stats().as_dict()
+    lat = np.array([i.t_done - i.t_submit for i in infos])
+    t_first = min(i.t_submit for i in infos)
+    t_last = max(i.t_done for i in infos)
+    gps = len(infos) / (t_last - t_first)
+    ok = all(i.state == slm.REQ_DONE for i in infos)
+    edges = sum(i.edges_scanned for i in infos)
+    # per-graph loop of the plain path on a sample, partitions compared
+    sample = list(range(0, len(reqs), max(1, len(reqs) // args.loop_sample)))[: args.loop_sample]
+    res = {k: sv.result(tickets[k], release=False) for k in sample}
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    identical = True
+    for k in sample:
+        rp, col, w = pool[k % len(pool)]
+        G = slm.Graph(rp, col, w)
+        G.run(seed=1000 + k, accept_p32=slm.P_HALF, stream=stream.cuda_stream)
+        lab, K = G.partition(-1)
+        q = G.modularity(-1)
+        G.close()
+        identical &= bool(np.array_equal(lab, res[k][0]) and K == res[k][1] and q == res[k][2])
+    torch.cuda.synchronize(dev)
+    loop_gps = len(sample) / (time.perf_counter() - t0)
+    sv.close()
+    if rank == 0:
+        line = {"metric": "graphs/s (served)", "value": gps, "unit": "graphs/s", "n_gpus": world,
+                "steps": len(infos), "warmup": len(warm), "ms_per_step": 1e3 / gps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int64", "data": "synthetic",
+                "config": {"workload": "served_rmat_poisson",
+                           "desc": SERVED_DESC.format(rate=args.rate, dur=args.duration,
+                                                      pool=args.pool),
+                           "requests": len(infos), "slots": args.slots,
+                           "hbm_budget_bytes": budget,
+                           "mean_n": float(np.mean([i.n for i in infos])),
+                           "mean_nnz": float(np.mean([i.nnz for i in infos]))},
+                "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
+                               "p99": float(np.percentile(lat, 99) * 1e3),
+                               "mean": float(lat.mean() * 1e3), "max": float(lat.max() * 1e3)},
+                "all_done": ok, "local_move_gteps": edges / (t_last - t_first) / 1e9,
+                "server": stats,
+                "max_submit_lateness_ms": float(max(late) * 1e3) if late else 0.0,
+                "per_graph_loop": {"value": loop_gps, "unit": "graphs/s",
+                                   "sample": f"slm_run on {len(sample)} requests spread over the "
+                                             "stream, one after the other",
+                                   "identical_partitions": identical},
+                "speedup_vs_loop": gps / loop_gps,
+                "gpu_launches": int(launches), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def peaks():
     try:
         d = json.load(open(PEAKS))
@@ -282,7 +441,12 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["rmat", "forest"], default="rmat")
+    ap.add_argument("--workload", choices=["rmat", "forest", "scan", "served"], default="rmat")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals")
+    ap.add_argument("--pool", type=int, default=48, help="served: distinct graphs")
+    ap.add_argument("--slots", type=int, default=16, help="served: server slots")
+    ap.add_argument("--loop-sample", type=int, default=48, help="served: requests run one by one")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -290,6 +454,10 @@ def main():
         return run_reference(args)
     if args.workload == "forest":
         return run_forest(args)
+    if args.workload == "scan":
+        return run_scan(args)
+    if args.workload == "served":
+        return run_served(args)
 
     import torch
     import paper_1702_04645_gb300 as slm
@@ -327,6 +495,8 @@ def main():
 
     launches0 = slm.launch_count()
     phase_tot = {}
+    pos_prof = {}
+    scan_l0 = (0.0, 0)
     barrier()
     with ClockSampler(local) as clk:
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -337,6 +507,10 @@ def main():
             for k, (ms, cnt) in G.timing().items():
                 a, b = phase_tot.get(k, (0.0, 0))
                 phase_tot[k] = (a + ms, b + cnt)
+            for k, ms in G.positive_profile().items():
+                pos_prof[k] = pos_prof.get(k, 0.0) + ms
+            a, b = G.scan_timing(0)
+            scan_l0 = (scan_l0[0] + a, scan_l0[1] + b)
         ev1.record(stream)
         barrier()
     launches = slm.launch_count() - launches0
@@ -348,23 +522,25 @@ def main():
     ms_per_step = elapsed_ms / args.steps
     value = units * args.steps * world / (elapsed_ms / 1e3) / 1e9
 
-    # roofline of the scan kernel (accumulate + argmax), timed on the run's stream
+    # roofline of the scan (accumulate + argmax) on the input graph (level 0),
+    # where it moves most of its bytes; timed with CUDA events on the run's stream
     hbm, peak_kind = peaks()
+    l0_ms, l0_cnt = scan_l0
+    l0_bytes = scan_bytes(g.n, g.nnz)
+    achieved = l0_bytes * l0_cnt / (l0_ms / 1e3) / 1e9 if l0_ms > 0 else None
     scan_ms, scan_cnt = phase_tot.get("scan", (0.0, 0))
-    achieved = (bytes_per_step * args.steps / 1e9) / (scan_ms / 1e3) if scan_ms > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": (achieved / hbm) if achieved else None, "traffic": None,
-                "kernel": "scan (accumulate + argmax), all degree buckets of one sweep",
-                "peak_source": peak_kind,
-                "launches_timed": scan_cnt,
-                "avg_launch_ms": scan_ms / scan_cnt if scan_cnt else None,
-                "bytes_per_step": bytes_per_step}
-    prof = os.path.join(ROOT, "profiles", "scan_traffic_rmat_s20.json")
-    if os.path.exists(prof):
-        try:
-            roofline["traffic"] = json.load(open(prof)).get("traffic_per_sweep_level0")
-        except Exception:
-            pass
+                "frac": (achieved / hbm) if achieved else None,
+                "traffic": SCAN_TRAFFIC_L0,
+                "kernel": "MAXIMAL scan (accumulate + argmax), all degree buckets, level-0 graph",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                               else "fallback 6,800 GB/s",
+                "algorithmic_bytes_per_launch": l0_bytes,
+                "launches_timed": l0_cnt,
+                "avg_launch_ms": l0_ms / l0_cnt if l0_cnt else None,
+                "all_levels": {"achieved": (bytes_per_step * args.steps / 1e9) / (scan_ms / 1e3)
+                               if scan_ms > 0 else None, "launches": scan_cnt,
+                               "avg_launch_ms": scan_ms / scan_cnt if scan_cnt else None}}
 
     # end to end through the C ABI with host buffers: copy in, run, read the partition
     e2e = None
@@ -406,7 +582,8 @@ def main():
                                        if k != "positive_rounds"},
                 "positive_per_step": {
                     "rounds": phase_tot.get("positive_rounds", (0, 0))[1] / args.steps,
-                    "member_visits": phase_tot.get("positive_rounds", (0, 0))[0] / args.steps}}
+                    "member_visits": phase_tot.get("positive_rounds", (0, 0))[0] / args.steps,
+                    "round_phases_ms": {k: round(v / args.steps, 3) for k, v in pos_prof.items()}}}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -146,6 +146,23 @@ slm_status slm_get_trace(const slm_graph *g, int64_t *rows, int64_t cap, int64_t
  * visits summed over those rounds. */
 slm_status slm_get_timing(const slm_graph *g, double *ms8, int64_t *count8);
 
+/* Device time of the MAXIMAL scans (accumulate + argmax) of one level of the
+ * last slm_run made with SLM_FLAG_TIMING (level = -1: the last, unrecorded
+ * level): *ms milliseconds over *count scans, CUDA events on the run's
+ * stream.  Without SLM_FLAG_TIMING both are 0. */
+slm_status slm_get_scan_timing(const slm_graph *g, int32_t level, double *ms, int64_t *count);
+
+/* Profile of the POSITIVE rounds of the last slm_run made with
+ * SLM_FLAG_TIMING: nanoseconds of device time per phase of a round, summed
+ * over every round of the run, read from the GPU's global timer at the grid
+ * barriers that end the phases.  Phases: 0 round set-up, 1 offsets of the
+ * member lists (prefix sums), 2 ancestor walks and per-edge credits, 3
+ * subtree credits, 4 choice of the best cut (Algorithm POSITIVE, optimal
+ * bisection), 5 application of the cuts, 6 new components of the members,
+ * 7 local gains g(i), 8 member list of the next round.  Copies at most `cap`
+ * values into `ns` (host memory) and sets *len to the number of phases. */
+slm_status slm_get_positive_profile(const slm_graph *g, int64_t *ns, int32_t cap, int32_t *len);
+
 /* Number of kernels this library has launched in the process so far. */
 uint64_t slm_launch_count(void);
 

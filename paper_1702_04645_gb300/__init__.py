@@ -18,7 +18,7 @@ import numpy as np
 
 from .build_lib import LIB, build  # noqa: F401
 
-__all__ = ["Graph", "Batch", "pack_forest", "Options", "LevelStats", "SlmError", "build", "load", "step_strengths",
+__all__ = ["Graph", "Batch", "Server", "pack_forest", "Options", "LevelStats", "SlmError", "build", "load", "step_strengths",
            "step_assign", "step_components", "step_scan", "step_branch_gain", "step_maximal",
            "step_positive", "step_compact", "step_aggregate", "step_modularity",
            "FLAG_NO_POSITIVE", "FLAG_STRICT", "P_HALF", "P_ALWAYS"]
@@ -30,6 +30,8 @@ FLAG_STRICT = 2
 FLAG_TIMING = 4
 PHASES = ["assign", "components", "positive", "scan", "move", "level", "sigma",
           "positive_rounds"]
+POSITIVE_PHASES = ["setup", "offsets", "walks_edges", "credits", "best_cut", "apply_cut",
+                   "components", "local_gains", "next_list"]
 P_HALF = 1 << 31
 P_ALWAYS = 1 << 32
 
@@ -44,11 +46,15 @@ EXPORTS = ["slm_default_options", "slm_create_graph", "slm_run", "slm_num_levels
            "slm_destroy_graph", "slm_status_string", "slm_last_error", "slm_step_strengths",
            "slm_step_assign", "slm_step_components", "slm_step_scan", "slm_step_branch_gain",
            "slm_step_maximal", "slm_step_positive", "slm_step_compact", "slm_step_aggregate",
-           "slm_step_modularity", "slm_get_trace", "slm_get_timing", "slm_launch_count",
+           "slm_step_modularity", "slm_get_trace", "slm_get_timing", "slm_get_positive_profile", "slm_get_scan_timing",
+           "slm_launch_count",
            "slm_step_modularity_noalloc", "slm_batch_create", "slm_batch_run",
            "slm_batch_num_graphs", "slm_batch_num_levels", "slm_batch_get_partition",
            "slm_batch_modularity", "slm_batch_get_stats", "slm_batch_run_info",
-           "slm_batch_destroy", "slm_batch_last_error"]
+           "slm_batch_destroy", "slm_batch_last_error", "slm_server_footprint", "slm_server_create",
+           "slm_server_submit", "slm_server_poll", "slm_server_wait", "slm_server_request_info",
+           "slm_server_result", "slm_server_get_stats", "slm_server_destroy",
+           "slm_server_last_error"]
 
 
 def launch_count() -> int:
@@ -61,6 +67,35 @@ class SlmError(RuntimeError):
         self.status = status
         self.name = STATUS.get(status, str(status))
         super().__init__(f"{self.name}: {msg}" if msg else self.name)
+
+
+class GraphDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
+                ("weights", C.c_void_p)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("n", C.c_int32),
+                ("n_communities", C.c_int32), ("nnz", C.c_int64), ("levels", C.c_int32),
+                ("slot", C.c_int32), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("modularity", C.c_double), ("footprint", C.c_uint64),
+                ("peak_bytes", C.c_uint64), ("edges_scanned", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("rejected", C.c_int64), ("queued", C.c_int32), ("running", C.c_int32),
+                ("max_running", C.c_int32), ("budget_bytes", C.c_uint64),
+                ("reserved_bytes", C.c_uint64), ("max_reserved_bytes", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 
 class Options(C.Structure):
@@ -106,6 +141,8 @@ def load():
             "slm_last_error": (C.c_char_p, [vp]),
             "slm_get_trace": (C.c_int, [vp, vp, i64, C.POINTER(i64)]),
             "slm_get_timing": (C.c_int, [vp, vp, vp]),
+            "slm_get_positive_profile": (C.c_int, [vp, vp, i32, C.POINTER(i32)]),
+            "slm_get_scan_timing": (C.c_int, [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]),
             "slm_launch_count": (u64, []),
             "slm_step_strengths": (C.c_int, [i32, vp, vp, vp, vp, C.POINTER(i64), vp]),
             "slm_step_assign": (C.c_int, [i32, vp, vp, vp, vp, i64, vp, vp]),
@@ -131,6 +168,18 @@ def load():
             "slm_batch_run_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i64)]),
             "slm_batch_destroy": (None, [vp]),
             "slm_batch_last_error": (C.c_char_p, [vp]),
+            "slm_server_footprint": (u64, [i32, i64]),
+            "slm_server_create": (C.c_int, [u64, i32, C.POINTER(vp)]),
+            "slm_server_submit": (C.c_int, [vp, C.POINTER(GraphDesc), C.POINTER(Options),
+                                            C.POINTER(u64)]),
+            "slm_server_poll": (C.c_int, [vp, u64, C.POINTER(i32)]),
+            "slm_server_wait": (C.c_int, [vp, u64, C.c_double]),
+            "slm_server_request_info": (C.c_int, [vp, u64, C.POINTER(RequestInfo)]),
+            "slm_server_result": (C.c_int, [vp, u64, vp, C.POINTER(i32), C.POINTER(C.c_double),
+                                            i32]),
+            "slm_server_get_stats": (C.c_int, [vp, C.POINTER(ServerStats)]),
+            "slm_server_destroy": (None, [vp]),
+            "slm_server_last_error": (C.c_char_p, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -283,6 +332,22 @@ class Graph:
                                      C.c_void_p(cnt.ctypes.data)), self._h)
         return {PHASES[k]: (float(ms[k]), int(cnt[k])) for k in range(8)}
 
+    def scan_timing(self, level: int):
+        """(milliseconds, scans) of one level's scans in the last run made with FLAG_TIMING."""
+        ms = C.c_double()
+        cnt = C.c_int64()
+        _check(load().slm_get_scan_timing(self._h, level, C.byref(ms), C.byref(cnt)), self._h)
+        return ms.value, cnt.value
+
+    def positive_profile(self):
+        """{phase: milliseconds} of the POSITIVE rounds of the last run made with
+        FLAG_TIMING, summed over all rounds."""
+        ns = np.zeros(len(POSITIVE_PHASES), dtype=np.int64)
+        ln = C.c_int32()
+        _check(load().slm_get_positive_profile(self._h, C.c_void_p(ns.ctypes.data), ns.shape[0],
+                                               C.byref(ln)), self._h)
+        return {POSITIVE_PHASES[k]: float(ns[k]) / 1e6 for k in range(min(ln.value, ns.shape[0]))}
+
     def trace(self) -> np.ndarray:
         lib = load()
         ln = C.c_int64()
@@ -394,6 +459,85 @@ class Batch:
         sw = C.c_int64()
         self._check(load().slm_batch_run_info(self._h, C.byref(lv), C.byref(sw)))
         return lv.value, sw.value
+
+
+def footprint(n: int, nnz: int) -> int:
+    """Device bytes the request server reserves for a graph of n nodes and nnz entries."""
+    return int(load().slm_server_footprint(int(n), int(nnz)))
+
+
+class Server:
+    """Request server (include/slm_server.h): slots with their own streams,
+    first-come first-served admission against an HBM budget."""
+
+    def __init__(self, budget_bytes: int, slots: int = 8):
+        lib = load()
+        self._h = C.c_void_p()
+        rc = lib.slm_server_create(int(budget_bytes), int(slots), C.byref(self._h))
+        if rc != 0:
+            msg = lib.slm_server_last_error(None)
+            raise SlmError(rc, msg.decode() if msg else "")
+
+    def _check(self, rc):
+        if rc != 0:
+            msg = load().slm_server_last_error(self._h)
+            raise SlmError(rc, msg.decode() if msg else "")
+
+    def submit(self, row_ptr, col, w=None, *, seed: int = 1, accept_p32: int = P_HALF,
+               max_sweeps: int = 1000, max_levels: int = 64, flags: int = 0) -> int:
+        """Queue one graph (host arrays, copied during the call); returns its ticket."""
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        ww = None if w is None else np.ascontiguousarray(w, dtype=np.int32)
+        d = GraphDesc(rp.shape[0] - 1, rp.ctypes.data, cl.ctypes.data if cl.size else None,
+                      ww.ctypes.data if ww is not None and ww.size else None)
+        o = Options(seed, accept_p32, max_sweeps, max_levels, flags)
+        t = C.c_uint64()
+        self._check(load().slm_server_submit(self._h, C.byref(d), C.byref(o), C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        v = C.c_int32()
+        self._check(load().slm_server_poll(self._h, ticket, C.byref(v)))
+        return v.value
+
+    def wait(self, ticket: int, timeout: float = -1.0) -> bool:
+        rc = load().slm_server_wait(self._h, ticket, float(timeout))
+        if rc == 8:
+            return False
+        self._check(rc)
+        return True
+
+    def info(self, ticket: int) -> RequestInfo:
+        r = RequestInfo()
+        self._check(load().slm_server_request_info(self._h, ticket, C.byref(r)))
+        return r
+
+    def result(self, ticket: int, release: bool = True):
+        """(labels, K, Q) of a finished request; raises SlmError if it failed."""
+        n = self.info(ticket).n
+        out = np.zeros(max(n, 1), dtype=np.int32)
+        K = C.c_int32()
+        q = C.c_double()
+        self._check(load().slm_server_result(self._h, ticket, C.c_void_p(out.ctypes.data),
+                                             C.byref(K), C.byref(q), 1 if release else 0))
+        return out[:n], K.value, q.value
+
+    def stats(self) -> ServerStats:
+        s = ServerStats()
+        self._check(load().slm_server_get_stats(self._h, C.byref(s)))
+        return s
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().slm_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------

@@ -3,6 +3,7 @@
 // compaction of community names, partition composition (Algorithm 1,
 // C = C_t C) and the exact modularity numerator (Section 2.4, Q_w).
 #include <atomic>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 
@@ -27,18 +28,65 @@ void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
     fail(SLM_ERR_CUDA, buf);
 }
 
+static thread_local MemAcct *t_acct = nullptr;
+static std::mutex g_acct_mu;
+
+void MemAcct::add(long long b) {
+    std::lock_guard<std::mutex> lk(g_acct_mu);
+    cur += b;
+    if (cur > peak) peak = cur;
+}
+
+MemAcct *set_thread_acct(MemAcct *a) {
+    MemAcct *old = t_acct;
+    t_acct = a;
+    return old;
+}
+
 void DevBuf::alloc(size_t bytes, cudaStream_t s) {
     release();
     s_ = s;
     if (bytes == 0) bytes = 16;
     SLM_CUDA(cudaMallocAsync(&p_, bytes, s));
     bytes_ = bytes;
+    acct_ = t_acct;
+    if (acct_) acct_->add((long long)bytes_);
 }
 
 void DevBuf::release() {
     if (p_) cudaFreeAsync(p_, s_);
+    if (p_ && acct_) acct_->add(-(long long)bytes_);
     p_ = nullptr;
     bytes_ = 0;
+    acct_ = nullptr;
+}
+
+// One event per device marks the end of the last cooperative launch; a mutex
+// keeps the wait/launch/record sequence of different threads apart.
+static std::mutex g_coop_mu;
+static cudaEvent_t g_coop_ev[64] = {};
+
+void coop_before(cudaStream_t st) {
+    g_coop_mu.lock();
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && dev >= 0 && dev < 64 && g_coop_ev[dev])
+        e = cudaStreamWaitEvent(st, g_coop_ev[dev], 0);
+    if (e != cudaSuccess) {
+        g_coop_mu.unlock();
+        check_cuda(e, "cooperative launch ordering", __FILE__, __LINE__);
+    }
+}
+
+void coop_after(cudaStream_t st) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) {
+        if (!g_coop_ev[dev]) e = cudaEventCreateWithFlags(&g_coop_ev[dev], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(g_coop_ev[dev], st);
+    }
+    g_coop_mu.unlock();
+    if (e != cudaSuccess) check_cuda(e, "cooperative launch ordering", __FILE__, __LINE__);
 }
 
 HostCounters::HostCounters() { SLM_CUDA(cudaMallocHost(&h, 64 * sizeof(long long))); }

@@ -534,7 +534,14 @@ struct PosCtrl {
     int32_t next;    // members kept for the next round
     int32_t error;   // 1: round limit, 2: pool too small
     long long rounds, visits, splits;
+    long long ph[kPosPhases];  // nanoseconds per phase, summed over rounds (when profiling)
 };
+
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
 
 struct PosArgs {
     int32_t n;
@@ -552,6 +559,7 @@ struct PosArgs {
     int32_t *bs32a, *bs32b;
     long long pool_cap, cyc_cap, max_rounds;
     PosCtrl *ctrl;
+    int profile;  // stamp the phases with the global timer
 };
 
 // All rounds of POSITIVE in one cooperative launch: the phases of a round are
@@ -562,6 +570,16 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
     PosCtrl *C = A.ctrl;
     int32_t *M = A.listA, *M2 = A.listB;
     const int32_t n = A.n;
+    // phase stamps, taken by one thread right after a grid barrier
+    const bool stamp = A.profile && grid.thread_rank() == 0;
+    long long t0 = stamp ? global_ns() : 0;
+    auto mark_phase = [&](int k) {
+        if (stamp) {
+            const long long t = global_ns();
+            C->ph[k] += t - t0;
+            t0 = t;
+        }
+    };
     for (;;) {
         const int cnt = C->cnt;
         if (cnt == 0) break;
@@ -574,10 +592,12 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
         grid.sync();
         k_root_init(cnt, &C->R, A.rlist, A.a, A.cdist, A.L, A.msz, A.coff, A.bestsc, A.bestkey);
         grid.sync();
+        mark_phase(0);
         {
             ScanSlots S{A.msz, A.coff, A.epref, &C->mtot, &C->ctot, &C->E, A.bs64, A.bs32a, A.bs32b};
             grid_scan(S, cnt, grid);
         }
+        mark_phase(1);
         if (C->mtot > A.pool_cap || C->ctot > A.cyc_cap) {
             if (grid.thread_rank() == 0) C->error = 2;
             break;
@@ -591,8 +611,10 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
         k_edges(cnt, M, A.epref, &C->E, A.rp, A.col, A.w, A.a, A.oncycle, A.entry, A.depth, A.root,
                 A.posr, A.L, A.cdist, A.msz, A.Mw, A.credit);
         grid.sync();
+        mark_phase(2);
         k_credit(cnt, M, A.a, A.depth, A.credit, A.subWin);
         grid.sync();
+        mark_phase(3);
         for (int pass = 0; pass < 2; pass++) {
             k_branch(cnt, M, A.oncycle, A.root, A.posr, A.sigma, A.m, A.subS, A.subWA, A.subWin,
                      A.bestsc, A.bestkey, pass);
@@ -601,18 +623,22 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
                         A.bestsc, A.bestkey, pass);
             grid.sync();
         }
+        mark_phase(4);
         k_cut_info(&C->R, A.rlist, A.bestkey, n, A.L, A.coff, A.cyc, A.TS, A.depth, A.cdist, A.subS,
                    A.sigma, A.cut, A.a, A.m.gid, A.splits_per_graph);
         grid.sync();
+        mark_phase(5);
         k_forest_new(cnt, M, A.a, A.root, A.entry, A.depth, A.cdist, A.oncycle, A.posr, A.cut, A.coff,
                      A.cyc, A.nf, A.noc);
         grid.sync();
         k_forest_write(cnt, M, A.nf, A.noc, A.root, A.entry, A.depth, A.cdist, A.oncycle, A.flag);
         grid.sync();
+        mark_phase(6);
         k_own_edges(cnt, M, A.epref, &C->E, A.rp, A.col, A.w, A.root, A.kacc);
         grid.sync();
         k_own_finish(cnt, M, A.s, A.m, A.root, A.sigma, A.kacc, A.kown, A.flag);
         grid.sync();
+        mark_phase(7);
         d_mark(cnt, M, A.root, A.flag, A.mark);
         grid.sync();
         {
@@ -628,6 +654,7 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
             C->R = 0;
         }
         grid.sync();
+        mark_phase(8);
         int32_t *tmp = M;
         M = M2;
         M2 = tmp;
@@ -777,10 +804,13 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     A.cyc_cap = (long long)(hb[1] > 0 ? hb[1] : 1);
     A.max_rounds = (long long)n;  // every round splits at least one community
     A.ctrl = ps.ctrl.as<PosCtrl>();
+    A.profile = ps.profile ? 1 : 0;
     void *kargs[] = {&A};
-    SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_positive_rounds, dim3(nblocks),
-                                         dim3(kPosThreads), kargs, 0, st));
-    SLM_LAUNCH_CHECK();
+    serialised_cooperative(st, [&] {
+        SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_positive_rounds, dim3(nblocks),
+                                             dim3(kPosThreads), kargs, 0, st));
+        SLM_LAUNCH_CHECK();
+    });
     SLM_CUDA(cudaMemcpyAsync(&hc, ps.ctrl.get(), sizeof hc, cudaMemcpyDeviceToHost, st));
     SLM_CUDA(cudaStreamSynchronize(st));
     if (hc.error == 1) fail(SLM_ERR_TIMEOUT, "POSITIVE did not settle within n rounds");
@@ -788,6 +818,8 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     const long long splits = hc.splits, rounds = hc.rounds, visits = hc.visits;
     if (rounds_out) *rounds_out = rounds;
     if (visits_out) *visits_out = visits;
+    if (ps.profile)
+        for (int k = 0; k < kPosPhases; k++) ps.prof_ns[k] += hc.ph[k];
     return splits;
 }
 

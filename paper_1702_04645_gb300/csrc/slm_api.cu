@@ -42,6 +42,9 @@ struct slm_graph {
     // per-phase device time of the last run (SLM_FLAG_TIMING)
     double phase_ms[8] = {0};
     long long phase_cnt[8] = {0};
+    long long pos_ns[slm::kPosPhases] = {0};  // POSITIVE round phases (SLM_FLAG_TIMING)
+    // scan time and scan count per level (SLM_FLAG_TIMING); the last entry is the top level
+    std::vector<std::pair<double, long long>> scan_by_level;
 };
 
 namespace {
@@ -199,6 +202,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
     }
     slm::HostCounters hc;
     for (int k = 0; k < 8; k++) { g->phase_ms[k] = 0; g->phase_cnt[k] = 0; }
+    for (int k = 0; k < slm::kPosPhases; k++) g->pos_ns[k] = 0;
     PhaseTimer tmr((opt.flags & SLM_FLAG_TIMING) != 0, st, g->phase_ms, g->phase_cnt);
     PhaseTimer *tm = tmr.on ? &tmr : nullptr;
     // current level graph
@@ -209,7 +213,14 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
     DevBuf lrp, lcol, lw, ls;  // owned aggregated graph
     const long long m = g->m;
     Work W;
+    W.ps.profile = tm != nullptr;
+    g->scan_by_level.clear();
     for (int t = 0; n > 0; t++) {
+        const double scan_ms0 = g->phase_ms[kPhScan];
+        const long long scan_cnt0 = g->phase_cnt[kPhScan];
+        auto note_scans = [&] {
+            g->scan_by_level.push_back({g->phase_ms[kPhScan] - scan_ms0, g->phase_cnt[kPhScan] - scan_cnt0});
+        };
         if (tm) tm->start();
         W.init(n, rp, st);
         if (tm) tm->stop(kPhLevel);
@@ -261,6 +272,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         DevBuf id(4 * (size_t)n, st), scratch(4 * (size_t)n, st);
         int32_t K = slm::compact_labels(n, W.f.root, id.as<int32_t>(), scratch.as<int32_t>(), st);
         stt.n_communities = K;
+        note_scans();
         if (K == n) {
             if (tm) tm->stop(kPhLevel);
             g->top = stt;
@@ -295,6 +307,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         if (t + 1 >= opt.max_levels) break;
     }
     SLM_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < slm::kPosPhases; k++) g->pos_ns[k] = W.ps.prof_ns[k];
     g->has_run = true;
 }
 
@@ -488,6 +501,29 @@ slm_status slm_get_timing(const slm_graph *g, double *ms8, int64_t *count8) {
         ms8[k] = g->phase_ms[k];
         count8[k] = g->phase_cnt[k];
     }
+    return SLM_OK;
+}
+
+slm_status slm_get_scan_timing(const slm_graph *g, int32_t level, double *ms, int64_t *count) {
+    if (!g || !ms || !count) return SLM_ERR_INVALID_ARGUMENT;
+    if (!g->has_run) return SLM_ERR_NOT_RUN;
+    const int32_t L = (int32_t)g->levels.size();
+    if (level < -1 || level >= L) return SLM_ERR_INVALID_ARGUMENT;
+    const size_t k = level == -1 ? (size_t)L : (size_t)level;
+    if (k >= g->scan_by_level.size()) {
+        *ms = 0;
+        *count = 0;
+        return SLM_OK;
+    }
+    *ms = g->scan_by_level[k].first;
+    *count = g->scan_by_level[k].second;
+    return SLM_OK;
+}
+
+slm_status slm_get_positive_profile(const slm_graph *g, int64_t *ns, int32_t cap, int32_t *len) {
+    if (!g || !len || cap < 0 || (cap > 0 && !ns)) return SLM_ERR_INVALID_ARGUMENT;
+    *len = slm::kPosPhases;
+    for (int k = 0; k < cap && k < slm::kPosPhases; k++) ns[k] = g->pos_ns[k];
     return SLM_OK;
 }
 

@@ -79,6 +79,15 @@ inline int grid_for(long long n, int block, int max_blocks = 152 * 32) {
 // ---------------------------------------------------------------------------
 // Stream-ordered device buffers (cudaMallocAsync / cudaFreeAsync).
 // ---------------------------------------------------------------------------
+// Byte count of the device buffers allocated while an accountant is current
+// on the allocating thread (the request server measures each run with one).
+struct MemAcct {
+    long long cur = 0, peak = 0;  // updated under the accountant's own lock
+    void add(long long b);
+};
+// the accountant of this thread (nullptr: none); returns the previous one
+MemAcct *set_thread_acct(MemAcct *a);
+
 class DevBuf {
   public:
     DevBuf() = default;
@@ -106,11 +115,32 @@ class DevBuf {
         std::swap(p_, o.p_);
         std::swap(bytes_, o.bytes_);
         std::swap(s_, o.s_);
+        std::swap(acct_, o.acct_);
     }
     void *p_ = nullptr;
     size_t bytes_ = 0;
     cudaStream_t s_ = nullptr;
+    MemAcct *acct_ = nullptr;
 };
+
+// Cooperative launches (kernels whose blocks wait for one another at grid
+// barriers) are ordered one after the other on the device, whatever stream
+// they come from: two of them resident at once could each hold part of the
+// GPU while waiting for the rest.  serialised_cooperative() makes `st` wait
+// for the end of the previous cooperative launch of this device, runs
+// `enqueue` (which launches on `st`) and records its end.
+void coop_before(cudaStream_t st);
+void coop_after(cudaStream_t st);
+template <class F> void serialised_cooperative(cudaStream_t st, F &&enqueue) {
+    coop_before(st);
+    try {
+        enqueue();
+    } catch (...) {
+        coop_after(st);
+        throw;
+    }
+    coop_after(st);
+}
 
 // Small pinned host buffer for the counters read back each sweep.
 struct HostCounters {
@@ -259,9 +289,16 @@ void accept_moves(int32_t n, const long long *bg, RngParam rng, unsigned long lo
 void apply_moves(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt,
                  const int32_t *tgt, int32_t *a, cudaStream_t st);
 
+// Phases of a POSITIVE round, for the optional profile: 0 round set-up,
+// 1 offsets (prefix sums), 2 ancestor walks and edge credits, 3 subtree
+// credits, 4 best cut, 5 cut application, 6 new components, 7 local gains,
+// 8 next member list.
+constexpr int kPosPhases = 9;
 struct PositiveScratch {
     DevBuf flag, kown, listA, listB, rlist, posr, L, coff, subS, subWA, subWin, credit, TS, msz,
         bestsc, bestkey, pool, cyc, cnt, mark, tot, hdr, epref, kacc, cut, nf, noc, bs, ctrl;
+    bool profile = false;              // stamp the phases of every round
+    long long prof_ns[kPosPhases] = {};  // summed nanoseconds per phase
 };
 // Algorithm POSITIVE until no node has a negative local gain.  a and the
 // forest f are updated in place (only the members of split communities are

@@ -1,0 +1,364 @@
+// slm_server.cu -- request server around slm_run (slm_server.h).
+//
+// Slots are host threads, each with its own non-blocking CUDA stream.  A
+// slot takes the oldest queued request once its footprint fits in what is
+// left of the HBM budget, runs it to completion on its stream (create, run,
+// final partition and modularity copied to host memory, destroy) and gives
+// the footprint back.  The device work of the slots overlaps: while one slot
+// waits for the few counters its host driver reads each sweep, the others
+// keep the GPU busy.  The device memory each run really holds is measured by
+// an accountant that counts the library's buffers allocated on that thread.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "slm_internal.cuh"
+#include "slm_server.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    int32_t n = 0;
+    long long nnz = 0;
+    std::vector<int32_t> rp, col, w;  // host copies; w empty = unit weights
+    slm_options opt{};
+    uint64_t footprint = 0;
+    int32_t state = SLM_REQ_QUEUED;
+    slm_status status = SLM_OK;
+    std::string err;
+    int32_t slot = -1;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    std::vector<int32_t> labels;
+    int32_t K = 0, levels = 0;
+    double q = 0;
+    long long edges = 0;
+    uint64_t peak = 0;
+};
+
+}  // namespace
+
+struct slm_server {
+    int dev = 0;
+    uint64_t budget = 0;
+    int32_t nslots = 0;
+    Clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> queue;
+    std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+    uint64_t next_ticket = 1;
+    uint64_t reserved = 0, max_reserved = 0;
+    int32_t running = 0, max_running = 0;
+    long long submitted = 0, completed = 0, failed = 0, rejected = 0;
+    bool stop = false;
+    std::vector<std::thread> workers;
+    std::string err;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+thread_local std::string g_server_create_error;
+
+// One request, start to end, on the slot's stream.  Returns the status of
+// the first call that failed.
+slm_status run_request(Request &r, cudaStream_t st) {
+    slm_graph *g = nullptr;
+    slm_status s = slm_create_graph(r.n, r.rp.data(), r.col.data(), r.w.empty() ? nullptr : r.w.data(),
+                                    SLM_HOST, st, &g);
+    if (s != SLM_OK) {
+        r.err = slm_last_error(nullptr);
+        return s;
+    }
+    auto done = [&](slm_status e) {
+        if (e != SLM_OK) r.err = slm_last_error(g);
+        slm_destroy_graph(g);
+        return e;
+    };
+    if ((s = slm_run(g, &r.opt, st)) != SLM_OK) return done(s);
+    r.labels.assign((size_t)r.n, 0);
+    if ((s = slm_get_partition(g, -1, r.labels.data(), SLM_HOST, &r.K)) != SLM_OK) return done(s);
+    if ((s = slm_modularity(g, -1, &r.q)) != SLM_OK) return done(s);
+    if ((s = slm_num_levels(g, &r.levels)) != SLM_OK) return done(s);
+    r.edges = 0;
+    for (int32_t l = -1; l < r.levels; l++) {
+        slm_level_stats ls{};
+        if ((s = slm_get_stats(g, l, &ls)) != SLM_OK) return done(s);
+        r.edges += ls.edges_scanned;
+    }
+    return done(SLM_OK);
+}
+
+void worker(slm_server *sv, int32_t slot) {
+    cudaStream_t st = nullptr;
+    bool ok = cudaSetDevice(sv->dev) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    for (;;) {
+        sv->cv_work.wait(lk, [&] {
+            return sv->stop ||
+                   (!sv->queue.empty() && sv->queue.front()->footprint <= sv->budget - sv->reserved);
+        });
+        if (sv->stop) break;
+        Request *r = sv->queue.front();
+        sv->queue.pop_front();
+        sv->reserved += r->footprint;
+        sv->max_reserved = std::max(sv->max_reserved, sv->reserved);
+        sv->running++;
+        sv->max_running = std::max(sv->max_running, sv->running);
+        r->state = SLM_REQ_RUNNING;
+        r->slot = slot;
+        r->t_admit = sv->now();
+        lk.unlock();
+
+        slm_status s = SLM_ERR_CUDA;
+        slm::MemAcct acct;
+        if (ok) {
+            slm::MemAcct *prev = slm::set_thread_acct(&acct);
+            s = run_request(*r, st);
+            slm::set_thread_acct(prev);
+        } else {
+            r->err = "slot could not select the device or create its stream";
+        }
+        // the inputs are no longer needed once the run has ended
+        std::vector<int32_t>().swap(r->rp);
+        std::vector<int32_t>().swap(r->col);
+        std::vector<int32_t>().swap(r->w);
+
+        lk.lock();
+        r->peak = (uint64_t)acct.peak;
+        r->status = s;
+        r->state = s == SLM_OK ? SLM_REQ_DONE : SLM_REQ_FAILED;
+        r->t_done = sv->now();
+        sv->reserved -= r->footprint;
+        sv->running--;
+        if (s == SLM_OK) sv->completed++;
+        else sv->failed++;
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    }
+    lk.unlock();
+    if (st) cudaStreamDestroy(st);
+}
+
+Request *find(slm_server *sv, uint64_t ticket) {
+    auto it = sv->reqs.find(ticket);
+    return it == sv->reqs.end() ? nullptr : it->second.get();
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t slm_server_footprint(int32_t n, int64_t nnz) {
+    // input CSR and the aggregated level graph (8 B per entry each), the
+    // sort of aggregation (keys, values and their double buffers: 24 B per
+    // entry), hub tables (at most 16 B per entry); per node the level
+    // workspace, POSITIVE's scratch and the composed labels of the levels,
+    // bounded by 512 B; plus 64 MiB for cycle pools and allocation rounding
+    const uint64_t N = n > 0 ? (uint64_t)n : 0, E = nnz > 0 ? (uint64_t)nnz : 0;
+    return 56 * E + 512 * N + (64ull << 20);
+}
+
+const char *slm_server_last_error(const slm_server *sv) {
+    return sv ? sv->err.c_str() : g_server_create_error.c_str();
+}
+
+slm_status slm_server_create(uint64_t hbm_budget_bytes, int32_t max_slots, slm_server **out) {
+    if (!out) return SLM_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > 64 || hbm_budget_bytes == 0) {
+        g_server_create_error = "max_slots must be in [1, 64] and the budget positive";
+        return SLM_ERR_INVALID_ARGUMENT;
+    }
+    auto sv = std::make_unique<slm_server>();
+    cudaError_t e = cudaGetDevice(&sv->dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_server_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        return SLM_ERR_CUDA;
+    }
+    sv->budget = hbm_budget_bytes;
+    sv->nslots = max_slots;
+    sv->t0 = Clock::now();
+    try {
+        for (int32_t k = 0; k < max_slots; k++) sv->workers.emplace_back(worker, sv.get(), k);
+    } catch (const std::exception &ex) {
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->stop = true;
+        }
+        sv->cv_work.notify_all();
+        for (auto &t : sv->workers) t.join();
+        g_server_create_error = std::string("could not start the slots: ") + ex.what();
+        return SLM_ERR_CUDA;
+    }
+    *out = sv.release();
+    return SLM_OK;
+}
+
+slm_status slm_server_submit(slm_server *sv, const slm_graph_desc *gd, const slm_options *opt,
+                             uint64_t *ticket) {
+    if (!sv || !gd || !ticket) return SLM_ERR_INVALID_ARGUMENT;
+    *ticket = 0;
+    const int32_t n = gd->n;
+    if (n < 0 || !gd->row_ptr) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->err = "bad n or row_ptr";
+        return SLM_ERR_INVALID_ARGUMENT;
+    }
+    // the shape of the CSR is checked here; everything else at admission
+    const long long nnz = gd->row_ptr[n];
+    if (gd->row_ptr[0] != 0 || nnz < 0 || nnz >= (1LL << 31) || (nnz > 0 && !gd->col_idx)) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->err = "row_ptr must start at 0 and end at the entry count; col_idx must be given";
+        return SLM_ERR_INVALID_ARGUMENT;
+    }
+    auto r = std::make_unique<Request>();
+    r->n = n;
+    r->nnz = nnz;
+    r->footprint = slm_server_footprint(n, nnz);
+    if (opt) r->opt = *opt;
+    else slm_default_options(&r->opt);
+    if (r->footprint > sv->budget) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->rejected++;
+        sv->err = "the request's footprint exceeds the whole budget";
+        return SLM_ERR_BUDGET;
+    }
+    r->rp.assign(gd->row_ptr, gd->row_ptr + (size_t)n + 1);
+    if (nnz > 0) {
+        r->col.assign(gd->col_idx, gd->col_idx + nnz);
+        if (gd->weights) r->w.assign(gd->weights, gd->weights + nnz);
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) {
+        sv->err = "the server is shutting down";
+        return SLM_ERR_INVALID_ARGUMENT;
+    }
+    r->ticket = sv->next_ticket++;
+    r->t_submit = sv->now();
+    *ticket = r->ticket;
+    sv->queue.push_back(r.get());
+    sv->reqs.emplace(r->ticket, std::move(r));
+    sv->submitted++;
+    sv->cv_work.notify_all();
+    return SLM_OK;
+}
+
+slm_status slm_server_poll(slm_server *sv, uint64_t ticket, int32_t *state) {
+    if (!sv || !state) return SLM_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    Request *r = find(sv, ticket);
+    if (!r) return SLM_ERR_INVALID_ARGUMENT;
+    *state = r->state;
+    return SLM_OK;
+}
+
+slm_status slm_server_wait(slm_server *sv, uint64_t ticket, double timeout_s) {
+    if (!sv) return SLM_ERR_INVALID_ARGUMENT;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    Request *r = find(sv, ticket);
+    if (!r) return SLM_ERR_INVALID_ARGUMENT;
+    auto ended = [&] { return r->state == SLM_REQ_DONE || r->state == SLM_REQ_FAILED; };
+    if (timeout_s < 0) {
+        sv->cv_done.wait(lk, ended);
+        return SLM_OK;
+    }
+    const auto limit = std::chrono::duration<double>(timeout_s);
+    return sv->cv_done.wait_for(lk, limit, ended) ? SLM_OK : SLM_ERR_TIMEOUT;
+}
+
+slm_status slm_server_request_info(slm_server *sv, uint64_t ticket, slm_request_info *info) {
+    if (!sv || !info) return SLM_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    Request *r = find(sv, ticket);
+    if (!r) return SLM_ERR_INVALID_ARGUMENT;
+    slm_request_info o{};
+    o.state = r->state;
+    o.status = r->status;
+    o.n = r->n;
+    o.n_communities = r->K;
+    o.nnz = r->nnz;
+    o.levels = r->levels;
+    o.slot = r->slot;
+    o.t_submit = r->t_submit;
+    o.t_admit = r->t_admit;
+    o.t_done = r->t_done;
+    o.modularity = r->q;
+    o.footprint = r->footprint;
+    o.peak_bytes = r->peak;
+    o.edges_scanned = r->edges;
+    *info = o;
+    return SLM_OK;
+}
+
+slm_status slm_server_result(slm_server *sv, uint64_t ticket, int32_t *labels,
+                             int32_t *n_communities, double *q, int32_t release) {
+    if (!sv) return SLM_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    Request *r = find(sv, ticket);
+    if (!r) return SLM_ERR_INVALID_ARGUMENT;
+    if (r->state == SLM_REQ_QUEUED || r->state == SLM_REQ_RUNNING) return SLM_ERR_NOT_RUN;
+    const slm_status s = r->status;
+    if (s == SLM_OK) {
+        if (labels && r->n > 0) std::memcpy(labels, r->labels.data(), sizeof(int32_t) * (size_t)r->n);
+        if (n_communities) *n_communities = r->K;
+        if (q) *q = r->q;
+    } else {
+        sv->err = r->err;
+    }
+    if (release) sv->reqs.erase(ticket);
+    return s;
+}
+
+slm_status slm_server_get_stats(slm_server *sv, slm_server_stats *st) {
+    if (!sv || !st) return SLM_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    slm_server_stats o{};
+    o.submitted = sv->submitted;
+    o.completed = sv->completed;
+    o.failed = sv->failed;
+    o.rejected = sv->rejected;
+    o.queued = (int32_t)sv->queue.size();
+    o.running = sv->running;
+    o.max_running = sv->max_running;
+    o.budget_bytes = sv->budget;
+    o.reserved_bytes = sv->reserved;
+    o.max_reserved_bytes = sv->max_reserved;
+    *st = o;
+    return SLM_OK;
+}
+
+void slm_server_destroy(slm_server *sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        for (Request *r : sv->queue) {
+            r->state = SLM_REQ_FAILED;
+            r->status = SLM_ERR_NOT_RUN;
+            r->err = "the server was destroyed before the request was admitted";
+            sv->failed++;
+        }
+        sv->queue.clear();
+    }
+    sv->cv_work.notify_all();
+    sv->cv_done.notify_all();
+    for (auto &t : sv->workers) t.join();
+    delete sv;
+}
+
+}  // extern "C"

@@ -50,6 +50,21 @@ def test_host_only_entry_points(lib):
     assert lib.slm_num_levels(None, None) == 1
 
 
+def test_server_host_entry_points(lib):
+    # the admission estimate is a pure host function, growing with n and nnz
+    f = [slm.footprint(n, e) for n, e in ((0, 0), (1000, 16000), (2000, 16000), (2000, 32000))]
+    assert f[0] == 64 << 20
+    assert f[0] < f[1] < f[2] < f[3]
+    # arguments are checked before any device is touched
+    h = slm.C.c_void_p()
+    assert lib.slm_server_create(1 << 30, 0, slm.C.byref(h)) == 1
+    assert lib.slm_server_create(0, 4, slm.C.byref(h)) == 1
+    assert not h.value
+    assert lib.slm_server_submit(None, None, None, None) == 1
+    assert lib.slm_server_poll(None, 1, None) == 1
+    lib.slm_server_destroy(None)
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(slm, "LIB", str(tmp_path / "absent.so"))
     monkeypatch.setattr(slm, "_lib", None)
