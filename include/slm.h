@@ -19,8 +19,10 @@
  *   - `where` says whether a pointer is host (SLM_HOST) or device (SLM_DEVICE)
  *     memory of the current device;
  *   - inputs are copied; the caller keeps ownership of every pointer it passes;
- *   - the library allocates its device memory with cudaMallocAsync on the
- *     given stream and frees it in slm_destroy_graph.
+ *   - the library allocates its device memory in stream order on the given
+ *     stream, from a memory pool of its own per device, and frees it in
+ *     slm_destroy_graph; freed memory stays cached in that pool for the next
+ *     allocation until slm_release_cached_memory returns it to the device.
  */
 #ifndef SLM_H
 #define SLM_H
@@ -122,7 +124,11 @@ slm_status slm_get_stats(const slm_graph *g, int32_t level, slm_level_stats *st)
  * nodes; labels in `where` memory.  Synchronous. */
 slm_status slm_modularity_of(const slm_graph *g, const int32_t *labels, int where, double *q);
 
+/* Free the graph's device memory (stream-ordered; no device-wide wait). */
 void slm_destroy_graph(slm_graph *g);
+/* Return the device memory cached in the library's pools (every device) to
+ * the driver.  Memory still held by live handles is not affected. */
+void slm_release_cached_memory(void);
 const char *slm_status_string(slm_status s);
 /* Message of the last error on this handle (or of the last failed create when g is NULL). */
 const char *slm_last_error(const slm_graph *g);

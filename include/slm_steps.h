@@ -163,6 +163,19 @@ slm_status slm_get_scan_timing(const slm_graph *g, int32_t level, double *ms, in
  * values into `ns` (host memory) and sets *len to the number of phases. */
 slm_status slm_get_positive_profile(const slm_graph *g, int64_t *ns, int32_t cap, int32_t *len);
 
+/* Self-check of the failure path of the cooperative kernels (POSITIVE runs
+ * all its rounds in one launch whose blocks meet at grid barriers; each
+ * barrier wait has a time limit, 4 s in POSITIVE, after which the launch is
+ * abandoned and slm_run returns SLM_ERR_TIMEOUT).  Launches `blocks` blocks
+ * that pass three such barriers with a limit of limit_s seconds (0 < limit_s
+ * <= 60); block `absent_block` (-1: none) leaves before the first barrier,
+ * so that the other blocks' waits run out.  Returns SLM_OK when every block
+ * passed every barrier, SLM_ERR_TIMEOUT when a wait ran out (the device and
+ * the context stay usable), SLM_ERR_INVALID_ARGUMENT for a block count that
+ * cannot be resident at once.  Synchronous. */
+slm_status slm_check_grid_barrier(int32_t blocks, int32_t absent_block, double limit_s,
+                                  void *stream);
+
 /* Number of kernels this library has launched in the process so far. */
 uint64_t slm_launch_count(void);
 

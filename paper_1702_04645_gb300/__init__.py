@@ -46,7 +46,7 @@ EXPORTS = ["slm_default_options", "slm_create_graph", "slm_run", "slm_num_levels
            "slm_destroy_graph", "slm_status_string", "slm_last_error", "slm_step_strengths",
            "slm_step_assign", "slm_step_components", "slm_step_scan", "slm_step_branch_gain",
            "slm_step_maximal", "slm_step_positive", "slm_step_compact", "slm_step_aggregate",
-           "slm_step_modularity", "slm_get_trace", "slm_get_timing", "slm_get_positive_profile", "slm_get_scan_timing",
+           "slm_step_modularity", "slm_get_trace", "slm_get_timing", "slm_get_positive_profile", "slm_get_scan_timing", "slm_release_cached_memory", "slm_check_grid_barrier",
            "slm_launch_count",
            "slm_step_modularity_noalloc", "slm_batch_create", "slm_batch_run",
            "slm_batch_num_graphs", "slm_batch_num_levels", "slm_batch_get_partition",
@@ -144,6 +144,8 @@ def load():
             "slm_get_positive_profile": (C.c_int, [vp, vp, i32, C.POINTER(i32)]),
             "slm_get_scan_timing": (C.c_int, [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]),
             "slm_launch_count": (u64, []),
+            "slm_release_cached_memory": (None, []),
+            "slm_check_grid_barrier": (C.c_int, [i32, i32, C.c_double, vp]),
             "slm_step_strengths": (C.c_int, [i32, vp, vp, vp, vp, C.POINTER(i64), vp]),
             "slm_step_assign": (C.c_int, [i32, vp, vp, vp, vp, i64, vp, vp]),
             "slm_step_components": (C.c_int, [i32, vp, vp, vp]),

@@ -43,18 +43,77 @@ MemAcct *set_thread_acct(MemAcct *a) {
     return old;
 }
 
+static thread_local bool t_blocking = false;
+static thread_local cudaEvent_t t_ev = nullptr;
+static thread_local int t_ev_dev = -1;
+
+void set_thread_blocking_sync(bool on) { t_blocking = on; }
+
+void stream_sync(cudaStream_t st) {
+    if (!t_blocking) {
+        SLM_CUDA(cudaStreamSynchronize(st));
+        return;
+    }
+    int dev = 0;
+    SLM_CUDA(cudaGetDevice(&dev));
+    if (!t_ev || t_ev_dev != dev) {
+        if (t_ev) cudaEventDestroy(t_ev);
+        t_ev = nullptr;
+        SLM_CUDA(cudaEventCreateWithFlags(&t_ev, cudaEventBlockingSync | cudaEventDisableTiming));
+        t_ev_dev = dev;
+    }
+    SLM_CUDA(cudaEventRecord(t_ev, st));
+    SLM_CUDA(cudaEventSynchronize(t_ev));
+}
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+cudaMemPool_t lib_pool() {
+    int dev = 0;
+    SLM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(SLM_ERR_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        SLM_CUDA(cudaMemPoolCreate(&p, &props));
+        unsigned long long keep = ~0ull;  // keep freed blocks for reuse
+        cudaError_t e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            check_cuda(e, "cudaMemPoolSetAttribute", __FILE__, __LINE__);
+        }
+        g_pool[dev] = p;
+    }
+    return g_pool[dev];
+}
+
+void trim_pool() {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (int d = 0; d < 64; d++)
+        if (g_pool[d]) cudaMemPoolTrimTo(g_pool[d], 0);
+}
+
 void DevBuf::alloc(size_t bytes, cudaStream_t s) {
     release();
     s_ = s;
     if (bytes == 0) bytes = 16;
-    SLM_CUDA(cudaMallocAsync(&p_, bytes, s));
+    SLM_CUDA(cudaMallocFromPoolAsync(&p_, bytes, lib_pool(), s));
     bytes_ = bytes;
     acct_ = t_acct;
     if (acct_) acct_->add((long long)bytes_);
 }
 
+static thread_local bool t_release_default = false;
+ReleaseOnDefaultStream::ReleaseOnDefaultStream() : prev(t_release_default) { t_release_default = true; }
+ReleaseOnDefaultStream::~ReleaseOnDefaultStream() { t_release_default = prev; }
+
 void DevBuf::release() {
-    if (p_) cudaFreeAsync(p_, s_);
+    if (p_) cudaFreeAsync(p_, t_release_default ? cudaStream_t(0) : s_);
     if (p_ && acct_) acct_->add(-(long long)bytes_);
     p_ = nullptr;
     bytes_ = 0;
@@ -89,10 +148,24 @@ void coop_after(cudaStream_t st) {
     if (e != cudaSuccess) check_cuda(e, "cooperative launch ordering", __FILE__, __LINE__);
 }
 
-HostCounters::HostCounters() { SLM_CUDA(cudaMallocHost(&h, 64 * sizeof(long long))); }
-HostCounters::~HostCounters() {
-    if (h) cudaFreeHost(h);
+// Each thread keeps one pinned block for its counters for as long as it
+// lives: freeing pinned memory waits for the whole device, which would stall
+// every other stream at the end of each run.
+namespace {
+struct PinnedCounters {
+    long long *h = nullptr;
+    ~PinnedCounters() {
+        if (h) cudaFreeHost(h);
+    }
+};
+thread_local PinnedCounters t_counters;
+}  // namespace
+
+HostCounters::HostCounters() {
+    if (!t_counters.h) SLM_CUDA(cudaMallocHost(&t_counters.h, 64 * sizeof(long long)));
+    h = t_counters.h;
 }
+HostCounters::~HostCounters() = default;
 
 // ---------------------------------------------------------------------------
 // Exclusive prefix sums: reduce tiles, scan the tile sums (recursively), then
@@ -259,7 +332,7 @@ int validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const int32_t
     }
     int h = 0;
     SLM_CUDA(cudaMemcpyAsync(&h, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
-    SLM_CUDA(cudaStreamSynchronize(s));
+    slm::stream_sync(s);
     return h;
 }
 
@@ -278,7 +351,7 @@ int count_out_of_range(long long cnt, const int32_t *x, int32_t n, cudaStream_t 
     SLM_LAUNCH_CHECK();
     int h = 0;
     SLM_CUDA(cudaMemcpyAsync(&h, bad.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
-    SLM_CUDA(cudaStreamSynchronize(s));
+    slm::stream_sync(s);
     return h;
 }
 
@@ -315,7 +388,7 @@ long long strengths(int32_t n, const int32_t *rp, const int32_t *w, int32_t *s_o
     }
     unsigned long long h = 0;
     SLM_CUDA(cudaMemcpyAsync(&h, m.get(), sizeof h, cudaMemcpyDeviceToHost, s));
-    SLM_CUDA(cudaStreamSynchronize(s));
+    slm::stream_sync(s);
     return (long long)h;
 }
 
@@ -361,7 +434,7 @@ int32_t compact_labels(int32_t n, const int32_t *root, int32_t *id, int32_t *scr
     SLM_LAUNCH_CHECK();
     int32_t K = 0;
     SLM_CUDA(cudaMemcpyAsync(&K, tot.get(), sizeof K, cudaMemcpyDeviceToHost, s));
-    SLM_CUDA(cudaStreamSynchronize(s));
+    slm::stream_sync(s);
     return K;
 }
 
@@ -444,7 +517,7 @@ long long modularity_num(int32_t n, const int32_t *rp, const int32_t *col, const
     SLM_LAUNCH_CHECK();
     unsigned long long h[2];
     SLM_CUDA(cudaMemcpyAsync(h, out.get(), sizeof h, cudaMemcpyDeviceToHost, s));
-    SLM_CUDA(cudaStreamSynchronize(s));
+    slm::stream_sync(s);
     return (long long)h[0] - (long long)h[1];
 }
 
@@ -507,7 +580,7 @@ long long forest_check_and_weights(int32_t n, const int32_t *rp, const int32_t *
     }
     unsigned long long h = 0;
     SLM_CUDA(cudaMemcpyAsync(&h, cross.get(), 8, cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
+    slm::stream_sync(st);
     return (long long)h;
 }
 

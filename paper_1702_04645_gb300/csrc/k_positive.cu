@@ -21,11 +21,9 @@
 #include <algorithm>
 #include <climits>
 
-#include <cooperative_groups.h>
 
 #include "forest_dev.cuh"
 
-namespace cg = cooperative_groups;
 
 namespace slm {
 
@@ -77,13 +75,13 @@ __device__ __forceinline__ void d_compact(int cnt, const int32_t *list, const in
 // ---------------------------------------------------------------------------
 // one round (phases of the persistent kernel below)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void k_round_init(int cnt, const int32_t *M, const int32_t *rp, const int32_t *root,
+__device__ __forceinline__ void k_round_init(int cnt, const int32_t *M, const int32_t *ideg, const int32_t *root,
                              long long *subS, long long *subWA, long long *subWin,
                              long long *credit, long long *TS, int32_t *rlist, int32_t *rcnt,
                              int32_t *posr, int32_t *degm, long long *kacc) {
     GRID_STRIDE(k, cnt) {
         int v = M[k];
-        degm[k] = rp[v + 1] - rp[v];
+        degm[k] = ideg[v];
         kacc[k] = 0;
         subS[v] = 0;
         subWA[v] = 0;
@@ -151,9 +149,9 @@ __device__ __forceinline__ void k_cycle_order(int cnt, const int32_t *M, const u
     }
 }
 
-// member owning edge slot e of the members' concatenated rows
-__device__ __forceinline__ int owner_of(long long e, const int32_t *epref, int cnt) {
-    int lo = 0, hi = cnt - 1;
+// member owning edge slot e of the members' concatenated rows: the last k
+// in [lo, hi] with epref[k] <= e
+__device__ __forceinline__ int owner_in(long long e, const int32_t *epref, int lo, int hi) {
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if ((long long)epref[mid] <= e) lo = mid;
@@ -162,22 +160,44 @@ __device__ __forceinline__ int owner_of(long long e, const int32_t *epref, int c
     return lo;
 }
 
-// one thread per edge of a member: LCA credits inside a tree, tree-to-tree
-// weights of the cycle
+// The 32 lanes of a warp hold the consecutive slots base .. base+31: lanes 0
+// and 31 search the whole list for the owners of the first and last slot,
+// then every lane searches only between those two owners.  Every lane of
+// the warp must call this (shuffles); e is clamped to the last slot E-1.
+__device__ __forceinline__ int warp_owner(long long base, long long E, const int32_t *epref,
+                                          int cnt, long long &e) {
+    const int lane = threadIdx.x & 31;
+    const long long last = min(base + 31, E - 1);
+    e = min(base + lane, last);
+    int k = 0;
+    if (lane == 0 || lane == 31) k = owner_in(lane == 0 ? base : last, epref, 0, cnt - 1);
+    const int lo = __shfl_sync(0xffffffffu, k, 0), hi = __shfl_sync(0xffffffffu, k, 31);
+    return owner_in(e, epref, lo, hi);
+}
+
+// loop over the slots [0, E) in warp-sized runs of consecutive slots
+#define WARP_SLOTS(base, E)                                                               \
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;     \
+         base < (E); base += (long long)gridDim.x * blockDim.x)
+
+// one thread per internal edge of a member: LCA credits inside a tree,
+// tree-to-tree weights of the cycle
 __device__ __forceinline__ void k_edges(int cnt, const int32_t *M, const int32_t *epref, const int32_t *Edev,
-                        const int32_t *rp, const int32_t *col, const int32_t *w, const int32_t *a,
+                        const int32_t *istart, const int32_t *col, const int32_t *w, const int32_t *a,
                         const uint8_t *oncycle, const int32_t *entry, const int32_t *depth,
                         const int32_t *root, const int32_t *posr, const int32_t *L,
                         const int32_t *cdist, const long long *moff, long long *Mw,
                         long long *credit) {
     const long long E = *Edev;
-    GRID_STRIDE(e, E) {
-        int k = owner_of(e, epref, cnt);
+    WARP_SLOTS(base, E) {
+        long long e;
+        const int k = warp_owner(base, E, epref, cnt, e);
+        if (e != base + (threadIdx.x & 31)) continue;  // past the last slot
         const int x = M[k];
-        const int p = rp[x] + (int)(e - epref[k]);
+        const int p = istart[x] + (int)(e - epref[k]);
         const int j = col[p];
         const int r = root[x];
-        if (j == x || root[j] != r) continue;
+        if (root[j] != r) continue;  // joined by a cut of an earlier round
         const int ex = entry[x], ej = entry[j], wv = w[p];
         if (ej == ex) {
             int l = lca_walk(x, j, a, depth);
@@ -366,17 +386,75 @@ __device__ __forceinline__ void k_forest_write(int cnt, const int32_t *M, const 
     }
 }
 
-// own-community weight of every member, one thread per member edge
+// own-community weight of every member, one thread per internal edge
 __device__ __forceinline__ void k_own_edges(int cnt, const int32_t *M, const int32_t *epref, const int32_t *Edev,
-                            const int32_t *rp, const int32_t *col, const int32_t *w,
+                            const int32_t *istart, const int32_t *col, const int32_t *w,
                             const int32_t *root, long long *kacc) {
     const long long E = *Edev;
-    GRID_STRIDE(e, E) {
-        int k = owner_of(e, epref, cnt);
+    WARP_SLOTS(base, E) {
+        long long e;
+        const int k = warp_owner(base, E, epref, cnt, e);
+        if (e != base + (threadIdx.x & 31)) continue;  // past the last slot
         const int x = M[k];
-        const int p = rp[x] + (int)(e - epref[k]);
-        const int j = col[p];
-        if (j != x && root[j] == root[x]) add64(&kacc[k], w[p]);
+        const int p = istart[x] + (int)(e - epref[k]);
+        if (root[col[p]] == root[x]) add64(&kacc[k], w[p]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Internal edges of the members: POSITIVE only splits communities, so an
+// entry (x, j) with root[j] != root[x] at the start never becomes internal
+// again.  The rounds read a compacted copy of the members' internal entries
+// (j != x, same community) instead of their whole rows: hubs whose rows
+// mostly leave the community cost their internal degree only.
+// ---------------------------------------------------------------------------
+__global__ void k_int_count(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
+                            const int32_t *root, int32_t *icnt) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = warp; k < cnt; k += nw) {
+        const int x = M[k], r = root[x];
+        const int b = rp[x], e = rp[x + 1];
+        int c = 0;
+        for (int p = b + lane; p < e; p += 32) {
+            const int j = col[p];
+            c += (j != x && root[j] == r) ? 1 : 0;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) icnt[k] = c;
+    }
+}
+
+__global__ void k_int_fill(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
+                           const int32_t *w, const int32_t *root, const int32_t *icnt,
+                           const int32_t *ioff, int32_t *istart, int32_t *ideg, int32_t *icol,
+                           int32_t *iw) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = warp; k < cnt; k += nw) {
+        const int x = M[k], r = root[x];
+        const int b = rp[x], e = rp[x + 1];
+        int out = ioff[k];
+        if (lane == 0) {
+            istart[x] = out;
+            ideg[x] = icnt[k];
+        }
+        for (int p0 = b; p0 < e; p0 += 32) {
+            const int p = p0 + lane;
+            int j = -1;
+            if (p < e) j = col[p];
+            const bool in = p < e && j != x && root[j] == r;
+            const unsigned bal = __ballot_sync(0xffffffffu, in);
+            if (in) {
+                const int q = out + __popc(bal & ((1u << lane) - 1u));
+                icol[q] = j;
+                iw[q] = w[p];
+            }
+            out += __popc(bal);
+        }
     }
 }
 __device__ __forceinline__ void k_own_finish(int cnt, const int32_t *M, const int32_t *s, MParam mp,
@@ -399,6 +477,12 @@ __device__ __forceinline__ void k_own_finish(int cnt, const int32_t *M, const in
 // the same length are scanned together.  Ends after a grid barrier.
 // ---------------------------------------------------------------------------
 constexpr int kPosThreads = 256;
+// a POSITIVE call continues on a grid of kPosTailBlocks blocks, whose
+// barriers are much cheaper, once a round has at most this many members and
+// internal entries
+constexpr int kPosTailBlocks = 16;
+constexpr int kPosTailMembers = 8192;
+constexpr long long kPosTailEntries = 65536;
 
 template <class T> __device__ T block_sum(T v, T *red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -453,7 +537,63 @@ struct ScanSlots {
     int32_t *bs_b, *bs_c;
 };
 
-__device__ void grid_scan(const ScanSlots &S, int n, cg::grid_group &grid) {
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
+// Grid barrier with a time limit (the kernel is launched cooperatively, so
+// every block is resident).  Thread 0 of each block arrives on a counter;
+// the last to arrive resets it and advances the generation; the others wait
+// for the generation to change for at most `limit_ns` of global time, then
+// set the failure word.  Returns false once any block has failed: the
+// caller leaves the kernel, and every other block does the same at its next
+// barrier, which is bounded the same way, so the launch always ends.  A grid
+// of one block needs the block barrier only.
+// longest a block waits at a grid barrier before the launch is abandoned
+constexpr long long kBarrierLimitNs = 4000000000LL;
+
+struct GridBarrier {
+    unsigned count;
+    unsigned gen;
+    int failed;
+    int pad;
+};
+
+__device__ __noinline__ bool gbar(GridBarrier *b, long long limit_ns) {
+    __syncthreads();
+    if (gridDim.x > 1) {
+        if (threadIdx.x == 0) {
+            volatile unsigned *vgen = &b->gen;
+            const unsigned g = *vgen;
+            __threadfence();
+            if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+                atomicExch(&b->count, 0u);
+                __threadfence();
+                atomicAdd(&b->gen, 1u);
+            } else {
+                const long long t0 = global_ns();
+                while (*vgen == g) {
+                    if (global_ns() - t0 > limit_ns) {
+                        atomicExch(&b->failed, 1);
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+    }
+    return *((volatile int *)&b->failed) == 0;
+}
+#define GBAR_OR_RETURN(r)                        \
+    do {                                         \
+        if (!gbar(A.bar, A.barrier_ns)) return r; \
+    } while (0)
+
+__device__ bool grid_scan(const ScanSlots &S, int n, GridBarrier *bar, long long barrier_ns) {
     __shared__ long long red64[kPosThreads / 32 + 1];
     __shared__ int32_t red32[kPosThreads / 32 + 1];
     const int nb = gridDim.x;
@@ -474,7 +614,7 @@ __device__ void grid_scan(const ScanSlots &S, int n, cg::grid_group &grid) {
         S.bs_b[blockIdx.x] = sb;
         if (S.c) S.bs_c[blockIdx.x] = sc;
     }
-    grid.sync();
+    if (!gbar(bar, barrier_ns)) return false;
     if (blockIdx.x == 0) {
         long long ca = 0;
         int32_t cb = 0, cc = 0;
@@ -501,7 +641,7 @@ __device__ void grid_scan(const ScanSlots &S, int n, cg::grid_group &grid) {
             if (S.c) *S.tot_c = cc;
         }
     }
-    grid.sync();
+    if (!gbar(bar, barrier_ns)) return false;
     long long ca = S.a ? S.bs_a[blockIdx.x] : 0;
     int32_t cb = S.bs_b[blockIdx.x], cc = S.c ? S.bs_c[blockIdx.x] : 0;
     for (int k0 = lo; k0 < hi; k0 += blockDim.x) {
@@ -521,7 +661,7 @@ __device__ void grid_scan(const ScanSlots &S, int n, cg::grid_group &grid) {
         cb += tb;
         cc += tc;
     }
-    grid.sync();
+    return gbar(bar, barrier_ns);
 }
 
 // Control block shared by the host and the persistent kernel.
@@ -533,19 +673,18 @@ struct PosCtrl {
     long long mtot;  // tree-weight pool entries in use
     int32_t next;    // members kept for the next round
     int32_t error;   // 1: round limit, 2: pool too small
+    int32_t handoff; // 1: the grid stopped so that a smaller one continues
+    int32_t list_b;  // 1: the current member list is listB
+    GridBarrier bar; // zeroed by the host before every launch
     long long rounds, visits, splits;
     long long ph[kPosPhases];  // nanoseconds per phase, summed over rounds (when profiling)
 };
 
-__device__ __forceinline__ long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return (long long)t;
-}
 
 struct PosArgs {
     int32_t n;
-    const int32_t *rp, *col, *w, *s;
+    const int32_t *istart, *ideg, *icol, *iw;  // internal entries of the members
+    const int32_t *s;
     MParam m;
     int32_t *a, *root, *entry, *depth, *cdist;
     uint8_t *oncycle;
@@ -559,19 +698,23 @@ struct PosArgs {
     int32_t *bs32a, *bs32b;
     long long pool_cap, cyc_cap, max_rounds;
     PosCtrl *ctrl;
-    int profile;  // stamp the phases with the global timer
+    int profile;       // stamp the phases with the global timer
+    GridBarrier *bar;  // zeroed before each launch
+    long long barrier_ns;  // time limit of one barrier wait
+    int handoff_cnt;   // > 0: stop (handoff = 1) once a round has at most this many members
+    long long handoff_edges;  // ... and at most this many internal entries
 };
 
 // All rounds of POSITIVE in one cooperative launch: the phases of a round are
 // separated by grid barriers and the loop ends on the device when no member
 // is left.
 __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
-    cg::grid_group grid = cg::this_grid();
+    const bool rank0 = blockIdx.x == 0 && threadIdx.x == 0;
     PosCtrl *C = A.ctrl;
     int32_t *M = A.listA, *M2 = A.listB;
     const int32_t n = A.n;
     // phase stamps, taken by one thread right after a grid barrier
-    const bool stamp = A.profile && grid.thread_rank() == 0;
+    const bool stamp = A.profile && rank0;
     long long t0 = stamp ? global_ns() : 0;
     auto mark_phase = [&](int k) {
         if (stamp) {
@@ -583,37 +726,44 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
     for (;;) {
         const int cnt = C->cnt;
         if (cnt == 0) break;
-        if (C->rounds >= A.max_rounds) {
-            if (grid.thread_rank() == 0) C->error = 1;
+        if (A.handoff_cnt > 0 && cnt <= A.handoff_cnt && C->E <= A.handoff_edges) {
+            if (rank0) {
+                C->handoff = 1;
+                C->list_b = (M == A.listB) ? 1 : 0;
+            }
             break;
         }
-        k_round_init(cnt, M, A.rp, A.root, A.subS, A.subWA, A.subWin, A.credit, A.TS, A.rlist, &C->R,
+        if (C->rounds >= A.max_rounds) {
+            if (rank0) C->error = 1;
+            break;
+        }
+        k_round_init(cnt, M, A.ideg, A.root, A.subS, A.subWA, A.subWin, A.credit, A.TS, A.rlist, &C->R,
                      A.posr, A.epref, A.kacc);
-        grid.sync();
+        GBAR_OR_RETURN();
         k_root_init(cnt, &C->R, A.rlist, A.a, A.cdist, A.L, A.msz, A.coff, A.bestsc, A.bestkey);
-        grid.sync();
+        GBAR_OR_RETURN();
         mark_phase(0);
         {
             ScanSlots S{A.msz, A.coff, A.epref, &C->mtot, &C->ctot, &C->E, A.bs64, A.bs32a, A.bs32b};
-            grid_scan(S, cnt, grid);
+            if (!grid_scan(S, cnt, A.bar, A.barrier_ns)) return;
         }
         mark_phase(1);
         if (C->mtot > A.pool_cap || C->ctot > A.cyc_cap) {
-            if (grid.thread_rank() == 0) C->error = 2;
+            if (rank0) C->error = 2;
             break;
         }
         const long long mtot = C->mtot, ctot = C->ctot;
         GRID_STRIDE(k, mtot) A.Mw[k] = 0;
         GRID_STRIDE(k, ctot) A.cyc[k] = -1;
-        grid.sync();
+        GBAR_OR_RETURN();
         k_walk(cnt, M, A.a, A.depth, A.s, A.kown, A.subS, A.subWA, A.TS);
         if (ctot > 0) k_cycle_order(cnt, M, A.oncycle, A.root, A.posr, A.L, A.cdist, A.coff, A.cyc);
-        k_edges(cnt, M, A.epref, &C->E, A.rp, A.col, A.w, A.a, A.oncycle, A.entry, A.depth, A.root,
+        k_edges(cnt, M, A.epref, &C->E, A.istart, A.icol, A.iw, A.a, A.oncycle, A.entry, A.depth, A.root,
                 A.posr, A.L, A.cdist, A.msz, A.Mw, A.credit);
-        grid.sync();
+        GBAR_OR_RETURN();
         mark_phase(2);
         k_credit(cnt, M, A.a, A.depth, A.credit, A.subWin);
-        grid.sync();
+        GBAR_OR_RETURN();
         mark_phase(3);
         for (int pass = 0; pass < 2; pass++) {
             k_branch(cnt, M, A.oncycle, A.root, A.posr, A.sigma, A.m, A.subS, A.subWA, A.subWin,
@@ -621,39 +771,39 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
             if (ctot > 0)
                 k_cycle(&C->R, A.rlist, A.L, A.coff, A.cyc, A.msz, A.Mw, A.TS, A.sigma, A.m, n,
                         A.bestsc, A.bestkey, pass);
-            grid.sync();
+            GBAR_OR_RETURN();
         }
         mark_phase(4);
         k_cut_info(&C->R, A.rlist, A.bestkey, n, A.L, A.coff, A.cyc, A.TS, A.depth, A.cdist, A.subS,
                    A.sigma, A.cut, A.a, A.m.gid, A.splits_per_graph);
-        grid.sync();
+        GBAR_OR_RETURN();
         mark_phase(5);
         k_forest_new(cnt, M, A.a, A.root, A.entry, A.depth, A.cdist, A.oncycle, A.posr, A.cut, A.coff,
                      A.cyc, A.nf, A.noc);
-        grid.sync();
+        GBAR_OR_RETURN();
         k_forest_write(cnt, M, A.nf, A.noc, A.root, A.entry, A.depth, A.cdist, A.oncycle, A.flag);
-        grid.sync();
+        GBAR_OR_RETURN();
         mark_phase(6);
-        k_own_edges(cnt, M, A.epref, &C->E, A.rp, A.col, A.w, A.root, A.kacc);
-        grid.sync();
+        k_own_edges(cnt, M, A.epref, &C->E, A.istart, A.icol, A.iw, A.root, A.kacc);
+        GBAR_OR_RETURN();
         k_own_finish(cnt, M, A.s, A.m, A.root, A.sigma, A.kacc, A.kown, A.flag);
-        grid.sync();
+        GBAR_OR_RETURN();
         mark_phase(7);
         d_mark(cnt, M, A.root, A.flag, A.mark);
-        grid.sync();
+        GBAR_OR_RETURN();
         {
             ScanSlots S{nullptr, A.mark, nullptr, nullptr, &C->next, nullptr, nullptr, A.bs32a, nullptr};
-            grid_scan(S, cnt, grid);
+            if (!grid_scan(S, cnt, A.bar, A.barrier_ns)) return;
         }
         d_compact(cnt, M, A.root, A.flag, A.mark, M2);
-        if (grid.thread_rank() == 0) {
+        if (rank0) {
             C->rounds += 1;
             C->visits += cnt;
             C->splits += C->R;
             C->cnt = C->next;
             C->R = 0;
         }
-        grid.sync();
+        GBAR_OR_RETURN();
         mark_phase(8);
         int32_t *tmp = M;
         M = M2;
@@ -693,7 +843,7 @@ static int32_t compact_members(long long cnt, const int32_t *list, const int32_t
     SLM_LAUNCH_CHECK();
     int32_t h = 0;
     SLM_CUDA(cudaMemcpyAsync(&h, tot.get(), sizeof h, cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
+    slm::stream_sync(st);
     return h;
 }
 
@@ -735,34 +885,54 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     ps.nf.ensure(16 * (N + 1), st);
     ps.noc.ensure(N + 1, st);
     ps.mark.ensure(4 * (N + 1), st);
-    // pools sized once: the first round holds the longest cycles
+    // pools sized once: the first round holds the longest cycles; the internal
+    // entries of the members are counted in the same pass over the host
     ps.hdr.ensure(64, st);
     SLM_CUDA(cudaMemsetAsync(ps.hdr.get(), 0, 64, st));
     unsigned long long *bnd = ps.hdr.as<unsigned long long>();
     k_pool_bound<<<grid_for(cnt, 256), 256, 0, st>>>(cnt, M, f.root, a, f.cdist, bnd, bnd + 1);
     SLM_LAUNCH_CHECK();
-    unsigned long long hb[2] = {0, 0};
-    SLM_CUDA(cudaMemcpyAsync(hb, bnd, 16, cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
+    ps.icnt.ensure(4 * (N + 1), st);
+    ps.ioff.ensure(4 * (N + 1), st);
+    k_int_count<<<grid_for((long long)cnt * 32, 256), 256, 0, st>>>(cnt, M, rp, col, f.root,
+                                                                     ps.icnt.as<int32_t>());
+    SLM_LAUNCH_CHECK();
+    exclusive_scan_i32(ps.icnt.as<int32_t>(), ps.ioff.as<int32_t>(), cnt,
+                       reinterpret_cast<int32_t *>(bnd + 2), st);
+    unsigned long long hb[3] = {0, 0, 0};
+    SLM_CUDA(cudaMemcpyAsync(hb, bnd, 24, cudaMemcpyDeviceToHost, st));
+    slm::stream_sync(st);
+    const long long itot = (long long)(int32_t)(hb[2] & 0xffffffffu);
     ps.pool.ensure(8 * (size_t)(hb[0] > 0 ? hb[0] : 1), st);
     ps.cyc.ensure(4 * (size_t)(hb[1] > 0 ? hb[1] : 1), st);
-    // one cooperative launch runs every round
+    ps.istart.ensure(4 * (N + 1), st);
+    ps.ideg.ensure(4 * (N + 1), st);
+    ps.icol.ensure(4 * (size_t)(itot > 0 ? itot : 1), st);
+    ps.iw.ensure(4 * (size_t)(itot > 0 ? itot : 1), st);
+    k_int_fill<<<grid_for((long long)cnt * 32, 256), 256, 0, st>>>(
+        cnt, M, rp, col, w, f.root, ps.icnt.as<int32_t>(), ps.ioff.as<int32_t>(),
+        ps.istart.as<int32_t>(), ps.ideg.as<int32_t>(), ps.icol.as<int32_t>(), ps.iw.as<int32_t>());
+    SLM_LAUNCH_CHECK();
+    // the rounds run in cooperative launches: a full grid while the member
+    // lists are large, then a small grid for the tail of the rounds
     int dev = 0, sms = 0, per_sm = 0;
     SLM_CUDA(cudaGetDevice(&dev));
     SLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_positive_rounds, kPosThreads, 0));
     if (per_sm < 1) fail(SLM_ERR_CUDA, "POSITIVE kernel cannot be resident");
-    const int nblocks = sms * std::min(per_sm, 4);
-    ps.bs.ensure(8 * (size_t)nblocks * 3, st);
+    const int nblocks_full = sms * std::min(per_sm, 4);
+    ps.bs.ensure(8 * (size_t)nblocks_full * 3, st);
     ps.ctrl.ensure(sizeof(PosCtrl), st);
     PosCtrl hc{};
     hc.cnt = cnt;
+    hc.E = (int32_t)itot;  // bound on the first round's internal entries
     SLM_CUDA(cudaMemcpyAsync(ps.ctrl.get(), &hc, sizeof hc, cudaMemcpyHostToDevice, st));
     PosArgs A;
     A.n = n;
-    A.rp = rp;
-    A.col = col;
-    A.w = w;
+    A.istart = ps.istart.as<int32_t>();
+    A.ideg = ps.ideg.as<int32_t>();
+    A.icol = ps.icol.as<int32_t>();
+    A.iw = ps.iw.as<int32_t>();
     A.s = s;
     A.m = m;
     A.a = a;
@@ -798,21 +968,37 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     A.noc = ps.noc.as<uint8_t>();
     A.splits_per_graph = splits_per_graph;
     A.bs64 = ps.bs.as<long long>();
-    A.bs32a = reinterpret_cast<int32_t *>(ps.bs.as<long long>() + nblocks);
-    A.bs32b = reinterpret_cast<int32_t *>(ps.bs.as<long long>() + 2 * nblocks);
+    A.bs32a = reinterpret_cast<int32_t *>(ps.bs.as<long long>() + nblocks_full);
+    A.bs32b = reinterpret_cast<int32_t *>(ps.bs.as<long long>() + 2 * nblocks_full);
     A.pool_cap = (long long)(hb[0] > 0 ? hb[0] : 1);
     A.cyc_cap = (long long)(hb[1] > 0 ? hb[1] : 1);
     A.max_rounds = (long long)n;  // every round splits at least one community
     A.ctrl = ps.ctrl.as<PosCtrl>();
     A.profile = ps.profile ? 1 : 0;
-    void *kargs[] = {&A};
-    serialised_cooperative(st, [&] {
-        SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_positive_rounds, dim3(nblocks),
-                                             dim3(kPosThreads), kargs, 0, st));
-        SLM_LAUNCH_CHECK();
-    });
-    SLM_CUDA(cudaMemcpyAsync(&hc, ps.ctrl.get(), sizeof hc, cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
+    A.bar = &A.ctrl->bar;
+    A.barrier_ns = kBarrierLimitNs;
+    const bool small_now = cnt <= kPosTailMembers && itot <= kPosTailEntries;
+    for (int launch = 0; launch < 2; launch++) {
+        const bool tail = small_now || launch == 1;
+        A.handoff_cnt = tail ? 0 : kPosTailMembers;
+        A.handoff_edges = kPosTailEntries;
+        const int nb = tail ? std::min(kPosTailBlocks, nblocks_full) : nblocks_full;
+        void *kargs[] = {&A};
+        serialised_cooperative(st, [&] {
+            SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_positive_rounds, dim3(nb),
+                                                 dim3(kPosThreads), kargs, 0, st));
+            SLM_LAUNCH_CHECK();
+        });
+        SLM_CUDA(cudaMemcpyAsync(&hc, ps.ctrl.get(), sizeof hc, cudaMemcpyDeviceToHost, st));
+        slm::stream_sync(st);
+        if (tail || !hc.handoff || hc.error || hc.bar.failed) break;
+        // continue from the list the full grid stopped on
+        if (hc.list_b) std::swap(A.listA, A.listB);
+        hc.handoff = 0;
+        hc.bar = GridBarrier{};
+        SLM_CUDA(cudaMemcpyAsync(ps.ctrl.get(), &hc, sizeof hc, cudaMemcpyHostToDevice, st));
+    }
+    if (hc.bar.failed) fail(SLM_ERR_TIMEOUT, "a POSITIVE grid barrier waited past its time limit");
     if (hc.error == 1) fail(SLM_ERR_TIMEOUT, "POSITIVE did not settle within n rounds");
     if (hc.error == 2) fail(SLM_ERR_CUDA, "POSITIVE cycle pools smaller than their bound");
     const long long splits = hc.splits, rounds = hc.rounds, visits = hc.visits;
@@ -821,6 +1007,43 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     if (ps.profile)
         for (int k = 0; k < kPosPhases; k++) ps.prof_ns[k] += hc.ph[k];
     return splits;
+}
+
+// ---------------------------------------------------------------------------
+// Self-check of the grid barrier: `absent` (when >= 0) leaves before the first
+// barrier, so the other blocks' waits run out after limit_ns.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_barrier_check(GridBarrier *b, int absent, long long limit_ns, int *passed) {
+    if ((int)blockIdx.x == absent) return;
+    for (int k = 0; k < 3; k++)
+        if (!gbar(b, limit_ns)) return;
+    if (threadIdx.x == 0) atomicAdd(passed, 1);
+}
+}  // namespace
+
+bool barrier_check(int blocks, int absent, long long limit_ns, cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0;
+    SLM_CUDA(cudaGetDevice(&dev));
+    SLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_barrier_check, 128, 0));
+    if (blocks < 1 || blocks > sms * per_sm) fail(SLM_ERR_INVALID_ARGUMENT, "block count not resident");
+    DevBuf mem(sizeof(GridBarrier) + 16, st);
+    SLM_CUDA(cudaMemsetAsync(mem.get(), 0, sizeof(GridBarrier) + 16, st));
+    GridBarrier *b = mem.as<GridBarrier>();
+    int *passed = reinterpret_cast<int *>(b + 1);
+    void *kargs[] = {&b, &absent, &limit_ns, &passed};
+    serialised_cooperative(st, [&] {
+        SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_barrier_check, dim3(blocks), dim3(128),
+                                             kargs, 0, st));
+        SLM_LAUNCH_CHECK();
+    });
+    GridBarrier hb{};
+    int hp = 0;
+    SLM_CUDA(cudaMemcpyAsync(&hb, b, sizeof hb, cudaMemcpyDeviceToHost, st));
+    SLM_CUDA(cudaMemcpyAsync(&hp, passed, sizeof hp, cudaMemcpyDeviceToHost, st));
+    stream_sync(st);
+    return hb.failed == 0 && hp == blocks;
 }
 
 }  // namespace slm

@@ -722,7 +722,7 @@ void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
                    vals_tmp.as<int32_t>(), n, 4, s);
     int32_t h[kNumBuckets];
     SLM_CUDA(cudaMemcpyAsync(h, counts.get(), sizeof h, cudaMemcpyDeviceToHost, s));
-    SLM_CUDA(cudaStreamSynchronize(s));
+    slm::stream_sync(s);
     for (int b = 0; b < kNumBuckets; b++) off[b + 1] = off[b] + h[b];
     // hubs: table offsets and chunk list, built on the host (hubs are few)
     nhub = off[kBucketHub + 1] - off[kBucketHub];
@@ -734,7 +734,7 @@ void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
         SLM_LAUNCH_CHECK();
         std::vector<int2> hr(nhub);
         SLM_CUDA(cudaMemcpyAsync(hr.data(), rows.get(), sizeof(int2) * nhub, cudaMemcpyDeviceToHost, s));
-        SLM_CUDA(cudaStreamSynchronize(s));
+        slm::stream_sync(s);
         std::vector<long long> hoff(nhub);
         std::vector<int32_t> hlg(nhub), tcoff(nhub + 1);
         std::vector<int4> ch;
@@ -774,7 +774,7 @@ void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
         // the tables start empty and every scan leaves them empty
         SLM_CUDA(cudaMemsetAsync(tkeys.get(), 0xff, sizeof(int) * tot, s));
         SLM_CUDA(cudaMemsetAsync(tvals.get(), 0, sizeof(int) * tot, s));
-        SLM_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+        slm::stream_sync(s);  // host vectors go out of scope
     }
 }
 

@@ -174,7 +174,7 @@ int32_t aggregate_graph(int32_t n, const int32_t *rp, const int32_t *col, const 
                         const int32_t *drop_graph, long long dropped) {
     int32_t nnz_all = 0;
     SLM_CUDA(cudaMemcpyAsync(&nnz_all, rp + n, sizeof nnz_all, cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
+    slm::stream_sync(st);
     const int32_t nnz = nnz_all - (int32_t)dropped;  // entries kept after the sort
     rp_out.alloc(sizeof(int32_t) * ((size_t)K + 1), st);
     SLM_CUDA(cudaMemsetAsync(rp_out.get(), 0, sizeof(int32_t) * ((size_t)K + 1), st));
@@ -198,7 +198,7 @@ int32_t aggregate_graph(int32_t n, const int32_t *rp, const int32_t *col, const 
     exclusive_scan_i32(seg.as<int32_t>(), seg.as<int32_t>(), nnz, tot.as<int32_t>(), st);
     int32_t nnz2 = 0;
     SLM_CUDA(cudaMemcpyAsync(&nnz2, tot.get(), sizeof nnz2, cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
+    slm::stream_sync(st);
     col_out.alloc(4 * (size_t)nnz2, st);
     w_out.alloc(4 * (size_t)nnz2, st);
     SLM_CUDA(cudaMemsetAsync(w_out.get(), 0, 4 * (size_t)nnz2, st));

@@ -158,7 +158,7 @@ SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const
     if (tm) tm->stop(kPhScan);
     if (tm) tm->start();
     SLM_CUDA(cudaMemcpyAsync(hc.h, ctr, 8, cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
+    slm::stream_sync(st);
     c.cand = (long long)hc.h[0];
     if (c.cand == 0 && stop_if_no_cand) {
         if (tm) tm->stop(kPhMove);
@@ -171,7 +171,7 @@ SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const
     slm::accept_moves(n, W.bg.as<long long>(), seed, P, level, sweep, W.acclist.as<int32_t>(),
                       acc_cnt, ctr + 1, st);
     SLM_CUDA(cudaMemcpyAsync(hc.h, ctr, 24, cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
+    slm::stream_sync(st);
     c.pos = (long long)hc.h[1];
     c.acc = (long long)(int32_t)(hc.h[2] & 0xffffffff);
     if (c.pos == 0 || c.acc == 0) {
@@ -306,7 +306,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         if (tm) tm->stop(kPhLevel);
         if (t + 1 >= opt.max_levels) break;
     }
-    SLM_CUDA(cudaStreamSynchronize(st));
+    slm::stream_sync(st);
     for (int k = 0; k < slm::kPosPhases; k++) g->pos_ns[k] = W.ps.prof_ns[k];
     g->has_run = true;
 }
@@ -366,7 +366,7 @@ slm_status slm_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *co
         else {
             SLM_CUDA(cudaMemcpyAsync(rp_h.data(), row_ptr, sizeof(int32_t) * rp_h.size(),
                                      cudaMemcpyDeviceToHost, s));
-            SLM_CUDA(cudaStreamSynchronize(s));
+            slm::stream_sync(s);
         }
         long long nnz = 0;
         check_csr_host(n, rp_h.data(), &nnz);
@@ -396,7 +396,7 @@ slm_status slm_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *co
         // bounded first so that the per-node strengths fit in int32
         g->m = slm::strengths(n, g->rp.as<int32_t>(), g->w.as<int32_t>(), g->s.as<int32_t>(), s);
         if (g->m >= (1LL << 31)) slm::fail(SLM_ERR_OVERFLOW, "m_w must be below 2^31");
-        SLM_CUDA(cudaStreamSynchronize(s));
+        slm::stream_sync(s);
     });
     if (st == SLM_OK) *out = g.release();
     return st;
@@ -529,9 +529,27 @@ slm_status slm_get_positive_profile(const slm_graph *g, int64_t *ns, int32_t cap
 
 uint64_t slm_launch_count(void) { return slm::launch_count(); }
 
+void slm_release_cached_memory(void) { slm::trim_pool(); }
+
+slm_status slm_check_grid_barrier(int32_t blocks, int32_t absent_block, double limit_s,
+                                  void *stream) {
+    if (blocks < 1 || absent_block < -1 || absent_block >= blocks || !(limit_s > 0) || limit_s > 60)
+        return SLM_ERR_INVALID_ARGUMENT;
+    bool ok = false;
+    slm_status st = guarded(nullptr, [&] {
+        ok = slm::barrier_check(blocks, absent_block, (long long)(limit_s * 1e9), as_stream(stream));
+    });
+    if (st != SLM_OK) return st;
+    if (!ok) {
+        slm::set_global_error("a grid barrier wait ran out of time");
+        return SLM_ERR_TIMEOUT;
+    }
+    return SLM_OK;
+}
+
 void slm_destroy_graph(slm_graph *g) {
     if (!g) return;
-    cudaDeviceSynchronize();
+    slm::ReleaseOnDefaultStream on_default;
     delete g;
 }
 
@@ -558,7 +576,7 @@ slm_status slm_step_assign(int32_t n, const int32_t *row_ptr, const int32_t *col
         slm::Buckets bk;
         bk.build(n, row_ptr, st);
         slm::assign_nodes(n, row_ptr, col, w, s, m_w, bk, a, st);
-        SLM_CUDA(cudaStreamSynchronize(st));
+        slm::stream_sync(st);
     });
 }
 
@@ -578,7 +596,7 @@ slm_status slm_step_components(int32_t n, const int32_t *a, int32_t *root, void 
         f.jmpA = ja.as<int2>();
         f.jmpB = jb.as<int2>();
         slm::forest_analyse(n, a, f, st);
-        SLM_CUDA(cudaStreamSynchronize(st));
+        slm::stream_sync(st);
     });
 }
 
@@ -615,7 +633,7 @@ slm_status slm_step_scan(int32_t n, const int32_t *row_ptr, const int32_t *col, 
             slm::local_gain_nodes(n, s, m_w, root, W.sigma.as<int32_t>(), W.kown.as<int32_t>(),
                                   reinterpret_cast<long long *>(g_out), st);
         }
-        SLM_CUDA(cudaStreamSynchronize(st));
+        slm::stream_sync(st);
     });
 }
 
@@ -637,7 +655,7 @@ slm_status slm_step_branch_gain(int32_t n, const int32_t *row_ptr, const int32_t
         slm::branch_gains(n, row_ptr, col, w, s, m_w, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
                           best, reinterpret_cast<const long long *>(gain), W.kown.as<int32_t>(), W.bs,
                           reinterpret_cast<long long *>(bg), st);
-        SLM_CUDA(cudaStreamSynchronize(st));
+        slm::stream_sync(st);
     });
 }
 
@@ -655,7 +673,7 @@ slm_status slm_step_maximal(int32_t n, const int32_t *row_ptr, const int32_t *co
         SweepCounts c = maximal_once(n, row_ptr, col, w, s, m_w, W, seed, accept_p32, level, sweep,
                                      false, st, hc);
         if (n > 0) SLM_CUDA(cudaMemcpyAsync(a, W.a.get(), 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
-        SLM_CUDA(cudaStreamSynchronize(st));
+        slm::stream_sync(st);
         counts_host[0] = c.cand;
         counts_host[1] = c.pos;
         counts_host[2] = c.acc;
@@ -675,7 +693,7 @@ slm_status slm_step_positive(int32_t n, const int32_t *row_ptr, const int32_t *c
             SLM_CUDA(cudaMemcpyAsync(a, W.a.get(), 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
             SLM_CUDA(cudaMemcpyAsync(root, W.f.root, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
         }
-        SLM_CUDA(cudaStreamSynchronize(st));
+        slm::stream_sync(st);
     });
 }
 
@@ -704,7 +722,7 @@ slm_status slm_step_aggregate(int32_t n, const int32_t *row_ptr, const int32_t *
             SLM_CUDA(cudaMemcpyAsync(col_out, col2.get(), 4 * (size_t)nnz2, cudaMemcpyDeviceToDevice, st));
             SLM_CUDA(cudaMemcpyAsync(w_out, w2.get(), 4 * (size_t)nnz2, cudaMemcpyDeviceToDevice, st));
         }
-        SLM_CUDA(cudaStreamSynchronize(st));
+        slm::stream_sync(st);
         *nnz_out_host = nnz2;
     });
 }

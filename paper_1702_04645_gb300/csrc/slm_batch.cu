@@ -85,7 +85,7 @@ std::vector<int32_t> graph_entry_offsets(int32_t G, const int32_t *goff_d, const
     SLM_LAUNCH_CHECK();
     std::vector<int32_t> h((size_t)G + 1);
     SLM_CUDA(cudaMemcpyAsync(h.data(), e.get(), 4 * h.size(), cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
+    slm::stream_sync(st);
     return h;
 }
 
@@ -179,7 +179,7 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
             candidates_per_graph(n, gid_d.as<int32_t>(), active_d.as<int32_t>(), W.gain.as<long long>(),
                                  cand_d.as<int32_t>(), st);
             SLM_CUDA(cudaMemcpyAsync(cand.data(), cand_d.get(), 4 * (size_t)G, cudaMemcpyDeviceToHost, st));
-            SLM_CUDA(cudaStreamSynchronize(st));
+            slm::stream_sync(st);
             int still = 0;
             for (int g = 0; g < G; g++) {
                 if (!active[g]) continue;
@@ -204,7 +204,7 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
                          acc_cnt, ctr + 1, st, active_d.as<int32_t>(), pg_d.as<int32_t>());
             SLM_CUDA(cudaMemcpyAsync(pg.data(), pg_d.get(), 8 * (size_t)G, cudaMemcpyDeviceToHost, st));
             SLM_CUDA(cudaMemcpyAsync(hc.h, ctr, 24, cudaMemcpyDeviceToHost, st));
-            SLM_CUDA(cudaStreamSynchronize(st));
+            slm::stream_sync(st);
             const int32_t nacc = (int32_t)(hc.h[2] & 0xffffffff);
             still = 0;
             for (int g = 0; g < G; g++) {
@@ -244,7 +244,7 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
         SLM_CUDA(cudaMemsetAsync(Kg_d.get(), 0, 4 * (size_t)G, st));
         roots_per_graph(n, W.f.root, gid_d.as<int32_t>(), Kg_d.as<int32_t>(), st);
         SLM_CUDA(cudaMemcpyAsync(Kg.data(), Kg_d.get(), 4 * (size_t)G, cudaMemcpyDeviceToHost, st));
-        SLM_CUDA(cudaStreamSynchronize(st));
+        slm::stream_sync(st);
         bool recorded = false;
         long long dropped = 0;
         for (int g = 0; g < G; g++) {
@@ -306,7 +306,7 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
                       koff_d.as<int32_t>(), G, B->mg_d.as<long long>(), nums_d.as<long long>(), st);
     std::vector<long long> nums(G);
     SLM_CUDA(cudaMemcpyAsync(nums.data(), nums_d.get(), 8 * (size_t)G, cudaMemcpyDeviceToHost, st));
-    SLM_CUDA(cudaStreamSynchronize(st));
+    slm::stream_sync(st);
     for (int g = 0; g < G; g++) B->q[g] = modularity_from_num(nums[g], B->mg[g]);
     B->has_run = true;
 }
@@ -340,7 +340,7 @@ slm_status slm_batch_create(int32_t num_graphs, const int32_t *graph_off, const 
         if (where == SLM_HOST) std::memcpy(rp_h.data(), row_ptr, 4 * rp_h.size());
         else {
             SLM_CUDA(cudaMemcpyAsync(rp_h.data(), row_ptr, 4 * rp_h.size(), cudaMemcpyDeviceToHost, s));
-            SLM_CUDA(cudaStreamSynchronize(s));
+            slm::stream_sync(s);
         }
         if (rp_h[0] != 0) fail(SLM_ERR_INVALID_ARGUMENT, "row_ptr[0] must be 0");
         for (int32_t i = 0; i < N; i++)
@@ -378,7 +378,7 @@ slm_status slm_batch_create(int32_t num_graphs, const int32_t *graph_off, const 
         B->mg.resize(G);
         if (G > 0)
             SLM_CUDA(cudaMemcpyAsync(B->mg.data(), B->mg_d.get(), 8 * (size_t)G, cudaMemcpyDeviceToHost, s));
-        SLM_CUDA(cudaStreamSynchronize(s));
+        slm::stream_sync(s);
         for (int g = 0; g < G; g++)
             if (B->mg[g] >= (1LL << 31)) fail(SLM_ERR_OVERFLOW, "a graph's m_w is not below 2^31");
     });
@@ -465,7 +465,7 @@ slm_status slm_batch_run_info(const slm_batch *b, int32_t *batch_levels, int64_t
 
 void slm_batch_destroy(slm_batch *b) {
     if (!b) return;
-    cudaDeviceSynchronize();
+    slm::ReleaseOnDefaultStream on_default;
     delete b;
 }
 

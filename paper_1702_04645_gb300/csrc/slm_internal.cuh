@@ -79,6 +79,29 @@ inline int grid_for(long long n, int block, int max_blocks = 152 * 32) {
 // ---------------------------------------------------------------------------
 // Stream-ordered device buffers (cudaMallocAsync / cudaFreeAsync).
 // ---------------------------------------------------------------------------
+// Host wait for the work queued on a stream.  By default the calling thread
+// spins (lowest latency); a thread that set blocking waits sleeps on an event
+// instead, leaving its core to other threads (the request server's slots).
+void stream_sync(cudaStream_t st);
+void set_thread_blocking_sync(bool on);
+
+// Device memory comes from one memory pool per device owned by the library;
+// freed blocks stay in the pool for the next allocation (no unmapping at each
+// synchronisation) until trim_pool() returns them.
+cudaMemPool_t lib_pool();
+void trim_pool();
+
+// While a ReleaseOnDefaultStream is alive on a thread, device buffers
+// released by that thread are freed in order on the legacy default stream
+// rather than on the stream that allocated them (which the caller may have
+// destroyed).  Handles are destroyed this way: every entry point has
+// finished its device work before it returns, so nothing still uses them.
+struct ReleaseOnDefaultStream {
+    ReleaseOnDefaultStream();
+    ~ReleaseOnDefaultStream();
+    bool prev;
+};
+
 // Byte count of the device buffers allocated while an accountant is current
 // on the allocating thread (the request server measures each run with one).
 struct MemAcct {
@@ -142,7 +165,8 @@ template <class F> void serialised_cooperative(cudaStream_t st, F &&enqueue) {
     coop_after(st);
 }
 
-// Small pinned host buffer for the counters read back each sweep.
+// Small pinned host buffer for the counters read back each sweep (one per
+// thread, shared by the runs made on that thread one after the other).
 struct HostCounters {
     long long *h = nullptr;
     HostCounters();
@@ -297,6 +321,7 @@ constexpr int kPosPhases = 9;
 struct PositiveScratch {
     DevBuf flag, kown, listA, listB, rlist, posr, L, coff, subS, subWA, subWin, credit, TS, msz,
         bestsc, bestkey, pool, cyc, cnt, mark, tot, hdr, epref, kacc, cut, nf, noc, bs, ctrl;
+    DevBuf icnt, ioff, istart, ideg, icol, iw;  // internal entries of the members
     bool profile = false;              // stamp the phases of every round
     long long prof_ns[kPosPhases] = {};  // summed nanoseconds per phase
 };
@@ -311,6 +336,11 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
                            const Buckets &bk, PositiveScratch &ps, cudaStream_t st,
                            long long *rounds_out, long long *visits_out,
                            int32_t *splits_per_graph = nullptr);
+
+// Self-check of the time-limited grid barrier of the cooperative kernels:
+// `blocks` resident blocks pass three barriers; block `absent` (>= 0) leaves
+// first, so the others give up after limit_ns.  True when every block passed.
+bool barrier_check(int blocks, int absent, long long limit_ns, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Aggregation (k_sort.cu)

@@ -102,6 +102,9 @@ slm_status run_request(Request &r, cudaStream_t st) {
 }
 
 void worker(slm_server *sv, int32_t slot) {
+    // slots wait for the device by sleeping, so that many of them can share
+    // the host's cores
+    slm::set_thread_blocking_sync(true);
     cudaStream_t st = nullptr;
     bool ok = cudaSetDevice(sv->dev) == cudaSuccess &&
               cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
@@ -359,6 +362,7 @@ void slm_server_destroy(slm_server *sv) {
     sv->cv_done.notify_all();
     for (auto &t : sv->workers) t.join();
     delete sv;
+    slm::trim_pool();
 }
 
 }  // extern "C"
