@@ -64,6 +64,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest of every rank's value (the slowest replica sets the time)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, elapsed_ms: float) -> float:
+    """Units of all ranks (each replica does the same work) per second of the
+    slowest rank."""
+    return units_per_rank * world / (elapsed_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -353,7 +369,9 @@ def run_served(args):
     ok = all(i.state == slm.REQ_DONE for i in infos)
     edges = sum(i.edges_scanned for i in infos)
     # per-graph loop of the plain path on a sample, partitions compared
-    sample = list(range(0, len(reqs), max(1, len(reqs) // args.loop_sample)))[: args.loop_sample]
+    # the loop sample covers the pool evenly: requests 0 .. loop_sample-1 run
+    # pool graphs 0, 1, 2, ... in turn
+    sample = list(range(min(args.loop_sample, len(reqs))))
     res = {k: sv.result(tickets[k], release=False) for k in sample}
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
@@ -389,8 +407,8 @@ def run_served(args):
                 "server": stats,
                 "max_submit_lateness_ms": float(max(late) * 1e3) if late else 0.0,
                 "per_graph_loop": {"value": loop_gps, "unit": "graphs/s",
-                                   "sample": f"slm_run on {len(sample)} requests spread over the "
-                                             "stream, one after the other",
+                                   "sample": f"slm_run on the first {len(sample)} requests of the "
+                                             "stream (every pool graph), one after the other",
                                    "identical_partitions": identical},
                 "speedup_vs_loop": gps / loop_gps,
                 "gpu_launches": int(launches), "clocks": clk.summary()}
@@ -514,13 +532,9 @@ def main():
         ev1.record(stream)
         barrier()
     launches = slm.launch_count() - launches0
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_per_step = elapsed_ms / args.steps
-    value = units * args.steps * world / (elapsed_ms / 1e3) / 1e9
+    value = whole_job_rate(units * args.steps, world, elapsed_ms) / 1e9
 
     # roofline of the scan (accumulate + argmax) on the input graph (level 0),
     # where it moves most of its bytes; timed with CUDA events on the run's stream

@@ -60,17 +60,27 @@ __global__ void k_compact(long long cnt, const int32_t *list, const int32_t *roo
     }
 }
 
-__device__ __forceinline__ void d_mark(int cnt, const int32_t *list, const int32_t *root,
-                                       const int32_t *flag, int32_t *mark) {
-    GRID_STRIDE(k, cnt) mark[k] = flag[root[list[k]]] ? 1 : 0;
-}
-__device__ __forceinline__ void d_compact(int cnt, const int32_t *list, const int32_t *root,
-                                          const int32_t *flag, const int32_t *pos, int32_t *out) {
-    GRID_STRIDE(k, cnt) {
-        int v = list[k];
-        if (flag[root[v]]) out[pos[k]] = v;
+// warp-aggregated append of the listed nodes whose community is flagged
+__device__ __forceinline__ void d_compact_atomic(int cnt, const int32_t *list, const int32_t *root,
+                                                 const int32_t *flag, int32_t *out, int32_t *count) {
+    const int lane = threadIdx.x & 31;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < cnt;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long k = base + lane;
+        int v = -1;
+        bool keep = false;
+        if (k < cnt) {
+            v = list[k];
+            keep = flag[root[v]] != 0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        int at = 0;
+        if (lane == 0 && bal) at = atomicAdd(count, __popc(bal));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (keep) out[at + __popc(bal & ((1u << lane) - 1u))] = v;
     }
 }
+
 
 // ---------------------------------------------------------------------------
 // one round (phases of the persistent kernel below)
@@ -230,16 +240,36 @@ __device__ __forceinline__ void k_branch(int cnt, const int32_t *M, const uint8_
                          const int32_t *posr, const int32_t *sigma, MParam mp,
                          const long long *subS, const long long *subWA, const long long *subWin,
                          long long *bestsc, unsigned long long *bestkey, int pass) {
-    GRID_STRIDE(k, cnt) {
-        int u = M[k];
-        const long long m = mp.of(u);
-        if (oncycle[u]) continue;
-        int r = root[u];
-        int q = posr[r];
-        long long sS = subS[u], sA = sigma[r];
-        long long sc = sS * (sA - sS) - m * (subWA[u] - subWin[u]);
-        if (pass == 0) atomicMax(&bestsc[q], sc);
-        else if (sc == bestsc[q]) atomicMin(&bestkey[q], split_key(0, u, 0));
+    const int lane = threadIdx.x & 31;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < cnt;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long k = base + lane;
+        int u = -1, q = -1;
+        long long sc = LLONG_MIN;
+        if (k < cnt) {
+            u = M[k];
+            if (!oncycle[u]) {
+                const int r = root[u];
+                q = posr[r];
+                const long long m = mp.of(u), sS = subS[u], sA = sigma[r];
+                sc = sS * (sA - sS) - m * (subWA[u] - subWin[u]);
+            }
+        }
+        if (pass == 0) {
+            // a warp whose branch cuts all belong to one community (the common
+            // case when one large community is split again and again) sends
+            // one atomic instead of 32
+            const int q0 = __shfl_sync(0xffffffffu, q, 0);
+            if (__all_sync(0xffffffffu, q == q0 || q < 0) && q0 >= 0) {
+#pragma unroll
+                for (int o = 16; o; o >>= 1) sc = max(sc, __shfl_xor_sync(0xffffffffu, sc, o));
+                if (lane == 0) atomicMax(&bestsc[q0], sc);
+            } else if (q >= 0) {
+                atomicMax(&bestsc[q], sc);
+            }
+        } else if (q >= 0 && sc == bestsc[q]) {
+            atomicMin(&bestkey[q], split_key(0, u, 0));
+        }
     }
 }
 
@@ -671,7 +701,7 @@ struct PosCtrl {
     int32_t E;       // member edges of the current round
     int32_t ctot;    // cycle-order pool entries in use
     long long mtot;  // tree-weight pool entries in use
-    int32_t next;    // members kept for the next round
+    int32_t nextc[2];// members kept, counted by atomics; round r uses nextc[r & 1]
     int32_t error;   // 1: round limit, 2: pool too small
     int32_t handoff; // 1: the grid stopped so that a smaller one continues
     int32_t list_b;  // 1: the current member list is listB
@@ -723,8 +753,10 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
             t0 = t;
         }
     };
+    int cnt = C->cnt;  // members of the first round
+    int parity = 0;
     for (;;) {
-        const int cnt = C->cnt;
+        if (rank0) C->cnt = cnt;
         if (cnt == 0) break;
         if (A.handoff_cnt > 0 && cnt <= A.handoff_cnt && C->E <= A.handoff_edges) {
             if (rank0) {
@@ -737,6 +769,7 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
             if (rank0) C->error = 1;
             break;
         }
+        if (rank0) C->nextc[parity] = 0;
         k_round_init(cnt, M, A.ideg, A.root, A.subS, A.subWA, A.subWin, A.credit, A.TS, A.rlist, &C->R,
                      A.posr, A.epref, A.kacc);
         GBAR_OR_RETURN();
@@ -789,25 +822,22 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
         k_own_finish(cnt, M, A.s, A.m, A.root, A.sigma, A.kacc, A.kown, A.flag);
         GBAR_OR_RETURN();
         mark_phase(7);
-        d_mark(cnt, M, A.root, A.flag, A.mark);
-        GBAR_OR_RETURN();
-        {
-            ScanSlots S{nullptr, A.mark, nullptr, nullptr, &C->next, nullptr, nullptr, A.bs32a, nullptr};
-            if (!grid_scan(S, cnt, A.bar, A.barrier_ns)) return;
-        }
-        d_compact(cnt, M, A.root, A.flag, A.mark, M2);
+        // members of the still-flagged communities form the next list (its
+        // order does not matter: every reduction of a round is order-free)
+        d_compact_atomic(cnt, M, A.root, A.flag, M2, &C->nextc[parity]);
         if (rank0) {
             C->rounds += 1;
             C->visits += cnt;
             C->splits += C->R;
-            C->cnt = C->next;
             C->R = 0;
         }
         GBAR_OR_RETURN();
+        cnt = *((volatile int32_t *)&C->nextc[parity]);
         mark_phase(8);
         int32_t *tmp = M;
         M = M2;
         M2 = tmp;
+        parity ^= 1;
     }
 }
 

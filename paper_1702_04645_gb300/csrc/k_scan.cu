@@ -27,7 +27,7 @@ namespace slm {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kHubSlice = 4096;  // hub table slots read by one block
+constexpr int kHubSlice = 2048;  // hub table slots read by one block
 constexpr int kBlockThreads = 256;
 constexpr int kWarpHashCap = 2 * kWarpHashMaxDeg;
 constexpr int kWarpHashWarps = 8;  // warps per block in the warp-hash kernel
@@ -40,6 +40,7 @@ __device__ __forceinline__ int bucket_of(int d) {
     if (d <= 32) return kBucketG32;
     if (d <= kWarpHashMaxDeg) return kBucketWarpHash;
     if (d <= kBlockSmallMaxDeg) return kBucketBlockS;
+    if (d <= kBlockMidMaxDeg) return kBucketBlockM;
     if (d <= kBlockSmemMaxDeg) return kBucketBlockL;
     return kBucketHub;
 }
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(256) k_scan_group(const int32_t *order, int32_
 // slots a node occupies are listed as they are claimed, so the decision pass
 // and the reset touch only the distinct communities, not the whole table.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWarpHashWarps * 32, 4) k_scan_warphash(const int32_t *order, int32_t cnt, const int32_t *rp,
+__global__ void __launch_bounds__(kWarpHashWarps * 32, 6) k_scan_warphash(const int32_t *order, int32_t cnt, const int32_t *rp,
                                 const int32_t *col, const int32_t *w, const int32_t *s,
                                 MParam mp, const int32_t *root, const int32_t *sigma,
                                 int32_t *best, long long *gain, int32_t *kown,
@@ -778,6 +779,18 @@ void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
     }
 }
 
+// Opt a kernel in to more than 48 KB of dynamic shared memory, once per device.
+template <class K> static void allow_smem(K kernel, size_t bytes, int which) {
+    static std::mutex mu;
+    static unsigned long long done[2] = {0, 0};  // bit d: device d set up
+    int dev = 0;
+    SLM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 64 && (done[which] >> dev) & 1ull) return;
+    SLM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (dev < 64) done[which] |= 1ull << dev;
+}
+
 static int blocks_for_groups(long long cnt, int nodes_per_warp, int threads = 256) {
     long long warps = (cnt + nodes_per_warp - 1) / nodes_per_warp;
     return grid_for(warps * 32, threads, kNumSMs * 16);
@@ -829,13 +842,17 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
     if (int c = cnt(kBucketBlockL)) {
         constexpr int CAP = 2 * kBlockSmemMaxDeg;
         const size_t smem = block_smem_bytes<CAP>();
-        static bool attr_set = false;
-        if (!attr_set) {
-            SLM_CUDA(cudaFuncSetAttribute(k_scan_block<CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr_set = true;
-        }
+        allow_smem(k_scan_block<CAP>, smem, 0);
         k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 3), kBlockThreads, smem, s0>>>(
             ord + bk.off[kBucketBlockL], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        SLM_LAUNCH_CHECK();
+    }
+    if (int c = cnt(kBucketBlockM)) {
+        constexpr int CAP = 2 * kBlockMidMaxDeg;
+        const size_t smem = block_smem_bytes<CAP>();
+        allow_smem(k_scan_block<CAP>, smem, 1);
+        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 6), kBlockThreads, smem, s0>>>(
+            ord + bk.off[kBucketBlockM], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
     }
     if (int c = cnt(kBucketWarpHash)) {

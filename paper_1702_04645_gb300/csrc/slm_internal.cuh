@@ -220,9 +220,10 @@ double modularity_from_num(long long num, long long m_w);
 // Degree buckets and the neighbourhood scans (k_scan.cu)
 // ---------------------------------------------------------------------------
 enum { kBucketEmpty = 0, kBucketG4, kBucketG8, kBucketG16, kBucketG32, kBucketWarpHash,
-       kBucketBlockS, kBucketBlockL, kBucketHub, kNumBuckets };
+       kBucketBlockS, kBucketBlockM, kBucketBlockL, kBucketHub, kNumBuckets };
 constexpr int kWarpHashMaxDeg = 256;
 constexpr int kBlockSmallMaxDeg = 1024; // block shape with a 16 KB table up to here
+constexpr int kBlockMidMaxDeg = 2048;   // block shape with a 32 KB table up to here
 constexpr int kBlockSmemMaxDeg = 4096;  // block shape with a 64 KB table up to here; above: hub
 constexpr int kHubChunk = 2048;         // edges of a hub handled by one block
 
