@@ -363,6 +363,9 @@ def run_served(args):
     infos = [sv.info(t) for t in tickets]
     stats = sv.stats().as_dict()
     lat = np.array([i.t_done - i.t_submit for i in infos])
+    svc = np.array([i.t_done - i.t_admit for i in infos])
+    wait = np.array([i.t_admit - i.t_submit for i in infos])
+    done_t = np.sort(np.array([i.t_done for i in infos]))
     t_first = min(i.t_submit for i in infos)
     t_last = max(i.t_done for i in infos)
     gps = len(infos) / (t_last - t_first)
@@ -403,6 +406,13 @@ def run_served(args):
                 "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
                                "p99": float(np.percentile(lat, 99) * 1e3),
                                "mean": float(lat.mean() * 1e3), "max": float(lat.max() * 1e3)},
+                "service_ms": {"p50": float(np.percentile(svc, 50) * 1e3),
+                               "p99": float(np.percentile(svc, 99) * 1e3)},
+                "queue_ms": {"p50": float(np.percentile(wait, 50) * 1e3),
+                             "p99": float(np.percentile(wait, 99) * 1e3)},
+                "completions_per_s_by_tenth": [
+                    round(len(c) / max(float(c[-1] - c[0]), 1e-9), 2) if len(c) > 1 else None
+                    for c in np.array_split(done_t, 10)],
                 "all_done": ok, "local_move_gteps": edges / (t_last - t_first) / 1e9,
                 "server": stats,
                 "max_submit_lateness_ms": float(max(late) * 1e3) if late else 0.0,

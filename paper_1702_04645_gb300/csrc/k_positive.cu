@@ -574,42 +574,39 @@ __device__ __forceinline__ long long global_ns() {
 }
 
 // Grid barrier with a time limit (the kernel is launched cooperatively, so
-// every block is resident).  Thread 0 of each block arrives on a counter;
-// the last to arrive resets it and advances the generation; the others wait
-// for the generation to change for at most `limit_ns` of global time, then
-// set the failure word.  Returns false once any block has failed: the
-// caller leaves the kernel, and every other block does the same at its next
-// barrier, which is bounded the same way, so the launch always ends.  A grid
-// of one block needs the block barrier only.
+// every block is resident).  One word serves every barrier of a launch:
+// block 0 adds 2^31 - (blocks - 1) and every other block adds 1, so the top
+// bit flips exactly when the last block arrives and the low bits return to
+// their value before the barrier.  Thread 0 of each block waits for the flip
+// for at most `limit_ns` of global time, then sets the failure word.  Returns
+// false once any block has failed: the caller leaves the kernel, and every
+// other block does the same at its next barrier, which is bounded the same
+// way, so the launch always ends.  A grid of one block needs the block
+// barrier only.
+struct GridBarrier {
+    unsigned word;
+    int failed;
+};
 // longest a block waits at a grid barrier before the launch is abandoned
 constexpr long long kBarrierLimitNs = 4000000000LL;
-
-struct GridBarrier {
-    unsigned count;
-    unsigned gen;
-    int failed;
-    int pad;
-};
 
 __device__ __noinline__ bool gbar(GridBarrier *b, long long limit_ns) {
     __syncthreads();
     if (gridDim.x > 1) {
         if (threadIdx.x == 0) {
-            volatile unsigned *vgen = &b->gen;
-            const unsigned g = *vgen;
+            const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
             __threadfence();
-            if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
-                atomicExch(&b->count, 0u);
-                __threadfence();
-                atomicAdd(&b->gen, 1u);
-            } else {
-                const long long t0 = global_ns();
-                while (*vgen == g) {
-                    if (global_ns() - t0 > limit_ns) {
+            const unsigned old = atomicAdd(&b->word, add);
+            volatile unsigned *vw = &b->word;
+            long long t0 = 0;
+            for (unsigned spin = 0; ((old ^ *vw) & 0x80000000u) == 0; spin++) {
+                if ((spin & 255u) == 0) {  // read the clock now and then
+                    const long long t = global_ns();
+                    if (t0 == 0) t0 = t;
+                    else if (t - t0 > limit_ns) {
                         atomicExch(&b->failed, 1);
                         break;
                     }
-                    __nanosleep(100);
                 }
             }
             __threadfence();

@@ -162,11 +162,50 @@ __global__ void __launch_bounds__(256) k_scan_group(const int32_t *order, int32_
 }
 
 // ---------------------------------------------------------------------------
+// Row prefetch shared by the warp and block shapes: the first batch of the
+// next node's row (its header, entries and their communities) is loaded
+// while the current node is decided, so the loads of consecutive nodes
+// overlap instead of waiting one after the other.
+// ---------------------------------------------------------------------------
+struct RowHead {
+    int i, start, end, ci, si;
+};
+
+template <int B>
+__device__ __forceinline__ void load_batch(const RowHead &h, int p0, int stride, const int32_t *col,
+                                           const int32_t *w, const int32_t *root, int (&cv)[B],
+                                           int (&wv)[B]) {
+#pragma unroll
+    for (int t = 0; t < B; t++) {
+        int p = p0 + t * stride;
+        bool ok = p < h.end;
+        cv[t] = ok ? col[p] : -1;
+        wv[t] = ok ? w[p] : 0;
+    }
+#pragma unroll
+    for (int t = 0; t < B; t++) cv[t] = (cv[t] >= 0 && cv[t] != h.i) ? root[cv[t]] : -1;
+}
+
+__device__ __forceinline__ RowHead load_head(const int32_t *order, long long idx, long long cnt,
+                                             const int32_t *rp, const int32_t *root,
+                                             const int32_t *s) {
+    RowHead h{-1, 0, 0, -1, 0};
+    if (idx < cnt) {
+        h.i = order[idx];
+        h.start = rp[h.i];
+        h.end = rp[h.i + 1];
+        h.ci = root[h.i];
+        h.si = s[h.i];
+    }
+    return h;
+}
+
+// ---------------------------------------------------------------------------
 // MAXIMAL scan, warp shape: one node per warp, shared-memory table.  The
 // slots a node occupies are listed as they are claimed, so the decision pass
 // and the reset touch only the distinct communities, not the whole table.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWarpHashWarps * 32, 6) k_scan_warphash(const int32_t *order, int32_t cnt, const int32_t *rp,
+__global__ void __launch_bounds__(kWarpHashWarps * 32, 5) k_scan_warphash(const int32_t *order, int32_t cnt, const int32_t *rp,
                                 const int32_t *col, const int32_t *w, const int32_t *s,
                                 MParam mp, const int32_t *root, const int32_t *sigma,
                                 int32_t *best, long long *gain, int32_t *kown,
@@ -174,6 +213,7 @@ __global__ void __launch_bounds__(kWarpHashWarps * 32, 6) k_scan_warphash(const 
     __shared__ int tab[kWarpHashWarps][2 * kWarpHashCap];
     __shared__ unsigned short used[kWarpHashWarps][kWarpHashMaxDeg];
     __shared__ int nused[kWarpHashWarps];
+    constexpr int B = kWarpHashMaxDeg / 32;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *keys = tab[wib], *vals = tab[wib] + kWarpHashCap;
     unsigned short *ul = used[wib];
@@ -183,45 +223,38 @@ __global__ void __launch_bounds__(kWarpHashWarps * 32, 6) k_scan_warphash(const 
     if (lane == 0) nused[wib] = 0;
     __syncwarp();
     unsigned cand = 0;
-    for (long long idx = warp; idx < cnt; idx += nwarps) {
-        int i = order[idx];
+    long long idx = warp;
+    RowHead h = load_head(order, idx, cnt, rp, root, s);
+    int cv[B], wv[B];
+    load_batch<B>(h, h.start + lane, 32, col, w, root, cv, wv);
+    for (; idx < cnt; idx += nwarps) {
+        const int i = h.i, ci = h.ci, si = h.si;
         const long long m = mp.of(i);
-        int start = rp[i], deg = rp[i + 1] - start;
-        int ci = root[i], si = s[i];
-        int lg = ilog2_pow2_at_least(2 * deg);
-        int cap = 1 << lg;
-        // every lane fetches its (at most 8) edges and their communities before
-        // inserting, so the loads overlap instead of waiting one by one
-        int cv[kWarpHashMaxDeg / 32], wv[kWarpHashMaxDeg / 32];
+        const int lg = ilog2_pow2_at_least(2 * (h.end - h.start));
+        const int cap = 1 << lg;
 #pragma unroll
-        for (int t = 0; t < kWarpHashMaxDeg / 32; t++) {
-            int p = start + lane + 32 * t;
-            bool ok = p < start + deg;
-            cv[t] = ok ? col[p] : -1;
-            wv[t] = ok ? w[p] : 0;
-        }
-#pragma unroll
-        for (int t = 0; t < kWarpHashMaxDeg / 32; t++) cv[t] = (cv[t] >= 0 && cv[t] != i) ? root[cv[t]] : -1;
-#pragma unroll
-        for (int t = 0; t < kWarpHashMaxDeg / 32; t++) {
+        for (int t = 0; t < B; t++) {
             if (cv[t] < 0) continue;
-            unsigned h = hash_slot(cv[t], lg);
+            unsigned hs = hash_slot(cv[t], lg);
             for (;;) {
-                int prev = atomicCAS(&keys[h], -1, cv[t]);
-                if (prev == -1) ul[atomicAdd(&nused[wib], 1)] = (unsigned short)h;
-                if (prev == -1 || prev == cv[t]) { atomicAdd(&vals[h], wv[t]); break; }
-                h = (h + 1) & (cap - 1);
+                int prev = atomicCAS(&keys[hs], -1, cv[t]);
+                if (prev == -1) ul[atomicAdd(&nused[wib], 1)] = (unsigned short)hs;
+                if (prev == -1 || prev == cv[t]) { atomicAdd(&vals[hs], wv[t]); break; }
+                hs = (hs + 1) & (cap - 1);
             }
         }
         __syncwarp();
+        // the next node's row is in flight while this one is decided
+        const RowHead hn = load_head(order, idx + nwarps, cnt, rp, root, s);
+        load_batch<B>(hn, hn.start + lane, 32, col, w, root, cv, wv);
         const int nu = nused[wib];
         long long own = 0, sc = LLONG_MIN;
         int cc = INT_MAX;
         for (int k = lane; k < nu; k += 32) {
-            int h = ul[k];
-            int c = keys[h], v = vals[h];
-            keys[h] = -1;  // leave the table empty for the next node
-            vals[h] = 0;
+            int hs = ul[k];
+            int c = keys[hs], v = vals[hs];
+            keys[hs] = -1;  // leave the table empty for the next node
+            vals[hs] = 0;
             if (c == ci) { own = v; continue; }
             long long x = m * (long long)v - (long long)si * (long long)sigma[c];
             if (better(x, c, sc, cc)) { sc = x; cc = c; }
@@ -238,6 +271,7 @@ __global__ void __launch_bounds__(kWarpHashWarps * 32, 6) k_scan_warphash(const 
             nused[wib] = 0;
         }
         __syncwarp();
+        h = hn;
     }
     count_add(ncand, cand);
 }
@@ -282,7 +316,7 @@ constexpr size_t block_smem_bytes() {
 }
 
 template <int CAP>
-__global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *order, int32_t cnt, const int32_t *rp,
+__global__ void __launch_bounds__(kBlockThreads, CAP <= 2 * kBlockMidMaxDeg ? 6 : 3) k_scan_block(const int32_t *order, int32_t cnt, const int32_t *rp,
                              const int32_t *col, const int32_t *w, const int32_t *s, MParam mp,
                              const int32_t *root, const int32_t *sigma, int32_t *best,
                              long long *gain, int32_t *kown, unsigned long long *ncand) {
@@ -295,46 +329,43 @@ __global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *ord
     if (threadIdx.x == 0) *nused = 0;
     __syncthreads();
     unsigned cand = 0;
-    for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
-        int i = order[idx];
+    long long idx = blockIdx.x;
+    RowHead h = load_head(order, idx, cnt, rp, root, s);
+    int cv[B], wv[B];
+    load_batch<B>(h, h.start + threadIdx.x, blockDim.x, col, w, root, cv, wv);
+    for (; idx < cnt; idx += gridDim.x) {
+        const int i = h.i, ci = h.ci, si = h.si;
         const long long m = mp.of(i);
-        int start = rp[i], end = rp[i + 1];
-        int deg = end - start;
-        int ci = root[i], si = s[i];
-        int lg = ilog2_pow2_at_least(2 * deg);
-        int cap = 1 << lg;  // <= CAP because deg <= CAP / 2
-        for (int p0 = start + threadIdx.x; p0 < end; p0 += B * blockDim.x) {
-            int cv[B], wv[B];
-#pragma unroll
-            for (int t = 0; t < B; t++) {
-                int p = p0 + t * blockDim.x;
-                bool ok = p < end;
-                cv[t] = ok ? col[p] : -1;
-                wv[t] = ok ? w[p] : 0;
-            }
-#pragma unroll
-            for (int t = 0; t < B; t++) cv[t] = (cv[t] >= 0 && cv[t] != i) ? root[cv[t]] : -1;
+        const int lg = ilog2_pow2_at_least(2 * (h.end - h.start));
+        const int cap = 1 << lg;  // <= CAP because deg <= CAP / 2
+        for (int p0 = h.start + threadIdx.x;;) {
 #pragma unroll
             for (int t = 0; t < B; t++) {
                 if (cv[t] < 0) continue;
-                unsigned h = hash_slot(cv[t], lg);
+                unsigned hs = hash_slot(cv[t], lg);
                 for (;;) {
-                    int prev = atomicCAS(&keys[h], -1, cv[t]);
-                    if (prev == -1) ul[atomicAdd(nused, 1)] = (unsigned short)h;
-                    if (prev == -1 || prev == cv[t]) { atomicAdd(&vals[h], wv[t]); break; }
-                    h = (h + 1) & (cap - 1);
+                    int prev = atomicCAS(&keys[hs], -1, cv[t]);
+                    if (prev == -1) ul[atomicAdd(nused, 1)] = (unsigned short)hs;
+                    if (prev == -1 || prev == cv[t]) { atomicAdd(&vals[hs], wv[t]); break; }
+                    hs = (hs + 1) & (cap - 1);
                 }
             }
+            p0 += B * blockDim.x;
+            if (p0 >= h.end) break;
+            load_batch<B>(h, p0, blockDim.x, col, w, root, cv, wv);
         }
         __syncthreads();
+        // the next node's first batch is in flight while this one is decided
+        const RowHead hn = load_head(order, idx + gridDim.x, cnt, rp, root, s);
+        load_batch<B>(hn, hn.start + threadIdx.x, blockDim.x, col, w, root, cv, wv);
         const int nu = *nused;
         long long own = 0, sc = LLONG_MIN;
         int cc = INT_MAX;
         for (int k = threadIdx.x; k < nu; k += blockDim.x) {
-            int h = ul[k];
-            int c = keys[h], v = vals[h];
-            keys[h] = -1;  // leave the table empty for the next node
-            vals[h] = 0;
+            int hs = ul[k];
+            int c = keys[hs], v = vals[hs];
+            keys[hs] = -1;  // leave the table empty for the next node
+            vals[hs] = 0;
             if (c == ci) { own = v; continue; }
             long long x = m * (long long)v - (long long)si * (long long)sigma[c];
             if (better(x, c, sc, cc)) { sc = x; cc = c; }
@@ -345,6 +376,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_scan_block(const int32_t *ord
             *nused = 0;
         }
         __syncthreads();
+        h = hn;
     }
     if (threadIdx.x == 0 && cand) atomicAdd(ncand, (unsigned long long)cand);
 }
