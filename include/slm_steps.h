@@ -159,8 +159,11 @@ slm_status slm_get_scan_timing(const slm_graph *g, int32_t level, double *ms, in
  * member lists (prefix sums), 2 ancestor walks and per-edge credits, 3
  * subtree credits, 4 choice of the best cut (Algorithm POSITIVE, optimal
  * bisection), 5 application of the cuts, 6 new components of the members,
- * 7 local gains g(i), 8 member list of the next round.  Copies at most `cap`
- * values into `ns` (host memory) and sets *len to the number of phases. */
+ * 7 local gains g(i), 8 member list of the next round; then two counts
+ * rather than times: 9 rounds run on the full grid (the others ran on the
+ * small grid that finishes a call), 10 member visits of those rounds.
+ * Copies at most `cap` values into `ns` (host memory) and sets *len to the
+ * number of values. */
 slm_status slm_get_positive_profile(const slm_graph *g, int64_t *ns, int32_t cap, int32_t *len);
 
 /* Self-check of the failure path of the cooperative kernels (POSITIVE runs

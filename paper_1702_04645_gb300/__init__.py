@@ -31,7 +31,8 @@ FLAG_TIMING = 4
 PHASES = ["assign", "components", "positive", "scan", "move", "level", "sigma",
           "positive_rounds"]
 POSITIVE_PHASES = ["setup", "offsets", "walks_edges", "credits", "best_cut", "apply_cut",
-                   "components", "local_gains", "next_list"]
+                   "components", "local_gains", "next_list", "full_grid_rounds",
+                   "full_grid_visits"]
 P_HALF = 1 << 31
 P_ALWAYS = 1 << 32
 
@@ -348,7 +349,10 @@ class Graph:
         ln = C.c_int32()
         _check(load().slm_get_positive_profile(self._h, C.c_void_p(ns.ctypes.data), ns.shape[0],
                                                C.byref(ln)), self._h)
-        return {POSITIVE_PHASES[k]: float(ns[k]) / 1e6 for k in range(min(ln.value, ns.shape[0]))}
+        out = {POSITIVE_PHASES[k]: float(ns[k]) / 1e6 for k in range(min(ln.value, 9))}
+        for k in range(9, min(ln.value, ns.shape[0])):
+            out[POSITIVE_PHASES[k]] = int(ns[k])  # counts, not times
+        return out
 
     def trace(self) -> np.ndarray:
         lib = load()

@@ -827,6 +827,10 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
             C->visits += cnt;
             C->splits += C->R;
             C->R = 0;
+            if (stamp && gridDim.x > kPosTailBlocks) {
+                C->ph[9] += 1;
+                C->ph[10] += cnt;
+            }
         }
         GBAR_OR_RETURN();
         cnt = *((volatile int32_t *)&C->nextc[parity]);

@@ -317,8 +317,9 @@ void apply_moves(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt,
 // Phases of a POSITIVE round, for the optional profile: 0 round set-up,
 // 1 offsets (prefix sums), 2 ancestor walks and edge credits, 3 subtree
 // credits, 4 best cut, 5 cut application, 6 new components, 7 local gains,
-// 8 next member list.
-constexpr int kPosPhases = 9;
+// 8 next member list (nanoseconds); then two counts: 9 rounds run on the
+// full grid, 10 member visits of those rounds.
+constexpr int kPosPhases = 11;
 struct PositiveScratch {
     DevBuf flag, kown, listA, listB, rlist, posr, L, coff, subS, subWA, subWin, credit, TS, msz,
         bestsc, bestkey, pool, cyc, cnt, mark, tot, hdr, epref, kacc, cut, nf, noc, bs, ctrl;
