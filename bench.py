@@ -469,6 +469,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default scan tuning instead of tuning it on the graph")
     ap.add_argument("--workload", choices=["rmat", "forest", "scan", "served"], default="rmat")
     ap.add_argument("--rate", type=float, default=200.0, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals")
@@ -503,6 +505,10 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     g = load_graph()
+    tuning = None
+    if not args.no_autotune:
+        from paper_1702_04645_gb300 import tune
+        tuning, _ = tune.autotune_scan(g.row_ptr, g.col, g.w)
     G = slm.Graph(g.row_ptr, g.col, g.w)
     run_kw = dict(seed=args.seed, accept_p32=slm.P_HALF, stream=stream.cuda_stream)
 
@@ -525,6 +531,7 @@ def main():
     phase_tot = {}
     pos_prof = {}
     scan_l0 = (0.0, 0)
+    bucket_ms = {}
     barrier()
     with ClockSampler(local) as clk:
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -539,6 +546,8 @@ def main():
                 pos_prof[k] = pos_prof.get(k, 0.0) + ms
             a, b = G.scan_timing(0)
             scan_l0 = (scan_l0[0] + a, scan_l0[1] + b)
+            for k, ms in G.scan_bucket_timing().items():
+                bucket_ms[k] = bucket_ms.get(k, 0.0) + ms
         ev1.record(stream)
         barrier()
     launches = slm.launch_count() - launches0
@@ -562,6 +571,8 @@ def main():
                 "algorithmic_bytes_per_launch": l0_bytes,
                 "launches_timed": l0_cnt,
                 "avg_launch_ms": l0_ms / l0_cnt if l0_cnt else None,
+                "level0_bucket_ms_per_scan": {k: round(v / max(l0_cnt, 1), 4)
+                                              for k, v in bucket_ms.items()},
                 "all_levels": {"achieved": (bytes_per_step * args.steps / 1e9) / (scan_ms / 1e3)
                                if scan_ms > 0 else None, "launches": scan_cnt,
                                "avg_launch_ms": scan_ms / scan_cnt if scan_cnt else None}}
@@ -601,6 +612,8 @@ def main():
                            "l2": "inputs larger than L2 (CSR %.0f MB > 129 MB)" % ((8 * g.nnz + 4 * g.n) / 1e6),
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "scan_tuning": tuning if tuning is not None else slm.get_scan_tuning(),
+                "scan_tuning_source": "default" if tuning is None else "autotuned on the graph",
                 "gpu_launches": int(launches), "clocks": clocks,
                 "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in phase_tot.items()
                                        if k != "positive_rounds"},

@@ -152,6 +152,15 @@ slm_status slm_get_timing(const slm_graph *g, double *ms8, int64_t *count8);
  * stream.  Without SLM_FLAG_TIMING both are 0. */
 slm_status slm_get_scan_timing(const slm_graph *g, int32_t level, double *ms, int64_t *count);
 
+/* Device time of the level-0 scans of the last slm_run made with
+ * SLM_FLAG_TIMING, split by degree bucket (each bucket's kernels are timed
+ * with CUDA events on the stream that runs them; the buckets run side by
+ * side on four streams, so the times overlap): ms[k] for buckets
+ * 0 isolated, 1 degrees 1-4, 2 5-8, 3 9-16, 4 17-32, 5 33-256 (warp table),
+ * 6 257-1024, 7 1025-2048, 8 2049-4096 (block tables), 9 above 4096 (hubs).
+ * Copies at most `cap` values and sets *len to the number of buckets. */
+slm_status slm_get_scan_bucket_timing(const slm_graph *g, double *ms, int32_t cap, int32_t *len);
+
 /* Profile of the POSITIVE rounds of the last slm_run made with
  * SLM_FLAG_TIMING: nanoseconds of device time per phase of a round, summed
  * over every round of the run, read from the GPU's global timer at the grid
@@ -178,6 +187,25 @@ slm_status slm_get_positive_profile(const slm_graph *g, int64_t *ns, int32_t cap
  * cannot be resident at once.  Synchronous. */
 slm_status slm_check_grid_barrier(int32_t blocks, int32_t absent_block, double limit_s,
                                   void *stream);
+
+/* Launch shapes of the MAXIMAL scan, process-wide (no counterpart in the
+ * paper; results never depend on them, only speed does).  streams: 1 runs
+ * the degree buckets one after another on the caller's stream, 4 runs them
+ * side by side on the caller's stream and three library streams; the other
+ * fields cap each kernel shape's grid at that many blocks per SM
+ * (1..64).  Defaults: {4, 3, 6, 8, 8, 8, 16}. */
+typedef struct {
+    int32_t streams;
+    int32_t blocks_large; /* 2049..4096 edges per node, 64 KB shared table */
+    int32_t blocks_mid;   /* 1025..2048 edges, 32 KB table */
+    int32_t blocks_small; /* 257..1024 edges, 16 KB table */
+    int32_t blocks_warp;  /* 33..256 edges, one warp table per node */
+    int32_t blocks_hub;   /* above 4096 edges: row chunks and table slices */
+    int32_t blocks_group; /* 1..32 edges: lane groups */
+} slm_scan_tuning;
+/* Set (INVALID_ARGUMENT when a field is out of range) or read the tuning. */
+slm_status slm_set_scan_tuning(const slm_scan_tuning *t);
+slm_status slm_get_scan_tuning(slm_scan_tuning *t);
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t slm_launch_count(void);

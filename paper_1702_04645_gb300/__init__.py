@@ -18,7 +18,7 @@ import numpy as np
 
 from .build_lib import LIB, build  # noqa: F401
 
-__all__ = ["Graph", "Batch", "Server", "pack_forest", "Options", "LevelStats", "SlmError", "build", "load", "step_strengths",
+__all__ = ["Graph", "Batch", "Server", "pack_forest", "get_scan_tuning", "set_scan_tuning", "Options", "LevelStats", "SlmError", "build", "load", "step_strengths",
            "step_assign", "step_components", "step_scan", "step_branch_gain", "step_maximal",
            "step_positive", "step_compact", "step_aggregate", "step_modularity",
            "FLAG_NO_POSITIVE", "FLAG_STRICT", "P_HALF", "P_ALWAYS"]
@@ -30,6 +30,8 @@ FLAG_STRICT = 2
 FLAG_TIMING = 4
 PHASES = ["assign", "components", "positive", "scan", "move", "level", "sigma",
           "positive_rounds"]
+SCAN_BUCKETS = ["isolated", "deg1_4", "deg5_8", "deg9_16", "deg17_32", "deg33_256",
+                "deg257_1024", "deg1025_2048", "deg2049_4096", "hubs"]
 POSITIVE_PHASES = ["setup", "offsets", "walks_edges", "credits", "best_cut", "apply_cut",
                    "components", "local_gains", "next_list", "full_grid_rounds",
                    "full_grid_visits"]
@@ -47,7 +49,8 @@ EXPORTS = ["slm_default_options", "slm_create_graph", "slm_run", "slm_num_levels
            "slm_destroy_graph", "slm_status_string", "slm_last_error", "slm_step_strengths",
            "slm_step_assign", "slm_step_components", "slm_step_scan", "slm_step_branch_gain",
            "slm_step_maximal", "slm_step_positive", "slm_step_compact", "slm_step_aggregate",
-           "slm_step_modularity", "slm_get_trace", "slm_get_timing", "slm_get_positive_profile", "slm_get_scan_timing", "slm_release_cached_memory", "slm_check_grid_barrier",
+           "slm_step_modularity", "slm_get_trace", "slm_get_timing", "slm_get_positive_profile", "slm_get_scan_timing", "slm_get_scan_bucket_timing", "slm_set_scan_tuning",
+           "slm_get_scan_tuning", "slm_release_cached_memory", "slm_check_grid_barrier",
            "slm_launch_count",
            "slm_step_modularity_noalloc", "slm_batch_create", "slm_batch_run",
            "slm_batch_num_graphs", "slm_batch_num_levels", "slm_batch_get_partition",
@@ -99,6 +102,30 @@ class ServerStats(C.Structure):
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 
+class ScanTuning(C.Structure):
+    _fields_ = [("streams", C.c_int32), ("blocks_large", C.c_int32), ("blocks_mid", C.c_int32),
+                ("blocks_small", C.c_int32), ("blocks_warp", C.c_int32), ("blocks_hub", C.c_int32),
+                ("blocks_group", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def get_scan_tuning() -> dict:
+    t = ScanTuning()
+    _check(load().slm_get_scan_tuning(C.byref(t)))
+    return t.as_dict()
+
+
+def set_scan_tuning(**fields) -> dict:
+    """Change some fields of the process-wide scan tuning; returns the new tuning."""
+    cur = get_scan_tuning()
+    cur.update(fields)
+    t = ScanTuning(**cur)
+    _check(load().slm_set_scan_tuning(C.byref(t)))
+    return cur
+
+
 class Options(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("accept_p32", C.c_uint64), ("max_sweeps", C.c_int32),
                 ("max_levels", C.c_int32), ("flags", C.c_uint32)]
@@ -144,6 +171,9 @@ def load():
             "slm_get_timing": (C.c_int, [vp, vp, vp]),
             "slm_get_positive_profile": (C.c_int, [vp, vp, i32, C.POINTER(i32)]),
             "slm_get_scan_timing": (C.c_int, [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]),
+            "slm_get_scan_bucket_timing": (C.c_int, [vp, vp, i32, C.POINTER(i32)]),
+            "slm_set_scan_tuning": (C.c_int, [C.POINTER(ScanTuning)]),
+            "slm_get_scan_tuning": (C.c_int, [C.POINTER(ScanTuning)]),
             "slm_launch_count": (u64, []),
             "slm_release_cached_memory": (None, []),
             "slm_check_grid_barrier": (C.c_int, [i32, i32, C.c_double, vp]),
@@ -341,6 +371,14 @@ class Graph:
         cnt = C.c_int64()
         _check(load().slm_get_scan_timing(self._h, level, C.byref(ms), C.byref(cnt)), self._h)
         return ms.value, cnt.value
+
+    def scan_bucket_timing(self):
+        """{bucket: milliseconds} of the level-0 scans of the last run made with FLAG_TIMING."""
+        ms = np.zeros(len(SCAN_BUCKETS), dtype=np.float64)
+        ln = C.c_int32()
+        _check(load().slm_get_scan_bucket_timing(self._h, C.c_void_p(ms.ctypes.data), ms.shape[0],
+                                                 C.byref(ln)), self._h)
+        return {SCAN_BUCKETS[k]: float(ms[k]) for k in range(min(ln.value, ms.shape[0]))}
 
     def positive_profile(self):
         """{phase: milliseconds} of the POSITIVE rounds of the last run made with

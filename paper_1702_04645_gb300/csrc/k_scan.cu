@@ -732,6 +732,9 @@ Buckets::~Buckets() {
         if (join[k]) cudaEventDestroy(join[k]);
     }
     if (fork) cudaEventDestroy(fork);
+    for (auto &pe : pev)
+        for (cudaEvent_t e : pe)
+            if (e) cudaEventDestroy(e);
 }
 
 void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
@@ -823,9 +826,22 @@ template <class K> static void allow_smem(K kernel, size_t bytes, int which) {
     if (dev < 64) done[which] |= 1ull << dev;
 }
 
-static int blocks_for_groups(long long cnt, int nodes_per_warp, int threads = 256) {
+static std::mutex g_tuning_mu;
+static ScanTuning g_tuning;
+
+ScanTuning scan_tuning() {
+    std::lock_guard<std::mutex> lk(g_tuning_mu);
+    return g_tuning;
+}
+void set_scan_tuning(const ScanTuning &t) {
+    std::lock_guard<std::mutex> lk(g_tuning_mu);
+    g_tuning = t;
+}
+
+static int blocks_for_groups(long long cnt, int nodes_per_warp, int threads = 256,
+                             int per_sm = 16) {
     long long warps = (cnt + nodes_per_warp - 1) / nodes_per_warp;
-    return grid_for(warps * 32, threads, kNumSMs * 16);
+    return grid_for(warps * 32, threads, kNumSMs * per_sm);
 }
 
 void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
@@ -867,38 +883,58 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
     if (n <= 0) return;
     const int32_t *ord = bk.order.as<int32_t>();
     auto cnt = [&](int b) { return bk.off[b + 1] - bk.off[b]; };
+    const ScanTuning tu = scan_tuning();
+    const bool side = tu.streams > 1;
     // the buckets write disjoint nodes: run them side by side
-    SLM_CUDA(cudaEventRecord(bk.fork, st));
-    for (int k = 0; k < Buckets::kSide; k++) SLM_CUDA(cudaStreamWaitEvent(bk.side[k], bk.fork, 0));
-    cudaStream_t s0 = st, s1 = bk.side[0], s2 = bk.side[1], s3 = bk.side[2];
+    if (side) {
+        SLM_CUDA(cudaEventRecord(bk.fork, st));
+        for (int k = 0; k < Buckets::kSide; k++) SLM_CUDA(cudaStreamWaitEvent(bk.side[k], bk.fork, 0));
+    }
+    cudaStream_t s0 = st, s1 = side ? bk.side[0] : st, s2 = side ? bk.side[1] : st,
+                 s3 = side ? bk.side[2] : st;
+    Buckets &bt = const_cast<Buckets &>(bk);
+    if (bt.prof_ms)
+        for (int b = 0; b < kNumBuckets; b++)
+            for (int e = 0; e < 2; e++)
+                if (!bt.pev[b][e]) SLM_CUDA(cudaEventCreate(&bt.pev[b][e]));
+    auto mark = [&](int b, int e, cudaStream_t so) {
+        if (bt.prof_ms) SLM_CUDA(cudaEventRecord(bt.pev[b][e], so));
+    };
     if (int c = cnt(kBucketBlockL)) {
+        mark(kBucketBlockL, 0, s0);
         constexpr int CAP = 2 * kBlockSmemMaxDeg;
         const size_t smem = block_smem_bytes<CAP>();
         allow_smem(k_scan_block<CAP>, smem, 0);
-        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 3), kBlockThreads, smem, s0>>>(
+        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * tu.blocks_large), kBlockThreads, smem, s0>>>(
             ord + bk.off[kBucketBlockL], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
+        mark(kBucketBlockL, 1, s0);
     }
     if (int c = cnt(kBucketBlockM)) {
+        mark(kBucketBlockM, 0, s0);
         constexpr int CAP = 2 * kBlockMidMaxDeg;
         const size_t smem = block_smem_bytes<CAP>();
         allow_smem(k_scan_block<CAP>, smem, 1);
-        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 6), kBlockThreads, smem, s0>>>(
+        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * tu.blocks_mid), kBlockThreads, smem, s0>>>(
             ord + bk.off[kBucketBlockM], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
+        mark(kBucketBlockM, 1, s0);
     }
     if (int c = cnt(kBucketWarpHash)) {
-        k_scan_warphash<<<grid_for((long long)c * 32, kWarpHashWarps * 32, kNumSMs * 8), kWarpHashWarps * 32, 0, s1>>>(
+        mark(kBucketWarpHash, 0, s1);
+        k_scan_warphash<<<grid_for((long long)c * 32, kWarpHashWarps * 32, kNumSMs * tu.blocks_warp), kWarpHashWarps * 32, 0, s1>>>(
             ord + bk.off[kBucketWarpHash], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
+        mark(kBucketWarpHash, 1, s1);
     }
     if (bk.nhub > 0) {
+        mark(kBucketHub, 0, s3);
         const int32_t *hubs = ord + bk.off[kBucketHub];
-        k_hub_insert<<<grid_for(bk.nchunk, 1, kNumSMs * 8), kBlockThreads, 0, s3>>>(
+        k_hub_insert<<<grid_for(bk.nchunk, 1, kNumSMs * tu.blocks_hub), kBlockThreads, 0, s3>>>(
             bk.chunks.as<int4>(), bk.nchunk, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(),
             col, w, root, bk.tkeys.as<int>(), bk.tvals.as<int>());
         SLM_LAUNCH_CHECK();
-        k_hub_slices<<<grid_for(bk.ntchunk, 1, kNumSMs * 8), kBlockThreads, 0, s3>>>(
+        k_hub_slices<<<grid_for(bk.ntchunk, 1, kNumSMs * tu.blocks_hub), kBlockThreads, 0, s3>>>(
             bk.tchunks.as<int2>(), bk.ntchunk, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(),
             s, m, root, sigma, bk.tkeys.as<int>(), bk.tvals.as<int>(), bk.part_own.as<long long>(),
             bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>());
@@ -907,36 +943,60 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
             bk.nhub, hubs, bk.tc_off.as<int32_t>(), s, m, root, sigma, bk.part_own.as<long long>(),
             bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>(), best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
+        mark(kBucketHub, 1, s3);
     }
     if (int c = cnt(kBucketBlockS)) {
+        mark(kBucketBlockS, 0, s2);
         constexpr int CAP = 2 * kBlockSmallMaxDeg;
-        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, block_smem_bytes<CAP>(), s2>>>(
+        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * tu.blocks_small), kBlockThreads, block_smem_bytes<CAP>(), s2>>>(
             ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
+        mark(kBucketBlockS, 1, s2);
     }
     if (int c = cnt(kBucketG16)) {
-        k_scan_group<16><<<blocks_for_groups(c, 2), 256, 0, s2>>>(ord + bk.off[kBucketG16], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        mark(kBucketG16, 0, s2);
+        k_scan_group<16><<<blocks_for_groups(c, 2, 256, tu.blocks_group), 256, 0, s2>>>(ord + bk.off[kBucketG16], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
+        mark(kBucketG16, 1, s2);
     }
     if (int c = cnt(kBucketG32)) {
-        k_scan_group<32><<<blocks_for_groups(c, 1), 256, 0, s2>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        mark(kBucketG32, 0, s2);
+        k_scan_group<32><<<blocks_for_groups(c, 1, 256, tu.blocks_group), 256, 0, s2>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
+        mark(kBucketG32, 1, s2);
     }
     if (int c = cnt(kBucketG4)) {
-        k_scan_group<4><<<blocks_for_groups(c, 8), 256, 0, s3>>>(ord + bk.off[kBucketG4], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        mark(kBucketG4, 0, s3);
+        k_scan_group<4><<<blocks_for_groups(c, 8, 256, tu.blocks_group), 256, 0, s3>>>(ord + bk.off[kBucketG4], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
+        mark(kBucketG4, 1, s3);
     }
     if (int c = cnt(kBucketG8)) {
-        k_scan_group<8><<<blocks_for_groups(c, 4), 256, 0, s3>>>(ord + bk.off[kBucketG8], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
+        mark(kBucketG8, 0, s3);
+        k_scan_group<8><<<blocks_for_groups(c, 4, 256, tu.blocks_group), 256, 0, s3>>>(ord + bk.off[kBucketG8], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
+        mark(kBucketG8, 1, s3);
     }
     if (int c = cnt(kBucketEmpty)) {
+        mark(kBucketEmpty, 0, s1);
         k_scan_empty<<<grid_for(c, 256), 256, 0, s1>>>(ord + bk.off[kBucketEmpty], c, root, best, gain, kown);
         SLM_LAUNCH_CHECK();
+        mark(kBucketEmpty, 1, s1);
     }
-    for (int k = 0; k < Buckets::kSide; k++) {
-        SLM_CUDA(cudaEventRecord(bk.join[k], bk.side[k]));
-        SLM_CUDA(cudaStreamWaitEvent(st, bk.join[k], 0));
+    if (side)
+        for (int k = 0; k < Buckets::kSide; k++) {
+            SLM_CUDA(cudaEventRecord(bk.join[k], bk.side[k]));
+            SLM_CUDA(cudaStreamWaitEvent(st, bk.join[k], 0));
+        }
+    if (bt.prof_ms) {
+        stream_sync(st);
+        for (int b = 0; b < kNumBuckets; b++) {
+            if (b != kBucketHub && bk.off[b + 1] == bk.off[b]) continue;
+            if (b == kBucketHub && bk.nhub == 0) continue;
+            float t = 0;
+            SLM_CUDA(cudaEventElapsedTime(&t, bt.pev[b][0], bt.pev[b][1]));
+            bt.prof_ms[b] += t;
+        }
     }
 }
 

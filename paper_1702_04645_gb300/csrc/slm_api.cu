@@ -45,6 +45,7 @@ struct slm_graph {
     long long pos_ns[slm::kPosPhases] = {0};  // POSITIVE round phases (SLM_FLAG_TIMING)
     // scan time and scan count per level (SLM_FLAG_TIMING); the last entry is the top level
     std::vector<std::pair<double, long long>> scan_by_level;
+    double bucket_ms[slm::kNumBuckets] = {0};  // level-0 scan time per degree bucket
 };
 
 namespace {
@@ -203,6 +204,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
     slm::HostCounters hc;
     for (int k = 0; k < 8; k++) { g->phase_ms[k] = 0; g->phase_cnt[k] = 0; }
     for (int k = 0; k < slm::kPosPhases; k++) g->pos_ns[k] = 0;
+    for (int k = 0; k < slm::kNumBuckets; k++) g->bucket_ms[k] = 0;
     PhaseTimer tmr((opt.flags & SLM_FLAG_TIMING) != 0, st, g->phase_ms, g->phase_cnt);
     PhaseTimer *tm = tmr.on ? &tmr : nullptr;
     // current level graph
@@ -223,6 +225,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         };
         if (tm) tm->start();
         W.init(n, rp, st);
+        W.bk.prof_ms = (tm && t == 0) ? g->bucket_ms : nullptr;
         if (tm) tm->stop(kPhLevel);
         slm_level_stats stt{};
         stt.n = n;
@@ -517,6 +520,38 @@ slm_status slm_get_scan_timing(const slm_graph *g, int32_t level, double *ms, in
     }
     *ms = g->scan_by_level[k].first;
     *count = g->scan_by_level[k].second;
+    return SLM_OK;
+}
+
+slm_status slm_set_scan_tuning(const slm_scan_tuning *t) {
+    if (!t || (t->streams != 1 && t->streams != 4)) return SLM_ERR_INVALID_ARGUMENT;
+    for (int32_t v : {t->blocks_large, t->blocks_mid, t->blocks_small, t->blocks_warp,
+                      t->blocks_hub, t->blocks_group})
+        if (v < 1 || v > 64) return SLM_ERR_INVALID_ARGUMENT;
+    slm::ScanTuning u;
+    u.streams = t->streams;
+    u.blocks_large = t->blocks_large;
+    u.blocks_mid = t->blocks_mid;
+    u.blocks_small = t->blocks_small;
+    u.blocks_warp = t->blocks_warp;
+    u.blocks_hub = t->blocks_hub;
+    u.blocks_group = t->blocks_group;
+    slm::set_scan_tuning(u);
+    return SLM_OK;
+}
+
+slm_status slm_get_scan_tuning(slm_scan_tuning *t) {
+    if (!t) return SLM_ERR_INVALID_ARGUMENT;
+    const slm::ScanTuning u = slm::scan_tuning();
+    *t = slm_scan_tuning{u.streams, u.blocks_large, u.blocks_mid, u.blocks_small,
+                         u.blocks_warp, u.blocks_hub, u.blocks_group};
+    return SLM_OK;
+}
+
+slm_status slm_get_scan_bucket_timing(const slm_graph *g, double *ms, int32_t cap, int32_t *len) {
+    if (!g || !len || cap < 0 || (cap > 0 && !ms)) return SLM_ERR_INVALID_ARGUMENT;
+    *len = slm::kNumBuckets;
+    for (int k = 0; k < cap && k < slm::kNumBuckets; k++) ms[k] = g->bucket_ms[k];
     return SLM_OK;
 }
 

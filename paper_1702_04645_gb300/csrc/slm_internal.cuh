@@ -227,6 +227,22 @@ constexpr int kBlockMidMaxDeg = 2048;   // block shape with a 32 KB table up to 
 constexpr int kBlockSmemMaxDeg = 4096;  // block shape with a 64 KB table up to here; above: hub
 constexpr int kHubChunk = 2048;         // edges of a hub handled by one block
 
+// Launch shapes of the MAXIMAL scan (results never depend on them): the
+// number of streams the degree buckets run on (1 or 4) and, per kernel
+// shape, the largest grid as blocks per SM.  Process-wide; set by
+// slm_set_scan_tuning (for instance from the autotuner).
+struct ScanTuning {
+    int streams = 4;
+    int blocks_large = 3;   // 2049..4096 edges, 64 KB table
+    int blocks_mid = 6;     // 1025..2048 edges, 32 KB table
+    int blocks_small = 8;   // 257..1024 edges, 16 KB table
+    int blocks_warp = 8;    // 33..256 edges, warp tables
+    int blocks_hub = 8;     // hub chunks and table slices
+    int blocks_group = 16;  // 1..32 edges, lane groups
+};
+ScanTuning scan_tuning();
+void set_scan_tuning(const ScanTuning &t);
+
 struct Buckets {
     DevBuf order;                       // int32[n]: nodes sorted by bucket (stable)
     int32_t off[kNumBuckets + 1] = {0}; // host copy of bucket offsets
@@ -241,6 +257,10 @@ struct Buckets {
     static constexpr int kSide = 3;
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork = nullptr, join[kSide] = {};
+    // optional per-bucket timing of the scans (milliseconds added to
+    // prof_ms[bucket]; events recorded on the bucket's stream)
+    double *prof_ms = nullptr;
+    cudaEvent_t pev[kNumBuckets][2] = {};
     void build(int32_t n, const int32_t *rp, cudaStream_t s);
     Buckets() = default;
     Buckets(const Buckets &) = delete;

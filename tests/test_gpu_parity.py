@@ -269,3 +269,31 @@ def test_invalid_inputs_are_rejected():
     with pytest.raises(slm.SlmError) as e:
         G.num_levels()
     assert e.value.status == 6
+
+
+def test_scan_tuning_changes_no_result():
+    """Every launch shape of the scan gives the same outputs (the autotuner
+    relies on it), and the autotuner returns a valid tuning."""
+    from paper_1702_04645_gb300 import tune
+    g = gg.rmat(scale=14, seed=9)
+    rp, col, w = dev(g.row_ptr), dev(g.col), dev(g.w)
+    s, m = slm.step_strengths(rp, col, w)
+    a = slm.step_assign(rp, col, w, s, m)
+    a, root, _ = slm.step_positive(rp, col, w, s, m, a)
+    start = slm.get_scan_tuning()
+    ref = [host(t) for t in slm.step_scan(rp, col, w, s, m, root)]
+    try:
+        for t in ({"streams": 1}, {"blocks_large": 1, "blocks_mid": 2, "blocks_warp": 4},
+                  {"blocks_group": 32, "blocks_hub": 16, "blocks_small": 4}):
+            slm.set_scan_tuning(**t)
+            out = [host(x) for x in slm.step_scan(rp, col, w, s, m, root)]
+            for x, y in zip(out, ref):
+                assert np.array_equal(x, y)
+        best, rep = tune.autotune_scan(g.row_ptr, g.col, g.w, reps=2, use_cache=False)
+        assert set(best) == set(start)
+        assert rep["best_ms"] <= rep["start_ms"]
+    finally:
+        slm.set_scan_tuning(**start)
+    with pytest.raises(slm.SlmError):
+        slm.set_scan_tuning(streams=3)
+    assert slm.get_scan_tuning() == start
