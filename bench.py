@@ -57,6 +57,11 @@ def load_graph():
     return gg.cached("rmat_s20_seed2", gg.rmat, scale=20, seed=2)
 
 
+def note(msg: str):
+    """Progress line on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -163,7 +168,7 @@ def load_forest():
         z = np.load(cache)
         return z["goff"], z["rp"], z["col"], z["w"], z["seeds"]
     params = gg.forest_sbm_params()
-    goff, rp, col, w, sds = gg.forest_sbm(params)
+    goff, rp, col, w, sds = gg.forest_sbm(params, workers=os.cpu_count() or 1)
     os.makedirs(os.path.dirname(cache), exist_ok=True)
     np.savez(cache + ".tmp.npz", goff=goff, rp=rp, col=col, w=w, seeds=sds)
     os.replace(cache + ".tmp.npz", cache)
@@ -189,11 +194,17 @@ def run_forest(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
     goff, rp, col, w, sds = load_forest()
     G = len(goff) - 1
+    note(f"forest ready: {G} graphs, {int(goff[-1])} nodes, {int(rp[-1])} entries "
+         f"({time.perf_counter() - t0:.1f} s)")
     B = slm.Batch(graph_off=goff, row_ptr=rp, col=col, w=w, seeds=sds)
-    for _ in range(args.warmup):
+    for k in range(args.warmup):
+        t0 = time.perf_counter()
         B.run(accept_p32=slm.P_HALF, stream=stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        note(f"warm-up run {k}: {time.perf_counter() - t0:.2f} s")
     torch.cuda.synchronize(dev)
     launches0 = slm.launch_count()
     with ClockSampler(local) as clk:

@@ -352,13 +352,20 @@ def forest_sbm_graph(n: int, blocks: int, seed: int, deg_in: float = 12.0,
 
 
 def forest_sbm(params, deg_in: float = 12.0, deg_out: float = 3.0, wmin: int = 1, wmax: int = 4,
-               chunk: int = 256):
+               chunk: int = 256, workers: int = 0):
     """All graphs of forest_sbm_params packed as one block-diagonal CSR:
     returns (graph_off, row_ptr, col, w, seeds).  Graph g is exactly
     forest_sbm_graph(n_g, blocks_g, seed_g) shifted by graph_off[g].  Graphs
-    are drawn `chunk` at a time with vectorised draws."""
-    parts = [_forest_sbm_chunk(params[k:k + chunk], deg_in, deg_out, wmin, wmax)
-             for k in range(0, len(params), chunk)]
+    are drawn `chunk` at a time with vectorised draws, in `workers` spawned
+    processes when workers > 1 (the result does not depend on it)."""
+    jobs = [(params[k:k + chunk], deg_in, deg_out, wmin, wmax)
+            for k in range(0, len(params), chunk)]
+    if workers and workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, len(jobs))) as pool:
+            parts = pool.starmap(_forest_sbm_chunk, jobs)
+    else:
+        parts = [_forest_sbm_chunk(*j) for j in jobs]
     G = len(params)
     goff = np.zeros(G + 1, dtype=np.int64)
     rps, cols, ws = [], [], []
