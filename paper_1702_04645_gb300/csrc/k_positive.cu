@@ -86,18 +86,21 @@ __device__ __forceinline__ void d_compact_atomic(int cnt, const int32_t *list, c
 // one round (phases of the persistent kernel below)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void k_round_init(int cnt, const int32_t *M, const int32_t *ideg, const int32_t *root,
-                             long long *subS, long long *subWA, long long *subWin,
-                             long long *credit, long long *TS, int32_t *rlist, int32_t *rcnt,
-                             int32_t *posr, int32_t *degm, long long *kacc) {
+                             const int32_t *freshN, bool first, long long *subS, long long *subWA,
+                             long long *subWin, long long *credit, long long *TS, int32_t *rlist,
+                             int32_t *rcnt, int32_t *posr, int32_t *degm, long long *kacc) {
     GRID_STRIDE(k, cnt) {
         int v = M[k];
-        degm[k] = ideg[v];
+        const bool fr = first || freshN[root[v]];
+        degm[k] = fr ? ideg[v] : 0;  // only new parts rescan their entries
         kacc[k] = 0;
-        subS[v] = 0;
-        subWA[v] = 0;
-        subWin[v] = 0;
-        credit[v] = 0;
-        TS[v] = 0;
+        if (fr) {
+            subS[v] = 0;
+            subWA[v] = 0;
+            subWin[v] = 0;
+            credit[v] = 0;
+            TS[v] = 0;
+        }
         if (root[v] == v) {
             int q = atomicAdd(rcnt, 1);
             rlist[q] = v;
@@ -129,10 +132,12 @@ __device__ __forceinline__ void k_root_init(int cnt, const int32_t *Rdev, const 
 // every member adds itself to its non-cycle ancestors (itself included) and to
 // the total of the tree hanging from its entry
 __device__ __forceinline__ void k_walk(int cnt, const int32_t *M, const int32_t *a, const int32_t *depth,
-                       const int32_t *s, const int32_t *kown, long long *subS, long long *subWA,
+                       const int32_t *s, const int32_t *kown, const int32_t *root,
+                       const int32_t *freshN, bool first, long long *subS, long long *subWA,
                        long long *TS) {
     GRID_STRIDE(k, cnt) {
         int x = M[k];
+        if (!first && !freshN[root[x]]) continue;
         long long sx = s[x], kx = kown[x];
         int y = x;
         for (int d = depth[x]; d > 0; d--) {
@@ -146,7 +151,7 @@ __device__ __forceinline__ void k_walk(int cnt, const int32_t *M, const int32_t 
 
 __device__ __forceinline__ void k_cycle_order(int cnt, const int32_t *M, const uint8_t *oncycle,
                               const int32_t *root, const int32_t *posr, const int32_t *L,
-                              const int32_t *cdist, const int32_t *coff, int32_t *cyc) {
+                              const int32_t *cdist, const int32_t *coffN, int32_t *cyc) {
     GRID_STRIDE(k, cnt) {
         int v = M[k];
         if (!oncycle[v]) continue;
@@ -155,7 +160,7 @@ __device__ __forceinline__ void k_cycle_order(int cnt, const int32_t *M, const u
         int l = L[q];
         if (l < 2) continue;
         int c = cyc_index(v, r, l, cdist);
-        if (c >= 0 && c < l) cyc[coff[q] + c] = v;
+        if (c >= 0 && c < l) cyc[coffN[r] + c] = v;
     }
 }
 
@@ -196,7 +201,7 @@ __device__ __forceinline__ void k_edges(int cnt, const int32_t *M, const int32_t
                         const int32_t *istart, const int32_t *col, const int32_t *w, const int32_t *a,
                         const uint8_t *oncycle, const int32_t *entry, const int32_t *depth,
                         const int32_t *root, const int32_t *posr, const int32_t *L,
-                        const int32_t *cdist, const long long *moff, long long *Mw,
+                        const int32_t *cdist, const long long *moffN, long long *Mw,
                         long long *credit) {
     const long long E = *Edev;
     WARP_SLOTS(base, E) {
@@ -217,15 +222,17 @@ __device__ __forceinline__ void k_edges(int cnt, const int32_t *M, const int32_t
             int l = L[q];
             int kx = cyc_index(ex, r, l, cdist), kj = cyc_index(ej, r, l, cdist);
             if (l >= 2 && kx >= 0 && kx < l && kj >= 0 && kj < l)
-                add64(&Mw[moff[q] + (long long)kx * l + kj], wv);
+                add64(&Mw[moffN[r] + (long long)kx * l + kj], wv);
         }
     }
 }
 
 __device__ __forceinline__ void k_credit(int cnt, const int32_t *M, const int32_t *a, const int32_t *depth,
+                         const int32_t *root, const int32_t *freshN, bool first,
                          const long long *credit, long long *subWin) {
     GRID_STRIDE(k, cnt) {
         int x = M[k];
+        if (!first && !freshN[root[x]]) continue;
         long long c = credit[x];
         if (c == 0) continue;
         int y = x;
@@ -275,8 +282,8 @@ __device__ __forceinline__ void k_branch(int cnt, const int32_t *M, const uint8_
 
 // one block per community with a cycle of length >= 2; one thread per p, the
 // part V = trees (p, q] grows with q: W(V+q, U-q) = W(V,U) + row(q) - 2 W(V,q)
-__device__ __forceinline__ void k_cycle(const int32_t *Rdev, const int32_t *rlist, const int32_t *L, const int32_t *coff,
-                        const int32_t *cyc, const long long *moff, const long long *Mw,
+__device__ __forceinline__ void k_cycle(const int32_t *Rdev, const int32_t *rlist, const int32_t *L, const int32_t *coffN,
+                        const int32_t *cyc, const long long *moffN, const long long *Mw,
                         const long long *TS, const int32_t *sigma, MParam mp, int32_t n,
                         long long *bestsc, unsigned long long *bestkey, int pass) {
     const int R = *Rdev;
@@ -285,8 +292,8 @@ __device__ __forceinline__ void k_cycle(const int32_t *Rdev, const int32_t *rlis
         if (l < 2) continue;
         const int r = rlist[q0];
         const long long m = mp.of(r);
-        const int32_t *cy = cyc + coff[q0];
-        const long long *Mr = Mw + moff[q0];
+        const int32_t *cy = cyc + coffN[r];
+        const long long *Mr = Mw + moffN[r];
         const long long sA = sigma[r];
         for (int p = threadIdx.x; p < l; p += blockDim.x) {
             long long cut = 0, sV = 0;
@@ -308,12 +315,18 @@ __device__ __forceinline__ void k_cycle(const int32_t *Rdev, const int32_t *rlis
 }
 
 // per split community: record the cut, set the totals of the two parts from
-// the subtree sums, and remove the cut assignments (a(u) <- u, a(v) <- v)
+// the subtree sums, and remove the cut assignments (a(u) <- u, a(v) <- v).
+// A branch cut keeps the remainder's sums (they are corrected in place after
+// the cut), so it records what the corrections need: the cut subtree's sums,
+// u's old parent and entry.  The part cut off, and both parts of a cycle
+// cut, are new (their sums are recomputed in the next round).
 __device__ __forceinline__ void k_cut_info(const int32_t *Rdev, const int32_t *rlist,
                            const unsigned long long *bestkey, int32_t n, const int32_t *L,
-                           const int32_t *coff, const int32_t *cyc, const long long *TS,
-                           const int32_t *depth, const int32_t *cdist, const long long *subS,
-                           int32_t *sigma, int4 *cut, int32_t *a, const int32_t *gid,
+                           const int32_t *coffN, const int32_t *cyc, const long long *TS,
+                           const int32_t *depth, const int32_t *entry, const int32_t *cdist,
+                           const long long *subS, const long long *subWA,
+                           const long long *subWin, int32_t *sigma, int4 *cut, long long *cutsum,
+                           int32_t *cutpar, int32_t *freshN, int32_t *a, const int32_t *gid,
                            int32_t *splits_per_graph) {
     const int R = *Rdev;
     GRID_STRIDE(q, R) {
@@ -322,6 +335,7 @@ __device__ __forceinline__ void k_cut_info(const int32_t *Rdev, const int32_t *r
         const unsigned long long key = bestkey[q];
         if (key == ~0ull) {  // no option recorded (cannot happen for size >= 2)
             cut[q] = make_int4(-1, 0, 0, 0);
+            freshN[r] = 1;
             continue;
         }
         const int type = (int)(key >> 62);
@@ -329,19 +343,26 @@ __device__ __forceinline__ void k_cut_info(const int32_t *Rdev, const int32_t *r
         const int v = (int)(key & 0x7fffffffu);
         if (u >= n || (type == 1 && v >= n)) {
             cut[q] = make_int4(-1, 0, 0, 0);
+            freshN[r] = 1;
             continue;
         }
         if (type == 0) {
             const long long sS = subS[u];
-            cut[q] = make_int4(0, u, depth[u], 0);
+            cut[q] = make_int4(0, u, depth[u], entry[u]);
+            cutsum[3 * q] = sS;
+            cutsum[3 * q + 1] = subWA[u];
+            cutsum[3 * q + 2] = subWin[u];
+            cutpar[q] = a[u];
             sigma[r] = (int32_t)((long long)sigma[r] - sS);
             sigma[u] = (int32_t)sS;
             a[u] = u;
+            freshN[r] = 0;
+            freshN[u] = 1;
         } else {
             const int l = L[q];
             const int iu = cyc_index(u, r, l, cdist), iv = cyc_index(v, r, l, cdist);
             const int p = min(iu, iv), pq = max(iu, iv);
-            const int32_t *cy = cyc + coff[q];
+            const int32_t *cy = cyc + coffN[r];
             long long sV = 0;
             for (int k = p + 1; k <= pq; k++) sV += TS[cy[k]];
             const long long sA = sigma[r];
@@ -351,6 +372,8 @@ __device__ __forceinline__ void k_cut_info(const int32_t *Rdev, const int32_t *r
             sigma[cp] = (int32_t)(sA - sV);
             a[cp] = cp;
             a[cq] = cq;
+            freshN[cp] = 1;
+            freshN[cq] = 1;
         }
     }
 }
@@ -363,13 +386,15 @@ __device__ __forceinline__ void k_cut_info(const int32_t *Rdev, const int32_t *r
 __device__ __forceinline__ void k_forest_new(int cnt, const int32_t *M, const int32_t *a, const int32_t *root,
                              const int32_t *entry, const int32_t *depth, const int32_t *cdist,
                              const uint8_t *oncycle, const int32_t *posr, const int4 *cut,
-                             const int32_t *coff, const int32_t *cyc, int4 *nf, uint8_t *noc) {
+                             const int32_t *coffN, const int32_t *cyc, int4 *nf, uint8_t *noc,
+                             int32_t *oldroot, uint8_t *recomp) {
     GRID_STRIDE(k, cnt) {
         const int x = M[k];
         const int r = root[x];
         const int4 ct = cut[posr[r]];
         int4 v = make_int4(r, entry[x], depth[x], cdist[x]);
         uint8_t oc = oncycle[x];
+        uint8_t rc = 0;  // 1: x's new part is new (its local gain is recomputed)
         if (ct.x == 0) {
             const int u = ct.y, du = ct.z;
             int dx = depth[x];
@@ -379,13 +404,15 @@ __device__ __forceinline__ void k_forest_new(int cnt, const int32_t *M, const in
                 if (y == u) {
                     v = make_int4(u, u, dx - du, 0);
                     oc = (x == u);
+                    rc = 1;
                 }
             }
         } else if (ct.x == 1) {
+            rc = 1;
             const int p = ct.y, pq = ct.z, l = ct.w;
             const int e = entry[x];
             const int ie = cyc_index(e, r, l, cdist);
-            const int32_t *cy = cyc + coff[posr[r]];
+            const int32_t *cy = cyc + coffN[r];
             if (ie > p && ie <= pq) {
                 const int cq = cy[pq];
                 v = make_int4(cq, cq, depth[x] + (pq - ie), 0);
@@ -398,6 +425,83 @@ __device__ __forceinline__ void k_forest_new(int cnt, const int32_t *M, const in
         }
         nf[k] = v;
         noc[k] = oc;
+        oldroot[k] = r;
+        recomp[k] = rc;
+    }
+}
+
+// Corrections of a branch cut's remainder R = A \ S (S = tail(u)), with the
+// values before the cut: every non-cycle ancestor of u loses S's strength
+// total, S's own-weight total and S's internal weight, and the tree total of
+// u's entry loses S's strength total (one thread per cut).  Then every entry
+// (x, y) with x in S and y in R removes w from y's own weight and from the
+// own-weight totals of y's non-cycle ancestors, 2w from the internal weight
+// of the common non-cycle ancestors of u and y (both directions of the
+// pair), or, when y hangs from another tree of the cycle, w from both
+// directions of the tree-to-tree weight (one warp per member of S).
+__device__ __forceinline__ void k_cut_fix(int cnt, const int32_t *M, const int32_t *Rdev,
+                                          const int4 *cut, const long long *cutsum,
+                                          const int32_t *cutpar, const int32_t *oldroot,
+                                          const uint8_t *recomp, const int32_t *posr,
+                                          const int32_t *root, const int32_t *a,
+                                          const int32_t *depth, const int32_t *entry,
+                                          const int32_t *cdist, const int32_t *istart,
+                                          const int32_t *ideg, const int32_t *icol,
+                                          const int32_t *iw, const long long *moffN,
+                                          int32_t *kown, long long *subS, long long *subWA,
+                                          long long *subWin, long long *TS, long long *Mw) {
+    const int R = *Rdev;
+    GRID_STRIDE(q, R) {
+        const int4 ct = cut[q];
+        if (ct.x != 0) continue;
+        const long long cS = cutsum[3 * q], cWA = cutsum[3 * q + 1], cWin = cutsum[3 * q + 2];
+        int y = cutpar[q];
+        for (int d = depth[y]; d > 0; d--) {
+            add64(&subS[y], -cS);
+            add64(&subWA[y], -cWA);
+            add64(&subWin[y], -cWin);
+            y = a[y];
+        }
+        add64(&TS[y], -cS);
+    }
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = warp; k < cnt; k += nw) {
+        if (!recomp[k]) continue;
+        const int r = oldroot[k];
+        const int q = posr[r];
+        const int4 ct = cut[q];
+        const int x = M[k];
+        if (ct.x != 0 || root[x] == r) continue;  // x is not in a cut subtree
+        const int e = ct.w, p = cutpar[q];
+        const int l = (a[r] == r) ? 1 : cdist[a[r]] + 1;  // R keeps A's cycle
+        const int ke = cyc_index(e, r, l, cdist);
+        const int b = istart[x], end = b + ideg[x];
+        for (int t = b + lane; t < end; t += 32) {
+            const int yv = icol[t];
+            if (root[yv] != r) continue;  // inside S, or left A in an earlier round
+            const int wv = iw[t];
+            atomicSub(&kown[yv], wv);
+            int z = yv;
+            for (int d = depth[yv]; d > 0; d--) {
+                add64(&subWA[z], -(long long)wv);
+                z = a[z];
+            }
+            if (entry[yv] == e) {
+                z = lca_walk(p, yv, a, depth);
+                for (int d = depth[z]; d > 0; d--) {
+                    add64(&subWin[z], -2 * (long long)wv);
+                    z = a[z];
+                }
+            } else if (l >= 2) {
+                const int ky = cyc_index(entry[yv], r, l, cdist);
+                if (ke >= 0 && ke < l && ky >= 0 && ky < l) {
+                    add64(&Mw[moffN[r] + (long long)ke * l + ky], -(long long)wv);
+                    add64(&Mw[moffN[r] + (long long)ky * l + ke], -(long long)wv);
+                }
+            }
+        }
     }
 }
 
@@ -416,21 +520,26 @@ __device__ __forceinline__ void k_forest_write(int cnt, const int32_t *M, const 
     }
 }
 
-// own-community weight of every member, one thread per internal edge
-__device__ __forceinline__ void k_own_edges(int cnt, const int32_t *M, const int32_t *epref, const int32_t *Edev,
-                            const int32_t *istart, const int32_t *col, const int32_t *w,
-                            const int32_t *root, long long *kacc) {
-    const long long E = *Edev;
-    WARP_SLOTS(base, E) {
-        long long e;
-        const int k = warp_owner(base, E, epref, cnt, e);
-        if (e != base + (threadIdx.x & 31)) continue;  // past the last slot
-        const int x = M[k];
-        const int p = istart[x] + (int)(e - epref[k]);
-        if (root[col[p]] == root[x]) add64(&kacc[k], w[p]);
+// own-community weight of the members of new parts (one warp per member)
+__device__ __forceinline__ void k_own_members(int cnt, const int32_t *M, const uint8_t *recomp,
+                                              const int32_t *istart, const int32_t *ideg,
+                                              const int32_t *col, const int32_t *w,
+                                              const int32_t *root, long long *kacc) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = warp; k < cnt; k += nw) {
+        if (!recomp[k]) continue;
+        const int x = M[k], rx = root[x];
+        const int b = istart[x], end = b + ideg[x];
+        long long acc = 0;
+        for (int t = b + lane; t < end; t += 32)
+            if (root[col[t]] == rx) acc += w[t];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) kacc[k] = acc;
     }
 }
-
 // ---------------------------------------------------------------------------
 // Internal edges of the members: POSITIVE only splits communities, so an
 // entry (x, j) with root[j] != root[x] at the start never becomes internal
@@ -489,13 +598,16 @@ __global__ void k_int_fill(int cnt, const int32_t *M, const int32_t *rp, const i
 }
 __device__ __forceinline__ void k_own_finish(int cnt, const int32_t *M, const int32_t *s, MParam mp,
                              const int32_t *root, const int32_t *sigma, const long long *kacc,
-                             int32_t *kown, int32_t *flag) {
+                             const uint8_t *recomp, int32_t *kown, int32_t *flag) {
     GRID_STRIDE(k, cnt) {
         int i = M[k];
         const long long m = mp.of(i);
         int ci = root[i];
-        long long own = kacc[k];
-        kown[i] = (int32_t)own;
+        long long own = kown[i];  // a remainder's own weights were corrected in place
+        if (recomp[k]) {
+            own = kacc[k];
+            kown[i] = (int32_t)own;
+        }
         long long si = s[i];
         if (m * own - si * ((long long)sigma[ci] - si) < 0) flag[ci] = 1;
     }
@@ -719,7 +831,10 @@ struct PosArgs {
     long long *msz, *subS, *subWA, *subWin, *credit, *TS, *bestsc, *kacc, *Mw;
     unsigned long long *bestkey;
     int4 *cut, *nf;
-    uint8_t *noc;
+    uint8_t *noc, *recomp;
+    long long *moffN, *cutsum;
+    int32_t *coffN, *freshN, *cutpar, *oldroot;
+    int first_round;  // 1 in the first launch of a call: every community is new
     int32_t *splits_per_graph;
     long long *bs64;
     int32_t *bs32a, *bs32b;
@@ -752,6 +867,7 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
     };
     int cnt = C->cnt;  // members of the first round
     int parity = 0;
+    bool first = A.first_round != 0;
     for (;;) {
         if (rank0) C->cnt = cnt;
         if (cnt == 0) break;
@@ -767,56 +883,76 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
             break;
         }
         if (rank0) C->nextc[parity] = 0;
-        k_round_init(cnt, M, A.ideg, A.root, A.subS, A.subWA, A.subWin, A.credit, A.TS, A.rlist, &C->R,
-                     A.posr, A.epref, A.kacc);
+        k_round_init(cnt, M, A.ideg, A.root, A.freshN, first, A.subS, A.subWA, A.subWin, A.credit,
+                     A.TS, A.rlist, &C->R, A.posr, A.epref, A.kacc);
         GBAR_OR_RETURN();
         k_root_init(cnt, &C->R, A.rlist, A.a, A.cdist, A.L, A.msz, A.coff, A.bestsc, A.bestkey);
         GBAR_OR_RETURN();
         mark_phase(0);
-        {
+        if (first) {
+            // the cycles of every community are laid out once per call: cuts
+            // never make a cycle longer, and a part that loses its cycle gets
+            // a self-loop, so the layout stays valid for the remainders
             ScanSlots S{A.msz, A.coff, A.epref, &C->mtot, &C->ctot, &C->E, A.bs64, A.bs32a, A.bs32b};
+            if (!grid_scan(S, cnt, A.bar, A.barrier_ns)) return;
+        } else {
+            ScanSlots S{nullptr, A.epref, nullptr, nullptr, &C->E, nullptr, nullptr, A.bs32a, nullptr};
             if (!grid_scan(S, cnt, A.bar, A.barrier_ns)) return;
         }
         mark_phase(1);
-        if (C->mtot > A.pool_cap || C->ctot > A.cyc_cap) {
-            if (rank0) C->error = 2;
-            break;
+        if (first) {
+            if (C->mtot > A.pool_cap || C->ctot > A.cyc_cap) {
+                if (rank0) C->error = 2;
+                break;
+            }
+            const long long mtot = C->mtot, ctot = C->ctot;
+            const int R = C->R;
+            GRID_STRIDE(q, R) {
+                const int r = A.rlist[q];
+                A.moffN[r] = A.msz[q];
+                A.coffN[r] = A.coff[q];
+            }
+            GRID_STRIDE(k, mtot) A.Mw[k] = 0;
+            GRID_STRIDE(k, ctot) A.cyc[k] = -1;
+            GBAR_OR_RETURN();
         }
-        const long long mtot = C->mtot, ctot = C->ctot;
-        GRID_STRIDE(k, mtot) A.Mw[k] = 0;
-        GRID_STRIDE(k, ctot) A.cyc[k] = -1;
-        GBAR_OR_RETURN();
-        k_walk(cnt, M, A.a, A.depth, A.s, A.kown, A.subS, A.subWA, A.TS);
-        if (ctot > 0) k_cycle_order(cnt, M, A.oncycle, A.root, A.posr, A.L, A.cdist, A.coff, A.cyc);
+        const bool cycles = C->ctot > 0;
+        k_walk(cnt, M, A.a, A.depth, A.s, A.kown, A.root, A.freshN, first, A.subS, A.subWA, A.TS);
+        if (first && cycles)
+            k_cycle_order(cnt, M, A.oncycle, A.root, A.posr, A.L, A.cdist, A.coffN, A.cyc);
         k_edges(cnt, M, A.epref, &C->E, A.istart, A.icol, A.iw, A.a, A.oncycle, A.entry, A.depth, A.root,
-                A.posr, A.L, A.cdist, A.msz, A.Mw, A.credit);
+                A.posr, A.L, A.cdist, A.moffN, A.Mw, A.credit);
         GBAR_OR_RETURN();
         mark_phase(2);
-        k_credit(cnt, M, A.a, A.depth, A.credit, A.subWin);
+        k_credit(cnt, M, A.a, A.depth, A.root, A.freshN, first, A.credit, A.subWin);
         GBAR_OR_RETURN();
         mark_phase(3);
         for (int pass = 0; pass < 2; pass++) {
             k_branch(cnt, M, A.oncycle, A.root, A.posr, A.sigma, A.m, A.subS, A.subWA, A.subWin,
                      A.bestsc, A.bestkey, pass);
-            if (ctot > 0)
-                k_cycle(&C->R, A.rlist, A.L, A.coff, A.cyc, A.msz, A.Mw, A.TS, A.sigma, A.m, n,
+            if (cycles)
+                k_cycle(&C->R, A.rlist, A.L, A.coffN, A.cyc, A.moffN, A.Mw, A.TS, A.sigma, A.m, n,
                         A.bestsc, A.bestkey, pass);
             GBAR_OR_RETURN();
         }
         mark_phase(4);
-        k_cut_info(&C->R, A.rlist, A.bestkey, n, A.L, A.coff, A.cyc, A.TS, A.depth, A.cdist, A.subS,
-                   A.sigma, A.cut, A.a, A.m.gid, A.splits_per_graph);
+        k_cut_info(&C->R, A.rlist, A.bestkey, n, A.L, A.coffN, A.cyc, A.TS, A.depth, A.entry, A.cdist,
+                   A.subS, A.subWA, A.subWin, A.sigma, A.cut, A.cutsum, A.cutpar, A.freshN, A.a,
+                   A.m.gid, A.splits_per_graph);
         GBAR_OR_RETURN();
         mark_phase(5);
-        k_forest_new(cnt, M, A.a, A.root, A.entry, A.depth, A.cdist, A.oncycle, A.posr, A.cut, A.coff,
-                     A.cyc, A.nf, A.noc);
+        k_forest_new(cnt, M, A.a, A.root, A.entry, A.depth, A.cdist, A.oncycle, A.posr, A.cut,
+                     A.coffN, A.cyc, A.nf, A.noc, A.oldroot, A.recomp);
         GBAR_OR_RETURN();
         k_forest_write(cnt, M, A.nf, A.noc, A.root, A.entry, A.depth, A.cdist, A.oncycle, A.flag);
         GBAR_OR_RETURN();
         mark_phase(6);
-        k_own_edges(cnt, M, A.epref, &C->E, A.istart, A.icol, A.iw, A.root, A.kacc);
+        k_cut_fix(cnt, M, &C->R, A.cut, A.cutsum, A.cutpar, A.oldroot, A.recomp, A.posr, A.root, A.a,
+                  A.depth, A.entry, A.cdist, A.istart, A.ideg, A.icol, A.iw, A.moffN, A.kown, A.subS,
+                  A.subWA, A.subWin, A.TS, A.Mw);
+        k_own_members(cnt, M, A.recomp, A.istart, A.ideg, A.icol, A.iw, A.root, A.kacc);
         GBAR_OR_RETURN();
-        k_own_finish(cnt, M, A.s, A.m, A.root, A.sigma, A.kacc, A.kown, A.flag);
+        k_own_finish(cnt, M, A.s, A.m, A.root, A.sigma, A.kacc, A.recomp, A.kown, A.flag);
         GBAR_OR_RETURN();
         mark_phase(7);
         // members of the still-flagged communities form the next list (its
@@ -839,6 +975,7 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
         M = M2;
         M2 = tmp;
         parity ^= 1;
+        first = false;
     }
 }
 
@@ -915,6 +1052,13 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     ps.cut.ensure(16 * (N + 1), st);
     ps.nf.ensure(16 * (N + 1), st);
     ps.noc.ensure(N + 1, st);
+    ps.recomp.ensure(N + 1, st);
+    ps.moffN.ensure(8 * (N + 1), st);
+    ps.cutsum.ensure(24 * (N + 1), st);
+    ps.coffN.ensure(4 * (N + 1), st);
+    ps.freshN.ensure(4 * (N + 1), st);
+    ps.cutpar.ensure(4 * (N + 1), st);
+    ps.oldroot.ensure(4 * (N + 1), st);
     ps.mark.ensure(4 * (N + 1), st);
     // pools sized once: the first round holds the longest cycles; the internal
     // entries of the members are counted in the same pass over the host
@@ -997,6 +1141,13 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     A.cut = ps.cut.as<int4>();
     A.nf = ps.nf.as<int4>();
     A.noc = ps.noc.as<uint8_t>();
+    A.recomp = ps.recomp.as<uint8_t>();
+    A.moffN = ps.moffN.as<long long>();
+    A.cutsum = ps.cutsum.as<long long>();
+    A.coffN = ps.coffN.as<int32_t>();
+    A.freshN = ps.freshN.as<int32_t>();
+    A.cutpar = ps.cutpar.as<int32_t>();
+    A.oldroot = ps.oldroot.as<int32_t>();
     A.splits_per_graph = splits_per_graph;
     A.bs64 = ps.bs.as<long long>();
     A.bs32a = reinterpret_cast<int32_t *>(ps.bs.as<long long>() + nblocks_full);
@@ -1011,6 +1162,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     const bool small_now = cnt <= kPosTailMembers && itot <= kPosTailEntries;
     for (int launch = 0; launch < 2; launch++) {
         const bool tail = small_now || launch == 1;
+        A.first_round = launch == 0 ? 1 : 0;
         A.handoff_cnt = tail ? 0 : kPosTailMembers;
         A.handoff_edges = kPosTailEntries;
         const int nb = tail ? std::min(kPosTailBlocks, nblocks_full) : nblocks_full;

@@ -399,14 +399,16 @@ __global__ void k_scan_empty(const int32_t *order, int32_t cnt, const int32_t *r
 // and picks the best community.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks, int nchunk, const int32_t *hubs,
-                             const long long *hoff, const int32_t *hlg, const int32_t *col,
-                             const int32_t *w, const int32_t *root, int *tkeys, int *tvals) {
+                             const long long *hoff, const int32_t *hlg, const long long *uoff,
+                             const int32_t *col, const int32_t *w, const int32_t *root, int *tkeys,
+                             int *tvals, int *ulist, int *ucnt) {
     for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
         int4 ch = chunks[c];  // (hub index, first edge, end edge, unused)
         const int i = hubs[ch.x];
         const int lg = hlg[ch.x];
         const int cap = 1 << lg;
         int *keys = tkeys + hoff[ch.x], *vals = tvals + hoff[ch.x];
+        int *ul = ulist + uoff[ch.x];
         for (int p = ch.y + threadIdx.x; p < ch.z; p += blockDim.x) {
             int j = col[p];
             if (j == i) continue;
@@ -414,6 +416,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks
             unsigned h = hash_slot(cc, lg);
             for (;;) {
                 int prev = atomicCAS(&keys[h], -1, cc);
+                if (prev == -1) ul[atomicAdd(&ucnt[ch.x], 1)] = (int)h;  // list the claimed slot
                 if (prev == -1 || prev == cc) { atomicAdd(&vals[h], wv); break; }
                 h = (h + 1) & (cap - 1);
             }
@@ -421,42 +424,44 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks
     }
 }
 
-// one block per slice of kHubSlice slots of a hub table: partial (own
-// weight, best score, best community), and the slots are reset
+// one block per slice of kHubSlice entries of a hub's list of occupied
+// table slots: partial (own weight, best score, best community), and the
+// slots are reset for the next scan
 __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunks, int ntchunk, const int32_t *hubs,
-                             const long long *hoff, const int32_t *hlg, const int32_t *s,
-                             MParam mp, const int32_t *root, const int32_t *sigma, int *tkeys,
-                             int *tvals, long long *part_own, long long *part_sc,
-                             int32_t *part_cc) {
+                             const long long *hoff, const long long *uoff, const int *ulist,
+                             const int *ucnt, const int32_t *s, MParam mp, const int32_t *root,
+                             const int32_t *sigma, int *tkeys, int *tvals, long long *part_own,
+                             long long *part_sc, int32_t *part_cc) {
     constexpr int B = kHubSlice / kBlockThreads;
     for (int tc = blockIdx.x; tc < ntchunk; tc += gridDim.x) {
-        const int2 d = tchunks[tc];  // (hub index, first slot)
+        const int2 d = tchunks[tc];  // (hub index, first list entry)
         const int i = hubs[d.x];
         const long long m = mp.of(i);
         const int ci = root[i], si = s[i];
-        const int cap = 1 << hlg[d.x];
+        const int nu = ucnt[d.x];
         int *keys = tkeys + hoff[d.x], *vals = tvals + hoff[d.x];
-        int kk[B], vv[B], sg[B];
+        const int *ul = ulist + uoff[d.x];
+        int hh[B], kk[B], vv[B], sg[B];
 #pragma unroll
         for (int t = 0; t < B; t++) {
             int k = d.y + threadIdx.x + t * kBlockThreads;
-            kk[t] = k < cap ? keys[k] : -1;
+            hh[t] = k < nu ? ul[k] : -1;
         }
 #pragma unroll
         for (int t = 0; t < B; t++) {
-            int k = d.y + threadIdx.x + t * kBlockThreads;
-            vv[t] = kk[t] >= 0 ? vals[k] : 0;
-            sg[t] = (kk[t] >= 0 && kk[t] != ci) ? sigma[kk[t]] : 0;
+            kk[t] = hh[t] >= 0 ? keys[hh[t]] : -1;
+            vv[t] = hh[t] >= 0 ? vals[hh[t]] : 0;
         }
+#pragma unroll
+        for (int t = 0; t < B; t++) sg[t] = (kk[t] >= 0 && kk[t] != ci) ? sigma[kk[t]] : 0;
         long long own = 0, sc = LLONG_MIN;
         int cc = INT_MAX;
 #pragma unroll
         for (int t = 0; t < B; t++) {
             int c = kk[t];
             if (c < 0) continue;
-            int k = d.y + threadIdx.x + t * kBlockThreads;
-            keys[k] = -1;  // leave the table empty for the next sweep
-            vals[k] = 0;
+            keys[hh[t]] = -1;  // leave the table empty for the next sweep
+            vals[hh[t]] = 0;
             if (c == ci) { own = vv[t]; continue; }
             long long x = m * (long long)vv[t] - (long long)si * (long long)sg[t];
             if (better(x, c, sc, cc)) { sc = x; cc = c; }
@@ -469,12 +474,10 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunk
         }
     }
 }
-
-// one warp per hub: reduce the slices' partials and decide
 __global__ void k_hub_finish(int nhub, const int32_t *hubs, const int32_t *tc_off, const int32_t *s,
                              MParam mp, const int32_t *root, const int32_t *sigma,
                              const long long *part_own, const long long *part_sc,
-                             const int32_t *part_cc, int32_t *best, long long *gain,
+                             const int32_t *part_cc, int *ucnt, int32_t *best, long long *gain,
                              int32_t *kown, unsigned long long *ncand) {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -496,7 +499,10 @@ __global__ void k_hub_finish(int nhub, const int32_t *hubs, const int32_t *tc_of
             int occ = __shfl_xor_sync(FULL, cc, o);
             if (better(osc, occ, sc, cc)) { sc = osc; cc = occ; }
         }
-        if (lane == 0) scan_emit(i, root[i], s[i], m, sigma, own, sc, cc, best, gain, kown, cand);
+        if (lane == 0) {
+            scan_emit(i, root[i], s[i], m, sigma, own, sc, cc, best, gain, kown, cand);
+            ucnt[h] = 0;  // the hub's slot list starts empty at the next scan
+        }
     }
     count_add(ncand, cand);
 }
@@ -776,6 +782,8 @@ void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
         std::vector<int4> ch;
         std::vector<int2> tch;
         long long tot = 0;
+        std::vector<long long> uoff(nhub);
+        long long utot = 0;
         for (int k = 0; k < nhub; k++) {
             int deg = hr[k].y - hr[k].x;
             int lg = 0;
@@ -783,11 +791,18 @@ void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
             hoff[k] = tot;
             hlg[k] = lg;
             tot += 1LL << lg;
+            uoff[k] = utot;  // the hub's list of occupied slots holds at most deg entries
+            utot += deg;
             for (int p0 = hr[k].x; p0 < hr[k].y; p0 += kHubChunk)
                 ch.push_back(make_int4(k, p0, std::min(p0 + kHubChunk, hr[k].y), 0));
             tcoff[k] = (int32_t)tch.size();
-            for (long long s0 = 0; s0 < (1LL << lg); s0 += kHubSlice) tch.push_back(make_int2(k, (int)s0));
+            for (long long s0 = 0; s0 < deg; s0 += kHubSlice) tch.push_back(make_int2(k, (int)s0));
         }
+        hub_uoff.alloc(sizeof(long long) * nhub, s);
+        hub_ucnt.alloc(sizeof(int) * nhub, s);
+        ulist.alloc(sizeof(int) * (utot > 0 ? utot : 1), s);
+        SLM_CUDA(cudaMemcpyAsync(hub_uoff.get(), uoff.data(), sizeof(long long) * nhub, cudaMemcpyHostToDevice, s));
+        SLM_CUDA(cudaMemsetAsync(hub_ucnt.get(), 0, sizeof(int) * nhub, s));
         tcoff[nhub] = (int32_t)tch.size();
         ntchunk = (int32_t)tch.size();
         tchunks.alloc(sizeof(int2) * tch.size(), s);
@@ -900,6 +915,28 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
     auto mark = [&](int b, int e, cudaStream_t so) {
         if (bt.prof_ms) SLM_CUDA(cudaEventRecord(bt.pev[b][e], so));
     };
+    // the hub chain (insert, slices, decisions) is the longest: start it first
+    if (bk.nhub > 0) {
+        mark(kBucketHub, 0, s3);
+        const int32_t *hubs = ord + bk.off[kBucketHub];
+        k_hub_insert<<<grid_for(bk.nchunk, 1, kNumSMs * tu.blocks_hub), kBlockThreads, 0, s3>>>(
+            bk.chunks.as<int4>(), bk.nchunk, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(),
+            bk.hub_uoff.as<long long>(), col, w, root, bk.tkeys.as<int>(), bk.tvals.as<int>(),
+            bk.ulist.as<int>(), bk.hub_ucnt.as<int>());
+        SLM_LAUNCH_CHECK();
+        k_hub_slices<<<grid_for(bk.ntchunk, 1, kNumSMs * tu.blocks_hub), kBlockThreads, 0, s3>>>(
+            bk.tchunks.as<int2>(), bk.ntchunk, hubs, bk.hub_off.as<long long>(),
+            bk.hub_uoff.as<long long>(), bk.ulist.as<int>(), bk.hub_ucnt.as<int>(), s, m, root, sigma,
+            bk.tkeys.as<int>(), bk.tvals.as<int>(), bk.part_own.as<long long>(),
+            bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>());
+        SLM_LAUNCH_CHECK();
+        k_hub_finish<<<grid_for((long long)bk.nhub * 32, 256), 256, 0, s3>>>(
+            bk.nhub, hubs, bk.tc_off.as<int32_t>(), s, m, root, sigma, bk.part_own.as<long long>(),
+            bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>(), bk.hub_ucnt.as<int>(), best, gain,
+            kown, ncand);
+        SLM_LAUNCH_CHECK();
+        mark(kBucketHub, 1, s3);
+    }
     if (int c = cnt(kBucketBlockL)) {
         mark(kBucketBlockL, 0, s0);
         constexpr int CAP = 2 * kBlockSmemMaxDeg;
@@ -926,24 +963,6 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
             ord + bk.off[kBucketWarpHash], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
         SLM_LAUNCH_CHECK();
         mark(kBucketWarpHash, 1, s1);
-    }
-    if (bk.nhub > 0) {
-        mark(kBucketHub, 0, s3);
-        const int32_t *hubs = ord + bk.off[kBucketHub];
-        k_hub_insert<<<grid_for(bk.nchunk, 1, kNumSMs * tu.blocks_hub), kBlockThreads, 0, s3>>>(
-            bk.chunks.as<int4>(), bk.nchunk, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(),
-            col, w, root, bk.tkeys.as<int>(), bk.tvals.as<int>());
-        SLM_LAUNCH_CHECK();
-        k_hub_slices<<<grid_for(bk.ntchunk, 1, kNumSMs * tu.blocks_hub), kBlockThreads, 0, s3>>>(
-            bk.tchunks.as<int2>(), bk.ntchunk, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(),
-            s, m, root, sigma, bk.tkeys.as<int>(), bk.tvals.as<int>(), bk.part_own.as<long long>(),
-            bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>());
-        SLM_LAUNCH_CHECK();
-        k_hub_finish<<<grid_for((long long)bk.nhub * 32, 256), 256, 0, s3>>>(
-            bk.nhub, hubs, bk.tc_off.as<int32_t>(), s, m, root, sigma, bk.part_own.as<long long>(),
-            bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>(), best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-        mark(kBucketHub, 1, s3);
     }
     if (int c = cnt(kBucketBlockS)) {
         mark(kBucketBlockS, 0, s2);

@@ -250,7 +250,10 @@ struct Buckets {
     // (hub index, first edge, end edge) that split its row across blocks
     int32_t nhub = 0, nchunk = 0, ntchunk = 0;
     DevBuf hub_off, hub_lg, chunks, tkeys, tvals, hub_acc;
-    // slices of the hub tables read by one block each, and their partial results
+    // per hub: its list of occupied table slots (offset, count), so that the
+    // decision reads the distinct communities only
+    DevBuf hub_uoff, hub_ucnt, ulist;
+    // slices of the hubs' slot lists read by one block each, and their partial results
     DevBuf tchunks, tc_off, part_own, part_sc, part_cc;
     // side streams on which the independent bucket kernels of a scan overlap
     // (owned here so that concurrent runs never share fork/join events)
@@ -344,6 +347,7 @@ struct PositiveScratch {
     DevBuf flag, kown, listA, listB, rlist, posr, L, coff, subS, subWA, subWin, credit, TS, msz,
         bestsc, bestkey, pool, cyc, cnt, mark, tot, hdr, epref, kacc, cut, nf, noc, bs, ctrl;
     DevBuf icnt, ioff, istart, ideg, icol, iw;  // internal entries of the members
+    DevBuf recomp, moffN, cutsum, coffN, freshN, cutpar, oldroot;  // incremental rounds
     bool profile = false;              // stamp the phases of every round
     long long prof_ns[kPosPhases] = {};  // summed nanoseconds per phase
 };
