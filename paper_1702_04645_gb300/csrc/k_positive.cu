@@ -31,6 +31,18 @@ namespace {
 
 #define GRID_STRIDE SLM_GRID_STRIDE
 
+// Warp loops over the members that need work: each warp tests 32 consecutive
+// members at once and then serves the selected ones one after the other with
+// all its lanes (an entry of the member's row per lane).
+#define WARP_SELECTED(k, cnt, pred)                                                           \
+    for (long long _b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; _b < (cnt); \
+         _b += (long long)gridDim.x * blockDim.x)                                             \
+        for (unsigned _sel = __ballot_sync(0xffffffffu, _b + (threadIdx.x & 31) < (cnt) &&    \
+                                                         (pred)(_b + (threadIdx.x & 31)));     \
+             _sel; _sel &= _sel - 1)                                                          \
+            for (long long k = _b + __ffs(_sel) - 1, _once = 1; _once; _once = 0)
+
+
 __device__ __forceinline__ unsigned long long split_key(int type, int u, int v) {
     return ((unsigned long long)type << 62) | ((unsigned long long)(unsigned)u << 31) |
            (unsigned long long)(unsigned)v;
@@ -86,9 +98,11 @@ __device__ __forceinline__ void d_compact_atomic(int cnt, const int32_t *list, c
 // one round (phases of the persistent kernel below)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void k_round_init(int cnt, const int32_t *M, const int32_t *ideg, const int32_t *root,
-                             const int32_t *freshN, bool first, long long *subS, long long *subWA,
+                             const int32_t *freshN, bool first, const int32_t *a,
+                             const int32_t *cdist, long long *subS, long long *subWA,
                              long long *subWin, long long *credit, long long *TS, int32_t *rlist,
-                             int32_t *rcnt, int32_t *posr, int32_t *degm, long long *kacc) {
+                             int32_t *rcnt, int32_t *posr, int32_t *L, int32_t *degm,
+                             long long *kacc, long long *bestsc, unsigned long long *bestkey) {
     GRID_STRIDE(k, cnt) {
         int v = M[k];
         const bool fr = first || freshN[root[v]];
@@ -105,27 +119,22 @@ __device__ __forceinline__ void k_round_init(int cnt, const int32_t *M, const in
             int q = atomicAdd(rcnt, 1);
             rlist[q] = v;
             posr[v] = q;
+            L[q] = (a[v] == v) ? 1 : cdist[a[v]] + 1;  // cycle length of v's community
+            bestsc[q] = LLONG_MIN;
+            bestkey[q] = ~0ull;
         }
     }
 }
 
-__device__ __forceinline__ void k_root_init(int cnt, const int32_t *Rdev, const int32_t *rlist, const int32_t *a,
-                            const int32_t *cdist, int32_t *L, long long *msz, int32_t *csz,
-                            long long *bestsc, unsigned long long *bestkey) {
+// pool sizes of the first round, padded with zeros to cnt entries so that
+// the offsets can be scanned over the member list's length
+__device__ __forceinline__ void k_root_pools(int cnt, const int32_t *Rdev, const int32_t *L,
+                                             long long *msz, int32_t *csz) {
     const int R = *Rdev;
     GRID_STRIDE(q, cnt) {
-        if (q >= R) {  // padding so that the offsets can be scanned over cnt entries
-            msz[q] = 0;
-            csz[q] = 0;
-            continue;
-        }
-        int r = rlist[q];
-        int l = (a[r] == r) ? 1 : cdist[a[r]] + 1;
-        L[q] = l;
+        const int l = q < R ? L[q] : 0;
         msz[q] = l >= 2 ? (long long)l * l : 0;
         csz[q] = l >= 2 ? l : 0;
-        bestsc[q] = LLONG_MIN;
-        bestkey[q] = ~0ull;
     }
 }
 
@@ -223,6 +232,29 @@ __device__ __forceinline__ void k_edges(int cnt, const int32_t *M, const int32_t
             int kx = cyc_index(ex, r, l, cdist), kj = cyc_index(ej, r, l, cdist);
             if (l >= 2 && kx >= 0 && kx < l && kj >= 0 && kj < l)
                 add64(&Mw[moffN[r] + (long long)kx * l + kj], wv);
+        }
+    }
+}
+
+// credits of the entries of new parts after the first round: every new part
+// hangs from a self-loop, so all its entries join nodes of one tree (one warp
+// per member of a new part)
+__device__ __forceinline__ void k_edges_members(int cnt, const int32_t *M, const int32_t *root,
+                                                const int32_t *freshN, const int32_t *istart,
+                                                const int32_t *ideg, const int32_t *col,
+                                                const int32_t *w, const int32_t *a,
+                                                const uint8_t *oncycle, const int32_t *depth,
+                                                long long *credit) {
+    const int lane = threadIdx.x & 31;
+    auto sel = [&](long long k) { return freshN[root[M[k]]] != 0; };
+    WARP_SELECTED(k, cnt, sel) {
+        const int x = M[k], r = root[x];
+        const int b = istart[x], end = b + ideg[x];
+        for (int t = b + lane; t < end; t += 32) {
+            const int j = col[t];
+            if (root[j] != r) continue;
+            const int l = lca_walk(x, j, a, depth);
+            if (!oncycle[l]) add64(&credit[l], w[t]);
         }
     }
 }
@@ -465,15 +497,18 @@ __device__ __forceinline__ void k_cut_fix(int cnt, const int32_t *M, const int32
         add64(&TS[y], -cS);
     }
     const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long k = warp; k < cnt; k += nw) {
-        if (!recomp[k]) continue;
+    // x is in a cut subtree: its part is new, its old community had a branch
+    // cut, and x no longer carries the old name
+    auto sel = [&](long long k) {
+        if (!recomp[k]) return false;
+        const int r = oldroot[k];
+        return cut[posr[r]].x == 0 && root[M[k]] != r;
+    };
+    WARP_SELECTED(k, cnt, sel) {
         const int r = oldroot[k];
         const int q = posr[r];
         const int4 ct = cut[q];
         const int x = M[k];
-        if (ct.x != 0 || root[x] == r) continue;  // x is not in a cut subtree
         const int e = ct.w, p = cutpar[q];
         const int l = (a[r] == r) ? 1 : cdist[a[r]] + 1;  // R keeps A's cycle
         const int ke = cyc_index(e, r, l, cdist);
@@ -526,10 +561,8 @@ __device__ __forceinline__ void k_own_members(int cnt, const int32_t *M, const u
                                               const int32_t *col, const int32_t *w,
                                               const int32_t *root, long long *kacc) {
     const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long k = warp; k < cnt; k += nw) {
-        if (!recomp[k]) continue;
+    auto sel = [&](long long k) { return recomp[k] != 0; };
+    WARP_SELECTED(k, cnt, sel) {
         const int x = M[k], rx = root[x];
         const int b = istart[x], end = b + ideg[x];
         long long acc = 0;
@@ -623,6 +656,13 @@ constexpr int kPosThreads = 256;
 // barriers are much cheaper, once a round has at most this many members and
 // internal entries
 constexpr int kPosTailBlocks = 16;
+// blocks per SM of the full grid: rounds hold tens of thousands of members at
+// most, and a grid barrier costs one atomic per block, so one block per SM
+// is enough
+#ifndef SLM_POS_BLOCKS_PER_SM
+#define SLM_POS_BLOCKS_PER_SM 1
+#endif
+constexpr int kPosBlocksPerSM = SLM_POS_BLOCKS_PER_SM;
 constexpr int kPosTailMembers = 8192;
 constexpr long long kPosTailEntries = 65536;
 
@@ -871,7 +911,7 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
     for (;;) {
         if (rank0) C->cnt = cnt;
         if (cnt == 0) break;
-        if (A.handoff_cnt > 0 && cnt <= A.handoff_cnt && C->E <= A.handoff_edges) {
+        if (A.handoff_cnt > 0 && cnt <= A.handoff_cnt && (!first || C->E <= A.handoff_edges)) {
             if (rank0) {
                 C->handoff = 1;
                 C->list_b = (M == A.listB) ? 1 : 0;
@@ -883,24 +923,20 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
             break;
         }
         if (rank0) C->nextc[parity] = 0;
-        k_round_init(cnt, M, A.ideg, A.root, A.freshN, first, A.subS, A.subWA, A.subWin, A.credit,
-                     A.TS, A.rlist, &C->R, A.posr, A.epref, A.kacc);
-        GBAR_OR_RETURN();
-        k_root_init(cnt, &C->R, A.rlist, A.a, A.cdist, A.L, A.msz, A.coff, A.bestsc, A.bestkey);
+        k_round_init(cnt, M, A.ideg, A.root, A.freshN, first, A.a, A.cdist, A.subS, A.subWA, A.subWin,
+                     A.credit, A.TS, A.rlist, &C->R, A.posr, A.L, A.epref, A.kacc, A.bestsc,
+                     A.bestkey);
         GBAR_OR_RETURN();
         mark_phase(0);
         if (first) {
             // the cycles of every community are laid out once per call: cuts
             // never make a cycle longer, and a part that loses its cycle gets
             // a self-loop, so the layout stays valid for the remainders
+            k_root_pools(cnt, &C->R, A.L, A.msz, A.coff);
+            GBAR_OR_RETURN();
             ScanSlots S{A.msz, A.coff, A.epref, &C->mtot, &C->ctot, &C->E, A.bs64, A.bs32a, A.bs32b};
             if (!grid_scan(S, cnt, A.bar, A.barrier_ns)) return;
-        } else {
-            ScanSlots S{nullptr, A.epref, nullptr, nullptr, &C->E, nullptr, nullptr, A.bs32a, nullptr};
-            if (!grid_scan(S, cnt, A.bar, A.barrier_ns)) return;
-        }
-        mark_phase(1);
-        if (first) {
+            mark_phase(1);
             if (C->mtot > A.pool_cap || C->ctot > A.cyc_cap) {
                 if (rank0) C->error = 2;
                 break;
@@ -915,13 +951,18 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
             GRID_STRIDE(k, mtot) A.Mw[k] = 0;
             GRID_STRIDE(k, ctot) A.cyc[k] = -1;
             GBAR_OR_RETURN();
+            k_walk(cnt, M, A.a, A.depth, A.s, A.kown, A.root, A.freshN, true, A.subS, A.subWA, A.TS);
+            if (ctot > 0)
+                k_cycle_order(cnt, M, A.oncycle, A.root, A.posr, A.L, A.cdist, A.coffN, A.cyc);
+            k_edges(cnt, M, A.epref, &C->E, A.istart, A.icol, A.iw, A.a, A.oncycle, A.entry, A.depth,
+                    A.root, A.posr, A.L, A.cdist, A.moffN, A.Mw, A.credit);
+        } else {
+            // later rounds: only the parts cut off in the last round are new
+            k_walk(cnt, M, A.a, A.depth, A.s, A.kown, A.root, A.freshN, false, A.subS, A.subWA, A.TS);
+            k_edges_members(cnt, M, A.root, A.freshN, A.istart, A.ideg, A.icol, A.iw, A.a, A.oncycle,
+                            A.depth, A.credit);
         }
         const bool cycles = C->ctot > 0;
-        k_walk(cnt, M, A.a, A.depth, A.s, A.kown, A.root, A.freshN, first, A.subS, A.subWA, A.TS);
-        if (first && cycles)
-            k_cycle_order(cnt, M, A.oncycle, A.root, A.posr, A.L, A.cdist, A.coffN, A.cyc);
-        k_edges(cnt, M, A.epref, &C->E, A.istart, A.icol, A.iw, A.a, A.oncycle, A.entry, A.depth, A.root,
-                A.posr, A.L, A.cdist, A.moffN, A.Mw, A.credit);
         GBAR_OR_RETURN();
         mark_phase(2);
         k_credit(cnt, M, A.a, A.depth, A.root, A.freshN, first, A.credit, A.subWin);
@@ -1095,7 +1136,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     SLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_positive_rounds, kPosThreads, 0));
     if (per_sm < 1) fail(SLM_ERR_CUDA, "POSITIVE kernel cannot be resident");
-    const int nblocks_full = sms * std::min(per_sm, 4);
+    const int nblocks_full = sms * std::min(per_sm, kPosBlocksPerSM);
     ps.bs.ensure(8 * (size_t)nblocks_full * 3, st);
     ps.ctrl.ensure(sizeof(PosCtrl), st);
     PosCtrl hc{};
