@@ -259,7 +259,7 @@ def run_forest(args):
             "config": {"workload": "forest_sbm_4096", "desc": FOREST_DESC, "graphs": G,
                        "nodes": int(goff[-1]), "nnz": int(rp[-1]), "batch_levels": levels,
                        "batch_sweeps": sweeps,
-                       "l2": "inputs larger than L2 (CSR %.0f MB)" % ((8 * rp[-1] + 4 * goff[-1]) / 1e6)},
+                       "l2": "inputs larger than L2 (CSR %.0f MB)" % ((8 * int(rp[-1]) + 4 * int(goff[-1])) / 1e6)},
             "per_graph_loop": {"value": loop_gps, "unit": "graphs/s",
                                "sample": f"slm_run on every 16th graph ({len(sample)} graphs), "
                                          "host CSR in, labels out",

@@ -11,6 +11,8 @@ struct Work {
     int32_t n = 0;
     DevBuf a, sigma, best, kown, tgt, acclist, gain, bg, counters;
     DevBuf root, oncycle, entry, depth, cdist, jmpA, jmpB;
+    DevBuf prev_root;  // community names after the last POSITIVE
+    DevBuf alist, amark, ascratch, atot;  // nodes of the communities a write touched
     DevBuf bs_i32, bs_i64;
     slm::Forest f;
     slm::BranchScratch bs{};
@@ -30,6 +32,8 @@ struct Work {
         bg.ensure(8 * N, st);
         counters.ensure(64, st);
         root.ensure(4 * N, st);
+        prev_root.ensure(4 * N, st);
+        alist.ensure(4 * N, st);
         oncycle.ensure(N, st);
         entry.ensure(4 * N, st);
         depth.ensure(4 * N, st);

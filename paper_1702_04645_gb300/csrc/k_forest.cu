@@ -26,43 +26,51 @@ constexpr unsigned FULL = 0xffffffffu;
 // ---------------------------------------------------------------------------
 // Components
 // ---------------------------------------------------------------------------
-__global__ void k_jump_init(int32_t n, const int32_t *a, int2 *J) {
-    GRID_STRIDE(v, n) J[v] = make_int2(a[v], (int)v);
+// Every kernel of COMPONENTS runs over all n nodes (list == nullptr) or over
+// the n nodes listed, a set closed under a (their paths never leave it).
+#define NODE_LOOP(v, n, list)            \
+    GRID_STRIDE(_k, n)                   \
+    for (long long v = list ? list[_k] : _k, _o = 1; _o; _o = 0)
+
+__global__ void k_jump_init(int32_t n, const int32_t *list, const int32_t *a, int2 *J) {
+    NODE_LOOP(v, n, list) J[v] = make_int2(a[v], (int)v);
 }
 // (next, min) <- (next(next), min(min, min(next)))
-__global__ void k_jump_round(int32_t n, const int2 *in, int2 *out) {
-    GRID_STRIDE(v, n) {
+__global__ void k_jump_round(int32_t n, const int32_t *list, const int2 *in, int2 *out) {
+    NODE_LOOP(v, n, list) {
         int2 x = in[v];
         int2 y = in[x.x];
         out[v] = make_int2(y.x, min(x.y, y.y));
     }
 }
-__global__ void k_root_final(int32_t n, const int2 *J, int32_t *root, uint8_t *oncycle) {
-    GRID_STRIDE(v, n) {
+__global__ void k_root_final(int32_t n, const int32_t *list, const int2 *J, int32_t *root,
+                             uint8_t *oncycle) {
+    NODE_LOOP(v, n, list) {
         int c = J[v].x;  // a^(2^K)(v): on the cycle because 2^K >= n
         root[v] = J[c].y;  // minimum over 2^K >= L consecutive cycle nodes
         oncycle[c] = 1;    // a^(2^K) permutes the cycle nodes
     }
 }
-__global__ void k_dist_init(int32_t n, const int32_t *a, const int32_t *root,
+__global__ void k_dist_init(int32_t n, const int32_t *list, const int32_t *a, const int32_t *root,
                             const uint8_t *oncycle, int2 *D) {
-    GRID_STRIDE(v, n) {
+    NODE_LOOP(v, n, list) {
         if (oncycle[v] && root[v] == v) D[v] = make_int2((int)v, 0);
         else D[v] = make_int2(a[v], 1);
     }
 }
 // tree nodes stop at their entry; cycle nodes stop at the community's name
-__global__ void k_dist_round(int32_t n, const int2 *in, int2 *out, const uint8_t *oncycle) {
-    GRID_STRIDE(v, n) {
+__global__ void k_dist_round(int32_t n, const int32_t *list, const int2 *in, int2 *out,
+                             const uint8_t *oncycle) {
+    NODE_LOOP(v, n, list) {
         int2 x = in[v];
         if (!oncycle[v] && oncycle[x.x]) { out[v] = x; continue; }
         int2 y = in[x.x];
         out[v] = make_int2(y.x, x.y + y.y);
     }
 }
-__global__ void k_dist_final(int32_t n, const int2 *D, const uint8_t *oncycle, int32_t *entry,
-                             int32_t *depth, int32_t *cdist) {
-    GRID_STRIDE(v, n) {
+__global__ void k_dist_final(int32_t n, const int32_t *list, const int2 *D, const uint8_t *oncycle,
+                             int32_t *entry, int32_t *depth, int32_t *cdist) {
+    NODE_LOOP(v, n, list) {
         int2 d = D[v];
         if (oncycle[v]) { entry[v] = (int)v; depth[v] = 0; cdist[v] = d.y; }
         else { entry[v] = d.x; depth[v] = d.y; cdist[v] = 0; }
@@ -286,32 +294,55 @@ static int jump_rounds(int32_t n) {
     return K;
 }
 
-void forest_analyse(int32_t n, const int32_t *a, Forest &f, cudaStream_t st) {
-    if (n <= 0) return;
-    const int K = jump_rounds(n);
-    const int g = grid_for(n, 256);
-    k_jump_init<<<g, 256, 0, st>>>(n, a, f.jmpA);
+namespace {
+__global__ void k_clear_oncycle(int32_t n, const int32_t *list, uint8_t *oncycle) {
+    NODE_LOOP(v, n, list) oncycle[v] = 0;
+}
+}  // namespace
+
+static void forest_pass(int32_t cnt, const int32_t *list, const int32_t *a, Forest &f,
+                        cudaStream_t st) {
+    // 2^K >= cnt jumps reach the cycle from any listed node and cover its cycle
+    const int K = jump_rounds(cnt);
+    const int g = grid_for(cnt, 256);
+    k_jump_init<<<g, 256, 0, st>>>(cnt, list, a, f.jmpA);
     SLM_LAUNCH_CHECK();
     int2 *cur = f.jmpA, *nxt = f.jmpB;
     for (int k = 0; k < K; k++) {
-        k_jump_round<<<g, 256, 0, st>>>(n, cur, nxt);
+        k_jump_round<<<g, 256, 0, st>>>(cnt, list, cur, nxt);
         SLM_LAUNCH_CHECK();
         std::swap(cur, nxt);
     }
-    SLM_CUDA(cudaMemsetAsync(f.oncycle, 0, n, st));
-    k_root_final<<<g, 256, 0, st>>>(n, cur, f.root, f.oncycle);
+    if (list) {
+        k_clear_oncycle<<<g, 256, 0, st>>>(cnt, list, f.oncycle);
+        SLM_LAUNCH_CHECK();
+    } else {
+        SLM_CUDA(cudaMemsetAsync(f.oncycle, 0, cnt, st));
+    }
+    k_root_final<<<g, 256, 0, st>>>(cnt, list, cur, f.root, f.oncycle);
     SLM_LAUNCH_CHECK();
-    k_dist_init<<<g, 256, 0, st>>>(n, a, f.root, f.oncycle, f.jmpA);
+    k_dist_init<<<g, 256, 0, st>>>(cnt, list, a, f.root, f.oncycle, f.jmpA);
     SLM_LAUNCH_CHECK();
     cur = f.jmpA;
     nxt = f.jmpB;
     for (int k = 0; k < K; k++) {
-        k_dist_round<<<g, 256, 0, st>>>(n, cur, nxt, f.oncycle);
+        k_dist_round<<<g, 256, 0, st>>>(cnt, list, cur, nxt, f.oncycle);
         SLM_LAUNCH_CHECK();
         std::swap(cur, nxt);
     }
-    k_dist_final<<<g, 256, 0, st>>>(n, cur, f.oncycle, f.entry, f.depth, f.cdist);
+    k_dist_final<<<g, 256, 0, st>>>(cnt, list, cur, f.oncycle, f.entry, f.depth, f.cdist);
     SLM_LAUNCH_CHECK();
+}
+
+void forest_analyse(int32_t n, const int32_t *a, Forest &f, cudaStream_t st) {
+    if (n <= 0) return;
+    forest_pass(n, nullptr, a, f, st);
+}
+
+void forest_analyse_subset(int32_t cnt, const int32_t *list, const int32_t *a, Forest &f,
+                           cudaStream_t st) {
+    if (cnt <= 0) return;
+    forest_pass(cnt, list, a, f, st);
 }
 
 void branch_gains(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,

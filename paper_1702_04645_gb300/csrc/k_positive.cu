@@ -1020,6 +1020,89 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
     }
 }
 
+// Communities a synchronous write touched: the old community and the target
+// community of every accepted node.
+__global__ void k_mark_moved(const int32_t *acc, const int32_t *acc_cnt, const int32_t *root,
+                             const int32_t *best, int32_t *mark) {
+    const int c = *acc_cnt;
+    GRID_STRIDE(k, c) {
+        const int i = acc[k];
+        mark[root[i]] = 1;
+        mark[best[i]] = 1;
+    }
+}
+
+// Communities whose membership changed since the last POSITIVE: a node whose
+// name changed marks its new and its old name (the old name, when it is
+// still in use, is the community that lost it).
+__global__ void k_dirty(int32_t n, const int32_t *root, const int32_t *prev_root, int32_t *dirty) {
+    GRID_STRIDE(v, n) {
+        const int r = root[v], p = prev_root[v];
+        if (r != p) {
+            dirty[r] = 1;
+            dirty[p] = 1;
+        }
+    }
+}
+
+// Own weight and local gain of listed nodes (one warp per node; rows longer
+// than kOwnWarpMaxDeg are left to k_own_listed_big): flag[root] = 1 when the
+// local gain is negative.
+constexpr int kOwnWarpMaxDeg = 8192;
+__global__ void k_own_listed(int cnt, const int32_t *list, const int32_t *rp, const int32_t *col,
+                             const int32_t *w, const int32_t *s, MParam mp, const int32_t *root,
+                             const int32_t *sigma, int32_t *kown, int32_t *flag) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = warp; k < cnt; k += nw) {
+        const int x = list[k];
+        const int b = rp[x], e = rp[x + 1];
+        if (e - b > kOwnWarpMaxDeg) continue;
+        const int rx = root[x];
+        long long acc = 0;
+        for (int t = b + lane; t < e; t += 32) {
+            const int j = col[t];
+            if (j != x && root[j] == rx) acc += w[t];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            kown[x] = (int32_t)acc;
+            const long long m = mp.of(x), si = s[x];
+            if (m * acc - si * ((long long)sigma[rx] - si) < 0) flag[rx] = 1;
+        }
+    }
+}
+__global__ void k_own_listed_big(int cnt, const int32_t *list, const int32_t *rp, const int32_t *col,
+                                 const int32_t *w, const int32_t *s, MParam mp, const int32_t *root,
+                                 const int32_t *sigma, int32_t *kown, int32_t *flag) {
+    __shared__ long long red[32];
+    for (long long k = blockIdx.x; k < cnt; k += gridDim.x) {
+        const int x = list[k];
+        const int b = rp[x], e = rp[x + 1];
+        if (e - b <= kOwnWarpMaxDeg) continue;  // uniform over the block
+        const int rx = root[x];
+        long long acc = 0;
+        for (int t = b + threadIdx.x; t < e; t += blockDim.x) {
+            const int j = col[t];
+            if (j != x && root[j] == rx) acc += w[t];
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long t = 0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += red[q];
+            kown[x] = (int32_t)t;
+            const long long m = mp.of(x), si = s[x];
+            if (m * t - si * ((long long)sigma[rx] - si) < 0) flag[rx] = 1;
+        }
+        __syncthreads();
+    }
+}
+
 // bound of the pools: cycle lengths never grow during POSITIVE
 __global__ void k_pool_bound(int cnt, const int32_t *M, const int32_t *root, const int32_t *a,
                              const int32_t *cdist, unsigned long long *msum,
@@ -1039,9 +1122,9 @@ __global__ void k_pool_bound(int cnt, const int32_t *M, const int32_t *root, con
 
 // Member list of the flagged communities: from all nodes (list == nullptr) or
 // from a previous list; returns its length (host-synchronous).
-static int32_t compact_members(long long cnt, const int32_t *list, const int32_t *root,
-                               const int32_t *flag, int32_t *out, DevBuf &mark, DevBuf &tot,
-                               cudaStream_t st) {
+int32_t compact_members(long long cnt, const int32_t *list, const int32_t *root,
+                        const int32_t *flag, int32_t *out, DevBuf &mark, DevBuf &tot,
+                        cudaStream_t st) {
     if (cnt <= 0) return 0;
     mark.ensure(4 * (size_t)cnt, st);
     const int g = grid_for(cnt, 256);
@@ -1056,11 +1139,24 @@ static int32_t compact_members(long long cnt, const int32_t *list, const int32_t
     return h;
 }
 
+int32_t moved_members(int32_t n, const int32_t *acc, const int32_t *acc_cnt, int32_t max_acc,
+                      const int32_t *root, const int32_t *best, int32_t *out, DevBuf &mark,
+                      DevBuf &scratch, DevBuf &tot, cudaStream_t st) {
+    if (n <= 0) return 0;
+    mark.ensure(4 * ((size_t)n + 1), st);
+    tot.ensure(16, st);
+    SLM_CUDA(cudaMemsetAsync(mark.get(), 0, 4 * (size_t)n, st));
+    k_mark_moved<<<grid_for(max_acc > 0 ? max_acc : 1, 256), 256, 0, st>>>(acc, acc_cnt, root, best,
+                                                                         mark.as<int32_t>());
+    SLM_LAUNCH_CHECK();
+    return compact_members(n, nullptr, root, mark.as<int32_t>(), out, scratch, tot, st);
+}
+
 long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                            const int32_t *s, MParam m, int32_t *a, Forest &f, int32_t *sigma,
                            const Buckets &bk, PositiveScratch &ps, cudaStream_t st,
                            long long *rounds_out, long long *visits_out,
-                           int32_t *splits_per_graph) {
+                           int32_t *splits_per_graph, const int32_t *prev_root) {
     if (rounds_out) *rounds_out = 0;
     if (visits_out) *visits_out = 0;
     if (n <= 0) return 0;
@@ -1075,12 +1171,34 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     int32_t *flag = ps.flag.as<int32_t>(), *kown = ps.kown.as<int32_t>();
     int32_t *rcnt = ps.cnt.as<int32_t>();
 
-    // local gains of every node for the current forest
+    // local gains for the current forest
     community_sigma(n, f.root, s, sigma, st);
     SLM_CUDA(cudaMemsetAsync(flag, 0, 4 * N, st));
-    own_weight_nodes(n, rp, col, w, s, m, f.root, sigma, bk, kown, flag, st);
     int32_t *M = ps.listA.as<int32_t>(), *M2 = ps.listB.as<int32_t>();
-    int32_t cnt = compact_members(n, nullptr, f.root, flag, M, ps.mark, ps.tot, st);
+    int32_t cnt = 0;
+    int32_t nd = n;
+    if (prev_root) {
+        // every community was left without a negative local gain by the last
+        // POSITIVE; only those whose membership changed since can hold one
+        ps.dirty.ensure(4 * (N + 1), st);
+        SLM_CUDA(cudaMemsetAsync(ps.dirty.get(), 0, 4 * N, st));
+        k_dirty<<<grid_for(n, 256), 256, 0, st>>>(n, f.root, prev_root, ps.dirty.as<int32_t>());
+        SLM_LAUNCH_CHECK();
+        nd = compact_members(n, nullptr, f.root, ps.dirty.as<int32_t>(), M2, ps.mark, ps.tot, st);
+        if (nd == 0) return 0;
+    }
+    if (nd * 4LL > n) {
+        own_weight_nodes(n, rp, col, w, s, m, f.root, sigma, bk, kown, flag, st);
+        cnt = compact_members(n, nullptr, f.root, flag, M, ps.mark, ps.tot, st);
+    } else {
+        k_own_listed<<<grid_for((long long)nd * 32, 256), 256, 0, st>>>(nd, M2, rp, col, w, s, m, f.root,
+                                                                       sigma, kown, flag);
+        SLM_LAUNCH_CHECK();
+        k_own_listed_big<<<grid_for(nd, 1, kNumSMs * 4), 256, 0, st>>>(nd, M2, rp, col, w, s, m, f.root,
+                                                                       sigma, kown, flag);
+        SLM_LAUNCH_CHECK();
+        cnt = compact_members(nd, M2, f.root, flag, M, ps.mark, ps.tot, st);
+    }
 
     if (cnt == 0) return 0;
     long long *subS = ps.subS.as<long long>(), *subWA = ps.subWA.as<long long>(),

@@ -409,16 +409,31 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks
         const int cap = 1 << lg;
         int *keys = tkeys + hoff[ch.x], *vals = tvals + hoff[ch.x];
         int *ul = ulist + uoff[ch.x];
-        for (int p = ch.y + threadIdx.x; p < ch.z; p += blockDim.x) {
-            int j = col[p];
-            if (j == i) continue;
-            int cc = root[j], wv = w[p];
-            unsigned h = hash_slot(cc, lg);
-            for (;;) {
-                int prev = atomicCAS(&keys[h], -1, cc);
-                if (prev == -1) ul[atomicAdd(&ucnt[ch.x], 1)] = (int)h;  // list the claimed slot
-                if (prev == -1 || prev == cc) { atomicAdd(&vals[h], wv); break; }
-                h = (h + 1) & (cap - 1);
+        // the row's chunk is covered in whole warps so that the claimed slots
+        // of a warp are listed with one atomic on the hub's count
+        for (int p0 = ch.y + (threadIdx.x & ~31); p0 < ch.z; p0 += blockDim.x) {
+            const int p = p0 + (threadIdx.x & 31);
+            int claimed = -1;
+            if (p < ch.z) {
+                const int j = col[p];
+                if (j != i) {
+                    const int cc = root[j], wv = w[p];
+                    unsigned h = hash_slot(cc, lg);
+                    for (;;) {
+                        int prev = atomicCAS(&keys[h], -1, cc);
+                        if (prev == -1) claimed = (int)h;
+                        if (prev == -1 || prev == cc) { atomicAdd(&vals[h], wv); break; }
+                        h = (h + 1) & (cap - 1);
+                    }
+                }
+            }
+            const unsigned bal = __ballot_sync(FULL, claimed >= 0);
+            if (bal) {
+                const int lane = threadIdx.x & 31;
+                int at = 0;
+                if (lane == 0) at = atomicAdd(&ucnt[ch.x], __popc(bal));
+                at = __shfl_sync(FULL, at, 0);
+                if (claimed >= 0) ul[at + __popc(bal & ((1u << lane) - 1u))] = claimed;
             }
         }
     }

@@ -124,12 +124,13 @@ __global__ void k_fill_ones(long long n, int32_t *p) {
 // POSITIVE until no community holds a node with a negative local gain.
 long long positive_all(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                        const int32_t *s, long long m, Work &W, cudaStream_t st,
-                       PhaseTimer *tm = nullptr) {
+                       PhaseTimer *tm = nullptr, bool since_last = false) {
     if (tm) tm->start();
     long long rounds = 0, visits = 0;
     long long splits = slm::positive_correct(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f,
                                              W.sigma.as<int32_t>(), W.bk, W.ps, st, &rounds,
-                                             &visits);
+                                             &visits, nullptr,
+                                             since_last ? W.prev_root.as<int32_t>() : nullptr);
     if (tm) {
         tm->stop(kPhPositive);
         tm->ms[kPhPosRounds] += (double)visits;
@@ -260,9 +261,20 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
             stt.moves += c.acc;
             if (c.acc > 0) {
                 if (tm) tm->start();
-                slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
+                // names before the moves: the next POSITIVE examines only the
+                // communities whose membership the moves changed
+                SLM_CUDA(cudaMemcpyAsync(W.prev_root.get(), W.f.root, 4 * (size_t)n,
+                                         cudaMemcpyDeviceToDevice, st));
+                // only the communities the write touched change: their nodes
+                // form a set closed under the new assignments
+                const int32_t na = slm::moved_members(
+                    n, W.acclist.as<int32_t>(), reinterpret_cast<int32_t *>(W.ctr() + 2), (int32_t)c.acc,
+                    W.f.root, W.best.as<int32_t>(), W.alist.as<int32_t>(), W.amark, W.ascratch, W.atot, st);
+                if (2LL * na > n) slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
+                else slm::forest_analyse_subset(na, W.alist.as<int32_t>(), W.a.as<int32_t>(), W.f, st);
                 if (tm) tm->stop(kPhComponents);
-                if (!(opt.flags & SLM_FLAG_NO_POSITIVE)) spl = positive_all(n, rp, col, w, s, m, W, st, tm);
+                if (!(opt.flags & SLM_FLAG_NO_POSITIVE))
+                    spl = positive_all(n, rp, col, w, s, m, W, st, tm, true);
                 stt.splits += spl;
             }
             g->trace.push_back({t, sweep, c.cand, c.pos, c.acc, spl});

@@ -224,10 +224,19 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
                              W.best.as<int32_t>(), W.tgt.as<int32_t>(), st);
                 apply_moves(W.acclist.as<int32_t>(), acc_cnt, nacc, W.tgt.as<int32_t>(),
                             W.a.as<int32_t>(), st);
-                forest_analyse(n, W.a.as<int32_t>(), W.f, st);
+                // as in slm_run: the components change only in the communities
+                // the write touched, and only those can hold a negative local gain
+                SLM_CUDA(cudaMemcpyAsync(W.prev_root.get(), W.f.root, 4 * (size_t)n,
+                                         cudaMemcpyDeviceToDevice, st));
+                const int32_t na = moved_members(n, W.acclist.as<int32_t>(), acc_cnt, nacc, W.f.root,
+                                                 W.best.as<int32_t>(), W.alist.as<int32_t>(), W.amark,
+                                                 W.ascratch, W.atot, st);
+                if (2LL * na > n) forest_analyse(n, W.a.as<int32_t>(), W.f, st);
+                else forest_analyse_subset(na, W.alist.as<int32_t>(), W.a.as<int32_t>(), W.f, st);
                 if (!(opt.flags & SLM_FLAG_NO_POSITIVE))
                     positive_correct(n, rp, col, w, s, mp, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
-                                     W.bk, W.ps, st, &rounds, &visits, spl_d.as<int32_t>());
+                                     W.bk, W.ps, st, &rounds, &visits, spl_d.as<int32_t>(),
+                                     W.prev_root.as<int32_t>());
             }
             if (sweep + 1 == opt.max_sweeps)
                 for (int g = 0; g < G; g++)

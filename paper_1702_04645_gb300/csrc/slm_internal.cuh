@@ -315,6 +315,11 @@ struct Forest {
 };
 // Components, cycle flags, entry, depth and cycle distances of a.
 void forest_analyse(int32_t n, const int32_t *a, Forest &f, cudaStream_t st);
+// The same for the cnt listed nodes only: the list must be closed under a
+// (the forward path of a listed node stays in the list); the other nodes'
+// values are left as they are.
+void forest_analyse_subset(int32_t cnt, const int32_t *list, const int32_t *a, Forest &f,
+                           cudaStream_t st);
 
 struct BranchScratch {
     int32_t *haschild, *active, *covered, *treeact, *commcyc;
@@ -348,6 +353,7 @@ struct PositiveScratch {
         bestsc, bestkey, pool, cyc, cnt, mark, tot, hdr, epref, kacc, cut, nf, noc, bs, ctrl;
     DevBuf icnt, ioff, istart, ideg, icol, iw;  // internal entries of the members
     DevBuf recomp, moffN, cutsum, coffN, freshN, cutpar, oldroot;  // incremental rounds
+    DevBuf dirty;  // communities whose membership changed since the last call
     bool profile = false;              // stamp the phases of every round
     long long prof_ns[kPosPhases] = {};  // summed nanoseconds per phase
 };
@@ -357,11 +363,29 @@ struct PositiveScratch {
 // *rounds_out gets the number of rounds and *visits_out the member visits
 // summed over the rounds.
 // With a forest, splits_per_graph (int32[G], may be null) counts each graph's splits.
+// prev_root (may be null): the names after the last POSITIVE on this state;
+// when given, only communities whose membership changed since are examined
+// (the others cannot hold a negative local gain).
 long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                            const int32_t *s, MParam m, int32_t *a, Forest &f, int32_t *sigma,
                            const Buckets &bk, PositiveScratch &ps, cudaStream_t st,
                            long long *rounds_out, long long *visits_out,
-                           int32_t *splits_per_graph = nullptr);
+                           int32_t *splits_per_graph = nullptr,
+                           const int32_t *prev_root = nullptr);
+
+// Nodes (listed in node order) of the communities flagged in flag[name],
+// taken from the cnt listed nodes (list == nullptr: every node); returns the
+// count (host-synchronous).  mark and tot are scratch.
+int32_t compact_members(long long cnt, const int32_t *list, const int32_t *root,
+                        const int32_t *flag, int32_t *out, DevBuf &mark, DevBuf &tot,
+                        cudaStream_t st);
+// Nodes of the communities that the last synchronous write touched (the old
+// and the target community of every accepted node, names of `root` before
+// the components are updated): a set closed under the new assignments.
+// Returns the count (host-synchronous).
+int32_t moved_members(int32_t n, const int32_t *acc, const int32_t *acc_cnt, int32_t max_acc,
+                      const int32_t *root, const int32_t *best, int32_t *out, DevBuf &mark,
+                      DevBuf &scratch, DevBuf &tot, cudaStream_t st);
 
 // Self-check of the time-limited grid barrier of the cooperative kernels:
 // `blocks` resident blocks pass three barriers; block `absent` (>= 0) leaves
