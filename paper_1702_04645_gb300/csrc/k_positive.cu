@@ -1187,7 +1187,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
         nd = compact_members(n, nullptr, f.root, ps.dirty.as<int32_t>(), M2, ps.mark, ps.tot, st);
         if (nd == 0) return 0;
     }
-    if (nd * 4LL > n) {
+    if (nd * 16LL > n) {  // most of the graph: the bucketed full pass is cheaper
         own_weight_nodes(n, rp, col, w, s, m, f.root, sigma, bk, kown, flag, st);
         cnt = compact_members(n, nullptr, f.root, flag, M, ps.mark, ps.tot, st);
     } else {

@@ -85,16 +85,18 @@ __device__ __forceinline__ void count_add(unsigned long long *ctr, unsigned v) {
 // ---------------------------------------------------------------------------
 // Buckets
 // ---------------------------------------------------------------------------
-__global__ void k_bucket_keys(int32_t n, const int32_t *rp, uint32_t *keys, int32_t *vals,
-                              int32_t *counts) {
+// bucket keys of all n nodes (list == nullptr) or of the n listed nodes
+__global__ void k_bucket_keys(int32_t n, const int32_t *list, const int32_t *rp, uint32_t *keys,
+                              int32_t *vals, int32_t *counts) {
     __shared__ int loc[kNumBuckets];
     if (threadIdx.x < kNumBuckets) loc[threadIdx.x] = 0;
     __syncthreads();
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int v = list ? list[k] : (int)k;
         int b = bucket_of(rp[v + 1] - rp[v]);
-        keys[v] = (uint32_t)b;
-        vals[v] = (int32_t)v;
+        keys[k] = (uint32_t)b;
+        vals[k] = v;
         atomicAdd(&loc[b], 1);
     }
     __syncthreads();
@@ -758,7 +760,9 @@ Buckets::~Buckets() {
             if (e) cudaEventDestroy(e);
 }
 
-void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
+void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) { build_list(n, nullptr, rp, s); }
+
+void Buckets::build_list(int32_t n, const int32_t *list, const int32_t *rp, cudaStream_t s) {
     if (!fork) {
         for (int k = 0; k < kSide; k++) {
             SLM_CUDA(cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking));
@@ -772,7 +776,7 @@ void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) {
     DevBuf keys(sizeof(uint32_t) * n, s), keys_tmp(sizeof(uint32_t) * n, s),
         vals_tmp(sizeof(int32_t) * n, s), counts(sizeof(int32_t) * kNumBuckets, s);
     SLM_CUDA(cudaMemsetAsync(counts.get(), 0, counts.bytes(), s));
-    k_bucket_keys<<<grid_for(n, 256), 256, 0, s>>>(n, rp, keys.as<uint32_t>(), order.as<int32_t>(),
+    k_bucket_keys<<<grid_for(n, 256), 256, 0, s>>>(n, list, rp, keys.as<uint32_t>(), order.as<int32_t>(),
                                                    counts.as<int32_t>());
     SLM_LAUNCH_CHECK();
     radix_sort_u32(keys.as<uint32_t>(), order.as<int32_t>(), keys_tmp.as<uint32_t>(),

@@ -267,14 +267,16 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
                                          cudaMemcpyDeviceToDevice, st));
                 // only the communities the write touched change: their nodes
                 // form a set closed under the new assignments
-                const int32_t na = slm::moved_members(
+                // (many moves: the touched set is most of the graph, and the
+                // full pass is cheaper than listing it)
+                const int32_t na = 16LL * c.acc > n ? n : slm::moved_members(
                     n, W.acclist.as<int32_t>(), reinterpret_cast<int32_t *>(W.ctr() + 2), (int32_t)c.acc,
                     W.f.root, W.best.as<int32_t>(), W.alist.as<int32_t>(), W.amark, W.ascratch, W.atot, st);
                 if (2LL * na > n) slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
                 else slm::forest_analyse_subset(na, W.alist.as<int32_t>(), W.a.as<int32_t>(), W.f, st);
                 if (tm) tm->stop(kPhComponents);
                 if (!(opt.flags & SLM_FLAG_NO_POSITIVE))
-                    spl = positive_all(n, rp, col, w, s, m, W, st, tm, true);
+                    spl = positive_all(n, rp, col, w, s, m, W, st, tm, 16LL * c.acc <= n);
                 stt.splits += spl;
             }
             g->trace.push_back({t, sweep, c.cand, c.pos, c.acc, spl});

@@ -166,9 +166,22 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
             sl[g].status = 2;
             sl[g].sweeps = 0;
         }
+        long long bucket_nodes = n;  // nodes the degree buckets cover
         for (int sweep = 0; sweep < opt.max_sweeps && nactive > 0; sweep++) {
             B->batch_sweeps++;
             to_device(active_d, active, st);
+            // once the graphs still running hold under half of the nodes the
+            // buckets cover, the buckets are rebuilt over their nodes only, so
+            // the scans skip the graphs that have stopped
+            long long act_nodes = 0;
+            for (int g = 0; g < G; g++)
+                if (active[g]) act_nodes += goff[g + 1] - goff[g];
+            if (2 * act_nodes < bucket_nodes) {
+                const int32_t cnt = compact_members(n, nullptr, gid_d.as<int32_t>(), active_d.as<int32_t>(),
+                                                    W.alist.as<int32_t>(), W.amark, W.atot, st);
+                W.bk.build_list(cnt, W.alist.as<int32_t>(), rp, st);
+                bucket_nodes = cnt;
+            }
             unsigned long long *ctr = W.ctr();
             SLM_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
             community_sigma(n, W.f.root, s, W.sigma.as<int32_t>(), st);
@@ -228,15 +241,16 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
                 // the write touched, and only those can hold a negative local gain
                 SLM_CUDA(cudaMemcpyAsync(W.prev_root.get(), W.f.root, 4 * (size_t)n,
                                          cudaMemcpyDeviceToDevice, st));
-                const int32_t na = moved_members(n, W.acclist.as<int32_t>(), acc_cnt, nacc, W.f.root,
-                                                 W.best.as<int32_t>(), W.alist.as<int32_t>(), W.amark,
-                                                 W.ascratch, W.atot, st);
+                const int32_t na = 16LL * nacc > n ? n
+                                   : moved_members(n, W.acclist.as<int32_t>(), acc_cnt, nacc, W.f.root,
+                                                   W.best.as<int32_t>(), W.alist.as<int32_t>(), W.amark,
+                                                   W.ascratch, W.atot, st);
                 if (2LL * na > n) forest_analyse(n, W.a.as<int32_t>(), W.f, st);
                 else forest_analyse_subset(na, W.alist.as<int32_t>(), W.a.as<int32_t>(), W.f, st);
                 if (!(opt.flags & SLM_FLAG_NO_POSITIVE))
                     positive_correct(n, rp, col, w, s, mp, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
                                      W.bk, W.ps, st, &rounds, &visits, spl_d.as<int32_t>(),
-                                     W.prev_root.as<int32_t>());
+                                     16LL * nacc <= n ? W.prev_root.as<int32_t>() : nullptr);
             }
             if (sweep + 1 == opt.max_sweeps)
                 for (int g = 0; g < G; g++)

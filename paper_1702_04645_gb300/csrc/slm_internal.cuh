@@ -265,6 +265,8 @@ struct Buckets {
     double *prof_ms = nullptr;
     cudaEvent_t pev[kNumBuckets][2] = {};
     void build(int32_t n, const int32_t *rp, cudaStream_t s);
+    // the same over the n listed nodes only (the scans then cover those nodes)
+    void build_list(int32_t n, const int32_t *list, const int32_t *rp, cudaStream_t s);
     Buckets() = default;
     Buckets(const Buckets &) = delete;
     Buckets &operator=(const Buckets &) = delete;
