@@ -32,51 +32,6 @@ constexpr unsigned FULL = 0xffffffffu;
     GRID_STRIDE(_k, n)                   \
     for (long long v = list ? list[_k] : _k, _o = 1; _o; _o = 0)
 
-__global__ void k_jump_init(int32_t n, const int32_t *list, const int32_t *a, int2 *J) {
-    NODE_LOOP(v, n, list) J[v] = make_int2(a[v], (int)v);
-}
-// (next, min) <- (next(next), min(min, min(next)))
-__global__ void k_jump_round(int32_t n, const int32_t *list, const int2 *in, int2 *out) {
-    NODE_LOOP(v, n, list) {
-        int2 x = in[v];
-        int2 y = in[x.x];
-        out[v] = make_int2(y.x, min(x.y, y.y));
-    }
-}
-__global__ void k_root_final(int32_t n, const int32_t *list, const int2 *J, int32_t *root,
-                             uint8_t *oncycle) {
-    NODE_LOOP(v, n, list) {
-        int c = J[v].x;  // a^(2^K)(v): on the cycle because 2^K >= n
-        root[v] = J[c].y;  // minimum over 2^K >= L consecutive cycle nodes
-        oncycle[c] = 1;    // a^(2^K) permutes the cycle nodes
-    }
-}
-__global__ void k_dist_init(int32_t n, const int32_t *list, const int32_t *a, const int32_t *root,
-                            const uint8_t *oncycle, int2 *D) {
-    NODE_LOOP(v, n, list) {
-        if (oncycle[v] && root[v] == v) D[v] = make_int2((int)v, 0);
-        else D[v] = make_int2(a[v], 1);
-    }
-}
-// tree nodes stop at their entry; cycle nodes stop at the community's name
-__global__ void k_dist_round(int32_t n, const int32_t *list, const int2 *in, int2 *out,
-                             const uint8_t *oncycle) {
-    NODE_LOOP(v, n, list) {
-        int2 x = in[v];
-        if (!oncycle[v] && oncycle[x.x]) { out[v] = x; continue; }
-        int2 y = in[x.x];
-        out[v] = make_int2(y.x, x.y + y.y);
-    }
-}
-__global__ void k_dist_final(int32_t n, const int32_t *list, const int2 *D, const uint8_t *oncycle,
-                             int32_t *entry, int32_t *depth, int32_t *cdist) {
-    NODE_LOOP(v, n, list) {
-        int2 d = D[v];
-        if (oncycle[v]) { entry[v] = (int)v; depth[v] = 0; cdist[v] = d.y; }
-        else { entry[v] = d.x; depth[v] = d.y; cdist[v] = 0; }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Branch gains of Algorithm MAXIMAL
 // ---------------------------------------------------------------------------
@@ -295,43 +250,113 @@ static int jump_rounds(int32_t n) {
 }
 
 namespace {
-__global__ void k_clear_oncycle(int32_t n, const int32_t *list, uint8_t *oncycle) {
-    NODE_LOOP(v, n, list) oncycle[v] = 0;
+// Every round of COMPONENTS in one launch, its phases separated by barriers
+// (block barriers for a single block, the time-limited grid barrier for a
+// cooperative grid): pointer jumping with a running minimum names every
+// component by the smallest node on its cycle and marks the cycle nodes; a
+// second jumping pass gives every node its entry (first cycle node on its
+// path) and depth, and every cycle node its forward distance to the name.
+constexpr int kForestThreads = 1024;
+constexpr int kForestOneBlock = 32768;  // listed nodes up to which one block runs them all
+
+__global__ void __launch_bounds__(kForestThreads) k_forest_rounds(
+    int32_t cnt, const int32_t *list, const int32_t *a, int2 *JA, int2 *JB, int32_t *root,
+    uint8_t *oncycle, int32_t *entry, int32_t *depth, int32_t *cdist, int K, GridBarrier *bar,
+    long long limit_ns) {
+    NODE_LOOP(v, cnt, list) JA[v] = make_int2(a[v], (int)v);
+    if (!gbar(bar, limit_ns)) return;
+    int2 *cur = JA, *nxt = JB;
+    for (int k = 0; k < K; k++) {
+        NODE_LOOP(v, cnt, list) {
+            const int2 x = cur[v];
+            const int2 y = cur[x.x];
+            nxt[v] = make_int2(y.x, min(x.y, y.y));
+        }
+        if (!gbar(bar, limit_ns)) return;
+        int2 *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    NODE_LOOP(v, cnt, list) oncycle[v] = 0;
+    if (!gbar(bar, limit_ns)) return;
+    NODE_LOOP(v, cnt, list) {
+        const int c = cur[v].x;  // a^(2^K)(v): on the cycle
+        root[v] = cur[c].y;      // minimum over 2^K >= L consecutive cycle nodes
+        oncycle[c] = 1;
+    }
+    if (!gbar(bar, limit_ns)) return;
+    // the tree nodes walk to their entry, the cycle nodes to their name; the
+    // buffer that does not hold the names' jumps takes the distances
+    int2 *D0 = (cur == JA) ? JB : JA, *D1 = cur;
+    NODE_LOOP(v, cnt, list) {
+        if (oncycle[v] && root[v] == v) D0[v] = make_int2((int)v, 0);
+        else D0[v] = make_int2(a[v], 1);
+    }
+    if (!gbar(bar, limit_ns)) return;
+    cur = D0;
+    nxt = D1;
+    for (int k = 0; k < K; k++) {
+        NODE_LOOP(v, cnt, list) {
+            const int2 x = cur[v];
+            if (!oncycle[v] && oncycle[x.x]) {
+                nxt[v] = x;
+            } else {
+                const int2 y = cur[x.x];
+                nxt[v] = make_int2(y.x, x.y + y.y);
+            }
+        }
+        if (!gbar(bar, limit_ns)) return;
+        int2 *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    NODE_LOOP(v, cnt, list) {
+        const int2 d = cur[v];
+        if (oncycle[v]) {
+            entry[v] = (int)v;
+            depth[v] = 0;
+            cdist[v] = d.y;
+        } else {
+            entry[v] = d.x;
+            depth[v] = d.y;
+            cdist[v] = 0;
+        }
+    }
 }
 }  // namespace
 
 static void forest_pass(int32_t cnt, const int32_t *list, const int32_t *a, Forest &f,
                         cudaStream_t st) {
     // 2^K >= cnt jumps reach the cycle from any listed node and cover its cycle
-    const int K = jump_rounds(cnt);
-    const int g = grid_for(cnt, 256);
-    k_jump_init<<<g, 256, 0, st>>>(cnt, list, a, f.jmpA);
-    SLM_LAUNCH_CHECK();
-    int2 *cur = f.jmpA, *nxt = f.jmpB;
-    for (int k = 0; k < K; k++) {
-        k_jump_round<<<g, 256, 0, st>>>(cnt, list, cur, nxt);
+    int K = jump_rounds(cnt);
+    DevBuf barm(sizeof(GridBarrier), st);
+    SLM_CUDA(cudaMemsetAsync(barm.get(), 0, sizeof(GridBarrier), st));
+    GridBarrier *bar = barm.as<GridBarrier>();
+    long long lim = kBarrierLimitNs;
+    if (cnt <= kForestOneBlock) {
+        // one block: block barriers only, an ordinary launch
+        k_forest_rounds<<<1, kForestThreads, 0, st>>>(cnt, list, a, f.jmpA, f.jmpB, f.root, f.oncycle,
+                                                      f.entry, f.depth, f.cdist, K, bar, lim);
         SLM_LAUNCH_CHECK();
-        std::swap(cur, nxt);
+        return;
     }
-    if (list) {
-        k_clear_oncycle<<<g, 256, 0, st>>>(cnt, list, f.oncycle);
+    int dev = 0, sms = 0, per_sm = 0;
+    SLM_CUDA(cudaGetDevice(&dev));
+    SLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forest_rounds, kForestThreads, 0));
+    if (per_sm < 1) fail(SLM_ERR_CUDA, "COMPONENTS kernel cannot be resident");
+    int nb = (int)std::min<long long>((long long)sms, (cnt + kForestThreads - 1) / kForestThreads);
+    void *kargs[] = {&cnt, (void *)&list, (void *)&a, &f.jmpA, &f.jmpB, &f.root, &f.oncycle,
+                     &f.entry, &f.depth, &f.cdist, &K, &bar, &lim};
+    serialised_cooperative(st, [&] {
+        SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_forest_rounds, dim3(nb),
+                                             dim3(kForestThreads), kargs, 0, st));
         SLM_LAUNCH_CHECK();
-    } else {
-        SLM_CUDA(cudaMemsetAsync(f.oncycle, 0, cnt, st));
-    }
-    k_root_final<<<g, 256, 0, st>>>(cnt, list, cur, f.root, f.oncycle);
-    SLM_LAUNCH_CHECK();
-    k_dist_init<<<g, 256, 0, st>>>(cnt, list, a, f.root, f.oncycle, f.jmpA);
-    SLM_LAUNCH_CHECK();
-    cur = f.jmpA;
-    nxt = f.jmpB;
-    for (int k = 0; k < K; k++) {
-        k_dist_round<<<g, 256, 0, st>>>(cnt, list, cur, nxt, f.oncycle);
-        SLM_LAUNCH_CHECK();
-        std::swap(cur, nxt);
-    }
-    k_dist_final<<<g, 256, 0, st>>>(cnt, list, cur, f.oncycle, f.entry, f.depth, f.cdist);
-    SLM_LAUNCH_CHECK();
+    });
+    GridBarrier hb{};
+    SLM_CUDA(cudaMemcpyAsync(&hb, bar, sizeof hb, cudaMemcpyDeviceToHost, st));
+    stream_sync(st);
+    if (hb.failed) fail(SLM_ERR_TIMEOUT, "a COMPONENTS grid barrier waited past its time limit");
 }
 
 void forest_analyse(int32_t n, const int32_t *a, Forest &f, cudaStream_t st) {

@@ -719,54 +719,6 @@ struct ScanSlots {
     int32_t *bs_b, *bs_c;
 };
 
-__device__ __forceinline__ long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return (long long)t;
-}
-
-// Grid barrier with a time limit (the kernel is launched cooperatively, so
-// every block is resident).  One word serves every barrier of a launch:
-// block 0 adds 2^31 - (blocks - 1) and every other block adds 1, so the top
-// bit flips exactly when the last block arrives and the low bits return to
-// their value before the barrier.  Thread 0 of each block waits for the flip
-// for at most `limit_ns` of global time, then sets the failure word.  Returns
-// false once any block has failed: the caller leaves the kernel, and every
-// other block does the same at its next barrier, which is bounded the same
-// way, so the launch always ends.  A grid of one block needs the block
-// barrier only.
-struct GridBarrier {
-    unsigned word;
-    int failed;
-};
-// longest a block waits at a grid barrier before the launch is abandoned
-constexpr long long kBarrierLimitNs = 4000000000LL;
-
-__device__ __noinline__ bool gbar(GridBarrier *b, long long limit_ns) {
-    __syncthreads();
-    if (gridDim.x > 1) {
-        if (threadIdx.x == 0) {
-            const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
-            __threadfence();
-            const unsigned old = atomicAdd(&b->word, add);
-            volatile unsigned *vw = &b->word;
-            long long t0 = 0;
-            for (unsigned spin = 0; ((old ^ *vw) & 0x80000000u) == 0; spin++) {
-                if ((spin & 255u) == 0) {  // read the clock now and then
-                    const long long t = global_ns();
-                    if (t0 == 0) t0 = t;
-                    else if (t - t0 > limit_ns) {
-                        atomicExch(&b->failed, 1);
-                        break;
-                    }
-                }
-            }
-            __threadfence();
-        }
-        __syncthreads();
-    }
-    return *((volatile int *)&b->failed) == 0;
-}
 #define GBAR_OR_RETURN(r)                        \
     do {                                         \
         if (!gbar(A.bar, A.barrier_ns)) return r; \
