@@ -257,7 +257,7 @@ namespace {
 // second jumping pass gives every node its entry (first cycle node on its
 // path) and depth, and every cycle node its forward distance to the name.
 constexpr int kForestThreads = 1024;
-constexpr int kForestOneBlock = 32768;  // listed nodes up to which one block runs them all
+constexpr int kForestOneBlock = 4096;  // listed nodes up to which one block runs them all
 
 __global__ void __launch_bounds__(kForestThreads) k_forest_rounds(
     int32_t cnt, const int32_t *list, const int32_t *a, int2 *JA, int2 *JB, int32_t *root,
