@@ -90,11 +90,13 @@ __global__ void k_edges_tree(int32_t n, const int32_t *rp, const int32_t *col, c
                              long long *credit) {
     __shared__ int lst[8][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long xx = warp; xx < n; xx += nwarps) {
-        if (!covered[xx]) continue;
-        const int x = (int)xx;
+    // each warp tests 32 consecutive nodes at once and then serves the
+    // covered ones with all its lanes
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < n;
+         base += (long long)gridDim.x * blockDim.x)
+    for (unsigned sel = __ballot_sync(FULL, base + lane < n && covered[base + lane]); sel;
+         sel &= sel - 1) {
+        const int x = (int)(base + __ffs(sel) - 1);
         const int rx = root[x], ex = entry[x];
         int y = x, dleft = depth[x];
         bool first_pass = true;
@@ -152,12 +154,12 @@ __global__ void k_edges_cycle(int32_t n, const int32_t *rp, const int32_t *col, 
                               long long *WB) {
     __shared__ int lst[8][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long xx = warp; xx < n; xx += nwarps) {
-        const int x = (int)xx;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < n;
+         base += (long long)gridDim.x * blockDim.x)
+    for (unsigned sel = __ballot_sync(FULL, base + lane < n && commcyc[root[base + lane]]); sel;
+         sel &= sel - 1) {
+        const int x = (int)(base + __ffs(sel) - 1);
         const int r = root[x];
-        if (!commcyc[r]) continue;
         int c = r;
         // cycle length: the name's successor is L-1 steps from the name
         int left = (a[r] == r) ? 1 : cdist[a[r]] + 1;
