@@ -125,11 +125,14 @@ def test_scan_sampled(big):
 
 
 @pytest.fixture(scope="module")
-def runs(big):
-    name, g = big
+def runs():
+    # a whole run at full size is checked on the R-MAT graph; on the LFR-style
+    # graph the method needs many minutes (POSITIVE peels its large
+    # communities one branch at a time), beyond a test suite's budget
+    g = _rmat()
     G = slm.Graph(g.row_ptr, g.col, g.w)
     G.run(seed=1, accept_p32=slm.P_HALF)
-    return name, g, G
+    return "rmat_s20", g, G
 
 
 def test_run_properties(runs):
@@ -145,6 +148,24 @@ def test_run_properties(runs):
         assert st.status in (0, 1, 2)
     top = G.stats(-1)
     assert top.status in (0, 1) and top.n_communities == top.n
+
+
+def test_lfr_bounded_run():
+    """The LFR-style graph with at most 5 sweeps per level and 3 levels (the
+    method does not settle on it: the oracle on a 16,384-node graph of the same
+    recipe reaches the 1,000-sweep limit at level 0): the run stops at the
+    limits with consistent levels and the oracle's modularity of the GPU
+    partition."""
+    g = _lfr()
+    G = slm.Graph(g.row_ptr, g.col, g.w)
+    G.run(seed=1, accept_p32=slm.P_HALF, max_sweeps=5, max_levels=3)
+    lab, K = G.partition(-1)
+    assert lab.shape[0] == g.n and np.unique(lab).shape[0] == K
+    assert G.modularity(-1) == O.modularity(g, lab)
+    for lv in range(G.num_levels()):
+        st = G.stats(lv)
+        assert st.sweeps <= 5 and st.status in (0, 1, 2)
+    G.close()
 
 
 @pytest.mark.skipif(os.environ.get("SLM_FULL_ORACLE") != "1",
