@@ -43,7 +43,7 @@ FALLBACK_HBM = 6800.0
 # DRAM bytes (read + write) of one level-0 scan of the benchmark graph, from the
 # ncu capture summarised in profiles/scan_rmat_s20_level0.md; None once the
 # scan kernels change after that capture
-SCAN_TRAFFIC_L0 = 585.2e6
+SCAN_TRAFFIC_L0 = 599.9e6
 
 
 def scan_bytes(n: int, nnz: int) -> int:
