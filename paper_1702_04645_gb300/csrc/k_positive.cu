@@ -580,6 +580,9 @@ __device__ __forceinline__ void k_own_members(int cnt, const int32_t *M, const u
 // (j != x, same community) instead of their whole rows: hubs whose rows
 // mostly leave the community cost their internal degree only.
 // ---------------------------------------------------------------------------
+// members with longer rows are served by whole blocks (k_int_*_big)
+constexpr int kIntWarpMaxDeg = 1024;
+
 __global__ void k_int_count(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
                             const int32_t *root, int32_t *icnt) {
     const int lane = threadIdx.x & 31;
@@ -588,6 +591,7 @@ __global__ void k_int_count(int cnt, const int32_t *M, const int32_t *rp, const 
     for (long long k = warp; k < cnt; k += nw) {
         const int x = M[k], r = root[x];
         const int b = rp[x], e = rp[x + 1];
+        if (e - b > kIntWarpMaxDeg) continue;
         int c = 0;
         for (int p = b + lane; p < e; p += 32) {
             const int j = col[p];
@@ -596,6 +600,30 @@ __global__ void k_int_count(int cnt, const int32_t *M, const int32_t *rp, const 
 #pragma unroll
         for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (lane == 0) icnt[k] = c;
+    }
+}
+
+__global__ void k_int_count_big(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
+                                const int32_t *root, int32_t *icnt) {
+    __shared__ int tot;
+    for (long long k = blockIdx.x; k < cnt; k += gridDim.x) {
+        const int x = M[k];
+        const int b = rp[x], e = rp[x + 1];
+        if (e - b <= kIntWarpMaxDeg) continue;  // uniform over the block
+        const int r = root[x];
+        if (threadIdx.x == 0) tot = 0;
+        __syncthreads();
+        int c = 0;
+        for (int p = b + threadIdx.x; p < e; p += blockDim.x) {
+            const int j = col[p];
+            c += (j != x && root[j] == r) ? 1 : 0;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&tot, c);
+        __syncthreads();
+        if (threadIdx.x == 0) icnt[k] = tot;
+        __syncthreads();
     }
 }
 
@@ -609,6 +637,7 @@ __global__ void k_int_fill(int cnt, const int32_t *M, const int32_t *rp, const i
     for (long long k = warp; k < cnt; k += nw) {
         const int x = M[k], r = root[x];
         const int b = rp[x], e = rp[x + 1];
+        if (e - b > kIntWarpMaxDeg) continue;
         int out = ioff[k];
         if (lane == 0) {
             istart[x] = out;
@@ -627,6 +656,45 @@ __global__ void k_int_fill(int cnt, const int32_t *M, const int32_t *rp, const i
             }
             out += __popc(bal);
         }
+    }
+}
+
+// a long row filled by a whole block: the order of a member's internal
+// entries does not matter (every use of them is a sum or a test), so each
+// warp claims its slots with one atomic on the member's cursor
+__global__ void k_int_fill_big(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
+                               const int32_t *w, const int32_t *root, const int32_t *icnt,
+                               const int32_t *ioff, int32_t *istart, int32_t *ideg, int32_t *icol,
+                               int32_t *iw) {
+    __shared__ int cursor;
+    const int lane = threadIdx.x & 31;
+    for (long long k = blockIdx.x; k < cnt; k += gridDim.x) {
+        const int x = M[k];
+        const int b = rp[x], e = rp[x + 1];
+        if (e - b <= kIntWarpMaxDeg) continue;  // uniform over the block
+        const int r = root[x];
+        if (threadIdx.x == 0) {
+            cursor = ioff[k];
+            istart[x] = ioff[k];
+            ideg[x] = icnt[k];
+        }
+        __syncthreads();
+        for (int p0 = b + (threadIdx.x & ~31); p0 < e; p0 += blockDim.x) {
+            const int p = p0 + lane;
+            int j = -1;
+            if (p < e) j = col[p];
+            const bool in = p < e && j != x && root[j] == r;
+            const unsigned bal = __ballot_sync(0xffffffffu, in);
+            int at = 0;
+            if (lane == 0 && bal) at = atomicAdd(&cursor, __popc(bal));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (in) {
+                const int q = at + __popc(bal & ((1u << lane) - 1u));
+                icol[q] = j;
+                iw[q] = w[p];
+            }
+        }
+        __syncthreads();
     }
 }
 __device__ __forceinline__ void k_own_finish(int cnt, const int32_t *M, const int32_t *s, MParam mp,
@@ -1000,7 +1068,7 @@ __global__ void k_dirty(int32_t n, const int32_t *root, const int32_t *prev_root
 // Own weight and local gain of listed nodes (one warp per node; rows longer
 // than kOwnWarpMaxDeg are left to k_own_listed_big): flag[root] = 1 when the
 // local gain is negative.
-constexpr int kOwnWarpMaxDeg = 8192;
+constexpr int kOwnWarpMaxDeg = 1024;
 __global__ void k_own_listed(int cnt, const int32_t *list, const int32_t *rp, const int32_t *col,
                              const int32_t *w, const int32_t *s, MParam mp, const int32_t *root,
                              const int32_t *sigma, int32_t *kown, int32_t *flag) {
@@ -1183,6 +1251,9 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     k_int_count<<<grid_for((long long)cnt * 32, 256), 256, 0, st>>>(cnt, M, rp, col, f.root,
                                                                      ps.icnt.as<int32_t>());
     SLM_LAUNCH_CHECK();
+    k_int_count_big<<<grid_for(cnt, 1, kNumSMs * 4), 256, 0, st>>>(cnt, M, rp, col, f.root,
+                                                                    ps.icnt.as<int32_t>());
+    SLM_LAUNCH_CHECK();
     exclusive_scan_i32(ps.icnt.as<int32_t>(), ps.ioff.as<int32_t>(), cnt,
                        reinterpret_cast<int32_t *>(bnd + 2), st);
     unsigned long long hb[3] = {0, 0, 0};
@@ -1196,6 +1267,10 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     ps.icol.ensure(4 * (size_t)(itot > 0 ? itot : 1), st);
     ps.iw.ensure(4 * (size_t)(itot > 0 ? itot : 1), st);
     k_int_fill<<<grid_for((long long)cnt * 32, 256), 256, 0, st>>>(
+        cnt, M, rp, col, w, f.root, ps.icnt.as<int32_t>(), ps.ioff.as<int32_t>(),
+        ps.istart.as<int32_t>(), ps.ideg.as<int32_t>(), ps.icol.as<int32_t>(), ps.iw.as<int32_t>());
+    SLM_LAUNCH_CHECK();
+    k_int_fill_big<<<grid_for(cnt, 1, kNumSMs * 4), 256, 0, st>>>(
         cnt, M, rp, col, w, f.root, ps.icnt.as<int32_t>(), ps.ioff.as<int32_t>(),
         ps.istart.as<int32_t>(), ps.ideg.as<int32_t>(), ps.icol.as<int32_t>(), ps.iw.as<int32_t>());
     SLM_LAUNCH_CHECK();
