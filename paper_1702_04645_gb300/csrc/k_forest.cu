@@ -264,7 +264,7 @@ constexpr int kForestOneBlock = 4096;  // listed nodes up to which one block run
 __global__ void __launch_bounds__(kForestThreads) k_forest_rounds(
     int32_t cnt, const int32_t *list, const int32_t *a, int2 *JA, int2 *JB, int32_t *root,
     uint8_t *oncycle, int32_t *entry, int32_t *depth, int32_t *cdist, int K, GridBarrier *bar,
-    long long limit_ns) {
+    long long limit_ns, int *changed) {
     NODE_LOOP(v, cnt, list) JA[v] = make_int2(a[v], (int)v);
     if (!gbar(bar, limit_ns)) return;
     int2 *cur = JA, *nxt = JB;
@@ -297,20 +297,32 @@ __global__ void __launch_bounds__(kForestThreads) k_forest_rounds(
     if (!gbar(bar, limit_ns)) return;
     cur = D0;
     nxt = D1;
+    // this pass reaches a fixed point (tree nodes stop at their entry, cycle
+    // nodes at the name): once a round changes nothing, the later rounds
+    // would not either; changed[k] (zeroed by the host) records round k
+    __shared__ int any;
     for (int k = 0; k < K; k++) {
+        if (threadIdx.x == 0) any = 0;
+        __syncthreads();
+        int mine = 0;
         NODE_LOOP(v, cnt, list) {
             const int2 x = cur[v];
-            if (!oncycle[v] && oncycle[x.x]) {
-                nxt[v] = x;
-            } else {
+            int2 z = x;
+            if (oncycle[v] || !oncycle[x.x]) {
                 const int2 y = cur[x.x];
-                nxt[v] = make_int2(y.x, x.y + y.y);
+                z = make_int2(y.x, x.y + y.y);
             }
+            nxt[v] = z;
+            mine |= (z.x != x.x || z.y != x.y) ? 1 : 0;
         }
+        if (mine) any = 1;
+        __syncthreads();
+        if (threadIdx.x == 0 && any) atomicOr(&changed[k], 1);
         if (!gbar(bar, limit_ns)) return;
         int2 *t = cur;
         cur = nxt;
         nxt = t;
+        if (*((volatile int *)&changed[k]) == 0) break;  // the same in every block
     }
     NODE_LOOP(v, cnt, list) {
         const int2 d = cur[v];
@@ -331,14 +343,16 @@ static void forest_pass(int32_t cnt, const int32_t *list, const int32_t *a, Fore
                         cudaStream_t st) {
     // 2^K >= cnt jumps reach the cycle from any listed node and cover its cycle
     int K = jump_rounds(cnt);
-    DevBuf barm(sizeof(GridBarrier), st);
-    SLM_CUDA(cudaMemsetAsync(barm.get(), 0, sizeof(GridBarrier), st));
+    // the barrier word, then one "changed" word per round of the second pass
+    DevBuf barm(sizeof(GridBarrier) + sizeof(int) * 64, st);
+    SLM_CUDA(cudaMemsetAsync(barm.get(), 0, sizeof(GridBarrier) + sizeof(int) * 64, st));
     GridBarrier *bar = barm.as<GridBarrier>();
+    int *changed = reinterpret_cast<int *>(bar + 1);
     long long lim = kBarrierLimitNs;
     if (cnt <= kForestOneBlock) {
         // one block: block barriers only, an ordinary launch
         k_forest_rounds<<<1, kForestThreads, 0, st>>>(cnt, list, a, f.jmpA, f.jmpB, f.root, f.oncycle,
-                                                      f.entry, f.depth, f.cdist, K, bar, lim);
+                                                      f.entry, f.depth, f.cdist, K, bar, lim, changed);
         SLM_LAUNCH_CHECK();
         return;
     }
@@ -349,7 +363,7 @@ static void forest_pass(int32_t cnt, const int32_t *list, const int32_t *a, Fore
     if (per_sm < 1) fail(SLM_ERR_CUDA, "COMPONENTS kernel cannot be resident");
     int nb = (int)std::min<long long>((long long)sms, (cnt + kForestThreads - 1) / kForestThreads);
     void *kargs[] = {&cnt, (void *)&list, (void *)&a, &f.jmpA, &f.jmpB, &f.root, &f.oncycle,
-                     &f.entry, &f.depth, &f.cdist, &K, &bar, &lim};
+                     &f.entry, &f.depth, &f.cdist, &K, &bar, &lim, &changed};
     serialised_cooperative(st, [&] {
         SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_forest_rounds, dim3(nb),
                                              dim3(kForestThreads), kargs, 0, st));
