@@ -288,46 +288,69 @@ void exclusive_scan_i64(const long long *in, long long *out, long long n, long l
 }
 
 // ---------------------------------------------------------------------------
-// CSR validation: one warp per row.
+// CSR validation, one thread per entry (row_ptr was checked on the host:
+// rp[0] = 0, non-decreasing, rp[n] = nnz).  A warp covers 32 consecutive
+// entries; lanes 0 and 31 find the rows of the first and last of them, and
+// every lane searches its own row between the two, so a long row is spread
+// over many warps instead of one.
 // ---------------------------------------------------------------------------
-__global__ void k_validate(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                           int *bad) {
-    int lane = threadIdx.x & 31;
-    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long i = warp; i < n; i += nwarps) {
+namespace {
+// the row r in [lo, hi] with rp[r] <= e < rp[r + 1] (e < rp[n])
+__device__ __forceinline__ int row_of_entry(long long e, const int32_t *rp, int lo, int hi) {
+    while (lo < hi) {
+        const int mid = lo + (hi - lo + 1) / 2;
+        if ((long long)rp[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+}  // namespace
+
+__global__ void k_validate(int32_t n, long long nnz, const int32_t *rp, const int32_t *col,
+                           const int32_t *w, int *bad) {
+    const int lane = threadIdx.x & 31;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < nnz;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long p = base + lane;
+        const long long last = min(base + 31, nnz - 1);
+        int r = 0;
+        if (lane == 0 || lane == 31) r = row_of_entry(lane == 0 ? base : last, rp, 0, n - 1);
+        const int rlo = __shfl_sync(0xffffffffu, r, 0), rhi = __shfl_sync(0xffffffffu, r, 31);
         int b = 0;
-        int lo = rp[i], hi = rp[i + 1];
-        if (lane == 0 && (hi < lo || (i == 0 && lo != 0))) b |= 8;
-        if (hi >= lo) {
-            for (int p = lo + lane; p < hi; p += 32) {
-                int j = col[p];
-                if (j < 0 || j >= n) { b |= 1; continue; }
-                if (p > lo && col[p - 1] >= j) b |= 1;
-                int wp = w ? w[p] : 1;
+        if (p < nnz) {
+            const int i = row_of_entry(p, rp, rlo, rhi);
+            const int j = col[p];
+            if (j < 0 || j >= n) {
+                b |= 1;
+            } else {
+                if (p > rp[i] && col[p - 1] >= j) b |= 1;  // sorted, no duplicates
+                const int wp = w ? w[p] : 1;
                 if (wp <= 0) b |= 2;
                 // W_ji must exist with the same weight
                 int a = rp[j], c = rp[j + 1] - 1;
                 int found = -1;
                 while (a <= c) {
-                    int mid = (a + c) >> 1;
-                    int v = col[mid];
-                    if (v == (int)i) { found = mid; break; }
-                    if (v < (int)i) a = mid + 1; else c = mid - 1;
+                    const int mid = (a + c) >> 1;
+                    const int v = col[mid];
+                    if (v == i) { found = mid; break; }
+                    if (v < i) a = mid + 1;
+                    else c = mid - 1;
                 }
                 if (found < 0 || (w ? w[found] : 1) != wp) b |= 4;
             }
         }
-        if (b) atomicOr(bad, b);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
+        if (lane == 0 && b) atomicOr(bad, b);
     }
 }
 
-int validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+int validate_csr(int32_t n, long long nnz, const int32_t *rp, const int32_t *col, const int32_t *w,
                  cudaStream_t s) {
     DevBuf bad(sizeof(int), s);
     SLM_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
-    if (n > 0) {
-        k_validate<<<grid_for((long long)n * 32, 256), 256, 0, s>>>(n, rp, col, w, bad.as<int>());
+    if (n > 0 && nnz > 0) {
+        k_validate<<<grid_for(nnz, 256), 256, 0, s>>>(n, nnz, rp, col, w, bad.as<int>());
         SLM_LAUNCH_CHECK();
     }
     int h = 0;

@@ -278,7 +278,8 @@ __device__ __forceinline__ void k_credit(int cnt, const int32_t *M, const int32_
 __device__ __forceinline__ void k_branch(int cnt, const int32_t *M, const uint8_t *oncycle, const int32_t *root,
                          const int32_t *posr, const int32_t *sigma, MParam mp,
                          const long long *subS, const long long *subWA, const long long *subWin,
-                         long long *bestsc, unsigned long long *bestkey, int pass) {
+                         long long *bestsc, unsigned long long *bestkey, long long *msc,
+                         int32_t *mq, int pass) {
     const int lane = threadIdx.x & 31;
     for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < cnt;
          base += (long long)gridDim.x * blockDim.x) {
@@ -287,11 +288,18 @@ __device__ __forceinline__ void k_branch(int cnt, const int32_t *M, const uint8_
         long long sc = LLONG_MIN;
         if (k < cnt) {
             u = M[k];
-            if (!oncycle[u]) {
-                const int r = root[u];
-                q = posr[r];
-                const long long m = mp.of(u), sS = subS[u], sA = sigma[r];
-                sc = sS * (sA - sS) - m * (subWA[u] - subWin[u]);
+            if (pass == 0) {
+                if (!oncycle[u]) {
+                    const int r = root[u];
+                    q = posr[r];
+                    const long long m = mp.of(u), sS = subS[u], sA = sigma[r];
+                    sc = sS * (sA - sS) - m * (subWA[u] - subWin[u]);
+                }
+                msc[k] = sc;  // the tie pass reads the member's value back
+                mq[k] = q;
+            } else {
+                sc = msc[k];
+                q = mq[k];
             }
         }
         if (pass == 0) {
@@ -541,17 +549,18 @@ __device__ __forceinline__ void k_cut_fix(int cnt, const int32_t *M, const int32
 }
 
 __device__ __forceinline__ void k_forest_write(int cnt, const int32_t *M, const int4 *nf, const uint8_t *noc,
-                               int32_t *root, int32_t *entry, int32_t *depth, int32_t *cdist,
-                               uint8_t *oncycle, int32_t *flag) {
+                               const uint8_t *recomp, int32_t *root, int32_t *entry, int32_t *depth,
+                               int32_t *cdist, uint8_t *oncycle, int32_t *flag) {
     GRID_STRIDE(k, cnt) {
         const int x = M[k];
+        flag[x] = 0;  // the names in use inside the member set are members
+        if (!recomp[k]) continue;  // a remainder keeps its components
         const int4 v = nf[k];
         root[x] = v.x;
         entry[x] = v.y;
         depth[x] = v.z;
         cdist[x] = v.w;
         oncycle[x] = noc[k];
-        flag[x] = 0;  // the names in use inside the member set are members
     }
 }
 
@@ -566,8 +575,15 @@ __device__ __forceinline__ void k_own_members(int cnt, const int32_t *M, const u
         const int x = M[k], rx = root[x];
         const int b = istart[x], end = b + ideg[x];
         long long acc = 0;
-        for (int t = b + lane; t < end; t += 32)
-            if (root[col[t]] == rx) acc += w[t];
+        // four entries per lane in flight: a row's loads do not wait on one another
+        for (int t0 = b + lane; t0 < end; t0 += 128) {
+            int c[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) c[u] = (t0 + 32 * u < end) ? col[t0 + 32 * u] : -1;
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (c[u] >= 0 && root[c[u]] == rx) acc += w[t0 + 32 * u];
+        }
 #pragma unroll
         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) kacc[k] = acc;
@@ -583,54 +599,9 @@ __device__ __forceinline__ void k_own_members(int cnt, const int32_t *M, const u
 // members with longer rows are served by whole blocks (k_int_*_big)
 constexpr int kIntWarpMaxDeg = 1024;
 
-__global__ void k_int_count(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
-                            const int32_t *root, int32_t *icnt) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long k = warp; k < cnt; k += nw) {
-        const int x = M[k], r = root[x];
-        const int b = rp[x], e = rp[x + 1];
-        if (e - b > kIntWarpMaxDeg) continue;
-        int c = 0;
-        for (int p = b + lane; p < e; p += 32) {
-            const int j = col[p];
-            c += (j != x && root[j] == r) ? 1 : 0;
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane == 0) icnt[k] = c;
-    }
-}
-
-__global__ void k_int_count_big(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
-                                const int32_t *root, int32_t *icnt) {
-    __shared__ int tot;
-    for (long long k = blockIdx.x; k < cnt; k += gridDim.x) {
-        const int x = M[k];
-        const int b = rp[x], e = rp[x + 1];
-        if (e - b <= kIntWarpMaxDeg) continue;  // uniform over the block
-        const int r = root[x];
-        if (threadIdx.x == 0) tot = 0;
-        __syncthreads();
-        int c = 0;
-        for (int p = b + threadIdx.x; p < e; p += blockDim.x) {
-            const int j = col[p];
-            c += (j != x && root[j] == r) ? 1 : 0;
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&tot, c);
-        __syncthreads();
-        if (threadIdx.x == 0) icnt[k] = tot;
-        __syncthreads();
-    }
-}
-
 __global__ void k_int_fill(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
-                           const int32_t *w, const int32_t *root, const int32_t *icnt,
-                           const int32_t *ioff, int32_t *istart, int32_t *ideg, int32_t *icol,
-                           int32_t *iw) {
+                           const int32_t *w, const int32_t *root, const int32_t *ioff,
+                           int32_t *istart, int32_t *ideg, int32_t *icol, int32_t *iw) {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -638,11 +609,8 @@ __global__ void k_int_fill(int cnt, const int32_t *M, const int32_t *rp, const i
         const int x = M[k], r = root[x];
         const int b = rp[x], e = rp[x + 1];
         if (e - b > kIntWarpMaxDeg) continue;
-        int out = ioff[k];
-        if (lane == 0) {
-            istart[x] = out;
-            ideg[x] = icnt[k];
-        }
+        const int first = ioff[k];
+        int out = first;
         for (int p0 = b; p0 < e; p0 += 32) {
             const int p = p0 + lane;
             int j = -1;
@@ -656,6 +624,10 @@ __global__ void k_int_fill(int cnt, const int32_t *M, const int32_t *rp, const i
             }
             out += __popc(bal);
         }
+        if (lane == 0) {
+            istart[x] = first;
+            ideg[x] = out - first;
+        }
     }
 }
 
@@ -663,9 +635,8 @@ __global__ void k_int_fill(int cnt, const int32_t *M, const int32_t *rp, const i
 // entries does not matter (every use of them is a sum or a test), so each
 // warp claims its slots with one atomic on the member's cursor
 __global__ void k_int_fill_big(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
-                               const int32_t *w, const int32_t *root, const int32_t *icnt,
-                               const int32_t *ioff, int32_t *istart, int32_t *ideg, int32_t *icol,
-                               int32_t *iw) {
+                               const int32_t *w, const int32_t *root, const int32_t *ioff,
+                               int32_t *istart, int32_t *ideg, int32_t *icol, int32_t *iw) {
     __shared__ int cursor;
     const int lane = threadIdx.x & 31;
     for (long long k = blockIdx.x; k < cnt; k += gridDim.x) {
@@ -673,11 +644,7 @@ __global__ void k_int_fill_big(int cnt, const int32_t *M, const int32_t *rp, con
         const int b = rp[x], e = rp[x + 1];
         if (e - b <= kIntWarpMaxDeg) continue;  // uniform over the block
         const int r = root[x];
-        if (threadIdx.x == 0) {
-            cursor = ioff[k];
-            istart[x] = ioff[k];
-            ideg[x] = icnt[k];
-        }
+        if (threadIdx.x == 0) cursor = ioff[k];
         __syncthreads();
         for (int p0 = b + (threadIdx.x & ~31); p0 < e; p0 += blockDim.x) {
             const int p = p0 + lane;
@@ -693,6 +660,11 @@ __global__ void k_int_fill_big(int cnt, const int32_t *M, const int32_t *rp, con
                 icol[q] = j;
                 iw[q] = w[p];
             }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            istart[x] = ioff[k];
+            ideg[x] = cursor - ioff[k];
         }
         __syncthreads();
     }
@@ -990,7 +962,7 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
         mark_phase(3);
         for (int pass = 0; pass < 2; pass++) {
             k_branch(cnt, M, A.oncycle, A.root, A.posr, A.sigma, A.m, A.subS, A.subWA, A.subWin,
-                     A.bestsc, A.bestkey, pass);
+                     A.bestsc, A.bestkey, A.kacc, A.epref, pass);
             if (cycles)
                 k_cycle(&C->R, A.rlist, A.L, A.coffN, A.cyc, A.moffN, A.Mw, A.TS, A.sigma, A.m, n,
                         A.bestsc, A.bestkey, pass);
@@ -1005,7 +977,8 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
         k_forest_new(cnt, M, A.a, A.root, A.entry, A.depth, A.cdist, A.oncycle, A.posr, A.cut,
                      A.coffN, A.cyc, A.nf, A.noc, A.oldroot, A.recomp);
         GBAR_OR_RETURN();
-        k_forest_write(cnt, M, A.nf, A.noc, A.root, A.entry, A.depth, A.cdist, A.oncycle, A.flag);
+        k_forest_write(cnt, M, A.nf, A.noc, A.recomp, A.root, A.entry, A.depth, A.cdist, A.oncycle,
+                       A.flag);
         GBAR_OR_RETURN();
         mark_phase(6);
         k_cut_fix(cnt, M, &C->R, A.cut, A.cutsum, A.cutpar, A.oldroot, A.recomp, A.posr, A.root, A.a,
@@ -1125,10 +1098,11 @@ __global__ void k_own_listed_big(int cnt, const int32_t *list, const int32_t *rp
 
 // bound of the pools: cycle lengths never grow during POSITIVE
 __global__ void k_pool_bound(int cnt, const int32_t *M, const int32_t *root, const int32_t *a,
-                             const int32_t *cdist, unsigned long long *msum,
-                             unsigned long long *csum) {
+                             const int32_t *cdist, const int32_t *rp, int32_t *rowlen,
+                             unsigned long long *msum, unsigned long long *csum) {
     GRID_STRIDE(k, cnt) {
         int r = M[k];
+        rowlen[k] = rp[r + 1] - rp[r];  // room for the member's internal entries
         if (root[r] != r) continue;
         long long l = (a[r] == r) ? 1 : cdist[a[r]] + 1;
         if (l >= 2) {
@@ -1239,20 +1213,16 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     ps.cutpar.ensure(4 * (N + 1), st);
     ps.oldroot.ensure(4 * (N + 1), st);
     ps.mark.ensure(4 * (N + 1), st);
-    // pools sized once: the first round holds the longest cycles; the internal
-    // entries of the members are counted in the same pass over the host
+    // pools sized once: the first round holds the longest cycles.  The
+    // internal entries of a member get room for its whole row (the fill
+    // counts them), so no separate counting pass reads the rows.
     ps.hdr.ensure(64, st);
     SLM_CUDA(cudaMemsetAsync(ps.hdr.get(), 0, 64, st));
     unsigned long long *bnd = ps.hdr.as<unsigned long long>();
-    k_pool_bound<<<grid_for(cnt, 256), 256, 0, st>>>(cnt, M, f.root, a, f.cdist, bnd, bnd + 1);
-    SLM_LAUNCH_CHECK();
     ps.icnt.ensure(4 * (N + 1), st);
     ps.ioff.ensure(4 * (N + 1), st);
-    k_int_count<<<grid_for((long long)cnt * 32, 256), 256, 0, st>>>(cnt, M, rp, col, f.root,
-                                                                     ps.icnt.as<int32_t>());
-    SLM_LAUNCH_CHECK();
-    k_int_count_big<<<grid_for(cnt, 1, kNumSMs * 4), 256, 0, st>>>(cnt, M, rp, col, f.root,
-                                                                    ps.icnt.as<int32_t>());
+    k_pool_bound<<<grid_for(cnt, 256), 256, 0, st>>>(cnt, M, f.root, a, f.cdist, rp,
+                                                     ps.icnt.as<int32_t>(), bnd, bnd + 1);
     SLM_LAUNCH_CHECK();
     exclusive_scan_i32(ps.icnt.as<int32_t>(), ps.ioff.as<int32_t>(), cnt,
                        reinterpret_cast<int32_t *>(bnd + 2), st);
@@ -1267,12 +1237,12 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     ps.icol.ensure(4 * (size_t)(itot > 0 ? itot : 1), st);
     ps.iw.ensure(4 * (size_t)(itot > 0 ? itot : 1), st);
     k_int_fill<<<grid_for((long long)cnt * 32, 256), 256, 0, st>>>(
-        cnt, M, rp, col, w, f.root, ps.icnt.as<int32_t>(), ps.ioff.as<int32_t>(),
-        ps.istart.as<int32_t>(), ps.ideg.as<int32_t>(), ps.icol.as<int32_t>(), ps.iw.as<int32_t>());
+        cnt, M, rp, col, w, f.root, ps.ioff.as<int32_t>(), ps.istart.as<int32_t>(),
+        ps.ideg.as<int32_t>(), ps.icol.as<int32_t>(), ps.iw.as<int32_t>());
     SLM_LAUNCH_CHECK();
     k_int_fill_big<<<grid_for(cnt, 1, kNumSMs * 4), 256, 0, st>>>(
-        cnt, M, rp, col, w, f.root, ps.icnt.as<int32_t>(), ps.ioff.as<int32_t>(),
-        ps.istart.as<int32_t>(), ps.ideg.as<int32_t>(), ps.icol.as<int32_t>(), ps.iw.as<int32_t>());
+        cnt, M, rp, col, w, f.root, ps.ioff.as<int32_t>(), ps.istart.as<int32_t>(),
+        ps.ideg.as<int32_t>(), ps.icol.as<int32_t>(), ps.iw.as<int32_t>());
     SLM_LAUNCH_CHECK();
     // the rounds run in cooperative launches: a full grid while the member
     // lists are large, then a small grid for the tail of the rounds

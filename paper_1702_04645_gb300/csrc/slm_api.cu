@@ -405,7 +405,7 @@ slm_status slm_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *co
                 SLM_LAUNCH_CHECK();
             }
         }
-        int bad = slm::validate_csr(n, g->rp.as<int32_t>(), g->col.as<int32_t>(), g->w.as<int32_t>(), s);
+        int bad = slm::validate_csr(n, nnz, g->rp.as<int32_t>(), g->col.as<int32_t>(), g->w.as<int32_t>(), s);
         if (bad & (1 | 8)) slm::fail(SLM_ERR_INVALID_ARGUMENT, "column index out of range, unsorted or duplicated");
         if (bad & 2) slm::fail(SLM_ERR_INVALID_ARGUMENT, "non-positive weight");
         if (bad & 4) slm::fail(SLM_ERR_NOT_SYMMETRIC, "W is not symmetric");

@@ -386,7 +386,7 @@ slm_status slm_batch_create(int32_t num_graphs, const int32_t *graph_off, const 
                 SLM_LAUNCH_CHECK();
             }
         }
-        int bad = validate_csr(N, B->rp.as<int32_t>(), B->col.as<int32_t>(), B->w.as<int32_t>(), s);
+        int bad = validate_csr(N, nnz, B->rp.as<int32_t>(), B->col.as<int32_t>(), B->w.as<int32_t>(), s);
         if (bad & (1 | 8)) fail(SLM_ERR_INVALID_ARGUMENT, "column index out of range, unsorted or duplicated");
         if (bad & 2) fail(SLM_ERR_INVALID_ARGUMENT, "non-positive weight");
         if (bad & 4) fail(SLM_ERR_NOT_SYMMETRIC, "W is not symmetric");

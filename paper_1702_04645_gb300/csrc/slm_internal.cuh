@@ -196,7 +196,7 @@ void radix_sort_u32(uint32_t *keys, int32_t *vals, uint32_t *keys_tmp, int32_t *
 // ---------------------------------------------------------------------------
 // Validation of a CSR: returns a bit mask of problems (1 bad column/order,
 // 2 non-positive weight, 4 not symmetric, 8 bad row_ptr).
-int validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+int validate_csr(int32_t n, long long nnz, const int32_t *rp, const int32_t *col, const int32_t *w,
                  cudaStream_t s);
 // Number of the cnt entries of x outside [0, n) (host-synchronous).
 int count_out_of_range(long long cnt, const int32_t *x, int32_t n, cudaStream_t s);

@@ -271,6 +271,37 @@ def test_invalid_inputs_are_rejected():
     assert e.value.status == 6
 
 
+def test_invalid_entries_in_long_rows_are_rejected():
+    """The validator spreads a row over many warps: a defect anywhere in a hub
+    row (at a warp boundary, deep inside, in its last entry) is still found."""
+    rng = np.random.default_rng(5)
+    n = 6000
+    leaves = np.arange(1, n)
+    u = np.concatenate([np.zeros(n - 1, np.int64), rng.integers(1, n, 3000)])
+    v = np.concatenate([leaves, rng.integers(1, n, 3000)])
+    g = gg.from_edges(n, u, v, rng.integers(1, 5, u.shape[0]))
+    slm.Graph(g.row_ptr, g.col, g.w).close()  # valid
+    lo, hi = int(g.row_ptr[0]), int(g.row_ptr[1])
+    assert hi - lo > 4000
+    for p in (lo + 32, lo + 2049, hi - 1):
+        bad = g.w.copy()
+        bad[p] += 1  # W_0j != W_j0
+        with pytest.raises(slm.SlmError) as e:
+            slm.Graph(g.row_ptr, g.col, bad)
+        assert e.value.status == 2, p
+    for p in (lo + 64, lo + 3001):
+        col = g.col.copy()
+        col[p], col[p - 1] = col[p - 1], col[p]  # unsorted across a warp boundary
+        with pytest.raises(slm.SlmError) as e:
+            slm.Graph(g.row_ptr, col, g.w)
+        assert e.value.status == 1, p
+    col = g.col.copy()
+    col[hi - 1] = n  # out of range in the row's last entry
+    with pytest.raises(slm.SlmError) as e:
+        slm.Graph(g.row_ptr, col, g.w)
+    assert e.value.status == 1
+
+
 def test_scan_tuning_changes_no_result():
     """Every launch shape of the scan gives the same outputs (the autotuner
     relies on it), and the autotuner returns a valid tuning."""
