@@ -437,6 +437,106 @@ def run_served(args):
     return 0
 
 
+LFR_PAIRS = [(0.2, 0.1), (0.5, 0.4), (0.8, 0.7)]
+LFR_DESC = ("weighted LFR-style graphs, mean degree 50, maximum degree 100, degree exponent 2, "
+            "community sizes log-uniform in [100, 1000], mixing (mu_t, mu_w) in "
+            "{(0.2,0.1),(0.5,0.4),(0.8,0.7)}, internal/external weights uniform with means "
+            "round(8(1-mu_w)/(1-mu_t)) / round(8 mu_w/mu_t), seed 5")
+
+
+def _lfr_job(args):
+    n, mt, mw = args
+    g, comm = gg.lfr_weighted(n, mt, mw)
+    return g.row_ptr, g.col, g.w, comm
+
+
+def nmi(a, b) -> float:
+    """Normalised mutual information of two labelings (arithmetic-mean normalisation)."""
+    a = np.unique(np.asarray(a), return_inverse=True)[1].astype(np.int64)
+    b = np.unique(np.asarray(b), return_inverse=True)[1].astype(np.int64)
+    n, kb = a.shape[0], int(b.max()) + 1
+    keys, cnt = np.unique(a * kb + b, return_counts=True)
+    pa, pb, pij = np.bincount(a) / n, np.bincount(b) / n, cnt / n
+    ha, hb = -(pa * np.log(pa)).sum(), -(pb * np.log(pb)).sum()
+    mi = (pij * np.log(pij / (pa[keys // kb] * pb[keys % kb]))).sum()
+    return float(2 * mi / (ha + hb)) if ha + hb > 0 else 1.0
+
+
+def run_lfr_table1(args):
+    """The paper's experimental grid (mixing pairs of its LFR benchmark graphs
+    against the number of nodes): one complete run per case, timed with CUDA
+    events, beside the oracle on the smallest size (same partition)."""
+    import multiprocessing as mp
+    sizes = [int(x) for x in args.lfr_sizes.split(",")]
+    cases = [(n, mt, mw) for n in sizes for (mt, mw) in LFR_PAIRS]
+    t0 = time.perf_counter()
+    ctx = mp.get_context("spawn")  # before any CUDA use
+    with ctx.Pool(min(len(cases), os.cpu_count() or 1)) as pool:
+        graphs = pool.map(_lfr_job, cases)
+    note(f"{len(cases)} LFR graphs ready ({time.perf_counter() - t0:.1f} s)")
+    import torch
+    import paper_1702_04645_gb300 as slm
+    import oracle as O
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    run_kw = dict(seed=args.seed, accept_p32=slm.P_HALF, stream=stream.cuda_stream)
+    out, tot_units, tot_ms, launches = [], 0, 0.0, 0
+    with ClockSampler(local) as clk:
+        for (n, mt, mw), (rp, col, w, comm) in zip(cases, graphs):
+            G = slm.Graph(rp, col, w)
+            G.run(**run_kw)  # warm-up
+            torch.cuda.synchronize(dev)
+            l0 = slm.launch_count()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            G.run(**run_kw)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            launches += slm.launch_count() - l0
+            ms = ev0.elapsed_time(ev1)
+            levels = G.num_levels()
+            per_level = [G.stats(l) for l in range(levels)] + [G.stats(-1)]
+            units = sum(st.edges_scanned for st in per_level)
+            lab, K = G.partition(-1)
+            case = {"n": n, "mu_t": mt, "mu_w": mw, "nnz": int(rp[-1]), "ms": ms,
+                    "gteps": units / (ms / 1e3) / 1e9, "levels": levels,
+                    "sweeps": [st.sweeps for st in per_level],
+                    "status": [st.status for st in per_level],
+                    "communities": int(K), "planted": int(np.unique(comm).shape[0]),
+                    "modularity": G.modularity(-1), "nmi_planted": nmi(lab, comm)}
+            if n == sizes[0] and not args.no_cpu_baseline:
+                g = gg.CSR(n, rp, col, w)
+                t1 = time.perf_counter()
+                r = O.slm(g, seed=args.seed, P=O.P_HALF)
+                case["oracle_ms"] = 1e3 * (time.perf_counter() - t1)
+                case["identical_to_oracle"] = bool(np.array_equal(r.final, lab))
+            G.close()
+            out.append(case)
+            tot_units += units
+            tot_ms += ms
+            note(f"n={n} mu=({mt},{mw}): {ms:.1f} ms, {levels} levels, sweeps {case['sweeps']}, "
+                 f"K={K} (planted {case['planted']}), NMI {case['nmi_planted']:.3f}")
+    small = [c for c in out if "oracle_ms" in c]
+    cpu = None
+    if small:
+        cpu = {"value": sum(c["gteps"] * c["ms"] / c["oracle_ms"] for c in small) / len(small),
+               "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"oracle whole runs on the {sizes[0]}-node cases (mean GTEPS)"}
+    line = {"metric": METRIC, "value": tot_units / (tot_ms / 1e3) / 1e9, "unit": "GTEPS",
+            "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": tot_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": "lfr_weighted_table1", "desc": LFR_DESC, "sizes": sizes,
+                       "l2": "largest inputs larger than L2"},
+            "cases": out, "cpu_baseline": cpu, "gpu_launches": int(launches),
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def peaks():
     try:
         d = json.load(open(PEAKS))
@@ -482,7 +582,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default scan tuning instead of tuning it on the graph")
-    ap.add_argument("--workload", choices=["rmat", "forest", "scan", "served"], default="rmat")
+    ap.add_argument("--workload", choices=["rmat", "forest", "scan", "served", "lfr_table1"],
+                    default="rmat")
+    ap.add_argument("--lfr-sizes", default="10000,100000,1000000",
+                    help="lfr_table1: node counts")
     ap.add_argument("--rate", type=float, default=200.0, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of arrivals")
     ap.add_argument("--pool", type=int, default=48, help="served: distinct graphs")
@@ -499,6 +602,8 @@ def main():
         return run_scan(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "lfr_table1":
+        return run_lfr_table1(args)
 
     import torch
     import paper_1702_04645_gb300 as slm

@@ -214,6 +214,9 @@ def _powerlaw_int(seed, stream, count, expo, lo, hi):
     """Integers in [lo, hi] with P(k) ~ k^-expo, by inverse transform of the
     continuous law on [lo, hi+1) followed by flooring."""
     r = uniform01(seed, stream, np.arange(count, dtype=np.int64))
+    if expo == 1.0:  # log-uniform
+        x = float(lo) * (float(hi + 1) / float(lo)) ** r
+        return np.clip(np.floor(x).astype(np.int64), lo, hi)
     g = 1.0 - expo
     a_ = float(lo) ** g
     b_ = float(hi + 1) ** g
@@ -225,7 +228,7 @@ def _powerlaw_mean(expo, lo, hi):
     k = np.arange(lo, hi + 1, dtype=np.float64)
     # continuous law on [k, k+1) integrated, matching _powerlaw_int
     g = 1.0 - expo
-    cdf = lambda x: x ** g  # noqa: E731
+    cdf = (lambda x: np.log(x)) if expo == 1.0 else (lambda x: x ** g)  # noqa: E731
     p = (cdf(k + 1) - cdf(k)) / (cdf(float(hi + 1)) - cdf(float(lo)))
     return float((p * k).sum())
 
@@ -242,6 +245,36 @@ def lfr_style(n: int = 4194304, tau1: float = 2.5, kavg: float = 20.0, kmax: int
     Stubs are paired uniformly at random inside each community and across the
     whole graph; self-loops are dropped and duplicate pairs collapse to one
     unit-weight edge."""
+    u, v, _, comm = _lfr_wiring(n, tau1, kavg, kmax, tau2, cmin, cmax, mu, seed)
+    return from_edges(n, u, v, unit=True), comm
+
+
+def lfr_weighted(n: int, mu_t: float, mu_w: float, kavg: float = 50.0, kmax: int = 100,
+                 tau1: float = 2.0, tau2: float = 1.0, cmin: int = 100, cmax: int = 1000,
+                 wbar: int = 8, seed: int = 5) -> tuple[CSR, np.ndarray]:
+    """Weighted LFR-style graph with topology mixing mu_t and weight mixing
+    mu_w (the benchmark family of the paper's experiments: mean degree 50,
+    maximum degree 100, (mu_t, mu_w) in {(0.2, 0.1), (0.5, 0.4), (0.8, 0.7)});
+    returns (CSR, planted community of each node).
+
+    The wiring is lfr_style's.  An internal edge draws its weight uniformly
+    from [1, 2*t_in - 1] and an external one from [1, 2*t_out - 1], with
+    t_in = round(wbar*(1 - mu_w)/(1 - mu_t)) and t_out = round(wbar*mu_w/mu_t)
+    (at least 1), so that a node of degree d has expected strength about
+    d*wbar of which about a fraction mu_w lies on external edges.  One draw
+    gives both directions of an edge; duplicate pairs sum their weights."""
+    u, v, internal, comm = _lfr_wiring(n, tau1, kavg, kmax, tau2, cmin, cmax, mu_t, seed)
+    t_in = max(1, int(round(wbar * (1.0 - mu_w) / (1.0 - mu_t))))
+    t_out = max(1, int(round(wbar * mu_w / mu_t)))
+    idx = np.arange(u.shape[0], dtype=np.int64)
+    w = np.where(internal, uniform_int(seed, 5, idx, 1, 2 * t_in - 1),
+                 uniform_int(seed, 6, idx, 1, 2 * t_out - 1))
+    return from_edges(n, u, v, w), comm
+
+
+def _lfr_wiring(n, tau1, kavg, kmax, tau2, cmin, cmax, mu, seed):
+    """The stub pairs of an LFR-style graph without self-loops: (u, v, drawn
+    inside a community, planted community of each node)."""
     # minimum degree giving the requested mean
     kmin = 1
     for k0 in range(1, kmax):
@@ -301,8 +334,9 @@ def lfr_style(n: int = 4194304, tau1: float = 2.5, kavg: float = 20.0, kmax: int
     ue, ve = ext[0::2], ext[1::2]
     u = np.concatenate([ui, ue])
     v = np.concatenate([vi, ve])
+    internal = np.concatenate([np.ones(ui.shape[0], bool), np.zeros(ue.shape[0], bool)])
     keep = u != v
-    return from_edges(n, u[keep], v[keep], unit=True), comm
+    return u[keep], v[keep], internal[keep], comm
 
 
 # ---------------------------------------------------------------------------

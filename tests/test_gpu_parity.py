@@ -245,6 +245,14 @@ def test_sbm_planted_config_full_run():
     assert G.modularity(-1) > 0.7
 
 
+@pytest.mark.parametrize("mu_t,mu_w", [(0.2, 0.1), (0.5, 0.4), (0.8, 0.7)])
+def test_weighted_lfr_mixing_pairs_full_run(mu_t, mu_w):
+    """The paper's benchmark family at its three mixing pairs (10,000 nodes,
+    mean degree 50): every level, sweep and the final partition as the oracle's."""
+    g, _ = gg.lfr_weighted(10000, mu_t, mu_w)
+    compare_run(g, seed=1, P=O.P_HALF)
+
+
 def test_invalid_inputs_are_rejected():
     g = gg.random_small(20, 0.3, 1)
     bad = g.w.copy()
