@@ -646,19 +646,36 @@ __global__ void k_int_fill_big(int cnt, const int32_t *M, const int32_t *rp, con
         const int r = root[x];
         if (threadIdx.x == 0) cursor = ioff[k];
         __syncthreads();
-        for (int p0 = b + (threadIdx.x & ~31); p0 < e; p0 += blockDim.x) {
-            const int p = p0 + lane;
-            int j = -1;
-            if (p < e) j = col[p];
-            const bool in = p < e && j != x && root[j] == r;
-            const unsigned bal = __ballot_sync(0xffffffffu, in);
+        // eight entries per lane in flight; one cursor claim per warp and batch
+        const unsigned below = (1u << lane) - 1u;
+        for (int p0 = b + (threadIdx.x & ~31); p0 < e; p0 += 8 * blockDim.x) {
+            int j[8];
+            bool in[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                const int p = p0 + t * (int)blockDim.x + lane;
+                j[t] = p < e ? col[p] : -1;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; t++) in[t] = j[t] >= 0 && j[t] != x && root[j[t]] == r;
+            unsigned bal[8];
+            int tot = 0;
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                bal[t] = __ballot_sync(0xffffffffu, in[t]);
+                tot += __popc(bal[t]);
+            }
             int at = 0;
-            if (lane == 0 && bal) at = atomicAdd(&cursor, __popc(bal));
+            if (lane == 0 && tot) at = atomicAdd(&cursor, tot);
             at = __shfl_sync(0xffffffffu, at, 0);
-            if (in) {
-                const int q = at + __popc(bal & ((1u << lane) - 1u));
-                icol[q] = j;
-                iw[q] = w[p];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                if (in[t]) {
+                    const int q = at + __popc(bal[t] & below);
+                    icol[q] = j[t];
+                    iw[q] = w[p0 + t * (int)blockDim.x + lane];
+                }
+                at += __popc(bal[t]);
             }
         }
         __syncthreads();
@@ -1077,9 +1094,17 @@ __global__ void k_own_listed_big(int cnt, const int32_t *list, const int32_t *rp
         if (e - b <= kOwnWarpMaxDeg) continue;  // uniform over the block
         const int rx = root[x];
         long long acc = 0;
-        for (int t = b + threadIdx.x; t < e; t += blockDim.x) {
-            const int j = col[t];
-            if (j != x && root[j] == rx) acc += w[t];
+        // eight entries per thread in flight: a hub's row takes few dependent steps
+        for (int p0 = b + threadIdx.x; p0 < e; p0 += 8 * blockDim.x) {
+            int j[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                const int p = p0 + t * (int)blockDim.x;
+                j[t] = p < e ? col[p] : -1;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; t++)
+                if (j[t] >= 0 && j[t] != x && root[j[t]] == rx) acc += w[p0 + t * (int)blockDim.x];
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

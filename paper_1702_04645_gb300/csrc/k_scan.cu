@@ -716,9 +716,18 @@ __global__ void __launch_bounds__(kBlockThreads) k_own_block(const int32_t *orde
         const long long m = mp.of(i);
         int ci = root[i];
         long long own = 0;
-        for (int p = rp[i] + threadIdx.x; p < rp[i + 1]; p += blockDim.x) {
-            int j = col[p];
-            if (j != i && root[j] == ci) own += w[p];
+        const int e = rp[i + 1];
+        // eight entries per thread in flight
+        for (int p0 = rp[i] + threadIdx.x; p0 < e; p0 += 8 * blockDim.x) {
+            int j[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                const int p = p0 + t * (int)blockDim.x;
+                j[t] = p < e ? col[p] : -1;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; t++)
+                if (j[t] >= 0 && j[t] != i && root[j[t]] == ci) own += w[p0 + t * (int)blockDim.x];
         }
         long long sc = LLONG_MIN;
         int cc = INT_MAX;
