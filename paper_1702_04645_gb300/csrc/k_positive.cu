@@ -1244,12 +1244,12 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     ps.hdr.ensure(64, st);
     SLM_CUDA(cudaMemsetAsync(ps.hdr.get(), 0, 64, st));
     unsigned long long *bnd = ps.hdr.as<unsigned long long>();
-    ps.icnt.ensure(4 * (N + 1), st);
+    ps.rowlen.ensure(4 * (N + 1), st);
     ps.ioff.ensure(4 * (N + 1), st);
     k_pool_bound<<<grid_for(cnt, 256), 256, 0, st>>>(cnt, M, f.root, a, f.cdist, rp,
-                                                     ps.icnt.as<int32_t>(), bnd, bnd + 1);
+                                                     ps.rowlen.as<int32_t>(), bnd, bnd + 1);
     SLM_LAUNCH_CHECK();
-    exclusive_scan_i32(ps.icnt.as<int32_t>(), ps.ioff.as<int32_t>(), cnt,
+    exclusive_scan_i32(ps.rowlen.as<int32_t>(), ps.ioff.as<int32_t>(), cnt,
                        reinterpret_cast<int32_t *>(bnd + 2), st);
     unsigned long long hb[3] = {0, 0, 0};
     SLM_CUDA(cudaMemcpyAsync(hb, bnd, 24, cudaMemcpyDeviceToHost, st));

@@ -353,7 +353,7 @@ constexpr int kPosPhases = 11;
 struct PositiveScratch {
     DevBuf flag, kown, listA, listB, rlist, posr, L, coff, subS, subWA, subWin, credit, TS, msz,
         bestsc, bestkey, pool, cyc, cnt, mark, tot, hdr, epref, kacc, cut, nf, noc, bs, ctrl;
-    DevBuf icnt, ioff, istart, ideg, icol, iw;  // internal entries of the members
+    DevBuf rowlen, ioff, istart, ideg, icol, iw;  // internal entries of the members (room: whole rows)
     DevBuf recomp, moffN, cutsum, coffN, freshN, cutpar, oldroot;  // incremental rounds
     DevBuf dirty;  // communities whose membership changed since the last call
     bool profile = false;              // stamp the phases of every round
