@@ -168,11 +168,13 @@ extern "C" {
 uint64_t slm_server_footprint(int32_t n, int64_t nnz) {
     // input CSR and the aggregated level graph (8 B per entry each), the
     // sort of aggregation (keys, values and their double buffers: 24 B per
-    // entry), hub tables (at most 16 B per entry); per node the level
-    // workspace, POSITIVE's scratch and the composed labels of the levels,
-    // bounded by 512 B; plus 64 MiB for cycle pools and allocation rounding
+    // entry), hub tables (at most 16 B per entry), POSITIVE's copy of its
+    // members' internal entries (room for whole rows: at most 8 B per entry);
+    // per node the level workspace, POSITIVE's scratch and the composed
+    // labels of the levels, bounded by 512 B; plus 64 MiB for cycle pools and
+    // allocation rounding
     const uint64_t N = n > 0 ? (uint64_t)n : 0, E = nnz > 0 ? (uint64_t)nnz : 0;
-    return 56 * E + 512 * N + (64ull << 20);
+    return 64 * E + 512 * N + (64ull << 20);
 }
 
 const char *slm_server_last_error(const slm_server *sv) {
