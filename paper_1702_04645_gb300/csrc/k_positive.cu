@@ -977,6 +977,10 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
         k_credit(cnt, M, A.a, A.depth, A.root, A.freshN, first, A.credit, A.subWin);
         GBAR_OR_RETURN();
         mark_phase(3);
+        // the members' branch scores and community slots of the first pass are
+        // kept for the tie pass in two per-member arrays that are free here:
+        // kacc (rewritten by k_own_members before it is read) and epref (read
+        // only by the first round's k_edges, which has finished)
         for (int pass = 0; pass < 2; pass++) {
             k_branch(cnt, M, A.oncycle, A.root, A.posr, A.sigma, A.m, A.subS, A.subWA, A.subWin,
                      A.bestsc, A.bestkey, A.kacc, A.epref, pass);
