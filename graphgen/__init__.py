@@ -566,6 +566,48 @@ def isolated_and_loops(n: int, loops_every: int = 3) -> CSR:
     return from_edges(n, u, u, np.full(u.shape[0], 2))
 
 
+def directed_from_edges(n: int, u, v, w=None) -> CSR:
+    """CSR of a directed graph: a draw (u, v, w) adds w to W_uv only (row u);
+    duplicates are merged by summing.  Columns sorted, W need not be symmetric."""
+    u = np.asarray(u, dtype=np.int64)
+    v = np.asarray(v, dtype=np.int64)
+    w = np.ones(u.shape[0], np.int64) if w is None else np.asarray(w, dtype=np.int64)
+    key = u * np.int64(max(n, 1)) + v
+    order = np.argsort(key, kind="stable")
+    key, w = key[order], w[order]
+    if key.shape[0]:
+        first = np.ones(key.shape[0], dtype=bool)
+        first[1:] = key[1:] != key[:-1]
+        starts = np.flatnonzero(first)
+        ukey, uw = key[starts], np.add.reduceat(w, starts)
+    else:
+        ukey, uw = key, w
+    rows = ukey // max(n, 1)
+    counts = np.bincount(rows, minlength=n) if n else np.zeros(0, np.int64)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return CSR(n, row_ptr.astype(np.int32), (ukey % max(n, 1)).astype(np.int32),
+               uw.astype(np.int32))
+
+
+def random_directed(n: int, p: float, seed: int, wmax: int = 4, loops: float = 0.0,
+                    recip: float = 0.0) -> CSR:
+    """Directed graph on n nodes: each ordered pair (i, j), i != j, is an arc
+    with probability p; with probability `recip` an arc (i, j) also brings its
+    reverse (j, i) with an independent weight; node i has a self-loop with
+    probability `loops`.  Weights uniform in [1, wmax]."""
+    i, j = np.meshgrid(np.arange(n, dtype=np.int64), np.arange(n, dtype=np.int64), indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    pair = i * np.int64(max(n, 1)) + j
+    arc = (uniform01(seed, 21, pair) < p) & (i != j)
+    back = arc & (uniform01(seed, 22, pair) < recip)
+    loop = (i == j) & (uniform01(seed, 23, pair) < loops)
+    u = np.concatenate([i[arc], j[back], i[loop]])
+    v = np.concatenate([j[arc], i[back], i[loop]])
+    k = np.arange(u.shape[0], dtype=np.int64)
+    return directed_from_edges(n, u, v, uniform_int(seed, 24, k, 1, wmax))
+
+
 def cached(name: str, fn, *args, **kwargs):
     """Memoise a generator's CSR on disk under ``.graph_cache`` next to this package."""
     root = os.environ.get("SLM_GRAPH_CACHE") or os.path.join(

@@ -72,6 +72,19 @@ def _load():
                 "orc_run_trace": (None, [vp, i64p]),
                 "orc_run_top": (None, [vp, i32p]),
                 "orc_run_free": (None, [vp]),
+                "ord_strengths": (i64, [i32, i32p, i32p, i32p, i64p, i64p]),
+                "ord_symmetrise": (i32, [i32, i32p, i32p, i32p, i32p, i32p, i32p]),
+                "ord_modularity_num": (i64, [i32, i32p, i32p, i32p, i32p]),
+                "ord_modularity": (C.c_double, [i32, i32p, i32p, i32p, i32p]),
+                "ord_assign": (None, [i32, i32p, i32p, i32p, i64p, i64p, i64, i32p]),
+                "ord_sigma": (None, [i32, i32p, i64p, i64p, i64p, i64p]),
+                "ord_scan": (None, [i32, i32p, i32p, i32p, i64p, i64p, i64, i32p, i64p, i64p,
+                                    i32p, i64p, i64p]),
+                "ord_branch_gain": (i64, [i32, i32p, i32p, i32p, i64p, i64p, i64, i32p, i32p,
+                                          i64p, i64p, i32, i32]),
+                "ord_target": (i32, [i32p, i32p, i32p, i64p, i64p, i64, i32p, i32, i32]),
+                "ord_positive": (i32, [i32, i32p, i32p, i32p, i64p, i64p, i64, i32p, i32p]),
+                "ord_slm": (vp, [i32, i32p, i32p, i32p, u64, u64, i32, i32, C.c_uint32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -222,7 +235,10 @@ def slm(g, seed: int = 1, P: int = P_HALF, max_sweeps: int = 1000, max_levels: i
         flags: int = 0) -> Run:
     n, rp, col, w = _csr(g)
     lib = _load()
-    h = lib.orc_slm(n, rp, col, w, seed, P, max_sweeps, max_levels, flags)
+    return _collect(lib, lib.orc_slm(n, rp, col, w, seed, P, max_sweeps, max_levels, flags), n)
+
+
+def _collect(lib, h, n) -> Run:
     try:
         L = lib.orc_run_levels(h)
         levels = []
@@ -245,3 +261,107 @@ def slm(g, seed: int = 1, P: int = P_HALF, max_sweeps: int = 1000, max_levels: i
         return Run(levels, final[:n], stats, tr[: nt * 6].reshape(nt, 6), tuple(int(x) for x in top))
     finally:
         lib.orc_run_free(h)
+
+
+# ---------------------------------------------------------------------------
+# Directed graphs (the ord_* functions): g is any CSR with sorted unique
+# columns and positive weights, W_ij stored in row i.  Values are the exact
+# change of the directed modularity numerator; m_w must stay below 2^30.
+# ---------------------------------------------------------------------------
+def directed_strengths(g):
+    """(s_out, s_in, m_w) of a directed CSR."""
+    n, rp, col, w = _csr(g)
+    so = np.zeros(max(n, 1), np.int64)
+    si = np.zeros(max(n, 1), np.int64)
+    m = _load().ord_strengths(n, rp, col, w, so, si)
+    return so[:n], si[:n], int(m)
+
+
+def symmetrise(g):
+    """U = W + W^T as a graphgen.CSR (U_ii = 2 W_ii)."""
+    from graphgen import CSR
+    n, rp, col, w = _csr(g)
+    rpu = np.zeros(n + 1, np.int32)
+    colu = np.zeros(max(2 * g.nnz, 1), np.int32)
+    wu = np.zeros(max(2 * g.nnz, 1), np.int32)
+    k = _load().ord_symmetrise(n, rp, col, w, rpu, colu, wu)
+    return CSR(n, rpu, colu[:k].copy(), wu[:k].copy())
+
+
+def _directed(g):
+    so, si, m = directed_strengths(g)
+    if m >= 1 << 30:
+        raise ValueError("directed oracle needs m_w < 2^30")
+    u = symmetrise(g)
+    n, rpu, colu, wu = _csr(u)
+    pad = lambda x: _i64(x if n else np.zeros(1))  # noqa: E731
+    return n, rpu, colu, wu, pad(so), pad(si), m
+
+
+def directed_modularity_num(g, labels) -> int:
+    n, rp, col, w = _csr(g)
+    return int(_load().ord_modularity_num(n, rp, col, w, _i32(labels)))
+
+
+def directed_modularity(g, labels) -> float:
+    n, rp, col, w = _csr(g)
+    return float(_load().ord_modularity(n, rp, col, w, _i32(labels)))
+
+
+def directed_assign(g):
+    n, rpu, colu, wu, so, si, m = _directed(g)
+    a = np.zeros(max(n, 1), np.int32)
+    _load().ord_assign(n, rpu, colu, wu, so, si, m, a)
+    return a[:n]
+
+
+def directed_sigma(root, so, si):
+    root = _i32(root)
+    n = root.shape[0]
+    go = np.zeros(max(n, 1), np.int64)
+    gi = np.zeros(max(n, 1), np.int64)
+    _load().ord_sigma(n, root, _i64(so), _i64(si), go, gi)
+    return go[:n], gi[:n]
+
+
+def directed_scan(g, root):
+    """(best, gain, g) of every node of a directed graph."""
+    n, rpu, colu, wu, so, si, m = _directed(g)
+    root = _i32(root)
+    go, gi = directed_sigma(root, so[:n], si[:n])
+    best = np.zeros(n, np.int32)
+    gain = np.zeros(n, np.int64)
+    gl = np.zeros(n, np.int64)
+    _load().ord_scan(n, rpu, colu, wu, so, si, m, root, _i64(go), _i64(gi), best, gain, gl)
+    return best, gain, gl
+
+
+def directed_branch_gain(g, a, root, i: int, B: int) -> int:
+    n, rpu, colu, wu, so, si, m = _directed(g)
+    root = _i32(root)
+    go, gi = directed_sigma(root, so[:n], si[:n])
+    return int(_load().ord_branch_gain(n, rpu, colu, wu, so, si, m, _i32(a), root, _i64(go),
+                                       _i64(gi), i, B))
+
+
+def directed_target(g, root, i: int, B: int) -> int:
+    n, rpu, colu, wu, so, si, m = _directed(g)
+    return int(_load().ord_target(rpu, colu, wu, so, si, m, _i32(root), i, B))
+
+
+def directed_positive(g, a, root=None):
+    """POSITIVE on a directed graph; returns (a, root, number of splits)."""
+    n, rpu, colu, wu, so, si, m = _directed(g)
+    a = _i32(a).copy()
+    root = rootlabel(a) if root is None else _i32(root).copy()
+    k = _load().ord_positive(n, rpu, colu, wu, so, si, m, a, root)
+    return a, root, int(k)
+
+
+def directed_slm(g, seed: int = 1, P: int = P_HALF, max_sweeps: int = 1000,
+                 max_levels: int = 64, flags: int = 0) -> Run:
+    """The whole method on a directed graph (entries scanned count U's entries)."""
+    _directed(g)  # range check
+    n, rp, col, w = _csr(g)
+    lib = _load()
+    return _collect(lib, lib.ord_slm(n, rp, col, w, seed, P, max_sweeps, max_levels, flags), n)

@@ -22,6 +22,10 @@
  * node i at level t, sweep k is accepted iff
  *     (mix64(seed ^ mix64((t<<48) | (k<<32) | i)) >> 32) < P,
  * where mix64 is the splitmix64 output function (Steele, Lea, Flood 2014).
+ *
+ * The functions named ord_* at the end restate the method for a directed W
+ * (Q_w with out- and in-strengths, Section 2.4), reusing the parts that do
+ * not depend on the null model (components, tails, compaction, aggregation).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -740,4 +744,486 @@ void orc_run_free(orc_run *r) {
     free(r->sweeps); free(r->status); free(r->moves); free(r->splits); free(r->cands);
     free(r->edges_scanned); free(r->trace);
     free(r);
+}
+
+/* ========================================================================= */
+/* Directed graphs (Section 2.4: Q_w with out- and in-strengths).            */
+/*                                                                           */
+/* W is any non-negative integer matrix in CSR (row i lists W_ij > 0 with    */
+/* sorted unique columns; W_ii stored once).  With s_i^out = sum_j W_ij,     */
+/* s_j^in = sum_i W_ij and m_w = sum_ij W_ij the modularity numerator is     */
+/*     sum_C ( m_w W_in(C) - Sigma_C^out Sigma_C^in ),  Q = num / m_w^2.     */
+/* A move of a node or of a set S changes W_in by weights of U = W + W^T     */
+/* (U(S,X) = W(S,X) + W(X,S)), and each null-model product s Sigma of the    */
+/* symmetric functions above becomes s^out Sigma^in + s^in Sigma^out.  The   */
+/* values below are the numerator's exact change (the symmetric functions    */
+/* give half of it), so on a symmetric W each is twice the symmetric value   */
+/* and every decision (argmax, sign, tie) is the same.  Exact in int64 when  */
+/* m_w < 2^30.  The neighbours of a node are the nodes j with U_ij > 0.      */
+/* ========================================================================= */
+
+/* Out- and in-strengths of a directed CSR; returns m_w. */
+i64 ord_strengths(i32 n, const i32 *rp, const i32 *col, const i32 *w, i64 *so, i64 *si) {
+    for (i32 i = 0; i < n; i++) { so[i] = 0; si[i] = 0; }
+    i64 m = 0;
+    for (i32 i = 0; i < n; i++)
+        for (i32 p = rp[i]; p < rp[i + 1]; p++) {
+            so[i] += w[p];
+            si[col[p]] += w[p];
+            m += w[p];
+        }
+    return m;
+}
+
+/* U = W + W^T as a CSR with sorted unique columns (U_ii = 2 W_ii): row i of  */
+/* W and row i of W^T (built by counting, so its columns ascend) are merged.  */
+/* Output arrays hold up to 2 nnz(W) entries; returns nnz(U).                 */
+i32 ord_symmetrise(i32 n, const i32 *rp, const i32 *col, const i32 *w, i32 *rpu, i32 *colu,
+                   i32 *wu) {
+    i32 nnz = rp[n];
+    i32 *tp = (i32 *)calloc((size_t)n + 2, sizeof(i32));
+    i32 *tc = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+    i32 *tw = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+    i32 *fill = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    for (i32 p = 0; p < nnz; p++) tp[col[p] + 1]++;
+    for (i32 v = 0; v < n; v++) tp[v + 1] += tp[v];
+    for (i32 v = 0; v < n; v++) fill[v] = tp[v];
+    for (i32 i = 0; i < n; i++)
+        for (i32 p = rp[i]; p < rp[i + 1]; p++) {
+            i32 q = fill[col[p]]++;
+            tc[q] = i;
+            tw[q] = w[p];
+        }
+    i32 k = 0;
+    rpu[0] = 0;
+    for (i32 i = 0; i < n; i++) {
+        i32 x = rp[i], y = tp[i];
+        while (x < rp[i + 1] || y < tp[i + 1]) {
+            if (y >= tp[i + 1] || (x < rp[i + 1] && col[x] < tc[y])) {
+                colu[k] = col[x]; wu[k] = w[x]; x++;
+            } else if (x >= rp[i + 1] || tc[y] < col[x]) {
+                colu[k] = tc[y]; wu[k] = tw[y]; y++;
+            } else {
+                colu[k] = col[x]; wu[k] = w[x] + tw[y]; x++; y++;
+            }
+            k++;
+        }
+        rpu[i + 1] = k;
+    }
+    free(tp); free(tc); free(tw); free(fill);
+    return k;
+}
+
+/* Modularity numerator of a labelling on a directed W (definition above). */
+i64 ord_modularity_num(i32 n, const i32 *rp, const i32 *col, const i32 *w, const i32 *labels) {
+    i64 *so = (i64 *)calloc((size_t)n + 1, sizeof(i64));
+    i64 *si = (i64 *)calloc((size_t)n + 1, sizeof(i64));
+    i64 *win = (i64 *)calloc((size_t)n + 1, sizeof(i64));
+    i64 *go = (i64 *)calloc((size_t)n + 1, sizeof(i64));
+    i64 *gi = (i64 *)calloc((size_t)n + 1, sizeof(i64));
+    i64 m = ord_strengths(n, rp, col, w, so, si);
+    for (i32 u = 0; u < n; u++) {
+        go[labels[u]] += so[u];
+        gi[labels[u]] += si[u];
+        for (i32 p = rp[u]; p < rp[u + 1]; p++)
+            if (labels[col[p]] == labels[u]) win[labels[u]] += w[p];
+    }
+    __int128 num = 0;
+    for (i32 c = 0; c < n; c++) num += (__int128)m * win[c] - (__int128)go[c] * gi[c];
+    free(so); free(si); free(win); free(go); free(gi);
+    return (i64)num; /* |num| <= m_w^2 */
+}
+
+double ord_modularity(i32 n, const i32 *rp, const i32 *col, const i32 *w, const i32 *labels) {
+    i64 m = 0;
+    for (i32 p = 0; p < rp[n]; p++) m += w[p];
+    if (m == 0) return 0.0;
+    return (double)ord_modularity_num(n, rp, col, w, labels) / ((double)m * (double)m);
+}
+
+/* Pair score of i joining the singleton {j} (ASSIGN, target): the change of  */
+/* the numerator from the all-singleton state.                               */
+static i64 ord_pair(i64 m, i64 uij, const i64 *so, const i64 *si, i32 i, i32 j) {
+    return m * uij - (so[i] * si[j] + si[i] * so[j]);
+}
+
+/* ASSIGN (Section 3.1) on a directed graph, over the rows of U. */
+void ord_assign(i32 n, const i32 *rpu, const i32 *colu, const i32 *wu, const i64 *so,
+                const i64 *si, i64 m, i32 *a) {
+    for (i32 i = 0; i < n; i++) {
+        i32 bestj = -1;
+        i64 bests = 0;
+        for (i32 p = rpu[i]; p < rpu[i + 1]; p++) {
+            i32 j = colu[p];
+            if (j == i) continue;
+            i64 sc = ord_pair(m, wu[p], so, si, i, j);
+            if (bestj < 0 || sc > bests || (sc == bests && j < bestj)) { bestj = j; bests = sc; }
+        }
+        a[i] = (bestj >= 0 && bests > 0) ? bestj : i;
+    }
+}
+
+/* Sigma_C^out and Sigma_C^in of the communities named by root. */
+void ord_sigma(i32 n, const i32 *root, const i64 *so, const i64 *si, i64 *go, i64 *gi) {
+    for (i32 v = 0; v < n; v++) { go[v] = 0; gi[v] = 0; }
+    for (i32 v = 0; v < n; v++) { go[root[v]] += so[v]; gi[root[v]] += si[v]; }
+}
+
+/* MAXIMAL's per-node half (Section 3.4) on a directed graph.  With k_{i,C}  */
+/* the U-weight between i and C (self-loop excluded),                        */
+/*   score(C) = m_w k_{i,C} - (s_i^out (Sigma_C^in - [C = c_i] s_i^in)       */
+/*                             + s_i^in (Sigma_C^out - [C = c_i] s_i^out)),  */
+/* and moving i from c_i to C changes the numerator by score(C) - score(c_i);*/
+/* g(i) = score(c_i).  Readings as in orc_scan.                              */
+void ord_scan(i32 n, const i32 *rpu, const i32 *colu, const i32 *wu, const i64 *so,
+              const i64 *si, i64 m, const i32 *root, const i64 *go, const i64 *gi, i32 *best,
+              i64 *gain, i64 *g) {
+    i64 *acc = (i64 *)calloc((size_t)n + 1, sizeof(i64));
+    i32 *touched = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    for (i32 i = 0; i < n; i++) {
+        i32 nt = 0, ci = root[i];
+        for (i32 p = rpu[i]; p < rpu[i + 1]; p++) {
+            i32 j = colu[p];
+            if (j == i) continue;
+            i32 c = root[j];
+            if (acc[c] == 0) touched[nt++] = c;
+            acc[c] += wu[p];
+        }
+        i64 own = m * acc[ci] - (so[i] * (gi[ci] - si[i]) + si[i] * (go[ci] - so[i]));
+        i32 bc = -1;
+        i64 bs = 0;
+        for (i32 k = 0; k < nt; k++) {
+            i32 c = touched[k];
+            if (c == ci) continue;
+            i64 sc = m * acc[c] - (so[i] * gi[c] + si[i] * go[c]);
+            if (bc < 0 || sc > bs || (sc == bs && c < bc)) { bc = c; bs = sc; }
+        }
+        for (i32 k = 0; k < nt; k++) acc[touched[k]] = 0;
+        g[i] = own;
+        if (bc >= 0 && bs - own > 0) { best[i] = bc; gain[i] = bs - own; }
+        else { best[i] = ci; gain[i] = 0; }
+    }
+    free(acc);
+    free(touched);
+}
+
+/* Branch gain on a directed graph: moving the tail S of i from A = c_i to B */
+/* changes the numerator by                                                  */
+/*   m_w (U(S,B) - U(S,A\S)) - (Sigma_S^out (Sigma_B^in - Sigma_A^in + Sigma_S^in)   */
+/*                              + Sigma_S^in (Sigma_B^out - Sigma_A^out + Sigma_S^out)). */
+static i64 ord_branch_gain_impl(i32 i, i32 B, const i32 *rpu, const i32 *colu, const i32 *wu,
+                                const i64 *so, const i64 *si, i64 m, const i32 *root,
+                                const i64 *go, const i64 *gi, const i32 *cp, const i32 *ch,
+                                i32 *buf, unsigned char *mark) {
+    i32 A = root[i];
+    i32 k = tail_of(i, cp, ch, buf, mark);
+    i64 sSo = 0, sSi = 0, uB = 0, uA = 0;
+    for (i32 t = 0; t < k; t++) {
+        i32 u = buf[t];
+        sSo += so[u];
+        sSi += si[u];
+        for (i32 p = rpu[u]; p < rpu[u + 1]; p++) {
+            i32 v = colu[p];
+            if (root[v] == B) uB += wu[p];
+            else if (root[v] == A && !mark[v]) uA += wu[p];
+        }
+    }
+    for (i32 t = 0; t < k; t++) mark[buf[t]] = 0;
+    return m * (uB - uA) - (sSo * (gi[B] - gi[A] + sSi) + sSi * (go[B] - go[A] + sSo));
+}
+
+i64 ord_branch_gain(i32 n, const i32 *rpu, const i32 *colu, const i32 *wu, const i64 *so,
+                    const i64 *si, i64 m, const i32 *a, const i32 *root, const i64 *go,
+                    const i64 *gi, i32 i, i32 B) {
+    i32 *cp = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    i32 *ch = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    i32 *buf = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    unsigned char *mark = (unsigned char *)calloc((size_t)n + 1, 1);
+    build_children(n, a, cp, ch);
+    i64 r = ord_branch_gain_impl(i, B, rpu, colu, wu, so, si, m, root, go, gi, cp, ch, buf, mark);
+    free(cp); free(ch); free(buf); free(mark);
+    return r;
+}
+
+/* Target node on a directed graph: the U-neighbour j of i in B with the      */
+/* largest pair score; ties to the smallest j, taken even when negative.     */
+i32 ord_target(const i32 *rpu, const i32 *colu, const i32 *wu, const i64 *so, const i64 *si,
+               i64 m, const i32 *root, i32 i, i32 B) {
+    i32 bj = -1;
+    i64 bs = 0;
+    for (i32 p = rpu[i]; p < rpu[i + 1]; p++) {
+        i32 j = colu[p];
+        if (j == i || root[j] != B) continue;
+        i64 sc = ord_pair(m, wu[p], so, si, i, j);
+        if (bj < 0 || sc > bs || (sc == bs && j < bj)) { bj = j; bs = sc; }
+    }
+    return bj;
+}
+
+/* POSITIVE (Section 3.3) on a directed graph: local gain g(i) = score(c_i)  */
+/* of ord_scan; splitting A into S and R changes the numerator by            */
+/*   Sigma_S^out Sigma_R^in + Sigma_S^in Sigma_R^out - m_w U(S,R).           */
+/* Candidate cuts, readings and tie order as in orc_positive.  The context's */
+/* graph is U and its strengths are s^out; s^in travels beside it.           */
+typedef struct {
+    pos_ctx b;
+    const i64 *si;
+} pos_ctx_d;
+
+static int ord_positive_one(pos_ctx_d *d, i32 *mem, i32 cnt, i32 *k1) {
+    pos_ctx *c = &d->b;
+    const i64 *so = c->s, *si = d->si;
+    if (cnt < 2) return 0;
+    i32 A = c->root[mem[0]];
+    i64 sAo = 0, sAi = 0;
+    for (i32 t = 0; t < cnt; t++) { sAo += so[mem[t]]; sAi += si[mem[t]]; }
+    int neg = 0;
+    for (i32 t = 0; t < cnt && !neg; t++) {
+        i32 i = mem[t];
+        i64 kown = 0;
+        for (i32 p = c->rp[i]; p < c->rp[i + 1]; p++) {
+            i32 j = c->col[p];
+            if (j != i && c->root[j] == A) kown += c->w[p];
+        }
+        i64 g = c->m * kown - (so[i] * (sAi - si[i]) + si[i] * (sAo - so[i]));
+        if (g < 0) neg = 1;
+    }
+    if (!neg) return 0;
+
+    i32 L = 0;
+    {
+        i32 x = mem[0];
+        for (i32 t = 0; t < cnt; t++) c->mark[mem[t]] = 0;
+        while (!c->mark[x]) { c->mark[x] = 1; x = c->a[x]; }
+        i32 r = x;
+        for (i32 y = c->a[x]; y != x; y = c->a[y]) if (y < r) r = y;
+        i32 y = r;
+        do { c->cyc[L] = y; c->cidx[y] = L; L++; y = c->a[y]; } while (y != r);
+        for (i32 t = 0; t < cnt; t++) c->mark[mem[t]] = 0;
+        for (i32 t = 0; t < cnt; t++) c->oncyc[mem[t]] = 0;
+        for (i32 t = 0; t < L; t++) c->oncyc[c->cyc[t]] = 1;
+    }
+
+    int have = 0, btype = 0;
+    i64 bscore = 0;
+    i32 bu = -1, bv = -1;
+#define ORD_BETTER(sc, ty, uu, vv) \
+    (!have || (sc) > bscore || ((sc) == bscore && ((ty) < btype || ((ty) == btype && \
+      ((uu) < bu || ((uu) == bu && (vv) < bv))))))
+
+    for (i32 t = 0; t < cnt; t++) {
+        i32 u = mem[t];
+        if (c->oncyc[u]) continue;
+        i32 k = tail_of(u, c->cp, c->ch, c->buf, c->inpart);
+        i64 sSo = 0, sSi = 0;
+        for (i32 q = 0; q < k; q++) { sSo += so[c->buf[q]]; sSi += si[c->buf[q]]; }
+        i64 cw = cut_weight(c, c->buf, k, A);
+        for (i32 q = 0; q < k; q++) c->inpart[c->buf[q]] = 0;
+        i64 sc = sSo * (sAi - sSi) + sSi * (sAo - sSo) - c->m * cw;
+        if (ORD_BETTER(sc, 0, u, -1)) { have = 1; bscore = sc; btype = 0; bu = u; bv = -1; }
+    }
+    if (L >= 2) {
+        for (i32 t = 0; t < cnt; t++) {
+            i32 x = mem[t];
+            while (!c->oncyc[x]) x = c->a[x];
+            c->entry[mem[t]] = c->cidx[x];
+        }
+        for (i32 p = 0; p < L; p++) {
+            for (i32 q = p + 1; q < L; q++) {
+                i32 k = 0;
+                i64 sVo = 0, sVi = 0;
+                for (i32 t = 0; t < cnt; t++) {
+                    i32 x = mem[t];
+                    if (c->entry[x] > p && c->entry[x] <= q) {
+                        c->buf[k++] = x; c->inpart[x] = 1; sVo += so[x]; sVi += si[x];
+                    }
+                }
+                i64 cw = cut_weight(c, c->buf, k, A);
+                for (i32 t = 0; t < k; t++) c->inpart[c->buf[t]] = 0;
+                i64 sc = sVo * (sAi - sVi) + sVi * (sAo - sVo) - c->m * cw;
+                i32 u = c->cyc[p] < c->cyc[q] ? c->cyc[p] : c->cyc[q];
+                i32 v = c->cyc[p] < c->cyc[q] ? c->cyc[q] : c->cyc[p];
+                if (ORD_BETTER(sc, 1, u, v)) { have = 1; bscore = sc; btype = 1; bu = u; bv = v; }
+            }
+        }
+    }
+#undef ORD_BETTER
+    drop_child(c, c->a[bu], bu);
+    c->a[bu] = bu;
+    if (btype == 1) { drop_child(c, c->a[bv], bv); c->a[bv] = bv; }
+    relabel_members(c, mem, cnt);
+    i32 r1 = c->root[bu];
+    i32 lo = 0, hi = cnt - 1;
+    while (lo <= hi) {
+        if (c->root[mem[lo]] == r1) lo++;
+        else { i32 tmp = mem[lo]; mem[lo] = mem[hi]; mem[hi] = tmp; hi--; }
+    }
+    *k1 = lo;
+    return 1;
+}
+
+i32 ord_positive(i32 n, const i32 *rpu, const i32 *colu, const i32 *wu, const i64 *so,
+                 const i64 *si, i64 m, i32 *a, i32 *root) {
+    pos_ctx_d d;
+    pos_ctx *c = &d.b;
+    d.si = si;
+    c->n = n; c->rp = rpu; c->col = colu; c->w = wu; c->s = so; c->m = m; c->a = a; c->root = root;
+    size_t N = (size_t)n + 1;
+    c->cp = (i32 *)malloc(N * sizeof(i32));
+    c->ch = (i32 *)malloc(N * sizeof(i32));
+    c->buf = (i32 *)malloc(N * sizeof(i32));
+    c->entry = (i32 *)malloc(N * sizeof(i32));
+    c->cyc = (i32 *)malloc(N * sizeof(i32));
+    c->cidx = (i32 *)malloc(N * sizeof(i32));
+    c->stk = (i32 *)malloc(N * sizeof(i32));
+    c->mark = (unsigned char *)calloc(N, 1);
+    c->inpart = (unsigned char *)calloc(N, 1);
+    c->oncyc = (unsigned char *)calloc(N, 1);
+    c->state = (unsigned char *)calloc(N, 1);
+    build_children(n, a, c->cp, c->ch);
+    i32 *mem = (i32 *)malloc(N * sizeof(i32));
+    i32 *cnt = (i32 *)calloc(N, sizeof(i32));
+    i32 *off = (i32 *)calloc(N + 1, sizeof(i32));
+    for (i32 v = 0; v < n; v++) cnt[root[v]]++;
+    for (i32 v = 0; v < n; v++) off[v + 1] = off[v] + cnt[v];
+    for (i32 v = 0; v < n; v++) cnt[v] = 0;
+    for (i32 v = 0; v < n; v++) mem[off[root[v]] + cnt[root[v]]++] = v;
+    i32 *wl_off = (i32 *)malloc(2 * N * sizeof(i32));
+    i32 *wl_len = (i32 *)malloc(2 * N * sizeof(i32));
+    i32 nw = 0;
+    for (i32 v = n - 1; v >= 0; v--)
+        if (cnt[v] > 0) { wl_off[nw] = off[v]; wl_len[nw] = cnt[v]; nw++; }
+    i32 splits = 0;
+    while (nw > 0) {
+        nw--;
+        i32 o = wl_off[nw], l = wl_len[nw], k1 = 0;
+        if (ord_positive_one(&d, mem + o, l, &k1)) {
+            splits++;
+            wl_off[nw] = o; wl_len[nw] = k1; nw++;
+            wl_off[nw] = o + k1; wl_len[nw] = l - k1; nw++;
+        }
+    }
+    free(mem); free(cnt); free(off); free(wl_off); free(wl_len);
+    free(c->cp); free(c->ch); free(c->buf); free(c->entry); free(c->cyc); free(c->cidx);
+    free(c->stk); free(c->mark); free(c->inpart); free(c->oncyc); free(c->state);
+    return splits;
+}
+
+/* The whole method (Algorithm 1) on a directed graph: every level works on  */
+/* U = W + W^T with the strengths of W; AGGREGATE sums W itself (orc_aggregate */
+/* makes no use of symmetry), so out- and in-strengths and m_w are kept.     */
+/* Stats and trace as in orc_slm; entries scanned count the entries of U.    */
+orc_run *ord_slm(i32 n0, const i32 *rp0, const i32 *col0, const i32 *w0, u64 seed, u64 P,
+                 i32 max_sweeps, i32 max_levels, uint32_t flags) {
+    orc_run *r = (orc_run *)calloc(1, sizeof(orc_run));
+    r->n0 = n0;
+    r->final_labels = (i32 *)malloc(((size_t)n0 + 1) * sizeof(i32));
+    for (i32 v = 0; v < n0; v++) r->final_labels[v] = v;
+    i32 n = n0;
+    i32 nnz = rp0[n0];
+    i32 *rp = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    i32 *col = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+    i32 *w = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+    memcpy(rp, rp0, ((size_t)n + 1) * sizeof(i32));
+    memcpy(col, col0, (size_t)nnz * sizeof(i32));
+    memcpy(w, w0, (size_t)nnz * sizeof(i32));
+    i32 t = 0;
+    for (;;) {
+        size_t N = (size_t)n + 1;
+        i32 *rpu = (i32 *)malloc(N * sizeof(i32));
+        i32 *colu = (i32 *)malloc((2 * (size_t)nnz + 1) * sizeof(i32));
+        i32 *wu = (i32 *)malloc((2 * (size_t)nnz + 1) * sizeof(i32));
+        i32 nnzu = ord_symmetrise(n, rp, col, w, rpu, colu, wu);
+        i64 *so = (i64 *)malloc(N * sizeof(i64));
+        i64 *si = (i64 *)malloc(N * sizeof(i64));
+        i64 *go = (i64 *)malloc(N * sizeof(i64));
+        i64 *gi = (i64 *)malloc(N * sizeof(i64));
+        i64 *gain = (i64 *)malloc(N * sizeof(i64));
+        i64 *g = (i64 *)malloc(N * sizeof(i64));
+        i64 *bg = (i64 *)malloc(N * sizeof(i64));
+        i32 *a = (i32 *)malloc(N * sizeof(i32));
+        i32 *root = (i32 *)malloc(N * sizeof(i32));
+        i32 *best = (i32 *)malloc(N * sizeof(i32));
+        i32 *tgt = (i32 *)malloc(N * sizeof(i32));
+        i32 *cp = (i32 *)malloc(N * sizeof(i32));
+        i32 *ch = (i32 *)malloc(N * sizeof(i32));
+        i32 *buf = (i32 *)malloc(N * sizeof(i32));
+        unsigned char *mark = (unsigned char *)calloc(N, 1);
+        unsigned char *acc = (unsigned char *)calloc(N, 1);
+        i64 m = ord_strengths(n, rp, col, w, so, si);
+
+        ord_assign(n, rpu, colu, wu, so, si, m, a);
+        orc_rootlabel(n, a, root);
+        i64 lv_splits = 0, lv_moves = 0, lv_cands = 0, lv_edges = 0;
+        if (!(flags & ORC_FLAG_NO_POSITIVE))
+            lv_splits += ord_positive(n, rpu, colu, wu, so, si, m, a, root);
+
+        i32 sweep = 0;
+        int status = 2;
+        for (; sweep < max_sweeps; sweep++) {
+            ord_sigma(n, root, so, si, go, gi);
+            ord_scan(n, rpu, colu, wu, so, si, m, root, go, gi, best, gain, g);
+            lv_edges += nnzu;
+            i64 ncand = 0, npos = 0, nacc = 0, nspl = 0;
+            for (i32 i = 0; i < n; i++) if (gain[i] > 0) ncand++;
+            lv_cands += ncand;
+            if (ncand == 0) { status = 0; trace_push(r, t, sweep, 0, 0, 0, 0); sweep++; break; }
+            build_children(n, a, cp, ch);
+            for (i32 i = 0; i < n; i++) {
+                acc[i] = 0;
+                if (gain[i] <= 0) continue;
+                bg[i] = ord_branch_gain_impl(i, best[i], rpu, colu, wu, so, si, m, root, go, gi,
+                                             cp, ch, buf, mark);
+                if (bg[i] > 0) {
+                    npos++;
+                    if ((u64)orc_draw(seed, t, sweep, i) < P) acc[i] = 1;
+                }
+            }
+            if (npos == 0) { status = 1; trace_push(r, t, sweep, ncand, 0, 0, 0); sweep++; break; }
+            for (i32 i = 0; i < n; i++)
+                if (acc[i]) { tgt[i] = ord_target(rpu, colu, wu, so, si, m, root, i, best[i]); nacc++; }
+            for (i32 i = 0; i < n; i++) if (acc[i]) a[i] = tgt[i];
+            lv_moves += nacc;
+            if (nacc > 0) {
+                orc_rootlabel(n, a, root);
+                if (!(flags & ORC_FLAG_NO_POSITIVE))
+                    nspl = ord_positive(n, rpu, colu, wu, so, si, m, a, root);
+                lv_splits += nspl;
+            }
+            trace_push(r, t, sweep, ncand, npos, nacc, nspl);
+        }
+        i32 *id = (i32 *)malloc(N * sizeof(i32));
+        i32 K = orc_compact(n, root, id);
+        free(rpu); free(colu); free(wu); free(so); free(si); free(go); free(gi); free(gain);
+        free(g); free(bg); free(a); free(root); free(best); free(tgt); free(cp); free(ch);
+        free(buf); free(mark); free(acc);
+        if (K == n) {
+            r->top_status = status;
+            r->top_sweeps = sweep;
+            free(id);
+            break;
+        }
+        run_grow(r);
+        r->level_n[r->levels] = n;
+        r->level_K[r->levels] = K;
+        r->level_labels[r->levels] = id;
+        r->sweeps[r->levels] = sweep;
+        r->status[r->levels] = status;
+        r->moves[r->levels] = lv_moves;
+        r->splits[r->levels] = lv_splits;
+        r->cands[r->levels] = lv_cands;
+        r->edges_scanned[r->levels] = lv_edges;
+        r->levels++;
+        for (i32 v = 0; v < n0; v++) r->final_labels[v] = id[r->final_labels[v]];
+        i32 *rp2 = (i32 *)malloc(((size_t)K + 1) * sizeof(i32));
+        i32 *col2 = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+        i32 *w2 = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+        i32 nnz2 = orc_aggregate(n, rp, col, w, id, K, rp2, col2, w2);
+        free(rp); free(col); free(w);
+        rp = rp2; col = col2; w = w2; n = K; nnz = nnz2;
+        t++;
+        if (t >= max_levels) { r->level_limit_hit = 1; break; }
+    }
+    free(rp); free(col); free(w);
+    return r;
 }

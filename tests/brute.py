@@ -86,3 +86,29 @@ def components(a):
             y = a[y]
         root[v] = min(cyc)
     return root
+
+
+def q_num_def_directed(W, labels):
+    """sum_{i,j} (m_w W_ij - s_i^out s_j^in) delta(c_i, c_j) for any (directed)
+    W: m_w^2 times the directed Q_w of Section 2.4."""
+    labels = np.asarray(labels)
+    so = W.sum(axis=1)
+    si = W.sum(axis=0)
+    m = int(W.sum())
+    same = labels[:, None] == labels[None, :]
+    return int((m * W - np.outer(so, si))[same].sum())
+
+
+def brute_max_q_num_directed(W):
+    """Largest m_w^2 Q of a directed W over every partition (exhaustive, n <= 9)."""
+    n = W.shape[0]
+    P = set_partitions(n)
+    m = int(W.sum())
+    C = m * W - np.outer(W.sum(axis=1), W.sum(axis=0))
+    tot = np.zeros(P.shape[0], dtype=np.int64)
+    for i in range(n):
+        for j in range(n):
+            if C[i, j]:
+                tot += C[i, j] * (P[:, i] == P[:, j])
+    k = int(np.argmax(tot))
+    return int(tot[k]), P[k]
