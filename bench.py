@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -95,7 +96,10 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples go to a scratch file (SLM_BENCH_CLOCKS_DIR keeps them elsewhere);
+        # the JSON line carries their summary
+        out_dir = os.environ.get("SLM_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"slm_clocks_rank{gpu_index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
