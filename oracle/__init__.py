@@ -85,6 +85,7 @@ def _load():
                 "ord_target": (i32, [i32p, i32p, i32p, i64p, i64p, i64, i32p, i32, i32]),
                 "ord_positive": (i32, [i32, i32p, i32p, i32p, i64p, i64p, i64, i32p, i32p]),
                 "ord_slm": (vp, [i32, i32p, i32p, i32p, u64, u64, i32, i32, C.c_uint32]),
+                "orc_louvain": (vp, [i32, i32p, i32p, i32p, i32, i32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -236,6 +237,14 @@ def slm(g, seed: int = 1, P: int = P_HALF, max_sweeps: int = 1000, max_levels: i
     n, rp, col, w = _csr(g)
     lib = _load()
     return _collect(lib, lib.orc_slm(n, rp, col, w, seed, P, max_sweeps, max_levels, flags), n)
+
+
+def louvain(g, max_passes: int = 1000, max_levels: int = 64) -> Run:
+    """Classical sequential-move Louvain on a symmetric graph, for comparison
+    (stats per level: passes, 0, moves, 0, 0, entries scanned)."""
+    n, rp, col, w = _csr(g)
+    lib = _load()
+    return _collect(lib, lib.orc_louvain(n, rp, col, w, max_passes, max_levels), n)
 
 
 def _collect(lib, h, n) -> Run:

@@ -1227,3 +1227,121 @@ orc_run *ord_slm(i32 n0, const i32 *rp0, const i32 *col0, const i32 *w0, u64 see
     free(rp); free(col); free(w);
     return r;
 }
+
+/* ========================================================================= */
+/* Classical (sequential-move) Louvain, the method the paper builds on and   */
+/* names for comparison in its conclusion (Section 6).  Restated from its    */
+/* published definition (Blondel, Guillaume, Lambiotte, Lefebvre 2008) on    */
+/* the symmetric W above: per level, nodes are visited one at a time in id   */
+/* order; node i leaves its community A and joins the community C holding a  */
+/* neighbour for which the numerator's change, twice                         */
+/*   (m_w k_{i,C} - s_i Sigma_C) - (m_w k_{i,A} - s_i (Sigma_A - s_i)),      */
+/* is largest, only when that change is strictly positive (else it stays).  */
+/* Readings: ties go to the smallest community name (names are node ids of  */
+/* the level graph, a community keeps the name it started with); passes     */
+/* repeat until one moves no node; a level whose first pass moves nothing,  */
+/* or that ends with every node alone, ends the run; otherwise the          */
+/* communities are compacted in name order and aggregated (Section 3.5).    */
+/* Stats per level: sweeps = passes, moves = node moves, edges scanned =    */
+/* passes x entries; the trace holds (level, pass, 0, 0, moves, 0).         */
+/* ========================================================================= */
+orc_run *orc_louvain(i32 n0, const i32 *rp0, const i32 *col0, const i32 *w0, i32 max_passes,
+                     i32 max_levels) {
+    orc_run *r = (orc_run *)calloc(1, sizeof(orc_run));
+    r->n0 = n0;
+    r->final_labels = (i32 *)malloc(((size_t)n0 + 1) * sizeof(i32));
+    for (i32 v = 0; v < n0; v++) r->final_labels[v] = v;
+    i32 n = n0;
+    i32 nnz = rp0[n0];
+    i32 *rp = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    i32 *col = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+    i32 *w = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+    memcpy(rp, rp0, ((size_t)n + 1) * sizeof(i32));
+    memcpy(col, col0, (size_t)nnz * sizeof(i32));
+    memcpy(w, w0, (size_t)nnz * sizeof(i32));
+    i32 t = 0;
+    for (;;) {
+        size_t N = (size_t)n + 1;
+        i64 *s = (i64 *)malloc(N * sizeof(i64));
+        i64 *sigma = (i64 *)calloc(N, sizeof(i64));
+        i64 *acc = (i64 *)calloc(N, sizeof(i64));
+        i32 *touched = (i32 *)malloc(N * sizeof(i32));
+        i32 *comm = (i32 *)malloc(N * sizeof(i32));
+        unsigned char *seen = (unsigned char *)calloc(N, 1);
+        i64 m = orc_strengths(n, rp, col, w, s);
+        for (i32 v = 0; v < n; v++) { comm[v] = v; sigma[v] = s[v]; }
+        i32 passes = 0;
+        i64 lv_moves = 0, first_moves = 0;
+        while (passes < max_passes) {
+            i64 moves = 0;
+            for (i32 i = 0; i < n; i++) {
+                i32 A = comm[i], nt = 0;
+                for (i32 p = rp[i]; p < rp[i + 1]; p++) {
+                    i32 j = col[p];
+                    if (j == i) continue;
+                    i32 c = comm[j];
+                    if (!seen[c]) { seen[c] = 1; touched[nt++] = c; }
+                    acc[c] += w[p];
+                }
+                i64 stay = m * acc[A] - s[i] * (sigma[A] - s[i]);
+                i32 bc = -1;
+                i64 bd = 0;
+                for (i32 k = 0; k < nt; k++) {
+                    i32 c = touched[k];
+                    if (c == A) continue;
+                    i64 d = (m * acc[c] - s[i] * sigma[c]) - stay;
+                    if (d > 0 && (bc < 0 || d > bd || (d == bd && c < bc))) { bc = c; bd = d; }
+                }
+                for (i32 k = 0; k < nt; k++) { acc[touched[k]] = 0; seen[touched[k]] = 0; }
+                if (bc >= 0) {
+                    sigma[A] -= s[i];
+                    sigma[bc] += s[i];
+                    comm[i] = bc;
+                    moves++;
+                }
+            }
+            passes++;
+            lv_moves += moves;
+            if (passes == 1) first_moves = moves;
+            trace_push(r, t, passes - 1, 0, 0, moves, 0);
+            if (moves == 0) break;
+        }
+        /* compaction in name order */
+        i32 *id = (i32 *)malloc(N * sizeof(i32));
+        i32 *rank = (i32 *)malloc(N * sizeof(i32));
+        for (i32 v = 0; v < n; v++) rank[v] = -1;
+        for (i32 v = 0; v < n; v++) rank[comm[v]] = 0;
+        i32 K = 0;
+        for (i32 v = 0; v < n; v++) if (rank[v] == 0) rank[v] = ++K;
+        for (i32 v = 0; v < n; v++) id[v] = rank[comm[v]] - 1;
+        free(rank); free(s); free(sigma); free(acc); free(touched); free(comm); free(seen);
+        if (first_moves == 0 || K == n) {
+            r->top_status = 0;
+            r->top_sweeps = passes;
+            free(id);
+            break;
+        }
+        run_grow(r);
+        r->level_n[r->levels] = n;
+        r->level_K[r->levels] = K;
+        r->level_labels[r->levels] = id;
+        r->sweeps[r->levels] = passes;
+        r->status[r->levels] = 0;
+        r->moves[r->levels] = lv_moves;
+        r->splits[r->levels] = 0;
+        r->cands[r->levels] = 0;
+        r->edges_scanned[r->levels] = (i64)passes * nnz;
+        r->levels++;
+        for (i32 v = 0; v < n0; v++) r->final_labels[v] = id[r->final_labels[v]];
+        i32 *rp2 = (i32 *)malloc(((size_t)K + 1) * sizeof(i32));
+        i32 *col2 = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+        i32 *w2 = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+        i32 nnz2 = orc_aggregate(n, rp, col, w, id, K, rp2, col2, w2);
+        free(rp); free(col); free(w);
+        rp = rp2; col = col2; w = w2; n = K; nnz = nnz2;
+        t++;
+        if (t >= max_levels) { r->level_limit_hit = 1; break; }
+    }
+    free(rp); free(col); free(w);
+    return r;
+}
