@@ -25,7 +25,8 @@
  *
  * The functions named ord_* at the end restate the method for a directed W
  * (Q_w with out- and in-strengths, Section 2.4), reusing the parts that do
- * not depend on the null model (components, tails, compaction, aggregation).
+ * not depend on the null model (components, tails, compaction, aggregation);
+ * orc_louvain, last, is classical sequential-move Louvain for comparison.
  */
 #include <stdint.h>
 #include <stdlib.h>
