@@ -272,6 +272,30 @@ def lfr_weighted(n: int, mu_t: float, mu_w: float, kavg: float = 50.0, kmax: int
     return from_edges(n, u, v, w), comm
 
 
+def lfr_directed(n: int, mu_t: float, mu_w: float, recip: float = 0.3, **kw) -> tuple[CSR, np.ndarray]:
+    """Directed weighted LFR-style graph: the wiring and weights of
+    lfr_weighted, each stub pair becoming an arc in a random direction, and
+    with probability `recip` also the reverse arc (its own weight draw).
+    Returns (directed CSR, planted community of each node)."""
+    args = dict(kavg=50.0, kmax=100, tau1=2.0, tau2=1.0, cmin=100, cmax=1000, wbar=8, seed=5)
+    args.update(kw)
+    seed, wbar = args.pop("seed"), args.pop("wbar")
+    u, v, internal, comm = _lfr_wiring(n, args["tau1"], args["kavg"], args["kmax"], args["tau2"],
+                                       args["cmin"], args["cmax"], mu_t, seed)
+    t_in = max(1, int(round(wbar * (1.0 - mu_w) / (1.0 - mu_t))))
+    t_out = max(1, int(round(wbar * mu_w / mu_t)))
+    idx = np.arange(u.shape[0], dtype=np.int64)
+    flip = uniform01(seed, 7, idx) < 0.5
+    a, b = np.where(flip, v, u), np.where(flip, u, v)
+    back = uniform01(seed, 8, idx) < recip
+    w1 = np.where(internal, uniform_int(seed, 5, idx, 1, 2 * t_in - 1),
+                  uniform_int(seed, 6, idx, 1, 2 * t_out - 1))
+    w2 = np.where(internal, uniform_int(seed, 9, idx, 1, 2 * t_in - 1),
+                  uniform_int(seed, 10, idx, 1, 2 * t_out - 1))
+    return (directed_from_edges(n, np.concatenate([a, b[back]]), np.concatenate([b, a[back]]),
+                                np.concatenate([w1, w2[back]])), comm)
+
+
 def _lfr_wiring(n, tau1, kavg, kmax, tau2, cmin, cmax, mu, seed):
     """The stub pairs of an LFR-style graph without self-loops: (u, v, drawn
     inside a community, planted community of each node)."""

@@ -50,3 +50,18 @@ def test_oracle_recovers_planted_lfr_communities(mu_t, mu_w):
     # the same partition up to names: every planted community is one label
     pairs = np.unique(np.stack([comm, lab]), axis=1)
     assert pairs.shape[1] == np.unique(comm).shape[0] == np.unique(lab).shape[0]
+
+
+def test_lfr_directed_orientation_and_mixing():
+    g, comm = gg.lfr_directed(20000, 0.5, 0.4, recip=0.3)
+    W_rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    pairs = set(zip(W_rows.tolist(), g.col.tolist()))
+    both = sum((j, i) in pairs for (i, j) in pairs) / len(pairs)
+    assert 0.3 < both < 0.6  # some arcs come with their reverse, most do not
+    ext = comm[W_rows] != comm[g.col]
+    assert abs(g.w[ext].sum() / g.w.sum() - 0.4) < 0.06
+    so, si, m = O.directed_strengths(g)
+    assert so.sum() == si.sum() == m and not (so == si).all()
+    a, ca = gg.lfr_directed(3000, 0.2, 0.1, seed=4)
+    b, cb = gg.lfr_directed(3000, 0.2, 0.1, seed=4)
+    assert np.array_equal(a.col, b.col) and np.array_equal(a.w, b.w) and np.array_equal(ca, cb)
