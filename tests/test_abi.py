@@ -1,11 +1,13 @@
 """The C ABI library loads and exports every entry point that include/*.h declares.
 
-No compute call is made, so this runs without a GPU.
+No compute call is made, so this runs without a GPU; the checks a call makes
+on the host before touching a device are exercised too.
 """
 import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_1702_04645_gb300 as slm
@@ -70,3 +72,27 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(slm, "_lib", None)
     with pytest.raises(RuntimeError):
         slm.load()
+
+
+def _create(lib, n, rp, col=None, w=None):
+    h = slm.C.c_void_p()
+    arr = [None if x is None else np.ascontiguousarray(x, np.int32) for x in (rp, col, w)]
+    ptr = [None if a is None else a.ctypes.data_as(slm.C.c_void_p) for a in arr]
+    st = lib.slm_create_graph(n, ptr[0], ptr[1], ptr[2], 0, None, slm.C.byref(h))
+    return st, h
+
+
+def test_csr_shape_is_checked_on_the_host(lib):
+    # row_ptr must start at 0 and never decrease; n >= 0; col_idx present when
+    # there are entries: all refused with INVALID_ARGUMENT before any device call
+    assert _create(lib, 2, [1, 1, 2], [0, 1], [1, 1])[0] == 1
+    assert _create(lib, 2, [0, 2, 1], [0, 1], [1, 1])[0] == 1
+    assert _create(lib, -1, [0])[0] == 1
+    assert _create(lib, 2, [0, 1, 2])[0] == 1
+    st, h = _create(lib, 2, [0, 1, 2], [1, 0], [1, 1])
+    # a valid graph needs a device: created where there is one, SLM_ERR_CUDA where not
+    assert st in (0, 5)
+    if st == 0:
+        lib.slm_destroy_graph(h)
+    else:
+        assert not h.value
