@@ -96,3 +96,23 @@ def test_csr_shape_is_checked_on_the_host(lib):
         lib.slm_destroy_graph(h)
     else:
         assert not h.value
+
+
+def test_forest_offsets_are_checked_on_the_host(lib):
+    def create(goff, rp, col=(1, 0), w=(1, 1)):
+        arr = [np.ascontiguousarray(x, np.int32) for x in (goff, rp, col, w)]
+        p = [a.ctypes.data_as(slm.C.c_void_p) for a in arr]
+        h = slm.C.c_void_p()
+        st = lib.slm_batch_create(len(goff) - 1, p[0], p[1], p[2], p[3], None, 0, None,
+                                  slm.C.byref(h))
+        return st, h
+    assert create([1, 2], [0, 1, 2])[0] == 1          # graph_off[0] != 0
+    assert create([0, 2, 1], [0, 1, 2])[0] == 1       # decreasing graph_off
+    assert create([0, 2], [1, 1, 2])[0] == 1          # row_ptr[0] != 0
+    assert create([0, 2], [0, 2, 1])[0] == 1          # decreasing row_ptr
+    st, h = create([0, 2], [0, 1, 2])
+    assert st in (0, 5)
+    if st == 0:
+        lib.slm_batch_destroy(h)
+    else:
+        assert not h.value
