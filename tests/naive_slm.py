@@ -8,17 +8,22 @@ that sum before and after the change, never the closed-form scores of the C
 oracle.  The acceptance draw is an input (the oracle's splitmix64 draw, pinned
 on its own against the published outputs).  The sweep loop, stop reasons,
 synchronous write, POSITIVE after each write, compaction, AGGREGATE and
-composition follow Algorithm 1 and the readings the C oracle takes.
+composition follow Algorithm 1 and the readings the C oracle takes.  With
+directed=True the same run uses the directed numerator (Section 2.4's Q_w with
+out- and in-strengths), the reference of the oracle's ord_slm.
 """
 import numpy as np
 
-from brute import components, q_num_def, tail
+from brute import components, q_num_def, q_num_def_directed, tail
+
+# the numerator in use: the symmetric one, or the directed one (run(directed=True))
+_NUM = [q_num_def]
 
 
 def _move_gain(W, root, idx, C):
     lab = root.copy()
     lab[idx] = C
-    return q_num_def(W, lab) - q_num_def(W, root)
+    return _NUM[0](W, lab) - _NUM[0](W, root)
 
 
 def _pair_gain(W, i, j):
@@ -26,14 +31,19 @@ def _pair_gain(W, i, j):
     single = np.arange(W.shape[0])
     lab = single.copy()
     lab[i] = j
-    return q_num_def(W, lab) - q_num_def(W, single)
+    return _NUM[0](W, lab) - _NUM[0](W, single)
+
+
+def _nbrs(W, i):
+    """Neighbours of i: nodes joined to it by an entry in either direction."""
+    return [int(j) for j in np.flatnonzero(W[i] + W[:, i]) if j != i]
 
 
 def assign(W):
     n = W.shape[0]
     a = np.arange(n)
     for i in range(n):
-        nb = [j for j in np.flatnonzero(W[i]) if j != i]
+        nb = _nbrs(W, i)
         if not nb:
             continue
         g = {j: _pair_gain(W, i, j) for j in nb}
@@ -87,10 +97,10 @@ def positive(W, a):
                 break
         if flagged is None:
             return a, splits
-        q0 = q_num_def(W, root)
+        q0 = _NUM[0](W, root)
         best = None
         for ty, u, v, b in _split_options(a, root, flagged):
-            d = q_num_def(W, components(b)) - q0
+            d = _NUM[0](W, components(b)) - q0
             key = (-d, ty, u, v)
             if best is None or key < best[0]:
                 best = (key, b)
@@ -98,9 +108,20 @@ def positive(W, a):
         splits += 1
 
 
-def run(W0, draw, seed, P, max_sweeps=1000, max_levels=64, no_positive=False):
+def run(W0, draw, seed, P, max_sweeps=1000, max_levels=64, no_positive=False, directed=False):
     """Levels [(ids, K)], final labels, per-level stats (sweeps, status, moves,
-    splits, candidates, entries scanned) and the per-sweep trace."""
+    splits, candidates, entries scanned) and the per-sweep trace.  With
+    directed=True, W0 is any (directed) weight matrix: the directed numerator
+    decides, neighbours are joined in either direction, and the entries
+    scanned per sweep are those of W + W^T."""
+    _NUM[0] = q_num_def_directed if directed else q_num_def
+    try:
+        return _run(W0, draw, seed, P, max_sweeps, max_levels, no_positive)
+    finally:
+        _NUM[0] = q_num_def
+
+
+def _run(W0, draw, seed, P, max_sweeps, max_levels, no_positive):
     n0 = W0.shape[0]
     final = np.arange(n0)
     levels, stats, trace = [], [], []
@@ -108,7 +129,7 @@ def run(W0, draw, seed, P, max_sweeps=1000, max_levels=64, no_positive=False):
     t = 0
     while True:
         n = W.shape[0]
-        nnz = int(np.count_nonzero(W))
+        nnz = int(np.count_nonzero(W + W.T))  # = entries of W when W is symmetric
         a = assign(W)
         splits = moves = cands = edges = 0
         if not no_positive:
@@ -122,9 +143,9 @@ def run(W0, draw, seed, P, max_sweeps=1000, max_levels=64, no_positive=False):
             gain = np.zeros(n, np.int64)
             for i in range(n):
                 d = {}
-                for j in np.flatnonzero(W[i]):
+                for j in _nbrs(W, i):
                     C = int(root[j])
-                    if j != i and C != root[i] and C not in d:
+                    if C != root[i] and C not in d:
                         d[C] = _move_gain(W, root, [i], C)
                 if d and max(d.values()) > 0:
                     top = max(d.values())
@@ -146,7 +167,7 @@ def run(W0, draw, seed, P, max_sweeps=1000, max_levels=64, no_positive=False):
             acc = [i for i in pos if draw(seed, t, sweep, i) < P]
             tgt = {}
             for i in acc:
-                js = [j for j in np.flatnonzero(W[i]) if j != i and root[j] == best[i]]
+                js = [j for j in _nbrs(W, i) if root[j] == best[i]]
                 g = {j: _pair_gain(W, i, j) for j in js}
                 top = max(g.values())
                 tgt[i] = min(j for j in js if g[j] == top)

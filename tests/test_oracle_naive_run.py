@@ -17,11 +17,12 @@ hypothesis = pytest.importorskip("hypothesis")
 from hypothesis import HealthCheck, given, settings, strategies as st  # noqa: E402
 
 
-def _compare(g, seed, P, max_sweeps=30, no_positive=False):
+def _compare(g, seed, P, max_sweeps=30, no_positive=False, directed=False):
     levels, final, stats, trace = naive_slm.run(dense(g), O.draw, seed, P, max_sweeps=max_sweeps,
-                                                no_positive=no_positive)
-    r = O.slm(g, seed=seed, P=P, max_sweeps=max_sweeps,
-              flags=O.FLAG_NO_POSITIVE if no_positive else 0)
+                                                no_positive=no_positive, directed=directed)
+    run = O.directed_slm if directed else O.slm
+    r = run(g, seed=seed, P=P, max_sweeps=max_sweeps,
+            flags=O.FLAG_NO_POSITIVE if no_positive else 0)
     assert r.num_levels == len(levels)
     for (a, ka), (b, kb) in zip(r.levels, levels):
         assert ka == kb and (a == b).all()
@@ -58,6 +59,21 @@ def test_oracle_run_equals_definition_level_run(g, seed, P):
 @given(g=tiny_graphs(), seed=st.integers(0, 2**32 - 1))
 def test_oracle_run_without_positive_equals_definition_level_run(g, seed):
     _compare(g, seed, O.P_HALF, no_positive=True)
+
+
+@st.composite
+def tiny_digraphs(draw):
+    return gg.random_directed(draw(st.integers(2, 12)), draw(st.sampled_from([0.2, 0.35, 0.5])),
+                              draw(st.integers(0, 10**6)), wmax=draw(st.sampled_from([1, 3, 6])),
+                              loops=draw(st.sampled_from([0.0, 0.3])),
+                              recip=draw(st.sampled_from([0.0, 0.3, 0.8])))
+
+
+@settings(max_examples=800, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+@given(g=tiny_digraphs(), seed=st.integers(0, 2**32 - 1),
+       P=st.sampled_from([O.P_HALF, O.P_ALWAYS, 3 << 30]))
+def test_directed_oracle_run_equals_definition_level_run(g, seed, P):
+    _compare(g, seed, P, directed=True)
 
 
 def test_the_random_cases_move_and_split():
