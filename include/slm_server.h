@@ -101,8 +101,9 @@ slm_status slm_server_submit(slm_server *sv, const slm_graph_desc *graph, const 
 slm_status slm_server_poll(slm_server *sv, uint64_t ticket, int32_t *state);
 
 /* Block until the request is DONE or FAILED, or until timeout_s seconds have
- * passed (timeout_s < 0: no limit).  Returns SLM_OK when it ended,
- * SLM_ERR_TIMEOUT otherwise. */
+ * passed (timeout_s < 0: no limit).  Returns SLM_OK when it ended (also when
+ * another thread took its result with release meanwhile), SLM_ERR_TIMEOUT
+ * otherwise, INVALID_ARGUMENT for an unknown or already released ticket. */
 slm_status slm_server_wait(slm_server *sv, uint64_t ticket, double timeout_s);
 
 /* Timing and size record of a request (any state). */

@@ -275,9 +275,13 @@ slm_status slm_server_poll(slm_server *sv, uint64_t ticket, int32_t *state) {
 slm_status slm_server_wait(slm_server *sv, uint64_t ticket, double timeout_s) {
     if (!sv) return SLM_ERR_INVALID_ARGUMENT;
     std::unique_lock<std::mutex> lk(sv->mu);
-    Request *r = find(sv, ticket);
-    if (!r) return SLM_ERR_INVALID_ARGUMENT;
-    auto ended = [&] { return r->state == SLM_REQ_DONE || r->state == SLM_REQ_FAILED; };
+    if (!find(sv, ticket)) return SLM_ERR_INVALID_ARGUMENT;
+    // looked up at every wake-up: another thread may take the result with
+    // release while this one sleeps, and a released request has ended
+    auto ended = [&] {
+        const Request *r = find(sv, ticket);
+        return !r || r->state == SLM_REQ_DONE || r->state == SLM_REQ_FAILED;
+    };
     if (timeout_s < 0) {
         sv->cv_done.wait(lk, ended);
         return SLM_OK;
