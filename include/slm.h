@@ -42,8 +42,10 @@ typedef enum {
     SLM_ERR_CUDA = 5,             /* a CUDA call failed; see slm_last_error */
     SLM_ERR_NOT_RUN = 6,          /* results asked before slm_run */
     SLM_ERR_NOT_CONVERGED = 7,    /* sweep limit reached and SLM_FLAG_STRICT set */
-    SLM_ERR_TIMEOUT = 8,          /* reserved for bounded device-side waits */
-    SLM_ERR_BUDGET = 9            /* reserved for admission against a memory budget */
+    SLM_ERR_TIMEOUT = 8,          /* a bounded device-side wait gave up */
+    SLM_ERR_BUDGET = 9,           /* a request exceeds the server's whole memory budget */
+    SLM_ERR_CANCELLED = 10,       /* a server request was cancelled (slm_server_cancel) */
+    SLM_ERR_DEADLINE = 11         /* a server request passed its deadline before it finished */
 } slm_status;
 
 #define SLM_HOST 0
@@ -94,9 +96,11 @@ slm_status slm_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *co
 
 /* Run Algorithm 1 on the graph: per level ASSIGN, COMPONENTS, POSITIVE, then
  * MAXIMAL and POSITIVE alternately until no positive move remains, then
- * AGGREGATE; stop when a level finds no community structure.  Replaces the
- * results of any previous run.  Returns after the work on `stream` has
- * finished (the host reads a few counters per sweep). */
+ * AGGREGATE; stop when a level finds no community structure.  On success the
+ * results replace those of any previous run; when the run fails (for
+ * instance OUT_OF_MEMORY) the handle keeps the previous run's results, if
+ * any, and stays usable.  Returns after the work on `stream` has finished
+ * (the host reads a few counters per sweep). */
 slm_status slm_run(slm_graph *g, const slm_options *opt, void *stream);
 
 /* Number of recorded (aggregated) levels of the last run. */

@@ -29,6 +29,12 @@ typedef struct slm_batch slm_batch; /* opaque, owned by the library */
  * (graph_off[G]+1 entries), col_idx and weights (NULL: unit) are in `where`
  * memory with global node ids; seeds (HOST, num_graphs entries, NULL: the
  * run's opt.seed for every graph) key each graph's acceptance draws.
+ * Limits: node ids and entry offsets are int32 over the whole forest, so the
+ * forest holds fewer than 2^31 nodes and fewer than 2^31 stored entries in
+ * all (row_ptr[graph_off[G]] < 2^31); a larger set of graphs is run as
+ * several forests.  Every node id in col_idx is global (graph g's nodes are
+ * graph_off[g] .. graph_off[g+1]-1), while results are reported with each
+ * graph's own local ids.
  * Errors: INVALID_ARGUMENT (bad offsets, CSR, or an entry joining two
  * graphs), NOT_SYMMETRIC, OVERFLOW (some graph's m_w >= 2^31),
  * OUT_OF_MEMORY, CUDA. */

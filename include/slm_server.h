@@ -96,6 +96,23 @@ slm_status slm_server_create(uint64_t hbm_budget_bytes, int32_t max_slots, slm_s
 slm_status slm_server_submit(slm_server *sv, const slm_graph_desc *graph, const slm_options *opt,
                              uint64_t *ticket);
 
+/* As slm_server_submit, with a deadline: deadline_s > 0 seconds after
+ * submission the request must have ended.  A request still queued then ends
+ * FAILED with SLM_ERR_DEADLINE without running (queued deadlines are checked
+ * at least every 10 ms); a running one stops before its next level or sweep
+ * with the same status, its device memory freed and its footprint returned.
+ * deadline_s = 0: no deadline; negative or NaN: INVALID_ARGUMENT. */
+slm_status slm_server_submit_deadline(slm_server *sv, const slm_graph_desc *graph,
+                                      const slm_options *opt, double deadline_s, uint64_t *ticket);
+
+/* Cancel a request.  A queued request ends FAILED with SLM_ERR_CANCELLED at
+ * once (it never runs); a running one stops before its next level or sweep
+ * and ends FAILED with SLM_ERR_CANCELLED (the device work already queued for
+ * it finishes first; a run that completes before it looks at the flag ends
+ * DONE); a request that has already ended is left as it is.  Returns SLM_OK,
+ * or INVALID_ARGUMENT for an unknown or released ticket. */
+slm_status slm_server_cancel(slm_server *sv, uint64_t ticket);
+
 /* Non-blocking state of a request (SLM_REQ_*).  INVALID_ARGUMENT for an
  * unknown or released ticket. */
 slm_status slm_server_poll(slm_server *sv, uint64_t ticket, int32_t *state);
@@ -120,7 +137,10 @@ slm_status slm_server_result(slm_server *sv, uint64_t ticket, int32_t *labels,
 slm_status slm_server_get_stats(slm_server *sv, slm_server_stats *st);
 
 /* Stop accepting requests, drop the queued ones (they end FAILED with
- * SLM_ERR_NOT_RUN), wait for the running ones and free everything. */
+ * SLM_ERR_NOT_RUN), wait for the running ones and free everything.  Threads
+ * blocked in slm_server_wait on this server return once their request has
+ * ended, and destroy frees nothing before they have left.  No other call on
+ * the same server may start once destroy has begun. */
 void slm_server_destroy(slm_server *sv);
 
 /* Message of the last error of the server (or of the last failed create when sv is NULL). */

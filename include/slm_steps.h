@@ -120,6 +120,9 @@ slm_status slm_step_modularity(int32_t n, const int32_t *row_ptr, const int32_t 
  *   - *num_out (int64) and *q_out (double) are DEVICE pointers receiving the
  *     exact numerator sum_C (m_w W_in(C) - Sigma_C^2) and its FP64 quotient by
  *     m_w^2 (0 when m_w = 0), the same values slm_step_modularity returns;
+ *     when a label or column is found outside [0, n) the call still writes
+ *     both outputs (values of the in-range part only) before it returns
+ *     SLM_ERR_INVALID_ARGUMENT, so a caller must ignore them then;
  *   - the first call on a device looks up the array's device address (a
  *     cudaGetSymbolAddress with that device current), so make that first call
  *     before any stream capture;
@@ -209,6 +212,17 @@ slm_status slm_get_scan_tuning(slm_scan_tuning *t);
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t slm_launch_count(void);
+
+/* Failure injection for tests of the error paths (the paper has no
+ * counterpart): the k-th device allocation the library makes from now on, on
+ * any thread, fails as if the device were out of memory, so the call that
+ * made it returns SLM_ERR_OUT_OF_MEMORY; k = 0 turns the hook off, and it
+ * turns itself off once it has fired.  Nothing is done to the device: the
+ * allocation is refused on the host before cudaMallocFromPoolAsync is
+ * called.  A failed slm_create_graph returns no handle and keeps no memory;
+ * a failed slm_run leaves the handle usable, with the results of its
+ * previous run (if any). */
+void slm_debug_fail_allocation(int64_t k);
 
 #ifdef __cplusplus
 }

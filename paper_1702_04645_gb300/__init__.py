@@ -41,7 +41,7 @@ P_ALWAYS = 1 << 32
 STATUS = {0: "SLM_OK", 1: "SLM_ERR_INVALID_ARGUMENT", 2: "SLM_ERR_NOT_SYMMETRIC",
           3: "SLM_ERR_OVERFLOW", 4: "SLM_ERR_OUT_OF_MEMORY", 5: "SLM_ERR_CUDA",
           6: "SLM_ERR_NOT_RUN", 7: "SLM_ERR_NOT_CONVERGED", 8: "SLM_ERR_TIMEOUT",
-          9: "SLM_ERR_BUDGET"}
+          9: "SLM_ERR_BUDGET", 10: "SLM_ERR_CANCELLED", 11: "SLM_ERR_DEADLINE"}
 
 # every exported entry point, as declared in include/*.h
 EXPORTS = ["slm_default_options", "slm_create_graph", "slm_run", "slm_num_levels",
@@ -51,12 +51,12 @@ EXPORTS = ["slm_default_options", "slm_create_graph", "slm_run", "slm_num_levels
            "slm_step_maximal", "slm_step_positive", "slm_step_compact", "slm_step_aggregate",
            "slm_step_modularity", "slm_get_trace", "slm_get_timing", "slm_get_positive_profile", "slm_get_scan_timing", "slm_get_scan_bucket_timing", "slm_set_scan_tuning",
            "slm_get_scan_tuning", "slm_release_cached_memory", "slm_check_grid_barrier",
-           "slm_launch_count",
+           "slm_launch_count", "slm_debug_fail_allocation",
            "slm_step_modularity_noalloc", "slm_batch_create", "slm_batch_run",
            "slm_batch_num_graphs", "slm_batch_num_levels", "slm_batch_get_partition",
            "slm_batch_modularity", "slm_batch_get_stats", "slm_batch_run_info",
            "slm_batch_destroy", "slm_batch_last_error", "slm_server_footprint", "slm_server_create",
-           "slm_server_submit", "slm_server_poll", "slm_server_wait", "slm_server_request_info",
+           "slm_server_submit", "slm_server_submit_deadline", "slm_server_cancel", "slm_server_poll", "slm_server_wait", "slm_server_request_info",
            "slm_server_result", "slm_server_get_stats", "slm_server_destroy",
            "slm_server_last_error"]
 
@@ -175,6 +175,7 @@ def load():
             "slm_set_scan_tuning": (C.c_int, [C.POINTER(ScanTuning)]),
             "slm_get_scan_tuning": (C.c_int, [C.POINTER(ScanTuning)]),
             "slm_launch_count": (u64, []),
+            "slm_debug_fail_allocation": (None, [i64]),
             "slm_release_cached_memory": (None, []),
             "slm_check_grid_barrier": (C.c_int, [i32, i32, C.c_double, vp]),
             "slm_step_strengths": (C.c_int, [i32, vp, vp, vp, vp, C.POINTER(i64), vp]),
@@ -205,6 +206,9 @@ def load():
             "slm_server_create": (C.c_int, [u64, i32, C.POINTER(vp)]),
             "slm_server_submit": (C.c_int, [vp, C.POINTER(GraphDesc), C.POINTER(Options),
                                             C.POINTER(u64)]),
+            "slm_server_submit_deadline": (C.c_int, [vp, C.POINTER(GraphDesc), C.POINTER(Options),
+                                                     C.c_double, C.POINTER(u64)]),
+            "slm_server_cancel": (C.c_int, [vp, u64]),
             "slm_server_poll": (C.c_int, [vp, u64, C.POINTER(i32)]),
             "slm_server_wait": (C.c_int, [vp, u64, C.c_double]),
             "slm_server_request_info": (C.c_int, [vp, u64, C.POINTER(RequestInfo)]),
@@ -505,6 +509,12 @@ class Batch:
         return lv.value, sw.value
 
 
+def debug_fail_allocation(k: int):
+    """The k-th device allocation of the library from now on fails as out of
+    memory (k = 0: off); a host-side test hook."""
+    load().slm_debug_fail_allocation(int(k))
+
+
 def footprint(n: int, nnz: int) -> int:
     """Device bytes the request server reserves for a graph of n nodes and nnz entries."""
     return int(load().slm_server_footprint(int(n), int(nnz)))
@@ -528,8 +538,10 @@ class Server:
             raise SlmError(rc, msg.decode() if msg else "")
 
     def submit(self, row_ptr, col, w=None, *, seed: int = 1, accept_p32: int = P_HALF,
-               max_sweeps: int = 1000, max_levels: int = 64, flags: int = 0) -> int:
-        """Queue one graph (host arrays, copied during the call); returns its ticket."""
+               max_sweeps: int = 1000, max_levels: int = 64, flags: int = 0,
+               deadline: float | None = None) -> int:
+        """Queue one graph (host arrays, copied during the call); returns its
+        ticket.  deadline: seconds after submission by which it must end."""
         rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
         cl = np.ascontiguousarray(col, dtype=np.int32)
         ww = None if w is None else np.ascontiguousarray(w, dtype=np.int32)
@@ -537,8 +549,16 @@ class Server:
                       ww.ctypes.data if ww is not None and ww.size else None)
         o = Options(seed, accept_p32, max_sweeps, max_levels, flags)
         t = C.c_uint64()
-        self._check(load().slm_server_submit(self._h, C.byref(d), C.byref(o), C.byref(t)))
+        if deadline is None:
+            self._check(load().slm_server_submit(self._h, C.byref(d), C.byref(o), C.byref(t)))
+        else:
+            self._check(load().slm_server_submit_deadline(self._h, C.byref(d), C.byref(o),
+                                                          float(deadline), C.byref(t)))
         return t.value
+
+    def cancel(self, ticket: int):
+        """Cancel a queued or running request (it ends FAILED, SLM_ERR_CANCELLED)."""
+        self._check(load().slm_server_cancel(self._h, ticket))
 
     def poll(self, ticket: int) -> int:
         v = C.c_int32()

@@ -3,6 +3,7 @@
 // compaction of community names, partition composition (Algorithm 1,
 // C = C_t C) and the exact modularity numerator (Section 2.4, Q_w).
 #include <atomic>
+#include <chrono>
 #include <mutex>
 #include <cstdio>
 #include <cstring>
@@ -98,10 +99,42 @@ void trim_pool() {
         if (g_pool[d]) cudaMemPoolTrimTo(g_pool[d], 0);
 }
 
+static std::atomic<long long> g_alloc_fail_in{0};
+
+void set_alloc_failure(long long k) { g_alloc_fail_in.store(k > 0 ? k : 0); }
+
+static thread_local RunControl *t_run_control = nullptr;
+
+RunControl *set_thread_run_control(RunControl *c) {
+    RunControl *prev = t_run_control;
+    t_run_control = c;
+    return prev;
+}
+
+double steady_seconds() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void check_run_control() {
+    const RunControl *c = t_run_control;
+    if (!c) return;
+    if (c->cancel && c->cancel->load(std::memory_order_relaxed))
+        fail(SLM_ERR_CANCELLED, "the request was cancelled");
+    if (c->deadline > 0 && steady_seconds() > c->deadline)
+        fail(SLM_ERR_DEADLINE, "the request passed its deadline");
+}
+
 void DevBuf::alloc(size_t bytes, cudaStream_t s) {
     release();
     s_ = s;
     if (bytes == 0) bytes = 16;
+    // injected failure (slm_debug_fail_allocation): the countdown reaches 1
+    for (long long k = g_alloc_fail_in.load(); k > 0;) {
+        if (g_alloc_fail_in.compare_exchange_weak(k, k - 1)) {
+            if (k == 1) fail(SLM_ERR_OUT_OF_MEMORY, "injected allocation failure (slm_debug_fail_allocation)");
+            break;
+        }
+    }
     SLM_CUDA(cudaMallocFromPoolAsync(&p_, bytes, lib_pool(), s));
     bytes_ = bytes;
     acct_ = t_acct;

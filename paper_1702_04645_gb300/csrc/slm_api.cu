@@ -219,6 +219,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
     W.ps.profile = tm != nullptr;
     g->scan_by_level.clear();
     for (int t = 0; n > 0; t++) {
+        slm::check_run_control();
         const double scan_ms0 = g->phase_ms[kPhScan];
         const long long scan_cnt0 = g->phase_cnt[kPhScan];
         auto note_scans = [&] {
@@ -241,6 +242,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         int sweep = 0;
         int status = 2;
         for (; sweep < opt.max_sweeps; sweep++) {
+            slm::check_run_control();
             SweepCounts c = maximal_once(n, rp, col, w, s, m, W, opt.seed, opt.accept_p32, t, sweep,
                                          true, st, hc, tm);
             stt.candidates += c.cand;
@@ -360,6 +362,8 @@ const char *slm_status_string(slm_status s) {
     case SLM_ERR_NOT_CONVERGED: return "sweep limit reached";
     case SLM_ERR_TIMEOUT: return "timeout";
     case SLM_ERR_BUDGET: return "memory budget exceeded";
+    case SLM_ERR_CANCELLED: return "request cancelled";
+    case SLM_ERR_DEADLINE: return "request deadline passed";
     }
     return "unknown status";
 }
@@ -424,7 +428,23 @@ slm_status slm_run(slm_graph *g, const slm_options *opt, void *stream) {
     slm_options o;
     slm_default_options(&o);
     if (opt) o = *opt;
-    return guarded(g, [&] { run_impl(g, o, as_stream(stream)); });
+    // the previous run's results, put back when this run fails
+    std::vector<slm_graph::Level> levels = std::move(g->levels);
+    std::vector<std::array<long long, 6>> trace = std::move(g->trace);
+    const slm_level_stats top = g->top;
+    DevBuf comp = std::move(g->final_comp);
+    const bool had_run = g->has_run;
+    g->levels.clear();
+    g->trace.clear();
+    const slm_status st = guarded(g, [&] { run_impl(g, o, as_stream(stream)); });
+    if (st != SLM_OK) {
+        g->levels = std::move(levels);
+        g->trace = std::move(trace);
+        g->top = top;
+        g->final_comp = std::move(comp);
+        g->has_run = had_run;
+    }
+    return st;
 }
 
 slm_status slm_num_levels(const slm_graph *g, int32_t *levels) {
@@ -577,6 +597,8 @@ slm_status slm_get_positive_profile(const slm_graph *g, int64_t *ns, int32_t cap
 }
 
 uint64_t slm_launch_count(void) { return slm::launch_count(); }
+
+void slm_debug_fail_allocation(int64_t k) { slm::set_alloc_failure(k); }
 
 void slm_release_cached_memory(void) { slm::trim_pool(); }
 

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <initializer_list>
 #include <string>
 #include <utility>
@@ -110,6 +111,24 @@ struct MemAcct {
 };
 // the accountant of this thread (nullptr: none); returns the previous one
 MemAcct *set_thread_acct(MemAcct *a);
+
+// Test hook behind slm_debug_fail_allocation: the k-th device allocation
+// from now on fails as if the device were out of memory (k = 0: off).
+void set_alloc_failure(long long k);
+
+// Host-side control of a run (the request server's cancellation and
+// deadlines).  While a RunControl is installed on a thread, every run made on
+// that thread checks it before each level and each sweep and stops with
+// SLM_ERR_CANCELLED (cancel flag set) or SLM_ERR_DEADLINE (steady clock past
+// the deadline).  Device work already queued finishes; nothing is abandoned
+// in flight.
+struct RunControl {
+    const std::atomic<int> *cancel = nullptr;
+    double deadline = 0;  // seconds of steady_seconds(); 0 = none
+};
+RunControl *set_thread_run_control(RunControl *c);  // returns the previous one
+void check_run_control();
+double steady_seconds();
 
 class DevBuf {
   public:

@@ -9,6 +9,7 @@
 // keep the GPU busy.  The device memory each run really holds is measured by
 // an accountant that counts the library's buffers allocated on that thread.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -44,6 +45,8 @@ struct Request {
     double q = 0;
     long long edges = 0;
     uint64_t peak = 0;
+    double deadline = 0;         // steady_seconds() by which the request must end; 0: none
+    std::atomic<int> cancel{0};  // set by slm_server_cancel while the request runs
 };
 
 }  // namespace
@@ -55,7 +58,11 @@ struct slm_server {
     Clock::time_point t0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
+    // threads inside slm_server_wait; destroy waits on cv_idle until none is left
+    int32_t waiters = 0;
+    std::condition_variable cv_idle;
     std::deque<Request *> queue;
+    int32_t queued_deadlines = 0;  // queued requests that carry a deadline
     std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
     uint64_t next_ticket = 1;
     uint64_t reserved = 0, max_reserved = 0;
@@ -101,6 +108,34 @@ slm_status run_request(Request &r, cudaStream_t st) {
     return done(SLM_OK);
 }
 
+// End `r` (queued or just refused) as FAILED with status `st`; mu held.
+void end_unrun(slm_server *sv, Request *r, slm_status st, const char *why) {
+    r->state = SLM_REQ_FAILED;
+    r->status = st;
+    r->err = why;
+    r->t_done = sv->now();
+    sv->failed++;
+}
+
+// Queued requests past their deadline end FAILED (SLM_ERR_DEADLINE); mu held.
+void drop_expired(slm_server *sv) {
+    if (sv->queued_deadlines == 0) return;
+    const double now = slm::steady_seconds();
+    bool any = false;
+    for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+        Request *r = *it;
+        if (r->deadline > 0 && now > r->deadline) {
+            end_unrun(sv, r, SLM_ERR_DEADLINE, "the request passed its deadline while queued");
+            sv->queued_deadlines--;
+            it = sv->queue.erase(it);
+            any = true;
+        } else {
+            ++it;
+        }
+    }
+    if (any) sv->cv_done.notify_all();
+}
+
 void worker(slm_server *sv, int32_t slot) {
     // slots wait for the device by sleeping, so that many of them can share
     // the host's cores
@@ -110,13 +145,17 @@ void worker(slm_server *sv, int32_t slot) {
               cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
     std::unique_lock<std::mutex> lk(sv->mu);
     for (;;) {
-        sv->cv_work.wait(lk, [&] {
-            return sv->stop ||
-                   (!sv->queue.empty() && sv->queue.front()->footprint <= sv->budget - sv->reserved);
-        });
+        drop_expired(sv);
         if (sv->stop) break;
+        if (sv->queue.empty() || sv->queue.front()->footprint > sv->budget - sv->reserved) {
+            // queued deadlines are checked at least every 10 ms
+            if (sv->queued_deadlines > 0) sv->cv_work.wait_for(lk, std::chrono::milliseconds(10));
+            else sv->cv_work.wait(lk);
+            continue;
+        }
         Request *r = sv->queue.front();
         sv->queue.pop_front();
+        if (r->deadline > 0) sv->queued_deadlines--;
         sv->reserved += r->footprint;
         sv->max_reserved = std::max(sv->max_reserved, sv->reserved);
         sv->running++;
@@ -130,7 +169,12 @@ void worker(slm_server *sv, int32_t slot) {
         slm::MemAcct acct;
         if (ok) {
             slm::MemAcct *prev = slm::set_thread_acct(&acct);
+            slm::RunControl rc;
+            rc.cancel = &r->cancel;
+            rc.deadline = r->deadline;
+            slm::RunControl *prev_rc = slm::set_thread_run_control(&rc);
             s = run_request(*r, st);
+            slm::set_thread_run_control(prev_rc);
             slm::set_thread_acct(prev);
         } else {
             r->err = "slot could not select the device or create its stream";
@@ -216,8 +260,18 @@ slm_status slm_server_create(uint64_t hbm_budget_bytes, int32_t max_slots, slm_s
 
 slm_status slm_server_submit(slm_server *sv, const slm_graph_desc *gd, const slm_options *opt,
                              uint64_t *ticket) {
+    return slm_server_submit_deadline(sv, gd, opt, 0.0, ticket);
+}
+
+slm_status slm_server_submit_deadline(slm_server *sv, const slm_graph_desc *gd,
+                                      const slm_options *opt, double deadline_s, uint64_t *ticket) {
     if (!sv || !gd || !ticket) return SLM_ERR_INVALID_ARGUMENT;
     *ticket = 0;
+    if (!(deadline_s >= 0.0)) {  // also refuses NaN
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->err = "deadline_s must be >= 0 (0: no deadline)";
+        return SLM_ERR_INVALID_ARGUMENT;
+    }
     const int32_t n = gd->n;
     if (n < 0 || !gd->row_ptr) {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -255,6 +309,10 @@ slm_status slm_server_submit(slm_server *sv, const slm_graph_desc *gd, const slm
     }
     r->ticket = sv->next_ticket++;
     r->t_submit = sv->now();
+    if (deadline_s > 0) {
+        r->deadline = slm::steady_seconds() + deadline_s;
+        sv->queued_deadlines++;
+    }
     *ticket = r->ticket;
     sv->queue.push_back(r.get());
     sv->reqs.emplace(r->ticket, std::move(r));
@@ -272,10 +330,36 @@ slm_status slm_server_poll(slm_server *sv, uint64_t ticket, int32_t *state) {
     return SLM_OK;
 }
 
+slm_status slm_server_cancel(slm_server *sv, uint64_t ticket) {
+    if (!sv) return SLM_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    Request *r = find(sv, ticket);
+    if (!r) return SLM_ERR_INVALID_ARGUMENT;
+    if (r->state == SLM_REQ_QUEUED) {
+        auto it = std::find(sv->queue.begin(), sv->queue.end(), r);
+        if (it != sv->queue.end()) sv->queue.erase(it);
+        if (r->deadline > 0) sv->queued_deadlines--;
+        end_unrun(sv, r, SLM_ERR_CANCELLED, "the request was cancelled while queued");
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();  // the head of the queue may have changed
+    } else if (r->state == SLM_REQ_RUNNING) {
+        r->cancel.store(1);  // the run stops before its next level or sweep
+    }
+    return SLM_OK;
+}
+
 slm_status slm_server_wait(slm_server *sv, uint64_t ticket, double timeout_s) {
     if (!sv) return SLM_ERR_INVALID_ARGUMENT;
     std::unique_lock<std::mutex> lk(sv->mu);
     if (!find(sv, ticket)) return SLM_ERR_INVALID_ARGUMENT;
+    // counted while inside, so that destroy frees nothing a waiter still uses
+    struct Inside {
+        slm_server *sv;
+        explicit Inside(slm_server *s) : sv(s) { sv->waiters++; }
+        ~Inside() {  // runs with mu held
+            if (--sv->waiters == 0) sv->cv_idle.notify_all();
+        }
+    } inside(sv);
     // looked up at every wake-up: another thread may take the result with
     // release while this one sleeps, and a released request has ended
     auto ended = [&] {
@@ -356,17 +440,22 @@ void slm_server_destroy(slm_server *sv) {
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stop = true;
-        for (Request *r : sv->queue) {
-            r->state = SLM_REQ_FAILED;
-            r->status = SLM_ERR_NOT_RUN;
-            r->err = "the server was destroyed before the request was admitted";
-            sv->failed++;
-        }
+        for (Request *r : sv->queue)
+            end_unrun(sv, r, SLM_ERR_NOT_RUN, "the server was destroyed before the request was admitted");
         sv->queue.clear();
+        sv->queued_deadlines = 0;
     }
     sv->cv_work.notify_all();
     sv->cv_done.notify_all();
     for (auto &t : sv->workers) t.join();
+    {
+        // every request has now ended, so every waiter's condition holds:
+        // wake them and let them leave before the mutex and the condition
+        // variables are freed
+        std::unique_lock<std::mutex> lk(sv->mu);
+        sv->cv_done.notify_all();
+        sv->cv_idle.wait(lk, [&] { return sv->waiters == 0; });
+    }
     delete sv;
     slm::trim_pool();
 }

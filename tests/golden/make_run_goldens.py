@@ -1,0 +1,108 @@
+"""Write the oracle's whole-run results on the benchmark-sized graphs.
+
+Usage: python tests/golden/make_run_goldens.py [case ...]   (all cases by default)
+
+Each case regenerates a seeded graph with ``graphgen`` and runs the CPU oracle
+(``oracle.slm``, Algorithm 1 with ASSIGN, POSITIVE and MAXIMAL as the oracle
+restates them) on it, single-threaded; nothing here touches the CUDA library.
+The result goes to ``tests/golden/run_<case>.json``:
+
+  graph    n, nnz, m_w and SHA-256 digests of row_ptr, col and w (int32,
+           little-endian), so a test can tell a changed generator from a
+           changed run;
+  levels   per recorded level: n, K, the SHA-256 of its int32 community ids
+           and the level stats (sweeps, stop reason, moves, splits,
+           candidates, entries scanned);
+  final    SHA-256 of the composed labels on the input nodes and their K;
+  trace    every sweep's row (level, sweep, candidates, positive branch
+           gains, accepted, splits);
+  top      stop reason and sweeps of the last, unrecorded level, and the
+           level-limit flag;
+  q        the oracle's modularity of the final partition (float.hex).
+
+The oracle needs minutes per case; the seconds each case took are stored as
+``oracle_seconds`` (wall clock on the machine that wrote the file).
+"""
+import hashlib
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+import oracle as O  # noqa: E402
+
+
+def _rmat_s20():
+    return gg.cached("rmat_s20_seed2", gg.rmat, scale=20, seed=2)
+
+
+def _lfr_4m():
+    return gg.cached("lfr_style_default", lambda: gg.lfr_style()[0])
+
+
+def _lfr_256k():
+    return gg.cached("lfr_style_n262144", lambda: gg.lfr_style(n=262144)[0])
+
+
+# case name -> (graph, run options, description)
+CASES = {
+    "rmat_s20": (_rmat_s20, dict(seed=1, P=O.P_HALF),
+                 "R-MAT scale 20 (seed 2), complete run, acceptance seed 1, p = 1/2"),
+    "lfr_4m_bounded": (_lfr_4m, dict(seed=1, P=O.P_HALF, max_sweeps=5, max_levels=3),
+                       "LFR-style 4,194,304 nodes (seed 3), at most 5 sweeps per level and 3 levels"),
+    "lfr_256k_bounded": (_lfr_256k, dict(seed=1, P=O.P_HALF, max_sweeps=40),
+                         "LFR-style 262,144 nodes (seed 3), at most 40 sweeps per level"),
+}
+
+
+def sha(x) -> str:
+    return hashlib.sha256(np.ascontiguousarray(x, dtype="<i4").tobytes()).hexdigest()
+
+
+def fingerprint(g) -> dict:
+    m = int(np.asarray(g.w, dtype=np.int64).sum())
+    return {"n": int(g.n), "nnz": int(g.nnz), "m_w": m, "row_ptr": sha(g.row_ptr),
+            "col": sha(g.col), "w": sha(g.w)}
+
+
+def make(case: str) -> dict:
+    gen, opts, desc = CASES[case]
+    g = gen()
+    t0 = time.time()
+    r = O.slm(g, **opts)
+    dt = time.time() - t0
+    q = O.modularity(g, r.final)
+    levels = []
+    for (ids, K), st in zip(r.levels, r.stats):
+        levels.append({"n": int(ids.shape[0]), "K": int(K), "ids": sha(ids), "stats": list(st)})
+    out = {
+        "case": case,
+        "description": desc,
+        "options": {k: int(v) for k, v in opts.items()},
+        "graph": fingerprint(g),
+        "levels": levels,
+        "final": {"labels": sha(r.final), "K": int(r.final.max()) + 1 if g.n else 0},
+        "trace": r.trace.tolist(),
+        "top": list(r.top),
+        "q": float(q).hex(),
+        "oracle_seconds": round(dt, 1),
+    }
+    with open(os.path.join(HERE, f"run_{case}.json"), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    return out
+
+
+if __name__ == "__main__":
+    for c in sys.argv[1:] or list(CASES):
+        o = make(c)
+        print(c, "levels", len(o["levels"]), "sweeps", len(o["trace"]), "oracle s", o["oracle_seconds"],
+              flush=True)

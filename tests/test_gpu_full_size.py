@@ -1,18 +1,24 @@
 """The benchmark-sized graphs on the GPU: R-MAT scale 20 (1,048,576 nodes) and
-the LFR-style graph (4,194,304 nodes).
+the LFR-style graph (4,194,304 nodes), plus a 262,144-node graph of the
+LFR-style recipe.
 
-At these sizes the oracle cannot redo a whole run inside the test suite's
-time, so the checks are
-  * sampled outputs recomputed one node at a time from the definitions
-    (ASSIGN's best neighbour, the MAXIMAL scan's best community, gain and
-    local gain), on the same launch configuration slm_run uses;
-  * properties that hold at any size: the final modularity equals the oracle's
-    modularity of the GPU's own final partition (exact integer numerator, one
-    FP64 division), every level's labels are 0..K-1, the last level stopped
-    for a stated reason, and strengths and m_w are preserved;
-  * with SLM_FULL_ORACLE=1 in the environment, the complete oracle run,
-    compared level by level (minutes of single-threaded CPU time).
+  * ASSIGN's best neighbour and the MAXIMAL scan's best community, gain and
+    local gain of EVERY node are recomputed from the definitions with
+    vectorised numpy (exact int64) and compared element by element, on the
+    launch configuration slm_run uses;
+  * whole runs are compared level by level (every level's ids, K, stats, the
+    per-sweep trace, the final labels and Q) with the oracle's runs stored
+    under tests/golden/ by tests/golden/make_run_goldens.py (which calls
+    only the oracle): the complete run on the R-MAT graph, and bounded runs
+    (a sweep limit per level, and on the 4M graph a level limit) on the
+    LFR-style graphs, where the method does not settle within the default
+    sweep limit;
+  * properties that hold at any size: every level's labels are 0..K-1, the
+    last level stopped for a stated reason, and the final modularity equals
+    the oracle's modularity of the GPU's own final partition.
 """
+import hashlib
+import json
 import os
 
 import numpy as np
@@ -20,6 +26,7 @@ import pytest
 
 import graphgen as gg
 import oracle as O
+from whole_array import expected_assign, expected_scan, strengths as _strengths
 
 pytestmark = pytest.mark.gpu
 
@@ -29,7 +36,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 import paper_1702_04645_gb300 as slm  # noqa: E402
 
-SAMPLES = 1500
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -46,6 +53,10 @@ def _lfr():
     return gg.cached("lfr_style_default", lambda: gg.lfr_style()[0])
 
 
+def _lfr_256k():
+    return gg.cached("lfr_style_n262144", lambda: gg.lfr_style(n=262144)[0])
+
+
 GRAPHS = {"rmat_s20": _rmat, "lfr_4m": _lfr}
 
 
@@ -55,88 +66,103 @@ def big(request):
     return request.param, g
 
 
-def _sample(g, seed):
-    rng = np.random.default_rng(seed)
-    deg = np.diff(g.row_ptr)
-    nz = np.nonzero(deg)[0]
-    pick = rng.choice(nz, size=min(SAMPLES, nz.shape[0]), replace=False)
-    # always include the largest rows (the hub shape)
-    hubs = np.argsort(deg)[-20:]
-    return np.unique(np.concatenate([pick, hubs]))
+def _sha(x) -> str:
+    return hashlib.sha256(np.ascontiguousarray(x, dtype="<i4").tobytes()).hexdigest()
 
 
-def _strengths(g):
-    row = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
-    return np.bincount(row, weights=g.w, minlength=g.n).astype(np.int64)  # exact: m_w < 2^31
-
-
-def test_assign_sampled(big):
+def test_assign_all_nodes(big):
     name, g = big
     rp, col, w = (torch.from_numpy(x).cuda() for x in (g.row_ptr, g.col, g.w))
     s_d, m = slm.step_strengths(rp, col, w)
     a = slm.step_assign(rp, col, w, s_d, m).cpu().numpy()
-    s = _strengths(g)
-    assert int(s.sum()) == m
-    for i in _sample(g, 1):
-        lo, hi = g.row_ptr[i], g.row_ptr[i + 1]
-        j = g.col[lo:hi].astype(np.int64)
-        wv = g.w[lo:hi].astype(np.int64)
-        keep = j != i
-        j, wv = j[keep], wv[keep]
-        if j.shape[0] == 0:
-            assert a[i] == i
-            continue
-        sc = m * wv - s[i] * s[j]
-        best = sc.max()
-        exp = int(j[sc == best].min()) if best > 0 else int(i)
-        assert a[i] == exp, (name, int(i))
+    exp, s, m_host = expected_assign(g)
+    assert m == m_host
+    assert np.array_equal(s_d.cpu().numpy().astype(np.int64), s)
+    bad = np.nonzero(a != exp)[0]
+    assert bad.shape[0] == 0, (name, bad[:10])
 
 
-def test_scan_sampled(big):
+def test_scan_all_nodes(big):
     name, g = big
     rp, col, w = (torch.from_numpy(x).cuda() for x in (g.row_ptr, g.col, g.w))
     s_d, m = slm.step_strengths(rp, col, w)
     a = slm.step_assign(rp, col, w, s_d, m)
     a, root_d, _ = slm.step_positive(rp, col, w, s_d, m, a)
     best, gain, gl = (t.cpu().numpy() for t in slm.step_scan(rp, col, w, s_d, m, root_d))
-    root = root_d.cpu().numpy().astype(np.int64)
     s = _strengths(g)
-    sigma = np.bincount(root, weights=s, minlength=g.n).astype(np.int64)
-    for i in _sample(g, 2):
-        lo, hi = g.row_ptr[i], g.row_ptr[i + 1]
-        j = g.col[lo:hi].astype(np.int64)
-        wv = g.w[lo:hi].astype(np.int64)
-        keep = j != i
-        cs, inv = np.unique(root[j[keep]], return_inverse=True)
-        kic = np.bincount(inv, weights=wv[keep], minlength=cs.shape[0]).astype(np.int64)
-        ci = root[i]
-        own = int(kic[cs == ci].sum())
-        g_own = m * own - int(s[i]) * (int(sigma[ci]) - int(s[i]))
-        other = cs != ci
-        exp_best, exp_gain = ci, 0
-        if other.any():
-            sc = m * kic[other] - int(s[i]) * sigma[cs[other]]
-            top = sc.max()
-            c_top = int(cs[other][sc == top].min())
-            if top - g_own > 0:
-                exp_best, exp_gain = c_top, int(top - g_own)
-        assert gl[i] == g_own, (name, int(i))
-        assert best[i] == exp_best and gain[i] == exp_gain, (name, int(i))
+    eb, eg, el = expected_scan(g, root_d.cpu().numpy(), s, m)
+    for what, got, exp in (("local gain", gl, el), ("best", best, eb), ("gain", gain, eg)):
+        bad = np.nonzero(got.astype(np.int64) != exp)[0]
+        assert bad.shape[0] == 0, (name, what, bad[:10])
 
 
-@pytest.fixture(scope="module")
-def runs():
-    # a whole run at full size is checked on the R-MAT graph; on the LFR-style
-    # graph the method needs many minutes (POSITIVE peels its large
-    # communities one branch at a time), beyond a test suite's budget
+def _golden(case):
+    with open(os.path.join(GOLDEN, f"run_{case}.json")) as f:
+        return json.load(f)
+
+
+def compare_with_golden(g, gold, **run_kw):
+    fp = gold["graph"]
+    assert (g.n, g.nnz) == (fp["n"], fp["nnz"]), "the generator no longer makes the stored graph"
+    assert _sha(g.row_ptr) == fp["row_ptr"] and _sha(g.col) == fp["col"] and _sha(g.w) == fp["w"]
+    opts = gold["options"]
+    G = slm.Graph(g.row_ptr, g.col, g.w)
+    G.run(seed=opts["seed"], accept_p32=opts["P"], max_sweeps=opts.get("max_sweeps", 1000),
+          max_levels=opts.get("max_levels", 64), **run_kw)
+    tr = G.trace()
+    exp_tr = np.array(gold["trace"], dtype=np.int64).reshape(-1, 6)
+    assert tr.shape == exp_tr.shape, ("sweeps", tr.shape, exp_tr.shape)
+    rows = np.nonzero((tr != exp_tr).any(axis=1))[0]
+    assert rows.shape[0] == 0, ("first differing sweep", tr[rows[0]].tolist(), exp_tr[rows[0]].tolist())
+    assert G.num_levels() == len(gold["levels"])
+    for lv, exp in enumerate(gold["levels"]):
+        ids, K = G.partition(lv)
+        st = G.stats(lv)
+        assert (st.n, K) == (exp["n"], exp["K"]), lv
+        assert _sha(ids) == exp["ids"], f"level {lv} ids differ"
+        assert [st.sweeps, st.status, st.moves, st.splits, st.candidates,
+                st.edges_scanned] == exp["stats"], lv
+    fin, K = G.partition(-1)
+    assert _sha(fin) == gold["final"]["labels"] and K == gold["final"]["K"]
+    q = G.modularity(-1)
+    assert q == float.fromhex(gold["q"])           # same exact numerator, one FP64 division
+    return G
+
+
+def test_rmat_s20_whole_run_equals_oracle():
+    """The benchmark run (R-MAT scale 20, seed 1, p = 1/2, no limits) equals
+    the oracle's complete run level by level, with every sweep of the trace:
+    this covers ASSIGN, POSITIVE (incremental rounds), branch gains, targets,
+    the touched-set COMPONENTS and POSITIVE passes and AGGREGATE at the size
+    where their thresholds switch."""
+    G = compare_with_golden(_rmat(), _golden("rmat_s20"))
+    G.close()
+
+
+def test_rmat_s20_whole_run_timed_flags_equal():
+    """The timed run the benchmark makes (phase timers on) gives the same result."""
+    G = compare_with_golden(_rmat(), _golden("rmat_s20"), flags=slm.FLAG_TIMING)
+    G.close()
+
+
+def test_lfr_4m_bounded_run_equals_oracle():
+    """The 4,194,304-node LFR-style graph with at most 5 sweeps per level and
+    3 levels equals the oracle's bounded run level by level."""
+    G = compare_with_golden(_lfr(), _golden("lfr_4m_bounded"))
+    G.close()
+
+
+def test_lfr_256k_bounded_run_equals_oracle():
+    """A 262,144-node graph of the LFR-style recipe with at most 40 sweeps per
+    level, every level, equals the oracle's run."""
+    G = compare_with_golden(_lfr_256k(), _golden("lfr_256k_bounded"))
+    G.close()
+
+
+def test_run_properties():
     g = _rmat()
     G = slm.Graph(g.row_ptr, g.col, g.w)
     G.run(seed=1, accept_p32=slm.P_HALF)
-    return "rmat_s20", g, G
-
-
-def test_run_properties(runs):
-    name, g, G = runs
     lab, K = G.partition(-1)
     assert lab.shape[0] == g.n and lab.min() >= 0 and lab.max() == K - 1
     assert np.unique(lab).shape[0] == K
@@ -148,35 +174,4 @@ def test_run_properties(runs):
         assert st.status in (0, 1, 2)
     top = G.stats(-1)
     assert top.status in (0, 1) and top.n_communities == top.n
-
-
-def test_lfr_bounded_run():
-    """The LFR-style graph with at most 5 sweeps per level and 3 levels (the
-    method does not settle on it: the oracle on a 16,384-node graph of the same
-    recipe reaches the 1,000-sweep limit at level 0): the run stops at the
-    limits with consistent levels and the oracle's modularity of the GPU
-    partition."""
-    g = _lfr()
-    G = slm.Graph(g.row_ptr, g.col, g.w)
-    G.run(seed=1, accept_p32=slm.P_HALF, max_sweeps=5, max_levels=3)
-    lab, K = G.partition(-1)
-    assert lab.shape[0] == g.n and np.unique(lab).shape[0] == K
-    assert G.modularity(-1) == O.modularity(g, lab)
-    for lv in range(G.num_levels()):
-        st = G.stats(lv)
-        assert st.sweeps <= 5 and st.status in (0, 1, 2)
     G.close()
-
-
-@pytest.mark.skipif(os.environ.get("SLM_FULL_ORACLE") != "1",
-                    reason="complete oracle run at full size: set SLM_FULL_ORACLE=1")
-def test_full_oracle(runs):
-    name, g, G = runs
-    r = O.slm(g, seed=1, P=O.P_HALF)
-    assert G.num_levels() == r.num_levels
-    for lv, (ids, K) in enumerate(r.levels):
-        lab, k = G.partition(lv)
-        assert k == K and np.array_equal(lab, ids), (name, lv)
-    fin, _ = G.partition(-1)
-    assert np.array_equal(fin, r.final)
-    assert G.modularity(-1) == O.modularity(g, r.final)

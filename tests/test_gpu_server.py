@@ -151,3 +151,120 @@ def test_arrivals_while_running(solo):
         lab0, K0, q0 = solo[k]
         assert K == K0 and q == q0 and np.array_equal(lab, lab0)
     sv.close()
+
+
+# --------------------------------------------------------------------------
+# Cancellation, deadlines and injected allocation failures (all on the host:
+# a request stops between sweeps; nothing in flight on the GPU is abandoned)
+# --------------------------------------------------------------------------
+def _long_graph():
+    # the LFR-style recipe does not settle: with a 1,000-sweep limit a run
+    # lasts long enough to be caught while it runs
+    return gg.lfr_style(n=16384)[0]
+
+
+def _until(sv, t, state, limit=60.0):
+    t0 = time.time()
+    while sv.poll(t) != state:
+        assert time.time() - t0 < limit, "state never reached"
+        time.sleep(0.001)
+
+
+def test_cancel_running_and_queued_requests(solo):
+    sv = slm.Server(budget_bytes=8 << 30, slots=1)
+    lg = _long_graph()
+    a = sv.submit(lg.row_ptr, lg.col, lg.w, seed=1, max_sweeps=1000)
+    g, sd, p = REQS[2]
+    b = sv.submit(g.row_ptr, g.col, g.w, seed=sd, accept_p32=p)     # queued behind a
+    _until(sv, a, slm.REQ_RUNNING)
+    sv.cancel(b)                                                     # queued: ends at once
+    assert sv.poll(b) == slm.REQ_FAILED
+    ib = sv.info(b)
+    assert ib.status == 10 and ib.t_admit == 0.0 and ib.slot == -1
+    sv.cancel(a)                                                     # running: next sweep
+    assert sv.wait(a, timeout=60.0)
+    ia = sv.info(a)
+    assert ia.state == slm.REQ_FAILED and ia.status == 10
+    with pytest.raises(slm.SlmError) as e:
+        sv.result(a)
+    assert e.value.name == "SLM_ERR_CANCELLED"
+    # the server goes on; a later request's result is unchanged
+    c = sv.submit(g.row_ptr, g.col, g.w, seed=sd, accept_p32=p)
+    assert sv.wait(c, timeout=60.0)
+    lab, K, q = sv.result(c)
+    lab0, K0, q0 = solo[2]
+    assert K == K0 and q == q0 and np.array_equal(lab, lab0)
+    sv.cancel(c)                                                     # ended: no change
+    st = sv.stats()
+    assert st.failed == 2 and st.completed == 1 and st.reserved_bytes == 0
+    sv.close()
+
+
+def test_deadlines_queued_and_running(solo):
+    sv = slm.Server(budget_bytes=8 << 30, slots=1)
+    lg = _long_graph()
+    a = sv.submit(lg.row_ptr, lg.col, lg.w, seed=1, max_sweeps=1000, deadline=0.4)
+    g, sd, p = REQS[1]
+    b = sv.submit(g.row_ptr, g.col, g.w, seed=sd, accept_p32=p, deadline=0.05)
+    c = sv.submit(g.row_ptr, g.col, g.w, seed=sd, accept_p32=p, deadline=600.0)
+    assert sv.wait(b, timeout=60.0)
+    ib = sv.info(b)
+    assert ib.state == slm.REQ_FAILED and ib.status == 11 and ib.t_admit == 0.0
+    assert sv.wait(a, timeout=60.0)
+    ia = sv.info(a)
+    assert ia.state == slm.REQ_FAILED and ia.status == 11
+    assert ia.t_admit > 0 and ia.t_done - ia.t_submit >= 0.4
+    assert sv.wait(c, timeout=60.0)
+    lab, K, q = sv.result(c)
+    lab0, K0, q0 = solo[1]
+    assert K == K0 and q == q0 and np.array_equal(lab, lab0)
+    with pytest.raises(slm.SlmError):
+        sv.submit(g.row_ptr, g.col, g.w, deadline=-1.0)
+    assert sv.stats().reserved_bytes == 0
+    sv.close()
+
+
+def test_injected_allocation_failure_fails_one_request(solo):
+    sv = slm.Server(budget_bytes=8 << 30, slots=1)
+    g, sd, p = REQS[0]
+    slm.debug_fail_allocation(5)
+    try:
+        t = sv.submit(g.row_ptr, g.col, g.w, seed=sd, accept_p32=p)
+        assert sv.wait(t, timeout=60.0)
+    finally:
+        slm.debug_fail_allocation(0)
+    inf = sv.info(t)
+    assert inf.state == slm.REQ_FAILED and inf.status == 4
+    t2 = sv.submit(g.row_ptr, g.col, g.w, seed=sd, accept_p32=p)
+    assert sv.wait(t2, timeout=60.0)
+    lab, K, q = sv.result(t2)
+    lab0, K0, q0 = solo[0]
+    assert K == K0 and q == q0 and np.array_equal(lab, lab0)
+    assert sv.stats().reserved_bytes == 0
+    sv.close()
+
+
+def test_destroy_while_threads_wait():
+    """Threads blocked in wait() when the server is destroyed return once
+    their request has ended; destroy frees nothing they still use."""
+    import threading
+    sv = slm.Server(budget_bytes=8 << 30, slots=1)
+    lg = _long_graph()
+    ts = [sv.submit(lg.row_ptr, lg.col, lg.w, seed=1, max_sweeps=40) for _ in range(3)]
+    done = []
+    h = sv._h.value
+    lib = slm.load()
+
+    def waiter(t):
+        done.append(lib.slm_server_wait(h, t, -1.0))
+
+    th = [threading.Thread(target=waiter, args=(t,)) for t in ts]
+    for x in th:
+        x.start()
+    _until(sv, ts[0], slm.REQ_RUNNING)
+    time.sleep(0.2)   # every waiter is inside wait() before destroy begins
+    sv.close()
+    for x in th:
+        x.join(timeout=120.0)
+        assert not x.is_alive()
+    assert sorted(done) == [0, 0, 0]
