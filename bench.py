@@ -329,7 +329,7 @@ def run_scan(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    g = load_graph()
+    g = load_graph(args.rmat_scale)
     rp, col, w = (torch.from_numpy(x).to(dev) for x in (g.row_ptr, g.col, g.w))
     s, m = slm.step_strengths(rp, col, w)
     a = slm.step_assign(rp, col, w, s, m)
@@ -352,7 +352,8 @@ def run_scan(args):
                           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": ms, "higher_is_better": True, "dtype": "int64",
                           "data": "synthetic",
-                          "config": {"workload": WORKLOAD + "_scan_level0", "n": g.n, "nnz": g.nnz},
+                          "config": {"workload": f"rmat_s{args.rmat_scale}_scan_level0", "n": g.n,
+                                     "nnz": g.nnz},
                           "frac_of_peak": gbs / hbm, "peak_source": kind}), flush=True)
     return 0
 

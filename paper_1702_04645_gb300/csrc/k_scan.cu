@@ -3,22 +3,24 @@
 //  * scan_nodes: the per-node half of MAXIMAL (Section 3.4, Algorithm
 //    MAXIMAL's c_i^* = argmax_c Delta H(c_i -> i -> c)): accumulate the weight
 //    k_{i,C} from node i to every neighbouring community C and pick the best
-//    by the exact score m_w k_{i,C} - s_i Sigma_C (Section 2.4).
+//    by the exact score m_w k_{i,C} - s_i Sigma_C (Section 2.4).  Rows of up
+//    to 4096 entries are scanned by the kernels of k_scan_fine.cu; hubs by
+//    the global-table kernels here.
 //  * assign_nodes: ASSIGN (Section 3.1): best neighbour by m_w W_ij - s_i s_j.
 //  * target_nodes: the new assignment a(i) = argmax_{j in c_i^*} of the same
 //    pair score (Algorithm MAXIMAL).
 //  * own_weight_nodes: k_{i,c_i} and the local gain g(i) of POSITIVE
 //    (Section 3.3, Algorithm POSITIVE).
 //
-// Degree buckets pick the shape: groups of 4/8/16/32 lanes with one edge per
-// lane (communities grouped by shuffles), one warp per node with a shared-
-// memory open-addressing table (33..256 edges), one block per node with a
-// shared-memory table (257..4096 edges) or a global-memory table (hubs).
+// Degree buckets pick the shape of ASSIGN, the own weights and the scan: lane
+// groups or warps for short rows, blocks for long ones, and for hubs (more
+// than 4096 entries) a global-memory table shared by the blocks of a row.
 // Every reduction compares (score desc, name asc), so the result does not
 // depend on the order in which lanes or blocks finish.
 #include <algorithm>
-#include <mutex>
 #include <climits>
+#include <initializer_list>
+#include <mutex>
 
 #include "slm_internal.cuh"
 
@@ -29,21 +31,30 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kHubSlice = 2048;  // hub table slots read by one block
 constexpr int kBlockThreads = 256;
-constexpr int kWarpHashCap = 2 * kWarpHashMaxDeg;
-constexpr int kWarpHashWarps = 8;  // warps per block in the warp-hash kernel
 
-__device__ __forceinline__ int bucket_of(int d) {
-    if (d == 0) return kBucketEmpty;
-    if (d <= 4) return kBucketG4;
-    if (d <= 8) return kBucketG8;
-    if (d <= 16) return kBucketG16;
-    if (d <= 32) return kBucketG32;
-    if (d <= kWarpHashMaxDeg) return kBucketWarpHash;
-    if (d <= kBlockSmallMaxDeg) return kBucketBlockS;
-    if (d <= kBlockMidMaxDeg) return kBucketBlockM;
-    if (d <= kBlockSmemMaxDeg) return kBucketBlockL;
-    return kBucketHub;
+__device__ __forceinline__ int fine_of(int d) {
+    if (d == 0) return kFineEmpty;
+    if (d <= 4) return kFine4;
+    if (d <= 8) return kFine8;
+    if (d <= 16) return kFine16;
+    if (d <= 32) return kFine32;
+    if (d <= 64) return kFine64;
+    if (d <= 128) return kFine128;
+    if (d <= 256) return kFine256;
+    if (d <= 512) return kFine512;
+    if (d <= 1024) return kFine1024;
+    if (d <= 2048) return kFine2048;
+    if (d <= kBlockSmemMaxDeg) return kFine4096;
+    return kFineHub;
 }
+
+// coarse bucket of every fine class
+constexpr int kCoarseOf[kNumFine] = {kBucketEmpty, kBucketG4, kBucketG8, kBucketG16, kBucketG32,
+                                     kBucketWarpHash, kBucketWarpHash, kBucketWarpHash,
+                                     kBucketBlockS, kBucketBlockS, kBucketBlockM, kBucketBlockL,
+                                     kBucketHub};
+static_assert(kWarpHashMaxDeg == 256 && kBlockSmallMaxDeg == 1024 && kBlockMidMaxDeg == 2048,
+              "coarse buckets must be unions of fine classes");
 
 __device__ __forceinline__ bool better(long long sc, int c, long long bsc, int bc) {
     return sc > bsc || (sc == bsc && c < bc);
@@ -53,11 +64,6 @@ __device__ __forceinline__ unsigned hash_slot(int c, int lg) {
     return ((unsigned)c * 2654435761u) >> (32 - lg);
 }
 
-__device__ __forceinline__ int ilog2_pow2_at_least(int x) {
-    int lg = 0;
-    while ((1 << lg) < x) lg++;
-    return lg;
-}
 
 // Decision shared by every scan shape.
 __device__ __forceinline__ void scan_emit(int i, int ci, int si, long long m, const int32_t *sigma,
@@ -88,194 +94,19 @@ __device__ __forceinline__ void count_add(unsigned long long *ctr, unsigned v) {
 // bucket keys of all n nodes (list == nullptr) or of the n listed nodes
 __global__ void k_bucket_keys(int32_t n, const int32_t *list, const int32_t *rp, uint32_t *keys,
                               int32_t *vals, int32_t *counts) {
-    __shared__ int loc[kNumBuckets];
-    if (threadIdx.x < kNumBuckets) loc[threadIdx.x] = 0;
+    __shared__ int loc[kNumFine];
+    if (threadIdx.x < kNumFine) loc[threadIdx.x] = 0;
     __syncthreads();
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int v = list ? list[k] : (int)k;
-        int b = bucket_of(rp[v + 1] - rp[v]);
+        int b = fine_of(rp[v + 1] - rp[v]);
         keys[k] = (uint32_t)b;
         vals[k] = v;
         atomicAdd(&loc[b], 1);
     }
     __syncthreads();
-    if (threadIdx.x < kNumBuckets && loc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], loc[threadIdx.x]);
-}
-
-// ---------------------------------------------------------------------------
-// MAXIMAL scan, group shape: G lanes per node, one edge per lane.
-// ---------------------------------------------------------------------------
-template <int G>
-__global__ void __launch_bounds__(256) k_scan_group(const int32_t *order, int32_t cnt, const int32_t *rp,
-                             const int32_t *col, const int32_t *w, const int32_t *s, MParam mp,
-                             const int32_t *root, const int32_t *sigma, int32_t *best,
-                             long long *gain, int32_t *kown, unsigned long long *ncand) {
-    constexpr int NPW = 32 / G;  // nodes per warp
-    const int lane = threadIdx.x & 31, gl = lane % G, gbase = lane - gl;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    unsigned cand = 0;
-    for (long long base = warp * NPW; base < cnt; base += nwarps * NPW) {
-        long long idx = base + lane / G;
-        bool vn = idx < cnt;
-        int i = vn ? order[idx] : 0;
-        const long long m = mp.of(i);
-        int start = vn ? rp[i] : 0;
-        int deg = vn ? rp[i + 1] - start : 0;
-        int ci = vn ? root[i] : -1;
-        int c = -1, wv = 0;
-        if (gl < deg) {
-            int j = col[start + gl];
-            if (j != i) {
-                c = root[j];
-                wv = w[start + gl];
-            }
-        }
-        int sum = 0;
-        bool first = true;
-#pragma unroll
-        for (int k = 0; k < G; k++) {
-            int ck = __shfl_sync(FULL, c, gbase + k);
-            int wk = __shfl_sync(FULL, wv, gbase + k);
-            if (ck == c) {
-                sum += wk;
-                if (k < gl) first = false;
-            }
-        }
-        long long own = (c >= 0 && c == ci && first) ? sum : 0;
-        long long sc = LLONG_MIN;
-        int cc = INT_MAX;
-        int si = vn ? s[i] : 0;
-        if (c >= 0 && c != ci && first) {
-            sc = m * (long long)sum - (long long)si * (long long)sigma[c];
-            cc = c;
-        }
-#pragma unroll
-        for (int o = G / 2; o; o >>= 1) {
-            own += __shfl_xor_sync(FULL, own, o);
-            long long osc = __shfl_xor_sync(FULL, sc, o);
-            int occ = __shfl_xor_sync(FULL, cc, o);
-            if (better(osc, occ, sc, cc)) { sc = osc; cc = occ; }
-        }
-        if (gl == 0 && vn) scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
-    }
-    count_add(ncand, cand);
-}
-
-// ---------------------------------------------------------------------------
-// Row prefetch shared by the warp and block shapes: the first batch of the
-// next node's row (its header, entries and their communities) is loaded
-// while the current node is decided, so the loads of consecutive nodes
-// overlap instead of waiting one after the other.
-// ---------------------------------------------------------------------------
-struct RowHead {
-    int i, start, end, ci, si;
-};
-
-template <int B>
-__device__ __forceinline__ void load_batch(const RowHead &h, int p0, int stride, const int32_t *col,
-                                           const int32_t *w, const int32_t *root, int (&cv)[B],
-                                           int (&wv)[B]) {
-#pragma unroll
-    for (int t = 0; t < B; t++) {
-        int p = p0 + t * stride;
-        bool ok = p < h.end;
-        cv[t] = ok ? col[p] : -1;
-        wv[t] = ok ? w[p] : 0;
-    }
-#pragma unroll
-    for (int t = 0; t < B; t++) cv[t] = (cv[t] >= 0 && cv[t] != h.i) ? root[cv[t]] : -1;
-}
-
-__device__ __forceinline__ RowHead load_head(const int32_t *order, long long idx, long long cnt,
-                                             const int32_t *rp, const int32_t *root,
-                                             const int32_t *s) {
-    RowHead h{-1, 0, 0, -1, 0};
-    if (idx < cnt) {
-        h.i = order[idx];
-        h.start = rp[h.i];
-        h.end = rp[h.i + 1];
-        h.ci = root[h.i];
-        h.si = s[h.i];
-    }
-    return h;
-}
-
-// ---------------------------------------------------------------------------
-// MAXIMAL scan, warp shape: one node per warp, shared-memory table.  The
-// slots a node occupies are listed as they are claimed, so the decision pass
-// and the reset touch only the distinct communities, not the whole table.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWarpHashWarps * 32, 5) k_scan_warphash(const int32_t *order, int32_t cnt, const int32_t *rp,
-                                const int32_t *col, const int32_t *w, const int32_t *s,
-                                MParam mp, const int32_t *root, const int32_t *sigma,
-                                int32_t *best, long long *gain, int32_t *kown,
-                                unsigned long long *ncand) {
-    __shared__ int tab[kWarpHashWarps][2 * kWarpHashCap];
-    __shared__ unsigned short used[kWarpHashWarps][kWarpHashMaxDeg];
-    __shared__ int nused[kWarpHashWarps];
-    constexpr int B = kWarpHashMaxDeg / 32;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int *keys = tab[wib], *vals = tab[wib] + kWarpHashCap;
-    unsigned short *ul = used[wib];
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (int k = lane; k < kWarpHashCap; k += 32) { keys[k] = -1; vals[k] = 0; }
-    if (lane == 0) nused[wib] = 0;
-    __syncwarp();
-    unsigned cand = 0;
-    long long idx = warp;
-    RowHead h = load_head(order, idx, cnt, rp, root, s);
-    int cv[B], wv[B];
-    load_batch<B>(h, h.start + lane, 32, col, w, root, cv, wv);
-    for (; idx < cnt; idx += nwarps) {
-        const int i = h.i, ci = h.ci, si = h.si;
-        const long long m = mp.of(i);
-        const int lg = ilog2_pow2_at_least(2 * (h.end - h.start));
-        const int cap = 1 << lg;
-#pragma unroll
-        for (int t = 0; t < B; t++) {
-            if (cv[t] < 0) continue;
-            unsigned hs = hash_slot(cv[t], lg);
-            for (;;) {
-                int prev = atomicCAS(&keys[hs], -1, cv[t]);
-                if (prev == -1) ul[atomicAdd(&nused[wib], 1)] = (unsigned short)hs;
-                if (prev == -1 || prev == cv[t]) { atomicAdd(&vals[hs], wv[t]); break; }
-                hs = (hs + 1) & (cap - 1);
-            }
-        }
-        __syncwarp();
-        // the next node's row is in flight while this one is decided
-        const RowHead hn = load_head(order, idx + nwarps, cnt, rp, root, s);
-        load_batch<B>(hn, hn.start + lane, 32, col, w, root, cv, wv);
-        const int nu = nused[wib];
-        long long own = 0, sc = LLONG_MIN;
-        int cc = INT_MAX;
-        for (int k = lane; k < nu; k += 32) {
-            int hs = ul[k];
-            int c = keys[hs], v = vals[hs];
-            keys[hs] = -1;  // leave the table empty for the next node
-            vals[hs] = 0;
-            if (c == ci) { own = v; continue; }
-            long long x = m * (long long)v - (long long)si * (long long)sigma[c];
-            if (better(x, c, sc, cc)) { sc = x; cc = c; }
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            own += __shfl_xor_sync(FULL, own, o);
-            long long osc = __shfl_xor_sync(FULL, sc, o);
-            int occ = __shfl_xor_sync(FULL, cc, o);
-            if (better(osc, occ, sc, cc)) { sc = osc; cc = occ; }
-        }
-        if (lane == 0) {
-            scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
-            nused[wib] = 0;
-        }
-        __syncwarp();
-        h = hn;
-    }
-    count_add(ncand, cand);
+    if (threadIdx.x < kNumFine && loc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], loc[threadIdx.x]);
 }
 
 // Block-wide argmax + sum; result valid in thread 0.
@@ -307,82 +138,6 @@ __device__ void block_reduce_best(long long &own, long long &sc, int &cc) {
     __syncthreads();
 }
 
-// ---------------------------------------------------------------------------
-// MAXIMAL scan, block shape: one node per block, table of CAP slots in
-// shared memory followed by the list of occupied slots; every thread fetches
-// its edges in batches of 8.
-// ---------------------------------------------------------------------------
-template <int CAP>
-constexpr size_t block_smem_bytes() {
-    return sizeof(int) * 2 * CAP + sizeof(unsigned short) * (CAP / 2) + 16;
-}
-
-template <int CAP>
-__global__ void __launch_bounds__(kBlockThreads, CAP <= 2 * kBlockMidMaxDeg ? 6 : 3) k_scan_block(const int32_t *order, int32_t cnt, const int32_t *rp,
-                             const int32_t *col, const int32_t *w, const int32_t *s, MParam mp,
-                             const int32_t *root, const int32_t *sigma, int32_t *best,
-                             long long *gain, int32_t *kown, unsigned long long *ncand) {
-    extern __shared__ int sm[];
-    int *keys = sm, *vals = sm + CAP;
-    unsigned short *ul = reinterpret_cast<unsigned short *>(sm + 2 * CAP);
-    int *nused = reinterpret_cast<int *>(ul + CAP / 2);
-    constexpr int B = 8;
-    for (int k = threadIdx.x; k < CAP; k += blockDim.x) { keys[k] = -1; vals[k] = 0; }
-    if (threadIdx.x == 0) *nused = 0;
-    __syncthreads();
-    unsigned cand = 0;
-    long long idx = blockIdx.x;
-    RowHead h = load_head(order, idx, cnt, rp, root, s);
-    int cv[B], wv[B];
-    load_batch<B>(h, h.start + threadIdx.x, blockDim.x, col, w, root, cv, wv);
-    for (; idx < cnt; idx += gridDim.x) {
-        const int i = h.i, ci = h.ci, si = h.si;
-        const long long m = mp.of(i);
-        const int lg = ilog2_pow2_at_least(2 * (h.end - h.start));
-        const int cap = 1 << lg;  // <= CAP because deg <= CAP / 2
-        for (int p0 = h.start + threadIdx.x;;) {
-#pragma unroll
-            for (int t = 0; t < B; t++) {
-                if (cv[t] < 0) continue;
-                unsigned hs = hash_slot(cv[t], lg);
-                for (;;) {
-                    int prev = atomicCAS(&keys[hs], -1, cv[t]);
-                    if (prev == -1) ul[atomicAdd(nused, 1)] = (unsigned short)hs;
-                    if (prev == -1 || prev == cv[t]) { atomicAdd(&vals[hs], wv[t]); break; }
-                    hs = (hs + 1) & (cap - 1);
-                }
-            }
-            p0 += B * blockDim.x;
-            if (p0 >= h.end) break;
-            load_batch<B>(h, p0, blockDim.x, col, w, root, cv, wv);
-        }
-        __syncthreads();
-        // the next node's first batch is in flight while this one is decided
-        const RowHead hn = load_head(order, idx + gridDim.x, cnt, rp, root, s);
-        load_batch<B>(hn, hn.start + threadIdx.x, blockDim.x, col, w, root, cv, wv);
-        const int nu = *nused;
-        long long own = 0, sc = LLONG_MIN;
-        int cc = INT_MAX;
-        for (int k = threadIdx.x; k < nu; k += blockDim.x) {
-            int hs = ul[k];
-            int c = keys[hs], v = vals[hs];
-            keys[hs] = -1;  // leave the table empty for the next node
-            vals[hs] = 0;
-            if (c == ci) { own = v; continue; }
-            long long x = m * (long long)v - (long long)si * (long long)sigma[c];
-            if (better(x, c, sc, cc)) { sc = x; cc = c; }
-        }
-        block_reduce_best(own, sc, cc);
-        if (threadIdx.x == 0) {
-            scan_emit(i, ci, si, m, sigma, own, sc, cc, best, gain, kown, cand);
-            *nused = 0;
-        }
-        __syncthreads();
-        h = hn;
-    }
-    if (threadIdx.x == 0 && cand) atomicAdd(ncand, (unsigned long long)cand);
-}
-
 __global__ void k_scan_empty(const int32_t *order, int32_t cnt, const int32_t *root,
                              int32_t *best, long long *gain, int32_t *kown) {
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < cnt;
@@ -402,42 +157,82 @@ __global__ void k_scan_empty(const int32_t *order, int32_t cnt, const int32_t *r
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks, int nchunk, const int32_t *hubs,
                              const long long *hoff, const int32_t *hlg, const long long *uoff,
-                             const int32_t *col, const int32_t *w, const int32_t *root, int *tkeys,
-                             int *tvals, int *ulist, int *ucnt) {
+                             const int32_t *col, const int32_t *w, const int32_t *root,
+                             unsigned long long *tslot, int *ulist, int *ucnt,
+                             unsigned long long *own_acc) {
+    // a chunk is at most kHubChunk = 8 * kBlockThreads entries: eight per
+    // thread, loaded and inserted together so that their atomics overlap
+    constexpr int B = kHubChunk / kBlockThreads;
+    __shared__ unsigned long long red[kBlockThreads / 32];
+    const int lane = threadIdx.x & 31;
     for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
-        int4 ch = chunks[c];  // (hub index, first edge, end edge, unused)
+        const int4 ch = chunks[c];  // (hub index, first edge, end edge, unused)
         const int i = hubs[ch.x];
+        const int ci = root[i];
         const int lg = hlg[ch.x];
-        const int cap = 1 << lg;
-        int *keys = tkeys + hoff[ch.x], *vals = tvals + hoff[ch.x];
+        const unsigned mask = (1u << lg) - 1u;
+        unsigned long long *T = tslot + hoff[ch.x];
         int *ul = ulist + uoff[ch.x];
-        // the row's chunk is covered in whole warps so that the claimed slots
-        // of a warp are listed with one atomic on the hub's count
-        for (int p0 = ch.y + (threadIdx.x & ~31); p0 < ch.z; p0 += blockDim.x) {
-            const int p = p0 + (threadIdx.x & 31);
+        int cc[B], wv[B];
+#pragma unroll
+        for (int t = 0; t < B; t++) {
+            const int p = ch.y + threadIdx.x + t * kBlockThreads;
+            const int j = p < ch.z ? col[p] : i;
+            wv[t] = p < ch.z ? w[p] : 0;
+            cc[t] = j;
+        }
+#pragma unroll
+        for (int t = 0; t < B; t++) cc[t] = cc[t] != i ? root[cc[t]] : -1;
+        // the own community never enters the table (all of a star's leaves
+        // would hit its one slot): summed per block, one atomic per chunk
+        unsigned long long own = 0;
+        unsigned long long old[B];
+        unsigned h[B];
+#pragma unroll
+        for (int t = 0; t < B; t++) {
+            if (cc[t] == ci) own += (unsigned long long)wv[t];
+            const bool ins = cc[t] >= 0 && cc[t] != ci;
+            h[t] = ins ? (((unsigned)cc[t] * 2654435761u) >> (32 - lg)) : 0u;
+            old[t] = ins ? atomicCAS(&T[h[t]], 0ull,
+                                     ((unsigned long long)(unsigned)(cc[t] + 1) << 32) | (unsigned)wv[t])
+                         : 1ull;
+        }
+#pragma unroll
+        for (int t = 0; t < B; t++) {
             int claimed = -1;
-            if (p < ch.z) {
-                const int j = col[p];
-                if (j != i) {
-                    const int cc = root[j], wv = w[p];
-                    unsigned h = hash_slot(cc, lg);
-                    for (;;) {
-                        int prev = atomicCAS(&keys[h], -1, cc);
-                        if (prev == -1) claimed = (int)h;
-                        if (prev == -1 || prev == cc) { atomicAdd(&vals[h], wv); break; }
-                        h = (h + 1) & (cap - 1);
+            if (cc[t] >= 0 && cc[t] != ci) {
+                const unsigned long long key = (unsigned long long)(unsigned)(cc[t] + 1) << 32;
+                unsigned long long o = old[t];
+                unsigned hh = h[t];
+                for (;;) {
+                    if (o == 0ull) { claimed = (int)hh; break; }
+                    if ((o & 0xffffffff00000000ull) == key) {
+                        atomicAdd(&T[hh], (unsigned long long)(unsigned)wv[t]);
+                        break;
                     }
+                    hh = (hh + 1) & mask;
+                    o = atomicCAS(&T[hh], 0ull, key | (unsigned)wv[t]);
                 }
             }
+            // the claimed slots of a warp are listed with one atomic on the hub's count
             const unsigned bal = __ballot_sync(FULL, claimed >= 0);
             if (bal) {
-                const int lane = threadIdx.x & 31;
                 int at = 0;
                 if (lane == 0) at = atomicAdd(&ucnt[ch.x], __popc(bal));
                 at = __shfl_sync(FULL, at, 0);
                 if (claimed >= 0) ul[at + __popc(bal & ((1u << lane) - 1u))] = claimed;
             }
         }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
+        if (lane == 0) red[threadIdx.x >> 5] = own;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int k = 0; k < kBlockThreads / 32; k++) t += red[k];
+            if (t) atomicAdd(&own_acc[ch.x], t);
+        }
+        __syncthreads();
     }
 }
 
@@ -447,7 +242,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks
 __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunks, int ntchunk, const int32_t *hubs,
                              const long long *hoff, const long long *uoff, const int *ulist,
                              const int *ucnt, const int32_t *s, MParam mp, const int32_t *root,
-                             const int32_t *sigma, int *tkeys, int *tvals, long long *part_own,
+                             const int32_t *sigma, unsigned long long *tslot,
                              long long *part_sc, int32_t *part_cc) {
     constexpr int B = kHubSlice / kBlockThreads;
     for (int tc = blockIdx.x; tc < ntchunk; tc += gridDim.x) {
@@ -456,7 +251,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunk
         const long long m = mp.of(i);
         const int ci = root[i], si = s[i];
         const int nu = ucnt[d.x];
-        int *keys = tkeys + hoff[d.x], *vals = tvals + hoff[d.x];
+        unsigned long long *T = tslot + hoff[d.x];
         const int *ul = ulist + uoff[d.x];
         int hh[B], kk[B], vv[B], sg[B];
 #pragma unroll
@@ -466,26 +261,24 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunk
         }
 #pragma unroll
         for (int t = 0; t < B; t++) {
-            kk[t] = hh[t] >= 0 ? keys[hh[t]] : -1;
-            vv[t] = hh[t] >= 0 ? vals[hh[t]] : 0;
+            const unsigned long long v = hh[t] >= 0 ? T[hh[t]] : 0ull;
+            kk[t] = (int)(v >> 32) - 1;  // -1: no slot
+            vv[t] = (int)(unsigned)v;
         }
 #pragma unroll
-        for (int t = 0; t < B; t++) sg[t] = (kk[t] >= 0 && kk[t] != ci) ? sigma[kk[t]] : 0;
+        for (int t = 0; t < B; t++) sg[t] = kk[t] >= 0 ? sigma[kk[t]] : 0;
         long long own = 0, sc = LLONG_MIN;
         int cc = INT_MAX;
 #pragma unroll
         for (int t = 0; t < B; t++) {
             int c = kk[t];
             if (c < 0) continue;
-            keys[hh[t]] = -1;  // leave the table empty for the next sweep
-            vals[hh[t]] = 0;
-            if (c == ci) { own = vv[t]; continue; }
+            T[hh[t]] = 0ull;  // leave the table empty for the next sweep
             long long x = m * (long long)vv[t] - (long long)si * (long long)sg[t];
             if (better(x, c, sc, cc)) { sc = x; cc = c; }
         }
         block_reduce_best(own, sc, cc);
         if (threadIdx.x == 0) {
-            part_own[tc] = own;
             part_sc[tc] = sc;
             part_cc[tc] = cc;
         }
@@ -493,7 +286,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunk
 }
 __global__ void k_hub_finish(int nhub, const int32_t *hubs, const int32_t *tc_off, const int32_t *s,
                              MParam mp, const int32_t *root, const int32_t *sigma,
-                             const long long *part_own, const long long *part_sc,
+                             unsigned long long *own_acc, const long long *part_sc,
                              const int32_t *part_cc, int *ucnt, int32_t *best, long long *gain,
                              int32_t *kown, unsigned long long *ncand) {
     const int lane = threadIdx.x & 31;
@@ -503,22 +296,21 @@ __global__ void k_hub_finish(int nhub, const int32_t *hubs, const int32_t *tc_of
     for (long long h = warp; h < nhub; h += nwarps) {
         const int i = hubs[h];
         const long long m = mp.of(i);
-        long long own = 0, sc = LLONG_MIN;
+        long long sc = LLONG_MIN;
         int cc = INT_MAX;
-        for (int t = tc_off[h] + lane; t < tc_off[h + 1]; t += 32) {
-            own += part_own[t];
+        for (int t = tc_off[h] + lane; t < tc_off[h + 1]; t += 32)
             if (better(part_sc[t], part_cc[t], sc, cc)) { sc = part_sc[t]; cc = part_cc[t]; }
-        }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
-            own += __shfl_xor_sync(FULL, own, o);
             long long osc = __shfl_xor_sync(FULL, sc, o);
             int occ = __shfl_xor_sync(FULL, cc, o);
             if (better(osc, occ, sc, cc)) { sc = osc; cc = occ; }
         }
         if (lane == 0) {
+            const long long own = (long long)own_acc[h];
             scan_emit(i, root[i], s[i], m, sigma, own, sc, cc, best, gain, kown, cand);
-            ucnt[h] = 0;  // the hub's slot list starts empty at the next scan
+            ucnt[h] = 0;     // the hub's slot list starts empty at the next scan
+            own_acc[h] = 0;  // and so does its own-community sum
         }
     }
     count_add(ncand, cand);
@@ -759,6 +551,7 @@ void local_gain_nodes(int32_t n, const int32_t *s, MParam m, const int32_t *root
 // Host side
 // ---------------------------------------------------------------------------
 Buckets::~Buckets() {
+    if (cs_tex) cudaDestroyTextureObject(cs_tex);
     for (int k = 0; k < kSide; k++) {
         if (side[k]) cudaStreamDestroy(side[k]);
         if (join[k]) cudaEventDestroy(join[k]);
@@ -780,20 +573,27 @@ void Buckets::build_list(int32_t n, const int32_t *list, const int32_t *rp, cuda
         SLM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     }
     for (int b = 0; b <= kNumBuckets; b++) off[b] = 0;
+    for (int b = 0; b <= kNumFine; b++) foff[b] = 0;
+    lay_ready = false;
     order.ensure(sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s);
     if (n <= 0) return;
     DevBuf keys(sizeof(uint32_t) * n, s), keys_tmp(sizeof(uint32_t) * n, s),
-        vals_tmp(sizeof(int32_t) * n, s), counts(sizeof(int32_t) * kNumBuckets, s);
+        vals_tmp(sizeof(int32_t) * n, s), counts(sizeof(int32_t) * kNumFine, s);
     SLM_CUDA(cudaMemsetAsync(counts.get(), 0, counts.bytes(), s));
     k_bucket_keys<<<grid_for(n, 256), 256, 0, s>>>(n, list, rp, keys.as<uint32_t>(), order.as<int32_t>(),
                                                    counts.as<int32_t>());
     SLM_LAUNCH_CHECK();
     radix_sort_u32(keys.as<uint32_t>(), order.as<int32_t>(), keys_tmp.as<uint32_t>(),
                    vals_tmp.as<int32_t>(), n, 4, s);
-    int32_t h[kNumBuckets];
+    int32_t h[kNumFine];
     SLM_CUDA(cudaMemcpyAsync(h, counts.get(), sizeof h, cudaMemcpyDeviceToHost, s));
     slm::stream_sync(s);
-    for (int b = 0; b < kNumBuckets; b++) off[b + 1] = off[b] + h[b];
+    int32_t hc[kNumBuckets] = {0};
+    for (int b = 0; b < kNumFine; b++) {
+        foff[b + 1] = foff[b] + h[b];
+        hc[kCoarseOf[b]] += h[b];
+    }
+    for (int b = 0; b < kNumBuckets; b++) off[b + 1] = off[b] + hc[b];
     // hubs: table offsets and chunk list, built on the host (hubs are few)
     nhub = off[kBucketHub + 1] - off[kBucketHub];
     nchunk = 0;
@@ -835,7 +635,6 @@ void Buckets::build_list(int32_t n, const int32_t *list, const int32_t *rp, cuda
         ntchunk = (int32_t)tch.size();
         tchunks.alloc(sizeof(int2) * tch.size(), s);
         tc_off.alloc(sizeof(int32_t) * (nhub + 1), s);
-        part_own.alloc(sizeof(long long) * tch.size(), s);
         part_sc.alloc(sizeof(long long) * tch.size(), s);
         part_cc.alloc(sizeof(int32_t) * tch.size(), s);
         SLM_CUDA(cudaMemcpyAsync(tchunks.get(), tch.data(), sizeof(int2) * tch.size(), cudaMemcpyHostToDevice, s));
@@ -845,14 +644,14 @@ void Buckets::build_list(int32_t n, const int32_t *list, const int32_t *rp, cuda
         hub_lg.alloc(sizeof(int32_t) * nhub, s);
         chunks.alloc(sizeof(int4) * ch.size(), s);
         hub_acc.alloc(sizeof(unsigned long long) * nhub, s);
-        tkeys.alloc(sizeof(int) * tot, s);
-        tvals.alloc(sizeof(int) * tot, s);
+        hub_own.alloc(sizeof(unsigned long long) * nhub, s);
+        tslot.alloc(sizeof(unsigned long long) * tot, s);
         SLM_CUDA(cudaMemcpyAsync(hub_off.get(), hoff.data(), sizeof(long long) * nhub, cudaMemcpyHostToDevice, s));
         SLM_CUDA(cudaMemcpyAsync(hub_lg.get(), hlg.data(), sizeof(int32_t) * nhub, cudaMemcpyHostToDevice, s));
         SLM_CUDA(cudaMemcpyAsync(chunks.get(), ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice, s));
         // the tables start empty and every scan leaves them empty
-        SLM_CUDA(cudaMemsetAsync(tkeys.get(), 0xff, sizeof(int) * tot, s));
-        SLM_CUDA(cudaMemsetAsync(tvals.get(), 0, sizeof(int) * tot, s));
+        SLM_CUDA(cudaMemsetAsync(tslot.get(), 0, sizeof(unsigned long long) * tot, s));
+        SLM_CUDA(cudaMemsetAsync(hub_own.get(), 0, sizeof(unsigned long long) * nhub, s));
         slm::stream_sync(s);  // host vectors go out of scope
     }
 }
@@ -928,6 +727,9 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
     auto cnt = [&](int b) { return bk.off[b + 1] - bk.off[b]; };
     const ScanTuning tu = scan_tuning();
     const bool side = tu.streams > 1;
+    Buckets &bl = const_cast<Buckets &>(bk);
+    build_scan_layout(bl, n, rp, col, w, s, st);
+    pack_community_totals(n, root, sigma, bl.cs.as<int2>(), st);
     // the buckets write disjoint nodes: run them side by side
     if (side) {
         SLM_CUDA(cudaEventRecord(bk.fork, st));
@@ -949,81 +751,41 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
         const int32_t *hubs = ord + bk.off[kBucketHub];
         k_hub_insert<<<grid_for(bk.nchunk, 1, kNumSMs * tu.blocks_hub), kBlockThreads, 0, s3>>>(
             bk.chunks.as<int4>(), bk.nchunk, hubs, bk.hub_off.as<long long>(), bk.hub_lg.as<int32_t>(),
-            bk.hub_uoff.as<long long>(), col, w, root, bk.tkeys.as<int>(), bk.tvals.as<int>(),
-            bk.ulist.as<int>(), bk.hub_ucnt.as<int>());
+            bk.hub_uoff.as<long long>(), col, w, root, bk.tslot.as<unsigned long long>(),
+            bk.ulist.as<int>(), bk.hub_ucnt.as<int>(), bk.hub_own.as<unsigned long long>());
         SLM_LAUNCH_CHECK();
         k_hub_slices<<<grid_for(bk.ntchunk, 1, kNumSMs * tu.blocks_hub), kBlockThreads, 0, s3>>>(
             bk.tchunks.as<int2>(), bk.ntchunk, hubs, bk.hub_off.as<long long>(),
             bk.hub_uoff.as<long long>(), bk.ulist.as<int>(), bk.hub_ucnt.as<int>(), s, m, root, sigma,
-            bk.tkeys.as<int>(), bk.tvals.as<int>(), bk.part_own.as<long long>(),
+            bk.tslot.as<unsigned long long>(),
             bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>());
         SLM_LAUNCH_CHECK();
         k_hub_finish<<<grid_for((long long)bk.nhub * 32, 256), 256, 0, s3>>>(
-            bk.nhub, hubs, bk.tc_off.as<int32_t>(), s, m, root, sigma, bk.part_own.as<long long>(),
+            bk.nhub, hubs, bk.tc_off.as<int32_t>(), s, m, root, sigma, bk.hub_own.as<unsigned long long>(),
             bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>(), bk.hub_ucnt.as<int>(), best, gain,
             kown, ncand);
         SLM_LAUNCH_CHECK();
         mark(kBucketHub, 1, s3);
     }
-    if (int c = cnt(kBucketBlockL)) {
-        mark(kBucketBlockL, 0, s0);
-        constexpr int CAP = 2 * kBlockSmemMaxDeg;
-        const size_t smem = block_smem_bytes<CAP>();
-        allow_smem(k_scan_block<CAP>, smem, 0);
-        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * tu.blocks_large), kBlockThreads, smem, s0>>>(
-            ord + bk.off[kBucketBlockL], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-        mark(kBucketBlockL, 1, s0);
-    }
-    if (int c = cnt(kBucketBlockM)) {
-        mark(kBucketBlockM, 0, s0);
-        constexpr int CAP = 2 * kBlockMidMaxDeg;
-        const size_t smem = block_smem_bytes<CAP>();
-        allow_smem(k_scan_block<CAP>, smem, 1);
-        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * tu.blocks_mid), kBlockThreads, smem, s0>>>(
-            ord + bk.off[kBucketBlockM], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-        mark(kBucketBlockM, 1, s0);
-    }
-    if (int c = cnt(kBucketWarpHash)) {
-        mark(kBucketWarpHash, 0, s1);
-        k_scan_warphash<<<grid_for((long long)c * 32, kWarpHashWarps * 32, kNumSMs * tu.blocks_warp), kWarpHashWarps * 32, 0, s1>>>(
-            ord + bk.off[kBucketWarpHash], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-        mark(kBucketWarpHash, 1, s1);
-    }
-    if (int c = cnt(kBucketBlockS)) {
-        mark(kBucketBlockS, 0, s2);
-        constexpr int CAP = 2 * kBlockSmallMaxDeg;
-        k_scan_block<CAP><<<grid_for(c, 1, kNumSMs * tu.blocks_small), kBlockThreads, block_smem_bytes<CAP>(), s2>>>(
-            ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-        mark(kBucketBlockS, 1, s2);
-    }
-    if (int c = cnt(kBucketG16)) {
-        mark(kBucketG16, 0, s2);
-        k_scan_group<16><<<blocks_for_groups(c, 2, 256, tu.blocks_group), 256, 0, s2>>>(ord + bk.off[kBucketG16], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-        mark(kBucketG16, 1, s2);
-    }
-    if (int c = cnt(kBucketG32)) {
-        mark(kBucketG32, 0, s2);
-        k_scan_group<32><<<blocks_for_groups(c, 1, 256, tu.blocks_group), 256, 0, s2>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-        mark(kBucketG32, 1, s2);
-    }
-    if (int c = cnt(kBucketG4)) {
-        mark(kBucketG4, 0, s3);
-        k_scan_group<4><<<blocks_for_groups(c, 8, 256, tu.blocks_group), 256, 0, s3>>>(ord + bk.off[kBucketG4], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-        mark(kBucketG4, 1, s3);
-    }
-    if (int c = cnt(kBucketG8)) {
-        mark(kBucketG8, 0, s3);
-        k_scan_group<8><<<blocks_for_groups(c, 4, 256, tu.blocks_group), 256, 0, s3>>>(ord + bk.off[kBucketG8], c, rp, col, w, s, m, root, sigma, best, gain, kown, ncand);
-        SLM_LAUNCH_CHECK();
-        mark(kBucketG8, 1, s3);
-    }
+    // every other fine class on the layout of k_scan_fine.cu: the long
+    // blocks first on their stream, the lane groups and small blocks beside
+    auto run_classes = [&](int coarse, std::initializer_list<int> fines, cudaStream_t so) {
+        bool any = false;
+        for (int f : fines) any = any || bk.foff[f + 1] > bk.foff[f];
+        if (!any) return;
+        mark(coarse, 0, so);
+        for (int f : fines)
+            scan_fine_class(f, bk, m, best, gain, kown, ncand, tu, so);
+        mark(coarse, 1, so);
+    };
+    run_classes(kBucketBlockL, {kFine4096}, s0);
+    run_classes(kBucketBlockM, {kFine2048}, s0);
+    run_classes(kBucketWarpHash, {kFine256, kFine128, kFine64}, s1);
+    run_classes(kBucketBlockS, {kFine1024, kFine512}, s2);
+    run_classes(kBucketG16, {kFine16}, s2);
+    run_classes(kBucketG32, {kFine32}, s2);
+    run_classes(kBucketG4, {kFine4}, s3);
+    run_classes(kBucketG8, {kFine8}, s3);
     if (int c = cnt(kBucketEmpty)) {
         mark(kBucketEmpty, 0, s1);
         k_scan_empty<<<grid_for(c, 256), 256, 0, s1>>>(ord + bk.off[kBucketEmpty], c, root, best, gain, kown);

@@ -246,6 +246,13 @@ constexpr int kBlockMidMaxDeg = 2048;   // block shape with a 32 KB table up to 
 constexpr int kBlockSmemMaxDeg = 4096;  // block shape with a 64 KB table up to here; above: hub
 constexpr int kHubChunk = 2048;         // edges of a hub handled by one block
 
+// Fine degree classes: the launch shapes of the MAXIMAL scan.  The nodes are
+// sorted by fine class, and every coarse bucket above is a contiguous run of
+// fine classes (G4 = F4, G8 = F8, G16 = F16, G32 = F32, WarpHash = F64..F256,
+// BlockS = F512..F1024, BlockM = F2048, BlockL = F4096, Hub = FHub).
+enum { kFineEmpty = 0, kFine4, kFine8, kFine16, kFine32, kFine64, kFine128, kFine256, kFine512,
+       kFine1024, kFine2048, kFine4096, kFineHub, kNumFine };
+
 // Launch shapes of the MAXIMAL scan (results never depend on them): the
 // number of streams the degree buckets run on (1 or 4) and, per kernel
 // shape, the largest grid as blocks per SM.  Process-wide; set by
@@ -263,17 +270,31 @@ ScanTuning scan_tuning();
 void set_scan_tuning(const ScanTuning &t);
 
 struct Buckets {
-    DevBuf order;                       // int32[n]: nodes sorted by bucket (stable)
+    DevBuf order;                       // int32[n]: nodes sorted by fine class (stable)
     int32_t off[kNumBuckets + 1] = {0}; // host copy of bucket offsets
+    int32_t foff[kNumFine + 1] = {0};   // host copy of fine class offsets
+    // The scan's own copy of the level graph, built on first use by
+    // scan_nodes and kept until the next build: the rows of the bucketed
+    // nodes in bucket order as packed (column, weight) pairs, one record
+    // (node, first entry, degree, strength) per bucketed node in bucket
+    // order, and per node of the graph (community, community total),
+    // refreshed by every scan.
+    DevBuf ent, nrec, cs;
+    cudaTextureObject_t cs_tex = 0;  // cs through the texture path (0: plain loads)
+    const void *lay_src[4] = {nullptr, nullptr, nullptr, nullptr};  // rp, col, w, s of the copy
+    bool lay_ready = false;
     // hubs: per hub its global table (offset, log2 capacity), and the chunks
     // (hub index, first edge, end edge) that split its row across blocks
     int32_t nhub = 0, nchunk = 0, ntchunk = 0;
-    DevBuf hub_off, hub_lg, chunks, tkeys, tvals, hub_acc;
+    // tslot: 64-bit slots (community + 1) << 32 | weight, 0 = empty; hub_own:
+    // each hub's weight to its own community during a scan; hub_acc: the same
+    // for the own-weight pass
+    DevBuf hub_off, hub_lg, chunks, tslot, hub_acc, hub_own;
     // per hub: its list of occupied table slots (offset, count), so that the
     // decision reads the distinct communities only
     DevBuf hub_uoff, hub_ucnt, ulist;
     // slices of the hubs' slot lists read by one block each, and their partial results
-    DevBuf tchunks, tc_off, part_own, part_sc, part_cc;
+    DevBuf tchunks, tc_off, part_sc, part_cc;
     // side streams on which the independent bucket kernels of a scan overlap
     // (owned here so that concurrent runs never share fork/join events)
     static constexpr int kSide = 3;
@@ -291,6 +312,19 @@ struct Buckets {
     Buckets &operator=(const Buckets &) = delete;
     ~Buckets();
 };
+
+// The scan's copy of the level graph (Buckets::ent, nrec), built when the
+// buckets changed or the graph is another one; cs is sized for n nodes.
+void build_scan_layout(Buckets &bk, int32_t n, const int32_t *rp, const int32_t *col,
+                       const int32_t *w, const int32_t *s, cudaStream_t st);
+// cs[v] = (root_v, sigma[root_v]) for v < n.
+void pack_community_totals(int32_t n, const int32_t *root, const int32_t *sigma, int2 *cs,
+                           cudaStream_t st);
+// The MAXIMAL scan of the nodes of fine class f (kFine4 .. kFine4096) on the
+// layout and community totals above (k_scan_fine.cu).
+void scan_fine_class(int f, const Buckets &bk, MParam mp, int32_t *best, long long *gain,
+                     int32_t *kown, unsigned long long *ncand, const ScanTuning &tu,
+                     cudaStream_t so);
 
 // ASSIGN: a[i] = best neighbour by m_w W_ij - s_i s_j.
 void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,

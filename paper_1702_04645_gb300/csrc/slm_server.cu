@@ -213,12 +213,13 @@ uint64_t slm_server_footprint(int32_t n, int64_t nnz) {
     // input CSR and the aggregated level graph (8 B per entry each), the
     // sort of aggregation (keys, values and their double buffers: 24 B per
     // entry), hub tables (at most 16 B per entry), POSITIVE's copy of its
-    // members' internal entries (room for whole rows: at most 8 B per entry);
+    // members' internal entries (room for whole rows: at most 8 B per entry),
+    // the scan's bucket-ordered copy of the rows (8 B per entry);
     // per node the level workspace, POSITIVE's scratch and the composed
     // labels of the levels, bounded by 512 B; plus 64 MiB for cycle pools and
     // allocation rounding
     const uint64_t N = n > 0 ? (uint64_t)n : 0, E = nnz > 0 ? (uint64_t)nnz : 0;
-    return 64 * E + 512 * N + (64ull << 20);
+    return 72 * E + 512 * N + (64ull << 20);
 }
 
 const char *slm_server_last_error(const slm_server *sv) {
@@ -334,7 +335,10 @@ slm_status slm_server_cancel(slm_server *sv, uint64_t ticket) {
     if (!sv) return SLM_ERR_INVALID_ARGUMENT;
     std::lock_guard<std::mutex> lk(sv->mu);
     Request *r = find(sv, ticket);
-    if (!r) return SLM_ERR_INVALID_ARGUMENT;
+    if (!r) {
+        sv->err = "slm_server_cancel: unknown or released ticket";
+        return SLM_ERR_INVALID_ARGUMENT;
+    }
     if (r->state == SLM_REQ_QUEUED) {
         auto it = std::find(sv->queue.begin(), sv->queue.end(), r);
         if (it != sv->queue.end()) sv->queue.erase(it);

@@ -191,10 +191,15 @@ def test_cancel_running_and_queued_requests(solo):
     # the server goes on; a later request's result is unchanged
     c = sv.submit(g.row_ptr, g.col, g.w, seed=sd, accept_p32=p)
     assert sv.wait(c, timeout=60.0)
-    lab, K, q = sv.result(c)
+    lab, K, q = sv.result(c, release=False)
     lab0, K0, q0 = solo[2]
     assert K == K0 and q == q0 and np.array_equal(lab, lab0)
     sv.cancel(c)                                                     # ended: no change
+    assert sv.poll(c) == slm.REQ_DONE
+    sv.result(c)                                                     # released now
+    with pytest.raises(slm.SlmError) as e:
+        sv.cancel(c)
+    assert e.value.name == "SLM_ERR_INVALID_ARGUMENT"
     st = sv.stats()
     assert st.failed == 2 and st.completed == 1 and st.reserved_bytes == 0
     sv.close()
