@@ -44,7 +44,7 @@ FALLBACK_HBM = 6800.0
 # DRAM bytes (read + write) of one level-0 scan of the benchmark graph, from an
 # ncu capture of the scan kernels; None once the scan kernels change after
 # that capture
-SCAN_TRAFFIC_L0 = 599.9e6
+SCAN_TRAFFIC_L0 = None
 
 
 def scan_bytes(n: int, nnz: int) -> int:

@@ -196,7 +196,7 @@ slm_status slm_check_grid_barrier(int32_t blocks, int32_t absent_block, double l
  * the degree buckets one after another on the caller's stream, 4 runs them
  * side by side on the caller's stream and three library streams; the other
  * fields cap each kernel shape's grid at that many blocks per SM
- * (1..64).  Defaults: {4, 3, 6, 8, 8, 8, 16}. */
+ * (1..64).  Defaults: {4, 3, 6, 8, 8, 8, 16, 0}. */
 typedef struct {
     int32_t streams;
     int32_t blocks_large; /* 2049..4096 edges per node, 64 KB shared table */
@@ -205,6 +205,18 @@ typedef struct {
     int32_t blocks_warp;  /* 33..256 edges, one warp table per node */
     int32_t blocks_hub;   /* above 4096 edges: row chunks and table slices */
     int32_t blocks_group; /* 1..32 edges: lane groups */
+    /* Shape per fine degree class: bit k-1 set selects the second shape of
+     * class k (k = 1 for rows of 1..4 entries, 2: 5..8, 3: 9..16, 4: 17..32,
+     * 5: 33..64, 6: 65..128, 7: 129..256, 8: 257..512, 9: 513..1024,
+     * 10: 1025..2048, 11: 2049..4096).  First / second shape per class:
+     * 1: a thread per node / 4 lanes; 2: a thread / 8 lanes; 3: 4 lanes x 4
+     * entries / 8 x 2; 4: 8 x 4 / 16 x 2; 5: 16 x 4 / 32 x 2; 6: 32 x 4 / a
+     * 64-thread block x 2; 7: 32 x 8 / a 64-thread block x 4; 8: 128-thread
+     * blocks x 4 / 256 x 2; 9: 256 x 4 / 512 x 2; 10: 256 x 8 / 512 x 4;
+     * 11: 512 x 8 / 1024 x 4.  Classes 6 and 7 thereby move the boundary
+     * between the lane-group and the block kernels between 64, 128 and 256
+     * entries.  Default 0 (every first shape); 0 <= shape_alt < 2^11. */
+    int32_t shape_alt;
 } slm_scan_tuning;
 /* Set (INVALID_ARGUMENT when a field is out of range) or read the tuning. */
 slm_status slm_set_scan_tuning(const slm_scan_tuning *t);

@@ -105,7 +105,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 class ScanTuning(C.Structure):
     _fields_ = [("streams", C.c_int32), ("blocks_large", C.c_int32), ("blocks_mid", C.c_int32),
                 ("blocks_small", C.c_int32), ("blocks_warp", C.c_int32), ("blocks_hub", C.c_int32),
-                ("blocks_group", C.c_int32)]
+                ("blocks_group", C.c_int32), ("shape_alt", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -712,7 +712,10 @@ constexpr int kPosThreads = 256;
 // a POSITIVE call continues on a grid of kPosTailBlocks blocks, whose
 // barriers are much cheaper, once a round has at most this many members and
 // internal entries
-constexpr int kPosTailBlocks = 16;
+#ifndef SLM_POS_TAIL_BLOCKS
+#define SLM_POS_TAIL_BLOCKS 16
+#endif
+constexpr int kPosTailBlocks = SLM_POS_TAIL_BLOCKS;
 // blocks per SM of the full grid: rounds hold tens of thousands of members at
 // most, and a grid barrier costs one atomic per block, so one block per SM
 // is enough
@@ -720,8 +723,11 @@ constexpr int kPosTailBlocks = 16;
 #define SLM_POS_BLOCKS_PER_SM 1
 #endif
 constexpr int kPosBlocksPerSM = SLM_POS_BLOCKS_PER_SM;
-constexpr int kPosTailMembers = 8192;
-constexpr long long kPosTailEntries = 65536;
+#ifndef SLM_POS_TAIL_MEMBERS
+#define SLM_POS_TAIL_MEMBERS 8192
+#endif
+constexpr int kPosTailMembers = SLM_POS_TAIL_MEMBERS;
+constexpr long long kPosTailEntries = 8LL * SLM_POS_TAIL_MEMBERS;
 
 template <class T> __device__ T block_sum(T v, T *red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

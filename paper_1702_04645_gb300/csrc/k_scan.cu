@@ -155,6 +155,10 @@ __global__ void k_scan_empty(const int32_t *order, int32_t cnt, const int32_t *r
 // kernel, one block per hub, reads the table, resets it for the next sweep,
 // and picks the best community.
 // ---------------------------------------------------------------------------
+// A chunk's entries are first summed per community in a shared-memory table
+// (the entries of a hub often concentrate on a few large communities, whose
+// global slots would otherwise take thousands of atomics each); then every
+// community of the chunk goes into the hub's global table with one atomic.
 __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks, int nchunk, const int32_t *hubs,
                              const long long *hoff, const int32_t *hlg, const long long *uoff,
                              const int32_t *col, const int32_t *w, const int32_t *root,
@@ -163,8 +167,13 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks
     // a chunk is at most kHubChunk = 8 * kBlockThreads entries: eight per
     // thread, loaded and inserted together so that their atomics overlap
     constexpr int B = kHubChunk / kBlockThreads;
+    constexpr int SLG = 12;  // 4096 shared slots: twice a chunk
+    static_assert((1 << SLG) == 2 * kHubChunk, "shared table of twice a chunk");
+    __shared__ unsigned long long stab[1 << SLG];
     __shared__ unsigned long long red[kBlockThreads / 32];
     const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < (1 << SLG); k += kBlockThreads) stab[k] = 0ull;
+    __syncthreads();
     for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
         const int4 ch = chunks[c];  // (hub index, first edge, end edge, unused)
         const int i = hubs[ch.x];
@@ -183,44 +192,77 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks
         }
 #pragma unroll
         for (int t = 0; t < B; t++) cc[t] = cc[t] != i ? root[cc[t]] : -1;
-        // the own community never enters the table (all of a star's leaves
+        // the own community never enters a table (all of a star's leaves
         // would hit its one slot): summed per block, one atomic per chunk
         unsigned long long own = 0;
-        unsigned long long old[B];
-        unsigned h[B];
+        int cl[B];
 #pragma unroll
         for (int t = 0; t < B; t++) {
             if (cc[t] == ci) own += (unsigned long long)wv[t];
-            const bool ins = cc[t] >= 0 && cc[t] != ci;
-            h[t] = ins ? (((unsigned)cc[t] * 2654435761u) >> (32 - lg)) : 0u;
-            old[t] = ins ? atomicCAS(&T[h[t]], 0ull,
-                                     ((unsigned long long)(unsigned)(cc[t] + 1) << 32) | (unsigned)wv[t])
-                         : 1ull;
+            cl[t] = -1;
+            if (cc[t] < 0 || cc[t] == ci) continue;
+            const unsigned long long key = (unsigned long long)(unsigned)(cc[t] + 1) << 32;
+            unsigned h = ((unsigned)cc[t] * 2654435761u) >> (32 - SLG);
+            for (;;) {
+                const unsigned long long o = atomicCAS(&stab[h], 0ull, key | (unsigned)wv[t]);
+                if (o == 0ull) { cl[t] = (int)h; break; }
+                if ((o & 0xffffffff00000000ull) == key) {
+                    atomicAdd(&stab[h], (unsigned long long)(unsigned)wv[t]);
+                    break;
+                }
+                h = (h + 1) & ((1u << SLG) - 1u);
+            }
         }
+        __syncthreads();
+        // every community of the chunk into the hub's table: the home-slot
+        // CASes are issued before any result is looked at
+        unsigned long long gv[B], gold[B];
+        unsigned gh[B];
 #pragma unroll
         for (int t = 0; t < B; t++) {
-            int claimed = -1;
-            if (cc[t] >= 0 && cc[t] != ci) {
-                const unsigned long long key = (unsigned long long)(unsigned)(cc[t] + 1) << 32;
-                unsigned long long o = old[t];
-                unsigned hh = h[t];
+            gv[t] = 0ull;
+            gold[t] = 1ull;
+            gh[t] = 0u;
+            if (cl[t] < 0) continue;
+            gv[t] = stab[cl[t]];
+            stab[cl[t]] = 0ull;  // empty again for the next chunk
+            const unsigned cm = (unsigned)(gv[t] >> 32) - 1u;
+            gh[t] = (cm * 2654435761u) >> (32 - lg);
+            gold[t] = atomicCAS(&T[gh[t]], 0ull, gv[t]);
+        }
+        int claimed[B];
+        unsigned bal[B];
+        int nclaim = 0;
+#pragma unroll
+        for (int t = 0; t < B; t++) {
+            claimed[t] = -1;
+            if (cl[t] >= 0) {
+                const unsigned long long key = gv[t] & 0xffffffff00000000ull;
+                unsigned long long o = gold[t];
+                unsigned hh = gh[t];
                 for (;;) {
-                    if (o == 0ull) { claimed = (int)hh; break; }
+                    if (o == 0ull) { claimed[t] = (int)hh; break; }
                     if ((o & 0xffffffff00000000ull) == key) {
-                        atomicAdd(&T[hh], (unsigned long long)(unsigned)wv[t]);
+                        atomicAdd(&T[hh], gv[t] & 0xffffffffull);
                         break;
                     }
                     hh = (hh + 1) & mask;
-                    o = atomicCAS(&T[hh], 0ull, key | (unsigned)wv[t]);
+                    o = atomicCAS(&T[hh], 0ull, gv[t]);
                 }
             }
-            // the claimed slots of a warp are listed with one atomic on the hub's count
-            const unsigned bal = __ballot_sync(FULL, claimed >= 0);
-            if (bal) {
-                int at = 0;
-                if (lane == 0) at = atomicAdd(&ucnt[ch.x], __popc(bal));
-                at = __shfl_sync(FULL, at, 0);
-                if (claimed >= 0) ul[at + __popc(bal & ((1u << lane) - 1u))] = claimed;
+            bal[t] = __ballot_sync(FULL, claimed[t] >= 0);
+            nclaim += __popc(bal[t]);
+        }
+        // the slots a warp claimed are listed with one atomic on the hub's count
+        if (nclaim) {
+            int at = 0;
+            if (lane == 0) at = atomicAdd(&ucnt[ch.x], nclaim);
+            at = __shfl_sync(FULL, at, 0);
+            const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+            for (int t = 0; t < B; t++) {
+                if (claimed[t] >= 0) ul[at + __popc(bal[t] & below)] = claimed[t];
+                at += __popc(bal[t]);
             }
         }
 #pragma unroll
@@ -232,7 +274,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks
             for (int k = 0; k < kBlockThreads / 32; k++) t += red[k];
             if (t) atomicAdd(&own_acc[ch.x], t);
         }
-        __syncthreads();
+        __syncthreads();  // the shared table is empty and red is free
     }
 }
 

@@ -15,15 +15,25 @@
 //
 // Shapes, one per fine degree class: one thread per node (1..8 entries:
 // communities grouped in registers), 4/8/16/32 lanes per node (9..256), one
-// block per node (257..4096), each lane holding at most EPL entries.  The
-// lane-group and block shapes accumulate in a shared-memory open-addressing
-// table of 64-bit slots ((C + 1) << 32 | k_{i,C}; 0 = empty) with at least
-// twice as many slots as entries, so a new community costs one CAS and a
-// repeated one a CAS and an add; the weight to the node's own community is
-// summed in registers instead (often most of a row: it would make every lane
-// hit the same slot).  The lane that claims a slot keeps the slot,
-// the community and its total in registers, decides it after the inserts and
-// empties it again, so nothing scans the table or lists its slots.
+// block per node (257..4096), each lane holding at most EPL entries.  Both
+// table shapes accumulate in a shared-memory open-addressing table with at
+// least twice as many slots as the row has entries, and the lane that claims
+// a slot keeps the slot, the community and its total in registers and decides
+// it after the inserts, so nothing scans the table or lists its slots:
+//   * lane groups: 64-bit slots (C + 1) << 32 | k_{i,C} (0 = empty); a new
+//     community costs one CAS, a repeated one a CAS and an add, and the
+//     claimer empties its slot after deciding it;
+//   * blocks: 32-bit keys C + 1 and a separate weight word; every lane's
+//     home-slot CASes are issued before any result is looked at, the claimer
+//     keeps the first weight in a register, a repeated community adds to the
+//     weight word without a return value, and the used part of the table is
+//     cleared with 16-byte stores.
+// (Measured per class on the R-MAT scale-20 graph, each form is the faster
+// one for its shape.)  The weight to the node's own community is summed in
+// registers instead (often most of a row: every lane would hit one slot).
+// The (community, total) gathers go through the texture path (a separate data
+// pipe from the shared-memory table's), with plain loads when the array
+// exceeds a 1D texture's width.
 // Every comparison is (score desc, name asc) and every sum an integer
 // atomic: the result does not depend on scheduling.
 #include <atomic>
@@ -89,7 +99,6 @@ void build_scan_layout(Buckets &bk, int32_t n, const int32_t *rp, const int32_t 
     for (int k = 0; k < 4; k++) same = same && bk.lay_src[k] == src[k];
     const void *cs_before = bk.cs.get();
     bk.cs.ensure(sizeof(int2) * (size_t)(n > 0 ? n : 1), st);
-#ifdef SLM_SCAN_TEX
     if (bk.cs.get() != cs_before || !bk.cs_tex) {
         if (bk.cs_tex) cudaDestroyTextureObject(bk.cs_tex);
         bk.cs_tex = 0;
@@ -108,9 +117,6 @@ void build_scan_layout(Buckets &bk, int32_t n, const int32_t *rp, const int32_t 
             SLM_CUDA(cudaCreateTextureObject(&bk.cs_tex, &rd, &td, nullptr));
         }
     }
-#else
-    (void)cs_before;
-#endif
     if (same) return;
     const int32_t cnt = bk.off[kNumBuckets];
     const int32_t copy_end = bk.foff[kFineHub];  // hubs sit at the end of the order
@@ -192,6 +198,37 @@ __device__ __forceinline__ unsigned slot_of(int c, int lg) {
     return ((unsigned)c * 2654435761u) >> (32 - lg);
 }
 
+// Insert the E entries (c[t] >= 0: community, wv[t]: weight) of one lane into
+// a table of 2^lg slots: K[h] holds C + 1 (0 = empty), W[h] the weight added
+// by lanes that found C already there.  Every home-slot CAS is issued before
+// any result is looked at, so their latencies overlap.  On return cl[t] is
+// the slot this lane claimed for entry t (it keeps wv[t] as that slot's first
+// weight), or -1.
+template <int E>
+__device__ __forceinline__ void table_insert(unsigned *K, unsigned *W, int lg, const int (&c)[E],
+                                             const int (&wv)[E], int (&cl)[E]) {
+    const unsigned mask = (1u << lg) - 1u;
+    unsigned h[E], old[E];
+#pragma unroll
+    for (int t = 0; t < E; t++) {
+        h[t] = c[t] >= 0 ? slot_of(c[t], lg) : 0u;
+        old[t] = c[t] >= 0 ? atomicCAS(&K[h[t]], 0u, (unsigned)c[t] + 1u) : 1u;
+    }
+#pragma unroll
+    for (int t = 0; t < E; t++) {
+        cl[t] = -1;
+        if (c[t] < 0) continue;
+        const unsigned key = (unsigned)c[t] + 1u;
+        unsigned o = old[t], hh = h[t];
+        for (;;) {
+            if (o == 0u) { cl[t] = (int)hh; break; }
+            if (o == key) { atomicAdd(&W[hh], (unsigned)wv[t]); break; }
+            hh = (hh + 1) & mask;
+            o = atomicCAS(&K[hh], 0u, key);
+        }
+    }
+}
+
 // Add weight wv to community c in a table of 2^lg 64-bit slots; returns the
 // slot when this call claimed it, -1 when the community was already there.
 __device__ __forceinline__ int table_add(unsigned long long *T, int lg, int c, int wv) {
@@ -207,6 +244,24 @@ __device__ __forceinline__ int table_add(unsigned long long *T, int lg, int c, i
         }
         h = (h + 1) & mask;
     }
+}
+
+// Zero slots [0, 2^lg) of K and W with 16-byte stores by `nthr` threads
+// (rank `r`); 2^lg is a multiple of 4.
+__device__ __forceinline__ void table_clear(unsigned *K, unsigned *W, int lg, int r, int nthr) {
+    const int q = (1 << lg) >> 2;
+    uint4 *K4 = reinterpret_cast<uint4 *>(K), *W4 = reinterpret_cast<uint4 *>(W);
+    for (int k = r; k < q; k += nthr) {
+        K4[k] = make_uint4(0u, 0u, 0u, 0u);
+        W4[k] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// log2 of the table a row of d entries uses: at least 2 d slots, at least 4
+__device__ __forceinline__ int table_lg(int d) {
+    int lg = 2;
+    while ((1 << lg) < 2 * d) lg++;
+    return lg;
 }
 
 // ---------------------------------------------------------------------------
@@ -348,19 +403,19 @@ __global__ void __launch_bounds__(kFsWarps * 32) k_fs_lanes(FsArgs A) {
 // ---------------------------------------------------------------------------
 template <int T, int EPL>
 constexpr size_t fs_block_smem() {
-    return sizeof(unsigned long long) * 2 * T * EPL;
+    return 2 * sizeof(unsigned) * 2 * T * EPL;
 }
 
 template <int T, int EPL>
 __global__ void __launch_bounds__(T) k_fs_block(FsArgs A) {
     constexpr int CAP = 2 * T * EPL;
-    constexpr int LG = __builtin_ctz(CAP);
     constexpr int NW = T / 32;
-    extern __shared__ unsigned long long tabd[];
+    extern __shared__ __align__(16) unsigned tabd[];
+    unsigned *K = tabd, *W = tabd + CAP;
     __shared__ long long r_own[NW], r_sc[NW];
     __shared__ int r_cc[NW];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int k = tid; k < CAP; k += T) tabd[k] = 0ull;
+    for (int k = tid; k < 2 * CAP; k += T) tabd[k] = 0u;
     __syncthreads();
     unsigned cand = 0;
     long long k = blockIdx.x;
@@ -373,8 +428,9 @@ __global__ void __launch_bounds__(T) k_fs_block(FsArgs A) {
     }
     for (; k < A.cnt; k += gridDim.x) {
         const int i = r.x, si = r.w;
+        const int lg = table_lg(r.z);
         const int2 me = cs_at(A, i);
-        int c[EPL], wv[EPL], sg[EPL], cl[EPL];
+        int c[EPL], wv[EPL], sg[EPL], cl[EPL], ck[EPL];
 #pragma unroll
         for (int t = 0; t < EPL; t++) {
             wv[t] = pe[t].y;
@@ -390,8 +446,9 @@ __global__ void __launch_bounds__(T) k_fs_block(FsArgs A) {
 #pragma unroll
         for (int t = 0; t < EPL; t++) {
             if (c[t] == me.x) own += wv[t];
-            cl[t] = (c[t] >= 0 && c[t] != me.x) ? table_add(tabd, LG, c[t], wv[t]) : -1;
+            ck[t] = (c[t] >= 0 && c[t] != me.x) ? c[t] : -1;
         }
+        table_insert<EPL>(K, W, lg, ck, wv, cl);
         // the next node's entries are in flight while this one is decided
         const long long kn = k + gridDim.x;
         const int4 rn = kn < A.cnt ? A.nrec[kn] : make_int4(0, 0, 0, 0);
@@ -407,8 +464,7 @@ __global__ void __launch_bounds__(T) k_fs_block(FsArgs A) {
 #pragma unroll
         for (int t = 0; t < EPL; t++) {
             if (cl[t] < 0) continue;
-            const long long k_ic = (long long)(unsigned)tabd[cl[t]];
-            tabd[cl[t]] = 0ull;
+            const long long k_ic = (long long)wv[t] + (long long)W[cl[t]];
             const long long x = m * k_ic - (long long)si * (long long)sg[t];
             if (better(x, c[t], bsc, bc)) { bsc = x; bc = c[t]; }
         }
@@ -420,7 +476,8 @@ __global__ void __launch_bounds__(T) k_fs_block(FsArgs A) {
             if (better(osc, occ, bsc, bc)) { bsc = osc; bc = occ; }
         }
         if (lane == 0) { r_own[wid] = own; r_sc[wid] = bsc; r_cc[wid] = bc; }
-        __syncthreads();  // also orders the table's emptying before the next inserts
+        __syncthreads();                 // every thread has read its slots
+        table_clear(K, W, lg, tid, T);   // empty again for the next node
         if (wid == 0) {
             own = lane < NW ? r_own[lane] : 0;
             bsc = lane < NW ? r_sc[lane] : LLONG_MIN;
@@ -434,7 +491,7 @@ __global__ void __launch_bounds__(T) k_fs_block(FsArgs A) {
             }
             if (lane == 0) fs_emit(A, i, me.x, me.y, si, m, own, bsc, bc, cand);
         }
-        __syncthreads();  // r_* are rewritten by the next node
+        __syncthreads();  // the table is empty and r_* are free for the next node
         r = rn;
     }
     if (tid == 0 && cand) atomicAdd(A.ncand, (unsigned long long)cand);
@@ -472,44 +529,63 @@ void scan_fine_class(int f, const Buckets &bk, MParam mp, int32_t *best, long lo
     A.kown = kown;
     A.ncand = ncand;
     if (A.cnt <= 0) return;
-    static std::atomic<unsigned long long> smem_done{0};
+    const bool alt = (tu.shape_alt >> (f - 1)) & 1;
+    // lane groups of L lanes, EPL entries per lane: 32 / L nodes per warp
+    auto lanes = [&](auto kernel, int L, int per_sm) {
+        kernel<<<fs_grid(A.cnt, kFsWarps * (32 / L), per_sm), kFsWarps * 32, 0, so>>>(A);
+    };
+    // one block of T threads per node; tables above 48 KB are opted in once per device
+    auto block = [&](auto kernel, int T, size_t smem, std::atomic<unsigned long long> &done,
+                     int per_sm) {
+        if (smem > 48 * 1024) allow_smem(kernel, smem, done);
+        kernel<<<fs_grid(A.cnt, 1, per_sm), T, smem, so>>>(A);
+    };
+    static std::atomic<unsigned long long> d1{0}, d2{0};
     switch (f) {
     case kFine4:
-        k_fs_thread<4><<<fs_grid(A.cnt, 256, tu.blocks_group), 256, 0, so>>>(A);
+        if (alt) lanes(k_fs_lanes<4, 1>, 4, tu.blocks_group);
+        else k_fs_thread<4><<<fs_grid(A.cnt, 256, tu.blocks_group), 256, 0, so>>>(A);
         break;
     case kFine8:
-        k_fs_thread<8><<<fs_grid(A.cnt, 256, tu.blocks_group), 256, 0, so>>>(A);
+        if (alt) lanes(k_fs_lanes<8, 1>, 8, tu.blocks_group);
+        else k_fs_thread<8><<<fs_grid(A.cnt, 256, tu.blocks_group), 256, 0, so>>>(A);
         break;
     case kFine16:
-        k_fs_lanes<4, 4><<<fs_grid(A.cnt, kFsWarps * 8, tu.blocks_group), kFsWarps * 32, 0, so>>>(A);
+        if (alt) lanes(k_fs_lanes<8, 2>, 8, tu.blocks_group);
+        else lanes(k_fs_lanes<4, 4>, 4, tu.blocks_group);
         break;
     case kFine32:
-        k_fs_lanes<8, 4><<<fs_grid(A.cnt, kFsWarps * 4, tu.blocks_group), kFsWarps * 32, 0, so>>>(A);
+        if (alt) lanes(k_fs_lanes<16, 2>, 16, tu.blocks_group);
+        else lanes(k_fs_lanes<8, 4>, 8, tu.blocks_group);
         break;
     case kFine64:
-        k_fs_lanes<16, 4><<<fs_grid(A.cnt, kFsWarps * 2, tu.blocks_warp), kFsWarps * 32, 0, so>>>(A);
+        if (alt) lanes(k_fs_lanes<32, 2>, 32, tu.blocks_warp);
+        else lanes(k_fs_lanes<16, 4>, 16, tu.blocks_warp);
         break;
     case kFine128:
-        k_fs_lanes<32, 4><<<fs_grid(A.cnt, kFsWarps, tu.blocks_warp), kFsWarps * 32, 0, so>>>(A);
+        if (alt) block(k_fs_block<64, 2>, 64, fs_block_smem<64, 2>(), d1, 4 * tu.blocks_warp);
+        else lanes(k_fs_lanes<32, 4>, 32, tu.blocks_warp);
         break;
     case kFine256:
-        k_fs_lanes<32, 8><<<fs_grid(A.cnt, kFsWarps, tu.blocks_warp), kFsWarps * 32, 0, so>>>(A);
+        if (alt) block(k_fs_block<64, 4>, 64, fs_block_smem<64, 4>(), d1, 4 * tu.blocks_warp);
+        else lanes(k_fs_lanes<32, 8>, 32, tu.blocks_warp);
         break;
     case kFine512:
-        k_fs_block<128, 4><<<fs_grid(A.cnt, 1, 2 * tu.blocks_small), 128, fs_block_smem<128, 4>(), so>>>(A);
+        if (alt) block(k_fs_block<256, 2>, 256, fs_block_smem<256, 2>(), d1, tu.blocks_small);
+        else block(k_fs_block<128, 4>, 128, fs_block_smem<128, 4>(), d1, 2 * tu.blocks_small);
         break;
     case kFine1024:
-        k_fs_block<256, 4><<<fs_grid(A.cnt, 1, tu.blocks_small), 256, fs_block_smem<256, 4>(), so>>>(A);
+        if (alt) block(k_fs_block<512, 2>, 512, fs_block_smem<512, 2>(), d1, tu.blocks_small);
+        else block(k_fs_block<256, 4>, 256, fs_block_smem<256, 4>(), d1, tu.blocks_small);
         break;
     case kFine2048:
-        k_fs_block<256, 8><<<fs_grid(A.cnt, 1, tu.blocks_mid), 256, fs_block_smem<256, 8>(), so>>>(A);
+        if (alt) block(k_fs_block<512, 4>, 512, fs_block_smem<512, 4>(), d1, tu.blocks_mid);
+        else block(k_fs_block<256, 8>, 256, fs_block_smem<256, 8>(), d1, tu.blocks_mid);
         break;
-    case kFine4096: {
-        constexpr size_t sm = fs_block_smem<512, 8>();
-        allow_smem(k_fs_block<512, 8>, sm, smem_done);
-        k_fs_block<512, 8><<<fs_grid(A.cnt, 1, tu.blocks_large), 512, sm, so>>>(A);
+    case kFine4096:
+        if (alt) block(k_fs_block<1024, 4>, 1024, fs_block_smem<1024, 4>(), d2, tu.blocks_large);
+        else block(k_fs_block<512, 8>, 512, fs_block_smem<512, 8>(), d1, tu.blocks_large);
         break;
-    }
     default:
         return;
     }

@@ -562,6 +562,7 @@ slm_status slm_set_scan_tuning(const slm_scan_tuning *t) {
     for (int32_t v : {t->blocks_large, t->blocks_mid, t->blocks_small, t->blocks_warp,
                       t->blocks_hub, t->blocks_group})
         if (v < 1 || v > 64) return SLM_ERR_INVALID_ARGUMENT;
+    if (t->shape_alt < 0 || t->shape_alt >= (1 << 11)) return SLM_ERR_INVALID_ARGUMENT;
     slm::ScanTuning u;
     u.streams = t->streams;
     u.blocks_large = t->blocks_large;
@@ -570,6 +571,7 @@ slm_status slm_set_scan_tuning(const slm_scan_tuning *t) {
     u.blocks_warp = t->blocks_warp;
     u.blocks_hub = t->blocks_hub;
     u.blocks_group = t->blocks_group;
+    u.shape_alt = t->shape_alt;
     slm::set_scan_tuning(u);
     return SLM_OK;
 }
@@ -578,7 +580,7 @@ slm_status slm_get_scan_tuning(slm_scan_tuning *t) {
     if (!t) return SLM_ERR_INVALID_ARGUMENT;
     const slm::ScanTuning u = slm::scan_tuning();
     *t = slm_scan_tuning{u.streams, u.blocks_large, u.blocks_mid, u.blocks_small,
-                         u.blocks_warp, u.blocks_hub, u.blocks_group};
+                         u.blocks_warp, u.blocks_hub, u.blocks_group, u.shape_alt};
     return SLM_OK;
 }
 

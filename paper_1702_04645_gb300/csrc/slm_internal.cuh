@@ -265,6 +265,7 @@ struct ScanTuning {
     int blocks_warp = 8;    // 33..256 edges, warp tables
     int blocks_hub = 8;     // hub chunks and table slices
     int blocks_group = 16;  // 1..32 edges, lane groups
+    int shape_alt = 0;      // bit f-1: the second launch shape of fine class f
 };
 ScanTuning scan_tuning();
 void set_scan_tuning(const ScanTuning &t);

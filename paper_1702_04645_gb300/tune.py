@@ -1,16 +1,18 @@
 """Autotuner of the MAXIMAL scan's launch shapes.
 
-The scan runs one kernel shape per degree bucket (lane groups, warp tables,
-block tables of three sizes, hub chunks); how many blocks each shape may
-launch per SM, and whether the buckets run side by side on four streams or
-one after another, decide how well they share the GPU for a given degree
-distribution.  None of it changes a result.
+The scan runs one kernel shape per fine degree class (a thread per node,
+lane groups, blocks of several sizes, hub chunks).  Which of two shapes each
+class uses -- and with it where the boundaries between the thread, lane-group
+and block kernels fall --, how many blocks each shape may launch per SM, and
+whether the classes run side by side on four streams or one after another,
+decide how well they share the GPU for a given degree distribution.  None of
+it changes a result.
 
 ``autotune_scan`` times the scan (``slm_step_scan``: degree buckets,
 community totals and the scan kernels) on a graph's own level-0 state --
 after ASSIGN and POSITIVE -- under candidate tunings, by coordinate descent
 from the current tuning: each field in turn takes the value that makes the
-scan fastest.  Every candidate's outputs (best community, gain, local gain)
+scan fastest; then each class's shape bit in turn.  Every candidate's outputs (best community, gain, local gain)
 are compared with the starting tuning's and must be identical.  The winner
 is applied process-wide (``slm_set_scan_tuning``) and remembered per graph
 shape (node count, entry count and degree histogram) for the rest of the
@@ -33,6 +35,7 @@ SPACE = {
     "blocks_hub": [4, 8, 16],
     "blocks_group": [8, 16, 32],
 }
+NUM_CLASSES = 11  # fine degree classes with a choice of shape (bit k-1 of shape_alt)
 
 _cache: dict = {}
 
@@ -86,22 +89,26 @@ def autotune_scan(row_ptr, col, w, reps: int = 5, apply: bool = True, use_cache:
     best = dict(start)
     best_ms = _time_scan(args, reps, torch)
     report = {"start": dict(start), "start_ms": best_ms, "tried": []}
-    for field, values in SPACE.items():
-        for v in values:
-            if v == best[field]:
-                continue
-            cand = dict(best)
+    trials = [(f, v) for f, values in SPACE.items() for v in values]
+    trials += [("shape_alt", bit) for bit in range(NUM_CLASSES)]
+    for field, v in trials:
+        cand = dict(best)
+        if field == "shape_alt":
+            cand[field] = best[field] ^ (1 << v)
+        elif v == best[field]:
+            continue
+        else:
             cand[field] = v
-            set_scan_tuning(**cand)
-            out = [t.cpu() for t in step_scan(*args)]
-            for x, y in zip(out, ref):
-                if not torch.equal(x, y):
-                    set_scan_tuning(**start)
-                    raise RuntimeError(f"scan outputs changed under tuning {cand}")
-            ms = _time_scan(args, reps, torch)
-            report["tried"].append((cand, ms))
-            if ms < best_ms:
-                best, best_ms = cand, ms
+        set_scan_tuning(**cand)
+        out = [t.cpu() for t in step_scan(*args)]
+        for x, y in zip(out, ref):
+            if not torch.equal(x, y):
+                set_scan_tuning(**start)
+                raise RuntimeError(f"scan outputs changed under tuning {cand}")
+        ms = _time_scan(args, reps, torch)
+        report["tried"].append((cand, ms))
+        if ms < best_ms:
+            best, best_ms = cand, ms
         set_scan_tuning(**best)
     report["best"] = dict(best)
     report["best_ms"] = best_ms

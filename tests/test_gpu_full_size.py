@@ -10,9 +10,9 @@ LFR-style recipe.
     per-sweep trace, the final labels and Q) with the oracle's runs stored
     under tests/golden/ by tests/golden/make_run_goldens.py (which calls
     only the oracle): the complete run on the R-MAT graph, and bounded runs
-    (a sweep limit per level, and on the 4M graph a level limit) on the
-    LFR-style graphs, where the method does not settle within the default
-    sweep limit;
+    (3 sweeps per level, and on the 4M graph 3 levels) on the LFR-style
+    graphs, where the method does not settle: after a few sweeps long
+    assignment cycles form, whose cycle cuts cost the oracle hours;
   * properties that hold at any size: every level's labels are 0..K-1, the
     last level stopped for a stated reason, and the final modularity equals
     the oracle's modularity of the GPU's own final partition.
@@ -146,14 +146,14 @@ def test_rmat_s20_whole_run_timed_flags_equal():
 
 
 def test_lfr_4m_bounded_run_equals_oracle():
-    """The 4,194,304-node LFR-style graph with at most 5 sweeps per level and
+    """The 4,194,304-node LFR-style graph with at most 3 sweeps per level and
     3 levels equals the oracle's bounded run level by level."""
     G = compare_with_golden(_lfr(), _golden("lfr_4m_bounded"))
     G.close()
 
 
 def test_lfr_256k_bounded_run_equals_oracle():
-    """A 262,144-node graph of the LFR-style recipe with at most 40 sweeps per
+    """A 262,144-node graph of the LFR-style recipe with at most 3 sweeps per
     level, every level, equals the oracle's run."""
     G = compare_with_golden(_lfr_256k(), _golden("lfr_256k_bounded"))
     G.close()

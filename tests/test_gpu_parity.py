@@ -323,7 +323,8 @@ def test_scan_tuning_changes_no_result():
     ref = [host(t) for t in slm.step_scan(rp, col, w, s, m, root)]
     try:
         for t in ({"streams": 1}, {"blocks_large": 1, "blocks_mid": 2, "blocks_warp": 4},
-                  {"blocks_group": 32, "blocks_hub": 16, "blocks_small": 4}):
+                  {"blocks_group": 32, "blocks_hub": 16, "blocks_small": 4},
+                  {"shape_alt": 0x7FF}, {"shape_alt": 0x555}, {"shape_alt": 0x2AA, "streams": 1}):
             slm.set_scan_tuning(**t)
             out = [host(x) for x in slm.step_scan(rp, col, w, s, m, root)]
             for x, y in zip(out, ref):
@@ -336,3 +337,24 @@ def test_scan_tuning_changes_no_result():
     with pytest.raises(slm.SlmError):
         slm.set_scan_tuning(streams=3)
     assert slm.get_scan_tuning() == start
+
+
+@pytest.mark.parametrize("shape_alt", [0x7FF, 0x555, 0x2AA])
+def test_scan_alternative_shapes_equal_oracle(shape_alt):
+    """Each fine degree class's second launch shape gives the oracle's scan:
+    rows of every class from 1 to 4096 entries (the stars add a 3,000-entry
+    row) and, beside them, hub rows."""
+    start = slm.get_scan_tuning()
+    try:
+        slm.set_scan_tuning(shape_alt=shape_alt)
+        for g in (gg.rmat(scale=13, seed=4), gg.star(3000, w=2), gg.star(1500),
+                  gg.sbm_planted(n_blocks=8, block_size=100, p_in=0.1, p_out=0.005, seed=4)):
+            s, m = O.strengths(g)
+            for k, a in enumerate(states(g, 3)):
+                root = O.rootlabel(a)
+                best, gain, gl = slm.step_scan(g.row_ptr, g.col, g.w, s.astype(np.int32), m, root)
+                ob, og, ol = O.scan(g, root)
+                assert (host(best, g.n) == ob).all() and (host(gain, g.n) == og).all()
+                assert (host(gl, g.n) == ol).all()
+    finally:
+        slm.set_scan_tuning(**start)
