@@ -41,10 +41,11 @@ WORKLOAD_DESC = ("R-MAT scale 20, 16*2^20 draws (a,b,c)=(0.57,0.19,0.19), w~U[1,
 METRIC = "local-move GTEPS"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
-# DRAM bytes (read + write) of one level-0 scan of the benchmark graph, from an
-# ncu capture of the scan kernels; None once the scan kernels change after
-# that capture
-SCAN_TRAFFIC_L0 = None
+# DRAM bytes (read + write) of one level-0 scan of the benchmark graph: the
+# sum over the scan's kernels of an ncu capture (one launch each, serialised,
+# caches flushed before each); None once the scan kernels change after that
+# capture
+SCAN_TRAFFIC_L0 = 465.5e6
 
 
 def scan_bytes(n: int, nnz: int) -> int:
