@@ -517,8 +517,8 @@ LFR_DESC = ("weighted LFR-style graphs, mean degree 50, maximum degree 100, degr
 
 
 def _lfr_job(args):
-    n, mt, mw = args
-    g, comm = gg.lfr_weighted(n, mt, mw)
+    n, mt, mw, directed = args
+    g, comm = (gg.lfr_directed if directed else gg.lfr_weighted)(n, mt, mw)
     return g.row_ptr, g.col, g.w, comm
 
 
@@ -544,7 +544,7 @@ def run_lfr_table1(args):
     t0 = time.perf_counter()
     ctx = mp.get_context("spawn")  # before any CUDA use
     with ctx.Pool(min(len(cases), os.cpu_count() or 1)) as pool:
-        graphs = pool.map(_lfr_job, cases)
+        graphs = pool.map(_lfr_job, [c + (args.directed,) for c in cases])
     note(f"{len(cases)} LFR graphs ready ({time.perf_counter() - t0:.1f} s)")
     import torch
     import paper_1702_04645_gb300 as slm
@@ -557,7 +557,7 @@ def run_lfr_table1(args):
     out, tot_units, tot_ms, launches = [], 0, 0.0, 0
     with ClockSampler(local) as clk:
         for (n, mt, mw), (rp, col, w, comm) in zip(cases, graphs):
-            G = slm.Graph(rp, col, w)
+            G = slm.Graph(rp, col, w, directed=args.directed)
             G.run(**run_kw)  # warm-up
             torch.cuda.synchronize(dev)
             l0 = slm.launch_count()
@@ -579,10 +579,14 @@ def run_lfr_table1(args):
                     "status": [st.status for st in per_level],
                     "communities": int(K), "planted": int(np.unique(comm).shape[0]),
                     "modularity": G.modularity(-1), "nmi_planted": nmi(lab, comm)}
-            if n == sizes[0] and not args.no_cpu_baseline:
+            if args.directed and mt >= 0.8 and n == sizes[0]:
+                # the directed oracle needs several minutes here (hundreds of
+                # sweeps with long assignment cycles)
+                case["oracle_skipped"] = "directed (0.8, 0.7): minutes of oracle time"
+            elif n == sizes[0] and not args.no_cpu_baseline:
                 g = gg.CSR(n, rp, col, w)
                 t1 = time.perf_counter()
-                r = O.slm(g, seed=args.seed, P=O.P_HALF)
+                r = (O.directed_slm if args.directed else O.slm)(g, seed=args.seed, P=O.P_HALF)
                 case["oracle_ms"] = 1e3 * (time.perf_counter() - t1)
                 case["identical_to_oracle"] = bool(np.array_equal(r.final, lab))
             G.close()
@@ -601,7 +605,11 @@ def run_lfr_table1(args):
             "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": tot_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
-            "config": {"workload": "lfr_weighted_table1", "desc": LFR_DESC, "sizes": sizes,
+            "config": {"workload": "lfr_directed_table1" if args.directed else "lfr_weighted_table1",
+                       "desc": LFR_DESC + ("; directed: each pair an arc in a random direction, 30% "
+                                           "with the reverse arc too (directed Q_w)"
+                                           if args.directed else ""),
+                       "sizes": sizes,
                        "l2": "largest inputs larger than L2"},
             "cases": out, "cpu_baseline": cpu, "gpu_launches": int(launches),
             "clocks": clk.summary()}
@@ -658,6 +666,8 @@ def main():
                     default="rmat")
     ap.add_argument("--lfr-sizes", default="10000,100000,1000000",
                     help="lfr_table1: node counts")
+    ap.add_argument("--directed", action="store_true",
+                    help="lfr_table1: directed weighted LFR-style graphs (the paper's setting)")
     ap.add_argument("--rmat-scale", type=int, default=20,
                     help="rmat: graph scale (20 is the benchmark graph; smaller scales are "
                          "the cases profiled with many-pass ncu captures)")

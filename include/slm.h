@@ -94,6 +94,29 @@ void slm_default_options(slm_options *opt);
 slm_status slm_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                             const int32_t *weights, int where, void *stream, slm_graph **out);
 
+/* A directed graph, the setting of the paper's own experiments (Section 5.1,
+ * weighted directed LFR graphs).  W is given as a CSR of out-arcs: row i
+ * holds the arcs i -> j with positive weights W_ij, columns sorted ascending
+ * and unique per row, no symmetry required (a self-loop W_ii is stored once).
+ * The method then optimises Q_w of Section 2.4 with out- and in-strengths:
+ *   Q_w = (1/m_w) sum_ij [W_ij - s_i^out s_j^in / m_w] delta(c_i, c_j),
+ * with s_i^out = sum_j W_ij, s_j^in = sum_i W_ij and m_w = sum_ij W_ij.  A
+ * node's neighbours are the nodes joined to it by an arc either way, and every
+ * gain is the exact int64 change of the numerator (the weight term counts
+ * U = W + W^T, the null-model term s_i^out Sigma_C^in + s_i^in Sigma_C^out).
+ * U and the strengths are built on the host during the call (W in `where`
+ * memory is copied there first).  Errors: INVALID_ARGUMENT (CSR shape,
+ * column out of range, unsorted or duplicated, w <= 0), OVERFLOW (m_w >= 2^30
+ * or more than 2^30 arcs: the packed strength totals and the int64 gains
+ * need it), OUT_OF_MEMORY, CUDA.  slm_run, slm_get_partition, slm_modularity
+ * (the directed Q_w above), slm_get_stats and slm_destroy_graph take the
+ * handle as they take an undirected one. */
+slm_status slm_create_graph_directed(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                                     const int32_t *weights, int where, void *stream,
+                                     slm_graph **out);
+/* 1 for a handle made by slm_create_graph_directed, 0 otherwise. */
+int32_t slm_graph_is_directed(const slm_graph *g);
+
 /* Run Algorithm 1 on the graph: per level ASSIGN, COMPONENTS, POSITIVE, then
  * MAXIMAL and POSITIVE alternately until no positive move remains, then
  * AGGREGATE; stop when a level finds no community structure.  On success the

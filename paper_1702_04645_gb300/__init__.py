@@ -44,7 +44,8 @@ STATUS = {0: "SLM_OK", 1: "SLM_ERR_INVALID_ARGUMENT", 2: "SLM_ERR_NOT_SYMMETRIC"
           9: "SLM_ERR_BUDGET", 10: "SLM_ERR_CANCELLED", 11: "SLM_ERR_DEADLINE"}
 
 # every exported entry point, as declared in include/*.h
-EXPORTS = ["slm_default_options", "slm_create_graph", "slm_run", "slm_num_levels",
+EXPORTS = ["slm_default_options", "slm_create_graph", "slm_create_graph_directed",
+           "slm_graph_is_directed", "slm_run", "slm_num_levels",
            "slm_get_partition", "slm_modularity", "slm_get_stats", "slm_modularity_of",
            "slm_destroy_graph", "slm_status_string", "slm_last_error", "slm_step_strengths",
            "slm_step_assign", "slm_step_components", "slm_step_scan", "slm_step_branch_gain",
@@ -158,6 +159,8 @@ def load():
         sig = {
             "slm_default_options": (None, [C.POINTER(Options)]),
             "slm_create_graph": (C.c_int, [i32, vp, vp, vp, C.c_int, vp, C.POINTER(vp)]),
+            "slm_create_graph_directed": (C.c_int, [i32, vp, vp, vp, C.c_int, vp, C.POINTER(vp)]),
+            "slm_graph_is_directed": (i32, [vp]),
             "slm_run": (C.c_int, [vp, C.POINTER(Options), vp]),
             "slm_num_levels": (C.c_int, [vp, C.POINTER(i32)]),
             "slm_get_partition": (C.c_int, [vp, i32, vp, C.c_int, C.POINTER(i32)]),
@@ -275,7 +278,9 @@ def _empty(n, dtype):
 class Graph:
     """A graph resident on the device and the results of its last run."""
 
-    def __init__(self, row_ptr, col, w=None, stream=None):
+    def __init__(self, row_ptr, col, w=None, stream=None, directed: bool = False):
+        """directed=True: (row_ptr, col, w) is a directed W (out-arcs per row),
+        and the run optimises the directed Q_w (slm_create_graph_directed)."""
         lib = load()
         self._h = C.c_void_p()
         is_np = isinstance(row_ptr, np.ndarray)
@@ -295,8 +300,9 @@ class Graph:
             st = _stream(stream) if where == SLM_DEVICE else C.c_void_p(0)
             del torch
         self.n = int(len(self._keep[0]) - 1)
-        _check(lib.slm_create_graph(self.n, ptrs[0], ptrs[1], ptrs[2], where, st,
-                                    C.byref(self._h)))
+        create = lib.slm_create_graph_directed if directed else lib.slm_create_graph
+        _check(create(self.n, ptrs[0], ptrs[1], ptrs[2], where, st, C.byref(self._h)))
+        self.directed = bool(directed)
         self._keep = None
 
     def close(self):

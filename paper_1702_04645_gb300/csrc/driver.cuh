@@ -23,7 +23,7 @@ struct Work {
         n = n_;
         size_t N = (size_t)(n > 0 ? n : 1);
         a.ensure(4 * N, st);
-        sigma.ensure(4 * N, st);
+        sigma.ensure(8 * N, st);  // int32 totals, or packed (out, in) pairs of a directed graph
         best.ensure(4 * N, st);
         kown.ensure(4 * N, st);
         tgt.ensure(4 * N, st);

@@ -465,6 +465,30 @@ void community_sigma(int32_t n, const int32_t *root, const int32_t *s, int32_t *
     SLM_LAUNCH_CHECK();
 }
 
+// packed (out, in) pairs: one 64-bit add sums both components (each stays below 2^30)
+__global__ void k_sum_packed(int32_t n, const int32_t *idx, const unsigned long long *s,
+                             unsigned long long *out) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x)
+        if (s[v]) atomicAdd(&out[idx[v]], s[v]);
+}
+
+void community_sigma(int32_t n, const int32_t *root, const unsigned long long *s,
+                     unsigned long long *sigma, cudaStream_t st) {
+    if (n <= 0) return;
+    SLM_CUDA(cudaMemsetAsync(sigma, 0, sizeof(unsigned long long) * n, st));
+    k_sum_packed<<<grid_for(n, 256), 256, 0, st>>>(n, root, s, sigma);
+    SLM_LAUNCH_CHECK();
+}
+
+void sum_strengths_by(int32_t n, const int32_t *id, const unsigned long long *s, int32_t K,
+                      unsigned long long *out, cudaStream_t st) {
+    if (K > 0) SLM_CUDA(cudaMemsetAsync(out, 0, sizeof(unsigned long long) * K, st));
+    if (n <= 0) return;
+    k_sum_packed<<<grid_for(n, 256), 256, 0, st>>>(n, id, s, out);
+    SLM_LAUNCH_CHECK();
+}
+
 // ---------------------------------------------------------------------------
 // Compaction: names in use (root[x] == x) ranked in increasing order.
 // ---------------------------------------------------------------------------
@@ -575,6 +599,73 @@ long long modularity_num(int32_t n, const int32_t *rp, const int32_t *col, const
     SLM_CUDA(cudaMemcpyAsync(h, out.get(), sizeof h, cudaMemcpyDeviceToHost, s));
     slm::stream_sync(s);
     return (long long)h[0] - (long long)h[1];
+}
+
+// per label: internal U weight and the packed strength total
+__global__ void k_modd_accumulate(int32_t n, const int32_t *rp, const int32_t *col,
+                                  const int32_t *w, const unsigned long long *s2,
+                                  const int32_t *labels, unsigned long long *win,
+                                  unsigned long long *sig) {
+    int lane = threadIdx.x & 31;
+    long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = warp; u < n; u += nwarps) {
+        int lu = labels[u];
+        long long in = 0;
+        for (int p = rp[u] + lane; p < rp[u + 1]; p += 32)
+            if (labels[col[p]] == lu) in += w[p];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) in += __shfl_xor_sync(0xffffffffu, in, o);
+        if (lane == 0) {
+            if (in) atomicAdd(&win[lu], (unsigned long long)in);
+            if (s2[u]) atomicAdd(&sig[lu], s2[u]);
+        }
+    }
+}
+
+// out2[0] = m_w sum U_in, out2[1] = sum 2 Sigma^out Sigma^in (each below 2^62)
+__global__ void k_modd_reduce(int32_t n, const unsigned long long *win,
+                              const unsigned long long *sig, unsigned long long m,
+                              unsigned long long *out2) {
+    unsigned long long a = 0, b = 0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        a += m * win[c];
+        b += (unsigned long long)NMDir::cross((long long)sig[c], (long long)sig[c]);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicAdd(&out2[0], a);
+        if (b) atomicAdd(&out2[1], b);
+    }
+}
+
+long long modularity_num_directed(int32_t n, const int32_t *rp, const int32_t *col,
+                                  const int32_t *w, const unsigned long long *s2,
+                                  const int32_t *labels, long long m_w, cudaStream_t s) {
+    if (n <= 0 || m_w == 0) return 0;
+    DevBuf win(sizeof(unsigned long long) * n, s), sig(sizeof(unsigned long long) * n, s),
+        out(2 * sizeof(unsigned long long), s);
+    SLM_CUDA(cudaMemsetAsync(win.get(), 0, win.bytes(), s));
+    SLM_CUDA(cudaMemsetAsync(sig.get(), 0, sig.bytes(), s));
+    SLM_CUDA(cudaMemsetAsync(out.get(), 0, out.bytes(), s));
+    k_modd_accumulate<<<grid_for((long long)n * 32, 256), 256, 0, s>>>(
+        n, rp, col, w, s2, labels, win.as<unsigned long long>(), sig.as<unsigned long long>());
+    SLM_LAUNCH_CHECK();
+    k_modd_reduce<<<grid_for(n, 256, 1024), 256, 0, s>>>(n, win.as<unsigned long long>(),
+                                                          sig.as<unsigned long long>(),
+                                                          (unsigned long long)m_w,
+                                                          out.as<unsigned long long>());
+    SLM_LAUNCH_CHECK();
+    unsigned long long h[2];
+    SLM_CUDA(cudaMemcpyAsync(h, out.get(), sizeof h, cudaMemcpyDeviceToHost, s));
+    slm::stream_sync(s);
+    // both terms are even: U counts every internal arc in both rows
+    return ((long long)h[0] - (long long)h[1]) / 2;
 }
 
 double modularity_from_num(long long num, long long m_w) {

@@ -60,15 +60,18 @@ __global__ void k_classify(int32_t n, const int32_t *a, const uint8_t *oncycle,
 
 // every node of a tree holding an inner candidate adds itself to the
 // candidates among its ancestors (itself included)
+// (strengths are summed as 64-bit values: for a directed graph the packed
+// (out, in) pairs, whose components only grow)
+template <class NM>
 __global__ void k_walk_tree(int32_t n, const int32_t *a, const uint8_t *oncycle,
                             const int32_t *entry, const int32_t *depth, const int32_t *treeact,
                             const int32_t *active,
-                            const int32_t *s, const int32_t *kown, long long *subS,
+                            const typename NM::ST *s, const int32_t *kown, long long *subS,
                             long long *subWA, int32_t *covered) {
     GRID_STRIDE(x, n) {
         if (oncycle[x] || !treeact[entry[x]]) continue;
         int y = (int)x, cov = 0;
-        long long sx = s[x], kx = kown[x];
+        long long sx = (long long)s[x], kx = kown[x];
         for (int d = depth[x]; d > 0; d--) {  // the non-cycle ancestors, x included
             if (active[y]) {
                 add64(&subS[y], sx);
@@ -191,8 +194,10 @@ __global__ void k_edges_cycle(int32_t n, const int32_t *rp, const int32_t *col, 
     }
 }
 
+template <class NM>
 __global__ void k_bg_final(int32_t n, const int32_t *a, const uint8_t *oncycle,
-                           const int32_t *root, const int32_t *haschild, const int32_t *sigma,
+                           const int32_t *root, const int32_t *haschild,
+                           const typename NM::ST *sigma,
                            const int32_t *best, const long long *gain, MParam mp,
                            const long long *subS, const long long *subWA, const long long *subWin,
                            const long long *WB, long long *bg) {
@@ -200,13 +205,14 @@ __global__ void k_bg_final(int32_t n, const int32_t *a, const uint8_t *oncycle,
         const long long m = mp.of((int)i);
         int k = cand_kind((int)i, a, oncycle, haschild, gain);
         long long r = 0;
-        long long sA = sigma[root[i]], sB = sigma[best[i]];
+        long long sA = (long long)sigma[root[i]], sB = (long long)sigma[best[i]];
         if (k == 1) r = gain[i];
-        else if (k == 2) r = m * WB[i] - sA * sB;
+        else if (k == 2) r = m * WB[i] - NM::cross(sA, sB);
         else if (k == 3) {
             long long sS = subS[i];
             long long wout = subWA[i] - subWin[i];
-            r = m * (WB[i] - wout) - sS * (sB - sA + sS);
+            // S (sB - sA + S) expanded, so that no packed difference can go negative
+            r = m * (WB[i] - wout) - (NM::cross(sS, sB) - NM::cross(sS, sA) + NM::cross(sS, sS));
         }
         bg[i] = r;
     }
@@ -386,9 +392,10 @@ void forest_analyse_subset(int32_t cnt, const int32_t *list, const int32_t *a, F
     forest_pass(cnt, list, a, f, st);
 }
 
+template <class NM>
 void branch_gains(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                  const int32_t *s, MParam m, const int32_t *a, const Forest &f,
-                  const int32_t *sigma, const int32_t *best, const long long *gain,
+                  const typename NM::ST *s, MParam m, const int32_t *a, const Forest &f,
+                  const typename NM::ST *sigma, const int32_t *best, const long long *gain,
                   const int32_t *kown, BranchScratch &bs, long long *bg, cudaStream_t st) {
     if (n <= 0) return;
     const int g = grid_for(n, 256);
@@ -402,7 +409,7 @@ void branch_gains(int32_t n, const int32_t *rp, const int32_t *col, const int32_
     k_classify<<<g, 256, 0, st>>>(n, a, f.oncycle, f.entry, f.root, bs.haschild, gain, bs.active,
                                   bs.treeact, bs.commcyc);
     SLM_LAUNCH_CHECK();
-    k_walk_tree<<<g, 256, 0, st>>>(n, a, f.oncycle, f.entry, f.depth, bs.treeact, bs.active, s, kown,
+    k_walk_tree<NM><<<g, 256, 0, st>>>(n, a, f.oncycle, f.entry, f.depth, bs.treeact, bs.active, s, kown,
                                    bs.subS, bs.subWA, bs.covered);
     SLM_LAUNCH_CHECK();
     k_edges_tree<<<gw, 256, 0, st>>>(n, rp, col, w, a, f.oncycle, f.entry, f.depth, f.root, best,
@@ -412,7 +419,7 @@ void branch_gains(int32_t n, const int32_t *rp, const int32_t *col, const int32_
     SLM_LAUNCH_CHECK();
     k_edges_cycle<<<gw, 256, 0, st>>>(n, rp, col, w, a, f.root, f.cdist, best, gain, bs.commcyc, bs.WB);
     SLM_LAUNCH_CHECK();
-    k_bg_final<<<g, 256, 0, st>>>(n, a, f.oncycle, f.root, bs.haschild, sigma, best, gain, m,
+    k_bg_final<NM><<<g, 256, 0, st>>>(n, a, f.oncycle, f.root, bs.haschild, sigma, best, gain, m,
                                   bs.subS, bs.subWA, bs.subWin, bs.WB, bg);
     SLM_LAUNCH_CHECK();
 }
@@ -433,5 +440,15 @@ void apply_moves(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt, c
     k_apply<<<grid_for(max_cnt, 256), 256, 0, st>>>(list, cnt_dev, tgt, a);
     SLM_LAUNCH_CHECK();
 }
+
+template void branch_gains<NMSym>(int32_t, const int32_t *, const int32_t *, const int32_t *,
+                                 const int32_t *, MParam, const int32_t *, const Forest &,
+                                 const int32_t *, const int32_t *, const long long *,
+                                 const int32_t *, BranchScratch &, long long *, cudaStream_t);
+template void branch_gains<NMDir>(int32_t, const int32_t *, const int32_t *, const int32_t *,
+                                 const unsigned long long *, MParam, const int32_t *,
+                                 const Forest &, const unsigned long long *, const int32_t *,
+                                 const long long *, const int32_t *, BranchScratch &,
+                                 long long *, cudaStream_t);
 
 }  // namespace slm

@@ -140,14 +140,15 @@ __device__ __forceinline__ void k_root_pools(int cnt, const int32_t *Rdev, const
 
 // every member adds itself to its non-cycle ancestors (itself included) and to
 // the total of the tree hanging from its entry
+template <class NM>
 __device__ __forceinline__ void k_walk(int cnt, const int32_t *M, const int32_t *a, const int32_t *depth,
-                       const int32_t *s, const int32_t *kown, const int32_t *root,
+                       const typename NM::ST *s, const int32_t *kown, const int32_t *root,
                        const int32_t *freshN, bool first, long long *subS, long long *subWA,
                        long long *TS) {
     GRID_STRIDE(k, cnt) {
         int x = M[k];
         if (!first && !freshN[root[x]]) continue;
-        long long sx = s[x], kx = kown[x];
+        long long sx = (long long)s[x], kx = kown[x];
         int y = x;
         for (int d = depth[x]; d > 0; d--) {
             add64(&subS[y], sx);
@@ -275,8 +276,9 @@ __device__ __forceinline__ void k_credit(int cnt, const int32_t *M, const int32_
     }
 }
 
+template <class NM>
 __device__ __forceinline__ void k_branch(int cnt, const int32_t *M, const uint8_t *oncycle, const int32_t *root,
-                         const int32_t *posr, const int32_t *sigma, MParam mp,
+                         const int32_t *posr, const typename NM::ST *sigma, MParam mp,
                          const long long *subS, const long long *subWA, const long long *subWin,
                          long long *bestsc, unsigned long long *bestkey, long long *msc,
                          int32_t *mq, int pass) {
@@ -292,8 +294,8 @@ __device__ __forceinline__ void k_branch(int cnt, const int32_t *M, const uint8_
                 if (!oncycle[u]) {
                     const int r = root[u];
                     q = posr[r];
-                    const long long m = mp.of(u), sS = subS[u], sA = sigma[r];
-                    sc = sS * (sA - sS) - m * (subWA[u] - subWin[u]);
+                    const long long m = mp.of(u), sS = subS[u], sA = (long long)sigma[r];
+                    sc = NM::cross(sS, sA - sS) - m * (subWA[u] - subWin[u]);
                 }
                 msc[k] = sc;  // the tie pass reads the member's value back
                 mq[k] = q;
@@ -322,9 +324,10 @@ __device__ __forceinline__ void k_branch(int cnt, const int32_t *M, const uint8_
 
 // one block per community with a cycle of length >= 2; one thread per p, the
 // part V = trees (p, q] grows with q: W(V+q, U-q) = W(V,U) + row(q) - 2 W(V,q)
+template <class NM>
 __device__ __forceinline__ void k_cycle(const int32_t *Rdev, const int32_t *rlist, const int32_t *L, const int32_t *coffN,
                         const int32_t *cyc, const long long *moffN, const long long *Mw,
-                        const long long *TS, const int32_t *sigma, MParam mp, int32_t n,
+                        const long long *TS, const typename NM::ST *sigma, MParam mp, int32_t n,
                         long long *bestsc, unsigned long long *bestkey, int pass) {
     const int R = *Rdev;
     for (int q0 = blockIdx.x; q0 < R; q0 += gridDim.x) {
@@ -334,7 +337,7 @@ __device__ __forceinline__ void k_cycle(const int32_t *Rdev, const int32_t *rlis
         const long long m = mp.of(r);
         const int32_t *cy = cyc + coffN[r];
         const long long *Mr = Mw + moffN[r];
-        const long long sA = sigma[r];
+        const long long sA = (long long)sigma[r];
         for (int p = threadIdx.x; p < l; p += blockDim.x) {
             long long cut = 0, sV = 0;
             for (int q = p + 1; q < l; q++) {
@@ -345,7 +348,7 @@ __device__ __forceinline__ void k_cycle(const int32_t *Rdev, const int32_t *rlis
                 if (cp < 0 || cp >= n || cq < 0 || cq >= n) return;  // unfilled slot: skip the community
                 cut += rowq - 2 * inV;
                 sV += TS[cq];
-                long long sc = sV * (sA - sV) - m * cut;
+                long long sc = NM::cross(sV, sA - sV) - m * cut;
                 int u = min(cp, cq), v = max(cp, cq);
                 if (pass == 0) atomicMax(&bestsc[q0], sc);
                 else if (sc == bestsc[q0]) atomicMin(&bestkey[q0], split_key(1, u, v));
@@ -360,12 +363,13 @@ __device__ __forceinline__ void k_cycle(const int32_t *Rdev, const int32_t *rlis
 // the cut), so it records what the corrections need: the cut subtree's sums,
 // u's old parent and entry.  The part cut off, and both parts of a cycle
 // cut, are new (their sums are recomputed in the next round).
+template <class NM>
 __device__ __forceinline__ void k_cut_info(const int32_t *Rdev, const int32_t *rlist,
                            const unsigned long long *bestkey, int32_t n, const int32_t *L,
                            const int32_t *coffN, const int32_t *cyc, const long long *TS,
                            const int32_t *depth, const int32_t *entry, const int32_t *cdist,
                            const long long *subS, const long long *subWA,
-                           const long long *subWin, int32_t *sigma, int4 *cut, long long *cutsum,
+                           const long long *subWin, typename NM::ST *sigma, int4 *cut, long long *cutsum,
                            int32_t *cutpar, int32_t *freshN, int32_t *a, const int32_t *gid,
                            int32_t *splits_per_graph) {
     const int R = *Rdev;
@@ -393,8 +397,9 @@ __device__ __forceinline__ void k_cut_info(const int32_t *Rdev, const int32_t *r
             cutsum[3 * q + 1] = subWA[u];
             cutsum[3 * q + 2] = subWin[u];
             cutpar[q] = a[u];
-            sigma[r] = (int32_t)((long long)sigma[r] - sS);
-            sigma[u] = (int32_t)sS;
+            using ST = typename NM::ST;
+            sigma[r] = (ST)((long long)sigma[r] - sS);  // S is part of A: no component goes negative
+            sigma[u] = (ST)sS;
             a[u] = u;
             freshN[r] = 0;
             freshN[u] = 1;
@@ -405,11 +410,11 @@ __device__ __forceinline__ void k_cut_info(const int32_t *Rdev, const int32_t *r
             const int32_t *cy = cyc + coffN[r];
             long long sV = 0;
             for (int k = p + 1; k <= pq; k++) sV += TS[cy[k]];
-            const long long sA = sigma[r];
+            const long long sA = (long long)sigma[r];
             const int cp = cy[p], cq = cy[pq];
             cut[q] = make_int4(1, p, pq, l);
-            sigma[cq] = (int32_t)sV;
-            sigma[cp] = (int32_t)(sA - sV);
+            sigma[cq] = (typename NM::ST)sV;
+            sigma[cp] = (typename NM::ST)(sA - sV);
             a[cp] = cp;
             a[cq] = cq;
             freshN[cp] = 1;
@@ -686,8 +691,9 @@ __global__ void k_int_fill_big(int cnt, const int32_t *M, const int32_t *rp, con
         __syncthreads();
     }
 }
-__device__ __forceinline__ void k_own_finish(int cnt, const int32_t *M, const int32_t *s, MParam mp,
-                             const int32_t *root, const int32_t *sigma, const long long *kacc,
+template <class NM>
+__device__ __forceinline__ void k_own_finish(int cnt, const int32_t *M, const typename NM::ST *s, MParam mp,
+                             const int32_t *root, const typename NM::ST *sigma, const long long *kacc,
                              const uint8_t *recomp, int32_t *kown, int32_t *flag) {
     GRID_STRIDE(k, cnt) {
         int i = M[k];
@@ -698,8 +704,8 @@ __device__ __forceinline__ void k_own_finish(int cnt, const int32_t *M, const in
             own = kacc[k];
             kown[i] = (int32_t)own;
         }
-        long long si = s[i];
-        if (m * own - si * ((long long)sigma[ci] - si) < 0) flag[ci] = 1;
+        long long si = (long long)s[i];
+        if (m * own - NM::cross(si, (long long)sigma[ci] - si) < 0) flag[ci] = 1;
     }
 }
 
@@ -875,14 +881,16 @@ struct PosCtrl {
 };
 
 
+template <class NM>
 struct PosArgs {
     int32_t n;
     const int32_t *istart, *ideg, *icol, *iw;  // internal entries of the members
-    const int32_t *s;
+    const typename NM::ST *s;
     MParam m;
     int32_t *a, *root, *entry, *depth, *cdist;
     uint8_t *oncycle;
-    int32_t *sigma, *flag, *kown, *listA, *listB, *rlist, *posr, *L, *coff, *epref, *mark, *cyc;
+    typename NM::ST *sigma;
+    int32_t *flag, *kown, *listA, *listB, *rlist, *posr, *L, *coff, *epref, *mark, *cyc;
     long long *msz, *subS, *subWA, *subWin, *credit, *TS, *bestsc, *kacc, *Mw;
     unsigned long long *bestkey;
     int4 *cut, *nf;
@@ -905,7 +913,8 @@ struct PosArgs {
 // All rounds of POSITIVE in one cooperative launch: the phases of a round are
 // separated by grid barriers and the loop ends on the device when no member
 // is left.
-__global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
+template <class NM>
+__global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs<NM> A) {
     const bool rank0 = blockIdx.x == 0 && threadIdx.x == 0;
     PosCtrl *C = A.ctrl;
     int32_t *M = A.listA, *M2 = A.listB;
@@ -966,14 +975,14 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
             GRID_STRIDE(k, mtot) A.Mw[k] = 0;
             GRID_STRIDE(k, ctot) A.cyc[k] = -1;
             GBAR_OR_RETURN();
-            k_walk(cnt, M, A.a, A.depth, A.s, A.kown, A.root, A.freshN, true, A.subS, A.subWA, A.TS);
+            k_walk<NM>(cnt, M, A.a, A.depth, A.s, A.kown, A.root, A.freshN, true, A.subS, A.subWA, A.TS);
             if (ctot > 0)
                 k_cycle_order(cnt, M, A.oncycle, A.root, A.posr, A.L, A.cdist, A.coffN, A.cyc);
             k_edges(cnt, M, A.epref, &C->E, A.istart, A.icol, A.iw, A.a, A.oncycle, A.entry, A.depth,
                     A.root, A.posr, A.L, A.cdist, A.moffN, A.Mw, A.credit);
         } else {
             // later rounds: only the parts cut off in the last round are new
-            k_walk(cnt, M, A.a, A.depth, A.s, A.kown, A.root, A.freshN, false, A.subS, A.subWA, A.TS);
+            k_walk<NM>(cnt, M, A.a, A.depth, A.s, A.kown, A.root, A.freshN, false, A.subS, A.subWA, A.TS);
             k_edges_members(cnt, M, A.root, A.freshN, A.istart, A.ideg, A.icol, A.iw, A.a, A.oncycle,
                             A.depth, A.credit);
         }
@@ -988,15 +997,15 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
         // kacc (rewritten by k_own_members before it is read) and epref (read
         // only by the first round's k_edges, which has finished)
         for (int pass = 0; pass < 2; pass++) {
-            k_branch(cnt, M, A.oncycle, A.root, A.posr, A.sigma, A.m, A.subS, A.subWA, A.subWin,
+            k_branch<NM>(cnt, M, A.oncycle, A.root, A.posr, A.sigma, A.m, A.subS, A.subWA, A.subWin,
                      A.bestsc, A.bestkey, A.kacc, A.epref, pass);
             if (cycles)
-                k_cycle(&C->R, A.rlist, A.L, A.coffN, A.cyc, A.moffN, A.Mw, A.TS, A.sigma, A.m, n,
+                k_cycle<NM>(&C->R, A.rlist, A.L, A.coffN, A.cyc, A.moffN, A.Mw, A.TS, A.sigma, A.m, n,
                         A.bestsc, A.bestkey, pass);
             GBAR_OR_RETURN();
         }
         mark_phase(4);
-        k_cut_info(&C->R, A.rlist, A.bestkey, n, A.L, A.coffN, A.cyc, A.TS, A.depth, A.entry, A.cdist,
+        k_cut_info<NM>(&C->R, A.rlist, A.bestkey, n, A.L, A.coffN, A.cyc, A.TS, A.depth, A.entry, A.cdist,
                    A.subS, A.subWA, A.subWin, A.sigma, A.cut, A.cutsum, A.cutpar, A.freshN, A.a,
                    A.m.gid, A.splits_per_graph);
         GBAR_OR_RETURN();
@@ -1013,7 +1022,7 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs A) {
                   A.subWA, A.subWin, A.TS, A.Mw);
         k_own_members(cnt, M, A.recomp, A.istart, A.ideg, A.icol, A.iw, A.root, A.kacc);
         GBAR_OR_RETURN();
-        k_own_finish(cnt, M, A.s, A.m, A.root, A.sigma, A.kacc, A.recomp, A.kown, A.flag);
+        k_own_finish<NM>(cnt, M, A.s, A.m, A.root, A.sigma, A.kacc, A.recomp, A.kown, A.flag);
         GBAR_OR_RETURN();
         mark_phase(7);
         // members of the still-flagged communities form the next list (its
@@ -1069,9 +1078,11 @@ __global__ void k_dirty(int32_t n, const int32_t *root, const int32_t *prev_root
 // than kOwnWarpMaxDeg are left to k_own_listed_big): flag[root] = 1 when the
 // local gain is negative.
 constexpr int kOwnWarpMaxDeg = 1024;
+template <class NM>
 __global__ void k_own_listed(int cnt, const int32_t *list, const int32_t *rp, const int32_t *col,
-                             const int32_t *w, const int32_t *s, MParam mp, const int32_t *root,
-                             const int32_t *sigma, int32_t *kown, int32_t *flag) {
+                             const int32_t *w, const typename NM::ST *s, MParam mp,
+                             const int32_t *root, const typename NM::ST *sigma, int32_t *kown,
+                             int32_t *flag) {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -1089,14 +1100,16 @@ __global__ void k_own_listed(int cnt, const int32_t *list, const int32_t *rp, co
         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) {
             kown[x] = (int32_t)acc;
-            const long long m = mp.of(x), si = s[x];
-            if (m * acc - si * ((long long)sigma[rx] - si) < 0) flag[rx] = 1;
+            const long long m = mp.of(x), si = (long long)s[x];
+            if (m * acc - NM::cross(si, (long long)sigma[rx] - si) < 0) flag[rx] = 1;
         }
     }
 }
+template <class NM>
 __global__ void k_own_listed_big(int cnt, const int32_t *list, const int32_t *rp, const int32_t *col,
-                                 const int32_t *w, const int32_t *s, MParam mp, const int32_t *root,
-                                 const int32_t *sigma, int32_t *kown, int32_t *flag) {
+                                 const int32_t *w, const typename NM::ST *s, MParam mp,
+                                 const int32_t *root, const typename NM::ST *sigma, int32_t *kown,
+                                 int32_t *flag) {
     __shared__ long long red[32];
     for (long long k = blockIdx.x; k < cnt; k += gridDim.x) {
         const int x = list[k];
@@ -1124,8 +1137,8 @@ __global__ void k_own_listed_big(int cnt, const int32_t *list, const int32_t *rp
             long long t = 0;
             for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += red[q];
             kown[x] = (int32_t)t;
-            const long long m = mp.of(x), si = s[x];
-            if (m * t - si * ((long long)sigma[rx] - si) < 0) flag[rx] = 1;
+            const long long m = mp.of(x), si = (long long)s[x];
+            if (m * t - NM::cross(si, (long long)sigma[rx] - si) < 0) flag[rx] = 1;
         }
         __syncthreads();
     }
@@ -1181,8 +1194,10 @@ int32_t moved_members(int32_t n, const int32_t *acc, const int32_t *acc_cnt, int
     return compact_members(n, nullptr, root, mark.as<int32_t>(), out, scratch, tot, st);
 }
 
+template <class NM>
 long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                           const int32_t *s, MParam m, int32_t *a, Forest &f, int32_t *sigma,
+                           const typename NM::ST *s, MParam m, int32_t *a, Forest &f,
+                           typename NM::ST *sigma,
                            const Buckets &bk, PositiveScratch &ps, cudaStream_t st,
                            long long *rounds_out, long long *visits_out,
                            int32_t *splits_per_graph, const int32_t *prev_root) {
@@ -1217,13 +1232,13 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
         if (nd == 0) return 0;
     }
     if (nd * 16LL > n) {  // most of the graph: the bucketed full pass is cheaper
-        own_weight_nodes(n, rp, col, w, s, m, f.root, sigma, bk, kown, flag, st);
+        own_weight_nodes<NM>(n, rp, col, w, s, m, f.root, sigma, bk, kown, flag, st);
         cnt = compact_members(n, nullptr, f.root, flag, M, ps.mark, ps.tot, st);
     } else {
-        k_own_listed<<<grid_for((long long)nd * 32, 256), 256, 0, st>>>(nd, M2, rp, col, w, s, m, f.root,
+        k_own_listed<NM><<<grid_for((long long)nd * 32, 256), 256, 0, st>>>(nd, M2, rp, col, w, s, m, f.root,
                                                                        sigma, kown, flag);
         SLM_LAUNCH_CHECK();
-        k_own_listed_big<<<grid_for(nd, 1, kNumSMs * 4), 256, 0, st>>>(nd, M2, rp, col, w, s, m, f.root,
+        k_own_listed_big<NM><<<grid_for(nd, 1, kNumSMs * 4), 256, 0, st>>>(nd, M2, rp, col, w, s, m, f.root,
                                                                        sigma, kown, flag);
         SLM_LAUNCH_CHECK();
         cnt = compact_members(nd, M2, f.root, flag, M, ps.mark, ps.tot, st);
@@ -1284,7 +1299,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     int dev = 0, sms = 0, per_sm = 0;
     SLM_CUDA(cudaGetDevice(&dev));
     SLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_positive_rounds, kPosThreads, 0));
+    SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_positive_rounds<NM>, kPosThreads, 0));
     if (per_sm < 1) fail(SLM_ERR_CUDA, "POSITIVE kernel cannot be resident");
     const int nblocks_full = sms * std::min(per_sm, kPosBlocksPerSM);
     ps.bs.ensure(8 * (size_t)nblocks_full * 3, st);
@@ -1293,7 +1308,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     hc.cnt = cnt;
     hc.E = (int32_t)itot;  // bound on the first round's internal entries
     SLM_CUDA(cudaMemcpyAsync(ps.ctrl.get(), &hc, sizeof hc, cudaMemcpyHostToDevice, st));
-    PosArgs A;
+    PosArgs<NM> A;
     A.n = n;
     A.istart = ps.istart.as<int32_t>();
     A.ideg = ps.ideg.as<int32_t>();
@@ -1359,7 +1374,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
         const int nb = tail ? std::min(kPosTailBlocks, nblocks_full) : nblocks_full;
         void *kargs[] = {&A};
         serialised_cooperative(st, [&] {
-            SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_positive_rounds, dim3(nb),
+            SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_positive_rounds<NM>, dim3(nb),
                                                  dim3(kPosThreads), kargs, 0, st));
             SLM_LAUNCH_CHECK();
         });
@@ -1382,6 +1397,17 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
         for (int k = 0; k < kPosPhases; k++) ps.prof_ns[k] += hc.ph[k];
     return splits;
 }
+
+template long long positive_correct<NMSym>(int32_t, const int32_t *, const int32_t *,
+                                          const int32_t *, const int32_t *, MParam, int32_t *,
+                                          Forest &, int32_t *, const Buckets &,
+                                          PositiveScratch &, cudaStream_t, long long *,
+                                          long long *, int32_t *, const int32_t *);
+template long long positive_correct<NMDir>(int32_t, const int32_t *, const int32_t *,
+                                          const int32_t *, const unsigned long long *, MParam,
+                                          int32_t *, Forest &, unsigned long long *,
+                                          const Buckets &, PositiveScratch &, cudaStream_t,
+                                          long long *, long long *, int32_t *, const int32_t *);
 
 // ---------------------------------------------------------------------------
 // Self-check of the grid barrier: `absent` (when >= 0) leaves before the first

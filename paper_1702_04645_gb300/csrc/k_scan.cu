@@ -66,10 +66,12 @@ __device__ __forceinline__ unsigned hash_slot(int c, int lg) {
 
 
 // Decision shared by every scan shape.
-__device__ __forceinline__ void scan_emit(int i, int ci, int si, long long m, const int32_t *sigma,
-                                          long long own, long long bsc, int bc, int32_t *best,
+template <class NM>
+__device__ __forceinline__ void scan_emit(int i, int ci, long long si, long long m,
+                                          const typename NM::ST *sigma, long long own,
+                                          long long bsc, int bc, int32_t *best,
                                           long long *gain, int32_t *kown, unsigned &cand) {
-    long long g = m * own - (long long)si * ((long long)sigma[ci] - si);
+    long long g = m * own - NM::cross(si, (long long)sigma[ci] - si);
     long long gn = (bc != INT_MAX) ? bsc - g : 0;
     if (bc != INT_MAX && gn > 0) {
         best[i] = bc;
@@ -281,21 +283,23 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_insert(const int4 *chunks
 // one block per slice of kHubSlice entries of a hub's list of occupied
 // table slots: partial (own weight, best score, best community), and the
 // slots are reset for the next scan
+template <class NM>
 __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunks, int ntchunk, const int32_t *hubs,
                              const long long *hoff, const long long *uoff, const int *ulist,
-                             const int *ucnt, const int32_t *s, MParam mp, const int32_t *root,
-                             const int32_t *sigma, unsigned long long *tslot,
+                             const int *ucnt, const typename NM::ST *s, MParam mp, const int32_t *root,
+                             const typename NM::ST *sigma, unsigned long long *tslot,
                              long long *part_sc, int32_t *part_cc) {
     constexpr int B = kHubSlice / kBlockThreads;
     for (int tc = blockIdx.x; tc < ntchunk; tc += gridDim.x) {
         const int2 d = tchunks[tc];  // (hub index, first list entry)
         const int i = hubs[d.x];
         const long long m = mp.of(i);
-        const int ci = root[i], si = s[i];
+        const long long si = (long long)s[i];
         const int nu = ucnt[d.x];
         unsigned long long *T = tslot + hoff[d.x];
         const int *ul = ulist + uoff[d.x];
-        int hh[B], kk[B], vv[B], sg[B];
+        int hh[B], kk[B], vv[B];
+        long long sg[B];
 #pragma unroll
         for (int t = 0; t < B; t++) {
             int k = d.y + threadIdx.x + t * kBlockThreads;
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunk
             vv[t] = (int)(unsigned)v;
         }
 #pragma unroll
-        for (int t = 0; t < B; t++) sg[t] = kk[t] >= 0 ? sigma[kk[t]] : 0;
+        for (int t = 0; t < B; t++) sg[t] = kk[t] >= 0 ? (long long)sigma[kk[t]] : 0;
         long long own = 0, sc = LLONG_MIN;
         int cc = INT_MAX;
 #pragma unroll
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunk
             int c = kk[t];
             if (c < 0) continue;
             T[hh[t]] = 0ull;  // leave the table empty for the next sweep
-            long long x = m * (long long)vv[t] - (long long)si * (long long)sg[t];
+            long long x = m * (long long)vv[t] - NM::cross(si, sg[t]);
             if (better(x, c, sc, cc)) { sc = x; cc = c; }
         }
         block_reduce_best(own, sc, cc);
@@ -326,8 +330,10 @@ __global__ void __launch_bounds__(kBlockThreads) k_hub_slices(const int2 *tchunk
         }
     }
 }
-__global__ void k_hub_finish(int nhub, const int32_t *hubs, const int32_t *tc_off, const int32_t *s,
-                             MParam mp, const int32_t *root, const int32_t *sigma,
+template <class NM>
+__global__ void k_hub_finish(int nhub, const int32_t *hubs, const int32_t *tc_off,
+                             const typename NM::ST *s, MParam mp, const int32_t *root,
+                             const typename NM::ST *sigma,
                              unsigned long long *own_acc, const long long *part_sc,
                              const int32_t *part_cc, int *ucnt, int32_t *best, long long *gain,
                              int32_t *kown, unsigned long long *ncand) {
@@ -350,7 +356,7 @@ __global__ void k_hub_finish(int nhub, const int32_t *hubs, const int32_t *tc_of
         }
         if (lane == 0) {
             const long long own = (long long)own_acc[h];
-            scan_emit(i, root[i], s[i], m, sigma, own, sc, cc, best, gain, kown, cand);
+            scan_emit<NM>(i, root[i], (long long)s[i], m, sigma, own, sc, cc, best, gain, kown, cand);
             ucnt[h] = 0;     // the hub's slot list starts empty at the next scan
             own_acc[h] = 0;  // and so does its own-community sum
         }
@@ -385,8 +391,9 @@ __global__ void __launch_bounds__(kBlockThreads) k_own_hub_chunk(const int4 *chu
     }
 }
 
-__global__ void k_own_hub_finish(int nhub, const int32_t *hubs, const int32_t *s, MParam mp,
-                                 const int32_t *root, const int32_t *sigma,
+template <class NM>
+__global__ void k_own_hub_finish(int nhub, const int32_t *hubs, const typename NM::ST *s,
+                                 MParam mp, const int32_t *root, const typename NM::ST *sigma,
                                  const unsigned long long *acc, int32_t *kown, int32_t *flag) {
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < nhub; h += gridDim.x * blockDim.x) {
         int i = hubs[h];
@@ -394,8 +401,8 @@ __global__ void k_own_hub_finish(int nhub, const int32_t *hubs, const int32_t *s
         int ci = root[i];
         long long own = (long long)acc[h];
         kown[i] = (int32_t)own;
-        long long si = s[i];
-        if (m * own - si * ((long long)sigma[ci] - si) < 0) flag[ci] = 1;
+        long long si = (long long)s[i];
+        if (m * own - NM::cross(si, (long long)sigma[ci] - si) < 0) flag[ci] = 1;
     }
 }
 
@@ -416,9 +423,9 @@ __device__ __forceinline__ void pair_consider(PairBest &b, long long sc, int j) 
     if (better(sc, j, b.sc, b.j)) { b.sc = sc; b.j = j; }
 }
 
-template <int G>
+template <class NM, int G>
 __global__ void __launch_bounds__(256) k_assign_group(const int32_t *order, int32_t cnt, const int32_t *rp,
-                               const int32_t *col, const int32_t *w, const int32_t *s,
+                               const int32_t *col, const int32_t *w, const typename NM::ST *s,
                                MParam mp, int32_t *a) {
     constexpr int NPW = 32 / G;
     const int lane = threadIdx.x & 31, gl = lane % G;
@@ -430,12 +437,12 @@ __global__ void __launch_bounds__(256) k_assign_group(const int32_t *order, int3
         int i = vn ? order[idx] : 0;
         const long long m = mp.of(i);
         int start = vn ? rp[i] : 0, end = vn ? rp[i + 1] : 0;
-        long long si = vn ? s[i] : 0;
+        long long si = vn ? (long long)s[i] : 0;
         PairBest b{LLONG_MIN, INT_MAX};
         for (int p = start + gl; p < end; p += G) {
             int j = col[p];
             if (j == i) continue;
-            pair_consider(b, m * (long long)w[p] - si * (long long)s[j], j);
+            pair_consider(b, m * (long long)w[p] - NM::cross(si, (long long)s[j]), j);
         }
 #pragma unroll
         for (int o = G / 2; o; o >>= 1) {
@@ -447,18 +454,19 @@ __global__ void __launch_bounds__(256) k_assign_group(const int32_t *order, int3
     }
 }
 
+template <class NM>
 __global__ void __launch_bounds__(kBlockThreads) k_assign_block(const int32_t *order, int32_t cnt, const int32_t *rp,
-                               const int32_t *col, const int32_t *w, const int32_t *s,
+                               const int32_t *col, const int32_t *w, const typename NM::ST *s,
                                MParam mp, int32_t *a) {
     for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
         int i = order[idx];
         const long long m = mp.of(i);
-        long long si = s[i];
+        long long si = (long long)s[i];
         PairBest b{LLONG_MIN, INT_MAX};
         for (int p = rp[i] + threadIdx.x; p < rp[i + 1]; p += blockDim.x) {
             int j = col[p];
             if (j == i) continue;
-            pair_consider(b, m * (long long)w[p] - si * (long long)s[j], j);
+            pair_consider(b, m * (long long)w[p] - NM::cross(si, (long long)s[j]), j);
         }
         long long dummy = 0;
         block_reduce_best(dummy, b.sc, b.j);
@@ -473,8 +481,9 @@ __global__ void k_assign_empty(const int32_t *order, int32_t cnt, int32_t *a) {
 }
 
 // Target of every accepted node: one warp per node.
+template <class NM>
 __global__ void k_target(const int32_t *list, const int32_t *cnt_dev, const int32_t *rp,
-                         const int32_t *col, const int32_t *w, const int32_t *s, MParam mp,
+                         const int32_t *col, const int32_t *w, const typename NM::ST *s, MParam mp,
                          const int32_t *root, const int32_t *best, int32_t *tgt) {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -484,12 +493,12 @@ __global__ void k_target(const int32_t *list, const int32_t *cnt_dev, const int3
         int i = list[idx];
         const long long m = mp.of(i);
         int want = best[i];
-        long long si = s[i];
+        long long si = (long long)s[i];
         PairBest b{LLONG_MIN, INT_MAX};
         for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
             int j = col[p];
             if (j == i || root[j] != want) continue;
-            pair_consider(b, m * (long long)w[p] - si * (long long)s[j], j);
+            pair_consider(b, m * (long long)w[p] - NM::cross(si, (long long)s[j]), j);
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
@@ -506,18 +515,19 @@ __global__ void k_target(const int32_t *list, const int32_t *cnt_dev, const int3
 // ---------------------------------------------------------------------------
 // Own-community weight and POSITIVE's flags.
 // ---------------------------------------------------------------------------
+template <class NM>
 __device__ __forceinline__ void own_emit(int i, int ci, long long si, long long m,
-                                         const int32_t *sigma, long long own, int32_t *kown,
-                                         int32_t *flag) {
+                                         const typename NM::ST *sigma, long long own,
+                                         int32_t *kown, int32_t *flag) {
     kown[i] = (int32_t)own;
-    long long g = m * own - si * ((long long)sigma[ci] - si);
+    long long g = m * own - NM::cross(si, (long long)sigma[ci] - si);
     if (g < 0) flag[ci] = 1;
 }
 
-template <int G>
+template <class NM, int G>
 __global__ void __launch_bounds__(256) k_own_group(const int32_t *order, int32_t cnt, const int32_t *rp,
-                            const int32_t *col, const int32_t *w, const int32_t *s, MParam mp,
-                            const int32_t *root, const int32_t *sigma, int32_t *kown,
+                            const int32_t *col, const int32_t *w, const typename NM::ST *s, MParam mp,
+                            const int32_t *root, const typename NM::ST *sigma, int32_t *kown,
                             int32_t *flag) {
     constexpr int NPW = 32 / G;
     const int lane = threadIdx.x & 31, gl = lane % G;
@@ -537,13 +547,14 @@ __global__ void __launch_bounds__(256) k_own_group(const int32_t *order, int32_t
             }
 #pragma unroll
         for (int o = G / 2; o; o >>= 1) own += __shfl_xor_sync(FULL, own, o);
-        if (gl == 0 && vn) own_emit(i, ci, s[i], m, sigma, own, kown, flag);
+        if (gl == 0 && vn) own_emit<NM>(i, ci, (long long)s[i], m, sigma, own, kown, flag);
     }
 }
 
+template <class NM>
 __global__ void __launch_bounds__(kBlockThreads) k_own_block(const int32_t *order, int32_t cnt, const int32_t *rp,
-                            const int32_t *col, const int32_t *w, const int32_t *s, MParam mp,
-                            const int32_t *root, const int32_t *sigma, int32_t *kown,
+                            const int32_t *col, const int32_t *w, const typename NM::ST *s, MParam mp,
+                            const int32_t *root, const typename NM::ST *sigma, int32_t *kown,
                             int32_t *flag) {
     for (long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
         int i = order[idx];
@@ -566,26 +577,29 @@ __global__ void __launch_bounds__(kBlockThreads) k_own_block(const int32_t *orde
         long long sc = LLONG_MIN;
         int cc = INT_MAX;
         block_reduce_best(own, sc, cc);
-        if (threadIdx.x == 0) own_emit(i, ci, s[i], m, sigma, own, kown, flag);
+        if (threadIdx.x == 0) own_emit<NM>(i, ci, (long long)s[i], m, sigma, own, kown, flag);
     }
 }
 
-__global__ void k_local_gain(int32_t n, const int32_t *s, MParam mp, const int32_t *root,
-                             const int32_t *sigma, const int32_t *kown, long long *g) {
+template <class NM>
+__global__ void k_local_gain(int32_t n, const typename NM::ST *s, MParam mp, const int32_t *root,
+                             const typename NM::ST *sigma, const int32_t *kown, long long *g) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const long long m = mp.of((int)i);
-        long long si = s[i];
-        g[i] = m * (long long)kown[i] - si * ((long long)sigma[root[i]] - si);
+        long long si = (long long)s[i];
+        g[i] = m * (long long)kown[i] - NM::cross(si, (long long)sigma[root[i]] - si);
     }
 }
 
 }  // namespace
 
-void local_gain_nodes(int32_t n, const int32_t *s, MParam m, const int32_t *root,
-                      const int32_t *sigma, const int32_t *kown, long long *g, cudaStream_t st) {
+template <class NM>
+void local_gain_nodes(int32_t n, const typename NM::ST *s, MParam m, const int32_t *root,
+                      const typename NM::ST *sigma, const int32_t *kown, long long *g,
+                      cudaStream_t st) {
     if (n <= 0) return;
-    k_local_gain<<<grid_for(n, 256), 256, 0, st>>>(n, s, m, root, sigma, kown, g);
+    k_local_gain<NM><<<grid_for(n, 256), 256, 0, st>>>(n, s, m, root, sigma, kown, g);
     SLM_LAUNCH_CHECK();
 }
 
@@ -728,8 +742,9 @@ static int blocks_for_groups(long long cnt, int nodes_per_warp, int threads = 25
     return grid_for(warps * 32, threads, kNumSMs * per_sm);
 }
 
+template <class NM>
 void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                  const int32_t *s, MParam m, const Buckets &bk, int32_t *a, cudaStream_t st) {
+                  const typename NM::ST *s, MParam m, const Buckets &bk, int32_t *a, cudaStream_t st) {
     if (n <= 0) return;
     const int32_t *ord = bk.order.as<int32_t>();
     auto seg = [&](int b) { return std::make_pair(ord + bk.off[b], bk.off[b + 1] - bk.off[b]); };
@@ -739,39 +754,40 @@ void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_
     }
     {
         auto [o, c] = seg(kBucketG4);
-        if (c) { k_assign_group<4><<<blocks_for_groups(c, 8), 256, 0, st>>>(o, c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+        if (c) { k_assign_group<NM, 4><<<blocks_for_groups(c, 8), 256, 0, st>>>(o, c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
     }
     {
         auto [o, c] = seg(kBucketG8);
-        if (c) { k_assign_group<8><<<blocks_for_groups(c, 4), 256, 0, st>>>(o, c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+        if (c) { k_assign_group<NM, 8><<<blocks_for_groups(c, 4), 256, 0, st>>>(o, c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
     }
     {
         auto [o, c] = seg(kBucketG16);
-        if (c) { k_assign_group<16><<<blocks_for_groups(c, 2), 256, 0, st>>>(o, c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+        if (c) { k_assign_group<NM, 16><<<blocks_for_groups(c, 2), 256, 0, st>>>(o, c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
     }
     {
         // 17..256 edges: one warp per node, lanes stride over the row
         int c = bk.off[kBucketWarpHash + 1] - bk.off[kBucketG32];
-        if (c) { k_assign_group<32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+        if (c) { k_assign_group<NM, 32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
     }
     {
         int c = bk.off[kBucketHub + 1] - bk.off[kBucketBlockS];
-        if (c) { k_assign_block<<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
+        if (c) { k_assign_block<NM><<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, a); SLM_LAUNCH_CHECK(); }
     }
 }
 
+template <class NM>
 void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                const int32_t *s, MParam m, const int32_t *root, const int32_t *sigma,
-                const Buckets &bk, int32_t *best, long long *gain, int32_t *kown,
-                unsigned long long *ncand, cudaStream_t st) {
+                const typename NM::ST *s, MParam m, const int32_t *root,
+                const typename NM::ST *sigma, const Buckets &bk, int32_t *best,
+                long long *gain, int32_t *kown, unsigned long long *ncand, cudaStream_t st) {
     if (n <= 0) return;
     const int32_t *ord = bk.order.as<int32_t>();
     auto cnt = [&](int b) { return bk.off[b + 1] - bk.off[b]; };
     const ScanTuning tu = scan_tuning();
     const bool side = tu.streams > 1;
     Buckets &bl = const_cast<Buckets &>(bk);
-    build_scan_layout(bl, n, rp, col, w, s, st);
-    pack_community_totals(n, root, sigma, bl.cs.as<int2>(), st);
+    build_scan_layout<NM>(bl, n, rp, col, w, s, st);
+    pack_community_totals<NM>(n, root, sigma, bl, st);
     // the buckets write disjoint nodes: run them side by side
     if (side) {
         SLM_CUDA(cudaEventRecord(bk.fork, st));
@@ -796,13 +812,13 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
             bk.hub_uoff.as<long long>(), col, w, root, bk.tslot.as<unsigned long long>(),
             bk.ulist.as<int>(), bk.hub_ucnt.as<int>(), bk.hub_own.as<unsigned long long>());
         SLM_LAUNCH_CHECK();
-        k_hub_slices<<<grid_for(bk.ntchunk, 1, kNumSMs * tu.blocks_hub), kBlockThreads, 0, s3>>>(
+        k_hub_slices<NM><<<grid_for(bk.ntchunk, 1, kNumSMs * tu.blocks_hub), kBlockThreads, 0, s3>>>(
             bk.tchunks.as<int2>(), bk.ntchunk, hubs, bk.hub_off.as<long long>(),
             bk.hub_uoff.as<long long>(), bk.ulist.as<int>(), bk.hub_ucnt.as<int>(), s, m, root, sigma,
             bk.tslot.as<unsigned long long>(),
             bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>());
         SLM_LAUNCH_CHECK();
-        k_hub_finish<<<grid_for((long long)bk.nhub * 32, 256), 256, 0, s3>>>(
+        k_hub_finish<NM><<<grid_for((long long)bk.nhub * 32, 256), 256, 0, s3>>>(
             bk.nhub, hubs, bk.tc_off.as<int32_t>(), s, m, root, sigma, bk.hub_own.as<unsigned long long>(),
             bk.part_sc.as<long long>(), bk.part_cc.as<int32_t>(), bk.hub_ucnt.as<int>(), best, gain,
             kown, ncand);
@@ -817,7 +833,7 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
         if (!any) return;
         mark(coarse, 0, so);
         for (int f : fines)
-            scan_fine_class(f, bk, m, best, gain, kown, ncand, tu, so);
+            scan_fine_class<NM>(f, bk, s, m, best, gain, kown, ncand, tu, so);
         mark(coarse, 1, so);
     };
     run_classes(kBucketBlockL, {kFine4096}, s0);
@@ -851,35 +867,37 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
     }
 }
 
+template <class NM>
 void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                      const int32_t *s, MParam m, const int32_t *root, const int32_t *sigma,
-                      const Buckets &bk, int32_t *kown, int32_t *flag, cudaStream_t st) {
+                      const typename NM::ST *s, MParam m, const int32_t *root,
+                      const typename NM::ST *sigma, const Buckets &bk, int32_t *kown,
+                      int32_t *flag, cudaStream_t st) {
     if (n <= 0) return;
     const int32_t *ord = bk.order.as<int32_t>();
     // isolated nodes: own weight 0, local gain 0 (never flagged)
     int c0 = bk.off[kBucketEmpty + 1] - bk.off[kBucketEmpty];
     if (c0) {
-        k_own_group<4><<<blocks_for_groups(c0, 8), 256, 0, st>>>(ord, c0, rp, col, w, s, m, root, sigma, kown, flag);
+        k_own_group<NM, 4><<<blocks_for_groups(c0, 8), 256, 0, st>>>(ord, c0, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (int c = bk.off[kBucketG4 + 1] - bk.off[kBucketG4]) {
-        k_own_group<4><<<blocks_for_groups(c, 8), 256, 0, st>>>(ord + bk.off[kBucketG4], c, rp, col, w, s, m, root, sigma, kown, flag);
+        k_own_group<NM, 4><<<blocks_for_groups(c, 8), 256, 0, st>>>(ord + bk.off[kBucketG4], c, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (int c = bk.off[kBucketG8 + 1] - bk.off[kBucketG8]) {
-        k_own_group<8><<<blocks_for_groups(c, 4), 256, 0, st>>>(ord + bk.off[kBucketG8], c, rp, col, w, s, m, root, sigma, kown, flag);
+        k_own_group<NM, 8><<<blocks_for_groups(c, 4), 256, 0, st>>>(ord + bk.off[kBucketG8], c, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (int c = bk.off[kBucketG16 + 1] - bk.off[kBucketG16]) {
-        k_own_group<16><<<blocks_for_groups(c, 2), 256, 0, st>>>(ord + bk.off[kBucketG16], c, rp, col, w, s, m, root, sigma, kown, flag);
+        k_own_group<NM, 16><<<blocks_for_groups(c, 2), 256, 0, st>>>(ord + bk.off[kBucketG16], c, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (int c = bk.off[kBucketWarpHash + 1] - bk.off[kBucketG32]) {
-        k_own_group<32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, kown, flag);
+        k_own_group<NM, 32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (int c = bk.off[kBucketBlockL + 1] - bk.off[kBucketBlockS]) {
-        k_own_block<<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, root, sigma, kown, flag);
+        k_own_block<NM><<<grid_for(c, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(ord + bk.off[kBucketBlockS], c, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (bk.nhub > 0) {
@@ -888,19 +906,41 @@ void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const in
         k_own_hub_chunk<<<grid_for(bk.nchunk, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(
             bk.chunks.as<int4>(), bk.nchunk, hubs, col, w, root, bk.hub_acc.as<unsigned long long>());
         SLM_LAUNCH_CHECK();
-        k_own_hub_finish<<<grid_for(bk.nhub, 256), 256, 0, st>>>(bk.nhub, hubs, s, m, root, sigma,
+        k_own_hub_finish<NM><<<grid_for(bk.nhub, 256), 256, 0, st>>>(bk.nhub, hubs, s, m, root, sigma,
                                                                bk.hub_acc.as<unsigned long long>(), kown, flag);
         SLM_LAUNCH_CHECK();
     }
 }
 
+template <class NM>
 void target_nodes(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt, const int32_t *rp,
-                  const int32_t *col, const int32_t *w, const int32_t *s, MParam m,
+                  const int32_t *col, const int32_t *w, const typename NM::ST *s, MParam m,
                   const int32_t *root, const int32_t *best, int32_t *tgt, cudaStream_t st) {
     if (max_cnt <= 0) return;
-    k_target<<<grid_for((long long)max_cnt * 32, 256, kNumSMs * 16), 256, 0, st>>>(
+    k_target<NM><<<grid_for((long long)max_cnt * 32, 256, kNumSMs * 16), 256, 0, st>>>(
         list, cnt_dev, rp, col, w, s, m, root, best, tgt);
     SLM_LAUNCH_CHECK();
 }
+
+// the two null models (undirected and directed graphs)
+#define SLM_SCAN_INSTANTIATE(NM)                                                                   \
+    template void assign_nodes<NM>(int32_t, const int32_t *, const int32_t *, const int32_t *,    \
+                                   const NM::ST *, MParam, const Buckets &, int32_t *,            \
+                                   cudaStream_t);                                                 \
+    template void scan_nodes<NM>(int32_t, const int32_t *, const int32_t *, const int32_t *,      \
+                                 const NM::ST *, MParam, const int32_t *, const NM::ST *,         \
+                                 const Buckets &, int32_t *, long long *, int32_t *,              \
+                                 unsigned long long *, cudaStream_t);                             \
+    template void own_weight_nodes<NM>(int32_t, const int32_t *, const int32_t *, const int32_t *, \
+                                       const NM::ST *, MParam, const int32_t *, const NM::ST *,   \
+                                       const Buckets &, int32_t *, int32_t *, cudaStream_t);      \
+    template void local_gain_nodes<NM>(int32_t, const NM::ST *, MParam, const int32_t *,          \
+                                       const NM::ST *, const int32_t *, long long *, cudaStream_t); \
+    template void target_nodes<NM>(const int32_t *, const int32_t *, int32_t, const int32_t *,    \
+                                   const int32_t *, const int32_t *, const NM::ST *, MParam,      \
+                                   const int32_t *, const int32_t *, int32_t *, cudaStream_t);
+SLM_SCAN_INSTANTIATE(NMSym)
+SLM_SCAN_INSTANTIATE(NMDir)
+#undef SLM_SCAN_INSTANTIATE
 
 }  // namespace slm

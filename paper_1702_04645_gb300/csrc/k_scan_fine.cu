@@ -65,8 +65,9 @@ __global__ void k_lay_deg(int32_t cnt, int32_t copy_end, const int32_t *order, c
 }
 
 // one warp per bucketed node: its record, and its row copied into ent
+template <class NM>
 __global__ void k_lay_fill(int32_t cnt, int32_t copy_end, const int32_t *order, const int32_t *rp,
-                           const int32_t *col, const int32_t *w, const int32_t *s,
+                           const int32_t *col, const int32_t *w, const typename NM::ST *s,
                            const int32_t *est, int4 *nrec, int2 *ent) {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -75,13 +76,16 @@ __global__ void k_lay_fill(int32_t cnt, int32_t copy_end, const int32_t *order, 
         const int i = order[k];
         const int start = rp[i], d = rp[i + 1] - start;
         const int e0 = est[k];
-        if (lane == 0) nrec[k] = make_int4(i, e0, d, s[i]);
+        // a directed graph's packed strength does not fit: the scan reads it from s
+        if (lane == 0) nrec[k] = make_int4(i, e0, d, NM::kDirected ? 0 : (int)s[i]);
         if (k < copy_end)
             for (int p = lane; p < d; p += 32) ent[e0 + p] = make_int2(col[start + p], w[start + p]);
     }
 }
 
-// cs[v] = (root_v, Sigma_{root_v}) for every node of the graph
+// cs[v] = (root_v, Sigma_{root_v}) for every node of the graph: int2 for an
+// undirected graph; int4 (root, packed total low and high words, 0) for a
+// directed one
 __global__ void k_pack_cs(int32_t n, const int32_t *root, const int32_t *sigma, int2 *cs) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (long long)gridDim.x * blockDim.x) {
@@ -89,32 +93,47 @@ __global__ void k_pack_cs(int32_t n, const int32_t *root, const int32_t *sigma, 
         cs[v] = make_int2(c, sigma[c]);
     }
 }
+__global__ void k_pack_cs(int32_t n, const int32_t *root, const unsigned long long *sigma,
+                          int4 *cs) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int c = root[v];
+        const unsigned long long t = sigma[c];
+        cs[v] = make_int4(c, (int)(unsigned)(t & 0xffffffffull), (int)(unsigned)(t >> 32), 0);
+    }
+}
+
+template <class NM> struct CsOf { using T = int2; };
+template <> struct CsOf<NMDir> { using T = int4; };
 
 }  // namespace
 
+template <class NM>
 void build_scan_layout(Buckets &bk, int32_t n, const int32_t *rp, const int32_t *col,
-                       const int32_t *w, const int32_t *s, cudaStream_t st) {
+                       const int32_t *w, const typename NM::ST *s, cudaStream_t st) {
+    using CS = typename CsOf<NM>::T;
     const void *src[4] = {rp, col, w, s};
     bool same = bk.lay_ready;
     for (int k = 0; k < 4; k++) same = same && bk.lay_src[k] == src[k];
     const void *cs_before = bk.cs.get();
-    bk.cs.ensure(sizeof(int2) * (size_t)(n > 0 ? n : 1), st);
-    if (bk.cs.get() != cs_before || !bk.cs_tex) {
+    bk.cs.ensure(sizeof(CS) * (size_t)(n > 0 ? n : 1), st);
+    if (bk.cs.get() != cs_before || !bk.cs_tex || bk.cs_elem != (int)sizeof(CS)) {
         if (bk.cs_tex) cudaDestroyTextureObject(bk.cs_tex);
         bk.cs_tex = 0;
         int dev = 0, maxw = 0;
         SLM_CUDA(cudaGetDevice(&dev));
         SLM_CUDA(cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture1DLinearWidth, dev));
-        const size_t elems = bk.cs.bytes() / sizeof(int2);
+        const size_t elems = bk.cs.bytes() / sizeof(CS);
         if (elems <= (size_t)maxw) {
             cudaResourceDesc rd{};
             rd.resType = cudaResourceTypeLinear;
             rd.res.linear.devPtr = bk.cs.get();
-            rd.res.linear.desc = cudaCreateChannelDesc<int2>();
-            rd.res.linear.sizeInBytes = elems * sizeof(int2);
+            rd.res.linear.desc = cudaCreateChannelDesc<CS>();
+            rd.res.linear.sizeInBytes = elems * sizeof(CS);
             cudaTextureDesc td{};
             td.readMode = cudaReadModeElementType;
             SLM_CUDA(cudaCreateTextureObject(&bk.cs_tex, &rd, &td, nullptr));
+            bk.cs_elem = (int)sizeof(CS);
         }
     }
     if (same) return;
@@ -132,7 +151,7 @@ void build_scan_layout(Buckets &bk, int32_t n, const int32_t *rp, const int32_t 
         SLM_CUDA(cudaMemcpyAsync(&ne, tot.get(), sizeof ne, cudaMemcpyDeviceToHost, st));
         stream_sync(st);
         bk.ent.ensure(sizeof(int2) * (size_t)(ne > 0 ? ne : 1), st);
-        k_lay_fill<<<grid_for((long long)cnt * 32, 256), 256, 0, st>>>(
+        k_lay_fill<NM><<<grid_for((long long)cnt * 32, 256), 256, 0, st>>>(
             cnt, copy_end, ord, rp, col, w, s, est.as<int32_t>(), bk.nrec.as<int4>(), bk.ent.as<int2>());
         SLM_LAUNCH_CHECK();
     }
@@ -140,21 +159,25 @@ void build_scan_layout(Buckets &bk, int32_t n, const int32_t *rp, const int32_t 
     bk.lay_ready = true;
 }
 
-void pack_community_totals(int32_t n, const int32_t *root, const int32_t *sigma, int2 *cs,
-                           cudaStream_t st) {
+template <class NM>
+void pack_community_totals(int32_t n, const int32_t *root, const typename NM::ST *sigma,
+                           Buckets &bk, cudaStream_t st) {
     if (n <= 0) return;
-    k_pack_cs<<<grid_for(n, 256), 256, 0, st>>>(n, root, sigma, cs);
+    k_pack_cs<<<grid_for(n, 256), 256, 0, st>>>(n, root, sigma,
+                                                 bk.cs.as<typename CsOf<NM>::T>());
     SLM_LAUNCH_CHECK();
 }
 
 namespace {
 
+template <class NM>
 struct FsArgs {
     const int4 *nrec;  // records of this fine class (offset into the bucket order)
     int32_t cnt;       // nodes of this fine class
     const int2 *ent;
-    const int2 *cs;
+    const typename CsOf<NM>::T *cs;
     cudaTextureObject_t cs_tex;  // the same array through the texture path (0: none)
+    const typename NM::ST *s;    // node strengths (read only for a directed graph)
     MParam mp;
     int32_t *best;
     long long *gain;
@@ -164,10 +187,11 @@ struct FsArgs {
 
 // The decision of one node (Algorithm MAXIMAL): stay unless the best other
 // community beats the own one by a positive amount.
-__device__ __forceinline__ void fs_emit(const FsArgs &A, int i, int ci, int sig_ci, int si,
-                                        long long m, long long own, long long bsc, int bc,
-                                        unsigned &cand) {
-    const long long g = m * own - (long long)si * ((long long)sig_ci - si);
+template <class NM>
+__device__ __forceinline__ void fs_emit(const FsArgs<NM> &A, int i, int ci, long long sig_ci,
+                                        long long si, long long m, long long own, long long bsc,
+                                        int bc, unsigned &cand) {
+    const long long g = m * own - NM::cross(si, sig_ci - si);
     const long long gn = bc != INT_MAX ? bsc - g : 0;
     if (bc != INT_MAX && gn > 0) {
         A.best[i] = bc;
@@ -189,9 +213,21 @@ __device__ __forceinline__ void fs_count(unsigned long long *ctr, unsigned v) {
 // (community, total) of node j: through the texture pipe when the array has a
 // texture object (the random gathers then leave the load/store pipe to the
 // shared-memory table), else a plain load
-__device__ __forceinline__ int2 cs_at(const FsArgs &A, int j) {
-    if (A.cs_tex) return tex1Dfetch<int2>(A.cs_tex, j);
-    return A.cs[j];
+__device__ __forceinline__ void cs_at(const FsArgs<NMSym> &A, int j, int &c, int &sig) {
+    const int2 q = A.cs_tex ? tex1Dfetch<int2>(A.cs_tex, j) : A.cs[j];
+    c = q.x;
+    sig = q.y;
+}
+__device__ __forceinline__ void cs_at(const FsArgs<NMDir> &A, int j, int &c, long long &sig) {
+    const int4 q = A.cs_tex ? tex1Dfetch<int4>(A.cs_tex, j) : A.cs[j];
+    c = q.x;
+    sig = (long long)(((unsigned long long)(unsigned)q.z << 32) | (unsigned long long)(unsigned)q.y);
+}
+
+// strength of the node of record r
+__device__ __forceinline__ int node_s(const FsArgs<NMSym> &, const int4 &r) { return r.w; }
+__device__ __forceinline__ long long node_s(const FsArgs<NMDir> &A, const int4 &r) {
+    return (long long)A.s[r.x];
 }
 
 __device__ __forceinline__ unsigned slot_of(int c, int lg) {
@@ -267,16 +303,20 @@ __device__ __forceinline__ int table_lg(int d) {
 // ---------------------------------------------------------------------------
 // One thread per node, at most D entries: communities grouped in registers.
 // ---------------------------------------------------------------------------
-template <int D>
-__global__ void __launch_bounds__(256) k_fs_thread(FsArgs A) {
+template <class NM, int D>
+__global__ void __launch_bounds__(256) k_fs_thread(FsArgs<NM> A) {
     unsigned cand = 0;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < A.cnt;
          k += (long long)gridDim.x * blockDim.x) {
         const int4 r = A.nrec[k];
-        const int i = r.x, e0 = r.y, d = r.z, si = r.w;
-        const int2 me = cs_at(A, i);
+        const int i = r.x, e0 = r.y, d = r.z;
+        const typename NM::V si = node_s(A, r);
+        int me_c;
+        typename NM::V me_s;
+        cs_at(A, i, me_c, me_s);
         const long long m = A.mp.of(i);
-        int c[D], wv[D], sg[D];
+        int c[D], wv[D];
+        typename NM::V sg[D];
 #pragma unroll
         for (int t = 0; t < D; t++) {
             const int2 e = t < d ? A.ent[e0 + t] : make_int2(i, 0);
@@ -286,9 +326,7 @@ __global__ void __launch_bounds__(256) k_fs_thread(FsArgs A) {
 #pragma unroll
         for (int t = 0; t < D; t++) {
             if (c[t] != i) {
-                const int2 q = cs_at(A, c[t]);
-                c[t] = q.x;
-                sg[t] = q.y;
+                cs_at(A, c[t], c[t], sg[t]);
             } else {
                 c[t] = -1;  // the node's own self-loop, or a slot past the row
                 sg[t] = 0;
@@ -306,14 +344,14 @@ __global__ void __launch_bounds__(256) k_fs_thread(FsArgs A) {
             long long k_ic = 0;
 #pragma unroll
             for (int u = t; u < D; u++) k_ic += c[u] == c[t] ? wv[u] : 0;
-            if (c[t] == me.x) {
+            if (c[t] == me_c) {
                 own = k_ic;
             } else {
-                const long long x = m * k_ic - (long long)si * (long long)sg[t];
+                const long long x = m * k_ic - NM::cross(si, sg[t]);
                 if (better(x, c[t], bsc, bc)) { bsc = x; bc = c[t]; }
             }
         }
-        fs_emit(A, i, me.x, me.y, si, m, own, bsc, bc, cand);
+        fs_emit<NM>(A, i, me_c, me_s, si, m, own, bsc, bc, cand);
     }
     fs_count(A.ncand, cand);
 }
@@ -324,8 +362,8 @@ __global__ void __launch_bounds__(256) k_fs_thread(FsArgs A) {
 // ---------------------------------------------------------------------------
 constexpr int kFsWarps = 8;  // warps per block of the lane-group shape
 
-template <int L, int EPL>
-__global__ void __launch_bounds__(kFsWarps * 32) k_fs_lanes(FsArgs A) {
+template <class NM, int L, int EPL>
+__global__ void __launch_bounds__(kFsWarps * 32) k_fs_lanes(FsArgs<NM> A) {
     constexpr int NPW = 32 / L;
     constexpr int CAP = 2 * L * EPL;
     constexpr int LG = __builtin_ctz(CAP);
@@ -343,8 +381,10 @@ __global__ void __launch_bounds__(kFsWarps * 32) k_fs_lanes(FsArgs A) {
         const long long k = base + grp;
         const bool valid = k < A.cnt;
         const int4 r = valid ? A.nrec[k] : make_int4(0, 0, 0, 0);
-        const int i = r.x, e0 = r.y, d = r.z, si = r.w;
-        int c[EPL], wv[EPL], sg[EPL], cl[EPL];
+        const int i = r.x, e0 = r.y, d = r.z;
+        const typename NM::V si = valid ? node_s(A, r) : 0;
+        int c[EPL], wv[EPL], cl[EPL];
+        typename NM::V sg[EPL];
 #pragma unroll
         for (int t = 0; t < EPL; t++) {
             const int p = gl + t * L;
@@ -352,24 +392,21 @@ __global__ void __launch_bounds__(kFsWarps * 32) k_fs_lanes(FsArgs A) {
             c[t] = e.x;
             wv[t] = e.y;
         }
-        const int2 me = valid ? cs_at(A, i) : make_int2(-1, 0);
+        int me_c = -1;
+        typename NM::V me_s = 0;
+        if (valid) cs_at(A, i, me_c, me_s);
 #pragma unroll
         for (int t = 0; t < EPL; t++) {
-            if (c[t] != i) {
-                const int2 q = cs_at(A, c[t]);
-                c[t] = q.x;
-                sg[t] = q.y;
-            } else {
-                c[t] = -1;
-            }
+            if (c[t] != i) cs_at(A, c[t], c[t], sg[t]);
+            else c[t] = -1;
         }
         // weight to the own community is summed in registers: it never
         // enters the table, where all its entries would hit one slot
         long long own = 0;
 #pragma unroll
         for (int t = 0; t < EPL; t++) {
-            if (c[t] == me.x) own += wv[t];
-            cl[t] = (c[t] >= 0 && c[t] != me.x) ? table_add(T, LG, c[t], wv[t]) : -1;
+            if (c[t] == me_c) own += wv[t];
+            cl[t] = (c[t] >= 0 && c[t] != me_c) ? table_add(T, LG, c[t], wv[t]) : -1;
         }
         __syncwarp();
         const long long m = A.mp.of(i);
@@ -380,7 +417,7 @@ __global__ void __launch_bounds__(kFsWarps * 32) k_fs_lanes(FsArgs A) {
             if (cl[t] < 0) continue;
             const long long k_ic = (long long)(unsigned)T[cl[t]];
             T[cl[t]] = 0ull;  // empty again for the next node
-            const long long x = m * k_ic - (long long)si * (long long)sg[t];
+            const long long x = m * k_ic - NM::cross(si, sg[t]);
             if (better(x, c[t], bsc, bc)) { bsc = x; bc = c[t]; }
         }
 #pragma unroll
@@ -390,7 +427,7 @@ __global__ void __launch_bounds__(kFsWarps * 32) k_fs_lanes(FsArgs A) {
             const int occ = __shfl_xor_sync(FULL, bc, o);
             if (better(osc, occ, bsc, bc)) { bsc = osc; bc = occ; }
         }
-        if (gl == 0 && valid) fs_emit(A, i, me.x, me.y, si, m, own, bsc, bc, cand);
+        if (gl == 0 && valid) fs_emit<NM>(A, i, me_c, me_s, si, m, own, bsc, bc, cand);
         __syncwarp();
     }
     fs_count(A.ncand, cand);
@@ -406,8 +443,8 @@ constexpr size_t fs_block_smem() {
     return 2 * sizeof(unsigned) * 2 * T * EPL;
 }
 
-template <int T, int EPL>
-__global__ void __launch_bounds__(T) k_fs_block(FsArgs A) {
+template <class NM, int T, int EPL>
+__global__ void __launch_bounds__(T) k_fs_block(FsArgs<NM> A) {
     constexpr int CAP = 2 * T * EPL;
     constexpr int NW = T / 32;
     extern __shared__ __align__(16) unsigned tabd[];
@@ -427,26 +464,25 @@ __global__ void __launch_bounds__(T) k_fs_block(FsArgs A) {
         pe[t] = p < r.z ? A.ent[r.y + p] : make_int2(r.x, 0);
     }
     for (; k < A.cnt; k += gridDim.x) {
-        const int i = r.x, si = r.w;
+        const int i = r.x;
+        const typename NM::V si = node_s(A, r);
         const int lg = table_lg(r.z);
-        const int2 me = cs_at(A, i);
-        int c[EPL], wv[EPL], sg[EPL], cl[EPL], ck[EPL];
+        int me_c;
+        typename NM::V me_s;
+        cs_at(A, i, me_c, me_s);
+        int c[EPL], wv[EPL], cl[EPL], ck[EPL];
+        typename NM::V sg[EPL];
 #pragma unroll
         for (int t = 0; t < EPL; t++) {
             wv[t] = pe[t].y;
-            if (pe[t].x != i) {
-                const int2 q = cs_at(A, pe[t].x);
-                c[t] = q.x;
-                sg[t] = q.y;
-            } else {
-                c[t] = -1;
-            }
+            if (pe[t].x != i) cs_at(A, pe[t].x, c[t], sg[t]);
+            else c[t] = -1;
         }
         long long own = 0;  // the own community stays out of the table, as above
 #pragma unroll
         for (int t = 0; t < EPL; t++) {
-            if (c[t] == me.x) own += wv[t];
-            ck[t] = (c[t] >= 0 && c[t] != me.x) ? c[t] : -1;
+            if (c[t] == me_c) own += wv[t];
+            ck[t] = (c[t] >= 0 && c[t] != me_c) ? c[t] : -1;
         }
         table_insert<EPL>(K, W, lg, ck, wv, cl);
         // the next node's entries are in flight while this one is decided
@@ -465,7 +501,7 @@ __global__ void __launch_bounds__(T) k_fs_block(FsArgs A) {
         for (int t = 0; t < EPL; t++) {
             if (cl[t] < 0) continue;
             const long long k_ic = (long long)wv[t] + (long long)W[cl[t]];
-            const long long x = m * k_ic - (long long)si * (long long)sg[t];
+            const long long x = m * k_ic - NM::cross(si, sg[t]);
             if (better(x, c[t], bsc, bc)) { bsc = x; bc = c[t]; }
         }
 #pragma unroll
@@ -489,7 +525,7 @@ __global__ void __launch_bounds__(T) k_fs_block(FsArgs A) {
                 const int occ = __shfl_xor_sync(FULL, bc, o);
                 if (better(osc, occ, bsc, bc)) { bsc = osc; bc = occ; }
             }
-            if (lane == 0) fs_emit(A, i, me.x, me.y, si, m, own, bsc, bc, cand);
+            if (lane == 0) fs_emit<NM>(A, i, me_c, me_s, si, m, own, bsc, bc, cand);
         }
         __syncthreads();  // the table is empty and r_* are free for the next node
         r = rn;
@@ -514,15 +550,17 @@ int fs_grid(long long units, int per_block, int per_sm) {
 }  // namespace
 
 // Launch the scan of fine class f on stream so.
-void scan_fine_class(int f, const Buckets &bk, MParam mp, int32_t *best, long long *gain,
-                     int32_t *kown, unsigned long long *ncand, const ScanTuning &tu,
-                     cudaStream_t so) {
-    FsArgs A;
+template <class NM>
+void scan_fine_class(int f, const Buckets &bk, const typename NM::ST *s, MParam mp, int32_t *best,
+                     long long *gain, int32_t *kown, unsigned long long *ncand,
+                     const ScanTuning &tu, cudaStream_t so) {
+    FsArgs<NM> A;
     A.nrec = bk.nrec.as<int4>() + bk.foff[f];
     A.cnt = bk.foff[f + 1] - bk.foff[f];
     A.ent = bk.ent.as<int2>();
-    A.cs = bk.cs.as<int2>();
+    A.cs = bk.cs.as<typename CsOf<NM>::T>();
     A.cs_tex = bk.cs_tex;
+    A.s = s;
     A.mp = mp;
     A.best = best;
     A.gain = gain;
@@ -543,53 +581,65 @@ void scan_fine_class(int f, const Buckets &bk, MParam mp, int32_t *best, long lo
     static std::atomic<unsigned long long> d1{0}, d2{0};
     switch (f) {
     case kFine4:
-        if (alt) lanes(k_fs_lanes<4, 1>, 4, tu.blocks_group);
-        else k_fs_thread<4><<<fs_grid(A.cnt, 256, tu.blocks_group), 256, 0, so>>>(A);
+        if (alt) lanes(k_fs_lanes<NM, 4, 1>, 4, tu.blocks_group);
+        else k_fs_thread<NM, 4><<<fs_grid(A.cnt, 256, tu.blocks_group), 256, 0, so>>>(A);
         break;
     case kFine8:
-        if (alt) lanes(k_fs_lanes<8, 1>, 8, tu.blocks_group);
-        else k_fs_thread<8><<<fs_grid(A.cnt, 256, tu.blocks_group), 256, 0, so>>>(A);
+        if (alt) lanes(k_fs_lanes<NM, 8, 1>, 8, tu.blocks_group);
+        else k_fs_thread<NM, 8><<<fs_grid(A.cnt, 256, tu.blocks_group), 256, 0, so>>>(A);
         break;
     case kFine16:
-        if (alt) lanes(k_fs_lanes<8, 2>, 8, tu.blocks_group);
-        else lanes(k_fs_lanes<4, 4>, 4, tu.blocks_group);
+        if (alt) lanes(k_fs_lanes<NM, 8, 2>, 8, tu.blocks_group);
+        else lanes(k_fs_lanes<NM, 4, 4>, 4, tu.blocks_group);
         break;
     case kFine32:
-        if (alt) lanes(k_fs_lanes<16, 2>, 16, tu.blocks_group);
-        else lanes(k_fs_lanes<8, 4>, 8, tu.blocks_group);
+        if (alt) lanes(k_fs_lanes<NM, 16, 2>, 16, tu.blocks_group);
+        else lanes(k_fs_lanes<NM, 8, 4>, 8, tu.blocks_group);
         break;
     case kFine64:
-        if (alt) lanes(k_fs_lanes<32, 2>, 32, tu.blocks_warp);
-        else lanes(k_fs_lanes<16, 4>, 16, tu.blocks_warp);
+        if (alt) lanes(k_fs_lanes<NM, 32, 2>, 32, tu.blocks_warp);
+        else lanes(k_fs_lanes<NM, 16, 4>, 16, tu.blocks_warp);
         break;
     case kFine128:
-        if (alt) block(k_fs_block<64, 2>, 64, fs_block_smem<64, 2>(), d1, 4 * tu.blocks_warp);
-        else lanes(k_fs_lanes<32, 4>, 32, tu.blocks_warp);
+        if (alt) block(k_fs_block<NM, 64, 2>, 64, fs_block_smem<64, 2>(), d1, 4 * tu.blocks_warp);
+        else lanes(k_fs_lanes<NM, 32, 4>, 32, tu.blocks_warp);
         break;
     case kFine256:
-        if (alt) block(k_fs_block<64, 4>, 64, fs_block_smem<64, 4>(), d1, 4 * tu.blocks_warp);
-        else lanes(k_fs_lanes<32, 8>, 32, tu.blocks_warp);
+        if (alt) block(k_fs_block<NM, 64, 4>, 64, fs_block_smem<64, 4>(), d1, 4 * tu.blocks_warp);
+        else lanes(k_fs_lanes<NM, 32, 8>, 32, tu.blocks_warp);
         break;
     case kFine512:
-        if (alt) block(k_fs_block<256, 2>, 256, fs_block_smem<256, 2>(), d1, tu.blocks_small);
-        else block(k_fs_block<128, 4>, 128, fs_block_smem<128, 4>(), d1, 2 * tu.blocks_small);
+        if (alt) block(k_fs_block<NM, 256, 2>, 256, fs_block_smem<256, 2>(), d1, tu.blocks_small);
+        else block(k_fs_block<NM, 128, 4>, 128, fs_block_smem<128, 4>(), d1, 2 * tu.blocks_small);
         break;
     case kFine1024:
-        if (alt) block(k_fs_block<512, 2>, 512, fs_block_smem<512, 2>(), d1, tu.blocks_small);
-        else block(k_fs_block<256, 4>, 256, fs_block_smem<256, 4>(), d1, tu.blocks_small);
+        if (alt) block(k_fs_block<NM, 512, 2>, 512, fs_block_smem<512, 2>(), d1, tu.blocks_small);
+        else block(k_fs_block<NM, 256, 4>, 256, fs_block_smem<256, 4>(), d1, tu.blocks_small);
         break;
     case kFine2048:
-        if (alt) block(k_fs_block<512, 4>, 512, fs_block_smem<512, 4>(), d1, tu.blocks_mid);
-        else block(k_fs_block<256, 8>, 256, fs_block_smem<256, 8>(), d1, tu.blocks_mid);
+        if (alt) block(k_fs_block<NM, 512, 4>, 512, fs_block_smem<512, 4>(), d1, tu.blocks_mid);
+        else block(k_fs_block<NM, 256, 8>, 256, fs_block_smem<256, 8>(), d1, tu.blocks_mid);
         break;
     case kFine4096:
-        if (alt) block(k_fs_block<1024, 4>, 1024, fs_block_smem<1024, 4>(), d2, tu.blocks_large);
-        else block(k_fs_block<512, 8>, 512, fs_block_smem<512, 8>(), d1, tu.blocks_large);
+        if (alt) block(k_fs_block<NM, 1024, 4>, 1024, fs_block_smem<1024, 4>(), d2, tu.blocks_large);
+        else block(k_fs_block<NM, 512, 8>, 512, fs_block_smem<512, 8>(), d1, tu.blocks_large);
         break;
     default:
         return;
     }
     SLM_LAUNCH_CHECK();
 }
+
+#define SLM_FINE_INSTANTIATE(NM)                                                                \
+    template void build_scan_layout<NM>(Buckets &, int32_t, const int32_t *, const int32_t *,    \
+                                        const int32_t *, const NM::ST *, cudaStream_t);          \
+    template void pack_community_totals<NM>(int32_t, const int32_t *, const NM::ST *, Buckets &, \
+                                            cudaStream_t);                                       \
+    template void scan_fine_class<NM>(int, const Buckets &, const NM::ST *, MParam, int32_t *,   \
+                                      long long *, int32_t *, unsigned long long *,              \
+                                      const ScanTuning &, cudaStream_t);
+SLM_FINE_INSTANTIATE(NMSym)
+SLM_FINE_INSTANTIATE(NMDir)
+#undef SLM_FINE_INSTANTIATE
 
 }  // namespace slm

@@ -27,6 +27,10 @@ struct slm_graph {
     int32_t nnz0 = 0;
     long long m = 0;
     DevBuf rp, col, w, s;  // the input graph (device copies)
+    // a directed graph: rp/col/w hold U = W + W^T and s2 the packed (out, in)
+    // strengths (Section 2.4); s is unused
+    bool directed = false;
+    DevBuf s2;
     bool has_run = false;
     struct Level {
         int32_t n = 0, K = 0;
@@ -122,13 +126,14 @@ __global__ void k_fill_ones(long long n, int32_t *p) {
 }
 
 // POSITIVE until no community holds a node with a negative local gain.
+template <class NM>
 long long positive_all(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                       const int32_t *s, long long m, Work &W, cudaStream_t st,
+                       const typename NM::ST *s, long long m, Work &W, cudaStream_t st,
                        PhaseTimer *tm = nullptr, bool since_last = false) {
     if (tm) tm->start();
     long long rounds = 0, visits = 0;
-    long long splits = slm::positive_correct(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f,
-                                             W.sigma.as<int32_t>(), W.bk, W.ps, st, &rounds,
+    long long splits = slm::positive_correct<NM>(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f,
+                                             W.sigma.as<typename NM::ST>(), W.bk, W.ps, st, &rounds,
                                              &visits, nullptr,
                                              since_last ? W.prev_root.as<int32_t>() : nullptr);
     if (tm) {
@@ -144,18 +149,20 @@ struct SweepCounts {
 };
 
 // One MAXIMAL correction: scan, branch gains, draw, target, write.
+template <class NM>
 SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                         const int32_t *s, long long m, Work &W, unsigned long long seed,
+                         const typename NM::ST *s, long long m, Work &W, unsigned long long seed,
                          unsigned long long P, int level, int sweep, bool stop_if_no_cand,
                          cudaStream_t st, slm::HostCounters &hc, PhaseTimer *tm = nullptr) {
     SweepCounts c;
     unsigned long long *ctr = W.ctr();
     if (tm) tm->start();
     SLM_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
-    slm::community_sigma(n, W.f.root, s, W.sigma.as<int32_t>(), st);
+    using ST = typename NM::ST;
+    slm::community_sigma(n, W.f.root, s, W.sigma.as<ST>(), st);
     if (tm) tm->stop(kPhSigma);
     if (tm) tm->start();
-    slm::scan_nodes(n, rp, col, w, s, m, W.f.root, W.sigma.as<int32_t>(), W.bk,
+    slm::scan_nodes<NM>(n, rp, col, w, s, m, W.f.root, W.sigma.as<ST>(), W.bk,
                     W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), ctr, st);
     if (tm) tm->stop(kPhScan);
     if (tm) tm->start();
@@ -166,7 +173,7 @@ SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const
         if (tm) tm->stop(kPhMove);
         return c;
     }
-    slm::branch_gains(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
+    slm::branch_gains<NM>(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f, W.sigma.as<ST>(),
                       W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), W.bs,
                       W.bg.as<long long>(), st);
     int32_t *acc_cnt = reinterpret_cast<int32_t *>(ctr + 2);
@@ -180,7 +187,7 @@ SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const
         if (tm) tm->stop(kPhMove);
         return c;
     }
-    slm::target_nodes(W.acclist.as<int32_t>(), acc_cnt, (int32_t)c.acc, rp, col, w, s, m,
+    slm::target_nodes<NM>(W.acclist.as<int32_t>(), acc_cnt, (int32_t)c.acc, rp, col, w, s, m,
                       W.f.root, W.best.as<int32_t>(), W.tgt.as<int32_t>(), st);
     slm::apply_moves(W.acclist.as<int32_t>(), acc_cnt, (int32_t)c.acc, W.tgt.as<int32_t>(),
                      W.a.as<int32_t>(), st);
@@ -188,7 +195,9 @@ SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const
     return c;
 }
 
+template <class NM>
 void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
+    using ST = typename NM::ST;
     if (opt.max_sweeps < 0 || opt.max_sweeps > 65535 || opt.max_levels < 0 ||
         opt.max_levels > 65535 || opt.accept_p32 > (1ull << 32))
         slm::fail(SLM_ERR_INVALID_ARGUMENT, "options out of range");
@@ -212,7 +221,8 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
     int32_t n = n0;
     int32_t nnz = g->nnz0;
     const int32_t *rp = g->rp.as<int32_t>(), *col = g->col.as<int32_t>(), *w = g->w.as<int32_t>();
-    const int32_t *s = g->s.as<int32_t>();
+    const ST *s = NM::kDirected ? reinterpret_cast<const ST *>(g->s2.get())
+                                : reinterpret_cast<const ST *>(g->s.get());
     DevBuf lrp, lcol, lw, ls;  // owned aggregated graph
     const long long m = g->m;
     Work W;
@@ -233,17 +243,17 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         stt.n = n;
         stt.nnz = nnz;
         if (tm) tm->start();
-        slm::assign_nodes(n, rp, col, w, s, m, W.bk, W.a.as<int32_t>(), st);
+        slm::assign_nodes<NM>(n, rp, col, w, s, m, W.bk, W.a.as<int32_t>(), st);
         if (tm) tm->stop(kPhAssign);
         if (tm) tm->start();
         slm::forest_analyse(n, W.a.as<int32_t>(), W.f, st);
         if (tm) tm->stop(kPhComponents);
-        if (!(opt.flags & SLM_FLAG_NO_POSITIVE)) stt.splits += positive_all(n, rp, col, w, s, m, W, st, tm);
+        if (!(opt.flags & SLM_FLAG_NO_POSITIVE)) stt.splits += positive_all<NM>(n, rp, col, w, s, m, W, st, tm);
         int sweep = 0;
         int status = 2;
         for (; sweep < opt.max_sweeps; sweep++) {
             slm::check_run_control();
-            SweepCounts c = maximal_once(n, rp, col, w, s, m, W, opt.seed, opt.accept_p32, t, sweep,
+            SweepCounts c = maximal_once<NM>(n, rp, col, w, s, m, W, opt.seed, opt.accept_p32, t, sweep,
                                          true, st, hc, tm);
             stt.candidates += c.cand;
             stt.edges_scanned += nnz;
@@ -278,7 +288,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
                 else slm::forest_analyse_subset(na, W.alist.as<int32_t>(), W.a.as<int32_t>(), W.f, st);
                 if (tm) tm->stop(kPhComponents);
                 if (!(opt.flags & SLM_FLAG_NO_POSITIVE))
-                    spl = positive_all(n, rp, col, w, s, m, W, st, tm, 16LL * c.acc <= n);
+                    spl = positive_all<NM>(n, rp, col, w, s, m, W, st, tm, 16LL * c.acc <= n);
                 stt.splits += spl;
             }
             g->trace.push_back({t, sweep, c.cand, c.pos, c.acc, spl});
@@ -308,8 +318,14 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         // AGGREGATE
         DevBuf nrp, ncol, nw;
         int32_t nnz2 = slm::aggregate_graph(n, rp, col, w, id.as<int32_t>(), K, nrp, ncol, nw, st);
-        DevBuf ns(4 * (size_t)K, st);
-        slm::strengths(K, nrp.as<int32_t>(), nw.as<int32_t>(), ns.as<int32_t>(), st);
+        // strengths of the next level: row sums of the aggregated graph, or
+        // for a directed graph the (out, in) pairs summed per community
+        DevBuf ns(sizeof(ST) * (size_t)(K > 0 ? K : 1), st);
+        if (NM::kDirected)
+            slm::sum_strengths_by(n, id.as<int32_t>(), reinterpret_cast<const unsigned long long *>(s), K,
+                                  ns.as<unsigned long long>(), st);
+        else
+            slm::strengths(K, nrp.as<int32_t>(), nw.as<int32_t>(), ns.as<int32_t>(), st);
         L.labels = std::move(id);
         g->levels.push_back(std::move(L));
         lrp = std::move(nrp);
@@ -319,7 +335,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         rp = lrp.as<int32_t>();
         col = lcol.as<int32_t>();
         w = lw.as<int32_t>();
-        s = ls.as<int32_t>();
+        s = ls.as<ST>();
         n = K;
         nnz = nnz2;
         if (tm) tm->stop(kPhLevel);
@@ -423,6 +439,101 @@ slm_status slm_create_graph(int32_t n, const int32_t *row_ptr, const int32_t *co
     return st;
 }
 
+slm_status slm_create_graph_directed(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                                     const int32_t *weights, int where, void *stream,
+                                     slm_graph **out) {
+    if (!out) return SLM_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    auto g = std::make_unique<slm_graph>();
+    slm_status st = guarded(nullptr, [&] {
+        cudaStream_t s = as_stream(stream);
+        if (n < 0 || !row_ptr || (where != SLM_HOST && where != SLM_DEVICE))
+            slm::fail(SLM_ERR_INVALID_ARGUMENT, "bad n, row_ptr or where");
+        // W on the host: U = W + W^T is built here, once
+        std::vector<int32_t> rp((size_t)n + 1);
+        auto fetch = [&](void *dst, const void *src, size_t bytes) {
+            if (where == SLM_HOST) std::memcpy(dst, src, bytes);
+            else SLM_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+        };
+        fetch(rp.data(), row_ptr, sizeof(int32_t) * rp.size());
+        long long nnz = 0;
+        check_csr_host(n, rp.data(), &nnz);
+        if (nnz >= (1LL << 30)) slm::fail(SLM_ERR_OVERFLOW, "too many entries");
+        if (nnz > 0 && !col_idx) slm::fail(SLM_ERR_INVALID_ARGUMENT, "col_idx is NULL");
+        std::vector<int32_t> col((size_t)nnz), w((size_t)nnz, 1);
+        if (nnz > 0) {
+            fetch(col.data(), col_idx, sizeof(int32_t) * (size_t)nnz);
+            if (weights) fetch(w.data(), weights, sizeof(int32_t) * (size_t)nnz);
+        }
+        std::vector<long long> so((size_t)n, 0), si((size_t)n, 0);
+        long long m = 0;
+        for (int32_t i = 0; i < n; i++)
+            for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+                const int32_t j = col[p];
+                if (j < 0 || j >= n || (p > rp[i] && j <= col[p - 1]))
+                    slm::fail(SLM_ERR_INVALID_ARGUMENT, "column index out of range, unsorted or duplicated");
+                if (w[p] <= 0) slm::fail(SLM_ERR_INVALID_ARGUMENT, "non-positive weight");
+                so[i] += w[p];
+                si[j] += w[p];
+                m += w[p];
+                // m_w < 2^30 keeps every packed total and every int64 gain exact
+                if (m >= (1LL << 30)) slm::fail(SLM_ERR_OVERFLOW, "m_w must be below 2^30 for a directed graph");
+            }
+        // W^T by counting (its rows come out with ascending columns), then
+        // row i of U merges row i of W and row i of W^T
+        std::vector<int32_t> tp((size_t)n + 1, 0), tc((size_t)nnz), tw((size_t)nnz);
+        for (long long p = 0; p < nnz; p++) tp[(size_t)col[p] + 1]++;
+        for (int32_t v = 0; v < n; v++) tp[v + 1] += tp[v];
+        std::vector<int32_t> fill(tp.begin(), tp.end() - 1);
+        for (int32_t i = 0; i < n; i++)
+            for (int32_t p = rp[i]; p < rp[i + 1]; p++) {
+                const int32_t q = fill[col[p]]++;
+                tc[q] = i;
+                tw[q] = w[p];
+            }
+        std::vector<int32_t> urp((size_t)n + 1, 0), ucol, uw;
+        ucol.reserve((size_t)(2 * nnz));
+        uw.reserve((size_t)(2 * nnz));
+        for (int32_t i = 0; i < n; i++) {
+            int32_t x = rp[i], y = tp[i];
+            while (x < rp[i + 1] || y < tp[i + 1]) {
+                if (y >= tp[i + 1] || (x < rp[i + 1] && col[x] < tc[y])) {
+                    ucol.push_back(col[x]); uw.push_back(w[x]); x++;
+                } else if (x >= rp[i + 1] || tc[y] < col[x]) {
+                    ucol.push_back(tc[y]); uw.push_back(tw[y]); y++;
+                } else {
+                    ucol.push_back(col[x]); uw.push_back(w[x] + tw[y]); x++; y++;
+                }
+            }
+            urp[i + 1] = (int32_t)ucol.size();
+        }
+        const long long nnzu = (long long)ucol.size();
+        std::vector<unsigned long long> s2((size_t)n);
+        for (int32_t i = 0; i < n; i++) s2[i] = ((unsigned long long)so[i] << 32) | (unsigned long long)si[i];
+        g->directed = true;
+        g->n0 = n;
+        g->nnz0 = (int32_t)nnzu;
+        g->m = m;
+        g->rp.alloc(4 * ((size_t)n + 1), s);
+        g->col.alloc(4 * (size_t)(nnzu > 0 ? nnzu : 1), s);
+        g->w.alloc(4 * (size_t)(nnzu > 0 ? nnzu : 1), s);
+        g->s.alloc(16, s);
+        g->s2.alloc(8 * (size_t)(n > 0 ? n : 1), s);
+        SLM_CUDA(cudaMemcpyAsync(g->rp.get(), urp.data(), 4 * ((size_t)n + 1), cudaMemcpyHostToDevice, s));
+        if (nnzu > 0) {
+            SLM_CUDA(cudaMemcpyAsync(g->col.get(), ucol.data(), 4 * (size_t)nnzu, cudaMemcpyHostToDevice, s));
+            SLM_CUDA(cudaMemcpyAsync(g->w.get(), uw.data(), 4 * (size_t)nnzu, cudaMemcpyHostToDevice, s));
+        }
+        if (n > 0)
+            SLM_CUDA(cudaMemcpyAsync(g->s2.get(), s2.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+        slm::stream_sync(s);  // the host vectors go out of scope
+    });
+    if (st == SLM_OK) *out = g.release();
+    return st;
+}
+
+int32_t slm_graph_is_directed(const slm_graph *g) { return g && g->directed ? 1 : 0; }
+
 slm_status slm_run(slm_graph *g, const slm_options *opt, void *stream) {
     if (!g) return SLM_ERR_INVALID_ARGUMENT;
     slm_options o;
@@ -436,7 +547,10 @@ slm_status slm_run(slm_graph *g, const slm_options *opt, void *stream) {
     const bool had_run = g->has_run;
     g->levels.clear();
     g->trace.clear();
-    const slm_status st = guarded(g, [&] { run_impl(g, o, as_stream(stream)); });
+    const slm_status st = guarded(g, [&] {
+        if (g->directed) run_impl<slm::NMDir>(g, o, as_stream(stream));
+        else run_impl<slm::NMSym>(g, o, as_stream(stream));
+    });
     if (st != SLM_OK) {
         g->levels = std::move(levels);
         g->trace = std::move(trace);
@@ -483,6 +597,22 @@ slm_status slm_get_partition(const slm_graph *g, int32_t level, int32_t *labels,
     });
 }
 
+}  // extern "C"
+
+namespace {
+// exact numerator of a labelling of the input nodes, for either kind of graph
+long long graph_modularity_num(const slm_graph *g, const int32_t *labels) {
+    if (g->directed)
+        return slm::modularity_num_directed(g->n0, g->rp.as<int32_t>(), g->col.as<int32_t>(),
+                                            g->w.as<int32_t>(), g->s2.as<unsigned long long>(),
+                                            labels, g->m, nullptr);
+    return slm::modularity_num(g->n0, g->rp.as<int32_t>(), g->col.as<int32_t>(),
+                               g->w.as<int32_t>(), labels, g->m, nullptr);
+}
+}  // namespace
+
+extern "C" {
+
 slm_status slm_modularity(const slm_graph *g, int32_t level, double *q) {
     if (!g || !q) return SLM_ERR_INVALID_ARGUMENT;
     if (!g->has_run) return SLM_ERR_NOT_RUN;
@@ -490,8 +620,7 @@ slm_status slm_modularity(const slm_graph *g, int32_t level, double *q) {
     slm_graph *gm = const_cast<slm_graph *>(g);
     return guarded(gm, [&] {
         const DevBuf &lab = level == -1 ? g->final_comp : g->levels[level].comp;
-        long long num = slm::modularity_num(g->n0, g->rp.as<int32_t>(), g->col.as<int32_t>(),
-                                            g->w.as<int32_t>(), lab.as<int32_t>(), g->m, nullptr);
+        long long num = graph_modularity_num(g, lab.as<int32_t>());
         *q = slm::modularity_from_num(num, g->m);
     });
 }
@@ -510,8 +639,7 @@ slm_status slm_modularity_of(const slm_graph *g, const int32_t *labels, int wher
         if (g->n0 > 0) SLM_CUDA(cudaMemcpy(h.data(), lab.get(), 4 * h.size(), cudaMemcpyDeviceToHost));
         for (int32_t v : h)
             if (v < 0 || v >= g->n0) slm::fail(SLM_ERR_INVALID_ARGUMENT, "label out of range");
-        long long num = slm::modularity_num(g->n0, g->rp.as<int32_t>(), g->col.as<int32_t>(),
-                                            g->w.as<int32_t>(), lab.as<int32_t>(), g->m, nullptr);
+        long long num = graph_modularity_num(g, lab.as<int32_t>());
         *q = slm::modularity_from_num(num, g->m);
     });
 }
@@ -648,7 +776,7 @@ slm_status slm_step_assign(int32_t n, const int32_t *row_ptr, const int32_t *col
         cudaStream_t st = as_stream(stream);
         slm::Buckets bk;
         bk.build(n, row_ptr, st);
-        slm::assign_nodes(n, row_ptr, col, w, s, m_w, bk, a, st);
+        slm::assign_nodes<slm::NMSym>(n, row_ptr, col, w, s, m_w, bk, a, st);
         slm::stream_sync(st);
     });
 }
@@ -695,15 +823,15 @@ slm_status slm_step_scan(int32_t n, const int32_t *row_ptr, const int32_t *col, 
         W.init(n, row_ptr, st);
         slm::community_sigma(n, root, s, W.sigma.as<int32_t>(), st);
         SLM_CUDA(cudaMemsetAsync(W.ctr(), 0, 64, st));
-        slm::scan_nodes(n, row_ptr, col, w, s, m_w, root, W.sigma.as<int32_t>(), W.bk, best,
+        slm::scan_nodes<slm::NMSym>(n, row_ptr, col, w, s, m_w, root, W.sigma.as<int32_t>(), W.bk, best,
                         reinterpret_cast<long long *>(gain), W.kown.as<int32_t>(), W.ctr(), st);
         if (g_out && n > 0) {
             // own-community weights without the scan's early outs, then g
             DevBuf flag(4 * (size_t)n, st);
             SLM_CUDA(cudaMemsetAsync(flag.get(), 0, 4 * (size_t)n, st));
-            slm::own_weight_nodes(n, row_ptr, col, w, s, m_w, root, W.sigma.as<int32_t>(), W.bk,
+            slm::own_weight_nodes<slm::NMSym>(n, row_ptr, col, w, s, m_w, root, W.sigma.as<int32_t>(), W.bk,
                                   W.kown.as<int32_t>(), flag.as<int32_t>(), st);
-            slm::local_gain_nodes(n, s, m_w, root, W.sigma.as<int32_t>(), W.kown.as<int32_t>(),
+            slm::local_gain_nodes<slm::NMSym>(n, s, m_w, root, W.sigma.as<int32_t>(), W.kown.as<int32_t>(),
                                   reinterpret_cast<long long *>(g_out), st);
         }
         slm::stream_sync(st);
@@ -723,9 +851,9 @@ slm_status slm_step_branch_gain(int32_t n, const int32_t *row_ptr, const int32_t
         slm::community_sigma(n, W.f.root, s, W.sigma.as<int32_t>(), st);
         // own-community weights of the snapshot
         SLM_CUDA(cudaMemsetAsync(W.ctr(), 0, 64, st));
-        slm::scan_nodes(n, row_ptr, col, w, s, m_w, W.f.root, W.sigma.as<int32_t>(), W.bk,
+        slm::scan_nodes<slm::NMSym>(n, row_ptr, col, w, s, m_w, W.f.root, W.sigma.as<int32_t>(), W.bk,
                         W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), W.ctr(), st);
-        slm::branch_gains(n, row_ptr, col, w, s, m_w, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
+        slm::branch_gains<slm::NMSym>(n, row_ptr, col, w, s, m_w, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
                           best, reinterpret_cast<const long long *>(gain), W.kown.as<int32_t>(), W.bs,
                           reinterpret_cast<long long *>(bg), st);
         slm::stream_sync(st);
@@ -743,7 +871,7 @@ slm_status slm_step_maximal(int32_t n, const int32_t *row_ptr, const int32_t *co
         Work W;
         load_state(W, n, row_ptr, a, st);
         slm::HostCounters hc;
-        SweepCounts c = maximal_once(n, row_ptr, col, w, s, m_w, W, seed, accept_p32, level, sweep,
+        SweepCounts c = maximal_once<slm::NMSym>(n, row_ptr, col, w, s, m_w, W, seed, accept_p32, level, sweep,
                                      false, st, hc);
         if (n > 0) SLM_CUDA(cudaMemcpyAsync(a, W.a.get(), 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
         slm::stream_sync(st);
@@ -761,7 +889,7 @@ slm_status slm_step_positive(int32_t n, const int32_t *row_ptr, const int32_t *c
         cudaStream_t st = as_stream(stream);
         Work W;
         load_state(W, n, row_ptr, a, st);
-        *splits_host = positive_all(n, row_ptr, col, w, s, m_w, W, st);
+        *splits_host = positive_all<slm::NMSym>(n, row_ptr, col, w, s, m_w, W, st);
         if (n > 0) {
             SLM_CUDA(cudaMemcpyAsync(a, W.a.get(), 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
             SLM_CUDA(cudaMemcpyAsync(root, W.f.root, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));

@@ -153,11 +153,11 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
         spl_d.ensure(4 * (size_t)G, st);
         SLM_CUDA(cudaMemsetAsync(spl_d.get(), 0, 4 * (size_t)G, st));
         // ASSIGN, COMPONENTS, POSITIVE over the whole forest
-        assign_nodes(n, rp, col, w, s, mp, W.bk, W.a.as<int32_t>(), st);
+        assign_nodes<NMSym>(n, rp, col, w, s, mp, W.bk, W.a.as<int32_t>(), st);
         forest_analyse(n, W.a.as<int32_t>(), W.f, st);
         long long rounds = 0, visits = 0;
         if (!(opt.flags & SLM_FLAG_NO_POSITIVE))
-            positive_correct(n, rp, col, w, s, mp, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(), W.bk,
+            positive_correct<NMSym>(n, rp, col, w, s, mp, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(), W.bk,
                              W.ps, st, &rounds, &visits, spl_d.as<int32_t>());
         int nactive = 0;
         for (int g = 0; g < G; g++) {
@@ -185,7 +185,7 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
             unsigned long long *ctr = W.ctr();
             SLM_CUDA(cudaMemsetAsync(ctr, 0, 64, st));
             community_sigma(n, W.f.root, s, W.sigma.as<int32_t>(), st);
-            scan_nodes(n, rp, col, w, s, mp, W.f.root, W.sigma.as<int32_t>(), W.bk,
+            scan_nodes<NMSym>(n, rp, col, w, s, mp, W.f.root, W.sigma.as<int32_t>(), W.bk,
                        W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), ctr, st);
             cand_d.ensure(4 * (size_t)G, st);
             SLM_CUDA(cudaMemsetAsync(cand_d.get(), 0, 4 * (size_t)G, st));
@@ -207,7 +207,7 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
             nactive = still;
             if (nactive == 0) break;
             to_device(active_d, active, st);
-            branch_gains(n, rp, col, w, s, mp, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
+            branch_gains<NMSym>(n, rp, col, w, s, mp, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
                          W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), W.bs,
                          W.bg.as<long long>(), st);
             pg_d.ensure(8 * (size_t)G, st);
@@ -233,7 +233,7 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
             }
             nactive = still;
             if (nacc > 0) {
-                target_nodes(W.acclist.as<int32_t>(), acc_cnt, nacc, rp, col, w, s, mp, W.f.root,
+                target_nodes<NMSym>(W.acclist.as<int32_t>(), acc_cnt, nacc, rp, col, w, s, mp, W.f.root,
                              W.best.as<int32_t>(), W.tgt.as<int32_t>(), st);
                 apply_moves(W.acclist.as<int32_t>(), acc_cnt, nacc, W.tgt.as<int32_t>(),
                             W.a.as<int32_t>(), st);
@@ -248,7 +248,7 @@ void run_batch(slm_batch *B, const slm_options &opt, cudaStream_t st) {
                 if (2LL * na > n) forest_analyse(n, W.a.as<int32_t>(), W.f, st);
                 else forest_analyse_subset(na, W.alist.as<int32_t>(), W.a.as<int32_t>(), W.f, st);
                 if (!(opt.flags & SLM_FLAG_NO_POSITIVE))
-                    positive_correct(n, rp, col, w, s, mp, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
+                    positive_correct<NMSym>(n, rp, col, w, s, mp, W.a.as<int32_t>(), W.f, W.sigma.as<int32_t>(),
                                      W.bk, W.ps, st, &rounds, &visits, spl_d.as<int32_t>(),
                                      16LL * nacc <= n ? W.prev_root.as<int32_t>() : nullptr);
             }

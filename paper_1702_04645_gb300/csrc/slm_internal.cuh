@@ -69,6 +69,39 @@ struct RngParam {
     __device__ __forceinline__ int local(int i) const { return gid ? i - goff[gid[i]] : i; }
 };
 
+// Null model of the modularity (Section 2.4, Q_w).  Every gain is
+// m_w (weight term) minus null-model products of a strength and a total.
+//  * NMSym, undirected graphs: one strength s_i per node (int32), totals
+//    Sigma_C = sum of s, and a product is s * Sigma.
+//  * NMDir, directed graphs: the scans read U = W + W^T, and a node carries
+//    (s_i^out, s_i^in), a community (Sigma^out, Sigma^in), packed in one
+//    64-bit word as out << 32 | in (each below 2^30).  The product of two
+//    packed pairs is a^out b^in + a^in b^out.  Packed sums and differences
+//    are plain 64-bit arithmetic whenever no component goes negative, which
+//    holds for every sum of strengths and for the difference of a set's total
+//    and a subset's; expressions whose components may be negative are
+//    expanded into products of such terms instead.
+// Every value then equals the exact change of the numerator, in NMDir twice
+// what NMSym gives on a symmetric graph, so the decisions are the same.
+struct NMSym {
+    using ST = int32_t;  // stored strength or community total
+    using V = int32_t;   // the same held in registers by the scan kernels
+    static constexpr bool kDirected = false;
+    static constexpr int kDiv = 1;  // numerator = sum_C (m W_in - cross(S, S)) / kDiv
+    __host__ __device__ static long long cross(long long a, long long b) { return a * b; }
+};
+struct NMDir {
+    using ST = unsigned long long;
+    using V = long long;
+    static constexpr bool kDirected = true;
+    static constexpr int kDiv = 2;  // U counts every internal arc twice
+    __host__ __device__ static long long cross(long long a, long long b) {
+        const unsigned long long ua = (unsigned long long)a, ub = (unsigned long long)b;
+        return (long long)(ua >> 32) * (long long)(ub & 0xffffffffull) +
+               (long long)(ua & 0xffffffffull) * (long long)(ub >> 32);
+    }
+};
+
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 inline int grid_for(long long n, int block, int max_blocks = 152 * 32) {
     long long g = (n + block - 1) / block;
@@ -225,6 +258,13 @@ long long strengths(int32_t n, const int32_t *rp, const int32_t *w, int32_t *s_o
 // Sigma[C] = sum of s over root == C (Sigma zeroed here).
 void community_sigma(int32_t n, const int32_t *root, const int32_t *s, int32_t *sigma,
                      cudaStream_t st);
+// The same for packed (out, in) strengths of a directed graph.
+void community_sigma(int32_t n, const int32_t *root, const unsigned long long *s,
+                     unsigned long long *sigma, cudaStream_t st);
+// out[id[v]] += s[v] for packed strengths (out zeroed here): the strengths of
+// the next level of a directed graph.
+void sum_strengths_by(int32_t n, const int32_t *id, const unsigned long long *s, int32_t K,
+                      unsigned long long *out, cudaStream_t st);
 // id[v] = rank of root[v] among names in use; returns K (host-synchronous).
 int32_t compact_labels(int32_t n, const int32_t *root, int32_t *id, int32_t *scratch_n,
                        cudaStream_t s);
@@ -233,6 +273,11 @@ void compose_labels(int32_t n0, int32_t *comp, const int32_t *id, cudaStream_t s
 // exact modularity numerator of labels (values in [0, n)); host-synchronous.
 long long modularity_num(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                          const int32_t *labels, long long m_w, cudaStream_t s);
+// The same on a directed graph given as U = W + W^T with packed strengths:
+// sum_C (m_w U_in(C) - 2 Sigma_C^out Sigma_C^in) / 2.
+long long modularity_num_directed(int32_t n, const int32_t *rp, const int32_t *col,
+                                  const int32_t *w, const unsigned long long *s2,
+                                  const int32_t *labels, long long m_w, cudaStream_t s);
 double modularity_from_num(long long num, long long m_w);
 
 // ---------------------------------------------------------------------------
@@ -282,6 +327,7 @@ struct Buckets {
     // refreshed by every scan.
     DevBuf ent, nrec, cs;
     cudaTextureObject_t cs_tex = 0;  // cs through the texture path (0: plain loads)
+    int cs_elem = 0;                 // bytes of one cs element the texture object was made for
     const void *lay_src[4] = {nullptr, nullptr, nullptr, nullptr};  // rp, col, w, s of the copy
     bool lay_ready = false;
     // hubs: per hub its global table (offset, log2 capacity), and the chunks
@@ -314,47 +360,60 @@ struct Buckets {
     ~Buckets();
 };
 
+// Every function below that takes strengths s and totals sigma exists for
+// both null models (NM = NMSym or NMDir, whose stored type is NM::ST); for a
+// directed graph rp/col/w are U = W + W^T.
+//
 // The scan's copy of the level graph (Buckets::ent, nrec), built when the
 // buckets changed or the graph is another one; cs is sized for n nodes.
+template <class NM>
 void build_scan_layout(Buckets &bk, int32_t n, const int32_t *rp, const int32_t *col,
-                       const int32_t *w, const int32_t *s, cudaStream_t st);
+                       const int32_t *w, const typename NM::ST *s, cudaStream_t st);
 // cs[v] = (root_v, sigma[root_v]) for v < n.
-void pack_community_totals(int32_t n, const int32_t *root, const int32_t *sigma, int2 *cs,
-                           cudaStream_t st);
+template <class NM>
+void pack_community_totals(int32_t n, const int32_t *root, const typename NM::ST *sigma,
+                           Buckets &bk, cudaStream_t st);
 // The MAXIMAL scan of the nodes of fine class f (kFine4 .. kFine4096) on the
 // layout and community totals above (k_scan_fine.cu).
-void scan_fine_class(int f, const Buckets &bk, MParam mp, int32_t *best, long long *gain,
-                     int32_t *kown, unsigned long long *ncand, const ScanTuning &tu,
-                     cudaStream_t so);
+template <class NM>
+void scan_fine_class(int f, const Buckets &bk, const typename NM::ST *s, MParam mp, int32_t *best,
+                     long long *gain, int32_t *kown, unsigned long long *ncand,
+                     const ScanTuning &tu, cudaStream_t so);
 
-// ASSIGN: a[i] = best neighbour by m_w W_ij - s_i s_j.
+// ASSIGN: a[i] = best neighbour by m_w W_ij - s_i s_j (the null model's product).
+template <class NM>
 void assign_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                  const int32_t *s, MParam m_w, const Buckets &bk, int32_t *a,
+                  const typename NM::ST *s, MParam m_w, const Buckets &bk, int32_t *a,
                   cudaStream_t st);
 
 // The MAXIMAL scan: best community, gain (int64) and own-community weight
 // kown (int32); counts candidates into *ncand_dev (unsigned long long).
+template <class NM>
 void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                const int32_t *s, MParam m_w, const int32_t *root, const int32_t *sigma,
-                const Buckets &bk, int32_t *best, long long *gain, int32_t *kown,
-                unsigned long long *ncand_dev, cudaStream_t st);
+                const typename NM::ST *s, MParam m_w, const int32_t *root,
+                const typename NM::ST *sigma, const Buckets &bk, int32_t *best, long long *gain,
+                int32_t *kown, unsigned long long *ncand_dev, cudaStream_t st);
 
 // Own-community weight only (kown) for POSITIVE's local gains; flags the
 // communities holding a node with g < 0 (flag[root] = 1) and counts them.
+template <class NM>
 void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                      const int32_t *s, MParam m_w, const int32_t *root,
-                      const int32_t *sigma, const Buckets &bk, int32_t *kown,
+                      const typename NM::ST *s, MParam m_w, const int32_t *root,
+                      const typename NM::ST *sigma, const Buckets &bk, int32_t *kown,
                       int32_t *flag, cudaStream_t st);
 
 // Local gain g(i) = m_w kown_i - s_i (Sigma_{root_i} - s_i) of Algorithm POSITIVE.
-void local_gain_nodes(int32_t n, const int32_t *s, MParam m, const int32_t *root,
-                      const int32_t *sigma, const int32_t *kown, long long *g, cudaStream_t st);
+template <class NM>
+void local_gain_nodes(int32_t n, const typename NM::ST *s, MParam m, const int32_t *root,
+                      const typename NM::ST *sigma, const int32_t *kown, long long *g,
+                      cudaStream_t st);
 
 // Target node for the accepted nodes listed in list[0..cnt).
+template <class NM>
 void target_nodes(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt,
-                  const int32_t *rp, const int32_t *col, const int32_t *w, const int32_t *s,
-                  MParam m_w, const int32_t *root, const int32_t *best, int32_t *tgt,
-                  cudaStream_t st);
+                  const int32_t *rp, const int32_t *col, const int32_t *w,
+                  const typename NM::ST *s, MParam m_w, const int32_t *root, const int32_t *best,
+                  int32_t *tgt, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Assignment-forest kernels (k_forest.cu)
@@ -383,9 +442,10 @@ struct BranchScratch {
 };
 // Branch gains bg for candidates (gain > 0); counts positive ones and the
 // accepted ones, and lists the accepted nodes.
+template <class NM>
 void branch_gains(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                  const int32_t *s, MParam m_w, const int32_t *a, const Forest &f,
-                  const int32_t *sigma, const int32_t *best, const long long *gain,
+                  const typename NM::ST *s, MParam m_w, const int32_t *a, const Forest &f,
+                  const typename NM::ST *sigma, const int32_t *best, const long long *gain,
                   const int32_t *kown, BranchScratch &bs, long long *bg, cudaStream_t st);
 // Acceptance draw and list of accepted nodes.
 // With a forest (rng.gid set), per_graph gets, for every graph, the counts
@@ -422,8 +482,10 @@ struct PositiveScratch {
 // prev_root (may be null): the names after the last POSITIVE on this state;
 // when given, only communities whose membership changed since are examined
 // (the others cannot hold a negative local gain).
+template <class NM>
 long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                           const int32_t *s, MParam m, int32_t *a, Forest &f, int32_t *sigma,
+                           const typename NM::ST *s, MParam m, int32_t *a, Forest &f,
+                           typename NM::ST *sigma,
                            const Buckets &bk, PositiveScratch &ps, cudaStream_t st,
                            long long *rounds_out, long long *visits_out,
                            int32_t *splits_per_graph = nullptr,
