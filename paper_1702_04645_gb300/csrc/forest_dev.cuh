@@ -48,16 +48,31 @@ struct GridBarrier {
 // longest a block waits at a grid barrier before the launch is abandoned
 constexpr long long kBarrierLimitNs = 4000000000LL;
 
+// The arrival is one acq_rel atomic at GPU scope and the wait reads the word
+// with acquire loads: the block barrier before the arrival orders every
+// thread's writes before thread 0's release, and the block barrier after the
+// wait orders thread 0's acquire before every thread's reads, so the writes
+// of every block before the barrier are visible to every block after it
+// (release and acquire are cumulative), without a full fence on either side.
+__device__ __forceinline__ unsigned gbar_arrive(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned gbar_load(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __noinline__ bool gbar(GridBarrier *b, long long limit_ns) {
     __syncthreads();
     if (gridDim.x > 1) {
         if (threadIdx.x == 0) {
             const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
-            __threadfence();
-            const unsigned old = atomicAdd(&b->word, add);
-            volatile unsigned *vw = &b->word;
+            const unsigned old = gbar_arrive(&b->word, add);
             long long t0 = 0;
-            for (unsigned spin = 0; ((old ^ *vw) & 0x80000000u) == 0; spin++) {
+            for (unsigned spin = 0; ((old ^ gbar_load(&b->word)) & 0x80000000u) == 0; spin++) {
                 if ((spin & 255u) == 0) {  // read the clock now and then
                     const long long t = global_ns();
                     if (t0 == 0) t0 = t;
@@ -67,7 +82,6 @@ __device__ __noinline__ bool gbar(GridBarrier *b, long long limit_ns) {
                     }
                 }
             }
-            __threadfence();
         }
         __syncthreads();
     }

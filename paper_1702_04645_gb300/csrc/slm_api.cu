@@ -152,7 +152,7 @@ struct SweepCounts {
 template <class NM>
 SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
                          const typename NM::ST *s, long long m, Work &W, unsigned long long seed,
-                         unsigned long long P, int level, int sweep, bool stop_if_no_cand,
+                         unsigned long long P, int level, int sweep,
                          cudaStream_t st, slm::HostCounters &hc, PhaseTimer *tm = nullptr) {
     SweepCounts c;
     unsigned long long *ctr = W.ctr();
@@ -166,13 +166,9 @@ SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const
                     W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), ctr, st);
     if (tm) tm->stop(kPhScan);
     if (tm) tm->start();
-    SLM_CUDA(cudaMemcpyAsync(hc.h, ctr, 8, cudaMemcpyDeviceToHost, st));
-    slm::stream_sync(st);
-    c.cand = (long long)hc.h[0];
-    if (c.cand == 0 && stop_if_no_cand) {
-        if (tm) tm->stop(kPhMove);
-        return c;
-    }
+    // branch gains and the draw are queued before the candidate count is
+    // read: with no candidate they find nothing to accept, and the host waits
+    // once per sweep instead of twice
     slm::branch_gains<NM>(n, rp, col, w, s, m, W.a.as<int32_t>(), W.f, W.sigma.as<ST>(),
                       W.best.as<int32_t>(), W.gain.as<long long>(), W.kown.as<int32_t>(), W.bs,
                       W.bg.as<long long>(), st);
@@ -181,9 +177,10 @@ SweepCounts maximal_once(int32_t n, const int32_t *rp, const int32_t *col, const
                       acc_cnt, ctr + 1, st);
     SLM_CUDA(cudaMemcpyAsync(hc.h, ctr, 24, cudaMemcpyDeviceToHost, st));
     slm::stream_sync(st);
+    c.cand = (long long)hc.h[0];
     c.pos = (long long)hc.h[1];
     c.acc = (long long)(int32_t)(hc.h[2] & 0xffffffff);
-    if (c.pos == 0 || c.acc == 0) {
+    if (c.cand == 0 || c.pos == 0 || c.acc == 0) {
         if (tm) tm->stop(kPhMove);
         return c;
     }
@@ -254,7 +251,7 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
         for (; sweep < opt.max_sweeps; sweep++) {
             slm::check_run_control();
             SweepCounts c = maximal_once<NM>(n, rp, col, w, s, m, W, opt.seed, opt.accept_p32, t, sweep,
-                                         true, st, hc, tm);
+                                         st, hc, tm);
             stt.candidates += c.cand;
             stt.edges_scanned += nnz;
             if (c.cand == 0) {
@@ -872,7 +869,7 @@ slm_status slm_step_maximal(int32_t n, const int32_t *row_ptr, const int32_t *co
         load_state(W, n, row_ptr, a, st);
         slm::HostCounters hc;
         SweepCounts c = maximal_once<slm::NMSym>(n, row_ptr, col, w, s, m_w, W, seed, accept_p32, level, sweep,
-                                     false, st, hc);
+                                     st, hc);
         if (n > 0) SLM_CUDA(cudaMemcpyAsync(a, W.a.get(), 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
         slm::stream_sync(st);
         counts_host[0] = c.cand;

@@ -10,9 +10,10 @@ LFR-style recipe.
     per-sweep trace, the final labels and Q) with the oracle's runs stored
     under tests/golden/ by tests/golden/make_run_goldens.py (which calls
     only the oracle): the complete run on the R-MAT graph, and bounded runs
-    (3 sweeps per level, and on the 4M graph 3 levels) on the LFR-style
-    graphs, where the method does not settle: after a few sweeps long
-    assignment cycles form, whose cycle cuts cost the oracle hours;
+    (3 sweeps per level at 262,144 nodes; 2 sweeps per level and 3 levels
+    at 4,194,304) on the LFR-style graphs, where the method does not settle:
+    after a few sweeps long assignment cycles form, whose cycle cuts cost
+    the oracle hours;
   * properties that hold at any size: every level's labels are 0..K-1, the
     last level stopped for a stated reason, and the final modularity equals
     the oracle's modularity of the GPU's own final partition.
@@ -146,8 +147,10 @@ def test_rmat_s20_whole_run_timed_flags_equal():
 
 
 def test_lfr_4m_bounded_run_equals_oracle():
-    """The 4,194,304-node LFR-style graph with at most 3 sweeps per level and
-    3 levels equals the oracle's bounded run level by level."""
+    """The 4,194,304-node LFR-style graph with at most 2 sweeps per level and
+    3 levels equals the oracle's bounded run level by level (beyond the
+    second sweep long assignment cycles form and the oracle's cycle cuts
+    take hours at this size)."""
     G = compare_with_golden(_lfr(), _golden("lfr_4m_bounded"))
     G.close()
 
