@@ -86,6 +86,8 @@ def _load():
                 "ord_positive": (i32, [i32, i32p, i32p, i32p, i64p, i64p, i64, i32p, i32p]),
                 "ord_slm": (vp, [i32, i32p, i32p, i32p, u64, u64, i32, i32, C.c_uint32]),
                 "orc_louvain": (vp, [i32, i32p, i32p, i32p, i32, i32]),
+                "orc_colour": (i32, [i32, i32p, i32p, u64, i32, i32p]),
+                "orc_louvain_colour": (vp, [i32, i32p, i32p, i32p, u64, i32, i32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -245,6 +247,24 @@ def louvain(g, max_passes: int = 1000, max_levels: int = 64) -> Run:
     n, rp, col, w = _csr(g)
     lib = _load()
     return _collect(lib, lib.orc_louvain(n, rp, col, w, max_passes, max_levels), n)
+
+
+def colouring(g, seed: int = 1, level: int = 0):
+    """First-fit colouring of g's nodes in the key order of level `level`
+    (colour-synchronous Louvain); returns (colours, number of colours)."""
+    n, rp, col, w = _csr(g)
+    c = np.zeros(max(n, 1), np.int32)
+    k = _load().orc_colour(n, rp, col, seed, level, c)
+    return c[:n], int(k)
+
+
+def louvain_colour(g, seed: int = 1, max_passes: int = 1000, max_levels: int = 64) -> Run:
+    """Colour-synchronous Louvain on a symmetric graph: per pass the colour
+    classes in turn, every node of a class moving at once (stats per level:
+    passes, status, moves, 0, 0, entries scanned; status 2 = pass limit)."""
+    n, rp, col, w = _csr(g)
+    lib = _load()
+    return _collect(lib, lib.orc_louvain_colour(n, rp, col, w, seed, max_passes, max_levels), n)
 
 
 def _collect(lib, h, n) -> Run:

@@ -1346,3 +1346,187 @@ orc_run *orc_louvain(i32 n0, const i32 *rp0, const i32 *col0, const i32 *w0, i32
     free(rp); free(col); free(w);
     return r;
 }
+
+/* ========================================================================= */
+/* Colour-synchronous Louvain: the parallel form of classical Louvain that   */
+/* the conclusion (Section 6) leaves for later work, in the usual form of    */
+/* parallel Louvain codes: the nodes of one colour class of a distance-1     */
+/* colouring share no edge, so their moves are decided together.             */
+/*                                                                           */
+/* Colouring (readings; the paper gives none): at level t node v has the     */
+/* key mix64(seed ^ mix64((t << 32) | v)); u precedes v when key(u) > key(v),*/
+/* or the keys are equal and u < v.  Nodes are coloured one at a time in that */
+/* order, each with the smallest colour held by none of its neighbours       */
+/* already coloured (first fit; self-loops do not count).                   */
+/*                                                                           */
+/* Per level, passes repeat until one moves no node (or max_passes); a pass  */
+/* visits the colours 0, 1, ... in turn; every node of the colour decides    */
+/* its move exactly as orc_louvain does, but all of them against the         */
+/* communities and totals as they stand when the colour's turn begins, and   */
+/* then all of them move at once.  Levels end, compact, aggregate and stop   */
+/* as in orc_louvain; the trace holds (level, pass, 0, 0, moves, 0).         */
+/* ========================================================================= */
+static u64 colour_key(u64 seed, i32 t, i32 v) {
+    return orc_mix64(seed ^ orc_mix64(((u64)(uint32_t)t << 32) | (u64)(uint32_t)v));
+}
+
+/* Colours of the n nodes at level t (first fit in key order); returns the
+ * number of colours. */
+i32 orc_colour(i32 n, const i32 *rp, const i32 *col, u64 seed, i32 t, i32 *colour) {
+    if (n <= 0) return 0;
+    u64 *key = (u64 *)malloc((size_t)n * sizeof(u64));
+    i32 *ord = (i32 *)malloc((size_t)n * sizeof(i32));
+    i32 *used = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    for (i32 v = 0; v < n; v++) {
+        key[v] = colour_key(seed, t, v);
+        ord[v] = v;
+        colour[v] = -1;
+        used[v] = -1;
+    }
+    used[n] = -1;
+    /* the key order: bottom-up merge sort on (key descending, id ascending) */
+    i32 *tmp = (i32 *)malloc((size_t)n * sizeof(i32));
+    for (i32 width = 1; width < n; width *= 2) {
+        for (i32 lo = 0; lo < n; lo += 2 * width) {
+            i32 mid = lo + width < n ? lo + width : n;
+            i32 hi = lo + 2 * width < n ? lo + 2 * width : n;
+            i32 a = lo, b = mid, o = lo;
+            while (a < mid && b < hi) {
+                i32 x = ord[a], y = ord[b];
+                int x_first = key[x] > key[y] || (key[x] == key[y] && x < y);
+                tmp[o++] = x_first ? ord[a++] : ord[b++];
+            }
+            while (a < mid) tmp[o++] = ord[a++];
+            while (b < hi) tmp[o++] = ord[b++];
+        }
+        memcpy(ord, tmp, (size_t)n * sizeof(i32));
+    }
+    i32 ncol = 0;
+    for (i32 k = 0; k < n; k++) {
+        i32 v = ord[k];
+        /* mark the colours of v's coloured neighbours with v's name */
+        for (i32 p = rp[v]; p < rp[v + 1]; p++) {
+            i32 u = col[p];
+            if (u != v && colour[u] >= 0) used[colour[u]] = v;
+        }
+        i32 c = 0;
+        while (used[c] == v) c++;
+        colour[v] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(key); free(ord); free(used); free(tmp);
+    return ncol;
+}
+
+orc_run *orc_louvain_colour(i32 n0, const i32 *rp0, const i32 *col0, const i32 *w0, u64 seed,
+                            i32 max_passes, i32 max_levels) {
+    orc_run *r = (orc_run *)calloc(1, sizeof(orc_run));
+    r->n0 = n0;
+    r->final_labels = (i32 *)malloc(((size_t)n0 + 1) * sizeof(i32));
+    for (i32 v = 0; v < n0; v++) r->final_labels[v] = v;
+    i32 n = n0;
+    i32 nnz = rp0[n0];
+    i32 *rp = (i32 *)malloc(((size_t)n + 1) * sizeof(i32));
+    i32 *col = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+    i32 *w = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+    memcpy(rp, rp0, ((size_t)n + 1) * sizeof(i32));
+    memcpy(col, col0, (size_t)nnz * sizeof(i32));
+    memcpy(w, w0, (size_t)nnz * sizeof(i32));
+    i32 t = 0;
+    for (;;) {
+        size_t N = (size_t)n + 1;
+        i64 *s = (i64 *)malloc(N * sizeof(i64));
+        i64 *sigma = (i64 *)calloc(N, sizeof(i64));
+        i64 *acc = (i64 *)calloc(N, sizeof(i64));
+        i32 *touched = (i32 *)malloc(N * sizeof(i32));
+        i32 *comm = (i32 *)malloc(N * sizeof(i32));
+        i32 *colour = (i32 *)malloc(N * sizeof(i32));
+        i32 *dest = (i32 *)malloc(N * sizeof(i32));
+        unsigned char *seen = (unsigned char *)calloc(N, 1);
+        i64 m = orc_strengths(n, rp, col, w, s);
+        for (i32 v = 0; v < n; v++) { comm[v] = v; sigma[v] = s[v]; }
+        i32 ncol = orc_colour(n, rp, col, seed, t, colour);
+        i32 passes = 0;
+        i64 lv_moves = 0, first_moves = 0;
+        int settled = 0; /* the last pass moved no node */
+        while (passes < max_passes) {
+            i64 moves = 0;
+            for (i32 k = 0; k < ncol; k++) {
+                /* every node of colour k decides on the same state ... */
+                for (i32 i = 0; i < n; i++) {
+                    dest[i] = -1;
+                    if (colour[i] != k) continue;
+                    i32 A = comm[i], nt = 0;
+                    for (i32 p = rp[i]; p < rp[i + 1]; p++) {
+                        i32 j = col[p];
+                        if (j == i) continue;
+                        i32 c = comm[j];
+                        if (!seen[c]) { seen[c] = 1; touched[nt++] = c; }
+                        acc[c] += w[p];
+                    }
+                    i64 stay = m * acc[A] - s[i] * (sigma[A] - s[i]);
+                    i32 bc = -1;
+                    i64 bd = 0;
+                    for (i32 q = 0; q < nt; q++) {
+                        i32 c = touched[q];
+                        if (c == A) continue;
+                        i64 d = (m * acc[c] - s[i] * sigma[c]) - stay;
+                        if (d > 0 && (bc < 0 || d > bd || (d == bd && c < bc))) { bc = c; bd = d; }
+                    }
+                    for (i32 q = 0; q < nt; q++) { acc[touched[q]] = 0; seen[touched[q]] = 0; }
+                    dest[i] = bc;
+                }
+                /* ... and then all of them move at once */
+                for (i32 i = 0; i < n; i++) {
+                    if (dest[i] < 0) continue;
+                    sigma[comm[i]] -= s[i];
+                    sigma[dest[i]] += s[i];
+                    comm[i] = dest[i];
+                    moves++;
+                }
+            }
+            passes++;
+            lv_moves += moves;
+            if (passes == 1) first_moves = moves;
+            trace_push(r, t, passes - 1, 0, 0, moves, 0);
+            if (moves == 0) { settled = 1; break; }
+        }
+        i32 *id = (i32 *)malloc(N * sizeof(i32));
+        i32 *rank = (i32 *)malloc(N * sizeof(i32));
+        for (i32 v = 0; v < n; v++) rank[v] = -1;
+        for (i32 v = 0; v < n; v++) rank[comm[v]] = 0;
+        i32 K = 0;
+        for (i32 v = 0; v < n; v++) if (rank[v] == 0) rank[v] = ++K;
+        for (i32 v = 0; v < n; v++) id[v] = rank[comm[v]] - 1;
+        free(rank); free(s); free(sigma); free(acc); free(touched); free(comm); free(seen);
+        free(colour); free(dest);
+        if (first_moves == 0 || K == n) {
+            r->top_status = settled ? 0 : 2;
+            r->top_sweeps = passes;
+            free(id);
+            break;
+        }
+        run_grow(r);
+        r->level_n[r->levels] = n;
+        r->level_K[r->levels] = K;
+        r->level_labels[r->levels] = id;
+        r->sweeps[r->levels] = passes;
+        r->status[r->levels] = settled ? 0 : 2;
+        r->moves[r->levels] = lv_moves;
+        r->splits[r->levels] = 0;
+        r->cands[r->levels] = 0;
+        r->edges_scanned[r->levels] = (i64)passes * nnz;
+        r->levels++;
+        for (i32 v = 0; v < n0; v++) r->final_labels[v] = id[r->final_labels[v]];
+        i32 *rp2 = (i32 *)malloc(((size_t)K + 1) * sizeof(i32));
+        i32 *col2 = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+        i32 *w2 = (i32 *)malloc(((size_t)nnz + 1) * sizeof(i32));
+        i32 nnz2 = orc_aggregate(n, rp, col, w, id, K, rp2, col2, w2);
+        free(rp); free(col); free(w);
+        rp = rp2; col = col2; w = w2; n = K; nnz = nnz2;
+        t++;
+        if (t >= max_levels) { r->level_limit_hit = 1; break; }
+    }
+    free(rp); free(col); free(w);
+    return r;
+}

@@ -1,0 +1,252 @@
+"""Pins of the oracle's colour-synchronous Louvain (oracle.louvain_colour),
+the parallel form of classical Louvain that the conclusion (Section 6) leaves
+for later work: the nodes of one colour class of a distance-1 colouring share
+no edge and move together.
+
+* The colouring is checked against its definition by brute force: it is
+  proper, and every node holds the smallest colour not used by the
+  neighbours that precede it in the key order (first fit).
+* Whole runs are compared level by level with a definition-level
+  restatement that scores every candidate move by recomputing the modularity
+  numerator on the state at the start of the colour's turn.
+* Where every node has a colour of its own (complete graphs) the method is
+  sequential Louvain visiting the nodes in colour order.
+* Settled levels are local optima; closed-form graphs, the exhaustive optimum
+  and degenerate inputs.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+from brute import brute_max_q_num, dense, q_num_def
+
+M64 = (1 << 64) - 1
+
+
+def from_dense(W):
+    iu, ju = np.nonzero(np.triu(W))
+    return gg.from_edges(W.shape[0], iu, ju, W[iu, ju])
+
+
+def complete(n):
+    return from_dense(np.ones((n, n), np.int64) - np.eye(n, dtype=np.int64))
+
+
+def key_order(n, seed, level):
+    keys = [O.mix64(seed ^ O.mix64(((level << 32) | v) & M64)) for v in range(n)]
+    return sorted(range(n), key=lambda v: (-keys[v], v))
+
+
+def check_first_fit(W, colours, seed, level):
+    n = W.shape[0]
+    order = key_order(n, seed, level)
+    pos = {v: k for k, v in enumerate(order)}
+    for v in range(n):
+        nb = [u for u in np.flatnonzero(W[v]) if u != v]
+        assert all(colours[u] != colours[v] for u in nb), "not proper"
+        before = {int(colours[u]) for u in nb if pos[u] < pos[v]}
+        c = 0
+        while c in before:
+            c += 1
+        assert colours[v] == c, "not first fit"
+
+
+def colour_louvain_by_definition(W, seed, max_passes=1000):
+    """Levels (ids, K) and final labels, every decision taken on the
+    definition's numerator."""
+    n0 = W.shape[0]
+    final = np.arange(n0)
+    levels = []
+    Wl = W.copy()
+    t = 0
+    while True:
+        n = Wl.shape[0]
+        order = key_order(n, seed, t)
+        colours = np.full(n, -1)
+        for v in order:  # first fit in key order
+            used = {int(colours[u]) for u in np.flatnonzero(Wl[v]) if u != v and colours[u] >= 0}
+            c = 0
+            while c in used:
+                c += 1
+            colours[v] = c
+        comm = np.arange(n)
+        passes, first = 0, 0
+        while passes < max_passes:
+            moves = 0
+            for k in range(int(colours.max()) + 1 if n else 0):
+                q0 = q_num_def(Wl, comm)
+                dest = {}
+                for i in np.flatnonzero(colours == k):
+                    best = None
+                    for C in sorted({int(comm[j]) for j in np.flatnonzero(Wl[i]) if j != i}
+                                    - {int(comm[i])}):
+                        lab = comm.copy()
+                        lab[i] = C
+                        d = q_num_def(Wl, lab) - q0
+                        if d > 0 and (best is None or d > best[0]):
+                            best = (d, C)
+                    if best is not None:
+                        dest[int(i)] = best[1]
+                for i, C in dest.items():
+                    comm[i] = C
+                moves += len(dest)
+            passes += 1
+            if passes == 1:
+                first = moves
+            if moves == 0:
+                break
+        names = np.unique(comm)
+        K = names.shape[0]
+        ids = np.searchsorted(names, comm)
+        if first == 0 or K == n:
+            return levels, final
+        levels.append((ids, K))
+        final = ids[final]
+        P = np.zeros((n, K), np.int64)
+        P[np.arange(n), ids] = 1
+        Wl = P.T @ Wl @ P
+        t += 1
+
+
+def graphs():
+    out = [gg.random_small(5 + s % 8, 0.45, 900 + s, wmax=5, loops=0.3 if s % 2 else 0.0)
+           for s in range(14)]
+    out += [gg.random_small(9 + s % 4, 0.4, 950 + s, wmax=1) for s in range(8)]  # ties
+    return out + [gg.two_cliques(4), gg.path(9), gg.star(6), gg.ring_of_cliques(4, 3),
+                  gg.isolated_and_loops(7)]
+
+
+@pytest.mark.parametrize("seed", [1, 7])
+def test_colouring_is_first_fit_in_key_order(seed):
+    for g in graphs() + [gg.random_small(60, 0.1, 3, loops=0.2), complete(7)]:
+        for level in (0, 2):
+            c, k = O.colouring(g, seed=seed, level=level)
+            check_first_fit(dense(g), c, seed, level)
+            assert k == (int(c.max()) + 1 if g.n else 0)
+
+
+def test_colouring_special_cases():
+    c, k = O.colouring(complete(9))
+    assert k == 9 and sorted(c.tolist()) == list(range(9))   # every node its own colour
+    c, k = O.colouring(gg.from_edges(6, [], []))
+    assert k == 1 and (c == 0).all()                          # no edge: one class
+    c, k = O.colouring(gg.isolated_and_loops(5))
+    assert k == 1 and (c == 0).all()                          # self-loops do not count
+    c, _ = O.colouring(gg.star(8))
+    assert len(set(c[1:].tolist())) == 1 and c[0] != c[1]     # leaves share a colour
+
+
+@pytest.mark.parametrize("seed", [1, 5])
+def test_colour_louvain_matches_definition(seed):
+    total = 0
+    for g in graphs():
+        levels, final = colour_louvain_by_definition(dense(g), seed)
+        r = O.louvain_colour(g, seed=seed)
+        assert r.num_levels == len(levels)
+        for (a, ka), (b, kb) in zip(r.levels, levels):
+            assert ka == kb and (a == b).all()
+        assert (r.final == final).all()
+        total += len(levels)
+    assert total > 15
+
+
+def sequential_in_order(W, order):
+    """One level of sequential Louvain visiting nodes in `order` (definition
+    level); returns the final community names."""
+    n = W.shape[0]
+    comm = np.arange(n)
+    while True:
+        moves = 0
+        for i in order:
+            q0 = q_num_def(W, comm)
+            best = None
+            for C in sorted({int(comm[j]) for j in np.flatnonzero(W[i]) if j != i}
+                            - {int(comm[i])}):
+                lab = comm.copy()
+                lab[i] = C
+                d = q_num_def(W, lab) - q0
+                if d > 0 and (best is None or d > best[0]):
+                    best = (d, C)
+            if best is not None:
+                comm[i] = best[1]
+                moves += 1
+        if moves == 0:
+            return comm
+
+
+def test_distinct_colours_reduce_to_sequential_louvain():
+    """On a complete graph every class holds one node: the first level is
+    sequential Louvain in colour order."""
+    for s in range(6):
+        n = 6 + s
+        rng = np.random.default_rng(40 + s)
+        W = np.zeros((n, n), np.int64)
+        for i in range(n):
+            for j in range(i + 1, n):
+                W[i, j] = W[j, i] = rng.integers(1, 9)
+        g = from_dense(W)
+        c, k = O.colouring(g, seed=3)
+        assert k == n
+        comm = sequential_in_order(W, list(np.argsort(c)))
+        names = np.unique(comm)
+        r = O.louvain_colour(g, seed=3, max_levels=1)
+        if r.num_levels:
+            assert (r.levels[0][0] == np.searchsorted(names, comm)).all()
+        else:
+            assert names.shape[0] == n
+
+
+def _level_graphs(g, r):
+    out = [g]
+    for ids, K in r.levels[:-1]:
+        out.append(O.aggregate(out[-1], ids, K))
+    return out
+
+
+def test_settled_levels_are_local_optima():
+    """A level that ends on a pass without moves admits no improving single
+    move."""
+    for g in [gg.random_small(60, 0.08, 31, loops=0.1), gg.sbm_planted(n_blocks=3, block_size=20,
+              p_in=0.4, p_out=0.05, seed=2), gg.random_small(40, 0.15, 33, wmax=1)]:
+        r = O.louvain_colour(g)
+        assert r.num_levels >= 1
+        for h, (ids, K), st in zip(_level_graphs(g, r), r.levels, r.stats):
+            assert st[1] == 0
+            W = dense(h)
+            q0 = q_num_def(W, ids)
+            for i in range(h.n):
+                for C in {int(ids[j]) for j in np.flatnonzero(W[i]) if j != i} - {int(ids[i])}:
+                    lab = ids.copy()
+                    lab[i] = C
+                    assert q_num_def(W, lab) - q0 <= 0
+
+
+def test_bounded_by_the_exhaustive_optimum():
+    for g in [x for x in graphs() if x.n <= 10]:
+        W = dense(g)
+        best, _ = brute_max_q_num(W)
+        num = q_num_def(W, O.louvain_colour(g).final)
+        assert q_num_def(W, np.arange(g.n)) <= num <= best
+
+
+def test_closed_forms_stats_and_limits():
+    lab = O.louvain_colour(gg.two_cliques(5)).final
+    assert len(set(lab[:5])) == 1 and len(set(lab[5:])) == 1 and lab[0] != lab[5]
+    g = gg.ring_of_cliques(30, 5)
+    r = O.louvain_colour(g)
+    assert all(len(set(r.final[5 * c:5 * c + 5].tolist())) == 1 for c in range(30))
+    for lv, st in enumerate(r.stats):
+        rows = r.trace[r.trace[:, 0] == lv]
+        assert st[0] == rows.shape[0] and st[2] == int(rows[:, 4].sum())
+    assert r.stats[0][5] == r.stats[0][0] * g.nnz
+    assert (O.louvain_colour(g).final == r.final).all()
+    one = O.louvain_colour(g, max_passes=1)
+    assert one.stats[0][0] == 1 and one.stats[0][1] == 2   # stopped by the pass limit
+
+
+@pytest.mark.parametrize("n", [0, 1, 5])
+def test_degenerate_graphs(n):
+    r = O.louvain_colour(gg.from_edges(n, [], []))
+    assert r.num_levels == 0 and (r.final == np.arange(n)).all()
+    assert O.louvain_colour(gg.isolated_and_loops(max(n, 1))).num_levels == 0
