@@ -260,8 +260,10 @@ def colouring(g, seed: int = 1, level: int = 0):
 
 def louvain_colour(g, seed: int = 1, max_passes: int = 1000, max_levels: int = 64) -> Run:
     """Colour-synchronous Louvain on a symmetric graph: per pass the colour
-    classes in turn, every node of a class moving at once (stats per level:
-    passes, status, moves, 0, 0, entries scanned; status 2 = pass limit)."""
+    classes in turn, every node of a class moving at once; a level ends at a
+    pass without moves (status 0), with a numerator gain of at most
+    floor(m_w^2 / 2^20) (status 1) or at the pass limit (status 2).  Stats
+    per level: passes, status, moves, 0, 0, entries scanned."""
     n, rp, col, w = _csr(g)
     lib = _load()
     return _collect(lib, lib.orc_louvain_colour(n, rp, col, w, seed, max_passes, max_levels), n)

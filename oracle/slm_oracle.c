@@ -1359,12 +1359,17 @@ orc_run *orc_louvain(i32 n0, const i32 *rp0, const i32 *col0, const i32 *w0, i32
 /* order, each with the smallest colour held by none of its neighbours       */
 /* already coloured (first fit; self-loops do not count).                   */
 /*                                                                           */
-/* Per level, passes repeat until one moves no node (or max_passes); a pass  */
-/* visits the colours 0, 1, ... in turn; every node of the colour decides    */
-/* its move exactly as orc_louvain does, but all of them against the         */
-/* communities and totals as they stand when the colour's turn begins, and   */
-/* then all of them move at once.  Levels end, compact, aggregate and stop   */
-/* as in orc_louvain; the trace holds (level, pass, 0, 0, moves, 0).         */
+/* A pass visits the colours 0, 1, ... in turn; every node of the colour    */
+/* decides its move exactly as orc_louvain does, but all of them against    */
+/* the communities and totals as they stand when the colour's turn begins,  */
+/* and then all of them move at once.  Moves taken together can undo one    */
+/* another's gains (two nodes joining one community each count its total    */
+/* without the other), so passes need not settle; as parallel Louvain codes */
+/* do, the level ends at a pass that moves no node (status 0), or that      */
+/* raises the exact numerator sum_C (m_w W_in(C) - Sigma_C^2) by at most    */
+/* floor(m_w^2 / 2^20), i.e. Q by at most 2^-20 (status 1), or after        */
+/* max_passes passes (status 2).  Levels then compact, aggregate and stop   */
+/* as in orc_louvain; the trace holds (level, pass, 0, 0, moves, 0).        */
 /* ========================================================================= */
 static u64 colour_key(u64 seed, i32 t, i32 v) {
     return orc_mix64(seed ^ orc_mix64(((u64)(uint32_t)t << 32) | (u64)(uint32_t)v));
@@ -1448,7 +1453,9 @@ orc_run *orc_louvain_colour(i32 n0, const i32 *rp0, const i32 *col0, const i32 *
         i32 ncol = orc_colour(n, rp, col, seed, t, colour);
         i32 passes = 0;
         i64 lv_moves = 0, first_moves = 0;
-        int settled = 0; /* the last pass moved no node */
+        int status = 2;
+        const i64 theta = (i64)(((unsigned __int128)m * (unsigned __int128)m) >> 20);
+        i64 num = orc_modularity_num(n, rp, col, w, comm); /* singletons */
         while (passes < max_passes) {
             i64 moves = 0;
             for (i32 k = 0; k < ncol; k++) {
@@ -1489,7 +1496,11 @@ orc_run *orc_louvain_colour(i32 n0, const i32 *rp0, const i32 *col0, const i32 *
             lv_moves += moves;
             if (passes == 1) first_moves = moves;
             trace_push(r, t, passes - 1, 0, 0, moves, 0);
-            if (moves == 0) { settled = 1; break; }
+            if (moves == 0) { status = 0; break; }
+            const i64 num2 = orc_modularity_num(n, rp, col, w, comm);
+            const i64 gain = num2 - num;
+            num = num2;
+            if (gain <= theta) { status = 1; break; }
         }
         i32 *id = (i32 *)malloc(N * sizeof(i32));
         i32 *rank = (i32 *)malloc(N * sizeof(i32));
@@ -1501,7 +1512,7 @@ orc_run *orc_louvain_colour(i32 n0, const i32 *rp0, const i32 *col0, const i32 *
         free(rank); free(s); free(sigma); free(acc); free(touched); free(comm); free(seen);
         free(colour); free(dest);
         if (first_moves == 0 || K == n) {
-            r->top_status = settled ? 0 : 2;
+            r->top_status = status;
             r->top_sweeps = passes;
             free(id);
             break;
@@ -1511,7 +1522,7 @@ orc_run *orc_louvain_colour(i32 n0, const i32 *rp0, const i32 *col0, const i32 *
         r->level_K[r->levels] = K;
         r->level_labels[r->levels] = id;
         r->sweeps[r->levels] = passes;
-        r->status[r->levels] = settled ? 0 : 2;
+        r->status[r->levels] = status;
         r->moves[r->levels] = lv_moves;
         r->splits[r->levels] = 0;
         r->cands[r->levels] = 0;
