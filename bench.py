@@ -589,6 +589,9 @@ def run_lfr_table1(args):
                 r = (O.directed_slm if args.directed else O.slm)(g, seed=args.seed, P=O.P_HALF)
                 case["oracle_ms"] = 1e3 * (time.perf_counter() - t1)
                 case["identical_to_oracle"] = bool(np.array_equal(r.final, lab))
+            if args.compare_louvain and not args.directed:
+                case["louvain"] = louvain_case(G, (rp, col, w, comm), n == sizes[0] and
+                                               not args.no_cpu_baseline, args.seed, stream, dev)
             G.close()
             out.append(case)
             tot_units += units
@@ -615,6 +618,36 @@ def run_lfr_table1(args):
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def louvain_case(G, graph, with_oracle, seed, stream, dev):
+    """The comparison method (colour-synchronous Louvain, slm_run_louvain) on
+    the same graph handle: one warm-up run, one run timed with CUDA events."""
+    import torch
+    import oracle as O
+    rp, col, w, comm = graph
+    G.run_louvain(seed=seed, stream=stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    G.run_louvain(seed=seed, stream=stream.cuda_stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    levels = G.num_levels()
+    per_level = [G.stats(l) for l in range(levels)] + [G.stats(-1)]
+    lab, K = G.partition(-1)
+    out = {"ms": ev0.elapsed_time(ev1), "levels": levels,
+           "passes": [st.sweeps for st in per_level], "communities": int(K),
+           "modularity": G.modularity(-1), "nmi_planted": nmi(lab, comm)}
+    if with_oracle:
+        t1 = time.perf_counter()
+        r = O.louvain_colour(gg.CSR(len(rp) - 1, rp, col, w), seed=seed)
+        out["oracle_ms"] = 1e3 * (time.perf_counter() - t1)
+        out["identical_to_oracle"] = bool(np.array_equal(r.final, lab))
+    note(f"   colour-synchronous Louvain: {out['ms']:.1f} ms, passes {out['passes']}, K={K}, "
+         f"Q {out['modularity']:.4f}, NMI {out['nmi_planted']:.3f}")
+    return out
 
 
 def peaks():
@@ -666,6 +699,8 @@ def main():
                     default="rmat")
     ap.add_argument("--lfr-sizes", default="10000,100000,1000000",
                     help="lfr_table1: node counts")
+    ap.add_argument("--compare-louvain", action="store_true",
+                    help="lfr_table1: also time colour-synchronous Louvain on every graph")
     ap.add_argument("--directed", action="store_true",
                     help="lfr_table1: directed weighted LFR-style graphs (the paper's setting)")
     ap.add_argument("--rmat-scale", type=int, default=20,

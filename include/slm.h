@@ -126,6 +126,36 @@ int32_t slm_graph_is_directed(const slm_graph *g);
  * (the host reads a few counters per sweep). */
 slm_status slm_run(slm_graph *g, const slm_options *opt, void *stream);
 
+/* Colour-synchronous Louvain, the comparison method: classical Louvain's
+ * node moves (Section 3, Blondel et al.; leave the own community for the
+ * neighbouring one of largest strictly positive gain, ties to the smallest
+ * community name) in the parallel form that Section 6 leaves for later work.
+ * Per level the nodes get a first-fit colouring in a seeded order (node v at
+ * level t has the key mix64(seed ^ mix64((t << 32) | v)), mix64 the
+ * splitmix64 output function; larger keys first, equal keys by smaller id;
+ * each node takes the smallest colour no earlier neighbour holds; self-loops
+ * do not count).  A pass visits the colours 0, 1, ... in turn: all nodes of
+ * the colour decide on the communities and totals as they stand, then move at
+ * once.  Moves taken together can undo one another's gains, so a level ends
+ * at a pass that moves no node (status 0), or that raises the exact numerator
+ * sum_C (m_w W_in(C) - Sigma_C^2) by at most floor(m_w^2 / 2^20), i.e. Q by
+ * at most 2^-20 (status 1), or after `max_passes` (1..65535) passes (status
+ * 2); then the communities are compacted in name order and aggregated as
+ * slm_run's are, and the run stops at the first level whose
+ * first pass moves nothing or that ends with every node alone, or after
+ * `max_levels` (0..65535; at least one level is always run) recorded levels.
+ * The results replace the handle's, as slm_run's do (kept on failure), and are
+ * read with the same calls; per level slm_level_stats gives sweeps = passes,
+ * status (0, 1 or 2 as above), moves, splits =
+ * candidates = 0 and edges_scanned = passes x nnz; slm_get_trace (slm_steps.h) gives one row
+ * (level, pass, 0, 0, moves, 0) per pass.  A symmetric graph only: a handle
+ * from slm_create_graph_directed gives INVALID_ARGUMENT, as do options out of
+ * range.  Other errors: OUT_OF_MEMORY, CANCELLED / DEADLINE (run control),
+ * CUDA.  Returns after the work on `stream` has finished (the host reads a
+ * count per colouring round and per pass). */
+slm_status slm_run_louvain(slm_graph *g, uint64_t seed, int32_t max_passes, int32_t max_levels,
+                           void *stream);
+
 /* Number of recorded (aggregated) levels of the last run. */
 slm_status slm_num_levels(const slm_graph *g, int32_t *levels);
 

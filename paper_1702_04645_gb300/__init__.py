@@ -45,7 +45,7 @@ STATUS = {0: "SLM_OK", 1: "SLM_ERR_INVALID_ARGUMENT", 2: "SLM_ERR_NOT_SYMMETRIC"
 
 # every exported entry point, as declared in include/*.h
 EXPORTS = ["slm_default_options", "slm_create_graph", "slm_create_graph_directed",
-           "slm_graph_is_directed", "slm_run", "slm_num_levels",
+           "slm_graph_is_directed", "slm_run", "slm_run_louvain", "slm_num_levels",
            "slm_get_partition", "slm_modularity", "slm_get_stats", "slm_modularity_of",
            "slm_destroy_graph", "slm_status_string", "slm_last_error", "slm_step_strengths",
            "slm_step_assign", "slm_step_components", "slm_step_scan", "slm_step_branch_gain",
@@ -162,6 +162,7 @@ def load():
             "slm_create_graph_directed": (C.c_int, [i32, vp, vp, vp, C.c_int, vp, C.POINTER(vp)]),
             "slm_graph_is_directed": (i32, [vp]),
             "slm_run": (C.c_int, [vp, C.POINTER(Options), vp]),
+            "slm_run_louvain": (C.c_int, [vp, C.c_uint64, C.c_int32, C.c_int32, vp]),
             "slm_num_levels": (C.c_int, [vp, C.POINTER(i32)]),
             "slm_get_partition": (C.c_int, [vp, i32, vp, C.c_int, C.POINTER(i32)]),
             "slm_modularity": (C.c_int, [vp, i32, C.POINTER(C.c_double)]),
@@ -321,6 +322,14 @@ class Graph:
         o = Options(seed, accept_p32, max_sweeps, max_levels, flags)
         st = C.c_void_p(int(stream)) if stream is not None else C.c_void_p(0)
         _check(load().slm_run(self._h, C.byref(o), st), self._h)
+        return self
+
+    def run_louvain(self, seed: int = 1, max_passes: int = 1000, max_levels: int = 64,
+                    stream=None):
+        """Colour-synchronous Louvain (slm_run_louvain); results are read with
+        the same calls as those of run()."""
+        st = C.c_void_p(int(stream)) if stream is not None else C.c_void_p(0)
+        _check(load().slm_run_louvain(self._h, seed, max_passes, max_levels, st), self._h)
         return self
 
     def num_levels(self) -> int:

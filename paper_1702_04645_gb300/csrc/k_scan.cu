@@ -621,7 +621,7 @@ Buckets::~Buckets() {
 void Buckets::build(int32_t n, const int32_t *rp, cudaStream_t s) { build_list(n, nullptr, rp, s); }
 
 void Buckets::build_list(int32_t n, const int32_t *list, const int32_t *rp, cudaStream_t s) {
-    if (!fork) {
+    if (!fork && !one_stream) {
         for (int k = 0; k < kSide; k++) {
             SLM_CUDA(cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking));
             SLM_CUDA(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
@@ -784,7 +784,7 @@ void scan_nodes(int32_t n, const int32_t *rp, const int32_t *col, const int32_t 
     const int32_t *ord = bk.order.as<int32_t>();
     auto cnt = [&](int b) { return bk.off[b + 1] - bk.off[b]; };
     const ScanTuning tu = scan_tuning();
-    const bool side = tu.streams > 1;
+    const bool side = tu.streams > 1 && bk.fork != nullptr;
     Buckets &bl = const_cast<Buckets &>(bk);
     build_scan_layout<NM>(bl, n, rp, col, w, s, st);
     pack_community_totals<NM>(n, root, sigma, bl, st);

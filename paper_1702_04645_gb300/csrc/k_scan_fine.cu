@@ -115,19 +115,19 @@ void build_scan_layout(Buckets &bk, int32_t n, const int32_t *rp, const int32_t 
     const void *src[4] = {rp, col, w, s};
     bool same = bk.lay_ready;
     for (int k = 0; k < 4; k++) same = same && bk.lay_src[k] == src[k];
-    const void *cs_before = bk.cs.get();
-    bk.cs.ensure(sizeof(CS) * (size_t)(n > 0 ? n : 1), st);
-    if (bk.cs.get() != cs_before || !bk.cs_tex || bk.cs_elem != (int)sizeof(CS)) {
+    const void *cs_before = bk.csbuf().get();
+    bk.csbuf().ensure(sizeof(CS) * (size_t)(n > 0 ? n : 1), st);
+    if (bk.csbuf().get() != cs_before || !bk.cs_tex || bk.cs_elem != (int)sizeof(CS)) {
         if (bk.cs_tex) cudaDestroyTextureObject(bk.cs_tex);
         bk.cs_tex = 0;
         int dev = 0, maxw = 0;
         SLM_CUDA(cudaGetDevice(&dev));
         SLM_CUDA(cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture1DLinearWidth, dev));
-        const size_t elems = bk.cs.bytes() / sizeof(CS);
+        const size_t elems = bk.csbuf().bytes() / sizeof(CS);
         if (elems <= (size_t)maxw) {
             cudaResourceDesc rd{};
             rd.resType = cudaResourceTypeLinear;
-            rd.res.linear.devPtr = bk.cs.get();
+            rd.res.linear.devPtr = bk.csbuf().get();
             rd.res.linear.desc = cudaCreateChannelDesc<CS>();
             rd.res.linear.sizeInBytes = elems * sizeof(CS);
             cudaTextureDesc td{};
@@ -164,7 +164,7 @@ void pack_community_totals(int32_t n, const int32_t *root, const typename NM::ST
                            Buckets &bk, cudaStream_t st) {
     if (n <= 0) return;
     k_pack_cs<<<grid_for(n, 256), 256, 0, st>>>(n, root, sigma,
-                                                 bk.cs.as<typename CsOf<NM>::T>());
+                                                 bk.csbuf().as<typename CsOf<NM>::T>());
     SLM_LAUNCH_CHECK();
 }
 
@@ -558,7 +558,7 @@ void scan_fine_class(int f, const Buckets &bk, const typename NM::ST *s, MParam 
     A.nrec = bk.nrec.as<int4>() + bk.foff[f];
     A.cnt = bk.foff[f + 1] - bk.foff[f];
     A.ent = bk.ent.as<int2>();
-    A.cs = bk.cs.as<typename CsOf<NM>::T>();
+    A.cs = bk.csbuf().as<typename CsOf<NM>::T>();
     A.cs_tex = bk.cs_tex;
     A.s = s;
     A.mp = mp;

@@ -343,6 +343,131 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
     g->has_run = true;
 }
 
+// Colour-synchronous Louvain (k_louvain.cu): per level a first-fit colouring,
+// then passes over the colour classes, each class one scan of its nodes on
+// the communities and totals as they stand, then its moves at once.  A level
+// ends at a pass without moves (status 0), at a pass that raises the exact
+// numerator by at most floor(m_w^2 / 2^20) (status 1: moves taken together
+// can undo one another's gains, so passes need not settle), or at the pass
+// limit (status 2); levels then compact in name order and aggregate as the
+// method's do.
+void louvain_impl(slm_graph *g, unsigned long long seed, int max_passes, int max_levels,
+                  cudaStream_t st) {
+    if (g->directed) slm::fail(SLM_ERR_INVALID_ARGUMENT, "colour-synchronous Louvain takes a symmetric graph");
+    if (max_passes < 1 || max_passes > 65535 || max_levels < 0 || max_levels > 65535)
+        slm::fail(SLM_ERR_INVALID_ARGUMENT, "options out of range");
+    g->levels.clear();
+    g->trace.clear();
+    g->has_run = false;
+    g->top = slm_level_stats{};
+    const int32_t n0 = g->n0;
+    g->final_comp.alloc(4 * (size_t)(n0 > 0 ? n0 : 1), st);
+    if (n0 > 0) {
+        k_iota<<<slm::grid_for(n0, 256), 256, 0, st>>>(n0, g->final_comp.as<int32_t>());
+        SLM_LAUNCH_CHECK();
+    }
+    int32_t n = n0, nnz = g->nnz0;
+    const int32_t *rp = g->rp.as<int32_t>(), *col = g->col.as<int32_t>(), *w = g->w.as<int32_t>();
+    const int32_t *s = g->s.as<int32_t>();
+    DevBuf lrp, lcol, lw, ls;  // owned aggregated graph
+    const long long m = g->m;
+    DevBuf ctr(64, st), cs_all;
+    unsigned long long *moves_dev = ctr.as<unsigned long long>();
+    for (int t = 0; n > 0; t++) {
+        slm::check_run_control();
+        const size_t N = (size_t)n;
+        DevBuf colour(4 * N, st), order(4 * N, st), comm(4 * N, st), sigma(4 * N, st),
+            best(4 * N, st), gain(8 * N, st), kown(4 * N, st);
+        const std::vector<int32_t> coff = slm::colour_nodes(n, rp, col, seed, t, colour.as<int32_t>(),
+                                                            order.as<int32_t>(), st);
+        const int ncol = (int)coff.size() - 1;
+        // one scan layout per colour class, all on one stream and one
+        // (community, total) array
+        std::vector<std::unique_ptr<slm::Buckets>> cls(ncol);
+        for (int k = 0; k < ncol; k++) {
+            cls[k].reset(new slm::Buckets());
+            cls[k]->one_stream = true;
+            cls[k]->cs_shared = &cs_all;
+            cls[k]->build_list(coff[k + 1] - coff[k], order.as<int32_t>() + coff[k], rp, st);
+        }
+        slm::louvain_init(n, s, comm.as<int32_t>(), sigma.as<int32_t>(), st);
+        slm_level_stats stt{};
+        stt.n = n;
+        stt.nnz = nnz;
+        int passes = 0;
+        long long first_moves = 0;
+        int status = 2;
+        const long long theta = (long long)(((unsigned long long)m * (unsigned long long)m) >> 20);
+        long long num = slm::modularity_num(n, rp, col, w, comm.as<int32_t>(), m, st);
+        while (passes < max_passes) {
+            slm::check_run_control();
+            SLM_CUDA(cudaMemsetAsync(ctr.get(), 0, 64, st));
+            for (int k = 0; k < ncol; k++) {
+                slm::scan_nodes<slm::NMSym>(n, rp, col, w, s, m, comm.as<int32_t>(), sigma.as<int32_t>(),
+                                            *cls[k], best.as<int32_t>(), gain.as<long long>(),
+                                            kown.as<int32_t>(), moves_dev + 1, st);
+                slm::louvain_move(order.as<int32_t>() + coff[k], coff[k + 1] - coff[k], best.as<int32_t>(),
+                                  comm.as<int32_t>(), s, sigma.as<int32_t>(), moves_dev, st);
+            }
+            unsigned long long mv = 0;
+            SLM_CUDA(cudaMemcpyAsync(&mv, moves_dev, sizeof mv, cudaMemcpyDeviceToHost, st));
+            slm::stream_sync(st);
+            g->trace.push_back({t, passes, 0, 0, (long long)mv, 0});
+            passes++;
+            stt.moves += (long long)mv;
+            stt.edges_scanned += nnz;
+            if (passes == 1) first_moves = (long long)mv;
+            if (mv == 0) {
+                status = 0;
+                break;
+            }
+            const long long num2 = slm::modularity_num(n, rp, col, w, comm.as<int32_t>(), m, st);
+            const long long gain = num2 - num;
+            num = num2;
+            if (gain <= theta) {
+                status = 1;
+                break;
+            }
+        }
+        stt.sweeps = passes;
+        stt.status = status;
+        DevBuf id(4 * N, st), scratch(4 * N, st);
+        const int32_t K = slm::compact_names(n, comm.as<int32_t>(), id.as<int32_t>(), scratch.as<int32_t>(), st);
+        stt.n_communities = K;
+        if (first_moves == 0 || K == n) {
+            g->top = stt;
+            break;
+        }
+        slm::compose_labels(n0, g->final_comp.as<int32_t>(), id.as<int32_t>(), st);
+        slm_graph::Level L;
+        L.n = n;
+        L.K = K;
+        L.st = stt;
+        L.comp.alloc(4 * (size_t)n0, st);
+        SLM_CUDA(cudaMemcpyAsync(L.comp.get(), g->final_comp.get(), 4 * (size_t)n0,
+                                 cudaMemcpyDeviceToDevice, st));
+        DevBuf nrp, ncol_, nw;
+        const int32_t nnz2 = slm::aggregate_graph(n, rp, col, w, id.as<int32_t>(), K, nrp, ncol_, nw, st);
+        DevBuf ns(4 * (size_t)(K > 0 ? K : 1), st);
+        slm::strengths(K, nrp.as<int32_t>(), nw.as<int32_t>(), ns.as<int32_t>(), st);
+        L.labels = std::move(id);
+        g->levels.push_back(std::move(L));
+        lrp = std::move(nrp);
+        lcol = std::move(ncol_);
+        lw = std::move(nw);
+        ls = std::move(ns);
+        rp = lrp.as<int32_t>();
+        col = lcol.as<int32_t>();
+        w = lw.as<int32_t>();
+        s = ls.as<int32_t>();
+        n = K;
+        nnz = nnz2;
+        if (t + 1 >= max_levels) break;
+    }
+    slm::stream_sync(st);
+    g->has_run = true;
+}
+
 void check_csr_host(int32_t n, const int32_t *rp_h, long long *nnz) {
     if (rp_h[0] != 0) slm::fail(SLM_ERR_INVALID_ARGUMENT, "row_ptr[0] must be 0");
     for (int32_t i = 0; i < n; i++)
@@ -548,6 +673,27 @@ slm_status slm_run(slm_graph *g, const slm_options *opt, void *stream) {
         if (g->directed) run_impl<slm::NMDir>(g, o, as_stream(stream));
         else run_impl<slm::NMSym>(g, o, as_stream(stream));
     });
+    if (st != SLM_OK) {
+        g->levels = std::move(levels);
+        g->trace = std::move(trace);
+        g->top = top;
+        g->final_comp = std::move(comp);
+        g->has_run = had_run;
+    }
+    return st;
+}
+
+slm_status slm_run_louvain(slm_graph *g, uint64_t seed, int32_t max_passes, int32_t max_levels,
+                           void *stream) {
+    if (!g) return SLM_ERR_INVALID_ARGUMENT;
+    std::vector<slm_graph::Level> levels = std::move(g->levels);
+    std::vector<std::array<long long, 6>> trace = std::move(g->trace);
+    const slm_level_stats top = g->top;
+    DevBuf comp = std::move(g->final_comp);
+    const bool had_run = g->has_run;
+    g->levels.clear();
+    g->trace.clear();
+    const slm_status st = guarded(g, [&] { louvain_impl(g, seed, max_passes, max_levels, as_stream(stream)); });
     if (st != SLM_OK) {
         g->levels = std::move(levels);
         g->trace = std::move(trace);

@@ -326,6 +326,13 @@ struct Buckets {
     // order, and per node of the graph (community, community total),
     // refreshed by every scan.
     DevBuf ent, nrec, cs;
+    // when set, the (community, total) array lives there instead of in cs, so
+    // that the layouts of several node lists of one graph share it
+    DevBuf *cs_shared = nullptr;
+    DevBuf &csbuf() { return cs_shared ? *cs_shared : cs; }
+    const DevBuf &csbuf() const { return cs_shared ? *cs_shared : cs; }
+    // no side streams: every kernel of a scan runs on the caller's stream
+    bool one_stream = false;
     cudaTextureObject_t cs_tex = 0;  // cs through the texture path (0: plain loads)
     int cs_elem = 0;                 // bytes of one cs element the texture object was made for
     const void *lay_src[4] = {nullptr, nullptr, nullptr, nullptr};  // rp, col, w, s of the copy
@@ -466,7 +473,7 @@ void apply_moves(const int32_t *list, const int32_t *cnt_dev, int32_t max_cnt,
 constexpr int kPosPhases = 11;
 struct PositiveScratch {
     DevBuf flag, kown, listA, listB, rlist, posr, L, coff, subS, subWA, subWin, credit, TS, msz,
-        bestsc, bestkey, pool, cyc, cnt, mark, tot, hdr, epref, kacc, cut, nf, noc, bs, ctrl;
+        bestsc, bestkey, pool, pool2, cyc, cnt, mark, tot, hdr, epref, kacc, cut, nf, noc, bs, ctrl;
     DevBuf rowlen, ioff, istart, ideg, icol, iw;  // internal entries of the members (room: whole rows)
     DevBuf recomp, moffN, cutsum, coffN, freshN, cutpar, oldroot;  // incremental rounds
     DevBuf dirty;  // communities whose membership changed since the last call
@@ -544,6 +551,27 @@ void modularity_forest(int32_t n, const int32_t *rp, const int32_t *col, const i
                        const int32_t *labels, int32_t nlab, const int32_t *gid,
                        const int32_t *loff, int32_t G, const long long *mg, long long *nums,
                        cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Colour-synchronous Louvain (k_louvain.cu)
+// ---------------------------------------------------------------------------
+// First-fit colouring of the n nodes in the key order of level `level`:
+// colour[v], and order = the nodes sorted by colour (stable, so ascending
+// within a class); returns the class offsets into order (ncolours + 1
+// entries; host-synchronous).
+std::vector<int32_t> colour_nodes(int32_t n, const int32_t *rp, const int32_t *col,
+                                  unsigned long long seed, int32_t level, int32_t *colour,
+                                  int32_t *order, cudaStream_t st);
+// comm[v] = v, sigma[v] = s[v]
+void louvain_init(int32_t n, const int32_t *s, int32_t *comm, int32_t *sigma, cudaStream_t st);
+// the moves of the cnt listed nodes (best[i] != comm[i]), with their totals;
+// *moves += their number
+void louvain_move(const int32_t *list, int32_t cnt, const int32_t *best, int32_t *comm,
+                  const int32_t *s, int32_t *sigma, unsigned long long *moves, cudaStream_t st);
+// id[v] = rank of comm[v] among the names in use (ascending); returns K
+// (host-synchronous)
+int32_t compact_names(int32_t n, const int32_t *comm, int32_t *id, int32_t *scratch_n,
+                      cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Device helpers

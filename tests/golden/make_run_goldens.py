@@ -3,8 +3,10 @@
 Usage: python tests/golden/make_run_goldens.py [case ...]   (all cases by default)
 
 Each case regenerates a seeded graph with ``graphgen`` and runs the CPU oracle
-(``oracle.slm``, Algorithm 1 with ASSIGN, POSITIVE and MAXIMAL as the oracle
-restates them) on it, single-threaded; nothing here touches the CUDA library.
+on it, single-threaded: ``oracle.slm`` (Algorithm 1 with ASSIGN, POSITIVE and
+MAXIMAL as the oracle restates them), or for the comparison method
+``oracle.louvain_colour`` (colour-synchronous Louvain); nothing here touches
+the CUDA library.
 The result goes to ``tests/golden/run_<case>.json``:
 
   graph    n, nnz, m_w and SHA-256 digests of row_ptr, col and w (int32,
@@ -52,7 +54,7 @@ def _lfr_256k():
     return gg.cached("lfr_style_n262144", lambda: gg.lfr_style(n=262144)[0])
 
 
-# case name -> (graph, run options, description)
+# case name -> (graph, run options, description[, oracle method])
 CASES = {
     "rmat_s20": (_rmat_s20, dict(seed=1, P=O.P_HALF),
                  "R-MAT scale 20 (seed 2), complete run, acceptance seed 1, p = 1/2"),
@@ -60,6 +62,9 @@ CASES = {
                        "LFR-style 4,194,304 nodes (seed 3), at most 2 sweeps per level and 3 levels"),
     "lfr_256k_bounded": (_lfr_256k, dict(seed=1, P=O.P_HALF, max_sweeps=3),
                          "LFR-style 262,144 nodes (seed 3), at most 3 sweeps per level, every level"),
+    "louvain_rmat_s20": (_rmat_s20, dict(seed=1),
+                         "colour-synchronous Louvain on R-MAT scale 20 (seed 2), colouring seed 1, "
+                         "complete run", "louvain_colour"),
 }
 
 
@@ -74,10 +79,11 @@ def fingerprint(g) -> dict:
 
 
 def make(case: str) -> dict:
-    gen, opts, desc = CASES[case]
+    gen, opts, desc = CASES[case][:3]
+    method = CASES[case][3] if len(CASES[case]) > 3 else "slm"
     g = gen()
     t0 = time.time()
-    r = O.slm(g, **opts)
+    r = getattr(O, method)(g, **opts)
     dt = time.time() - t0
     q = O.modularity(g, r.final)
     levels = []
@@ -86,6 +92,7 @@ def make(case: str) -> dict:
     out = {
         "case": case,
         "description": desc,
+        "method": method,
         "options": {k: int(v) for k, v in opts.items()},
         "graph": fingerprint(g),
         "levels": levels,

@@ -108,8 +108,12 @@ def compare_with_golden(g, gold, **run_kw):
     assert _sha(g.row_ptr) == fp["row_ptr"] and _sha(g.col) == fp["col"] and _sha(g.w) == fp["w"]
     opts = gold["options"]
     G = slm.Graph(g.row_ptr, g.col, g.w)
-    G.run(seed=opts["seed"], accept_p32=opts["P"], max_sweeps=opts.get("max_sweeps", 1000),
-          max_levels=opts.get("max_levels", 64), **run_kw)
+    if gold.get("method", "slm") == "louvain_colour":
+        G.run_louvain(seed=opts["seed"], max_passes=opts.get("max_passes", 1000),
+                      max_levels=opts.get("max_levels", 64), **run_kw)
+    else:
+        G.run(seed=opts["seed"], accept_p32=opts["P"], max_sweeps=opts.get("max_sweeps", 1000),
+              max_levels=opts.get("max_levels", 64), **run_kw)
     tr = G.trace()
     exp_tr = np.array(gold["trace"], dtype=np.int64).reshape(-1, 6)
     assert tr.shape == exp_tr.shape, ("sweeps", tr.shape, exp_tr.shape)
@@ -137,6 +141,14 @@ def test_rmat_s20_whole_run_equals_oracle():
     the touched-set COMPONENTS and POSITIVE passes and AGGREGATE at the size
     where their thresholds switch."""
     G = compare_with_golden(_rmat(), _golden("rmat_s20"))
+    G.close()
+
+
+def test_louvain_rmat_s20_whole_run_equals_oracle():
+    """The comparison method (colour-synchronous Louvain, colouring seed 1)
+    on the benchmark graph equals the oracle's complete run: every level's
+    colouring-driven passes, the threshold stops and AGGREGATE."""
+    G = compare_with_golden(_rmat(), _golden("louvain_rmat_s20"))
     G.close()
 
 
