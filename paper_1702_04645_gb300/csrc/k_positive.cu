@@ -323,10 +323,15 @@ __device__ __forceinline__ void k_branch(int cnt, const int32_t *M, const uint8_
 }
 
 // one block per community with a cycle of length >= 2; one thread per p, the
-// part V = trees (p, q] grows with q: W(V+q, U-q) = W(V,U) + row(q) - 2 W(V,q)
+// part V = trees (p, q] grows with q: W(V+q, U-q) = W(V,U) + row(q) - 2 W(V,q).
+// The row total row(q) and the weight W(V,q) from the trees (p, q) to tree q
+// are read from a 2D prefix table of the tree-to-tree weights Mr, built by
+// the block in the first pass of each round (P[a][b] = sum of Mr[k][k'] over
+// k < a, k' < b), so every cut costs O(1) and a community O(l^2) instead of
+// O(l^3).  The sums are those of Mr itself: the values are unchanged.
 template <class NM>
 __device__ __forceinline__ void k_cycle(const int32_t *Rdev, const int32_t *rlist, const int32_t *L, const int32_t *coffN,
-                        const int32_t *cyc, const long long *moffN, const long long *Mw,
+                        const int32_t *cyc, const long long *moffN, const long long *Mw, long long *Mp,
                         const long long *TS, const typename NM::ST *sigma, MParam mp, int32_t n,
                         long long *bestsc, unsigned long long *bestkey, int pass) {
     const int R = *Rdev;
@@ -337,15 +342,42 @@ __device__ __forceinline__ void k_cycle(const int32_t *Rdev, const int32_t *rlis
         const long long m = mp.of(r);
         const int32_t *cy = cyc + coffN[r];
         const long long *Mr = Mw + moffN[r];
+        const long long l1 = l + 1;
+        // (l + 1)^2 <= l^2 + 3 l entries: the region of this community in Mp
+        long long *P = Mp + moffN[r] + 3LL * coffN[r];
+        if (pass == 0) {
+            for (int b = threadIdx.x; b <= l; b += blockDim.x) P[b] = 0;
+            for (int k = threadIdx.x; k < l; k += blockDim.x) {  // prefixes along each row
+                long long acc = 0;
+                long long *row = P + (long long)(k + 1) * l1;
+                row[0] = 0;
+                for (int t = 0; t < l; t++) {
+                    acc += Mr[(long long)k * l + t];
+                    row[t + 1] = acc;
+                }
+            }
+            __syncthreads();
+            for (int bcol = threadIdx.x; bcol <= l; bcol += blockDim.x) {  // then down each column
+                long long acc = 0;
+                for (int a = 1; a <= l; a++) {
+                    acc += P[(long long)a * l1 + bcol];
+                    P[(long long)a * l1 + bcol] = acc;
+                }
+            }
+            __syncthreads();
+        }
         const long long sA = (long long)sigma[r];
         for (int p = threadIdx.x; p < l; p += blockDim.x) {
+            const int cp = cy[p];
+            if (cp < 0 || cp >= n) continue;  // unfilled slot (cannot happen): no cut at p
+            const long long *Pp1 = P + (long long)(p + 1) * l1;
             long long cut = 0, sV = 0;
             for (int q = p + 1; q < l; q++) {
-                long long rowq = 0, inV = 0;
-                for (int t = 0; t < l; t++) rowq += Mr[(long long)q * l + t];
-                for (int k = p + 1; k < q; k++) inV += Mr[(long long)k * l + q];
-                int cp = cy[p], cq = cy[q];
-                if (cp < 0 || cp >= n || cq < 0 || cq >= n) return;  // unfilled slot: skip the community
+                const int cq = cy[q];
+                if (cq < 0 || cq >= n) break;
+                const long long *Pq = P + (long long)q * l1, *Pq1 = P + (long long)(q + 1) * l1;
+                const long long rowq = Pq1[l] - Pq[l];
+                const long long inV = (Pq[q + 1] - Pq[q]) - (Pp1[q + 1] - Pp1[q]);
                 cut += rowq - 2 * inV;
                 sV += TS[cq];
                 long long sc = NM::cross(sV, sA - sV) - m * cut;
@@ -604,6 +636,38 @@ __device__ __forceinline__ void k_own_members(int cnt, const int32_t *M, const u
 // members with longer rows are served by whole blocks (k_int_*_big)
 constexpr int kIntWarpMaxDeg = 1024;
 
+// The listed members k < cnt whose row is longer than `thr`, each handed to
+// body(k) by a whole block: the first warp tests 32 members at once and the
+// block walks the long ones in the tile, so finding the few long rows costs
+// one load step per tile instead of one per member.  Members of a tile are
+// taken in list order; the body may use __syncthreads.
+template <class F>
+__device__ __forceinline__ void for_long_rows(long long cnt, const int32_t *list, const int32_t *rp, int thr,
+                                              unsigned *sbal, F &&body) {
+    for (long long t0 = (long long)blockIdx.x * 32; t0 < cnt; t0 += (long long)gridDim.x * 32) {
+        if (threadIdx.x < 32) {
+            const long long k = t0 + threadIdx.x;
+            bool lng = false;
+            if (k < cnt) {
+                const int x = list[k];
+                lng = rp[x + 1] - rp[x] > thr;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, lng);
+            if (threadIdx.x == 0) *sbal = bal;
+        }
+        __syncthreads();
+        unsigned b = *sbal;
+        while (b) {
+            const int q = __ffs(b) - 1;
+            b &= b - 1;
+            body(t0 + q);
+        }
+        __syncthreads();
+    }
+}
+// blocks for for_long_rows over cnt members
+inline int long_row_blocks(long long cnt) { return grid_for((cnt + 31) / 32, 1, kNumSMs * 4); }
+
 __global__ void k_int_fill(int cnt, const int32_t *M, const int32_t *rp, const int32_t *col,
                            const int32_t *w, const int32_t *root, const int32_t *ioff,
                            int32_t *istart, int32_t *ideg, int32_t *icol, int32_t *iw) {
@@ -643,11 +707,11 @@ __global__ void k_int_fill_big(int cnt, const int32_t *M, const int32_t *rp, con
                                const int32_t *w, const int32_t *root, const int32_t *ioff,
                                int32_t *istart, int32_t *ideg, int32_t *icol, int32_t *iw) {
     __shared__ int cursor;
+    __shared__ unsigned sbal;
     const int lane = threadIdx.x & 31;
-    for (long long k = blockIdx.x; k < cnt; k += gridDim.x) {
+    for_long_rows(cnt, M, rp, kIntWarpMaxDeg, &sbal, [&](long long k) {
         const int x = M[k];
         const int b = rp[x], e = rp[x + 1];
-        if (e - b <= kIntWarpMaxDeg) continue;  // uniform over the block
         const int r = root[x];
         if (threadIdx.x == 0) cursor = ioff[k];
         __syncthreads();
@@ -689,7 +753,7 @@ __global__ void k_int_fill_big(int cnt, const int32_t *M, const int32_t *rp, con
             ideg[x] = cursor - ioff[k];
         }
         __syncthreads();
-    }
+    });
 }
 template <class NM>
 __device__ __forceinline__ void k_own_finish(int cnt, const int32_t *M, const typename NM::ST *s, MParam mp,
@@ -892,6 +956,7 @@ struct PosArgs {
     typename NM::ST *sigma;
     int32_t *flag, *kown, *listA, *listB, *rlist, *posr, *L, *coff, *epref, *mark, *cyc;
     long long *msz, *subS, *subWA, *subWin, *credit, *TS, *bestsc, *kacc, *Mw;
+    long long *Mp;  // 2D prefix tables of the cycles' tree-to-tree weights
     unsigned long long *bestkey;
     int4 *cut, *nf;
     uint8_t *noc, *recomp;
@@ -1000,7 +1065,7 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs<NM> A) 
             k_branch<NM>(cnt, M, A.oncycle, A.root, A.posr, A.sigma, A.m, A.subS, A.subWA, A.subWin,
                      A.bestsc, A.bestkey, A.kacc, A.epref, pass);
             if (cycles)
-                k_cycle<NM>(&C->R, A.rlist, A.L, A.coffN, A.cyc, A.moffN, A.Mw, A.TS, A.sigma, A.m, n,
+                k_cycle<NM>(&C->R, A.rlist, A.L, A.coffN, A.cyc, A.moffN, A.Mw, A.Mp, A.TS, A.sigma, A.m, n,
                         A.bestsc, A.bestkey, pass);
             GBAR_OR_RETURN();
         }
@@ -1111,10 +1176,10 @@ __global__ void k_own_listed_big(int cnt, const int32_t *list, const int32_t *rp
                                  const int32_t *root, const typename NM::ST *sigma, int32_t *kown,
                                  int32_t *flag) {
     __shared__ long long red[32];
-    for (long long k = blockIdx.x; k < cnt; k += gridDim.x) {
+    __shared__ unsigned sbal;
+    for_long_rows(cnt, list, rp, kOwnWarpMaxDeg, &sbal, [&](long long k) {
         const int x = list[k];
         const int b = rp[x], e = rp[x + 1];
-        if (e - b <= kOwnWarpMaxDeg) continue;  // uniform over the block
         const int rx = root[x];
         long long acc = 0;
         // eight entries per thread in flight: a hub's row takes few dependent steps
@@ -1141,7 +1206,7 @@ __global__ void k_own_listed_big(int cnt, const int32_t *list, const int32_t *rp
             if (m * t - NM::cross(si, (long long)sigma[rx] - si) < 0) flag[rx] = 1;
         }
         __syncthreads();
-    }
+    });
 }
 
 // bound of the pools: cycle lengths never grow during POSITIVE
@@ -1238,7 +1303,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
         k_own_listed<NM><<<grid_for((long long)nd * 32, 256), 256, 0, st>>>(nd, M2, rp, col, w, s, m, f.root,
                                                                        sigma, kown, flag);
         SLM_LAUNCH_CHECK();
-        k_own_listed_big<NM><<<grid_for(nd, 1, kNumSMs * 4), 256, 0, st>>>(nd, M2, rp, col, w, s, m, f.root,
+        k_own_listed_big<NM><<<long_row_blocks(nd), 256, 0, st>>>(nd, M2, rp, col, w, s, m, f.root,
                                                                        sigma, kown, flag);
         SLM_LAUNCH_CHECK();
         cnt = compact_members(nd, M2, f.root, flag, M, ps.mark, ps.tot, st);
@@ -1281,6 +1346,8 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     slm::stream_sync(st);
     const long long itot = (long long)(int32_t)(hb[2] & 0xffffffffu);
     ps.pool.ensure(8 * (size_t)(hb[0] > 0 ? hb[0] : 1), st);
+    // prefix tables: (l + 1)^2 <= l^2 + 3 l entries per cycle
+    ps.pool2.ensure(8 * ((size_t)(hb[0] > 0 ? hb[0] : 1) + 3 * (size_t)(hb[1] > 0 ? hb[1] : 1)), st);
     ps.cyc.ensure(4 * (size_t)(hb[1] > 0 ? hb[1] : 1), st);
     ps.istart.ensure(4 * (N + 1), st);
     ps.ideg.ensure(4 * (N + 1), st);
@@ -1290,7 +1357,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
         cnt, M, rp, col, w, f.root, ps.ioff.as<int32_t>(), ps.istart.as<int32_t>(),
         ps.ideg.as<int32_t>(), ps.icol.as<int32_t>(), ps.iw.as<int32_t>());
     SLM_LAUNCH_CHECK();
-    k_int_fill_big<<<grid_for(cnt, 1, kNumSMs * 4), 256, 0, st>>>(
+    k_int_fill_big<<<long_row_blocks(cnt), 256, 0, st>>>(
         cnt, M, rp, col, w, f.root, ps.ioff.as<int32_t>(), ps.istart.as<int32_t>(),
         ps.ideg.as<int32_t>(), ps.icol.as<int32_t>(), ps.iw.as<int32_t>());
     SLM_LAUNCH_CHECK();
@@ -1343,6 +1410,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     A.bestsc = bestsc;
     A.kacc = ps.kacc.as<long long>();
     A.Mw = ps.pool.as<long long>();
+    A.Mp = ps.pool2.as<long long>();
     A.bestkey = bestkey;
     A.cut = ps.cut.as<int4>();
     A.nf = ps.nf.as<int4>();
