@@ -62,6 +62,8 @@ CASES = {
                        "LFR-style 4,194,304 nodes (seed 3), at most 2 sweeps per level and 3 levels"),
     "lfr_4m_level0": (_lfr_4m, dict(seed=1, P=O.P_HALF, max_sweeps=2, max_levels=1),
                       "LFR-style 4,194,304 nodes (seed 3), level 0 only, at most 2 sweeps"),
+    "lfr_4m_level0": (_lfr_4m, dict(seed=1, P=O.P_HALF, max_sweeps=2, max_levels=1),
+                      "LFR-style 4,194,304 nodes (seed 3), level 0 only, at most 2 sweeps"),
     "lfr_256k_bounded": (_lfr_256k, dict(seed=1, P=O.P_HALF, max_sweeps=3),
                          "LFR-style 262,144 nodes (seed 3), at most 3 sweeps per level, every level"),
     "louvain_rmat_s20": (_rmat_s20, dict(seed=1),
