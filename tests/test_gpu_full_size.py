@@ -10,8 +10,8 @@ LFR-style recipe.
     per-sweep trace, the final labels and Q) with the oracle's runs stored
     under tests/golden/ by tests/golden/make_run_goldens.py (which calls
     only the oracle): the complete run on the R-MAT graph, and bounded runs
-    (3 sweeps per level at 262,144 nodes; 2 sweeps per level and 3 levels
-    at 4,194,304) on the LFR-style graphs, where the method does not settle:
+    (3 sweeps per level at 262,144 nodes; level 0 with 2 sweeps at
+    4,194,304) on the LFR-style graphs, where the method does not settle:
     after a few sweeps long assignment cycles form, whose cycle cuts cost
     the oracle hours;
   * properties that hold at any size: every level's labels are 0..K-1, the
@@ -158,12 +158,13 @@ def test_rmat_s20_whole_run_timed_flags_equal():
     G.close()
 
 
-def test_lfr_4m_bounded_run_equals_oracle():
-    """The 4,194,304-node LFR-style graph with at most 2 sweeps per level and
-    3 levels equals the oracle's bounded run level by level (beyond the
-    second sweep long assignment cycles form and the oracle's cycle cuts
-    take hours at this size)."""
-    G = compare_with_golden(_lfr(), _golden("lfr_4m_bounded"))
+def test_lfr_4m_level0_run_equals_oracle():
+    """The 4,194,304-node LFR-style graph, level 0 with at most 2 sweeps
+    (ASSIGN, COMPONENTS, the first POSITIVE over the whole graph, two MAXIMAL
+    corrections with their POSITIVE calls), equals the oracle's run: the
+    level's ids, stats, both sweeps of the trace and Q.  Deeper runs form
+    long assignment cycles whose cuts take the oracle hours at this size."""
+    G = compare_with_golden(_lfr(), _golden("lfr_4m_level0"))
     G.close()
 
 
