@@ -18,7 +18,11 @@
 // coloured in earlier rounds, and no neighbour that follows it is coloured
 // before it, so each node sees exactly the neighbours the sequential order
 // would show it.
-#include "slm_internal.cuh"
+#include <algorithm>
+#include <climits>
+#include <mutex>
+
+#include "forest_dev.cuh"
 
 namespace slm {
 namespace {
@@ -30,57 +34,87 @@ __device__ __forceinline__ unsigned long long colour_key(unsigned long long seed
 // cr[v] = -1 while v is uncoloured, then (round << 32) | colour.  A neighbour
 // coloured in the current round counts as uncoloured, so a decision never
 // depends on the order in which the round's writes land (64-bit stores are
-// seen whole).  One warp per node.
-__global__ void k_colour_round(int32_t n, const int32_t *rp, const int32_t *col,
-                               unsigned long long seed, int t, int round, long long *cr,
-                               int32_t *left) {
+// seen whole).  One warp per node; returns (to every lane) whether v stays
+// uncoloured because an uncoloured neighbour comes first.
+__device__ __forceinline__ bool colour_node(long long v, const int32_t *rp, const int32_t *col,
+                                            unsigned long long seed, int t, int round, long long *cr) {
     const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    int blocked_nodes = 0;
-    for (long long v = warp; v < n; v += nw) {
-        if (cr[v] >= 0) continue;  // uniform over the warp
-        const unsigned long long kv = colour_key(seed, t, (int)v);
-        const int b = rp[v], e = rp[v + 1];
+    const unsigned long long kv = colour_key(seed, t, (int)v);
+    const int b = rp[v], e = rp[v + 1];
+    // the whole warp stops at the first 32 entries that hold an uncoloured
+    // neighbour coming first (on a dense row that is usually the first look)
+    for (int p0 = b; p0 < e; p0 += 32) {
+        const int p = p0 + lane;
         bool blocked = false;
-        for (int p = b + lane; p < e && !blocked; p += 32) {
+        if (p < e) {
             const int u = col[p];
-            if (u == v) continue;
-            const long long c = cr[u];
-            const bool unc = c < 0 || (int)(c >> 32) == round;
-            if (unc) {
+            const long long c = u != v ? cr[u] : 0;
+            if (u != v && (c < 0 || (int)(c >> 32) == round)) {
                 const unsigned long long ku = colour_key(seed, t, u);
                 blocked = ku > kv || (ku == kv && u < (int)v);
             }
         }
-        if (__any_sync(0xffffffffu, blocked)) {
-            blocked_nodes++;
-            continue;
-        }
-        // the smallest colour held by no neighbour coloured before this round,
-        // 64 colours per look at the row
-        int colour = 0;
-        for (int base = 0;; base += 64) {
-            unsigned long long mask = 0;
-            for (int p = b + lane; p < e; p += 32) {
-                const int u = col[p];
-                if (u == v) continue;
-                const long long c = cr[u];
+        if (__any_sync(0xffffffffu, blocked)) return true;
+    }
+    // the smallest colour held by no neighbour coloured before this round,
+    // 64 colours per look at the row, four entries per lane in flight
+    int colour = 0;
+    for (int base = 0;; base += 64) {
+        unsigned long long mask = 0;
+        for (int p0 = b + lane; p0 < e; p0 += 128) {
+            int u[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) u[k] = p0 + 32 * k < e ? col[p0 + 32 * k] : (int)v;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (u[k] == v) continue;
+                const long long c = cr[u[k]];
                 if (c >= 0 && (int)(c >> 32) != round) {
                     const int cu = (int)(c & 0xffffffffll);
                     if (cu >= base && cu < base + 64) mask |= 1ull << (cu - base);
                 }
             }
-#pragma unroll
-            for (int o = 16; o; o >>= 1) mask |= __shfl_xor_sync(0xffffffffu, mask, o);
-            if (mask != ~0ull) {
-                colour = base + __ffsll((long long)~mask) - 1;
-                break;
-            }
         }
-        if (lane == 0) cr[v] = ((long long)round << 32) | (long long)colour;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mask |= __shfl_xor_sync(0xffffffffu, mask, o);
+        if (mask != ~0ull) {
+            colour = base + __ffsll((long long)~mask) - 1;
+            break;
+        }
     }
-    if (lane == 0 && blocked_nodes) atomicAdd(left, blocked_nodes);
+    if (lane == 0) cr[v] = ((long long)round << 32) | (long long)colour;
+    return false;
+}
+
+// Every round of the colouring in one cooperative launch (the rows of a dense
+// aggregated graph can need one round per node): rounds are separated by grid
+// barriers with a time limit.  Round r counts its still-uncoloured nodes in
+// cnt3[r % 3]; the counter of round r + 1 is cleared during round r by one
+// thread, after every block has passed the barrier that ended the reads of
+// its last use (round r - 2).  Ends when a round leaves no node uncoloured;
+// *rounds_out gets the number of rounds (at most n + 1).
+__global__ void __launch_bounds__(256) k_colour_rounds(int32_t n, const int32_t *rp, const int32_t *col,
+                                                       unsigned long long seed, int t, long long *cr,
+                                                       GridBarrier *bar, int32_t *cnt3, long long limit_ns,
+                                                       int32_t *rounds_out) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const bool rank0 = blockIdx.x == 0 && threadIdx.x == 0;
+    for (int round = 0; round <= n; round++) {
+        if (rank0) cnt3[(round + 1) % 3] = 0;
+        int blocked_nodes = 0;
+        for (long long v = warp; v < n; v += nw) {
+            if (cr[v] >= 0) continue;  // uniform over the warp
+            if (colour_node(v, rp, col, seed, t, round, cr)) blocked_nodes++;
+        }
+        if (lane == 0 && blocked_nodes) atomicAdd(&cnt3[round % 3], blocked_nodes);
+        if (!gbar(bar, limit_ns)) return;
+        if (*((volatile int32_t *)&cnt3[round % 3]) == 0) {
+            if (rank0) *rounds_out = round + 1;
+            return;
+        }
+    }
 }
 
 __global__ void k_colour_take(int32_t n, const long long *cr, int32_t *colour, uint32_t *key,
@@ -127,6 +161,106 @@ __global__ void k_louvain_move(const int32_t *list, int32_t cnt, const int32_t *
     if ((threadIdx.x & 31) == 0 && mv) atomicAdd(moves, (unsigned long long)mv);
 }
 
+// The decision of one listed node by one block, for level graphs small
+// enough that a colour class holds a few nodes: the MAXIMAL scan's decision
+// (stay unless the best other neighbouring community, ties to the smallest
+// name, beats the own one by a positive amount) from a shared-memory table of
+// the neighbouring communities' weights, 2^lg slots (at least twice the
+// row's length).  Self-loops are left out as the scan leaves them out.
+__global__ void __launch_bounds__(256) k_louvain_decide(const int32_t *list, int32_t cnt, const int32_t *rp,
+                                                        const int32_t *col, const int32_t *w,
+                                                        const int32_t *s, long long m, const int32_t *comm,
+                                                        const int32_t *sigma, int lg, int32_t *best) {
+    extern __shared__ int tab[];
+    __shared__ long long w_sc[8], w_own[8];
+    __shared__ int w_c[8];
+    const int T = 1 << lg;
+    int *keys = tab, *vals = tab + T;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (long long k = blockIdx.x; k < cnt; k += gridDim.x) {
+        const int i = list[k];
+        const int ci = comm[i];
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            keys[t] = -1;
+            vals[t] = 0;
+        }
+        __syncthreads();
+        long long own = 0;
+        const int b = rp[i], e = rp[i + 1];
+        for (int p = b + threadIdx.x; p < e; p += blockDim.x) {
+            const int j = col[p];
+            if (j == i) continue;
+            const int c = comm[j], wv = w[p];
+            if (c == ci) {
+                own += wv;
+                continue;
+            }
+            unsigned h = ((unsigned)c * 2654435761u) >> (32 - lg);
+            for (;;) {
+                const int prev = atomicCAS(&keys[h], -1, c);
+                if (prev == -1 || prev == c) {
+                    atomicAdd(&vals[h], wv);
+                    break;
+                }
+                h = (h + 1) & (unsigned)(T - 1);
+            }
+        }
+        __syncthreads();
+        const long long si = s[i];
+        long long bsc = LLONG_MIN;
+        int bc = INT_MAX;
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            const int c = keys[t];
+            if (c < 0) continue;
+            const long long sc = m * (long long)vals[t] - si * (long long)sigma[c];
+            if (sc > bsc || (sc == bsc && c < bc)) {
+                bsc = sc;
+                bc = c;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            own += __shfl_xor_sync(0xffffffffu, own, o);
+            const long long osc = __shfl_xor_sync(0xffffffffu, bsc, o);
+            const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+            if (osc > bsc || (osc == bsc && oc < bc)) {
+                bsc = osc;
+                bc = oc;
+            }
+        }
+        if (lane == 0) {
+            w_sc[wid] = bsc;
+            w_c[wid] = bc;
+            w_own[wid] = own;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long tsc = LLONG_MIN, town = 0;
+            int tc = INT_MAX;
+            for (int q = 0; q < (int)(blockDim.x >> 5); q++) {
+                town += w_own[q];
+                if (w_sc[q] > tsc || (w_sc[q] == tsc && w_c[q] < tc)) {
+                    tsc = w_sc[q];
+                    tc = w_c[q];
+                }
+            }
+            const long long g = m * town - si * ((long long)sigma[ci] - si);
+            best[i] = (tc != INT_MAX && tsc - g > 0) ? tc : ci;
+        }
+        __syncthreads();  // the table is cleared for the next node
+    }
+}
+
+__global__ void k_max_row(int32_t n, const int32_t *rp, int32_t *mx) {
+    int d = 0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x)
+        d = max(d, rp[v + 1] - rp[v]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) d = max(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if ((threadIdx.x & 31) == 0 && d > 0) atomicMax(mx, d);
+}
+
 __global__ void k_louvain_init(int32_t n, const int32_t *s, int32_t *comm, int32_t *sigma) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (long long)gridDim.x * blockDim.x) {
@@ -158,17 +292,35 @@ std::vector<int32_t> colour_nodes(int32_t n, const int32_t *rp, const int32_t *c
         vtmp(4 * (size_t)n, st);
     SLM_CUDA(cudaMemsetAsync(cr.get(), 0xff, 8 * (size_t)n, st));
     int32_t *lp = left.as<int32_t>();
-    const int grid = grid_for((long long)n * 32, 256, kNumSMs * 16);
-    // every round colours at least the first uncoloured node of the order
-    for (int round = 0;; round++) {
-        if (round > n) fail(SLM_ERR_CUDA, "colouring did not finish");
-        SLM_CUDA(cudaMemsetAsync(lp, 0, 8, st));
-        k_colour_round<<<grid, 256, 0, st>>>(n, rp, col, seed, level, round, cr.as<long long>(), lp);
-        SLM_LAUNCH_CHECK();
-        int32_t h = 0;
-        SLM_CUDA(cudaMemcpyAsync(&h, lp, sizeof h, cudaMemcpyDeviceToHost, st));
+    {
+        // the barrier word and the three round counters
+        DevBuf barm(sizeof(GridBarrier) + 16, st);
+        SLM_CUDA(cudaMemsetAsync(barm.get(), 0, sizeof(GridBarrier) + 16, st));
+        GridBarrier *bar = barm.as<GridBarrier>();
+        int32_t *cnt3 = reinterpret_cast<int32_t *>(bar + 1);
+        int dev = 0, sms = 0, per_sm = 0;
+        SLM_CUDA(cudaGetDevice(&dev));
+        SLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colour_rounds, 256, 0));
+        if (per_sm < 1) fail(SLM_ERR_CUDA, "colouring kernel cannot be resident");
+        // one block per SM: a small dense graph needs many rounds, and the
+        // barrier's cost grows with the blocks
+        const int nb = (int)std::min<long long>((long long)sms, ((long long)n * 32 + 255) / 256);
+        long long lim = kBarrierLimitNs;
+        long long *cr_p = cr.as<long long>();
+        int32_t *rounds = lp + 2;
+        void *kargs[] = {&n, (void *)&rp, (void *)&col, &seed, &level, (void *)&cr_p, &bar, &cnt3, &lim,
+                         &rounds};
+        serialised_cooperative(st, [&] {
+            SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_colour_rounds, dim3(nb), dim3(256), kargs,
+                                                 0, st));
+            SLM_LAUNCH_CHECK();
+        });
+        GridBarrier hb{};
+        SLM_CUDA(cudaMemcpyAsync(&hb, bar, sizeof hb, cudaMemcpyDeviceToHost, st));
         stream_sync(st);
-        if (h == 0) break;
+        if (hb.failed) fail(SLM_ERR_TIMEOUT, "a colouring grid barrier waited past its time limit");
+        SLM_CUDA(cudaMemsetAsync(lp, 0, 8, st));
     }
     k_colour_take<<<grid_for(n, 256), 256, 0, st>>>(n, cr.as<long long>(), colour, key.as<uint32_t>(),
                                                     order, lp + 1);
@@ -188,6 +340,43 @@ std::vector<int32_t> colour_nodes(int32_t n, const int32_t *rp, const int32_t *c
     stream_sync(st);
     for (int k = 0; k < ncol; k++) class_off.push_back(class_off.back() + h[k]);
     return class_off;
+}
+
+int32_t max_row_length(int32_t n, const int32_t *rp, cudaStream_t st) {
+    if (n <= 0) return 0;
+    DevBuf mx(16, st);
+    SLM_CUDA(cudaMemsetAsync(mx.get(), 0, 16, st));
+    k_max_row<<<grid_for(n, 256), 256, 0, st>>>(n, rp, mx.as<int32_t>());
+    SLM_LAUNCH_CHECK();
+    int32_t h = 0;
+    SLM_CUDA(cudaMemcpyAsync(&h, mx.get(), sizeof h, cudaMemcpyDeviceToHost, st));
+    stream_sync(st);
+    return h;
+}
+
+void louvain_decide(const int32_t *list, int32_t cnt, const int32_t *rp, const int32_t *col,
+                    const int32_t *w, const int32_t *s, long long m, const int32_t *comm,
+                    const int32_t *sigma, int32_t max_row, int32_t *best, cudaStream_t st) {
+    if (cnt <= 0) return;
+    if (max_row > kLouvainDecideMaxRow) fail(SLM_ERR_INVALID_ARGUMENT, "row too long for the direct decision");
+    int lg = 5;
+    while ((1 << lg) < 2 * max_row) lg++;
+    const size_t smem = (size_t)8 << lg;
+    static std::mutex mu;
+    static unsigned long long ready = 0;  // bit d: device d allows the largest table
+    int dev = 0;
+    SLM_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 64 || !((ready >> dev) & 1ull)) {
+            SLM_CUDA(cudaFuncSetAttribute(k_louvain_decide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)((size_t)8 << kLouvainDecideMaxLg)));
+            if (dev < 64) ready |= 1ull << dev;
+        }
+    }
+    k_louvain_decide<<<(int)std::min<long long>(cnt, (long long)kNumSMs * 8), 256, smem, st>>>(
+        list, cnt, rp, col, w, s, m, comm, sigma, lg, best);
+    SLM_LAUNCH_CHECK();
 }
 
 void louvain_init(int32_t n, const int32_t *s, int32_t *comm, int32_t *sigma, cudaStream_t st) {

@@ -779,11 +779,13 @@ __device__ __forceinline__ void k_own_finish(int cnt, const int32_t *M, const ty
 // the same length are scanned together.  Ends after a grid barrier.
 // ---------------------------------------------------------------------------
 constexpr int kPosThreads = 256;
-// a POSITIVE call continues on a grid of kPosTailBlocks blocks, whose
-// barriers are much cheaper, once a round has at most this many members and
-// internal entries
+// a POSITIVE call continues on a grid of kPosTailBlocks blocks (by default
+// one block, whose grid barriers are block barriers) once a round has at most
+// kPosTailMembers members and kPosTailEntries internal entries: measured on
+// R-MAT and weighted LFR graphs, one block with a 2,048-member handoff is the
+// fastest of 1, 4 and 16 blocks with 2,048, 8,192 or 32,768 members
 #ifndef SLM_POS_TAIL_BLOCKS
-#define SLM_POS_TAIL_BLOCKS 16
+#define SLM_POS_TAIL_BLOCKS 1
 #endif
 constexpr int kPosTailBlocks = SLM_POS_TAIL_BLOCKS;
 // blocks per SM of the full grid: rounds hold tens of thousands of members at
@@ -794,7 +796,7 @@ constexpr int kPosTailBlocks = SLM_POS_TAIL_BLOCKS;
 #endif
 constexpr int kPosBlocksPerSM = SLM_POS_BLOCKS_PER_SM;
 #ifndef SLM_POS_TAIL_MEMBERS
-#define SLM_POS_TAIL_MEMBERS 8192
+#define SLM_POS_TAIL_MEMBERS 2048
 #endif
 constexpr int kPosTailMembers = SLM_POS_TAIL_MEMBERS;
 constexpr long long kPosTailEntries = 8LL * SLM_POS_TAIL_MEMBERS;

@@ -562,6 +562,16 @@ void modularity_forest(int32_t n, const int32_t *rp, const int32_t *col, const i
 std::vector<int32_t> colour_nodes(int32_t n, const int32_t *rp, const int32_t *col,
                                   unsigned long long seed, int32_t level, int32_t *colour,
                                   int32_t *order, cudaStream_t st);
+// the longest row of the n-node graph (host-synchronous)
+int32_t max_row_length(int32_t n, const int32_t *rp, cudaStream_t st);
+// The MAXIMAL scan's decision (best[i]) for the cnt listed nodes, one block
+// per node with a shared-memory table: for graphs whose rows have at most
+// kLouvainDecideMaxRow entries (the table holds 2^kLouvainDecideMaxLg slots).
+constexpr int kLouvainDecideMaxLg = 14;
+constexpr int32_t kLouvainDecideMaxRow = 1 << (kLouvainDecideMaxLg - 1);
+void louvain_decide(const int32_t *list, int32_t cnt, const int32_t *rp, const int32_t *col,
+                    const int32_t *w, const int32_t *s, long long m, const int32_t *comm,
+                    const int32_t *sigma, int32_t max_row, int32_t *best, cudaStream_t st);
 // comm[v] = v, sigma[v] = s[v]
 void louvain_init(int32_t n, const int32_t *s, int32_t *comm, int32_t *sigma, cudaStream_t st);
 // the moves of the cnt listed nodes (best[i] != comm[i]), with their totals;

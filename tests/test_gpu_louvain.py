@@ -81,6 +81,15 @@ def test_louvain_rmat_hubs():
     compare_louvain(g, seed=2)
 
 
+def test_louvain_rmat_layout_path():
+    """R-MAT scale 17 (131,072 nodes): level 0 is above the size where the
+    colour classes are decided node by node, so every class runs the MAXIMAL
+    scan on its own bucketed layout; the aggregated levels take the direct
+    decision."""
+    g = gg.rmat(17, seed=2)
+    compare_louvain(g, seed=4)
+
+
 def test_louvain_rmat_threshold_stops():
     """R-MAT scale 16: the levels end on the numerator threshold (status 1)
     after passes whose moves undo one another."""
