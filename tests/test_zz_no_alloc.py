@@ -60,3 +60,36 @@ def test_noalloc_rejects_oversized_and_out_of_range_inputs():
     lab = labelled(g, 9, 4)
     assert slm.step_modularity_noalloc(g.row_ptr, g.col, g.w, lab) == \
         slm.step_modularity(g.row_ptr, g.col, g.w, lab)
+
+
+def test_noalloc_call_leaves_device_memory_unchanged():
+    """The defining property: with every input and output already on the
+    device, a call changes neither the device's free memory nor what the
+    caching allocator holds (nothing is allocated, not even temporarily
+    from a pool that would keep the memory afterwards)."""
+    import ctypes as C
+    g = gg.rmat(scale=14, seed=7)
+    lab = labelled(g, 3, 200)
+    dev = [torch.as_tensor(np.ascontiguousarray(x, dtype=np.int32)).cuda()
+           for x in (g.row_ptr, g.col, g.w, lab)]
+    num = torch.zeros(1, dtype=torch.int64, device="cuda")
+    q = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lib = slm.load()
+
+    def call():
+        st = lib.slm_step_modularity_noalloc(g.n, *(C.c_void_p(t.data_ptr()) for t in dev),
+                                             C.c_void_p(num.data_ptr()), C.c_void_p(q.data_ptr()),
+                                             C.c_void_p(0))
+        assert st == 0
+    call()  # the first call on the device looks up the array's address
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    q_ref, num_ref = slm.step_modularity(g.row_ptr, g.col, g.w, lab)
+    assert int(num.item()) == num_ref and float(q.item()) == q_ref
