@@ -874,26 +874,33 @@ void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const in
                       int32_t *flag, cudaStream_t st) {
     if (n <= 0) return;
     const int32_t *ord = bk.order.as<int32_t>();
+    // the classes write disjoint nodes: run them side by side, as the scan's
+    const bool side = scan_tuning().streams > 1 && bk.fork != nullptr;
+    if (side) {
+        SLM_CUDA(cudaEventRecord(bk.fork, st));
+        for (int k = 0; k < Buckets::kSide; k++) SLM_CUDA(cudaStreamWaitEvent(bk.side[k], bk.fork, 0));
+    }
+    cudaStream_t s1 = side ? bk.side[0] : st, s2 = side ? bk.side[1] : st, s3 = side ? bk.side[2] : st;
     // isolated nodes: own weight 0, local gain 0 (never flagged)
     int c0 = bk.off[kBucketEmpty + 1] - bk.off[kBucketEmpty];
     if (c0) {
-        k_own_group<NM, 4><<<blocks_for_groups(c0, 8), 256, 0, st>>>(ord, c0, rp, col, w, s, m, root, sigma, kown, flag);
+        k_own_group<NM, 4><<<blocks_for_groups(c0, 8), 256, 0, s3>>>(ord, c0, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (int c = bk.off[kBucketG4 + 1] - bk.off[kBucketG4]) {
-        k_own_group<NM, 4><<<blocks_for_groups(c, 8), 256, 0, st>>>(ord + bk.off[kBucketG4], c, rp, col, w, s, m, root, sigma, kown, flag);
+        k_own_group<NM, 4><<<blocks_for_groups(c, 8), 256, 0, s3>>>(ord + bk.off[kBucketG4], c, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (int c = bk.off[kBucketG8 + 1] - bk.off[kBucketG8]) {
-        k_own_group<NM, 8><<<blocks_for_groups(c, 4), 256, 0, st>>>(ord + bk.off[kBucketG8], c, rp, col, w, s, m, root, sigma, kown, flag);
+        k_own_group<NM, 8><<<blocks_for_groups(c, 4), 256, 0, s3>>>(ord + bk.off[kBucketG8], c, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (int c = bk.off[kBucketG16 + 1] - bk.off[kBucketG16]) {
-        k_own_group<NM, 16><<<blocks_for_groups(c, 2), 256, 0, st>>>(ord + bk.off[kBucketG16], c, rp, col, w, s, m, root, sigma, kown, flag);
+        k_own_group<NM, 16><<<blocks_for_groups(c, 2), 256, 0, s2>>>(ord + bk.off[kBucketG16], c, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (int c = bk.off[kBucketWarpHash + 1] - bk.off[kBucketG32]) {
-        k_own_group<NM, 32><<<blocks_for_groups(c, 1), 256, 0, st>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, kown, flag);
+        k_own_group<NM, 32><<<blocks_for_groups(c, 1), 256, 0, s2>>>(ord + bk.off[kBucketG32], c, rp, col, w, s, m, root, sigma, kown, flag);
         SLM_LAUNCH_CHECK();
     }
     if (int c = bk.off[kBucketBlockL + 1] - bk.off[kBucketBlockS]) {
@@ -902,14 +909,19 @@ void own_weight_nodes(int32_t n, const int32_t *rp, const int32_t *col, const in
     }
     if (bk.nhub > 0) {
         const int32_t *hubs = ord + bk.off[kBucketHub];
-        SLM_CUDA(cudaMemsetAsync(bk.hub_acc.get(), 0, sizeof(unsigned long long) * bk.nhub, st));
-        k_own_hub_chunk<<<grid_for(bk.nchunk, 1, kNumSMs * 8), kBlockThreads, 0, st>>>(
+        SLM_CUDA(cudaMemsetAsync(bk.hub_acc.get(), 0, sizeof(unsigned long long) * bk.nhub, s1));
+        k_own_hub_chunk<<<grid_for(bk.nchunk, 1, kNumSMs * 8), kBlockThreads, 0, s1>>>(
             bk.chunks.as<int4>(), bk.nchunk, hubs, col, w, root, bk.hub_acc.as<unsigned long long>());
         SLM_LAUNCH_CHECK();
-        k_own_hub_finish<NM><<<grid_for(bk.nhub, 256), 256, 0, st>>>(bk.nhub, hubs, s, m, root, sigma,
+        k_own_hub_finish<NM><<<grid_for(bk.nhub, 256), 256, 0, s1>>>(bk.nhub, hubs, s, m, root, sigma,
                                                                bk.hub_acc.as<unsigned long long>(), kown, flag);
         SLM_LAUNCH_CHECK();
     }
+    if (side)
+        for (int k = 0; k < Buckets::kSide; k++) {
+            SLM_CUDA(cudaEventRecord(bk.join[k], bk.side[k]));
+            SLM_CUDA(cudaStreamWaitEvent(st, bk.join[k], 0));
+        }
 }
 
 template <class NM>
