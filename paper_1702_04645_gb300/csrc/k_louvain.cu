@@ -36,14 +36,24 @@ __device__ __forceinline__ unsigned long long colour_key(unsigned long long seed
 // depends on the order in which the round's writes land (64-bit stores are
 // seen whole).  One warp per node; returns (to every lane) whether v stays
 // uncoloured because an uncoloured neighbour comes first.
+// bits per warp of the colour bitmaps: a node's first-fit colour is at most
+// its row length, so rows shorter than this take the bitmap
+constexpr int kColourBits = 8192;
+
+// resume[v] (zeroed before the first round) is the offset in v's row of the
+// first entry that may still hold a neighbour blocking v: the entries before
+// it were found coloured in an earlier round or ordered after v, and neither
+// ever changes, so each node's rows are checked O(row length) times in all.
+// cmax holds the largest colour given so far.
 __device__ __forceinline__ bool colour_node(long long v, const int32_t *rp, const int32_t *col,
-                                            unsigned long long seed, int t, int round, long long *cr) {
+                                            unsigned long long seed, int t, int round, long long *cr,
+                                            unsigned *bm, int32_t *resume, int32_t *cmax) {
     const int lane = threadIdx.x & 31;
     const unsigned long long kv = colour_key(seed, t, (int)v);
     const int b = rp[v], e = rp[v + 1];
     // the whole warp stops at the first 32 entries that hold an uncoloured
     // neighbour coming first (on a dense row that is usually the first look)
-    for (int p0 = b; p0 < e; p0 += 32) {
+    for (int p0 = b + resume[v]; p0 < e; p0 += 32) {
         const int p = p0 + lane;
         bool blocked = false;
         if (p < e) {
@@ -54,11 +64,52 @@ __device__ __forceinline__ bool colour_node(long long v, const int32_t *rp, cons
                 blocked = ku > kv || (ku == kv && u < (int)v);
             }
         }
-        if (__any_sync(0xffffffffu, blocked)) return true;
+        const unsigned bal = __ballot_sync(0xffffffffu, blocked);
+        if (bal) {
+            if (lane == 0) resume[v] = p0 - b + __ffs((int)bal) - 1;
+            return true;
+        }
     }
-    // the smallest colour held by no neighbour coloured before this round,
-    // 64 colours per look at the row, four entries per lane in flight
     int colour = 0;
+    // The bitmap holds colours below kColourBits.  It decides exactly when
+    // the row is shorter (a first-fit colour is at most the row length) or
+    // when every colour given in earlier rounds is below kColourBits - 1 (the
+    // neighbours then show at most kColourBits - 1 distinct colours, all in
+    // the bitmap, so its first clear bit is the answer).
+    const int words = e - b < kColourBits ? (e - b) / 32 + 1 : kColourBits / 32;
+    if (e - b < kColourBits || *((volatile int32_t *)cmax) < kColourBits - 1) {
+        // one look at the row: the colours of the neighbours coloured before
+        // this round as bits of the warp's bitmap, then its first clear bit
+        for (int q = lane; q < words; q += 32) bm[q] = 0u;
+        __syncwarp();
+        for (int p0 = b + lane; p0 < e; p0 += 128) {
+            int u[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) u[k] = p0 + 32 * k < e ? col[p0 + 32 * k] : (int)v;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (u[k] == v) continue;
+                const long long c = cr[u[k]];
+                if (c >= 0 && (int)(c >> 32) != round) {
+                    const int cu = (int)(c & 0xffffffffll);
+                    if (cu < 32 * words) atomicOr(&bm[cu >> 5], 1u << (cu & 31));
+                }
+            }
+        }
+        __syncwarp();
+        int first = INT_MAX;
+        for (int q = lane; q < words && first == INT_MAX; q += 32)
+            if (bm[q] != 0xffffffffu) first = 32 * q + __ffs((int)~bm[q]) - 1;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+        __syncwarp();  // the bitmap is reused by the warp's next node
+        if (lane == 0) {
+            cr[v] = ((long long)round << 32) | (long long)first;
+            atomicMax(cmax, first);
+        }
+        return false;
+    }
+    // a long row: 64 colours per look at the row, four entries per lane in flight
     for (int base = 0;; base += 64) {
         unsigned long long mask = 0;
         for (int p0 = b + lane; p0 < e; p0 += 128) {
@@ -82,38 +133,101 @@ __device__ __forceinline__ bool colour_node(long long v, const int32_t *rp, cons
             break;
         }
     }
-    if (lane == 0) cr[v] = ((long long)round << 32) | (long long)colour;
+    if (lane == 0) {
+        cr[v] = ((long long)round << 32) | (long long)colour;
+        atomicMax(cmax, colour);
+    }
     return false;
 }
 
 // Every round of the colouring in one cooperative launch (the rows of a dense
 // aggregated graph can need one round per node): rounds are separated by grid
-// barriers with a time limit.  Round r counts its still-uncoloured nodes in
-// cnt3[r % 3]; the counter of round r + 1 is cleared during round r by one
-// thread, after every block has passed the barrier that ended the reads of
-// its last use (round r - 2).  Ends when a round leaves no node uncoloured;
-// *rounds_out gets the number of rounds (at most n + 1).
+// barriers with a time limit, and a round visits only the nodes still
+// uncoloured.  Round r reads its list from wl[r & 1] (lcnt[r % 3] entries)
+// and appends the nodes it leaves uncoloured to wl[(r + 1) & 1], counting
+// them in lcnt[(r + 1) % 3]; lcnt[(r + 2) % 3], last read in round r - 1, is
+// cleared during round r.  Ends when a round leaves no node; *rounds_out gets
+// the number of rounds (at most n + 1).
 __global__ void __launch_bounds__(256) k_colour_rounds(int32_t n, const int32_t *rp, const int32_t *col,
                                                        unsigned long long seed, int t, long long *cr,
-                                                       GridBarrier *bar, int32_t *cnt3, long long limit_ns,
+                                                       int32_t *wl0, int32_t *wl1, int32_t *resume,
+                                                       GridBarrier *bar, int32_t *lcnt, long long limit_ns,
                                                        int32_t *rounds_out) {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const bool rank0 = blockIdx.x == 0 && threadIdx.x == 0;
+    __shared__ unsigned bitmaps[256 / 32][kColourBits / 32];
+    unsigned *bm = bitmaps[threadIdx.x >> 5];
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x)
+    {
+        wl0[v] = (int32_t)v;
+        resume[v] = 0;
+    }
+    if (rank0) {
+        lcnt[0] = n;
+        lcnt[1] = 0;
+        lcnt[2] = 0;
+        lcnt[3] = -1;  // the largest colour given so far
+    }
+    if (!gbar(bar, limit_ns)) return;
     for (int round = 0; round <= n; round++) {
-        if (rank0) cnt3[(round + 1) % 3] = 0;
-        int blocked_nodes = 0;
-        for (long long v = warp; v < n; v += nw) {
-            if (cr[v] >= 0) continue;  // uniform over the warp
-            if (colour_node(v, rp, col, seed, t, round, cr)) blocked_nodes++;
+        const int32_t *in = (round & 1) ? wl1 : wl0;
+        int32_t *out = (round & 1) ? wl0 : wl1;
+        const int32_t cnt = *((volatile int32_t *)&lcnt[round % 3]);
+        if (rank0) lcnt[(round + 2) % 3] = 0;
+        for (long long k = warp; k < cnt; k += nw) {
+            const int v = in[k];
+            if (colour_node(v, rp, col, seed, t, round, cr, bm, resume, lcnt + 3) && lane == 0)
+                out[atomicAdd(&lcnt[(round + 1) % 3], 1)] = v;
         }
-        if (lane == 0 && blocked_nodes) atomicAdd(&cnt3[round % 3], blocked_nodes);
         if (!gbar(bar, limit_ns)) return;
-        if (*((volatile int32_t *)&cnt3[round % 3]) == 0) {
+        if (*((volatile int32_t *)&lcnt[(round + 1) % 3]) == 0) {
             if (rank0) *rounds_out = round + 1;
             return;
         }
+    }
+}
+
+// Small graphs (at most kColourSeqMax nodes, so every row is shorter than
+// kColourBits): the first-fit colouring itself, one node after the other in
+// key order, by one block with a bitmap of the node's neighbours' colours.
+// Dense aggregated levels would need about one Jones-Plassmann round per node.
+constexpr int32_t kColourSeqMax = 4096;
+
+__global__ void k_colour_keys(int32_t n, unsigned long long seed, int t, unsigned long long *key,
+                              int32_t *node) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        key[v] = ~colour_key(seed, t, (int)v);  // ascending sort = descending key
+        node[v] = (int32_t)v;
+    }
+}
+
+__global__ void __launch_bounds__(512) k_colour_seq(int32_t n, const int32_t *order, const int32_t *rp,
+                                                    const int32_t *col, long long *cr) {
+    __shared__ unsigned bm[kColourBits / 32];
+    __shared__ int first;
+    for (int k = 0; k < n; k++) {
+        const int v = order[k];
+        const int b = rp[v], e = rp[v + 1];
+        const int words = (e - b) / 32 + 1;  // covers colours 0 .. row length
+        for (int q = threadIdx.x; q < words; q += blockDim.x) bm[q] = 0u;
+        if (threadIdx.x == 0) first = INT_MAX;
+        __syncthreads();
+        for (int p = b + threadIdx.x; p < e; p += blockDim.x) {
+            const int u = col[p];
+            if (u == v) continue;
+            const long long c = cr[u];
+            if (c >= 0 && c < 32LL * words) atomicOr(&bm[c >> 5], 1u << (c & 31));
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < words; q += blockDim.x)
+            if (bm[q] != 0xffffffffu) atomicMin(&first, 32 * q + __ffs((int)~bm[q]) - 1);
+        __syncthreads();
+        if (threadIdx.x == 0) cr[v] = first;
+        __syncthreads();  // the colour is visible to the next node's look
     }
 }
 
@@ -292,25 +406,37 @@ std::vector<int32_t> colour_nodes(int32_t n, const int32_t *rp, const int32_t *c
         vtmp(4 * (size_t)n, st);
     SLM_CUDA(cudaMemsetAsync(cr.get(), 0xff, 8 * (size_t)n, st));
     int32_t *lp = left.as<int32_t>();
-    {
-        // the barrier word and the three round counters
-        DevBuf barm(sizeof(GridBarrier) + 16, st);
+    if (n <= kColourSeqMax) {
+        DevBuf key(8 * (size_t)n, st), ktmp(8 * (size_t)n, st), ord(4 * (size_t)n, st), otmp(4 * (size_t)n, st);
+        k_colour_keys<<<grid_for(n, 256), 256, 0, st>>>(n, seed, level, key.as<unsigned long long>(),
+                                                        ord.as<int32_t>());
+        SLM_LAUNCH_CHECK();
+        radix_sort_u64(key.as<unsigned long long>(), ord.as<int32_t>(), ktmp.as<unsigned long long>(),
+                       otmp.as<int32_t>(), n, 64, st);
+        k_colour_seq<<<1, 512, 0, st>>>(n, ord.as<int32_t>(), rp, col, cr.as<long long>());
+        SLM_LAUNCH_CHECK();
+        SLM_CUDA(cudaMemsetAsync(lp, 0, 8, st));
+    } else {
+        // the barrier word, the three list counters and the largest colour,
+        // the two node lists and the resume offsets
+        DevBuf barm(sizeof(GridBarrier) + 16, st), wl(12 * (size_t)n, st);
         SLM_CUDA(cudaMemsetAsync(barm.get(), 0, sizeof(GridBarrier) + 16, st));
         GridBarrier *bar = barm.as<GridBarrier>();
         int32_t *cnt3 = reinterpret_cast<int32_t *>(bar + 1);
+        int32_t *wl0 = wl.as<int32_t>(), *wl1 = wl0 + n, *resume = wl0 + 2 * (size_t)n;
         int dev = 0, sms = 0, per_sm = 0;
         SLM_CUDA(cudaGetDevice(&dev));
         SLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colour_rounds, 256, 0));
         if (per_sm < 1) fail(SLM_ERR_CUDA, "colouring kernel cannot be resident");
-        // one block per SM: a small dense graph needs many rounds, and the
-        // barrier's cost grows with the blocks
-        const int nb = (int)std::min<long long>((long long)sms, ((long long)n * 32 + 255) / 256);
+        // every resident block while the lists are long (a warp per node),
+        // no more blocks than a warp per node needs
+        const int nb = (int)std::min<long long>((long long)sms * per_sm, ((long long)n * 32 + 255) / 256);
         long long lim = kBarrierLimitNs;
         long long *cr_p = cr.as<long long>();
         int32_t *rounds = lp + 2;
-        void *kargs[] = {&n, (void *)&rp, (void *)&col, &seed, &level, (void *)&cr_p, &bar, &cnt3, &lim,
-                         &rounds};
+        void *kargs[] = {&n, (void *)&rp, (void *)&col, &seed, &level, (void *)&cr_p, &wl0, &wl1, &resume,
+                         &bar, &cnt3, &lim, &rounds};
         serialised_cooperative(st, [&] {
             SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_colour_rounds, dim3(nb), dim3(256), kargs,
                                                  0, st));
