@@ -73,8 +73,55 @@ __global__ void k_compact(long long cnt, const int32_t *list, const int32_t *roo
 }
 
 // warp-aggregated append of the listed nodes whose community is flagged
-__device__ __forceinline__ void d_compact_atomic(int cnt, const int32_t *list, const int32_t *root,
-                                                 const int32_t *flag, int32_t *out, int32_t *count) {
+
+
+// ---------------------------------------------------------------------------
+// one round (phases of the persistent kernel below)
+// ---------------------------------------------------------------------------
+// The set-up of member v at position k of a round's list: new parts (every
+// part in the first round) start their sums from zero, and each community
+// root is listed once with its cycle length and an empty best cut.
+struct RoundInit {
+    const int32_t *ideg, *root, *freshN, *a, *cdist;
+    long long *subS, *subWA, *subWin, *credit, *TS;
+    int32_t *rlist, *posr, *L, *degm;
+    long long *kacc, *bestsc;
+    unsigned long long *bestkey;
+};
+__device__ __forceinline__ void init_member(const RoundInit &I, long long k, int v, bool first, int32_t *rcnt) {
+    const int r = I.root[v];
+    const bool fr = first || I.freshN[r];
+    I.degm[k] = fr ? I.ideg[v] : 0;  // only new parts rescan their entries
+    I.kacc[k] = 0;
+    if (fr) {
+        I.subS[v] = 0;
+        I.subWA[v] = 0;
+        I.subWin[v] = 0;
+        I.credit[v] = 0;
+        I.TS[v] = 0;
+    }
+    if (r == v) {
+        const int q = atomicAdd(rcnt, 1);
+        I.rlist[q] = v;
+        I.posr[v] = q;
+        I.L[q] = (I.a[v] == v) ? 1 : I.cdist[I.a[v]] + 1;  // cycle length of v's community
+        I.bestsc[q] = LLONG_MIN;
+        I.bestkey[q] = ~0ull;
+    }
+}
+
+__device__ __forceinline__ void k_round_init(int cnt, const int32_t *M, const RoundInit &I, bool first,
+                                             int32_t *rcnt) {
+    GRID_STRIDE(k, cnt) init_member(I, k, M[k], first, rcnt);
+}
+
+// The list of the next round from the members of the still-flagged
+// communities (in any order: every reduction of a round is order-free), each
+// kept member set up for that round at its new position as k_round_init
+// would, with its root listed in *rnext.
+__device__ __forceinline__ void d_compact_init(int cnt, const int32_t *list, const int32_t *root,
+                                               const int32_t *flag, int32_t *out, int32_t *count,
+                                               const RoundInit &I, int32_t *rnext) {
     const int lane = threadIdx.x & 31;
     for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < cnt;
          base += (long long)gridDim.x * blockDim.x) {
@@ -89,42 +136,14 @@ __device__ __forceinline__ void d_compact_atomic(int cnt, const int32_t *list, c
         int at = 0;
         if (lane == 0 && bal) at = atomicAdd(count, __popc(bal));
         at = __shfl_sync(0xffffffffu, at, 0);
-        if (keep) out[at + __popc(bal & ((1u << lane) - 1u))] = v;
-    }
-}
-
-
-// ---------------------------------------------------------------------------
-// one round (phases of the persistent kernel below)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void k_round_init(int cnt, const int32_t *M, const int32_t *ideg, const int32_t *root,
-                             const int32_t *freshN, bool first, const int32_t *a,
-                             const int32_t *cdist, long long *subS, long long *subWA,
-                             long long *subWin, long long *credit, long long *TS, int32_t *rlist,
-                             int32_t *rcnt, int32_t *posr, int32_t *L, int32_t *degm,
-                             long long *kacc, long long *bestsc, unsigned long long *bestkey) {
-    GRID_STRIDE(k, cnt) {
-        int v = M[k];
-        const bool fr = first || freshN[root[v]];
-        degm[k] = fr ? ideg[v] : 0;  // only new parts rescan their entries
-        kacc[k] = 0;
-        if (fr) {
-            subS[v] = 0;
-            subWA[v] = 0;
-            subWin[v] = 0;
-            credit[v] = 0;
-            TS[v] = 0;
-        }
-        if (root[v] == v) {
-            int q = atomicAdd(rcnt, 1);
-            rlist[q] = v;
-            posr[v] = q;
-            L[q] = (a[v] == v) ? 1 : cdist[a[v]] + 1;  // cycle length of v's community
-            bestsc[q] = LLONG_MIN;
-            bestkey[q] = ~0ull;
+        if (keep) {
+            const int q = at + __popc(bal & ((1u << lane) - 1u));
+            out[q] = v;
+            init_member(I, q, v, false, rnext);
         }
     }
 }
+
 
 // pool sizes of the first round, padded with zeros to cnt entries so that
 // the offsets can be scanned over the member list's length
@@ -933,7 +952,7 @@ __device__ bool grid_scan(const ScanSlots &S, int n, GridBarrier *bar, long long
 // Control block shared by the host and the persistent kernel.
 struct PosCtrl {
     int32_t cnt;     // members of the current round
-    int32_t R;       // roots of the current round
+    int32_t R[2];    // roots listed for the rounds of parity 0 and 1
     int32_t E;       // member edges of the current round
     int32_t ctot;    // cycle-order pool entries in use
     long long mtot;  // tree-weight pool entries in use
@@ -999,6 +1018,11 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs<NM> A) 
     int cnt = C->cnt;  // members of the first round
     int parity = 0;
     bool first = A.first_round != 0;
+    // the first round of a launch is set up here; every later one by the
+    // compaction that ends the round before it
+    bool need_init = true;
+    const RoundInit RI{A.ideg, A.root, A.freshN, A.a, A.cdist, A.subS, A.subWA, A.subWin, A.credit, A.TS,
+                       A.rlist, A.posr, A.L, A.epref, A.kacc, A.bestsc, A.bestkey};
     for (;;) {
         if (rank0) C->cnt = cnt;
         if (cnt == 0) break;
@@ -1013,17 +1037,23 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs<NM> A) 
             if (rank0) C->error = 1;
             break;
         }
-        if (rank0) C->nextc[parity] = 0;
-        k_round_init(cnt, M, A.ideg, A.root, A.freshN, first, A.a, A.cdist, A.subS, A.subWA, A.subWin,
-                     A.credit, A.TS, A.rlist, &C->R, A.posr, A.L, A.epref, A.kacc, A.bestsc,
-                     A.bestkey);
-        GBAR_OR_RETURN();
+        // this round's roots are counted in R[parity]; R[parity ^ 1], last
+        // read before the previous barrier, takes the next round's
+        int32_t *rcnt = &C->R[parity];
+        if (rank0) {
+            C->nextc[parity] = 0;
+            C->R[parity ^ 1] = 0;
+        }
+        if (need_init) {
+            k_round_init(cnt, M, RI, first, rcnt);
+            GBAR_OR_RETURN();
+        }
         mark_phase(0);
         if (first) {
             // the cycles of every community are laid out once per call: cuts
             // never make a cycle longer, and a part that loses its cycle gets
             // a self-loop, so the layout stays valid for the remainders
-            k_root_pools(cnt, &C->R, A.L, A.msz, A.coff);
+            k_root_pools(cnt, rcnt, A.L, A.msz, A.coff);
             GBAR_OR_RETURN();
             ScanSlots S{A.msz, A.coff, A.epref, &C->mtot, &C->ctot, &C->E, A.bs64, A.bs32a, A.bs32b};
             if (!grid_scan(S, cnt, A.bar, A.barrier_ns)) return;
@@ -1033,7 +1063,7 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs<NM> A) 
                 break;
             }
             const long long mtot = C->mtot, ctot = C->ctot;
-            const int R = C->R;
+            const int R = *rcnt;
             GRID_STRIDE(q, R) {
                 const int r = A.rlist[q];
                 A.moffN[r] = A.msz[q];
@@ -1067,12 +1097,12 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs<NM> A) 
             k_branch<NM>(cnt, M, A.oncycle, A.root, A.posr, A.sigma, A.m, A.subS, A.subWA, A.subWin,
                      A.bestsc, A.bestkey, A.kacc, A.epref, pass);
             if (cycles)
-                k_cycle<NM>(&C->R, A.rlist, A.L, A.coffN, A.cyc, A.moffN, A.Mw, A.Mp, A.TS, A.sigma, A.m, n,
+                k_cycle<NM>(rcnt, A.rlist, A.L, A.coffN, A.cyc, A.moffN, A.Mw, A.Mp, A.TS, A.sigma, A.m, n,
                         A.bestsc, A.bestkey, pass);
             GBAR_OR_RETURN();
         }
         mark_phase(4);
-        k_cut_info<NM>(&C->R, A.rlist, A.bestkey, n, A.L, A.coffN, A.cyc, A.TS, A.depth, A.entry, A.cdist,
+        k_cut_info<NM>(rcnt, A.rlist, A.bestkey, n, A.L, A.coffN, A.cyc, A.TS, A.depth, A.entry, A.cdist,
                    A.subS, A.subWA, A.subWin, A.sigma, A.cut, A.cutsum, A.cutpar, A.freshN, A.a,
                    A.m.gid, A.splits_per_graph);
         GBAR_OR_RETURN();
@@ -1084,7 +1114,7 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs<NM> A) 
                        A.flag);
         GBAR_OR_RETURN();
         mark_phase(6);
-        k_cut_fix(cnt, M, &C->R, A.cut, A.cutsum, A.cutpar, A.oldroot, A.recomp, A.posr, A.root, A.a,
+        k_cut_fix(cnt, M, rcnt, A.cut, A.cutsum, A.cutpar, A.oldroot, A.recomp, A.posr, A.root, A.a,
                   A.depth, A.entry, A.cdist, A.istart, A.ideg, A.icol, A.iw, A.moffN, A.kown, A.subS,
                   A.subWA, A.subWin, A.TS, A.Mw);
         k_own_members(cnt, M, A.recomp, A.istart, A.ideg, A.icol, A.iw, A.root, A.kacc);
@@ -1092,14 +1122,13 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs<NM> A) 
         k_own_finish<NM>(cnt, M, A.s, A.m, A.root, A.sigma, A.kacc, A.recomp, A.kown, A.flag);
         GBAR_OR_RETURN();
         mark_phase(7);
-        // members of the still-flagged communities form the next list (its
-        // order does not matter: every reduction of a round is order-free)
-        d_compact_atomic(cnt, M, A.root, A.flag, M2, &C->nextc[parity]);
+        // members of the still-flagged communities form the next list, set up
+        // for the next round as they are written
+        d_compact_init(cnt, M, A.root, A.flag, M2, &C->nextc[parity], RI, &C->R[parity ^ 1]);
         if (rank0) {
             C->rounds += 1;
             C->visits += cnt;
-            C->splits += C->R;
-            C->R = 0;
+            C->splits += *rcnt;
             if (stamp && gridDim.x > kPosTailBlocks) {
                 C->ph[9] += 1;
                 C->ph[10] += cnt;
@@ -1113,6 +1142,7 @@ __global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs<NM> A) 
         M2 = tmp;
         parity ^= 1;
         first = false;
+        need_init = false;
     }
 }
 
@@ -1455,6 +1485,7 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
         if (hc.list_b) std::swap(A.listA, A.listB);
         hc.handoff = 0;
         hc.bar = GridBarrier{};
+        hc.R[0] = hc.R[1] = 0;  // the next launch sets up its first round afresh
         SLM_CUDA(cudaMemcpyAsync(ps.ctrl.get(), &hc, sizeof hc, cudaMemcpyHostToDevice, st));
     }
     if (hc.bar.failed) fail(SLM_ERR_TIMEOUT, "a POSITIVE grid barrier waited past its time limit");
