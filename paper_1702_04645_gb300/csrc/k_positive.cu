@@ -798,6 +798,8 @@ __device__ __forceinline__ void k_own_finish(int cnt, const int32_t *M, const ty
 // the same length are scanned together.  Ends after a grid barrier.
 // ---------------------------------------------------------------------------
 constexpr int kPosThreads = 256;
+// threads of a one-block tail: every member of a small round gets its own thread
+constexpr int kPosTailThreads = 1024;
 // a POSITIVE call continues on a grid of kPosTailBlocks blocks (by default
 // one block, whose grid barriers are block barriers) once a round has at most
 // kPosTailMembers members and kPosTailEntries internal entries: measured on
@@ -828,7 +830,7 @@ template <class T> __device__ T block_sum(T v, T *red) {
     __syncthreads();
     T t = 0;
     if (threadIdx.x == 0)
-        for (int k = 0; k < kPosThreads / 32; k++) t += red[k];
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[k];
     __syncthreads();
     if (threadIdx.x == 0) red[0] = t;
     __syncthreads();
@@ -848,18 +850,19 @@ template <class T> __device__ T tile_scan(T v, T &excl, T *red) {
     }
     if (lane == 31) red[wid] = x;
     __syncthreads();
+    const int nw = (int)(blockDim.x >> 5);
     if (threadIdx.x == 0) {
         T acc = 0;
-        for (int k = 0; k < kPosThreads / 32; k++) {
+        for (int k = 0; k < nw; k++) {
             T c = red[k];
             red[k] = acc;
             acc += c;
         }
-        red[kPosThreads / 32] = acc;
+        red[nw] = acc;
     }
     __syncthreads();
     excl = red[wid] + x - v;
-    T tot = red[kPosThreads / 32];
+    T tot = red[nw];
     __syncthreads();
     return tot;
 }
@@ -879,8 +882,8 @@ struct ScanSlots {
     } while (0)
 
 __device__ bool grid_scan(const ScanSlots &S, int n, GridBarrier *bar, long long barrier_ns) {
-    __shared__ long long red64[kPosThreads / 32 + 1];
-    __shared__ int32_t red32[kPosThreads / 32 + 1];
+    __shared__ long long red64[33];  // one slot per warp (up to 32) and a total
+    __shared__ int32_t red32[33];
     const int nb = gridDim.x;
     const int chunk = (n + nb - 1) / nb;
     const int lo = min(n, (int)blockIdx.x * chunk), hi = min(n, lo + chunk);
@@ -999,8 +1002,8 @@ struct PosArgs {
 // All rounds of POSITIVE in one cooperative launch: the phases of a round are
 // separated by grid barriers and the loop ends on the device when no member
 // is left.
-template <class NM>
-__global__ void __launch_bounds__(kPosThreads) k_positive_rounds(PosArgs<NM> A) {
+template <class NM, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_positive_rounds(PosArgs<NM> A) {
     const bool rank0 = blockIdx.x == 0 && threadIdx.x == 0;
     PosCtrl *C = A.ctrl;
     int32_t *M = A.listA, *M2 = A.listB;
@@ -1398,7 +1401,12 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
     int dev = 0, sms = 0, per_sm = 0;
     SLM_CUDA(cudaGetDevice(&dev));
     SLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_positive_rounds<NM>, kPosThreads, 0));
+    SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_positive_rounds<NM, kPosThreads>,
+                                                           kPosThreads, 0));
+    // a one-block tail runs with kPosTailThreads threads when that block fits
+    int per_sm_tail = 0;
+    SLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_tail, k_positive_rounds<NM, kPosTailThreads>,
+                                                           kPosTailThreads, 0));
     if (per_sm < 1) fail(SLM_ERR_CUDA, "POSITIVE kernel cannot be resident");
     const int nblocks_full = sms * std::min(per_sm, kPosBlocksPerSM);
     ps.bs.ensure(8 * (size_t)nblocks_full * 3, st);
@@ -1472,10 +1480,15 @@ long long positive_correct(int32_t n, const int32_t *rp, const int32_t *col, con
         A.handoff_cnt = tail ? 0 : kPosTailMembers;
         A.handoff_edges = kPosTailEntries;
         const int nb = tail ? std::min(kPosTailBlocks, nblocks_full) : nblocks_full;
+        const bool wide = nb == 1 && per_sm_tail >= 1;
         void *kargs[] = {&A};
         serialised_cooperative(st, [&] {
-            SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_positive_rounds<NM>, dim3(nb),
-                                                 dim3(kPosThreads), kargs, 0, st));
+            if (wide)
+                SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_positive_rounds<NM, kPosTailThreads>, dim3(1),
+                                                     dim3(kPosTailThreads), kargs, 0, st));
+            else
+                SLM_CUDA(cudaLaunchCooperativeKernel((const void *)k_positive_rounds<NM, kPosThreads>, dim3(nb),
+                                                     dim3(kPosThreads), kargs, 0, st));
             SLM_LAUNCH_CHECK();
         });
         SLM_CUDA(cudaMemcpyAsync(&hc, ps.ctrl.get(), sizeof hc, cudaMemcpyDeviceToHost, st));
