@@ -55,25 +55,26 @@ __device__ __forceinline__ int cyc_index(int v, int r, int l, const int32_t *cdi
 // ---------------------------------------------------------------------------
 // member lists
 // ---------------------------------------------------------------------------
-// mark[k] = 1 when the k-th node (list[k], or k itself when list is null) lies
-// in a flagged community
-__global__ void k_mark(long long cnt, const int32_t *list, const int32_t *root,
-                       const int32_t *flag, int32_t *mark) {
-    GRID_STRIDE(k, cnt) {
-        int v = list ? list[k] : (int)k;
-        mark[k] = flag[root[v]] ? 1 : 0;
+// the listed (or all) nodes of flagged communities, one atomic per warp
+__global__ void k_compact_atomic(long long cnt, const int32_t *list, const int32_t *root,
+                                 const int32_t *flag, int32_t *out, int32_t *count) {
+    const int lane = threadIdx.x & 31;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < cnt;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long k = base + lane;
+        int v = -1;
+        bool keep = false;
+        if (k < cnt) {
+            v = list ? list[k] : (int)k;
+            keep = flag[root[v]] != 0;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        int at = 0;
+        if (lane == 0 && bal) at = atomicAdd(count, __popc(bal));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (keep) out[at + __popc(bal & ((1u << lane) - 1u))] = v;
     }
 }
-__global__ void k_compact(long long cnt, const int32_t *list, const int32_t *root,
-                          const int32_t *flag, const int32_t *pos, int32_t *out) {
-    GRID_STRIDE(k, cnt) {
-        int v = list ? list[k] : (int)k;
-        if (flag[root[v]]) out[pos[k]] = v;
-    }
-}
-
-// warp-aggregated append of the listed nodes whose community is flagged
-
 
 // ---------------------------------------------------------------------------
 // one round (phases of the persistent kernel below)
@@ -1263,17 +1264,18 @@ __global__ void k_pool_bound(int cnt, const int32_t *M, const int32_t *root, con
 }  // namespace
 
 // Member list of the flagged communities: from all nodes (list == nullptr) or
-// from a previous list; returns its length (host-synchronous).
+// from a previous list; returns its length (host-synchronous).  The list's
+// order is that of the warps' atomics: everything that reads a member list
+// (the own weights, COMPONENTS, the rounds of POSITIVE, whose roots are
+// listed by atomics too) is independent of it.
 int32_t compact_members(long long cnt, const int32_t *list, const int32_t *root,
                         const int32_t *flag, int32_t *out, DevBuf &mark, DevBuf &tot,
                         cudaStream_t st) {
+    (void)mark;
     if (cnt <= 0) return 0;
-    mark.ensure(4 * (size_t)cnt, st);
-    const int g = grid_for(cnt, 256);
-    k_mark<<<g, 256, 0, st>>>(cnt, list, root, flag, mark.as<int32_t>());
-    SLM_LAUNCH_CHECK();
-    exclusive_scan_i32(mark.as<int32_t>(), mark.as<int32_t>(), cnt, tot.as<int32_t>(), st);
-    k_compact<<<g, 256, 0, st>>>(cnt, list, root, flag, mark.as<int32_t>(), out);
+    SLM_CUDA(cudaMemsetAsync(tot.get(), 0, sizeof(int32_t), st));
+    k_compact_atomic<<<grid_for(cnt, 256, kNumSMs * 16), 256, 0, st>>>(cnt, list, root, flag, out,
+                                                                       tot.as<int32_t>());
     SLM_LAUNCH_CHECK();
     int32_t h = 0;
     SLM_CUDA(cudaMemcpyAsync(&h, tot.get(), sizeof h, cudaMemcpyDeviceToHost, st));
