@@ -451,10 +451,26 @@ long long strengths(int32_t n, const int32_t *rp, const int32_t *w, int32_t *s_o
 // ---------------------------------------------------------------------------
 // Sigma_C = sum of s over the community named C.
 // ---------------------------------------------------------------------------
+// One add per community and warp: the lanes of a warp that share a community
+// sum their strengths first (a community of a large share of the graph would
+// otherwise take one atomic per member on one address).
 __global__ void k_sigma(int32_t n, const int32_t *root, const int32_t *s, int32_t *sigma) {
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x)
-        if (s[v]) atomicAdd(&sigma[root[v]], s[v]);
+    const int lane = threadIdx.x & 31;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long v = base + lane;
+        int sv = 0, r = 0;
+        if (v < n) {
+            sv = s[v];
+            r = root[v];
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, sv != 0);
+        if (sv != 0) {
+            const unsigned grp = __match_any_sync(act, r);
+            const int sum = __reduce_add_sync(grp, sv);
+            if (lane == __ffs(grp) - 1) atomicAdd(&sigma[r], sum);
+        }
+    }
 }
 
 void community_sigma(int32_t n, const int32_t *root, const int32_t *s, int32_t *sigma,
@@ -466,11 +482,28 @@ void community_sigma(int32_t n, const int32_t *root, const int32_t *s, int32_t *
 }
 
 // packed (out, in) pairs: one 64-bit add sums both components (each stays below 2^30)
+// (the lanes of a warp that share an index add their pairs first)
 __global__ void k_sum_packed(int32_t n, const int32_t *idx, const unsigned long long *s,
                              unsigned long long *out) {
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x)
-        if (s[v]) atomicAdd(&out[idx[v]], s[v]);
+    const int lane = threadIdx.x & 31;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long v = base + lane;
+        unsigned long long sv = 0;
+        int r = 0;
+        if (v < n) {
+            sv = s[v];
+            r = idx[v];
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, sv != 0);
+        if (sv != 0) {
+            const unsigned grp = __match_any_sync(act, r);
+            unsigned long long sum = 0;
+            // 64-bit sum over the group: its lanes read each other's values
+            for (unsigned g = grp; g; g &= g - 1) sum += __shfl_sync(grp, sv, __ffs(g) - 1);
+            if (lane == __ffs(grp) - 1) atomicAdd(&out[r], sum);
+        }
+    }
 }
 
 void community_sigma(int32_t n, const int32_t *root, const unsigned long long *s,
