@@ -221,18 +221,30 @@ __global__ void k_bg_final(int32_t n, const int32_t *a, const uint8_t *oncycle,
 __global__ void k_accept(int32_t n, const long long *bg, RngParam rng, unsigned long long P,
                          int level, int sweep, int32_t *list, int32_t *cnt,
                          unsigned long long *npos, const int32_t *active, int32_t *per_graph) {
+    // the accepted nodes are appended with one atomic per warp (the list's
+    // order is free: every use of it is per node)
+    const int lane = threadIdx.x & 31;
     unsigned loc = 0;
-    GRID_STRIDE(i, n) {
-        if (bg[i] <= 0) continue;
-        const int g = rng.gid ? rng.gid[i] : 0;
-        if (active && !active[g]) continue;
-        loc++;
-        bool acc = (unsigned long long)accept_draw(rng.seed_of((int)i), level, sweep, rng.local((int)i)) < P;
-        if (per_graph) {
-            atomicAdd(&per_graph[2 * g], 1);
-            if (acc) atomicAdd(&per_graph[2 * g + 1], 1);
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long i = base + lane;
+        bool acc = false;
+        if (i < n && bg[i] > 0) {
+            const int g = rng.gid ? rng.gid[i] : 0;
+            if (!active || active[g]) {
+                loc++;
+                acc = (unsigned long long)accept_draw(rng.seed_of((int)i), level, sweep, rng.local((int)i)) < P;
+                if (per_graph) {
+                    atomicAdd(&per_graph[2 * g], 1);
+                    if (acc) atomicAdd(&per_graph[2 * g + 1], 1);
+                }
+            }
         }
-        if (acc) list[atomicAdd(cnt, 1)] = (int)i;
+        const unsigned bal = __ballot_sync(FULL, acc);
+        int at = 0;
+        if (lane == 0 && bal) at = atomicAdd(cnt, __popc(bal));
+        at = __shfl_sync(FULL, at, 0);
+        if (acc) list[at + __popc(bal & ((1u << lane) - 1u))] = (int)i;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) loc += __shfl_xor_sync(FULL, loc, o);
@@ -400,10 +412,20 @@ void branch_gains(int32_t n, const int32_t *rp, const int32_t *col, const int32_
     if (n <= 0) return;
     const int g = grid_for(n, 256);
     const int gw = grid_for((long long)n * 32, 256, kNumSMs * 16);
-    for (int32_t *p : {bs.haschild, bs.active, bs.covered, bs.treeact, bs.commcyc})
-        SLM_CUDA(cudaMemsetAsync(p, 0, sizeof(int32_t) * n, st));
-    for (long long *p : {bs.subS, bs.subWA, bs.subWin, bs.credit, bs.WB})
-        SLM_CUDA(cudaMemsetAsync(p, 0, sizeof(long long) * n, st));
+    // the five int32 and five int64 arrays, one memset each when they lie
+    // back to back (as the per-level workspace lays them out)
+    if (bs.active == bs.haschild + n && bs.covered == bs.active + n && bs.treeact == bs.covered + n &&
+        bs.commcyc == bs.treeact + n)
+        SLM_CUDA(cudaMemsetAsync(bs.haschild, 0, sizeof(int32_t) * 5 * (size_t)n, st));
+    else
+        for (int32_t *p : {bs.haschild, bs.active, bs.covered, bs.treeact, bs.commcyc})
+            SLM_CUDA(cudaMemsetAsync(p, 0, sizeof(int32_t) * n, st));
+    if (bs.subWA == bs.subS + n && bs.subWin == bs.subWA + n && bs.credit == bs.subWin + n &&
+        bs.WB == bs.credit + n)
+        SLM_CUDA(cudaMemsetAsync(bs.subS, 0, sizeof(long long) * 5 * (size_t)n, st));
+    else
+        for (long long *p : {bs.subS, bs.subWA, bs.subWin, bs.credit, bs.WB})
+            SLM_CUDA(cudaMemsetAsync(p, 0, sizeof(long long) * n, st));
     k_haschild<<<g, 256, 0, st>>>(n, a, bs.haschild);
     SLM_LAUNCH_CHECK();
     k_classify<<<g, 256, 0, st>>>(n, a, f.oncycle, f.entry, f.root, bs.haschild, gain, bs.active,
