@@ -10,8 +10,8 @@ LFR-style recipe.
     per-sweep trace, the final labels and Q) with the oracle's runs stored
     under tests/golden/ by tests/golden/make_run_goldens.py (which calls
     only the oracle): the complete run on the R-MAT graph, and bounded runs
-    (3 sweeps per level at 262,144 nodes; level 0 with 2 sweeps at
-    4,194,304) on the LFR-style graphs, where the method does not settle:
+    (3 sweeps per level at 262,144 nodes; 2 sweeps per level, for level 0
+    alone and for three levels, at 4,194,304) on the LFR-style graphs, where the method does not settle:
     after a few sweeps long assignment cycles form, whose cycle cuts cost
     the oracle hours;
   * properties that hold at any size: every level's labels are 0..K-1, the
@@ -155,6 +155,15 @@ def test_louvain_rmat_s20_whole_run_equals_oracle():
 def test_rmat_s20_whole_run_timed_flags_equal():
     """The timed run the benchmark makes (phase timers on) gives the same result."""
     G = compare_with_golden(_rmat(), _golden("rmat_s20"), flags=slm.FLAG_TIMING)
+    G.close()
+
+
+def test_lfr_4m_three_levels_run_equals_oracle():
+    """The 4,194,304-node LFR-style graph through three levels with at most 2
+    sweeps each (ASSIGN, COMPONENTS, POSITIVE and two corrections per level,
+    then AGGREGATE of each level graph) equals the oracle's run, stored
+    after 6,991 s of oracle time."""
+    G = compare_with_golden(_lfr(), _golden("lfr_4m_bounded"))
     G.close()
 
 
