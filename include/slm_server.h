@@ -105,6 +105,17 @@ slm_status slm_server_submit(slm_server *sv, const slm_graph_desc *graph, const 
 slm_status slm_server_submit_deadline(slm_server *sv, const slm_graph_desc *graph,
                                       const slm_options *opt, double deadline_s, uint64_t *ticket);
 
+/* As slm_server_submit_deadline for a directed graph: `graph` holds W as
+ * out-arcs (row i lists the heads of i's arcs, sorted and unique, positive
+ * weights; no symmetry required), run as slm_create_graph_directed and
+ * slm_run run it (the directed Q_w of Section 2.4; the result's modularity
+ * is that Q_w).  Its footprint counts U = W + W^T (at most twice the
+ * entries) and the packed (out, in) strengths.  Errors as
+ * slm_server_submit_deadline; what slm_create_graph_directed refuses
+ * (OVERFLOW included) fails the request at admission. */
+slm_status slm_server_submit_directed(slm_server *sv, const slm_graph_desc *graph,
+                                      const slm_options *opt, double deadline_s, uint64_t *ticket);
+
 /* Cancel a request.  A queued request ends FAILED with SLM_ERR_CANCELLED at
  * once (it never runs); a running one stops before its next level or sweep
  * and ends FAILED with SLM_ERR_CANCELLED (the device work already queued for

@@ -57,7 +57,7 @@ EXPORTS = ["slm_default_options", "slm_create_graph", "slm_create_graph_directed
            "slm_batch_num_graphs", "slm_batch_num_levels", "slm_batch_get_partition",
            "slm_batch_modularity", "slm_batch_get_stats", "slm_batch_run_info",
            "slm_batch_destroy", "slm_batch_last_error", "slm_server_footprint", "slm_server_create",
-           "slm_server_submit", "slm_server_submit_deadline", "slm_server_cancel", "slm_server_poll", "slm_server_wait", "slm_server_request_info",
+           "slm_server_submit", "slm_server_submit_deadline", "slm_server_submit_directed", "slm_server_cancel", "slm_server_poll", "slm_server_wait", "slm_server_request_info",
            "slm_server_result", "slm_server_get_stats", "slm_server_destroy",
            "slm_server_last_error"]
 
@@ -211,6 +211,8 @@ def load():
             "slm_server_submit": (C.c_int, [vp, C.POINTER(GraphDesc), C.POINTER(Options),
                                             C.POINTER(u64)]),
             "slm_server_submit_deadline": (C.c_int, [vp, C.POINTER(GraphDesc), C.POINTER(Options),
+                                                     C.c_double, C.POINTER(u64)]),
+            "slm_server_submit_directed": (C.c_int, [vp, C.POINTER(GraphDesc), C.POINTER(Options),
                                                      C.c_double, C.POINTER(u64)]),
             "slm_server_cancel": (C.c_int, [vp, u64]),
             "slm_server_poll": (C.c_int, [vp, u64, C.POINTER(i32)]),
@@ -554,9 +556,10 @@ class Server:
 
     def submit(self, row_ptr, col, w=None, *, seed: int = 1, accept_p32: int = P_HALF,
                max_sweeps: int = 1000, max_levels: int = 64, flags: int = 0,
-               deadline: float | None = None) -> int:
+               deadline: float | None = None, directed: bool = False) -> int:
         """Queue one graph (host arrays, copied during the call); returns its
-        ticket.  deadline: seconds after submission by which it must end."""
+        ticket.  deadline: seconds after submission by which it must end;
+        directed: the arrays hold W as out-arcs (slm_server_submit_directed)."""
         rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
         cl = np.ascontiguousarray(col, dtype=np.int32)
         ww = None if w is None else np.ascontiguousarray(w, dtype=np.int32)
@@ -564,7 +567,10 @@ class Server:
                       ww.ctypes.data if ww is not None and ww.size else None)
         o = Options(seed, accept_p32, max_sweeps, max_levels, flags)
         t = C.c_uint64()
-        if deadline is None:
+        if directed:
+            self._check(load().slm_server_submit_directed(self._h, C.byref(d), C.byref(o),
+                                                          float(deadline or 0.0), C.byref(t)))
+        elif deadline is None:
             self._check(load().slm_server_submit(self._h, C.byref(d), C.byref(o), C.byref(t)))
         else:
             self._check(load().slm_server_submit_deadline(self._h, C.byref(d), C.byref(o),

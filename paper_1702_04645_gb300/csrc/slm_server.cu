@@ -33,6 +33,7 @@ struct Request {
     int32_t n = 0;
     long long nnz = 0;
     std::vector<int32_t> rp, col, w;  // host copies; w empty = unit weights
+    bool directed = false;            // W as out-arcs (slm_create_graph_directed)
     slm_options opt{};
     uint64_t footprint = 0;
     int32_t state = SLM_REQ_QUEUED;
@@ -83,8 +84,10 @@ thread_local std::string g_server_create_error;
 // the first call that failed.
 slm_status run_request(Request &r, cudaStream_t st) {
     slm_graph *g = nullptr;
-    slm_status s = slm_create_graph(r.n, r.rp.data(), r.col.data(), r.w.empty() ? nullptr : r.w.data(),
-                                    SLM_HOST, st, &g);
+    const int32_t *w = r.w.empty() ? nullptr : r.w.data();
+    slm_status s = r.directed
+                       ? slm_create_graph_directed(r.n, r.rp.data(), r.col.data(), w, SLM_HOST, st, &g)
+                       : slm_create_graph(r.n, r.rp.data(), r.col.data(), w, SLM_HOST, st, &g);
     if (s != SLM_OK) {
         r.err = slm_last_error(nullptr);
         return s;
@@ -264,8 +267,9 @@ slm_status slm_server_submit(slm_server *sv, const slm_graph_desc *gd, const slm
     return slm_server_submit_deadline(sv, gd, opt, 0.0, ticket);
 }
 
-slm_status slm_server_submit_deadline(slm_server *sv, const slm_graph_desc *gd,
-                                      const slm_options *opt, double deadline_s, uint64_t *ticket) {
+namespace {
+slm_status submit_request(slm_server *sv, const slm_graph_desc *gd, const slm_options *opt,
+                          double deadline_s, bool directed, uint64_t *ticket) {
     if (!sv || !gd || !ticket) return SLM_ERR_INVALID_ARGUMENT;
     *ticket = 0;
     if (!(deadline_s >= 0.0)) {  // also refuses NaN
@@ -289,7 +293,11 @@ slm_status slm_server_submit_deadline(slm_server *sv, const slm_graph_desc *gd,
     auto r = std::make_unique<Request>();
     r->n = n;
     r->nnz = nnz;
-    r->footprint = slm_server_footprint(n, nnz);
+    r->directed = directed;
+    // a directed graph runs on U = W + W^T (at most twice the entries) and
+    // keeps its packed (out, in) strengths
+    r->footprint = directed ? slm_server_footprint(n, 2 * nnz) + 8 * ((uint64_t)n + 1)
+                            : slm_server_footprint(n, nnz);
     if (opt) r->opt = *opt;
     else slm_default_options(&r->opt);
     if (r->footprint > sv->budget) {
@@ -320,6 +328,17 @@ slm_status slm_server_submit_deadline(slm_server *sv, const slm_graph_desc *gd,
     sv->submitted++;
     sv->cv_work.notify_all();
     return SLM_OK;
+}
+}  // namespace
+
+slm_status slm_server_submit_deadline(slm_server *sv, const slm_graph_desc *gd,
+                                      const slm_options *opt, double deadline_s, uint64_t *ticket) {
+    return submit_request(sv, gd, opt, deadline_s, false, ticket);
+}
+
+slm_status slm_server_submit_directed(slm_server *sv, const slm_graph_desc *gd,
+                                      const slm_options *opt, double deadline_s, uint64_t *ticket) {
+    return submit_request(sv, gd, opt, deadline_s, true, ticket);
 }
 
 slm_status slm_server_poll(slm_server *sv, uint64_t ticket, int32_t *state) {

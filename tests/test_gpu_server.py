@@ -273,3 +273,34 @@ def test_destroy_while_threads_wait():
         x.join(timeout=120.0)
         assert not x.is_alive()
     assert sorted(done) == [0, 0, 0]
+
+
+def test_directed_requests_equal_directed_runs():
+    """Directed requests (slm_server_submit_directed: W as out-arcs, the
+    directed Q_w) mixed with undirected ones on four slots: each equals the
+    same graph run alone, which equals the directed oracle."""
+    dig = [gg.random_directed(300 + 90 * k, 0.03, 70 + k, wmax=4, loops=0.1, recip=0.3)
+           for k in range(4)]
+    dig.append(gg.lfr_directed(5000, 0.5, 0.4)[0])
+    solo_d = []
+    for k, g in enumerate(dig):
+        G = slm.Graph(g.row_ptr, g.col, g.w, directed=True)
+        G.run(seed=20 + k, accept_p32=slm.P_HALF)
+        solo_d.append((G.partition(-1), G.modularity(-1)))
+        G.close()
+    r = O.directed_slm(dig[0], seed=20, P=O.P_HALF)
+    assert np.array_equal(solo_d[0][0][0], r.final)
+    sv = slm.Server(budget_bytes=8 << 30, slots=4)
+    td = [sv.submit(g.row_ptr, g.col, g.w, seed=20 + k, accept_p32=slm.P_HALF, directed=True)
+          for k, g in enumerate(dig)]
+    tu = [sv.submit(g.row_ptr, g.col, g.w, seed=sd, accept_p32=p) for g, sd, p in REQS[:4]]
+    for t in td + tu:
+        assert sv.wait(t, timeout=120.0)
+    # a directed request is costed for U = W + W^T and its packed strengths
+    g = dig[-1]
+    assert sv.info(td[-1]).footprint == slm.load().slm_server_footprint(g.n, 2 * g.nnz) + 8 * (g.n + 1)
+    for t, ((lab0, K0), q0) in zip(td, solo_d):
+        assert sv.info(t).state == slm.REQ_DONE
+        lab, K, q = sv.result(t)
+        assert K == K0 and q == q0 and np.array_equal(lab, lab0)
+    sv.close()
