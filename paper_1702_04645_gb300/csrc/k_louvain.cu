@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(256) k_colour_rounds(int32_t n, const int32_t 
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const bool rank0 = blockIdx.x == 0 && threadIdx.x == 0;
     __shared__ unsigned bitmaps[256 / 32][kColourBits / 32];
+    __shared__ int keep[256 / 32][32];
     unsigned *bm = bitmaps[threadIdx.x >> 5];
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (long long)gridDim.x * blockDim.x)
@@ -177,10 +178,32 @@ __global__ void __launch_bounds__(256) k_colour_rounds(int32_t n, const int32_t 
         int32_t *out = (round & 1) ? wl0 : wl1;
         const int32_t cnt = *((volatile int32_t *)&lcnt[round % 3]);
         if (rank0) lcnt[(round + 2) % 3] = 0;
+        // the nodes left uncoloured are gathered per warp and appended 32 at
+        // a time, one atomic for each
+        int nbuf = 0;
+        int *buf = keep[threadIdx.x >> 5];
         for (long long k = warp; k < cnt; k += nw) {
             const int v = in[k];
-            if (colour_node(v, rp, col, seed, t, round, cr, bm, resume, lcnt + 3) && lane == 0)
-                out[atomicAdd(&lcnt[(round + 1) % 3], 1)] = v;
+            if (colour_node(v, rp, col, seed, t, round, cr, bm, resume, lcnt + 3)) {
+                if (lane == 0) buf[nbuf] = v;
+                if (++nbuf == 32) {
+                    __syncwarp();
+                    int at = 0;
+                    if (lane == 0) at = atomicAdd(&lcnt[(round + 1) % 3], 32);
+                    at = __shfl_sync(0xffffffffu, at, 0);
+                    out[at + lane] = buf[lane];
+                    __syncwarp();
+                    nbuf = 0;
+                }
+            }
+        }
+        if (nbuf > 0) {
+            __syncwarp();
+            int at = 0;
+            if (lane == 0) at = atomicAdd(&lcnt[(round + 1) % 3], nbuf);
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (lane < nbuf) out[at + lane] = buf[lane];
+            __syncwarp();
         }
         if (!gbar(bar, limit_ns)) return;
         if (*((volatile int32_t *)&lcnt[(round + 1) % 3]) == 0) {
