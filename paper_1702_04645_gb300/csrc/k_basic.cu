@@ -765,9 +765,13 @@ long long forest_check_and_weights(int32_t n, const int32_t *rp, const int32_t *
 }
 
 __global__ void k_roots_per_graph(int32_t n, const int32_t *root, const int32_t *gid, int32_t *Kg) {
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x)
-        if (root[v] == v) atomicAdd(&Kg[gid[v]], 1);
+    const int lane = threadIdx.x & 31;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long v = base + lane;
+        const bool isroot = v < n && root[v] == v;
+        warp_count(Kg, isroot ? gid[v] : 0, isroot);
+    }
 }
 
 void roots_per_graph(int32_t n, const int32_t *root, const int32_t *gid, int32_t *Kg,
@@ -779,12 +783,18 @@ void roots_per_graph(int32_t n, const int32_t *root, const int32_t *gid, int32_t
 
 __global__ void k_cands_per_graph(int32_t n, const int32_t *gid, const int32_t *active,
                                   long long *gain, int32_t *cand_g) {
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x) {
-        if (gain[v] <= 0) continue;
-        const int g = gid[v];
-        if (!active[g]) gain[v] = 0;  // a graph that stopped keeps its partition
-        else atomicAdd(&cand_g[g], 1);
+    const int lane = threadIdx.x & 31;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long v = base + lane;
+        int g = 0;
+        bool cand = false;
+        if (v < n && gain[v] > 0) {
+            g = gid[v];
+            if (!active[g]) gain[v] = 0;  // a graph that stopped keeps its partition
+            else cand = true;
+        }
+        warp_count(cand_g, g, cand);
     }
 }
 

@@ -228,17 +228,19 @@ __global__ void k_accept(int32_t n, const long long *bg, RngParam rng, unsigned 
     for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < n;
          base += (long long)gridDim.x * blockDim.x) {
         const long long i = base + lane;
-        bool acc = false;
+        bool acc = false, cand = false;
+        int g = 0;
         if (i < n && bg[i] > 0) {
-            const int g = rng.gid ? rng.gid[i] : 0;
+            g = rng.gid ? rng.gid[i] : 0;
             if (!active || active[g]) {
+                cand = true;
                 loc++;
                 acc = (unsigned long long)accept_draw(rng.seed_of((int)i), level, sweep, rng.local((int)i)) < P;
-                if (per_graph) {
-                    atomicAdd(&per_graph[2 * g], 1);
-                    if (acc) atomicAdd(&per_graph[2 * g + 1], 1);
-                }
             }
+        }
+        if (per_graph) {  // uniform over the launch
+            warp_count(per_graph, 2 * g, cand);
+            warp_count(per_graph, 2 * g + 1, acc);
         }
         const unsigned bal = __ballot_sync(FULL, acc);
         int at = 0;

@@ -586,6 +586,16 @@ int32_t compact_names(int32_t n, const int32_t *comm, int32_t *id, int32_t *scra
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------
+// Adds, for every lane with `pred`, one to ctr[g]: one atomic per distinct g
+// in the warp.  Every lane of the warp must call it.
+__device__ __forceinline__ void warp_count(int32_t *ctr, int g, bool pred) {
+    const unsigned act = __ballot_sync(0xffffffffu, pred);
+    if (pred) {
+        const unsigned grp = __match_any_sync(act, g);
+        if ((int)(threadIdx.x & 31) == __ffs((int)grp) - 1) atomicAdd(&ctr[g], __popc(grp));
+    }
+}
+
 // splitmix64 output function (Steele, Lea, Flood 2014).
 __host__ __device__ inline unsigned long long mix64(unsigned long long z) {
     z += 0x9E3779B97F4A7C15ull;
