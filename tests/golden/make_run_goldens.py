@@ -4,9 +4,9 @@ Usage: python tests/golden/make_run_goldens.py [case ...]   (all cases by defaul
 
 Each case regenerates a seeded graph with ``graphgen`` and runs the CPU oracle
 on it, single-threaded: ``oracle.slm`` (Algorithm 1 with ASSIGN, POSITIVE and
-MAXIMAL as the oracle restates them), or for the comparison method
-``oracle.louvain_colour`` (colour-synchronous Louvain); nothing here touches
-the CUDA library.
+MAXIMAL as the oracle restates them), ``oracle.directed_slm`` (the same on a
+directed graph), or for the comparison method ``oracle.louvain_colour``
+(colour-synchronous Louvain); nothing here touches the CUDA library.
 The result goes to ``tests/golden/run_<case>.json``:
 
   graph    n, nnz, m_w and SHA-256 digests of row_ptr, col and w (int32,
@@ -66,6 +66,9 @@ CASES = {
                       "LFR-style 4,194,304 nodes (seed 3), level 0 only, at most 2 sweeps"),
     "lfr_256k_bounded": (_lfr_256k, dict(seed=1, P=O.P_HALF, max_sweeps=3),
                          "LFR-style 262,144 nodes (seed 3), at most 3 sweeps per level, every level"),
+    "lfr_directed_1e4_high_mixing": (lambda: gg.lfr_directed(10000, 0.8, 0.7)[0], dict(seed=3, P=O.P_HALF),
+                                     "directed weighted LFR-style, 10,000 nodes, (mu_t, mu_w) = (0.8, 0.7), "
+                                     "complete run (directed Q_w)", "directed_slm"),
     "louvain_rmat_s20": (_rmat_s20, dict(seed=1),
                          "colour-synchronous Louvain on R-MAT scale 20 (seed 2), colouring seed 1, "
                          "complete run", "louvain_colour"),
@@ -89,7 +92,7 @@ def make(case: str) -> dict:
     t0 = time.time()
     r = getattr(O, method)(g, **opts)
     dt = time.time() - t0
-    q = O.modularity(g, r.final)
+    q = (O.directed_modularity if method == "directed_slm" else O.modularity)(g, r.final)
     levels = []
     for (ids, K), st in zip(r.levels, r.stats):
         levels.append({"n": int(ids.shape[0]), "K": int(K), "ids": sha(ids), "stats": list(st)})

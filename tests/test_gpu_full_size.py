@@ -107,7 +107,7 @@ def compare_with_golden(g, gold, **run_kw):
     assert (g.n, g.nnz) == (fp["n"], fp["nnz"]), "the generator no longer makes the stored graph"
     assert _sha(g.row_ptr) == fp["row_ptr"] and _sha(g.col) == fp["col"] and _sha(g.w) == fp["w"]
     opts = gold["options"]
-    G = slm.Graph(g.row_ptr, g.col, g.w)
+    G = slm.Graph(g.row_ptr, g.col, g.w, directed=gold.get("method") == "directed_slm")
     if gold.get("method", "slm") == "louvain_colour":
         G.run_louvain(seed=opts["seed"], max_passes=opts.get("max_passes", 1000),
                       max_levels=opts.get("max_levels", 64), **run_kw)
@@ -141,6 +141,17 @@ def test_rmat_s20_whole_run_equals_oracle():
     the touched-set COMPONENTS and POSITIVE passes and AGGREGATE at the size
     where their thresholds switch."""
     G = compare_with_golden(_rmat(), _golden("rmat_s20"))
+    G.close()
+
+
+def test_directed_lfr_high_mixing_whole_run_equals_oracle():
+    """The directed weighted LFR-style graph of 10,000 nodes at the paper's
+    highest mixing pair (0.8, 0.7), a whole run with the default limits: level
+    0 stops at the 1,000-sweep limit (long assignment cycles, tens of
+    thousands of POSITIVE rounds), then two more levels; every sweep equals
+    the directed oracle's, stored after 697 s of oracle time."""
+    g, _ = gg.lfr_directed(10000, 0.8, 0.7)
+    G = compare_with_golden(g, _golden("lfr_directed_1e4_high_mixing"))
     G.close()
 
 
