@@ -388,6 +388,14 @@ __global__ void __launch_bounds__(256) k_louvain_decide(const int32_t *list, int
     }
 }
 
+__global__ void k_class_max_row(int32_t n, const int32_t *rp, const int32_t *colour, int32_t *mx) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int d = rp[v + 1] - rp[v];
+        if (d > 0) atomicMax(&mx[colour[v]], d);
+    }
+}
+
 __global__ void k_max_row(int32_t n, const int32_t *rp, int32_t *mx) {
     int d = 0;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -499,6 +507,19 @@ int32_t max_row_length(int32_t n, const int32_t *rp, cudaStream_t st) {
     SLM_LAUNCH_CHECK();
     int32_t h = 0;
     SLM_CUDA(cudaMemcpyAsync(&h, mx.get(), sizeof h, cudaMemcpyDeviceToHost, st));
+    stream_sync(st);
+    return h;
+}
+
+std::vector<int32_t> class_max_rows(int32_t n, const int32_t *rp, const int32_t *colour, int32_t ncol,
+                                    cudaStream_t st) {
+    std::vector<int32_t> h((size_t)(ncol > 0 ? ncol : 0), 0);
+    if (n <= 0 || ncol <= 0) return h;
+    DevBuf mx(4 * (size_t)ncol, st);
+    SLM_CUDA(cudaMemsetAsync(mx.get(), 0, 4 * (size_t)ncol, st));
+    k_class_max_row<<<grid_for(n, 256), 256, 0, st>>>(n, rp, colour, mx.as<int32_t>());
+    SLM_LAUNCH_CHECK();
+    SLM_CUDA(cudaMemcpyAsync(h.data(), mx.get(), 4 * (size_t)ncol, cudaMemcpyDeviceToHost, st));
     stream_sync(st);
     return h;
 }

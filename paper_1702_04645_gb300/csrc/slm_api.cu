@@ -351,8 +351,8 @@ void run_impl(slm_graph *g, const slm_options &opt, cudaStream_t st) {
 // can undo one another's gains, so passes need not settle), or at the pass
 // limit (status 2); levels then compact in name order and aggregate as the
 // method's do.
-// levels of at most this many nodes decide their colour classes node by node
-constexpr int32_t kLouvainDirectMaxNodes = 65536;
+// colour classes of at most this many nodes may decide node by node
+constexpr int32_t kLouvainDirectMaxClass = 8192;
 
 void louvain_impl(slm_graph *g, unsigned long long seed, int max_passes, int max_levels,
                   cudaStream_t st) {
@@ -384,14 +384,16 @@ void louvain_impl(slm_graph *g, unsigned long long seed, int max_passes, int max
         const std::vector<int32_t> coff = slm::colour_nodes(n, rp, col, seed, t, colour.as<int32_t>(),
                                                             order.as<int32_t>(), st);
         const int ncol = (int)coff.size() - 1;
-        // A small level (an aggregated graph: few nodes, long rows, hundreds
-        // of colours of a few nodes each) decides each class node by node,
-        // one block per node; a large one gets one scan layout per colour
-        // class, all on one stream and one (community, total) array.
-        const int32_t max_row = slm::max_row_length(n, rp, st);
-        const bool direct = n <= kLouvainDirectMaxNodes && max_row <= slm::kLouvainDecideMaxRow;
-        std::vector<std::unique_ptr<slm::Buckets>> cls(direct ? 0 : ncol);
-        for (int k = 0; k < (int)cls.size(); k++) {
+        // A colour class of at most kLouvainDirectMaxClass nodes whose rows
+        // all have at most kLouvainDecideMaxRow entries decides node by node,
+        // one block per node (two launches per class and pass); a larger class,
+        // or one with longer rows (hubs), gets its own scan layout, all of them
+        // on one stream and one (community, total) array.
+        const std::vector<int32_t> cls_max = slm::class_max_rows(n, rp, colour.as<int32_t>(), ncol, st);
+        std::vector<std::unique_ptr<slm::Buckets>> cls(ncol);
+        for (int k = 0; k < ncol; k++) {
+            if (coff[k + 1] - coff[k] <= kLouvainDirectMaxClass && cls_max[k] <= slm::kLouvainDecideMaxRow)
+                continue;
             cls[k].reset(new slm::Buckets());
             cls[k]->one_stream = true;
             cls[k]->cs_shared = &cs_all;
@@ -410,9 +412,9 @@ void louvain_impl(slm_graph *g, unsigned long long seed, int max_passes, int max
             slm::check_run_control();
             SLM_CUDA(cudaMemsetAsync(ctr.get(), 0, 64, st));
             for (int k = 0; k < ncol; k++) {
-                if (direct)
+                if (!cls[k])
                     slm::louvain_decide(order.as<int32_t>() + coff[k], coff[k + 1] - coff[k], rp, col, w, s, m,
-                                        comm.as<int32_t>(), sigma.as<int32_t>(), max_row, best.as<int32_t>(), st);
+                                        comm.as<int32_t>(), sigma.as<int32_t>(), cls_max[k], best.as<int32_t>(), st);
                 else
                     slm::scan_nodes<slm::NMSym>(n, rp, col, w, s, m, comm.as<int32_t>(), sigma.as<int32_t>(),
                                                 *cls[k], best.as<int32_t>(), gain.as<long long>(),

@@ -564,6 +564,9 @@ std::vector<int32_t> colour_nodes(int32_t n, const int32_t *rp, const int32_t *c
                                   int32_t *order, cudaStream_t st);
 // the longest row of the n-node graph (host-synchronous)
 int32_t max_row_length(int32_t n, const int32_t *rp, cudaStream_t st);
+// per colour class (colour[v] in [0, ncol)) its longest row (host-synchronous)
+std::vector<int32_t> class_max_rows(int32_t n, const int32_t *rp, const int32_t *colour, int32_t ncol,
+                                    cudaStream_t st);
 // The MAXIMAL scan's decision (best[i]) for the cnt listed nodes, one block
 // per node with a shared-memory table: for graphs whose rows have at most
 // kLouvainDecideMaxRow entries (the table holds 2^kLouvainDecideMaxLg slots).

@@ -82,10 +82,10 @@ def test_louvain_rmat_hubs():
 
 
 def test_louvain_rmat_layout_path():
-    """R-MAT scale 17 (131,072 nodes): level 0 is above the size where the
-    colour classes are decided node by node, so every class runs the MAXIMAL
-    scan on its own bucketed layout; the aggregated levels take the direct
-    decision."""
+    """R-MAT scale 17 (131,072 nodes): the large colour classes of level 0
+    (more than 8,192 nodes) and the classes holding hub rows run the MAXIMAL
+    scan on their own bucketed layouts, the others take the direct decision,
+    one block per node."""
     g = gg.rmat(17, seed=2)
     compare_louvain(g, seed=4)
 
