@@ -43,10 +43,9 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 # DRAM bytes (read + write) of one level-0 scan of the benchmark graph: the
 # sum over the scan's kernels of an ncu capture (one launch each, serialised,
-# caches kept warm between them as in a run: --cache-control none; 465.5 MB
-# with the caches flushed before each kernel); None once the scan kernels
-# change after that capture
-SCAN_TRAFFIC_L0 = 420.0e6
+# caches kept warm between them as in a run: --cache-control none), taken on
+# the scan kernels as they stand; None once they change after that capture
+SCAN_TRAFFIC_L0 = 418.8e6
 
 
 def scan_bytes(n: int, nnz: int) -> int:

@@ -361,9 +361,8 @@ __global__ void __launch_bounds__(256) k_fs_thread(FsArgs<NM> A) {
 // table of 2 L EPL slots per node in shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kFsWarps = 8;  // warps per block of the lane-group shape
-
 template <class NM, int L, int EPL>
-__global__ void __launch_bounds__(kFsWarps * 32) k_fs_lanes(FsArgs<NM> A) {
+__device__ __forceinline__ void fs_lanes_body(const FsArgs<NM> &A) {
     constexpr int NPW = 32 / L;
     constexpr int CAP = 2 * L * EPL;
     constexpr int LG = __builtin_ctz(CAP);
@@ -431,6 +430,28 @@ __global__ void __launch_bounds__(kFsWarps * 32) k_fs_lanes(FsArgs<NM> A) {
         __syncwarp();
     }
     fs_count(A.ncand, cand);
+}
+
+// The undirected kernels are compiled for SLM_FS_LANES_MIN_BLOCKS resident
+// blocks per SM: 4 holds the 8-entry shape (32 lanes) at 64 registers without
+// spills, where it would take 74 and fit three blocks.  The directed records
+// are twice as wide and would spill at 64 registers, so the directed kernels
+// keep the compiler's own choice (no minimum).
+#ifndef SLM_FS_LANES_MIN_BLOCKS
+#define SLM_FS_LANES_MIN_BLOCKS 4
+#endif
+template <class NM, int L, int EPL>
+__global__ void __launch_bounds__(kFsWarps * 32, SLM_FS_LANES_MIN_BLOCKS) k_fs_lanes(FsArgs<NM> A) {
+    fs_lanes_body<NM, L, EPL>(A);
+}
+template <class NM, int L, int EPL>
+__global__ void __launch_bounds__(kFsWarps * 32) k_fs_lanes_wide(FsArgs<NM> A) {
+    fs_lanes_body<NM, L, EPL>(A);
+}
+template <class NM, int L, int EPL>
+constexpr auto lanes_kernel() {
+    if constexpr (NM::kDirected) return &k_fs_lanes_wide<NM, L, EPL>;
+    else return &k_fs_lanes<NM, L, EPL>;
 }
 
 // ---------------------------------------------------------------------------
@@ -581,32 +602,32 @@ void scan_fine_class(int f, const Buckets &bk, const typename NM::ST *s, MParam 
     static std::atomic<unsigned long long> d1{0}, d2{0};
     switch (f) {
     case kFine4:
-        if (alt) lanes(k_fs_lanes<NM, 4, 1>, 4, tu.blocks_group);
+        if (alt) lanes(lanes_kernel<NM, 4, 1>(), 4, tu.blocks_group);
         else k_fs_thread<NM, 4><<<fs_grid(A.cnt, 256, tu.blocks_group), 256, 0, so>>>(A);
         break;
     case kFine8:
-        if (alt) lanes(k_fs_lanes<NM, 8, 1>, 8, tu.blocks_group);
+        if (alt) lanes(lanes_kernel<NM, 8, 1>(), 8, tu.blocks_group);
         else k_fs_thread<NM, 8><<<fs_grid(A.cnt, 256, tu.blocks_group), 256, 0, so>>>(A);
         break;
     case kFine16:
-        if (alt) lanes(k_fs_lanes<NM, 8, 2>, 8, tu.blocks_group);
-        else lanes(k_fs_lanes<NM, 4, 4>, 4, tu.blocks_group);
+        if (alt) lanes(lanes_kernel<NM, 8, 2>(), 8, tu.blocks_group);
+        else lanes(lanes_kernel<NM, 4, 4>(), 4, tu.blocks_group);
         break;
     case kFine32:
-        if (alt) lanes(k_fs_lanes<NM, 16, 2>, 16, tu.blocks_group);
-        else lanes(k_fs_lanes<NM, 8, 4>, 8, tu.blocks_group);
+        if (alt) lanes(lanes_kernel<NM, 16, 2>(), 16, tu.blocks_group);
+        else lanes(lanes_kernel<NM, 8, 4>(), 8, tu.blocks_group);
         break;
     case kFine64:
-        if (alt) lanes(k_fs_lanes<NM, 32, 2>, 32, tu.blocks_warp);
-        else lanes(k_fs_lanes<NM, 16, 4>, 16, tu.blocks_warp);
+        if (alt) lanes(lanes_kernel<NM, 32, 2>(), 32, tu.blocks_warp);
+        else lanes(lanes_kernel<NM, 16, 4>(), 16, tu.blocks_warp);
         break;
     case kFine128:
         if (alt) block(k_fs_block<NM, 64, 2>, 64, fs_block_smem<64, 2>(), d1, 4 * tu.blocks_warp);
-        else lanes(k_fs_lanes<NM, 32, 4>, 32, tu.blocks_warp);
+        else lanes(lanes_kernel<NM, 32, 4>(), 32, tu.blocks_warp);
         break;
     case kFine256:
         if (alt) block(k_fs_block<NM, 64, 4>, 64, fs_block_smem<64, 4>(), d1, 4 * tu.blocks_warp);
-        else lanes(k_fs_lanes<NM, 32, 8>, 32, tu.blocks_warp);
+        else lanes(lanes_kernel<NM, 32, 8>(), 32, tu.blocks_warp);
         break;
     case kFine512:
         if (alt) block(k_fs_block<NM, 256, 2>, 256, fs_block_smem<256, 2>(), d1, tu.blocks_small);
